@@ -1,0 +1,357 @@
+"""Plain FP64 CPU oracle for the spectral D-bar CGO solve.
+
+TEST INFRASTRUCTURE ONLY.  This module is imported by ``tests/``,
+``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py``; the
+product path (the CUDA library and its Python binding) never imports, calls
+or links it, and it shares no code with that path.  It is deliberately slow
+and written step by step in the paper's order so that each line can be
+checked against the text by eye.
+
+Reference: C. Klein, K. McLaughlin, "Spectral approach to D-bar problems"
+(arXiv 1508.02363).
+
+What it computes (paper notation):
+
+* CGO problem (Sec. 1, eq:038/eq:039): m = psi e^{-kz} - 1 solves
+  dbar m = 1/2 E_k Q (conj(m) + 1),  E_k = e^{conj(kz) - kz}.
+* Fourier convention (Sec. 1): F f = (1/2pi) int f e^{-i xi.x};
+  F^{-1} has the same 1/2pi.  xi = xi1 + i xi2 is complex.
+* Unknown S = xi m^ (eq:042) solves (eq:MainEQa, Sec. 5.1 eq:MainEQDS)
+  A S := S + i F(E_k Q conj(F^{-1}(S/xi))) = b := -i F(E_k Q).
+* Regularisation (Sec. 4.2, eq. Sreg, Gchoice, fourreeg4, fourreg5,
+  fourreg5a): G = e^{-|xi|^2} sum_{n<=M} c_n conj(xi)^n with
+  n! c_n = (-i/2)^n F(z^n F^{-1} S)(0), and
+  F^{-1}(G/xi) = sum c_n W_n, W_n = F^{-1}(conj(xi)^n/xi e^{-|xi|^2}).
+* The algorithm of Sec. 4.3 (for k = 0, used with Q -> E_k Q for k != 0 as
+  in Sec. 5.1): GMRES on the stacked real and imaginary parts, each matrix
+  application doing (a) Taylor coefficients via one inverse FFT and a
+  summation at xi = 0, (b) G and sum c_n W_n, (c) h = F^{-1}((S-G)/xi) +
+  sum c_n W_n, (d) A S = S + i F(E_k Q conj(h)): three 2-D FFTs.
+
+Discretisation (Sec. 4.1, eq. domain, xidomain):
+  x_j = L(-pi + 2 pi j/N), xi_m = m/L with m in [-N/2+1, N/2] (Nyquist on
+  the positive side).  With h = 2 pi L/N the Riemann sums give
+    F_d f(xi_m)      = (2 pi L^2/N^2) (-1)^{m1+m2} DFT(f)[m mod N],
+    F_d^{-1} g(x_j)  = (1/(2 pi L^2)) IDFT((-1)^{m1+m2} g)[j],
+  with DFT = sum_j f_j e^{-2 pi i m.j/N} and IDFT unnormalised (e^{+}), so
+  F_d^{-1} F_d = identity.
+
+Readings where the paper is silent or misprinted (each pinned by a test):
+
+* The grid contains xi = 0, where (S-G)/xi has a removable singularity.
+  The value used there is the analytic limit d = dS/dxi(0)
+  = (-i/2) F(conj(z) F^{-1} S)(0) ("analytic" fill); "zero" fill (the
+  first-order rule of the prior method the paper reviews in Sec. 2) is
+  kept as an option.
+* The printed series form eq. fourreg5a lacks the factor e^{-|z|^2/4};
+  the series used here carries it (it then equals the closed form
+  eq. fourreg5 identically).
+* The test problem eq. dbartest has prefactor 1/a, not a.
+* GMRES restart length, orthogonalisation and starting guess are not
+  stated: restarted GMRES with modified Gram-Schmidt, x0 = 0, relative
+  2-norm of the stacked real residual.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+# ---------------------------------------------------------------------------
+# The oracle's own FFT: iterative radix-2 decimation in time, unnormalised.
+# ---------------------------------------------------------------------------
+
+
+def _bit_reverse(N: int) -> np.ndarray:
+    nbits = N.bit_length() - 1
+    idx = np.arange(N)
+    rev = np.zeros(N, dtype=np.int64)
+    for b in range(nbits):
+        rev |= ((idx >> b) & 1) << (nbits - 1 - b)
+    return rev
+
+
+def dft_last_axis(x: np.ndarray, sign: int) -> np.ndarray:
+    """sum_j x_j exp(sign * 2 pi i j p / N) along the last axis (N a power of 2).
+
+    Radix-2 DIT: bit-reverse, then log2 N butterfly sweeps; the sub-DFT pair
+    (E, O) of length m combines to X[p] = E[p] + w^p O[p],
+    X[p+m] = E[p] - w^p O[p], w = exp(sign * i pi / m).
+    """
+    x = np.asarray(x, dtype=np.complex128)
+    N = x.shape[-1]
+    if N < 1 or (N & (N - 1)):
+        raise ValueError("length must be a power of two")
+    lead = x.shape[:-1]
+    y = x[..., _bit_reverse(N)]
+    m = 1
+    while m < N:
+        w = np.exp(sign * 1j * np.pi * np.arange(m) / m)
+        y = y.reshape(lead + (N // (2 * m), 2, m))
+        a = y[..., 0, :]
+        b = y[..., 1, :] * w
+        y = np.stack([a + b, a - b], axis=-2).reshape(lead + (N,))
+        m *= 2
+    return y
+
+
+def dft2(f: np.ndarray, sign: int) -> np.ndarray:
+    """2-D unnormalised DFT over the last two axes ([..., y, x])."""
+    g = dft_last_axis(f, sign)
+    g = np.swapaxes(dft_last_axis(np.swapaxes(g, -1, -2), sign), -1, -2)
+    return g
+
+
+# ---------------------------------------------------------------------------
+# Grid and discrete transforms (Sec. 4.1, eq. domain / xidomain).
+# ---------------------------------------------------------------------------
+
+
+class Grid:
+    def __init__(self, N: int, L: float):
+        if N < 2 or (N & (N - 1)):
+            raise ValueError("N must be a power of two")
+        self.N, self.L = N, float(L)
+        j = np.arange(N)
+        x1 = L * (-np.pi + 2.0 * np.pi * j / N)            # x_j
+        m = np.where(j <= N // 2, j, j - N)                 # wavenumber index of DFT slot p
+        xi1 = m / L                                         # xi_m = m/L
+        self.x1d, self.xi1d = x1, xi1
+        self.X, self.Y = np.meshgrid(x1, x1, indexing="xy")  # [y][x]
+        self.z = self.X + 1j * self.Y
+        XI1, XI2 = np.meshgrid(xi1, xi1, indexing="xy")
+        self.xi = XI1 + 1j * XI2                            # complex xi = xi1 + i xi2
+        sgn1 = np.where(m % 2 == 0, 1.0, -1.0)
+        self.sign = np.outer(sgn1, sgn1)                    # (-1)^{m1+m2}
+        self.fwd_scale = 2.0 * np.pi * L * L / (N * N)
+        self.inv_scale = 1.0 / (2.0 * np.pi * L * L)
+
+    def F(self, f):
+        """F_d f on the xi-grid (Riemann sum of the Sec. 1 transform)."""
+        return self.fwd_scale * self.sign * dft2(f, -1)
+
+    def Finv(self, g):
+        """F_d^{-1} g on the x-grid."""
+        return self.inv_scale * dft2(self.sign * g, +1)
+
+    def F_at0(self, f):
+        """F_d f at xi = 0: the transform reduces to a summation there (Sec. 4.3 remark)."""
+        return self.fwd_scale * np.sum(f, axis=(-2, -1))
+
+    def E(self, k: complex):
+        """E_k = exp(conj(k z) - k z) = exp(-2i (k2 x + k1 y)) (eq:039)."""
+        return np.exp(np.conj(k * self.z) - k * self.z)
+
+
+# ---------------------------------------------------------------------------
+# W_n = F^{-1}(conj(xi)^n / xi e^{-|xi|^2})  (Sec. 4.2, eq. fourreg, fourreg5,
+# fourreg5a with the factor e^{-|z|^2/4} restored).
+# ---------------------------------------------------------------------------
+
+
+def W_closed(n: int, z):
+    """eq. fourreg5: i (2i)^n n!/z^{n+1} {1 - e^{-a} sum_{k<=n} a^k/k!}, a = |z|^2/4."""
+    z = np.asarray(z, dtype=np.complex128)
+    a = (z * np.conj(z)).real / 4.0
+    part = np.zeros_like(a)
+    term = np.ones_like(a)
+    for kk in range(n + 1):
+        if kk > 0:
+            term = term * a / kk
+        part = part + term
+    with np.errstate(divide="ignore", invalid="ignore"):
+        return 1j * (2j) ** n * math.factorial(n) / z ** (n + 1) * (1.0 - np.exp(-a) * part)
+
+
+def W_series(n: int, z, nterms: int = 200):
+    """eq. fourreg5a with e^{-a}: i(2i)^n n! (conj z/4)^{n+1} e^{-a} sum_j a^j/(j+n+1)!."""
+    z = np.asarray(z, dtype=np.complex128)
+    a = (z * np.conj(z)).real / 4.0
+    term = np.full(a.shape, 1.0 / math.factorial(n + 1))
+    acc = np.zeros_like(a)
+    for j in range(nterms):
+        acc = acc + term
+        term = term * a / (j + n + 2)
+    return 1j * (2j) ** n * math.factorial(n) * (np.conj(z) / 4.0) ** (n + 1) * np.exp(-a) * acc
+
+
+def W(n: int, z):
+    """W_n to full FP64 accuracy: series where a = |z|^2/4 < n+1 (cancellation
+    in the closed form near the origin, the paper's remark after eq. fourreg3),
+    closed form elsewhere.  W_n(0) = 0."""
+    z = np.asarray(z, dtype=np.complex128)
+    a = (z * np.conj(z)).real / 4.0
+    small = a < (n + 1)
+    out = np.empty(z.shape, dtype=np.complex128)
+    out[small] = W_series(n, z[small])
+    out[~small] = W_closed(n, z[~small])
+    return out
+
+
+# ---------------------------------------------------------------------------
+# The regularised F^{-1}(S/xi) (Sec. 4.3, steps 4a-4c).
+# ---------------------------------------------------------------------------
+
+
+def taylor_coeffs(S, g: Grid, M: int):
+    """c_n, n = 0..M, with n! c_n = (-i/2)^n F(z^n F^{-1} S)(0) (eq. fourreeg4), and
+    the fill value d = dS/dxi(0) = (-i/2) F(conj(z) F^{-1} S)(0).
+    Literal route: one inverse FFT, then summations at xi = 0."""
+    s = g.Finv(S)
+    c = [(-0.5j) ** n / math.factorial(n) * g.F_at0(g.z ** n * s) for n in range(M + 1)]
+    d = -0.5j * g.F_at0(np.conj(g.z) * s)
+    return c, d
+
+
+def h_of_S(S, g: Grid, M: int, fill: str = "analytic", Wn=None):
+    """h = F^{-1}(S/xi) = F^{-1}((S - G)/xi) + sum_n c_n W_n   (eq. Sreg, S0Taylor).
+
+    S may carry leading batch axes.  Returns h on the x-grid."""
+    c, d = taylor_coeffs(S, g, M)
+    if Wn is None:
+        Wn = [W(n, g.z) for n in range(M + 1)]
+    gauss = np.exp(-(g.xi * np.conj(g.xi)).real)
+    G = np.zeros_like(S)
+    for n in range(M + 1):
+        G = G + np.asarray(c[n])[..., None, None] * gauss * np.conj(g.xi) ** n
+    xi = g.xi.copy()
+    xi[0, 0] = 1.0                                # placeholder, overwritten below
+    U = (S - G) / xi
+    U[..., 0, 0] = d if fill == "analytic" else 0.0
+    h = g.Finv(U)
+    for n in range(M + 1):
+        h = h + np.asarray(c[n])[..., None, None] * Wn[n]
+    return h
+
+
+def dbar_inverse(f, g: Grid, M: int, fill: str = "analytic"):
+    """dbar^{-1} f = F^{-1}(-2i/xi F f) (Sec. 3 lemma), through the same regularisation."""
+    return h_of_S(-2j * g.F(f), g, M, fill)
+
+
+# ---------------------------------------------------------------------------
+# Operator, right-hand side and solution (Sec. 4.3 with Q -> E_k Q, Sec. 5.1).
+# ---------------------------------------------------------------------------
+
+
+class CGOProblem:
+    def __init__(self, Q, k: complex, N: int, L: float, M: int = 2, fill: str = "analytic"):
+        self.g = Grid(N, L)
+        self.Q = np.asarray(Q, dtype=np.complex128)
+        self.k = complex(k)
+        self.M = M
+        self.fill = fill
+        self.EQ = self.g.E(self.k) * self.Q
+        self.Wn = [W(n, self.g.z) for n in range(M + 1)]
+
+    def rhs(self):
+        """b = -i F(E_k Q)  (Sec. 4.3 step 3; eq. S0)."""
+        return -1j * self.g.F(self.EQ)
+
+    def h(self, S):
+        return h_of_S(S, self.g, self.M, self.fill, self.Wn)
+
+    def apply(self, S):
+        """A S = S + i F(E_k Q conj(h(S)))  (Sec. 4.3 step 4d)."""
+        return S + 1j * self.g.F(self.EQ * np.conj(self.h(S)))
+
+    # real-stacked view: x in R^{2N^2} <-> S in C^{N^2}
+    def to_real(self, S):
+        return np.ascontiguousarray(S).view(np.float64).reshape(S.shape[:-2] + (-1,))
+
+    def from_real(self, x):
+        N = self.g.N
+        return np.ascontiguousarray(x).view(np.complex128).reshape(x.shape[:-1] + (N, N))
+
+    def apply_real(self, x):
+        return self.to_real(self.apply(self.from_real(x)))
+
+    def dense_matrix(self, chunk: int = 256):
+        """The 2N^2 x 2N^2 real matrix of the real-linear operator A, column by column
+        (A applied to the real unit vectors)."""
+        n = 2 * self.g.N ** 2
+        A = np.empty((n, n))
+        for j0 in range(0, n, chunk):
+            j1 = min(n, j0 + chunk)
+            E = np.zeros((j1 - j0, n))
+            E[np.arange(j1 - j0), np.arange(j0, j1)] = 1.0
+            A[:, j0:j1] = self.apply_real(E).T
+        return A
+
+    def solve_dense(self):
+        """Direct solve of the same discrete system (LAPACK LU via numpy)."""
+        A = self.dense_matrix()
+        x = np.linalg.solve(A, self.to_real(self.rhs()))
+        return self.from_real(x)
+
+    def solve_gmres(self, tol=1e-13, restart=40, maxiter=2000):
+        b = self.to_real(self.rhs())
+        x, it, res = gmres(self.apply_real, b, tol=tol, restart=restart, maxiter=maxiter)
+        return self.from_real(x), it, res
+
+    def residual(self, S):
+        b = self.rhs()
+        r = b - self.apply(S)
+        return np.linalg.norm(r) / np.linalg.norm(b)
+
+
+# ---------------------------------------------------------------------------
+# Restarted GMRES on a real vector space (Saad & Schultz), modified Gram-Schmidt,
+# Givens rotations, x0 = 0.
+# ---------------------------------------------------------------------------
+
+
+def gmres(apply, b, tol=1e-13, restart=40, maxiter=2000, x0=None):
+    """Returns (x, total_iterations, final true relative residual)."""
+    b = np.asarray(b, dtype=np.float64)
+    nb = np.linalg.norm(b)
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64)
+    if nb == 0.0:
+        return x, 0, 0.0
+    total = 0
+    while True:
+        r = b - apply(x)
+        beta = np.linalg.norm(r)
+        if beta / nb <= tol or total >= maxiter:
+            return x, total, beta / nb
+        m = restart
+        V = np.zeros((m + 1, b.size))
+        H = np.zeros((m + 1, m))
+        cs = np.zeros(m)
+        sn = np.zeros(m)
+        e = np.zeros(m + 1)
+        e[0] = beta
+        V[0] = r / beta
+        j_done = 0
+        for j in range(m):
+            w = apply(V[j])
+            for i in range(j + 1):
+                H[i, j] = np.dot(V[i], w)
+                w = w - H[i, j] * V[i]
+            H[j + 1, j] = np.linalg.norm(w)
+            if H[j + 1, j] > 0:
+                V[j + 1] = w / H[j + 1, j]
+            for i in range(j):
+                t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+                H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
+                H[i, j] = t
+            rho = math.hypot(H[j, j], H[j + 1, j])
+            cs[j], sn[j] = H[j, j] / rho, H[j + 1, j] / rho
+            H[j, j] = rho
+            H[j + 1, j] = 0.0
+            e[j + 1] = -sn[j] * e[j]
+            e[j] = cs[j] * e[j]
+            total += 1
+            j_done = j + 1
+            if abs(e[j + 1]) / nb <= tol * 0.5 or total >= maxiter:
+                break
+        y = np.linalg.solve(np.triu(H[:j_done, :j_done]), e[:j_done])
+        x = x + V[:j_done].T @ y
+
+
+def solve_cgo(Q, k, N, L, M=2, tol=1e-13, restart=40, maxiter=2000, fill="analytic"):
+    """One CGO solve: returns dict(S, m, m1, iters, resid)."""
+    P = CGOProblem(Q, k, N, L, M, fill)
+    S, it, res = P.solve_gmres(tol=tol, restart=restart, maxiter=maxiter)
+    m = P.h(S)
+    return {"S": S, "m": m, "m1": 1j * S[0, 0], "iters": it, "resid": res}

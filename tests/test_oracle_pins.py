@@ -1,0 +1,282 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+None of these tests compares the oracle with itself: each checks it against a
+closed form, a library routine, brute force, an invariant or a value the paper
+states (see tests/golden/ for the paper's worked-example parameters).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import dbar_oracle as orc
+import workloads as wl
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --------------------------------------------------------------------------- FFT
+
+@pytest.mark.parametrize("N", [1, 2, 4, 8, 16])
+@pytest.mark.parametrize("sign", [-1, 1])
+def test_fft_matches_brute_force_dft(N, sign):
+    rng = np.random.default_rng(N)
+    x = rng.standard_normal((3, N)) + 1j * rng.standard_normal((3, N))
+    j = np.arange(N)
+    D = np.exp(sign * 2j * np.pi * np.outer(j, j) / N)
+    np.testing.assert_allclose(orc.dft_last_axis(x, sign), x @ D.T, atol=1e-13)
+
+
+def test_fft_matches_library_and_parseval():
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((2, 256)) + 1j * rng.standard_normal((2, 256))
+    X = orc.dft_last_axis(x, -1)
+    np.testing.assert_allclose(X, np.fft.fft(x), atol=1e-11)
+    np.testing.assert_allclose(np.sum(abs(X) ** 2, -1), 256 * np.sum(abs(x) ** 2, -1), rtol=1e-13)
+    f = rng.standard_normal((32, 64)) + 1j * rng.standard_normal((32, 64))
+    with pytest.raises(ValueError):
+        orc.dft_last_axis(np.ones(12), -1)
+    g = orc.Grid(32, 3.0)
+    f = rng.standard_normal((32, 32)) + 1j * rng.standard_normal((32, 32))
+    np.testing.assert_allclose(g.Finv(g.F(f)), f, atol=1e-13)
+
+
+def test_discrete_transform_of_gaussian_is_closed_form():
+    # F(exp(-|z|^2)) = 1/2 exp(-|xi|^2/4) with the 1/2pi convention of Sec. 1; this fixes
+    # the scale 2 pi L^2/N^2 and the (-1)^{m1+m2} phase of the grid x_j = L(-pi + 2 pi j/N).
+    g = orc.Grid(128, 4.0)
+    f = np.exp(-abs(g.z) ** 2)
+    np.testing.assert_allclose(g.F(f), 0.5 * np.exp(-abs(g.xi) ** 2 / 4), atol=1e-15)
+    # shifted Gaussian centred off the origin: phase exp(-i xi.x0)
+    x0 = 0.7 - 0.4j
+    f = np.exp(-abs(g.z - x0) ** 2)
+    ph = np.exp(-1j * (g.xi.real * x0.real + g.xi.imag * x0.imag))
+    np.testing.assert_allclose(g.F(f), 0.5 * np.exp(-abs(g.xi) ** 2 / 4) * ph, atol=1e-15)
+
+
+def test_Ek_shift_of_the_fourier_support():
+    # Sec. 5.1, eq. S0: F(E_k Q)(xi) = Q^(xi + 2i conj(k)); for Q = exp(-|z|^2) that is
+    # 1/2 exp(-|xi + 2i conj k|^2 / 4).  Fixes the sign convention of E_k.
+    g = orc.Grid(128, 5.0)
+    k = 0.9 - 0.6j
+    Q = np.exp(-abs(g.z) ** 2)
+    lhs = g.F(g.E(k) * Q)
+    rhs = 0.5 * np.exp(-abs(g.xi + 2j * np.conj(k)) ** 2 / 4)
+    np.testing.assert_allclose(lhs, rhs, atol=1e-13)
+    assert np.allclose(abs(g.E(k)), 1.0, atol=1e-15)
+
+
+# --------------------------------------------------------------------------- W_n
+
+def test_W0_is_the_lemma_closed_form():
+    z = np.array([0.3 + 0.1j, 1.0, -2.0 + 3.0j, 7.5 - 0.2j, 1e-3j])
+    exact = 1j / z * -np.expm1(-abs(z) ** 2 / 4)          # eq. fourreg, written without cancellation
+    np.testing.assert_allclose(orc.W(0, z), exact, rtol=1e-12)
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 3, 5, 8])
+def test_W_closed_form_equals_series(n):
+    # compared where both forms are well conditioned: a = |z|^2/4 in [(n+1)/2, 3(n+1)]
+    rng = np.random.default_rng(n)
+    a = rng.uniform(0.5 * (n + 1), 3.0 * (n + 1), 50)
+    z = 2 * np.sqrt(a) * np.exp(1j * rng.uniform(0, 2 * np.pi, 50))
+    np.testing.assert_allclose(orc.W_closed(n, z), orc.W_series(n, z), rtol=1e-12)
+    assert orc.W(n, np.array([0j]))[0] == 0
+
+
+def test_printed_series_lacks_gaussian_factor():
+    # eq. fourreg5a as printed has no e^{-|z|^2/4}; it then disagrees with eq. fourreg5.
+    z = np.array([0.7 + 0.2j, 2.5 - 1.3j])
+    n = 0
+    a = abs(z) ** 2 / 4
+    printed = 1j * (np.conj(z) / 4) * sum(a ** j / math.factorial(j + 1) for j in range(60))
+    assert np.all(abs(printed - orc.W_closed(n, z)) > 1e-2)
+    np.testing.assert_allclose(printed * np.exp(-a), orc.W_closed(n, z), rtol=1e-13)
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 4])
+def test_W_matches_bessel_quadrature(n):
+    # Polar form of F^{-1}(conj(xi)^n/xi e^{-|xi|^2}):
+    # W_n(z) = i^{n+1} e^{-i(n+1) arg z} int_0^inf r^n e^{-r^2} J_{n+1}(|z| r) dr.
+    from scipy import integrate, special
+    for z in [0.4 + 0.3j, -1.7 + 0.9j, 3.0 - 2.5j]:
+        rho, phi = abs(z), np.angle(z)
+        val, _ = integrate.quad(lambda r: r ** n * np.exp(-r * r) * special.jv(n + 1, rho * r),
+                                0, 12, epsabs=1e-15, epsrel=1e-13, limit=200)
+        ref = (1j) ** (n + 1) * np.exp(-1j * (n + 1) * phi) * val
+        assert abs(orc.W(n, np.array([z]))[0] - ref) <= 1e-12 * max(1.0, abs(ref))
+
+
+# --------------------------------------------------------------------------- Taylor data
+
+def test_taylor_coefficients_of_a_shifted_gaussian():
+    # S = F(exp(-alpha|z - z0|^2)) = (1/2alpha) exp(-|xi|^2/4alpha - i(xi conj z0 + conj xi z0)/2),
+    # so d^n S/d conj(xi)^n (0) = (1/2alpha)(-i z0/2)^n and dS/dxi(0) = (1/2alpha)(-i conj z0/2).
+    g = orc.Grid(128, 4.0)
+    alpha, z0 = 1.3, 0.6 - 0.35j
+    S = g.F(np.exp(-alpha * abs(g.z - z0) ** 2))
+    c, d = orc.taylor_coeffs(S, g, 5)
+    for n in range(6):
+        exact = (1 / (2 * alpha)) * (-0.5j * z0) ** n / math.factorial(n)
+        assert abs(c[n] - exact) < 1e-13, (n, c[n], exact)
+    assert abs(d - (1 / (2 * alpha)) * (-0.5j * np.conj(z0))) < 1e-13
+
+
+# --------------------------------------------------------------------------- dbar^{-1}
+
+def _dbartest(g, a, b, c):
+    f = np.exp(-a * (g.z - b) * (np.conj(g.z) - c))
+    with np.errstate(all="ignore"):
+        exact = (1 / (a * (g.z - b))) * (1 - f)
+    at_b = abs(g.z - b) < 1e-14
+    exact[at_b] = (np.conj(g.z) - c)[at_b]
+    return f, exact
+
+
+def test_dbar_inverse_worked_example_reaches_machine_precision():
+    with open(os.path.join(GOLDEN, "dbartest.json")) as fh:
+        gold = json.load(fh)
+    p = gold["parameters"]
+    g = orc.Grid(p["N"], p["L"])
+    f, exact = _dbartest(g, p["a"], p["b"], complex(p["c_re"], p["c_im"]))
+    err = abs(orc.dbar_inverse(f, g, p["M"]) - exact).max()
+    assert err < gold["claims"]["linf_error_below"], err
+
+
+def test_dbar_inverse_error_falls_with_M_and_N():
+    # Fig. 1: exponential decrease in M (N = 128) and in N (M = 11); M = 11 at N = 64
+    # already reaches machine precision.
+    g = orc.Grid(128, 4.0)
+    f, exact = _dbartest(g, 0.5, 1.0, 1j)
+    errs = [abs(orc.dbar_inverse(f, g, M) - exact).max() for M in (1, 3, 5, 7, 11)]
+    assert all(e2 < e1 for e1, e2 in zip(errs, errs[1:])), errs
+    assert errs[-1] < 1e-13
+    errN = []
+    for N in (16, 32, 64):
+        gN = orc.Grid(N, 4.0)
+        fN, exN = _dbartest(gN, 0.5, 1.0, 1j)
+        errN.append(abs(orc.dbar_inverse(fN, gN, 11) - exN).max())
+    assert errN[0] > errN[1] > errN[2] and errN[2] < 1e-12, errN
+
+
+def test_dbartest_prefactor_reading_and_fill_reading():
+    # The printed prefactor a/(z-b) is not the inverse (1/a is); zero-filling the xi = 0
+    # value (first-order rule) leaves an O(1e-2) error the analytic limit does not.
+    g = orc.Grid(64, 4.0)
+    a, b, c = 0.5, 1.0, 1j
+    f, exact = _dbartest(g, a, b, c)
+    num = orc.dbar_inverse(f, g, 11)
+    printed = exact * a * a
+    assert abs(num - printed).max() > 0.1
+    assert abs(orc.dbar_inverse(f, g, 11, fill="zero") - exact).max() > 1e-3
+    assert abs(num - exact).max() < 1e-12
+
+
+# --------------------------------------------------------------------------- operator and solve
+
+def test_zero_potential_gives_zero_solution():
+    N, L = 16, 3.0
+    P = orc.CGOProblem(np.zeros((N, N)), 0.4 + 0.1j, N, L)
+    S, it, res = P.solve_gmres()
+    assert np.all(S == 0) and it == 0
+    assert np.all(P.h(S) == 0)
+
+
+def test_operator_is_real_linear_not_complex_linear():
+    w = wl.small_gaussian(16, 3.0, 0.2 + 0.3j, amp=1.5 + 0.5j)
+    P = orc.CGOProblem(w.Q, w.k[0], w.N, w.L)
+    rng = np.random.default_rng(2)
+    S1 = rng.standard_normal((16, 16)) + 1j * rng.standard_normal((16, 16))
+    S2 = rng.standard_normal((16, 16)) + 1j * rng.standard_normal((16, 16))
+    np.testing.assert_allclose(P.apply(2.5 * S1), 2.5 * P.apply(S1), atol=1e-12)
+    np.testing.assert_allclose(P.apply(S1 + S2), P.apply(S1) + P.apply(S2), atol=1e-12)
+    assert abs(P.apply(1j * S1) - 1j * P.apply(S1)).max() > 1e-3
+
+
+@pytest.mark.parametrize("N", [8, 16, 32])
+def test_krylov_agrees_with_dense_direct_solve(N):
+    w = wl.small_gaussian(N, 2.0, 0.5 + 0.3j, amp=1.0)
+    P = orc.CGOProblem(w.Q, w.k[0], w.N, w.L)
+    Sd = P.solve_dense()
+    Sk, it, res = P.solve_gmres(tol=1e-14)
+    assert res < 1e-13
+    assert abs(Sk - Sd).max() <= 1e-12 * abs(Sd).max()
+
+
+@pytest.mark.slow
+def test_plain_fp64_workload_krylov_vs_dense_8192_unknowns():
+    w = wl.plain_fp64()
+    P = orc.CGOProblem(w.Q, w.k[0], w.N, w.L, w.M)
+    Sd = P.solve_dense()
+    Sk, it, res = P.solve_gmres(tol=1e-14)
+    assert abs(Sk - Sd).max() <= 1e-12 * abs(Sd).max()
+
+
+def test_born_limit_first_and_second_order():
+    # Q = eps q0, q0 = exp(-|z|^2): S = eps S0 + eps^2 S1 + O(eps^3) with
+    # S0 = -i F(E_k q0) = -i/2 exp(-|xi + 2i conj k|^2/4) (eq. S0) and, re-derived from
+    # S1 = K(S0) with the dbar^{-1} closed form, S1 = -i F[q0/(2(conj z - k)) (E_k e^{-|k|^2} - q0)].
+    N, L, k = 128, 5.0, 0.37 + 0.21j
+    g = orc.Grid(N, L)
+    q0 = np.exp(-abs(g.z) ** 2)
+    S0 = -0.5j * np.exp(-abs(g.xi + 2j * np.conj(k)) ** 2 / 4)
+    S1 = -1j * g.F(q0 / (2 * (np.conj(g.z) - k)) * (g.E(k) * np.exp(-abs(k) ** 2) - q0))
+    rem = []
+    for eps in (1e-2, 1e-3):
+        P = orc.CGOProblem(eps * q0, k, N, L, M=11)
+        S, it, res = P.solve_gmres(tol=1e-15)
+        rem.append(abs(S - eps * S0 - eps ** 2 * S1).max())
+    # third-order remainder: shrinks by ~1e3 when eps shrinks by 10
+    assert rem[0] < 1e-5 and 3e2 < rem[0] / rem[1] < 3e3, rem
+
+
+def test_spectral_convergence_on_nested_grids():
+    # x-grids of N and 2N share the points x_j^N = x_{2j}^{2N}; the discrete solutions
+    # converge exponentially in N (Sec. 4.2, Fig. 1 right).
+    L, k = 4.0, 0.3 + 0.2j
+    ms = {}
+    for N in (64, 128, 256):
+        w = wl.small_gaussian(N, L, k)
+        ms[N] = orc.solve_cgo(w.Q, k, N, L, M=11, tol=1e-14)["m"]
+    e1 = abs(ms[64] - ms[128][::2, ::2]).max()
+    e2 = abs(ms[128] - ms[256][::2, ::2]).max()
+    assert e2 < 1e-4 * e1 and e2 < 1e-10, (e1, e2)
+
+
+def test_decay_of_m_at_infinity():
+    # Theorem 3.1 / Sec. 6: m = m1/z + O(1/z^2) with m1 = i S(0).
+    N, L, k = 128, 8.0, 0.4 - 0.3j
+    w = wl.small_gaussian(N, L, k)
+    r = orc.solve_cgo(w.Q, k, N, L, M=11, tol=1e-14)
+    g = orc.Grid(N, L)
+    j0 = N // 2
+    devs = []
+    for dj in (24, 48):          # |z| ~ 9.4 and 18.8 along the positive x axis
+        z = g.z[j0, j0 + dj]
+        devs.append(abs(z * r["m"][j0, j0 + dj] - r["m1"]))
+    assert devs[1] < 0.7 * devs[0], devs
+    assert devs[1] < 0.05 * abs(r["m1"])
+
+
+def test_dbar_equation_holds_on_a_refined_grid():
+    # Non-tautological residual: zero-pad S to 2N (same L), rebuild m = h(S) on the finer
+    # grid and check dbar m = (i/2) F^{-1} S against 1/2 E_k Q (conj(m) + 1) there.
+    N, L, k = 256, 4.0, 0.3 + 0.2j
+    w = wl.small_gaussian(N, L, k)
+    r = orc.solve_cgo(w.Q, k, N, L, M=11, tol=1e-14)
+    S = r["S"]
+    N2 = 2 * N
+    m_idx = np.where(np.arange(N) <= N // 2, np.arange(N), np.arange(N) - N)
+    p2 = m_idx % N2
+    S2 = np.zeros((N2, N2), complex)
+    S2[np.ix_(p2, p2)] = S
+    g2 = orc.Grid(N2, L)
+    h2 = orc.h_of_S(S2, g2, 11)
+    Q2 = np.exp(-abs(g2.z) ** 2)
+    lhs = 0.5j * g2.Finv(S2)
+    rhs = 0.5 * g2.E(k) * Q2 * (np.conj(h2) + 1)
+    assert abs(lhs - rhs).max() < 1e-13
+    # coarse-grid points of the refined m agree with the solved m
+    assert abs(h2[::2, ::2] - r["m"]).max() < 1e-13

@@ -1,0 +1,139 @@
+"""Seeded synthetic inputs for the spectral D-bar CGO solve.
+
+This module only *generates inputs*: the potential Q sampled on the periodic
+x-grid, the list of spectral parameters k and the solver settings.  It holds
+none of the method's arithmetic (no transforms, no regularisation, no Krylov
+step), so both the CPU oracle and the CUDA path can take their inputs from
+here without sharing any computation.
+
+Grid convention (paper Sec. 4, eq. "domain"): x_j = L(-pi + 2 pi j / N),
+j = 0..N-1, identical in y.  Arrays are row-major [y][x] (axis 0 = y index,
+axis 1 = x index), complex128.
+
+Workloads (the paper's own test potentials are Gaussians, Sec. 4 test
+problem and Sec. 6 initial data q0 = exp(-x^2-y^2)):
+
+* ``plain_fp64``     N=64 on [-5pi,5pi]^2, Q = exp(-(x^2+y^2)), k = 0.5+0.3i.
+* ``batched_fp64``   N=512 on [-8pi,8pi]^2, Q = 2 exp(-(x^2+y^2)/1.5^2) e^{0.7i},
+                     256 k on the 16x16 grid linspace(-3,3,16)^2.
+* ``mixed_1024``     N=1024 on [-10pi,10pi]^2, Q = sum of 4 Gaussians
+                     c_j exp(-|z-z_j|^2/w_j^2), seed 7: centres U[-3,3]^2, widths
+                     U[0.5,2], |c_j| U[0,5], arg c_j U[0,2pi); then 128 k with
+                     |k| log-uniform in [0.1,8] and arg k U[0,2pi) from the same
+                     generator.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    N: int
+    L: float
+    Q: np.ndarray            # [N][N] complex128, row-major [y][x]
+    k: np.ndarray            # [nk] complex128
+    M: int = 2               # Taylor order of the regularising G
+    tol: float = 1e-12       # relative residual target of the stacked real system
+    mixed: bool = False      # FP32 inner Krylov with FP64 refinement
+    description: str = ""
+
+
+def x_grid(N: int, L: float) -> np.ndarray:
+    """Periodic grid x_j = L(-pi + 2 pi j/N) (paper Sec. 4, eq. "domain")."""
+    j = np.arange(N, dtype=np.float64)
+    return L * (-np.pi + 2.0 * np.pi * j / N)
+
+
+def mesh(N: int, L: float):
+    """X, Y sampled on the grid, shape [N][N], X varying along axis 1."""
+    x = x_grid(N, L)
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    return X, Y
+
+
+def gaussian_mixture(N, L, centres, widths, amps):
+    """Q = sum_j c_j exp(-|z - z_j|^2 / w_j^2) sampled on the grid."""
+    X, Y = mesh(N, L)
+    Q = np.zeros((N, N), dtype=np.complex128)
+    for (cx, cy), w, c in zip(centres, widths, amps):
+        Q += c * np.exp(-((X - cx) ** 2 + (Y - cy) ** 2) / (w * w))
+    return Q
+
+
+def draw_mixture(rng: np.random.Generator, nterms: int):
+    """Draw order: centres U[-3,3]^2, widths U[0.5,2], |c| U[0,5], arg c U[0,2pi)."""
+    centres = rng.uniform(-3.0, 3.0, size=(nterms, 2))
+    widths = rng.uniform(0.5, 2.0, size=nterms)
+    mags = rng.uniform(0.0, 5.0, size=nterms)
+    args = rng.uniform(0.0, 2.0 * np.pi, size=nterms)
+    return centres, widths, mags * np.exp(1j * args)
+
+
+def plain_fp64(N: int = 64) -> Workload:
+    X, Y = mesh(N, 5.0)
+    Q = np.exp(-(X * X + Y * Y)).astype(np.complex128)
+    return Workload("plain_fp64", N, 5.0, Q, np.array([0.5 + 0.3j]), M=2, tol=1e-12,
+                    mixed=False,
+                    description=f"N={N} on [-5pi,5pi]^2, Q=exp(-(x^2+y^2)), k=0.5+0.3i, M=2, FP64")
+
+
+def batched_fp64(N: int = 512, nk_side: int = 16) -> Workload:
+    L = 8.0
+    X, Y = mesh(N, L)
+    Q = 2.0 * np.exp(-(X * X + Y * Y) / 2.25) * np.exp(0.7j)
+    g = np.linspace(-3.0, 3.0, nk_side)
+    K1, K2 = np.meshgrid(g, g, indexing="xy")
+    k = (K1 + 1j * K2).ravel()
+    return Workload("batched_fp64", N, L, Q, k, M=2, tol=1e-12, mixed=False,
+                    description=f"N={N} on [-8pi,8pi]^2, Q=2exp(-r^2/2.25)e^(0.7i), "
+                                f"{k.size} k on linspace(-3,3,{nk_side})^2, FP64")
+
+
+def mixed_1024(N: int = 1024, nk: int = 128, seed: int = 7, L: float = 10.0) -> Workload:
+    rng = np.random.default_rng(seed)
+    centres, widths, amps = draw_mixture(rng, 4)
+    Q = gaussian_mixture(N, L, centres, widths, amps)
+    mod = np.exp(rng.uniform(np.log(0.1), np.log(8.0), size=nk))
+    arg = rng.uniform(0.0, 2.0 * np.pi, size=nk)
+    k = mod * np.exp(1j * arg)
+    return Workload("mixed_1024", N, L, Q, k, M=2, tol=1e-12, mixed=True,
+                    description=f"N={N} on [-{L:g}pi,{L:g}pi]^2, Q=4-Gaussian mixture (seed {seed}), "
+                                f"{nk} k with |k| log-uniform [0.1,8], FP32 inner + FP64 refinement")
+
+
+def small_gaussian(N: int, L: float, k: complex, amp: complex = 1.0, width: float = 1.0) -> Workload:
+    """A single centred Gaussian amp*exp(-|z|^2/width^2); the paper's q0 at amp=width=1."""
+    X, Y = mesh(N, L)
+    Q = amp * np.exp(-(X * X + Y * Y) / (width * width)) * np.ones((N, N), np.complex128)
+    return Workload(f"gauss_N{N}", N, L, Q, np.array([complex(k)]), M=2, tol=1e-12)
+
+
+def random_k_disc(rng: np.random.Generator, nk: int, kmax: float) -> np.ndarray:
+    r = kmax * np.sqrt(rng.uniform(0.0, 1.0, size=nk))
+    t = rng.uniform(0.0, 2.0 * np.pi, size=nk)
+    return r * np.exp(1j * t)
+
+
+def resolved(N: int, L: float, k: complex, xi_q: float) -> bool:
+    """Resolution rule for the k-shift of F(E_k Q): the Fourier support of E_k Q is
+    centred at -2i conj(k) (paper Sec. 5.1), so the box half-width N/(2L) must cover
+    2 max(|k1|,|k2|) plus the radius xi_q beyond which |Q^| is negligible."""
+    return N / (2.0 * L) >= 2.0 * max(abs(k.real), abs(k.imag)) + xi_q
+
+
+BY_NAME = {
+    "plain_fp64": plain_fp64,
+    "batched_fp64": batched_fp64,
+    "mixed_1024": mixed_1024,
+}
+
+
+def describe(w: Workload) -> dict:
+    return {"workload": w.name, "N": w.N, "L": w.L, "nk": int(w.k.size), "M": w.M,
+            "tol": w.tol, "mixed": w.mixed, "desc": w.description,
+            "box": f"[-{w.L:g}pi,{w.L:g}pi]^2", "h": 2 * math.pi * w.L / w.N}
