@@ -1,0 +1,149 @@
+/*
+ * dbar.h -- C ABI of the GB300 spectral D-bar CGO solver.
+ *
+ * Method: C. Klein, K. McLaughlin, "Spectral approach to D-bar problems".
+ * A CGO solution m of  dbar m = 1/2 E_k Q (conj(m) + 1),  E_k = e^{conj(kz)-kz}
+ * (Sec. 1, eq:038/eq:039) is found through S = xi m^ (eq:042), which solves
+ * the real-linear system (eq:MainEQa, Sec. 5.1 eq:MainEQDS)
+ *     A S := S + i F(E_k Q conj(F^{-1}(S/xi))) = b := -i F(E_k Q),
+ * with F^{-1}(S/xi) regularised as in Sec. 4.2 (eq. Sreg, Gchoice, fourreeg4,
+ * fourreg5): a Taylor-Gaussian G of order M is removed before the division by
+ * xi and its inverse transform sum_n c_n W_n is added back in closed form.
+ * The system is solved by GMRES on the stacked real and imaginary parts
+ * (Sec. 4.1, Sec. 4.3).
+ *
+ * Discretisation (Sec. 4.1, eq. domain / xidomain): x_j = L(-pi + 2 pi j/N),
+ * j = 0..N-1, the same in y; xi_m = m/L, m in [-N/2+1, N/2].
+ *
+ * Layouts (all arrays row-major, complex numbers interleaved re,im):
+ *   physical fields  [y index j2][x index j1]           (Q, m)
+ *   Fourier fields   [p2][p1], p = m mod N (natural DFT order; m = p for
+ *                    p <= N/2, else p - N)                (S, b, A S)
+ *   batched fields   [k][...] with stride N*N complex.
+ *
+ * Conventions: every entry point returns a dbar_status; no C++ exception
+ * crosses the ABI.  On failure the message of the calling thread's last error
+ * is available from dbar_last_error().  Host pointers are ordinary pageable
+ * or pinned memory; "device" pointers are CUDA global memory on the device
+ * the plan was created on.  The caller owns every buffer it passes; the plan
+ * owns its own device tables and workspaces.  Calls are ordered on the given
+ * CUDA stream (NULL = legacy default stream) and return after the stream has
+ * drained, unless stated otherwise.
+ */
+#ifndef DBAR_H
+#define DBAR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DBAR_OK = 0,
+  DBAR_EINVAL = 1,   /* bad argument: N not a power of two in [16, 2048], L <= 0,
+                        NaN/Inf in Q or k, null pointer where one is required  */
+  DBAR_ENOMEM = 2,   /* a device allocation failed                              */
+  DBAR_ENOCONV = 3,  /* some k missed tol within max_iter / max_outer; outputs
+                        are still written (best iterate and its residual)       */
+  DBAR_ETIMEOUT = 4, /* reserved: a bounded device wait ran out                 */
+  DBAR_ECUDA = 5,    /* a CUDA call failed; see dbar_last_error()               */
+  DBAR_EBUSY = 6     /* reserved for asynchronous interfaces                    */
+} dbar_status;
+
+typedef enum {
+  DBAR_FP64 = 0,     /* GMRES entirely in FP64 (restarted on the true residual) */
+  DBAR_MIXED = 1     /* FP32 inner GMRES, FP64 true residual and update
+                        (iterative refinement)                                  */
+} dbar_prec;
+
+typedef struct {
+  int N;             /* grid points per axis: power of two, 16 <= N <= 2048    */
+  double L;          /* box [-pi L, pi L]^2 (Sec. 4.1, eq. domain), L > 0        */
+  int M;             /* Taylor order of G (Sec. 4.2, eq. Gchoice), 0 <= M <= 16 */
+  int prec;          /* dbar_prec                                               */
+  int restart;       /* Krylov vectors per cycle, 1..128                        */
+  int max_iter;      /* cap on the total inner iterations of one k              */
+  double tol;        /* target ||b - A S||_2 / ||b||_2 (stacked real 2-norm)    */
+  int zero_fill;     /* value of (S-G)/xi at xi = 0: 0 = analytic limit
+                        dS/dxi(0) (default), 1 = zero                          */
+  int max_batch;     /* k values solved concurrently; 0 = chosen from memory    */
+  double inner_tol;  /* DBAR_MIXED: relative residual reduction per FP32 cycle  */
+  int max_outer;     /* cap on cycles (restarts / refinement steps)             */
+} dbar_params;
+
+typedef struct dbar_plan* dbar_plan_t;
+
+/* Defaults for a grid: M = 2, DBAR_MIXED, restart 32, tol 1e-12,
+ * inner_tol 1e-6, max_outer 40, max_iter 4000, analytic fill. */
+void dbar_params_init(dbar_params* p, int N, double L);
+
+/* Message describing the calling thread's most recent failure ("" if none). */
+const char* dbar_last_error(void);
+
+/* Builds the grid tables on the current CUDA device: twiddles, the per-axis
+ * moment tables D_a(p) = sum_j x_j^a e^{2 pi i p j/N} used for the Taylor
+ * coefficients (Sec. 4.3 step 4a, eq. fourreeg4), and the correction fields
+ * W_n - F_d^{-1}(e^{-|xi|^2} conj(xi)^n/xi) that carry the closed-form part of
+ * the regularisation (Sec. 4.2, eq. fourreg5).  Workspaces for max_batch k
+ * values are allocated here.  *out receives the plan; on failure *out = NULL.
+ * Errors: DBAR_EINVAL, DBAR_ENOMEM, DBAR_ECUDA. */
+dbar_status dbar_plan_create(const dbar_params* p, dbar_plan_t* out);
+
+/* Frees every device resource of the plan (NULL is accepted). */
+dbar_status dbar_plan_destroy(dbar_plan_t plan);
+
+/* Bytes of device memory the plan holds, and the batch size it uses. */
+dbar_status dbar_plan_info(dbar_plan_t plan, size_t* device_bytes, int* max_batch);
+
+/* CGO solve for nk values of k with one potential Q (Sec. 4.3 algorithm with
+ * Q -> E_k Q, Sec. 5.1).
+ *   Q        N*N complex (2*N*N doubles), physical layout; host or device
+ *   nk       number of k values (0 is accepted and does nothing)
+ *   k        2*nk doubles (Re k, Im k), host memory
+ *   S_out    nk*N*N complex: S = xi m^ on the Fourier grid; host or device
+ *   m_out    nk*N*N complex: m on the x-grid (Sec. 4.3, eq. S0Taylor: m = h);
+ *            may be NULL
+ *   iters    2*nk ints, host, may be NULL: (total inner iterations, cycles)
+ *   resid    nk doubles, host, may be NULL: final ||b - A S||/||b|| in FP64
+ *   io_on_device  1: Q, S_out, m_out are device pointers; 0: host pointers
+ *   stream   cudaStream_t or NULL
+ * m^(1) = i S(0) (the 1/z coefficient, Sec. 6 eq:m1def) is S_out[k][0][0]*i.
+ * Returns DBAR_ENOCONV when some k missed tol (outputs still written). */
+dbar_status dbar_solve_cgo(dbar_plan_t plan, const double* Q, int nk, const double* k,
+                           double* S_out, double* m_out, int* iters, double* resid,
+                           int io_on_device, void* stream);
+
+/* --- stage entry points (device pointers; used for parity checks) -------- */
+
+/* A S for nk fields (Sec. 4.3 step 4):  AS[i] = S[i] + i F(E_{k_i} Q conj(h(S[i]))).
+ * fp32 = 0: S, AS, Q are complex128 (double pairs); fp32 = 1: complex64 (float
+ * pairs), computed by the FP32 kernels of the inner solve.  nk <= max_batch. */
+dbar_status dbar_apply(dbar_plan_t plan, const void* Q, int nk, const double* k,
+                       const void* S, void* AS, int fp32, void* stream);
+
+/* b = -i F(E_k Q) (Sec. 4.3 step 3), complex128, nk <= max_batch. */
+dbar_status dbar_rhs(dbar_plan_t plan, const double* Q, int nk, const double* k,
+                     double* b, void* stream);
+
+/* m = h(S) = F^{-1}((S-G)/xi) + sum_n c_n W_n (eq. S0Taylor), complex128. */
+dbar_status dbar_m_from_S(dbar_plan_t plan, int nk, const double* S, double* m, void* stream);
+
+/* Taylor data of S (Sec. 4.3 step 4a, eq. fourreeg4): c[i][n], n = 0..M, with
+ * n! c_n = (-i/2)^n F(z^n F^{-1} S)(0), then the fill value d = dS/dxi(0)
+ * = (-i/2) F(conj(z) F^{-1} S)(0).  coef: host, nk*(M+2) complex (doubles).
+ * fp32 selects the complex64 kernels as in dbar_apply. */
+dbar_status dbar_taylor(dbar_plan_t plan, int nk, const void* S, double* coef, int fp32,
+                        void* stream);
+
+/* Unnormalised 2-D DFT over [y][x] (sign -1: forward e^{-2 pi i p.j/N}, +1:
+ * inverse e^{+...}), nk fields, complex128 or complex64 (fp32 = 1). */
+dbar_status dbar_fft2(dbar_plan_t plan, int nk, const void* in, void* out, int sign, int fp32,
+                      void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DBAR_H */

@@ -1,0 +1,226 @@
+// Complex arithmetic and the in-shared-memory Stockham FFT used by every pass.
+//
+// The paper computes all transforms with 2-D FFTs (Sec. 4.1: "discrete
+// Fourier series, computed via a Fast Fourier Transform"; Sec. 4.3 remark:
+// the cost is "mainly in the FFT commands").  Here each 2-D transform is split
+// into a row pass and a column pass; inside a pass every line (row or column)
+// of length N is transformed by N/16 threads, each holding 16 elements in
+// registers.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dbar {
+
+template <typename T>
+struct __align__(2 * sizeof(T)) cx {
+  T re, im;
+};
+
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> mkc(T a, T b) {
+  cx<T> r;
+  r.re = a;
+  r.im = b;
+  return r;
+}
+template <typename T>
+__device__ __forceinline__ cx<T> operator+(cx<T> a, cx<T> b) { return mkc(a.re + b.re, a.im + b.im); }
+template <typename T>
+__device__ __forceinline__ cx<T> operator-(cx<T> a, cx<T> b) { return mkc(a.re - b.re, a.im - b.im); }
+template <typename T>
+__device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
+  return mkc(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+// a * conj(b)
+template <typename T>
+__device__ __forceinline__ cx<T> cmulc(cx<T> a, cx<T> b) {
+  return mkc(a.re * b.re + a.im * b.im, a.im * b.re - a.re * b.im);
+}
+template <typename T>
+__device__ __forceinline__ cx<T> cscale(cx<T> a, T s) { return mkc(a.re * s, a.im * s); }
+template <typename T>
+__device__ __forceinline__ cx<T> cconj(cx<T> a) { return mkc(a.re, -a.im); }
+// i * a
+template <typename T>
+__device__ __forceinline__ cx<T> cmuli(cx<T> a) { return mkc(-a.im, a.re); }
+template <typename T, typename U>
+__device__ __forceinline__ cx<T> ccast(cx<U> a) { return mkc((T)a.re, (T)a.im); }
+
+template <typename T>
+__device__ __forceinline__ cx<T> ldg(const cx<T>* p) {
+  return *reinterpret_cast<const cx<T>*>(p);
+}
+template <>
+__device__ __forceinline__ cx<float> ldg(const cx<float>* p) {
+  float2 v = __ldg(reinterpret_cast<const float2*>(p));
+  return mkc(v.x, v.y);
+}
+template <>
+__device__ __forceinline__ cx<double> ldg(const cx<double>* p) {
+  double2 v = __ldg(reinterpret_cast<const double2*>(p));
+  return mkc(v.x, v.y);
+}
+
+// Sum over groups of `width` lanes (a power of two <= 32); every lane gets its group's sum.
+__device__ __forceinline__ double warp_sum(double v, int width) {
+  for (int off = width >> 1; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// Register DFT of size R in {2,4,8,16}: radix-2 decimation in time after a
+// bit-reversal permutation.  The butterfly twiddles exp(-+ i pi q/8) are the
+// exact values cos(pi q/8), sin(pi q/8) written out.
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr double cos8(int q) {
+  return q == 0 ? 1.0
+       : q == 1 ? 0.92387953251128675613
+       : q == 2 ? 0.70710678118654752440
+       : q == 3 ? 0.38268343236508977173
+       : q == 4 ? 0.0
+       : q == 5 ? -0.38268343236508977173
+       : q == 6 ? -0.70710678118654752440
+                : -0.92387953251128675613;
+}
+__host__ __device__ constexpr double sin8(int q) {
+  return q == 0 ? 0.0
+       : q == 1 ? 0.38268343236508977173
+       : q == 2 ? 0.70710678118654752440
+       : q == 3 ? 0.92387953251128675613
+       : q == 4 ? 1.0
+       : q == 5 ? 0.92387953251128675613
+       : q == 6 ? 0.70710678118654752440
+                : 0.38268343236508977173;
+}
+
+// x * exp(s i pi q/8), s = +1 for the inverse transform, -1 for the forward one.
+template <typename T, bool INV>
+__device__ __forceinline__ cx<T> rot8(cx<T> x, int q) {
+  if (q == 0) return x;
+  if (q == 4) return INV ? mkc(-x.im, x.re) : mkc(x.im, -x.re);
+  const T c = (T)cos8(q);
+  const T s = INV ? (T)sin8(q) : (T)-sin8(q);
+  return mkc(x.re * c - x.im * s, x.re * s + x.im * c);
+}
+
+__host__ __device__ constexpr int brev(int i, int bits) {
+  int r = 0;
+  for (int b = 0; b < bits; ++b) r |= ((i >> b) & 1) << (bits - 1 - b);
+  return r;
+}
+template <int R>
+struct Log2 {
+  static constexpr int v = R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : 4;
+};
+
+template <typename T, int R, bool INV>
+__device__ __forceinline__ void dft_reg(cx<T>* v) {
+  constexpr int LB = Log2<R>::v;
+  cx<T> t[R];
+#pragma unroll
+  for (int i = 0; i < R; ++i) t[i] = v[brev(i, LB)];
+#pragma unroll
+  for (int m = 1; m < R; m *= 2) {
+#pragma unroll
+    for (int k = 0; k < m; ++k) {
+#pragma unroll
+      for (int b = 0; b < R; b += 2 * m) {
+        const cx<T> a = t[b + k];
+        const cx<T> c = rot8<T, INV>(t[b + k + m], (8 * k) / m);
+        t[b + k] = a + c;
+        t[b + k + m] = a - c;
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < R; ++i) v[i] = t[i];
+}
+
+// Padded shared-memory index: one spare slot every 16 elements keeps the
+// stride-R writes of the first stage free of bank conflicts.
+__device__ __forceinline__ int padi(int i) { return i + (i >> 4); }
+__host__ __device__ __forceinline__ int line_pitch(int N) { return N + (N >> 4) + 1; }
+
+// One Stockham stage of radix R on a line of length N held by TPL = N/16
+// threads.  Each thread owns 16 elements: 16/R butterflies j = t + b*TPL.
+// Inputs x[j + r N/R] (from registers in the first stage, from shared memory
+// otherwise), twiddle w^{r (j mod Ns)} with w = e^{-+2 pi i/(Ns R)}, R-point
+// DFT, outputs at ((j - j mod Ns) R + j mod Ns) + r Ns.  The last stage keeps
+// its outputs in registers: v[q] = X[t + q TPL].
+template <typename T, int R, bool INV>
+__device__ __forceinline__ void fft_stage(cx<T> (&v)[16], cx<T>* line, int N, int Ns, int t, int TPL,
+                                          const cx<T>* __restrict__ tw, bool first, bool last) {
+  constexpr int B = 16 / R;
+  const int nb = N / R;
+  cx<T> u[16];
+  if (first) {
+#pragma unroll
+    for (int r = 0; r < 16; ++r) u[r] = v[r];
+  } else {
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int j = t + b * TPL;
+#pragma unroll
+      for (int r = 0; r < R; ++r) u[b * R + r] = line[padi(j + r * nb)];
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < B; ++b) {
+    const int j = t + b * TPL;
+    const int k = j & (Ns - 1);
+    if (Ns > 1) {
+      const int step = N / (Ns * R);
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        cx<T> w = ldg(tw + r * k * step);
+        if (INV) w.im = -w.im;
+        u[b * R + r] = cmul(u[b * R + r], w);
+      }
+    }
+    dft_reg<T, R, INV>(&u[b * R]);
+  }
+  if (last) {
+#pragma unroll
+    for (int b = 0; b < B; ++b)
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[b + r * B] = u[b * R + r];
+  } else {
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int j = t + b * TPL;
+      const int k = j & (Ns - 1);
+      const int base = (j - k) * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) line[padi(base + r * Ns)] = u[b * R + r];
+    }
+    __syncthreads();
+  }
+}
+
+// Full length-N transform (N = 2^logN >= 16) of one line per thread group.
+// On entry v[q] = x[t + q TPL]; on exit v[q] = X[t + q TPL], with
+// X[p] = sum_j x[j] e^{-+2 pi i p j / N} (unnormalised; + for INV).
+// Every thread of the block must call this with the same N.
+template <typename T, bool INV>
+__device__ __forceinline__ void fft_line(cx<T> (&v)[16], cx<T>* line, int N, int logN, int t, int TPL,
+                                         const cx<T>* __restrict__ tw) {
+  int rem = logN - 4;
+  fft_stage<T, 16, INV>(v, line, N, 1, t, TPL, tw, true, rem == 0);
+  int Ns = 16;
+  while (rem > 0) {
+    const int lr = rem >= 4 ? 4 : rem;
+    const bool last = (rem == lr);
+    switch (lr) {
+      case 4: fft_stage<T, 16, INV>(v, line, N, Ns, t, TPL, tw, false, last); break;
+      case 3: fft_stage<T, 8, INV>(v, line, N, Ns, t, TPL, tw, false, last); break;
+      case 2: fft_stage<T, 4, INV>(v, line, N, Ns, t, TPL, tw, false, last); break;
+      default: fft_stage<T, 2, INV>(v, line, N, Ns, t, TPL, tw, false, last); break;
+    }
+    Ns <<= lr;
+    rem -= lr;
+  }
+}
+
+}  // namespace dbar

@@ -1,0 +1,134 @@
+// FP64 (complex128) instantiations, the per-slot scalar Krylov kernels and the
+// small helper kernels used at plan and solve set-up.
+#include "kern_impl.cuh"
+
+namespace dbar {
+DBAR_INSTANTIATE(double, double)
+template cudaError_t launch_pass_c<double, double, PC_RHS>(const PassArgs<double>&, int, cudaStream_t);
+template cudaError_t launch_pass_c<double, float, PC_RHS>(const PassArgs<double>&, int, cudaStream_t);
+template cudaError_t launch_pass_c<double, double, PC_RES>(const PassArgs<double>&, int, cudaStream_t);
+template cudaError_t launch_pass_c<double, float, PC_RES>(const PassArgs<double>&, int, cudaStream_t);
+
+cudaError_t launch_finalize_h(const KryArgs& a, double* H, int j, int nslots, cudaStream_t s) {
+  if (nslots <= 0) return cudaSuccess;
+  k_finalize_h<<<nslots, KR_THREADS, 0, s>>>(a, H, j);
+  return cudaGetLastError();
+}
+cudaError_t launch_givens(const KryArgs& a, const CycleState& c, int j, int nslots, cudaStream_t s) {
+  if (nslots <= 0) return cudaSuccess;
+  k_givens<<<nslots, KR_THREADS, 0, s>>>(a, c, j);
+  return cudaGetLastError();
+}
+cudaError_t launch_solve_y(const CycleState& c, int nslots, cudaStream_t s) {
+  if (nslots <= 0) return cudaSuccess;
+  k_solve_y<<<(nslots + 63) / 64, 64, 0, s>>>(c, nslots);
+  return cudaGetLastError();
+}
+cudaError_t launch_cycle_start(const CycleState& c, const double* part, int nblk, int first, int nslots,
+                               cudaStream_t s) {
+  if (nslots <= 0) return cudaSuccess;
+  k_cycle_start<<<nslots, KR_THREADS, 0, s>>>(c, part, nblk, first);
+  return cudaGetLastError();
+}
+
+// QT[x][y] = Q[y][x] in both precisions (32x32 tiles through shared memory).
+__global__ void k_transpose_q(const cx<double>* __restrict__ Q, cx<double>* __restrict__ QT64,
+                              cx<float>* __restrict__ QT32, int N) {
+  __shared__ cx<double> tile[32][33];
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) tile[r][threadIdx.x] = Q[(size_t)(by + r) * N + bx + threadIdx.x];
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const cx<double> v = tile[threadIdx.x][r];
+    const size_t o = (size_t)(bx + r) * N + by + threadIdx.x;
+    QT64[o] = v;
+    QT32[o] = ccast<float>(v);
+  }
+}
+cudaError_t launch_transpose_q(const cx<double>* Q, cx<double>* QT64, cx<float>* QT32, int N, cudaStream_t s) {
+  k_transpose_q<<<dim3(N / 32, N / 32), dim3(32, 8), 0, s>>>(Q, QT64, QT32, N);
+  return cudaGetLastError();
+}
+
+// DT[n][x][y] = W[n][y][x] - V[n][y][x]
+__global__ void k_delta_build(const cx<double>* __restrict__ V, const cx<double>* __restrict__ W,
+                              cx<double>* __restrict__ DT64, cx<float>* __restrict__ DT32, int N) {
+  __shared__ cx<double> tile[32][33];
+  const size_t f = (size_t)blockIdx.z * N * N;
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const size_t i = f + (size_t)(by + r) * N + bx + threadIdx.x;
+    tile[r][threadIdx.x] = W[i] - V[i];
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const cx<double> v = tile[threadIdx.x][r];
+    const size_t o = f + (size_t)(bx + r) * N + by + threadIdx.x;
+    DT64[o] = v;
+    DT32[o] = ccast<float>(v);
+  }
+}
+cudaError_t launch_delta_build(const cx<double>* V, const cx<double>* W, cx<double>* DT64, cx<float>* DT32, int N,
+                               int nfields, cudaStream_t s) {
+  k_delta_build<<<dim3(N / 32, N / 32, nfields), dim3(32, 8), 0, s>>>(V, W, DT64, DT32, N);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_add_fields(const cx<T>* __restrict__ S, const cx<T>* __restrict__ KS, cx<T>* __restrict__ AS,
+                             long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    AS[i] = S[i] + KS[i];
+}
+cudaError_t launch_add_fields(const void* S, const void* KS, void* AS, long long n, int fp32, cudaStream_t s) {
+  const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+  if (fp32)
+    k_add_fields<float><<<blocks, 256, 0, s>>>((const cx<float>*)S, (const cx<float>*)KS, (cx<float>*)AS, n);
+  else
+    k_add_fields<double><<<blocks, 256, 0, s>>>((const cx<double>*)S, (const cx<double>*)KS, (cx<double>*)AS, n);
+  return cudaGetLastError();
+}
+
+// Taylor data of one field per slot from the pass-A partial sums: [slot][M+2] = c_0..c_M, d.
+__global__ void k_taylor_final(const cx<double>* __restrict__ partA, int nblkA, int M, int N,
+                               cx<double>* __restrict__ out) {
+  const int slot = blockIdx.x, lane = threadIdx.x;
+  const cx<double>* pa = partA + (size_t)slot * nblkA * (M + 2);
+  for (int n = 0; n < M + 2; ++n) {
+    double re = 0.0, im = 0.0;
+    for (int b = lane; b < nblkA; b += 32) {
+      re += pa[(size_t)b * (M + 2) + n].re;
+      im += pa[(size_t)b * (M + 2) + n].im;
+    }
+    re = warp_sum(re, 32);
+    im = warp_sum(im, 32);
+    if (lane == 0) out[(size_t)slot * (M + 2) + n] = taylor_coef(mkc(re, im), n, M, N, 1.0);
+  }
+}
+cudaError_t launch_taylor_final(const cx<double>* partA, int nblkA, int M, int N, cx<double>* out, int nslots,
+                                cudaStream_t s) {
+  k_taylor_final<<<nslots, 32, 0, s>>>(partA, nblkA, M, N, out);
+  return cudaGetLastError();
+}
+
+__global__ void k_cast_fields(const cx<double>* __restrict__ in, cx<float>* __restrict__ out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = ccast<float>(in[i]);
+}
+cudaError_t launch_cast_fields(const cx<double>* in, cx<float>* out, long long n, cudaStream_t s) {
+  const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+  k_cast_fields<<<blocks, 256, 0, s>>>(in, out, n);
+  return cudaGetLastError();
+}
+
+__global__ void k_check_finite(const double* __restrict__ p, long long n, int* flag) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    if (!isfinite(p[i])) *flag = 1;
+}
+cudaError_t launch_check_finite(const double* p, long long n, int* flag, cudaStream_t s) {
+  const int blocks = (int)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024);
+  k_check_finite<<<blocks, 256, 0, s>>>(p, n, flag);
+  return cudaGetLastError();
+}
+
+}  // namespace dbar

@@ -1,0 +1,835 @@
+// Plan, solve driver and C ABI of the spectral D-bar CGO solver.
+//
+// The driver runs the Sec. 4.3 algorithm (with Q -> E_k Q, Sec. 5.1) for a
+// batch of k values on one GPU: right-hand side b = -i F(E_k Q), then GMRES
+// cycles on the stacked real system.  In DBAR_FP64 mode a cycle is a
+// restarted FP64 GMRES cycle; in DBAR_MIXED mode a cycle is an FP32 GMRES
+// correction solve A d = r followed by the FP64 update x += d and the FP64
+// true residual r = b - A x (iterative refinement).  Both end each cycle with
+// the true FP64 residual, so the reported residual is always the FP64 one.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/dbar.h"
+#include "launch.cuh"
+
+using namespace dbar;
+typedef std::complex<double> zd;
+
+static thread_local std::string g_last_error;
+
+static dbar_status fail(dbar_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+#define CK(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess)                                                                    \
+      return fail(e_ == cudaErrorMemoryAllocation ? DBAR_ENOMEM : DBAR_ECUDA,                \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                       \
+  } while (0)
+
+struct dbar_plan {
+  dbar_params p;
+  int N = 0, logN = 0, M = 0, MA = 0, B = 0, m = 0;
+  bool mixed = false;
+  int device = 0;
+  long long n = 0;  // N*N
+  size_t bytes = 0;
+  std::vector<void*> allocs;
+
+  // tables
+  cx<double>* tw64 = nullptr;
+  cx<float>* tw32 = nullptr;
+  cx<double>* Da64 = nullptr;
+  cx<float>* Da32 = nullptr;
+  cx<double>* Dt64 = nullptr;  // Delta_n^T
+  cx<float>* Dt32 = nullptr;
+  cx<double>* QT64 = nullptr;
+  cx<float>* QT32 = nullptr;
+  cx<double>* Qdev = nullptr;  // staging for a host Q
+  cx<double>* ex64 = nullptr;
+  cx<double>* ey64 = nullptr;
+  cx<float>* ex32 = nullptr;
+  cx<float>* ey32 = nullptr;
+  // workspaces
+  cx<double>* x64 = nullptr;
+  cx<double>* b64 = nullptr;
+  void* T1 = nullptr;
+  void* T2 = nullptr;
+  void* V = nullptr;
+  void* KS = nullptr;
+  cx<double>* partA = nullptr;
+  double* part = nullptr;
+  double* part2 = nullptr;
+  double* coef = nullptr;
+  int* flag = nullptr;
+  CycleState cs;
+  // host staging
+  int* h_active = nullptr;
+  cx<double>* h_ek = nullptr;  // pinned [B][2N]
+
+  double inv2piL = 0, sw = 0, fillscale = 0;
+
+  template <typename X>
+  cudaError_t alloc(X** ptr, size_t count) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(X));
+    if (e != cudaSuccess) return e;
+    allocs.push_back(q);
+    bytes += count * sizeof(X);
+    *ptr = reinterpret_cast<X*>(q);
+    return cudaSuccess;
+  }
+  ~dbar_plan() {
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(device);
+    for (void* q : allocs) cudaFree(q);
+    if (h_active) cudaFreeHost(h_active);
+    if (h_ek) cudaFreeHost(h_ek);
+    cudaSetDevice(cur);
+  }
+  size_t inner_elem() const { return mixed ? sizeof(cx<float>) : sizeof(cx<double>); }
+};
+
+extern "C" void dbar_params_init(dbar_params* p, int N, double L) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->N = N;
+  p->L = L;
+  p->M = 2;
+  p->prec = DBAR_MIXED;
+  p->restart = 32;
+  p->max_iter = 4000;
+  p->tol = 1e-12;
+  p->zero_fill = 0;
+  p->max_batch = 0;
+  p->inner_tol = 1e-6;
+  p->max_outer = 40;
+}
+
+extern "C" const char* dbar_last_error(void) { return g_last_error.c_str(); }
+
+// ---------------------------------------------------------------------------
+// Host-side tables (FP64, plain libm).
+// ---------------------------------------------------------------------------
+
+// W_n(z) = F^{-1}(conj(xi)^n/xi e^{-|xi|^2}) (Sec. 4.2, eq. fourreg5): with a = |z|^2/4,
+//   closed form  i(2i)^n n!/z^{n+1} (1 - e^{-a} sum_{k<=n} a^k/k!)        (a >= n+1)
+//   series       i(2i)^n n! (conj z/4)^{n+1} e^{-a} sum_{j>=0} a^j/(j+n+1)! (a <  n+1),
+// the series being the expansion of the same bracket without cancellation.
+static zd W_host(int n, zd z) {
+  const double a = std::norm(z) / 4.0;
+  zd pref(0.0, 1.0);
+  double fact = 1.0;
+  for (int r = 1; r <= n; ++r) {
+    pref *= zd(0.0, 2.0);
+    fact *= r;
+  }
+  pref *= fact;
+  if (a < n + 1) {
+    double term = 1.0;
+    for (int r = 2; r <= n + 1; ++r) term /= r;  // 1/(n+1)!
+    double acc = 0.0;
+    for (int j = 0; j < 400; ++j) {
+      acc += term;
+      term *= a / (double)(j + n + 2);
+      if (term < 1e-18 * acc) break;
+    }
+    zd pw(1.0, 0.0);
+    const zd zb4 = std::conj(z) / 4.0;
+    for (int r = 0; r <= n; ++r) pw *= zb4;
+    return pref * pw * (std::exp(-a) * acc);
+  }
+  double part = 0.0, term = 1.0;
+  for (int r = 0; r <= n; ++r) {
+    if (r > 0) term *= a / r;
+    part += term;
+  }
+  zd zp(1.0, 0.0);
+  for (int r = 0; r <= n; ++r) zp *= z;
+  return pref / zp * (1.0 - std::exp(-a) * part);
+}
+
+static double xgrid(int j, int N, double L) { return L * (-M_PI + 2.0 * M_PI * (double)j / (double)N); }
+
+static void fill_ek(const dbar_plan* P, const double* k, int nb, cx<double>* dst /*[nb][2N]*/) {
+  const int N = P->N;
+  for (int s = 0; s < nb; ++s) {
+    const double k1 = k[2 * s], k2 = k[2 * s + 1];
+    for (int j = 0; j < N; ++j) {
+      const double x = xgrid(j, N, P->p.L);
+      // E_k = exp(conj(kz) - kz) = exp(-2i (k2 x + k1 y)) = ex(x) ey(y)
+      dst[(size_t)s * 2 * N + j] = mkc(std::cos(2.0 * k2 * x), -std::sin(2.0 * k2 * x));
+      dst[(size_t)s * 2 * N + N + j] = mkc(std::cos(2.0 * k1 * x), -std::sin(2.0 * k1 * x));
+    }
+  }
+}
+
+static dbar_status upload_ek(dbar_plan* P, const double* k, int nb, cudaStream_t st) {
+  const int N = P->N;
+  fill_ek(P, k, nb, P->h_ek);
+  for (int s = 0; s < nb; ++s) {
+    CK(cudaMemcpyAsync(P->ex64 + (size_t)s * N, P->h_ek + (size_t)s * 2 * N, N * sizeof(cx<double>),
+                       cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(P->ey64 + (size_t)s * N, P->h_ek + (size_t)s * 2 * N + N, N * sizeof(cx<double>),
+                       cudaMemcpyHostToDevice, st));
+  }
+  CK(launch_cast_fields(P->ex64, P->ex32, (long long)nb * N, st));
+  CK(launch_cast_fields(P->ey64, P->ey32, (long long)nb * N, st));
+  return DBAR_OK;
+}
+
+template <typename T>
+static PassArgs<T> base_args(const dbar_plan* P);
+
+template <>
+PassArgs<double> base_args<double>(const dbar_plan* P) {
+  PassArgs<double> a;
+  std::memset(&a, 0, sizeof(a));
+  a.g = make_geo<double>(P->N);
+  a.M = P->M;
+  a.tw = P->tw64;
+  a.Da = P->Da64;
+  a.Da64 = P->Da64;
+  a.DeltaT = P->Dt64;
+  a.QT = P->QT64;
+  a.ex = P->ex64;
+  a.ey = P->ey64;
+  a.inv2piL = P->inv2piL;
+  a.sw = P->sw;
+  a.fillscale = P->fillscale;
+  a.partA = P->partA;
+  a.nblkA = P->N / a.g.lines;
+  a.part = P->part2;
+  return a;
+}
+template <>
+PassArgs<float> base_args<float>(const dbar_plan* P) {
+  PassArgs<float> a;
+  std::memset(&a, 0, sizeof(a));
+  a.g = make_geo<float>(P->N);
+  a.M = P->M;
+  a.tw = P->tw32;
+  a.Da = P->Da32;
+  a.Da64 = P->Da64;
+  a.DeltaT = P->Dt32;
+  a.QT = P->QT32;
+  a.ex = P->ex32;
+  a.ey = P->ey32;
+  a.inv2piL = P->inv2piL;
+  a.sw = P->sw;
+  a.fillscale = P->fillscale;
+  a.partA = P->partA;
+  a.nblkA = P->N / a.g.lines;
+  a.part = P->part2;
+  return a;
+}
+
+// One application of K (A S = S + K S) to nb fields: S (T) -> T1 -> T2 -> out (T).
+template <typename T>
+static dbar_status apply_K(dbar_plan* P, const cx<T>* S, long long s_ss, const double* scale, int scale_ss,
+                           cx<T>* out, long long o_ss, const int* run, int nb, cudaStream_t st) {
+  PassArgs<T> a = base_args<T>(P);
+  a.run = run;
+  a.in = S;
+  a.in_ss = s_ss;
+  a.in_scale = scale;
+  a.in_scale_ss = scale_ss;
+  a.out = P->T1;
+  a.out_ss = P->n;
+  CK(launch_pass_a<T>(a, nb, st));
+  a.in = reinterpret_cast<const cx<T>*>(P->T1);
+  a.in_ss = P->n;
+  a.in_scale = nullptr;
+  a.out = P->T2;
+  CK((launch_pass_b<T, PB_MATVEC>(a, nb, st)));
+  a.in = reinterpret_cast<const cx<T>*>(P->T2);
+  a.out = out;
+  a.out_ss = o_ss;
+  CK((launch_pass_c<T, T, PC_KS>(a, nb, st)));
+  return DBAR_OK;
+}
+
+// h(S) for FP64 fields (m output): pass A then pass B without the forward transform.
+static dbar_status h_of_S64(dbar_plan* P, const cx<double>* S, long long s_ss, cx<double>* out, long long o_ss,
+                            int nb, cudaStream_t st) {
+  PassArgs<double> a = base_args<double>(P);
+  a.in = S;
+  a.in_ss = s_ss;
+  a.out = P->T1;
+  a.out_ss = P->n;
+  CK(launch_pass_a<double>(a, nb, st));
+  a.in = reinterpret_cast<const cx<double>*>(P->T1);
+  a.in_ss = P->n;
+  a.out = out;
+  a.out_ss = o_ss;
+  CK((launch_pass_b<double, PB_HOUT>(a, nb, st)));
+  return DBAR_OK;
+}
+
+// b = -i F(E_k Q) in FP64 -> b64, the Krylov start vector V[slot][0] (TI) and |b|^2 partials.
+template <typename TI>
+static dbar_status build_rhs(dbar_plan* P, int nb, cudaStream_t st) {
+  PassArgs<double> a = base_args<double>(P);
+  a.out = P->T2;
+  a.out_ss = P->n;
+  CK((launch_pass_b<double, PB_RHS>(a, nb, st)));
+  a.in = reinterpret_cast<const cx<double>*>(P->T2);
+  a.in_ss = P->n;
+  a.out = P->b64;
+  a.out_ss = P->n;
+  a.out2 = P->V;
+  a.out2_ss = (long long)(P->m + 1) * P->n;
+  CK((launch_pass_c<double, TI, PC_RHS>(a, nb, st)));
+  return DBAR_OK;
+}
+
+// r = b - A x in FP64 -> V[slot][0] (TI) and |r|^2 partials; only active slots.
+template <typename TI>
+static dbar_status true_residual(dbar_plan* P, int nb, cudaStream_t st) {
+  PassArgs<double> a = base_args<double>(P);
+  a.run = P->cs.active;
+  a.in = P->x64;
+  a.in_ss = P->n;
+  a.out = P->T1;
+  a.out_ss = P->n;
+  CK(launch_pass_a<double>(a, nb, st));
+  a.in = reinterpret_cast<const cx<double>*>(P->T1);
+  a.out = P->T2;
+  CK((launch_pass_b<double, PB_MATVEC>(a, nb, st)));
+  a.in = reinterpret_cast<const cx<double>*>(P->T2);
+  a.out = nullptr;
+  a.out2 = P->V;
+  a.out2_ss = (long long)(P->m + 1) * P->n;
+  a.b = P->b64;
+  a.x = P->x64;
+  a.f_ss = P->n;
+  CK((launch_pass_c<double, TI, PC_RES>(a, nb, st)));
+  return DBAR_OK;
+}
+
+template <typename TI>
+static dbar_status run_cycles(dbar_plan* P, int nb, cudaStream_t st) {
+  const long long n = P->n;
+  const int m = P->m;
+  const long long vss = (long long)(m + 1) * n;
+  cx<TI>* V = reinterpret_cast<cx<TI>*>(P->V);
+  cx<TI>* KS = reinterpret_cast<cx<TI>*>(P->KS);
+  KryArgs ka;
+  ka.n = n;
+  ka.mp1 = m + 1;
+  ka.nchunk = (int)((n + KR_CHUNK - 1) / KR_CHUNK);
+  ka.run = P->cs.run;
+  ka.sigma = P->cs.sigma;
+  ka.coef = P->coef;
+  ka.part = P->part;
+  ka.part2 = P->part2;
+  const int nblkC = P->N / make_geo<double>(P->N).lines;
+
+  CK(cudaMemsetAsync(P->x64, 0, (size_t)nb * n * sizeof(cx<double>), st));
+  dbar_status s = build_rhs<TI>(P, nb, st);
+  if (s != DBAR_OK) return s;
+  CK(launch_cycle_start(P->cs, P->part2, nblkC, 1, nb, st));
+
+  for (int cyc = 0; cyc < P->p.max_outer; ++cyc) {
+    CK(cudaMemcpyAsync(P->h_active, P->cs.active, nb * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    int any = 0;
+    for (int i = 0; i < nb; ++i) any |= P->h_active[i];
+    if (!any) break;
+    for (int j = 0; j < m; ++j) {
+      s = apply_K<TI>(P, V + (size_t)j * n, vss, P->cs.sigma + j, m + 1, KS, n, P->cs.run, nb, st);
+      if (s != DBAR_OK) return s;
+      CK(launch_dots<TI>(ka, V, vss, KS, n, j, nb, st));
+      CK(launch_finalize_h(ka, P->cs.H, j, nb, st));
+      CK(launch_update<TI>(ka, V, vss, KS, n, j, nb, st));
+      CK(launch_givens(ka, P->cs, j, nb, st));
+      if ((j & 7) == 7 && j + 1 < m) {  // stop launching once every slot has finished its cycle
+        CK(cudaMemcpyAsync(P->h_active, P->cs.run, nb * sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        int anyr = 0;
+        for (int i = 0; i < nb; ++i) anyr |= P->h_active[i];
+        if (!anyr) break;
+      }
+    }
+    CK(launch_solve_y(P->cs, nb, st));
+    CK(launch_xupdate<TI>(n, m + 1, P->cs.nsteps, P->cs.ycoef, V, vss, P->x64, n, nb, st));
+    s = true_residual<TI>(P, nb, st);
+    if (s != DBAR_OK) return s;
+    CK(launch_cycle_start(P->cs, P->part2, nblkC, 0, nb, st));
+  }
+  return DBAR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Plan creation.
+// ---------------------------------------------------------------------------
+static bool pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+static dbar_status check_params(const dbar_params* p) {
+  if (!p) return fail(DBAR_EINVAL, "params is NULL");
+  if (!pow2(p->N) || p->N < 32 || p->N > 2048) return fail(DBAR_EINVAL, "N must be a power of two in [32, 2048]");
+  if (!(p->L > 0.0) || !std::isfinite(p->L)) return fail(DBAR_EINVAL, "L must be finite and > 0");
+  if (p->M < 0 || p->M > 16) return fail(DBAR_EINVAL, "M must be in [0, 16]");
+  if (p->prec != DBAR_FP64 && p->prec != DBAR_MIXED) return fail(DBAR_EINVAL, "prec must be DBAR_FP64 or DBAR_MIXED");
+  if (p->restart < 1 || p->restart > 128) return fail(DBAR_EINVAL, "restart must be in [1, 128]");
+  if (p->max_iter < 1 || p->max_outer < 1) return fail(DBAR_EINVAL, "max_iter and max_outer must be >= 1");
+  if (!(p->tol > 0.0) || !(p->tol < 1.0)) return fail(DBAR_EINVAL, "tol must be in (0, 1)");
+  if (p->prec == DBAR_MIXED && !(p->inner_tol > 0.0 && p->inner_tol < 1.0))
+    return fail(DBAR_EINVAL, "inner_tol must be in (0, 1)");
+  if (p->max_batch < 0 || p->max_batch > 65535) return fail(DBAR_EINVAL, "max_batch must be in [0, 65535]");
+  return DBAR_OK;
+}
+
+static dbar_status plan_tables(dbar_plan* P) {
+  const int N = P->N;
+  const double L = P->p.L;
+  cudaStream_t st = 0;
+  // twiddles e^{-2 pi i t/N}
+  std::vector<cx<double>> tw(N);
+  std::vector<cx<float>> tw32(N);
+  for (int t = 0; t < N; ++t) {
+    const double ang = 2.0 * M_PI * (double)t / (double)N;
+    tw[t] = mkc(std::cos(ang), -std::sin(ang));
+    tw32[t] = mkc((float)tw[t].re, (float)tw[t].im);
+  }
+  CK(cudaMemcpy(P->tw64, tw.data(), N * sizeof(cx<double>), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(P->tw32, tw32.data(), N * sizeof(cx<float>), cudaMemcpyHostToDevice));
+  // D_a(p) = sum_j x_j^a e^{+2 pi i p j/N}
+  const int MA = P->MA;
+  std::vector<cx<double>> D((size_t)(MA + 1) * N);
+  std::vector<cx<float>> D32((size_t)(MA + 1) * N);
+  for (int aa = 0; aa <= MA; ++aa)
+    for (int p = 0; p < N; ++p) {
+      double re = 0.0, im = 0.0;
+      for (int j = 0; j < N; ++j) {
+        const double xa = std::pow(xgrid(j, N, L), aa);
+        const cx<double> w = tw[(size_t)((long long)p * j % N)];  // conj gives e^{+...}
+        re += xa * w.re;
+        im -= xa * w.im;
+      }
+      D[(size_t)aa * N + p] = mkc(re, im);
+      D32[(size_t)aa * N + p] = mkc((float)re, (float)im);
+    }
+  CK(cudaMemcpy(P->Da64, D.data(), D.size() * sizeof(cx<double>), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(P->Da32, D32.data(), D32.size() * sizeof(cx<float>), cudaMemcpyHostToDevice));
+
+  // Delta_n = W_n - V_n, V_n = F_d^{-1}(e^{-|xi|^2} conj(xi)^n / xi, 0 at xi = 0)
+  //         = (1/(2 pi L^2)) IDFT((-1)^{p1+p2} e^{-|xi|^2} conj(xi)^n / xi).
+  const int nf = P->M + 1;
+  const size_t nn = (size_t)N * N;
+  std::vector<cx<double>> hE(nf * nn), hW(nf * nn);
+  for (int p2 = 0; p2 < N; ++p2) {
+    const int m2 = p2 <= N / 2 ? p2 : p2 - N;
+    for (int p1 = 0; p1 < N; ++p1) {
+      const int m1 = p1 <= N / 2 ? p1 : p1 - N;
+      const zd xi((double)m1 / L, (double)m2 / L);
+      const double sg = ((p1 + p2) & 1) ? -1.0 : 1.0;
+      zd f(0.0, 0.0);
+      if (m1 != 0 || m2 != 0) f = std::exp(-std::norm(xi)) / xi * sg / (2.0 * M_PI * L * L);
+      for (int nn_ = 0; nn_ < nf; ++nn_) {
+        hE[nn_ * nn + (size_t)p2 * N + p1] = mkc(f.real(), f.imag());
+        f *= std::conj(xi);
+      }
+    }
+  }
+  for (int j2 = 0; j2 < N; ++j2)
+    for (int j1 = 0; j1 < N; ++j1) {
+      const zd z(xgrid(j1, N, L), xgrid(j2, N, L));
+      for (int nn_ = 0; nn_ < nf; ++nn_) {
+        const zd w = W_host(nn_, z);
+        hW[nn_ * nn + (size_t)j2 * N + j1] = mkc(w.real(), w.imag());
+      }
+    }
+  // device scratch for the inverse transforms: reuse the x and b workspaces when large
+  // enough, else allocate temporarily
+  cx<double>* dE = nullptr;
+  cx<double>* dW = nullptr;
+  CK(cudaMalloc(&dE, nf * nn * sizeof(cx<double>)));
+  cudaError_t e = cudaMalloc(&dW, nf * nn * sizeof(cx<double>));
+  if (e != cudaSuccess) {
+    cudaFree(dE);
+    return fail(DBAR_ENOMEM, "plan scratch allocation failed");
+  }
+  dbar_status s = DBAR_OK;
+  do {
+    if (cudaMemcpy(dE, hE.data(), nf * nn * sizeof(cx<double>), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(dW, hW.data(), nf * nn * sizeof(cx<double>), cudaMemcpyHostToDevice) != cudaSuccess) {
+      s = fail(DBAR_ECUDA, "table upload failed");
+      break;
+    }
+    // inverse 2-D DFT of the nf fields, in place through T1: rows (pass C raw inverse), columns (pass B raw inverse)
+    PassArgs<double> a = base_args<double>(P);
+    for (int f0 = 0; f0 < nf; f0 += P->B) {
+      const int cnt = std::min(P->B, nf - f0);
+      a.in = dE + f0 * nn;
+      a.in_ss = (long long)nn;
+      a.out = P->T1;
+      a.out_ss = (long long)nn;
+      if (launch_pass_c<double, double, PC_INV>(a, cnt, st) != cudaSuccess) { s = fail(DBAR_ECUDA, "pass C"); break; }
+      a.in = reinterpret_cast<const cx<double>*>(P->T1);
+      a.out = dE + f0 * nn;
+      if (launch_pass_b<double, PB_INV>(a, cnt, st) != cudaSuccess) { s = fail(DBAR_ECUDA, "pass B"); break; }
+    }
+    if (s != DBAR_OK) break;
+    if (launch_delta_build(dE, dW, P->Dt64, P->Dt32, N, nf, st) != cudaSuccess) {
+      s = fail(DBAR_ECUDA, "delta build");
+      break;
+    }
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) s = fail(DBAR_ECUDA, std::string("plan tables: ") + cudaGetErrorString(e));
+  } while (0);
+  cudaFree(dE);
+  cudaFree(dW);
+  return s;
+}
+
+extern "C" dbar_status dbar_plan_create(const dbar_params* p, dbar_plan_t* out) {
+  if (!out) return fail(DBAR_EINVAL, "out is NULL");
+  *out = nullptr;
+  dbar_status s = check_params(p);
+  if (s != DBAR_OK) return s;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return fail(DBAR_ECUDA, "no CUDA device is available");
+  }
+  dbar_plan* P = new (std::nothrow) dbar_plan();
+  if (!P) return fail(DBAR_ENOMEM, "host allocation failed");
+  P->p = *p;
+  P->N = p->N;
+  P->logN = 0;
+  while ((1 << P->logN) < P->N) ++P->logN;
+  P->M = p->M;
+  P->MA = std::max(1, p->M);
+  P->m = p->restart;
+  P->mixed = (p->prec == DBAR_MIXED);
+  P->n = (long long)P->N * P->N;
+  cudaGetDevice(&P->device);
+  const double L = p->L;
+  P->inv2piL = 1.0 / (2.0 * M_PI * L);
+  P->sw = 2.0 * M_PI * L * L / ((double)P->N * P->N);
+  P->fillscale = p->zero_fill ? 0.0 : 1.0 / (2.0 * M_PI * L * L);
+
+  const size_t F64 = (size_t)P->n * sizeof(cx<double>);
+  const size_t Fi = (size_t)P->n * P->inner_elem();
+  const int nchunk = (int)((P->n + KR_CHUNK - 1) / KR_CHUNK);
+  const int nblkA = P->N / std::min(make_geo<double>(P->N).lines, make_geo<float>(P->N).lines);
+  const size_t per_slot = 4 * F64 + (size_t)(P->m + 2) * Fi;
+  int B = p->max_batch;
+  if (B == 0) {
+    size_t freeb = 0, totb = 0;
+    cudaMemGetInfo(&freeb, &totb);
+    const size_t fixed = (size_t)(2 * (P->M + 1) + 3) * F64;
+    size_t avail = freeb > fixed ? (freeb - fixed) / 2 : 0;
+    B = (int)std::min<size_t>(256, std::max<size_t>(1, avail / per_slot));
+  }
+  P->B = B;
+  cudaError_t e = cudaSuccess;
+#define AL(ptr, cnt)                                                          \
+  do {                                                                        \
+    e = P->alloc(&(ptr), (cnt));                                              \
+    if (e != cudaSuccess) {                                                   \
+      delete P;                                                               \
+      return fail(e == cudaErrorMemoryAllocation ? DBAR_ENOMEM : DBAR_ECUDA,  \
+                  std::string("cudaMalloc failed for " #ptr ": ") +           \
+                      cudaGetErrorString(e));                                 \
+    }                                                                         \
+  } while (0)
+  const size_t n = (size_t)P->n;
+  AL(P->tw64, P->N);
+  AL(P->tw32, P->N);
+  AL(P->Da64, (size_t)(P->MA + 1) * P->N);
+  AL(P->Da32, (size_t)(P->MA + 1) * P->N);
+  AL(P->Dt64, (size_t)(P->M + 1) * n);
+  AL(P->Dt32, (size_t)(P->M + 1) * n);
+  AL(P->QT64, n);
+  AL(P->QT32, n);
+  AL(P->Qdev, n);
+  AL(P->ex64, (size_t)B * P->N);
+  AL(P->ey64, (size_t)B * P->N);
+  AL(P->ex32, (size_t)B * P->N);
+  AL(P->ey32, (size_t)B * P->N);
+  AL(P->x64, (size_t)B * n);
+  AL(P->b64, (size_t)B * n);
+  cx<double>* t1 = nullptr;
+  cx<double>* t2 = nullptr;
+  AL(t1, (size_t)B * n);
+  AL(t2, (size_t)B * n);
+  P->T1 = t1;
+  P->T2 = t2;
+  unsigned char* vb = nullptr;
+  AL(vb, (size_t)B * (P->m + 1) * Fi);
+  P->V = vb;
+  unsigned char* kb = nullptr;
+  AL(kb, (size_t)B * Fi);
+  P->KS = kb;
+  AL(P->partA, (size_t)B * nblkA * (P->M + 2));
+  AL(P->part, (size_t)B * (P->m + 1) * nchunk);
+  AL(P->part2, (size_t)B * std::max(std::max(nchunk, P->N), 2 * (P->M + 2)));
+  AL(P->coef, (size_t)B * (P->m + 1));
+  AL(P->flag, 4);
+  CycleState& c = P->cs;
+  const int m = P->m;
+  AL(c.H, (size_t)B * m * (m + 1));
+  AL(c.cs, (size_t)B * m);
+  AL(c.sn, (size_t)B * m);
+  AL(c.g, (size_t)B * (m + 1));
+  AL(c.sigma, (size_t)B * (m + 1));
+  AL(c.ycoef, (size_t)B * (m + 1));
+  AL(c.thr, B);
+  AL(c.bnorm, B);
+  AL(c.resid, B);
+  AL(c.run, B);
+  AL(c.active, B);
+  AL(c.nsteps, B);
+  AL(c.itot, B);
+  AL(c.ncyc, B);
+#undef AL
+  c.m = m;
+  c.max_iter = p->max_iter;
+  c.tol = p->tol;
+  c.inner_tol = P->mixed ? p->inner_tol : 0.0;
+  if (cudaMallocHost(&P->h_active, (size_t)B * sizeof(int)) != cudaSuccess ||
+      cudaMallocHost(&P->h_ek, (size_t)B * 2 * P->N * sizeof(cx<double>)) != cudaSuccess) {
+    delete P;
+    return fail(DBAR_ENOMEM, "pinned host allocation failed");
+  }
+  s = plan_tables(P);
+  if (s != DBAR_OK) {
+    delete P;
+    return s;
+  }
+  *out = P;
+  return DBAR_OK;
+}
+
+extern "C" dbar_status dbar_plan_destroy(dbar_plan_t plan) {
+  delete plan;
+  return DBAR_OK;
+}
+
+extern "C" dbar_status dbar_plan_info(dbar_plan_t plan, size_t* device_bytes, int* max_batch) {
+  if (!plan) return fail(DBAR_EINVAL, "plan is NULL");
+  if (device_bytes) *device_bytes = plan->bytes;
+  if (max_batch) *max_batch = plan->B;
+  return DBAR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Solve.
+// ---------------------------------------------------------------------------
+static dbar_status check_k(const double* k, int nk) {
+  if (nk < 0) return fail(DBAR_EINVAL, "nk < 0");
+  if (nk > 0 && !k) return fail(DBAR_EINVAL, "k is NULL");
+  for (int i = 0; i < 2 * nk; ++i)
+    if (!std::isfinite(k[i])) return fail(DBAR_EINVAL, "k has a non-finite entry");
+  return DBAR_OK;
+}
+
+// Q (complex128, device) -> QT64 / QT32, with a finiteness check.
+static dbar_status load_Q_device(dbar_plan* P, const cx<double>* Qd, cudaStream_t st) {
+  CK(cudaMemsetAsync(P->flag, 0, sizeof(int), st));
+  CK(launch_check_finite(reinterpret_cast<const double*>(Qd), 2 * P->n, P->flag, st));
+  CK(launch_transpose_q(Qd, P->QT64, P->QT32, P->N, st));
+  int bad = 0;
+  CK(cudaMemcpyAsync(&bad, P->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (bad) return fail(DBAR_EINVAL, "Q has a non-finite entry");
+  return DBAR_OK;
+}
+
+static dbar_status load_Q(dbar_plan* P, const double* Q, int on_device, cudaStream_t st) {
+  if (!Q) return fail(DBAR_EINVAL, "Q is NULL");
+  if (on_device) return load_Q_device(P, reinterpret_cast<const cx<double>*>(Q), st);
+  for (long long i = 0; i < 2 * P->n; ++i)
+    if (!std::isfinite(Q[i])) return fail(DBAR_EINVAL, "Q has a non-finite entry");
+  CK(cudaMemcpyAsync(P->Qdev, Q, P->n * sizeof(cx<double>), cudaMemcpyHostToDevice, st));
+  return load_Q_device(P, P->Qdev, st);
+}
+
+extern "C" dbar_status dbar_solve_cgo(dbar_plan_t P, const double* Q, int nk, const double* k, double* S_out,
+                                      double* m_out, int* iters, double* resid, int io_on_device, void* stream) {
+  if (!P) return fail(DBAR_EINVAL, "plan is NULL");
+  dbar_status s = check_k(k, nk);
+  if (s != DBAR_OK) return s;
+  if (nk > 0 && !S_out) return fail(DBAR_EINVAL, "S_out is NULL");
+  if (nk == 0) return DBAR_OK;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  s = load_Q(P, Q, io_on_device, st);
+  if (s != DBAR_OK) return s;
+  const long long n = P->n;
+  const cudaMemcpyKind d2o = io_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  bool noconv = false;
+  std::vector<int> it(2 * P->B), nc(P->B);
+  std::vector<double> rs(P->B);
+  for (int k0 = 0; k0 < nk; k0 += P->B) {
+    const int nb = std::min(P->B, nk - k0);
+    s = upload_ek(P, k + 2 * k0, nb, st);
+    if (s != DBAR_OK) return s;
+    s = P->mixed ? run_cycles<float>(P, nb, st) : run_cycles<double>(P, nb, st);
+    if (s != DBAR_OK) return s;
+    CK(cudaMemcpyAsync(S_out + (size_t)k0 * n * 2, P->x64, (size_t)nb * n * sizeof(cx<double>), d2o, st));
+    if (m_out) {
+      s = h_of_S64(P, P->x64, n, reinterpret_cast<cx<double>*>(P->T2), n, nb, st);
+      if (s != DBAR_OK) return s;
+      CK(cudaMemcpyAsync(m_out + (size_t)k0 * n * 2, P->T2, (size_t)nb * n * sizeof(cx<double>), d2o, st));
+    }
+    CK(cudaMemcpyAsync(it.data(), P->cs.itot, nb * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(nc.data(), P->cs.ncyc, nb * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(rs.data(), P->cs.resid, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int i = 0; i < nb; ++i) {
+      if (iters) {
+        iters[2 * (k0 + i)] = it[i];
+        iters[2 * (k0 + i) + 1] = nc[i];
+      }
+      if (resid) resid[k0 + i] = rs[i];
+      if (!(rs[i] <= P->p.tol)) noconv = true;
+    }
+  }
+  if (noconv) return fail(DBAR_ENOCONV, "some k did not reach tol");
+  return DBAR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Stage entry points.
+// ---------------------------------------------------------------------------
+static dbar_status check_stage(dbar_plan* P, int nk) {
+  if (!P) return fail(DBAR_EINVAL, "plan is NULL");
+  if (nk < 0 || nk > P->B) return fail(DBAR_EINVAL, "nk must be in [0, max_batch]");
+  return DBAR_OK;
+}
+
+extern "C" dbar_status dbar_apply(dbar_plan_t P, const void* Q, int nk, const double* k, const void* S, void* AS,
+                                  int fp32, void* stream) {
+  dbar_status s = check_stage(P, nk);
+  if (s != DBAR_OK) return s;
+  s = check_k(k, nk);
+  if (s != DBAR_OK) return s;
+  if (nk == 0) return DBAR_OK;
+  if (!Q || !S || !AS) return fail(DBAR_EINVAL, "NULL pointer");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  s = load_Q_device(P, reinterpret_cast<const cx<double>*>(Q), st);
+  if (s != DBAR_OK) return s;
+  s = upload_ek(P, k, nk, st);
+  if (s != DBAR_OK) return s;
+  const long long n = P->n;
+  if (fp32)
+    s = apply_K<float>(P, reinterpret_cast<const cx<float>*>(S), n, nullptr, 0, reinterpret_cast<cx<float>*>(P->KS), n,
+                       nullptr, nk, st);
+  else
+    s = apply_K<double>(P, reinterpret_cast<const cx<double>*>(S), n, nullptr, 0,
+                        reinterpret_cast<cx<double>*>(P->b64), n, nullptr, nk, st);
+  if (s != DBAR_OK) return s;
+  CK(launch_add_fields(S, fp32 ? P->KS : (void*)P->b64, AS, (long long)nk * n, fp32, st));
+  CK(cudaStreamSynchronize(st));
+  return DBAR_OK;
+}
+
+extern "C" dbar_status dbar_rhs(dbar_plan_t P, const double* Q, int nk, const double* k, double* b, void* stream) {
+  dbar_status s = check_stage(P, nk);
+  if (s != DBAR_OK) return s;
+  s = check_k(k, nk);
+  if (s != DBAR_OK) return s;
+  if (nk == 0) return DBAR_OK;
+  if (!Q || !b) return fail(DBAR_EINVAL, "NULL pointer");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  s = load_Q_device(P, reinterpret_cast<const cx<double>*>(Q), st);
+  if (s != DBAR_OK) return s;
+  s = upload_ek(P, k, nk, st);
+  if (s != DBAR_OK) return s;
+  s = P->mixed ? build_rhs<float>(P, nk, st) : build_rhs<double>(P, nk, st);
+  if (s != DBAR_OK) return s;
+  CK(cudaMemcpyAsync(b, P->b64, (size_t)nk * P->n * sizeof(cx<double>), cudaMemcpyDeviceToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  return DBAR_OK;
+}
+
+extern "C" dbar_status dbar_m_from_S(dbar_plan_t P, int nk, const double* S, double* m, void* stream) {
+  dbar_status s = check_stage(P, nk);
+  if (s != DBAR_OK) return s;
+  if (nk == 0) return DBAR_OK;
+  if (!S || !m) return fail(DBAR_EINVAL, "NULL pointer");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  s = h_of_S64(P, reinterpret_cast<const cx<double>*>(S), P->n, reinterpret_cast<cx<double>*>(m), P->n, nk, st);
+  if (s != DBAR_OK) return s;
+  CK(cudaStreamSynchronize(st));
+  return DBAR_OK;
+}
+
+extern "C" dbar_status dbar_taylor(dbar_plan_t P, int nk, const void* S, double* coef, int fp32, void* stream) {
+  dbar_status s = check_stage(P, nk);
+  if (s != DBAR_OK) return s;
+  if (nk == 0) return DBAR_OK;
+  if (!S || !coef) return fail(DBAR_EINVAL, "NULL pointer");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  int nblkA;
+  if (fp32) {
+    PassArgs<float> a = base_args<float>(P);
+    a.in = reinterpret_cast<const cx<float>*>(S);
+    a.in_ss = P->n;
+    a.out = P->T1;
+    a.out_ss = P->n;
+    nblkA = a.nblkA;
+    CK(launch_pass_a<float>(a, nk, st));
+  } else {
+    PassArgs<double> a = base_args<double>(P);
+    a.in = reinterpret_cast<const cx<double>*>(S);
+    a.in_ss = P->n;
+    a.out = P->T1;
+    a.out_ss = P->n;
+    nblkA = a.nblkA;
+    CK(launch_pass_a<double>(a, nk, st));
+  }
+  cx<double>* dc = reinterpret_cast<cx<double>*>(P->part2);
+  CK(launch_taylor_final(P->partA, nblkA, P->M, P->N, dc, nk, st));
+  CK(cudaMemcpyAsync(coef, dc, (size_t)nk * (P->M + 2) * sizeof(cx<double>), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return DBAR_OK;
+}
+
+extern "C" dbar_status dbar_fft2(dbar_plan_t P, int nk, const void* in, void* out, int sign, int fp32, void* stream) {
+  dbar_status s = check_stage(P, nk);
+  if (s != DBAR_OK) return s;
+  if (nk == 0) return DBAR_OK;
+  if (!in || !out) return fail(DBAR_EINVAL, "NULL pointer");
+  if (sign != 1 && sign != -1) return fail(DBAR_EINVAL, "sign must be +1 or -1");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (fp32) {
+    PassArgs<float> a = base_args<float>(P);
+    a.in = reinterpret_cast<const cx<float>*>(in);
+    a.in_ss = P->n;
+    a.out = P->T1;
+    a.out_ss = P->n;
+    CK(sign < 0 ? (launch_pass_c<float, float, PC_FWD>(a, nk, st)) : (launch_pass_c<float, float, PC_INV>(a, nk, st)));
+    a.in = reinterpret_cast<const cx<float>*>(P->T1);
+    a.out = out;
+    CK(sign < 0 ? (launch_pass_b<float, PB_FWD>(a, nk, st)) : (launch_pass_b<float, PB_INV>(a, nk, st)));
+  } else {
+    PassArgs<double> a = base_args<double>(P);
+    a.in = reinterpret_cast<const cx<double>*>(in);
+    a.in_ss = P->n;
+    a.out = P->T1;
+    a.out_ss = P->n;
+    CK(sign < 0 ? (launch_pass_c<double, double, PC_FWD>(a, nk, st))
+                : (launch_pass_c<double, double, PC_INV>(a, nk, st)));
+    a.in = reinterpret_cast<const cx<double>*>(P->T1);
+    a.out = out;
+    CK(sign < 0 ? (launch_pass_b<double, PB_FWD>(a, nk, st)) : (launch_pass_b<double, PB_INV>(a, nk, st)));
+  }
+  CK(cudaStreamSynchronize(st));
+  return DBAR_OK;
+}

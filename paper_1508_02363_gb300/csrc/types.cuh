@@ -1,0 +1,96 @@
+// Argument structures shared by the kernels and the host driver.
+#pragma once
+#include "cx.cuh"
+
+namespace dbar {
+
+struct Geo {
+  int N, logN, tpl, lines, P;
+};
+
+template <typename T>
+struct PassArgs {
+  Geo g;
+  int M;  // Taylor order
+  // input field (T), per-slot stride in complex elements; optional per-slot scale
+  const cx<T>* in;
+  long long in_ss;
+  const double* in_scale;
+  int in_scale_ss;
+  // outputs
+  void* out;
+  long long out_ss;
+  void* out2;  // second output (pass C right-hand side / residual: Krylov start vector)
+  long long out2_ss;
+  // pass C residual inputs (FP64 fields)
+  const cx<double>* b;
+  const cx<double>* x;
+  long long f_ss;
+  const int* run;  // per-slot flags (nullable)
+  // tables
+  const cx<T>* tw;       // [N]   e^{-2 pi i t/N}
+  const cx<T>* Da;       // [MA+1][N]
+  const cx<double>* Da64;
+  const cx<T>* DeltaT;   // [M+1][N (x index)][N (y index)]
+  const cx<T>* QT;       // [N (x index)][N (y index)]
+  const cx<T>* ex;       // [slot][N]  e^{-2 i k2 x_j}
+  const cx<T>* ey;       // [slot][N]  e^{-2 i k1 y_j}
+  double inv2piL;        // 1/(2 pi L)
+  double sw;             // 2 pi L^2 / N^2
+  double fillscale;      // 1/(2 pi L^2), or 0 for the zero-fill reading
+  cx<double>* partA;     // [slot][nblkA][M+2]
+  int nblkA;
+  double* part;          // [slot][gridDim.x] squared-norm partials (pass C)
+};
+
+template <typename T>
+struct KMax {
+  static constexpr int threads = 512;
+};
+template <>
+struct KMax<double> {
+  static constexpr int threads = 256;
+};
+
+constexpr int KR_THREADS = 256;
+constexpr int KR_EPT = 8;  // complex elements per thread
+constexpr int KR_CHUNK = KR_THREADS * KR_EPT;
+
+struct KryArgs {
+  long long n;       // complex elements per vector (N*N)
+  int mp1;           // basis vectors per slot (restart + 1)
+  int nchunk;        // blocks per slot
+  const int* run;    // per-slot flags of the current cycle
+  const double* sigma;  // [slot][mp1]
+  double* coef;         // [slot][mp1] update coefficients
+  double* part;         // [slot][mp1][nchunk]
+  double* part2;        // [slot][nchunk]
+};
+
+struct CycleState {
+  double* H;       // [slot][m][m+1]  column j holds rows 0..j+1
+  double* cs;      // [slot][m]
+  double* sn;      // [slot][m]
+  double* g;       // [slot][m+1]
+  double* sigma;   // [slot][m+1]
+  double* ycoef;   // [slot][m+1]
+  double* thr;     // [slot] stop threshold of the current cycle
+  double* bnorm;   // [slot]
+  double* resid;   // [slot] last true relative residual
+  int* run;        // [slot]
+  int* active;     // [slot]
+  int* nsteps;     // [slot]
+  int* itot;       // [slot] total inner iterations
+  int* ncyc;       // [slot]
+  int m;
+  int max_iter;
+  double tol;
+  double inner_tol;  // > 0: mixed-precision inner criterion relative to beta
+};
+
+// pass B modes: operator, right-hand side, h only, raw column DFTs
+enum { PB_MATVEC = 0, PB_RHS = 1, PB_HOUT = 2, PB_FWD = 3, PB_INV = 4 };
+// pass C modes: K S, right-hand side, FP64 residual, raw row DFTs
+enum { PC_KS = 0, PC_RHS = 1, PC_RES = 2, PC_FWD = 3, PC_INV = 4 };
+
+}  // namespace dbar

@@ -1,0 +1,204 @@
+"""ctypes binding of libdbar_gb300.so (include/dbar.h), argument marshalling only.
+
+Every step of the solve runs in the library's CUDA kernels; this module only
+converts arguments.  Device buffers are passed as torch CUDA tensors (torch is
+used for device memory and streams), host buffers as numpy arrays.  Importing
+this module fails if the library has not been built: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libdbar_gb300.so")
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(f"{_LIB_PATH} is missing: build it with `python -m paper_1508_02363_gb300.build`")
+_lib = ctypes.CDLL(_LIB_PATH)
+
+DBAR_OK, DBAR_EINVAL, DBAR_ENOMEM, DBAR_ENOCONV, DBAR_ETIMEOUT, DBAR_ECUDA, DBAR_EBUSY = range(7)
+DBAR_FP64, DBAR_MIXED = 0, 1
+STATUS_NAMES = ["DBAR_OK", "DBAR_EINVAL", "DBAR_ENOMEM", "DBAR_ENOCONV", "DBAR_ETIMEOUT", "DBAR_ECUDA",
+                "DBAR_EBUSY"]
+EXPORTED = ["dbar_params_init", "dbar_last_error", "dbar_plan_create", "dbar_plan_destroy", "dbar_plan_info",
+            "dbar_solve_cgo", "dbar_apply", "dbar_rhs", "dbar_m_from_S", "dbar_taylor", "dbar_fft2"]
+
+
+class dbar_params(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("L", ctypes.c_double), ("M", ctypes.c_int), ("prec", ctypes.c_int),
+                ("restart", ctypes.c_int), ("max_iter", ctypes.c_int), ("tol", ctypes.c_double),
+                ("zero_fill", ctypes.c_int), ("max_batch", ctypes.c_int), ("inner_tol", ctypes.c_double),
+                ("max_outer", ctypes.c_int)]
+
+
+class DbarError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 7 else status}: {msg}")
+        self.status = status
+
+
+_vp, _dp, _ip, _int, _dbl = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), \
+    ctypes.c_int, ctypes.c_double
+_lib.dbar_params_init.argtypes = [ctypes.POINTER(dbar_params), _int, _dbl]
+_lib.dbar_params_init.restype = None
+_lib.dbar_last_error.restype = ctypes.c_char_p
+_lib.dbar_plan_create.argtypes = [ctypes.POINTER(dbar_params), ctypes.POINTER(_vp)]
+_lib.dbar_plan_destroy.argtypes = [_vp]
+_lib.dbar_plan_info.argtypes = [_vp, ctypes.POINTER(ctypes.c_size_t), _ip]
+_lib.dbar_solve_cgo.argtypes = [_vp, _vp, _int, _dp, _vp, _vp, _ip, _dp, _int, _vp]
+_lib.dbar_apply.argtypes = [_vp, _vp, _int, _dp, _vp, _vp, _int, _vp]
+_lib.dbar_rhs.argtypes = [_vp, _vp, _int, _dp, _vp, _vp]
+_lib.dbar_m_from_S.argtypes = [_vp, _int, _vp, _vp, _vp]
+_lib.dbar_taylor.argtypes = [_vp, _int, _vp, _dp, _int, _vp]
+_lib.dbar_fft2.argtypes = [_vp, _int, _vp, _vp, _int, _int, _vp]
+for _f in EXPORTED:
+    if _f not in ("dbar_params_init", "dbar_last_error"):
+        getattr(_lib, _f).restype = _int
+
+
+def _check(st: int, allow=(DBAR_OK,)) -> int:
+    if st not in allow:
+        raise DbarError(st, _lib.dbar_last_error().decode())
+    return st
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return ctypes.c_void_p(0)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(x):
+    """Device pointer of a torch tensor or host pointer of a numpy array."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return ctypes.c_void_p(x.data_ptr())
+    return ctypes.c_void_p(x.ctypes.data)
+
+
+def _kbuf(k) -> np.ndarray:
+    k = np.ascontiguousarray(np.asarray(k, dtype=np.complex128).ravel())
+    return k.view(np.float64)
+
+
+def dbar_params_init(N: int, L: float, **overrides) -> dbar_params:
+    p = dbar_params()
+    _lib.dbar_params_init(ctypes.byref(p), int(N), float(L))
+    for key, v in overrides.items():
+        if key == "prec" and isinstance(v, str):
+            v = {"fp64": DBAR_FP64, "mixed": DBAR_MIXED}[v]
+        setattr(p, key, v)
+    return p
+
+
+def dbar_last_error() -> str:
+    return _lib.dbar_last_error().decode()
+
+
+def dbar_plan_create(params: dbar_params) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(_lib.dbar_plan_create(ctypes.byref(params), ctypes.byref(h)))
+    return h
+
+
+def dbar_plan_destroy(plan) -> None:
+    _check(_lib.dbar_plan_destroy(plan))
+
+
+def dbar_plan_info(plan):
+    b = ctypes.c_size_t()
+    mb = ctypes.c_int()
+    _check(_lib.dbar_plan_info(plan, ctypes.byref(b), ctypes.byref(mb)))
+    return b.value, mb.value
+
+
+def dbar_solve_cgo(plan, Q, k, S_out, m_out=None, iters=None, resid=None, io_on_device=None, stream=None) -> int:
+    """Q, S_out, m_out: numpy complex128 arrays (host) or torch complex128 CUDA tensors.
+    iters: numpy int32 [nk, 2]; resid: numpy float64 [nk].  Returns the status
+    (DBAR_OK or DBAR_ENOCONV); other failures raise DbarError."""
+    kb = _kbuf(k)
+    nk = kb.size // 2
+    if io_on_device is None:
+        io_on_device = hasattr(Q, "data_ptr")
+    ip = iters.ctypes.data_as(_ip) if iters is not None else None
+    rp = resid.ctypes.data_as(_dp) if resid is not None else None
+    st = _lib.dbar_solve_cgo(plan, _ptr(Q), nk, kb.ctypes.data_as(_dp), _ptr(S_out), _ptr(m_out), ip, rp,
+                             int(bool(io_on_device)), _stream(stream))
+    return _check(st, (DBAR_OK, DBAR_ENOCONV))
+
+
+def dbar_apply(plan, Q, k, S, AS, fp32: bool = False, stream=None) -> None:
+    kb = _kbuf(k)
+    _check(_lib.dbar_apply(plan, _ptr(Q), kb.size // 2, kb.ctypes.data_as(_dp), _ptr(S), _ptr(AS), int(fp32),
+                           _stream(stream)))
+
+
+def dbar_rhs(plan, Q, k, b, stream=None) -> None:
+    kb = _kbuf(k)
+    _check(_lib.dbar_rhs(plan, _ptr(Q), kb.size // 2, kb.ctypes.data_as(_dp), _ptr(b), _stream(stream)))
+
+
+def dbar_m_from_S(plan, nk: int, S, m, stream=None) -> None:
+    _check(_lib.dbar_m_from_S(plan, int(nk), _ptr(S), _ptr(m), _stream(stream)))
+
+
+def dbar_taylor(plan, nk: int, S, M: int, fp32: bool = False, stream=None) -> np.ndarray:
+    out = np.zeros((nk, M + 2), dtype=np.complex128)
+    _check(_lib.dbar_taylor(plan, int(nk), _ptr(S), out.view(np.float64).ctypes.data_as(_dp), int(fp32),
+                            _stream(stream)))
+    return out
+
+
+def dbar_fft2(plan, nk: int, x, y, sign: int, fp32: bool = False, stream=None) -> None:
+    _check(_lib.dbar_fft2(plan, int(nk), _ptr(x), _ptr(y), int(sign), int(fp32), _stream(stream)))
+
+
+class Plan:
+    """Owning wrapper: Plan(N, L, M=2, prec='mixed', ...) -> .solve(Q, k)."""
+
+    def __init__(self, N: int, L: float, **params):
+        self.params = dbar_params_init(N, L, **params)
+        self.N, self.L, self.M = N, L, self.params.M
+        self.handle = dbar_plan_create(self.params)
+        self.device_bytes, self.max_batch = dbar_plan_info(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            dbar_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, Q, k, want_m: bool = True, stream=None):
+        """Host in, host out: returns dict(S, m, iters, resid, status)."""
+        k = np.atleast_1d(np.asarray(k, dtype=np.complex128))
+        nk, N = k.size, self.N
+        Q = np.ascontiguousarray(np.asarray(Q, dtype=np.complex128).reshape(N, N))
+        S = np.zeros((nk, N, N), np.complex128)
+        m = np.zeros((nk, N, N), np.complex128) if want_m else None
+        iters = np.zeros((nk, 2), np.int32)
+        resid = np.zeros(nk, np.float64)
+        st = dbar_solve_cgo(self.handle, Q, k, S, m, iters, resid, io_on_device=False, stream=stream)
+        return {"S": S, "m": m, "iters": iters, "resid": resid, "status": st}
+
+    def solve_device(self, Q, k, S_out, m_out=None, stream=None):
+        """Device in, device out (torch complex128 CUDA tensors)."""
+        k = np.atleast_1d(np.asarray(k, dtype=np.complex128))
+        iters = np.zeros((k.size, 2), np.int32)
+        resid = np.zeros(k.size, np.float64)
+        st = dbar_solve_cgo(self.handle, Q, k, S_out, m_out, iters, resid, io_on_device=True, stream=stream)
+        return {"iters": iters, "resid": resid, "status": st}
