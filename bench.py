@@ -1,0 +1,374 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the GB300 spectral D-bar CGO solve.
+
+Workload (default): N = 1024 on [-10pi, 10pi]^2, Q a seeded 4-Gaussian mixture,
+128 values of k with |k| log-uniform in [0.1, 8]; FP32 inner GMRES with FP64
+refinement to ||b - A S||/||b|| <= 1e-12.  One step = one dbar_solve_cgo call
+solving all 128 k (right-hand sides, every Krylov cycle, FP64 residuals).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  With --gpus N > 1 (launched by torchrun) every
+rank solves its own copy of the workload (replicas over k, weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CGO solves/sec at N=1024^2 (rel err<=1e-10 vs FP64), %HBM roofline, p50/p99 ms"
+FALLBACK_HBM_GBS = 6800.0
+
+
+# ----------------------------------------------------------------------------- helpers
+
+def env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            for key in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if key in d:
+                    return float(d[key]), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def source_digest():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1508_02363_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kind):
+    """DRAM bytes per launch of `kind` from the committed ncu summary, if it was
+    taken on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path))
+        if d.get("source_digest") != source_digest():
+            return None
+        return d.get("kinds", {}).get(kind, {}).get("dram_bytes_per_launch")
+    except Exception:
+        return None
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+
+def _oracle_solve(args):
+    N, L, M, tol, Q, k = args
+    from oracle import dbar_oracle as orc
+    r = orc.solve_cgo(Q, k, N, L, M=M, tol=tol, restart=40)
+    return r["iters"], r["resid"]
+
+
+def cpu_oracle_step(w, ks, cores):
+    """Solve len(ks) k values with the CPU oracle, one per process, in parallel."""
+    ctx = mp.get_context("spawn")
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    os.environ.setdefault("MKL_NUM_THREADS", "1")
+    with ctx.Pool(processes=min(cores, len(ks))) as pool:
+        t0 = time.perf_counter()
+        out = pool.map(_oracle_solve, [(w.N, w.L, w.M, w.tol, w.Q, complex(k)) for k in ks])
+        dt = time.perf_counter() - t0
+    return dt, out
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# ----------------------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import torch
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1508_02363_gb300 import dbar
+    import workloads as wl
+
+    w = wl.BY_NAME[args.workload]()
+    nk, N = w.k.size, w.N
+    plan = dbar.Plan(N, w.L, M=w.M, prec="mixed" if w.mixed else "fp64", tol=w.tol, restart=args.restart,
+                     inner_tol=args.inner_tol)
+    stream = torch.cuda.current_stream()
+    Qd = torch.from_numpy(w.Q).cuda()
+    Sd = torch.empty((nk, N, N), dtype=torch.complex128, device="cuda")
+
+    def step():
+        return plan.solve_device(Qd, w.k, Sd, stream=stream)
+
+    for _ in range(args.warmup):
+        r = step()
+    torch.cuda.synchronize()
+    barrier()
+    dbar.dbar_profile(plan.handle, True)
+    launches0 = dbar.dbar_launch_count(plan.handle)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    results = []
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        barrier()
+        evs[0].record(stream)
+        for i in range(args.steps):
+            results.append(step())
+            evs[i + 1].record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    launches = dbar.dbar_launch_count(plan.handle) - launches0
+    step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
+    total_ms = sum(step_ms)
+    prof = dbar.profile_table(plan.handle)
+    dbar.dbar_profile(plan.handle, False)
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = nk * world * args.steps / (total_ms / 1e3)
+    last = results[-1]
+    iters = last["iters"]
+    resid = last["resid"]
+
+    # error of the mixed results against the plain FP64 GPU solve, per sampled k,
+    # and the plain single-k FP64 solve rate on the same GPU
+    sample = np.unique(np.linspace(0, nk - 1, min(nk, args.check_k)).astype(int))
+    p64 = dbar.Plan(N, w.L, M=w.M, prec="fp64", tol=min(w.tol, 1e-13), restart=args.restart, max_batch=len(sample))
+    S64 = torch.empty((len(sample), N, N), dtype=torch.complex128, device="cuda")
+    p64.solve_device(Qd, w.k[sample], S64, stream=stream)
+    torch.cuda.synchronize()
+    errs = []
+    for j, i in enumerate(sample):
+        d = (Sd[i] - S64[j]).abs().max().item() / S64[j].abs().max().item()
+        errs.append(d)
+    p1 = dbar.Plan(N, w.L, M=w.M, prec="fp64", tol=w.tol, restart=args.restart, max_batch=1)
+    S1 = torch.empty((1, N, N), dtype=torch.complex128, device="cuda")
+    p1.solve_device(Qd, w.k[:1], S1, stream=stream)  # warm
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    nrep = 3
+    for _ in range(nrep):
+        p1.solve_device(Qd, w.k[:1], S1, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fp64_single_rate = nrep / (e0.elapsed_time(e1) / 1e3)
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    Qh = torch.from_numpy(w.Q).pin_memory()
+    Sh = torch.empty((nk, N, N), dtype=torch.complex128).pin_memory()
+    kh = np.ascontiguousarray(w.k)
+    e2e_steps = max(1, min(args.steps, 2))
+    plan.solve(Qh.numpy(), kh, want_m=False)  # warm the host path
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        dbar.dbar_solve_cgo(plan.handle, Qh.numpy(), kh, Sh.numpy(), None, None, None, io_on_device=False,
+                            stream=stream)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e = {"value": nk / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": int(Qh.numel() * 16 + kh.size * 16),
+           "d2h_bytes_per_step": int(Sh.numel() * 16)}
+
+    # roofline of the dominant kernel kind
+    peak, peak_kind = peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    dom_name, (dom_ms, dom_launches, dom_bytes) = dom
+    achieved = dom_bytes / (dom_ms / 1e3) / 1e9 if dom_ms > 0 else 0.0
+    traffic = ncu_traffic(dom_name)
+    all_bytes = sum(v[2] for v in prof.values())
+    all_ms = sum(v[0] for v in prof.values())
+    roofline = {"bound": "hbm", "kernel": dom_name, "achieved": round(achieved, 1), "peak": peak,
+                "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": traffic,
+                "algorithmic_bytes_per_launch": dom_bytes / max(dom_launches, 1),
+                "avg_launch_ms": dom_ms / max(dom_launches, 1),
+                "whole_step": {"bytes_per_step": all_bytes / args.steps,
+                               "gbs_over_kernel_time": round(all_bytes / (all_ms / 1e3) / 1e9, 1) if all_ms else 0,
+                               "gbs_over_step_time": round(all_bytes / args.steps / (ms_per_step / 1e3) / 1e9, 1),
+                               "frac_of_peak_over_step_time": round(
+                                   all_bytes / args.steps / (ms_per_step / 1e3) / 1e9 / peak, 4)},
+                "kinds": {k: {"ms": round(v[0], 3), "launches": v[1], "GBs": round(v[2] / (v[0] / 1e3) / 1e9, 1)
+                              if v[0] > 0 else 0.0} for k, v in prof.items()}}
+
+    out = {"metric": METRIC, "value": round(value, 3), "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if w.mixed else "f64",
+           "data": "synthetic (seeded Gaussian-mixture potential and k list)",
+           "config": {"workload": w.name, "N": N, "L": w.L, "nk": nk, "M": w.M, "tol": w.tol,
+                      "prec": "mixed" if w.mixed else "fp64", "restart": args.restart, "inner_tol": args.inner_tol,
+                      "parallelism": f"replicas over k x{world}",
+                      "l2": "inputs larger than L2 (device working set %.1f GB)" % (plan.device_bytes / 1e9)},
+           "p50_ms": round(statistics.median(step_ms), 3),
+           "p99_ms": round(float(np.percentile(step_ms, 99)), 3),
+           "iters_inner_mean": float(np.mean(iters[:, 0])), "cycles_max": int(np.max(iters[:, 1])),
+           "resid_max": float(np.max(resid)), "err_vs_fp64_max": float(max(errs)),
+           "err_vs_fp64_sampled_k": [int(i) for i in sample],
+           "fp64_plain_single_k_solves_per_s": round(fp64_single_rate, 3),
+           "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline, "clocks": clk.summary()}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = cpu_cores()
+        ncpu = min(cores, args.cpu_sample)
+        ks = w.k[np.linspace(0, nk - 1, ncpu).astype(int)]
+        dt, res = cpu_oracle_step(w, ks, cores)
+        out["cpu_baseline"] = {"value": round(len(ks) / dt, 4), "unit": "solves/s", "cores": min(cores, len(ks)),
+                               "kind": "oracle",
+                               "sample": f"{len(ks)} of the {nk} k values solved once each by the FP64 CPU "
+                                         f"oracle, one process per core, wall {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return
+    import workloads as wl
+    w = wl.BY_NAME[args.workload]()
+    cores = cpu_cores()
+    nper = min(cores, args.cpu_sample)
+    small = wl.plain_fp64()
+    for _ in range(args.warmup):  # warm-up: start the pool and touch the code paths on a small case
+        cpu_oracle_step(small, small.k[:1], 1)
+    times, done = [], 0
+    for s in range(args.steps):
+        idx = (np.arange(nper) * max(1, w.k.size // nper) + s) % w.k.size
+        dt, _ = cpu_oracle_step(w, w.k[idx], cores)
+        times.append(dt)
+        done += nper
+    total = sum(times)
+    value = done / total
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "solves/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total / args.steps * 1e3, 1),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded Gaussian-mixture potential and k list)",
+           "config": {"workload": w.name, "N": w.N, "L": w.L, "nk": int(w.k.size), "M": w.M, "tol": w.tol,
+                      "parallelism": "CPU processes"},
+           "cpu_baseline": {"value": round(value, 4), "unit": "solves/s", "cores": min(cores, nper),
+                            "kind": "oracle",
+                            "sample": f"each step solves {nper} of the {w.k.size} k values with the FP64 CPU "
+                                      f"oracle, one process per core"},
+           "e2e": {"value": round(value, 4), "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="mixed_1024")
+    ap.add_argument("--restart", type=int, default=32)
+    ap.add_argument("--inner-tol", dest="inner_tol", type=float, default=1e-6)
+    ap.add_argument("--check-k", dest="check_k", type=int, default=4)
+    ap.add_argument("--cpu-sample", dest="cpu_sample", type=int, default=16)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

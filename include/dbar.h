@@ -142,6 +142,26 @@ dbar_status dbar_taylor(dbar_plan_t plan, int nk, const void* S, double* coef, i
 dbar_status dbar_fft2(dbar_plan_t plan, int nk, const void* in, void* out, int sign, int fp32,
                       void* stream);
 
+/* --- tracing ------------------------------------------------------------ */
+
+/* Number of kernel kinds the profiler distinguishes, and the name of one. */
+int dbar_profile_nkinds(void);
+const char* dbar_profile_kind_name(int kind);
+
+/* Turns CUDA-event timing of every kernel launch of dbar_solve_cgo on (1) or
+ * off (0) and clears the counters.  With timing on, each launch is bracketed
+ * by two events on the solve's stream; the totals are folded in at the
+ * solve's host synchronisation points. */
+dbar_status dbar_profile(dbar_plan_t plan, int enable);
+
+/* Totals of one kind since dbar_profile(plan, 1): summed event time in ms,
+ * launches, and the algorithmic bytes of those launches (every field the
+ * method reads or writes counted once per use).  Any pointer may be NULL. */
+dbar_status dbar_profile_read(dbar_plan_t plan, int kind, double* ms, long long* launches, double* bytes);
+
+/* Kernels launched by this plan since its creation (profiling on or off). */
+dbar_status dbar_launch_count(dbar_plan_t plan, long long* count);
+
 #ifdef __cplusplus
 }
 #endif

@@ -39,8 +39,67 @@ static dbar_status fail(dbar_status st, const std::string& msg) {
                   std::string(#call) + ": " + cudaGetErrorString(e_));                       \
   } while (0)
 
+// Kernel kinds for the event profiler (dbar_profile_*).
+enum {
+  K_PASS_A, K_PASS_B, K_PASS_C, K_DOTS, K_UPDATE, K_SCALAR, K_XUPDATE,
+  K_RES_A, K_RES_B, K_RES_C, K_RHS, K_OTHER, K_NKINDS
+};
+static const char* const kKindNames[K_NKINDS] = {
+    "inner_pass_a_rows", "inner_pass_b_cols", "inner_pass_c_rows", "arnoldi_dots", "arnoldi_update",
+    "krylov_scalar", "solution_update", "fp64_residual_pass_a", "fp64_residual_pass_b",
+    "fp64_residual_pass_c", "rhs", "other"};
+
+// CUDA-event timing of every launch of the solve, grouped by kind, plus the
+// algorithmic bytes of each kind (fields read and written once per use).
+struct Profiler {
+  bool on = false;
+  struct Rec {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  std::vector<cudaEvent_t> pool;
+  std::vector<Rec> pending;
+  double ms[K_NKINDS] = {0};
+  long long launches[K_NKINDS] = {0};
+  double bytes[K_NKINDS] = {0};
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
+  void reset() {
+    harvest();
+    for (int i = 0; i < K_NKINDS; ++i) ms[i] = bytes[i] = 0, launches[i] = 0;
+  }
+  // after a stream synchronisation: fold every recorded pair into the totals
+  void harvest() {
+    for (const Rec& r : pending) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) ms[r.kind] += t;
+      pool.push_back(r.a);
+      pool.push_back(r.b);
+    }
+    pending.clear();
+    cudaGetLastError();
+  }
+  ~Profiler() {
+    for (const Rec& r : pending) {
+      pool.push_back(r.a);
+      pool.push_back(r.b);
+    }
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+  }
+};
+
 struct dbar_plan {
   dbar_params p;
+  Profiler prof;
+  long long nlaunch = 0;  // kernels launched by this plan
   int N = 0, logN = 0, M = 0, MA = 0, B = 0, m = 0;
   bool mixed = false;
   int device = 0;
@@ -77,6 +136,7 @@ struct dbar_plan {
   CycleState cs;
   // host staging
   int* h_active = nullptr;
+  int* h_nsteps = nullptr;
   cx<double>* h_ek = nullptr;  // pinned [B][2N]
 
   double inv2piL = 0, sw = 0, fillscale = 0;
@@ -97,6 +157,7 @@ struct dbar_plan {
     cudaSetDevice(device);
     for (void* q : allocs) cudaFree(q);
     if (h_active) cudaFreeHost(h_active);
+    if (h_nsteps) cudaFreeHost(h_nsteps);
     if (h_ek) cudaFreeHost(h_ek);
     cudaSetDevice(cur);
   }
@@ -164,6 +225,21 @@ static zd W_host(int n, zd z) {
 
 static double xgrid(int j, int N, double L) { return L * (-M_PI + 2.0 * M_PI * (double)j / (double)N); }
 
+// Launch through the profiler: counts the launch and, when profiling is on,
+// brackets it with CUDA events on the launching stream.
+template <typename F>
+static cudaError_t timed(dbar_plan* P, cudaStream_t st, int kind, F&& f) {
+  ++P->nlaunch;
+  if (!P->prof.on) return f();
+  cudaEvent_t a = P->prof.get(), b = P->prof.get();
+  cudaEventRecord(a, st);
+  cudaError_t e = f();
+  cudaEventRecord(b, st);
+  P->prof.pending.push_back({kind, a, b});
+  P->prof.launches[kind] += 1;
+  return e;
+}
+
 static void fill_ek(const dbar_plan* P, const double* k, int nb, cx<double>* dst /*[nb][2N]*/) {
   const int N = P->N;
   for (int s = 0; s < nb; ++s) {
@@ -186,8 +262,8 @@ static dbar_status upload_ek(dbar_plan* P, const double* k, int nb, cudaStream_t
     CK(cudaMemcpyAsync(P->ey64 + (size_t)s * N, P->h_ek + (size_t)s * 2 * N + N, N * sizeof(cx<double>),
                        cudaMemcpyHostToDevice, st));
   }
-  CK(launch_cast_fields(P->ex64, P->ex32, (long long)nb * N, st));
-  CK(launch_cast_fields(P->ey64, P->ey32, (long long)nb * N, st));
+  CK(timed(P, st, K_OTHER, [&] { return launch_cast_fields(P->ex64, P->ex32, (long long)nb * N, st); }));
+  CK(timed(P, st, K_OTHER, [&] { return launch_cast_fields(P->ey64, P->ey32, (long long)nb * N, st); }));
   return DBAR_OK;
 }
 
@@ -249,16 +325,16 @@ static dbar_status apply_K(dbar_plan* P, const cx<T>* S, long long s_ss, const d
   a.in_scale_ss = scale_ss;
   a.out = P->T1;
   a.out_ss = P->n;
-  CK(launch_pass_a<T>(a, nb, st));
+  CK(timed(P, st, K_PASS_A, [&] { return launch_pass_a<T>(a, nb, st); }));
   a.in = reinterpret_cast<const cx<T>*>(P->T1);
   a.in_ss = P->n;
   a.in_scale = nullptr;
   a.out = P->T2;
-  CK((launch_pass_b<T, PB_MATVEC>(a, nb, st)));
+  CK(timed(P, st, K_PASS_B, [&] { return launch_pass_b<T, PB_MATVEC>(a, nb, st); }));
   a.in = reinterpret_cast<const cx<T>*>(P->T2);
   a.out = out;
   a.out_ss = o_ss;
-  CK((launch_pass_c<T, T, PC_KS>(a, nb, st)));
+  CK(timed(P, st, K_PASS_C, [&] { return launch_pass_c<T, T, PC_KS>(a, nb, st); }));
   return DBAR_OK;
 }
 
@@ -270,12 +346,12 @@ static dbar_status h_of_S64(dbar_plan* P, const cx<double>* S, long long s_ss, c
   a.in_ss = s_ss;
   a.out = P->T1;
   a.out_ss = P->n;
-  CK(launch_pass_a<double>(a, nb, st));
+  CK(timed(P, st, K_OTHER, [&] { return launch_pass_a<double>(a, nb, st); }));
   a.in = reinterpret_cast<const cx<double>*>(P->T1);
   a.in_ss = P->n;
   a.out = out;
   a.out_ss = o_ss;
-  CK((launch_pass_b<double, PB_HOUT>(a, nb, st)));
+  CK(timed(P, st, K_OTHER, [&] { return launch_pass_b<double, PB_HOUT>(a, nb, st); }));
   return DBAR_OK;
 }
 
@@ -285,14 +361,14 @@ static dbar_status build_rhs(dbar_plan* P, int nb, cudaStream_t st) {
   PassArgs<double> a = base_args<double>(P);
   a.out = P->T2;
   a.out_ss = P->n;
-  CK((launch_pass_b<double, PB_RHS>(a, nb, st)));
+  CK(timed(P, st, K_RHS, [&] { return launch_pass_b<double, PB_RHS>(a, nb, st); }));
   a.in = reinterpret_cast<const cx<double>*>(P->T2);
   a.in_ss = P->n;
   a.out = P->b64;
   a.out_ss = P->n;
   a.out2 = P->V;
   a.out2_ss = (long long)(P->m + 1) * P->n;
-  CK((launch_pass_c<double, TI, PC_RHS>(a, nb, st)));
+  CK(timed(P, st, K_RHS, [&] { return launch_pass_c<double, TI, PC_RHS>(a, nb, st); }));
   return DBAR_OK;
 }
 
@@ -305,10 +381,10 @@ static dbar_status true_residual(dbar_plan* P, int nb, cudaStream_t st) {
   a.in_ss = P->n;
   a.out = P->T1;
   a.out_ss = P->n;
-  CK(launch_pass_a<double>(a, nb, st));
+  CK(timed(P, st, K_RES_A, [&] { return launch_pass_a<double>(a, nb, st); }));
   a.in = reinterpret_cast<const cx<double>*>(P->T1);
   a.out = P->T2;
-  CK((launch_pass_b<double, PB_MATVEC>(a, nb, st)));
+  CK(timed(P, st, K_RES_B, [&] { return launch_pass_b<double, PB_MATVEC>(a, nb, st); }));
   a.in = reinterpret_cast<const cx<double>*>(P->T2);
   a.out = nullptr;
   a.out2 = P->V;
@@ -316,8 +392,39 @@ static dbar_status true_residual(dbar_plan* P, int nb, cudaStream_t st) {
   a.b = P->b64;
   a.x = P->x64;
   a.f_ss = P->n;
-  CK((launch_pass_c<double, TI, PC_RES>(a, nb, st)));
+  CK(timed(P, st, K_RES_C, [&] { return launch_pass_c<double, TI, PC_RES>(a, nb, st); }));
   return DBAR_OK;
+}
+
+// Algorithmic bytes of one finished cycle (profiling only): every field the
+// method reads or writes counted once per use, F = one inner-precision field,
+// F64 = one FP64 field.  Per Krylov step j of a slot: pass A 2F (read v_j,
+// write T1), pass B 2F (read T1, write T2), pass C 2F (read T2, write K v_j),
+// dots (j+2)F (v_0..v_j and K v_j), update (j+3)F (the same, plus the new
+// vector); per launch of pass B the shared tables Q and Delta_0..Delta_M,
+// (M+2)F.  Per cycle and slot: solution update (ns F + 2 F64), FP64 residual
+// passes 2 F64 + 2 F64 + (3 F64 + F), plus (M+2) F64 of tables per pass-B launch.
+static void account_cycle(dbar_plan* P, const int* act, const int* ns, int nb, int launched_steps) {
+  if (!P->prof.on) return;
+  const double F = (double)P->n * P->inner_elem(), F64 = (double)P->n * sizeof(cx<double>);
+  double* by = P->prof.bytes;
+  int nact = 0;
+  for (int s = 0; s < nb; ++s) {
+    if (!act[s]) continue;
+    ++nact;
+    const int k = ns[s];
+    by[K_PASS_A] += 2.0 * F * k;
+    by[K_PASS_B] += 2.0 * F * k;
+    by[K_PASS_C] += 2.0 * F * k;
+    by[K_DOTS] += F * (k * 2.0 + k * (k - 1) / 2.0);
+    by[K_UPDATE] += F * (k * 3.0 + k * (k - 1) / 2.0);
+    by[K_XUPDATE] += F * k + 2.0 * F64;
+    by[K_RES_A] += 2.0 * F64;
+    by[K_RES_B] += 2.0 * F64;
+    by[K_RES_C] += 3.0 * F64 + F;
+  }
+  by[K_PASS_B] += (double)launched_steps * (P->M + 2) * F;
+  if (nact) by[K_RES_B] += (P->M + 2) * F64;
 }
 
 template <typename TI>
@@ -341,21 +448,34 @@ static dbar_status run_cycles(dbar_plan* P, int nb, cudaStream_t st) {
   CK(cudaMemsetAsync(P->x64, 0, (size_t)nb * n * sizeof(cx<double>), st));
   dbar_status s = build_rhs<TI>(P, nb, st);
   if (s != DBAR_OK) return s;
-  CK(launch_cycle_start(P->cs, P->part2, nblkC, 1, nb, st));
+  CK(timed(P, st, K_SCALAR, [&] { return launch_cycle_start(P->cs, P->part2, nblkC, 1, nb, st); }));
+  if (P->prof.on) {
+    const double F = (double)n * P->inner_elem(), F64 = (double)n * sizeof(cx<double>);
+    P->prof.bytes[K_RHS] += nb * (4.0 * F64 + F) + (P->M + 2) * F64;
+  }
 
+  std::vector<int> prev_act(nb, 0);
+  int prev_launched = 0;
+  bool pending_account = false;
   for (int cyc = 0; cyc < P->p.max_outer; ++cyc) {
     CK(cudaMemcpyAsync(P->h_active, P->cs.active, nb * sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    P->prof.harvest();
+    if (pending_account) account_cycle(P, prev_act.data(), P->h_nsteps, nb, prev_launched);
+    pending_account = false;
     int any = 0;
     for (int i = 0; i < nb; ++i) any |= P->h_active[i];
     if (!any) break;
+    std::copy(P->h_active, P->h_active + nb, prev_act.begin());
+    int launched = 0;
     for (int j = 0; j < m; ++j) {
       s = apply_K<TI>(P, V + (size_t)j * n, vss, P->cs.sigma + j, m + 1, KS, n, P->cs.run, nb, st);
       if (s != DBAR_OK) return s;
-      CK(launch_dots<TI>(ka, V, vss, KS, n, j, nb, st));
-      CK(launch_finalize_h(ka, P->cs.H, j, nb, st));
-      CK(launch_update<TI>(ka, V, vss, KS, n, j, nb, st));
-      CK(launch_givens(ka, P->cs, j, nb, st));
+      CK(timed(P, st, K_DOTS, [&] { return launch_dots<TI>(ka, V, vss, KS, n, j, nb, st); }));
+      CK(timed(P, st, K_SCALAR, [&] { return launch_finalize_h(ka, P->cs.H, j, nb, st); }));
+      CK(timed(P, st, K_UPDATE, [&] { return launch_update<TI>(ka, V, vss, KS, n, j, nb, st); }));
+      CK(timed(P, st, K_SCALAR, [&] { return launch_givens(ka, P->cs, j, nb, st); }));
+      ++launched;
       if ((j & 7) == 7 && j + 1 < m) {  // stop launching once every slot has finished its cycle
         CK(cudaMemcpyAsync(P->h_active, P->cs.run, nb * sizeof(int), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
@@ -364,11 +484,21 @@ static dbar_status run_cycles(dbar_plan* P, int nb, cudaStream_t st) {
         if (!anyr) break;
       }
     }
-    CK(launch_solve_y(P->cs, nb, st));
-    CK(launch_xupdate<TI>(n, m + 1, P->cs.nsteps, P->cs.ycoef, V, vss, P->x64, n, nb, st));
+    CK(timed(P, st, K_SCALAR, [&] { return launch_solve_y(P->cs, nb, st); }));
+    CK(cudaMemcpyAsync(P->h_nsteps, P->cs.nsteps, nb * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(timed(P, st, K_XUPDATE, [&] {
+      return launch_xupdate<TI>(n, m + 1, P->cs.nsteps, P->cs.ycoef, V, vss, P->x64, n, nb, st);
+    }));
     s = true_residual<TI>(P, nb, st);
     if (s != DBAR_OK) return s;
-    CK(launch_cycle_start(P->cs, P->part2, nblkC, 0, nb, st));
+    CK(timed(P, st, K_SCALAR, [&] { return launch_cycle_start(P->cs, P->part2, nblkC, 0, nb, st); }));
+    pending_account = true;
+    prev_launched = launched;
+  }
+  if (pending_account) {
+    CK(cudaStreamSynchronize(st));
+    P->prof.harvest();
+    account_cycle(P, prev_act.data(), P->h_nsteps, nb, prev_launched);
   }
   return DBAR_OK;
 }
@@ -603,6 +733,7 @@ extern "C" dbar_status dbar_plan_create(const dbar_params* p, dbar_plan_t* out) 
   c.tol = p->tol;
   c.inner_tol = P->mixed ? p->inner_tol : 0.0;
   if (cudaMallocHost(&P->h_active, (size_t)B * sizeof(int)) != cudaSuccess ||
+      cudaMallocHost(&P->h_nsteps, (size_t)B * sizeof(int)) != cudaSuccess ||
       cudaMallocHost(&P->h_ek, (size_t)B * 2 * P->N * sizeof(cx<double>)) != cudaSuccess) {
     delete P;
     return fail(DBAR_ENOMEM, "pinned host allocation failed");
@@ -642,8 +773,8 @@ static dbar_status check_k(const double* k, int nk) {
 // Q (complex128, device) -> QT64 / QT32, with a finiteness check.
 static dbar_status load_Q_device(dbar_plan* P, const cx<double>* Qd, cudaStream_t st) {
   CK(cudaMemsetAsync(P->flag, 0, sizeof(int), st));
-  CK(launch_check_finite(reinterpret_cast<const double*>(Qd), 2 * P->n, P->flag, st));
-  CK(launch_transpose_q(Qd, P->QT64, P->QT32, P->N, st));
+  CK(timed(P, st, K_OTHER, [&] { return launch_check_finite(reinterpret_cast<const double*>(Qd), 2 * P->n, P->flag, st); }));
+  CK(timed(P, st, K_OTHER, [&] { return launch_transpose_q(Qd, P->QT64, P->QT32, P->N, st); }));
   int bad = 0;
   CK(cudaMemcpyAsync(&bad, P->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -831,5 +962,37 @@ extern "C" dbar_status dbar_fft2(dbar_plan_t P, int nk, const void* in, void* ou
     CK(sign < 0 ? (launch_pass_b<double, PB_FWD>(a, nk, st)) : (launch_pass_b<double, PB_INV>(a, nk, st)));
   }
   CK(cudaStreamSynchronize(st));
+  return DBAR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Profiling.
+// ---------------------------------------------------------------------------
+extern "C" int dbar_profile_nkinds(void) { return K_NKINDS; }
+
+extern "C" const char* dbar_profile_kind_name(int kind) {
+  return (kind >= 0 && kind < K_NKINDS) ? kKindNames[kind] : "";
+}
+
+extern "C" dbar_status dbar_profile(dbar_plan_t P, int enable) {
+  if (!P) return fail(DBAR_EINVAL, "plan is NULL");
+  P->prof.reset();
+  P->prof.on = enable != 0;
+  return DBAR_OK;
+}
+
+extern "C" dbar_status dbar_profile_read(dbar_plan_t P, int kind, double* ms, long long* launches, double* bytes) {
+  if (!P) return fail(DBAR_EINVAL, "plan is NULL");
+  if (kind < 0 || kind >= K_NKINDS) return fail(DBAR_EINVAL, "kind out of range");
+  P->prof.harvest();
+  if (ms) *ms = P->prof.ms[kind];
+  if (launches) *launches = P->prof.launches[kind];
+  if (bytes) *bytes = P->prof.bytes[kind];
+  return DBAR_OK;
+}
+
+extern "C" dbar_status dbar_launch_count(dbar_plan_t P, long long* count) {
+  if (!P || !count) return fail(DBAR_EINVAL, "NULL argument");
+  *count = P->nlaunch;
   return DBAR_OK;
 }

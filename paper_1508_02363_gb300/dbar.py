@@ -22,7 +22,9 @@ DBAR_FP64, DBAR_MIXED = 0, 1
 STATUS_NAMES = ["DBAR_OK", "DBAR_EINVAL", "DBAR_ENOMEM", "DBAR_ENOCONV", "DBAR_ETIMEOUT", "DBAR_ECUDA",
                 "DBAR_EBUSY"]
 EXPORTED = ["dbar_params_init", "dbar_last_error", "dbar_plan_create", "dbar_plan_destroy", "dbar_plan_info",
-            "dbar_solve_cgo", "dbar_apply", "dbar_rhs", "dbar_m_from_S", "dbar_taylor", "dbar_fft2"]
+            "dbar_solve_cgo", "dbar_apply", "dbar_rhs", "dbar_m_from_S", "dbar_taylor", "dbar_fft2",
+            "dbar_profile_nkinds", "dbar_profile_kind_name", "dbar_profile", "dbar_profile_read",
+            "dbar_launch_count"]
 
 
 class dbar_params(ctypes.Structure):
@@ -52,8 +54,14 @@ _lib.dbar_rhs.argtypes = [_vp, _vp, _int, _dp, _vp, _vp]
 _lib.dbar_m_from_S.argtypes = [_vp, _int, _vp, _vp, _vp]
 _lib.dbar_taylor.argtypes = [_vp, _int, _vp, _dp, _int, _vp]
 _lib.dbar_fft2.argtypes = [_vp, _int, _vp, _vp, _int, _int, _vp]
+_lib.dbar_profile_nkinds.argtypes = []
+_lib.dbar_profile_kind_name.argtypes = [_int]
+_lib.dbar_profile_kind_name.restype = ctypes.c_char_p
+_lib.dbar_profile.argtypes = [_vp, _int]
+_lib.dbar_profile_read.argtypes = [_vp, _int, _dp, ctypes.POINTER(ctypes.c_longlong), _dp]
+_lib.dbar_launch_count.argtypes = [_vp, ctypes.POINTER(ctypes.c_longlong)]
 for _f in EXPORTED:
-    if _f not in ("dbar_params_init", "dbar_last_error"):
+    if _f not in ("dbar_params_init", "dbar_last_error", "dbar_profile_kind_name"):
         getattr(_lib, _f).restype = _int
 
 
@@ -161,6 +169,35 @@ def dbar_taylor(plan, nk: int, S, M: int, fp32: bool = False, stream=None) -> np
 
 def dbar_fft2(plan, nk: int, x, y, sign: int, fp32: bool = False, stream=None) -> None:
     _check(_lib.dbar_fft2(plan, int(nk), _ptr(x), _ptr(y), int(sign), int(fp32), _stream(stream)))
+
+
+def dbar_profile_nkinds() -> int:
+    return _lib.dbar_profile_nkinds()
+
+
+def dbar_profile_kind_name(kind: int) -> str:
+    return _lib.dbar_profile_kind_name(int(kind)).decode()
+
+
+def dbar_profile(plan, enable: bool) -> None:
+    _check(_lib.dbar_profile(plan, int(bool(enable))))
+
+
+def dbar_profile_read(plan, kind: int):
+    ms, n, by = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double()
+    _check(_lib.dbar_profile_read(plan, int(kind), ctypes.byref(ms), ctypes.byref(n), ctypes.byref(by)))
+    return ms.value, n.value, by.value
+
+
+def dbar_launch_count(plan) -> int:
+    c = ctypes.c_longlong()
+    _check(_lib.dbar_launch_count(plan, ctypes.byref(c)))
+    return c.value
+
+
+def profile_table(plan) -> dict:
+    """{kind name: (ms, launches, algorithmic bytes)} for every kernel kind."""
+    return {dbar_profile_kind_name(i): dbar_profile_read(plan, i) for i in range(dbar_profile_nkinds())}
 
 
 class Plan:
