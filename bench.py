@@ -183,8 +183,11 @@ def run_ours(args):
 
     w = wl.BY_NAME[args.workload]()
     nk, N = w.k.size, w.N
+    if args.nk:
+        w.k = w.k[:args.nk]
+    nk = w.k.size
     plan = dbar.Plan(N, w.L, M=w.M, prec="mixed" if w.mixed else "fp64", tol=w.tol, restart=args.restart,
-                     inner_tol=args.inner_tol)
+                     inner_tol=args.inner_tol, max_batch=nk, max_outer=args.max_outer)
     stream = torch.cuda.current_stream()
     Qd = torch.from_numpy(w.Q).cuda()
     Sd = torch.empty((nk, N, N), dtype=torch.complex128, device="cuda")
@@ -223,6 +226,14 @@ def run_ours(args):
     last = results[-1]
     iters = last["iters"]
     resid = last["resid"]
+    if args.quick:
+        if rank == 0:
+            print(json.dumps({"quick": True, "workload": w.name, "nk": nk, "ms_per_step": ms_per_step,
+                              "solves_per_s": value, "iters_inner_mean": float(np.mean(iters[:, 0])),
+                              "resid_max": float(np.max(resid)), "gpu_launches": int(launches),
+                              "kinds": {k: [round(v[0], 3), v[1], round(v[2] / (v[0] / 1e3) / 1e9, 1)
+                                            if v[0] > 0 else 0] for k, v in prof.items()}}))
+        return
 
     # error of the mixed results against the plain FP64 GPU solve, per sampled k,
     # and the plain single-k FP64 solve rate on the same GPU
@@ -363,6 +374,10 @@ def main():
     ap.add_argument("--check-k", dest="check_k", type=int, default=4)
     ap.add_argument("--cpu-sample", dest="cpu_sample", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nk", type=int, default=0, help="solve only the first nk k values (profiling cases)")
+    ap.add_argument("--max-outer", dest="max_outer", type=int, default=40)
+    ap.add_argument("--quick", action="store_true",
+                    help="time the solve only (no FP64 comparison, end-to-end leg or CPU baseline)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -18,7 +18,12 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libdbar_gb300.so")
-SOURCES = ["kern_f64.cu", "kern_f32.cu", "plan.cu"]
+SIZES = range(5, 12)  # N = 32 .. 2048
+# (source, object name, extra flags): the pass kernels once per precision and size
+UNITS = ([("kern_pass.cu", f"pass_{t}_{l}", [f"-DDBAR_T={t}", f"-DDBAR_LOGN={l}",
+                                              f"-DDBAR_T_IS_DOUBLE={int(t == 'double')}"])
+          for t in ("double", "float") for l in SIZES] +
+         [("kern_krylov.cu", "krylov", []), ("dispatch.cu", "dispatch", []), ("plan.cu", "plan", [])])
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -29,15 +34,16 @@ def nvcc() -> str:
     return exe
 
 
-def _compile(src: str, verbose: bool) -> str:
-    obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
-    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+def _compile(unit, verbose: bool) -> str:
+    src, name, flags = unit
+    obj = os.path.join(BUILD, name + ".o")
+    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", *flags,
            "-I", os.path.join(ROOT, "include"), "-c", os.path.join(CSRC, src), "-o", obj]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
-        raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
+        raise RuntimeError(f"nvcc failed for {name}:\n{r.stdout}\n{r.stderr}")
     if verbose:
         sys.stderr.write(r.stderr)
     return obj
@@ -57,8 +63,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not _stale():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose), SOURCES))
+    workers = max(1, min(len(UNITS), os.cpu_count() or 1))
+    with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+        objs = list(ex.map(lambda u: _compile(u, verbose), UNITS))
     tmp = LIB + ".tmp"
     cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)

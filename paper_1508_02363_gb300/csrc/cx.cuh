@@ -138,89 +138,105 @@ __device__ __forceinline__ void dft_reg(cx<T>* v) {
 }
 
 // Padded shared-memory index: one spare slot every 16 elements keeps the
-// stride-R writes of the first stage free of bank conflicts.
+// stride-R writes of the first stage free of bank conflicts.  Lines (rows or
+// columns) sit `pitch_of(N)` elements apart; the pitch is 2 mod 16, so the
+// lanes of a warp that work on neighbouring lines hit distinct banks.
 __device__ __forceinline__ int padi(int i) { return i + (i >> 4); }
-__host__ __device__ __forceinline__ int line_pitch(int N) { return N + (N >> 4) + 1; }
+__host__ __device__ constexpr int pitch_of(int N) { return N + (N >> 4) + 2; }
 
 // One Stockham stage of radix R on a line of length N held by TPL = N/16
-// threads.  Each thread owns 16 elements: 16/R butterflies j = t + b*TPL.
-// Inputs x[j + r N/R] (from registers in the first stage, from shared memory
-// otherwise), twiddle w^{r (j mod Ns)} with w = e^{-+2 pi i/(Ns R)}, R-point
-// DFT, outputs at ((j - j mod Ns) R + j mod Ns) + r Ns.  The last stage keeps
-// its outputs in registers: v[q] = X[t + q TPL].
-template <typename T, int R, bool INV>
-__device__ __forceinline__ void fft_stage(cx<T> (&v)[16], cx<T>* line, int N, int Ns, int t, int TPL,
-                                          const cx<T>* __restrict__ tw, bool first, bool last) {
-  constexpr int B = 16 / R;
-  const int nb = N / R;
-  cx<T> u[16];
-  if (first) {
-#pragma unroll
-    for (int r = 0; r < 16; ++r) u[r] = v[r];
-  } else {
-#pragma unroll
-    for (int b = 0; b < B; ++b) {
-      const int j = t + b * TPL;
-#pragma unroll
-      for (int r = 0; r < R; ++r) u[b * R + r] = line[padi(j + r * nb)];
-    }
-  }
-#pragma unroll
-  for (int b = 0; b < B; ++b) {
-    const int j = t + b * TPL;
-    const int k = j & (Ns - 1);
-    if (Ns > 1) {
-      const int step = N / (Ns * R);
-#pragma unroll
-      for (int r = 1; r < R; ++r) {
-        cx<T> w = ldg(tw + r * k * step);
-        if (INV) w.im = -w.im;
-        u[b * R + r] = cmul(u[b * R + r], w);
-      }
-    }
-    dft_reg<T, R, INV>(&u[b * R]);
-  }
-  if (last) {
+// threads; each thread owns 16 elements, i.e. 16/R butterflies j = t + b TPL.
+// Inputs x[j + r N/R] (already in registers in the first stage: v[r] =
+// x[t + r TPL]), twiddle w^{r (j mod NS)} with w = e^{-+2 pi i/(NS R)} read
+// from the table tw[s] = e^{-2 pi i s/N}, R-point DFT, outputs at
+// ((j - j mod NS) R + j mod NS) + r NS.  The last stage (NS R = N) keeps its
+// outputs in registers: v[q] = X[t + q TPL].
+template <typename T, int N, int R, int NS, bool INV, bool FIRST, bool LAST>
+__device__ __forceinline__ void fft_stage(cx<T> (&v)[16], cx<T>* line, int t, const cx<T>* __restrict__ tw) {
+  constexpr int TPL = N / 16, B = 16 / R, NB = N / R;
+  static_assert(!FIRST || R == 16, "the first stage is radix 16");
+  if (!FIRST) {
 #pragma unroll
     for (int b = 0; b < B; ++b)
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[b + r * B] = u[b * R + r];
+      for (int r = 0; r < R; ++r) v[b * R + r] = line[padi(t + b * TPL + r * NB)];
+  }
+#pragma unroll
+  for (int b = 0; b < B; ++b) {
+    if (NS > 1) {
+      constexpr int STEP = N / (NS * R);
+      const int k = (t + b * TPL) & (NS - 1);
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        cx<T> w = ldg(tw + r * k * STEP);
+        if (INV) w.im = -w.im;
+        v[b * R + r] = cmul(v[b * R + r], w);
+      }
+    }
+    dft_reg<T, R, INV>(&v[b * R]);
+  }
+  if (LAST) {
+    static_assert(!LAST || NS * R == N, "the last stage completes the transform");
+    cx<T> u[16];
+#pragma unroll
+    for (int b = 0; b < B; ++b)
+#pragma unroll
+      for (int r = 0; r < R; ++r) u[b + r * B] = v[b * R + r];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = u[i];
   } else {
-    __syncthreads();
+    __syncthreads();  // every thread has read the inputs of this stage
 #pragma unroll
     for (int b = 0; b < B; ++b) {
       const int j = t + b * TPL;
-      const int k = j & (Ns - 1);
+      const int k = j & (NS - 1);
       const int base = (j - k) * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) line[padi(base + r * Ns)] = u[b * R + r];
+      for (int r = 0; r < R; ++r) line[padi(base + r * NS)] = v[b * R + r];
     }
     __syncthreads();
   }
 }
 
-// Full length-N transform (N = 2^logN >= 16) of one line per thread group.
-// On entry v[q] = x[t + q TPL]; on exit v[q] = X[t + q TPL], with
-// X[p] = sum_j x[j] e^{-+2 pi i p j / N} (unnormalised; + for INV).
-// Every thread of the block must call this with the same N.
-template <typename T, bool INV>
-__device__ __forceinline__ void fft_line(cx<T> (&v)[16], cx<T>* line, int N, int logN, int t, int TPL,
-                                         const cx<T>* __restrict__ tw) {
-  int rem = logN - 4;
-  fft_stage<T, 16, INV>(v, line, N, 1, t, TPL, tw, true, rem == 0);
-  int Ns = 16;
-  while (rem > 0) {
-    const int lr = rem >= 4 ? 4 : rem;
-    const bool last = (rem == lr);
-    switch (lr) {
-      case 4: fft_stage<T, 16, INV>(v, line, N, Ns, t, TPL, tw, false, last); break;
-      case 3: fft_stage<T, 8, INV>(v, line, N, Ns, t, TPL, tw, false, last); break;
-      case 2: fft_stage<T, 4, INV>(v, line, N, Ns, t, TPL, tw, false, last); break;
-      default: fft_stage<T, 2, INV>(v, line, N, Ns, t, TPL, tw, false, last); break;
-    }
-    Ns <<= lr;
-    rem -= lr;
+// Full length-N transform, N = 2^LOGN in [32, 4096]: radix 16 first, then
+// 16 and the remainder.  On entry v[q] = x[t + q TPL]; on exit v[q] = X[t + q TPL],
+// X[p] = sum_j x[j] e^{-+2 pi i p j/N} (unnormalised; + for INV).  Every thread
+// of the block calls this together (it synchronises the block).
+template <typename T, int LOGN, bool INV>
+__device__ __forceinline__ void fft_line(cx<T> (&v)[16], cx<T>* line, int t, const cx<T>* __restrict__ tw) {
+  constexpr int N = 1 << LOGN;
+  constexpr int L1 = LOGN - 4;
+  static_assert(L1 >= 1 && L1 <= 8, "N must be in [32, 4096]");
+  if constexpr (L1 <= 4) {
+    fft_stage<T, N, 16, 1, INV, true, false>(v, line, t, tw);
+    fft_stage<T, N, (1 << L1), 16, INV, false, true>(v, line, t, tw);
+  } else {
+    fft_stage<T, N, 16, 1, INV, true, false>(v, line, t, tw);
+    fft_stage<T, N, 16, 16, INV, false, false>(v, line, t, tw);
+    fft_stage<T, N, (1 << (L1 - 4)), 256, INV, false, true>(v, line, t, tw);
   }
+}
+
+// Block shapes (shared by the kernels and the host launchers).
+//  rows:    LINES lines of TPL = N/16 consecutive threads, 256 threads at most.
+//  columns: COLS columns; a warp covers CW neighbouring columns x 32/CW
+//           consecutive t, so each load of the 16 elements of a thread is a
+//           set of 32*sizeof(cx)/CW-byte row segments (coalesced straight
+//           from/to registers).
+__host__ __device__ constexpr int row_lines(int logN) {
+  return (256 / ((1 << logN) / 16)) < (1 << logN) ? (256 / ((1 << logN) / 16)) : (1 << logN);
+}
+__host__ __device__ constexpr int col_cap(int logN, int esz) { return (esz == 8 ? 512 : 256) / ((1 << logN) / 16) > 0 ? (esz == 8 ? 512 : 256) / ((1 << logN) / 16) : 1; }
+__host__ __device__ constexpr int col_cw(int logN, int esz) {
+  // 64-byte row segments when possible; small N: one warp spans all t of CW columns
+  return ((1 << logN) / 16 >= 32 / (esz == 8 ? 8 : 4))
+             ? ((esz == 8 ? 8 : 4) < col_cap(logN, esz) ? (esz == 8 ? 8 : 4) : col_cap(logN, esz))
+             : 32 / ((1 << logN) / 16);
+}
+__host__ __device__ constexpr int col_cols(int logN, int esz) {
+  return (col_cap(logN, esz) > col_cw(logN, esz) ? col_cap(logN, esz) : col_cw(logN, esz)) < (1 << logN)
+             ? (col_cap(logN, esz) > col_cw(logN, esz) ? col_cap(logN, esz) : col_cw(logN, esz))
+             : (1 << logN);
 }
 
 }  // namespace dbar

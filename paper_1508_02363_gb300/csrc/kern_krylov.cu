@@ -1,13 +1,43 @@
-// FP64 (complex128) instantiations, the per-slot scalar Krylov kernels and the
-// small helper kernels used at plan and solve set-up.
-#include "kern_impl.cuh"
+// Krylov kernels (both precisions), the per-slot scalar kernels and the small
+// helper kernels used at plan and solve set-up.
+#include "krylov.cuh"
+#include "launch.cuh"
+#include "passes.cuh"
 
 namespace dbar {
-DBAR_INSTANTIATE(double, double)
-template cudaError_t launch_pass_c<double, double, PC_RHS>(const PassArgs<double>&, int, cudaStream_t);
-template cudaError_t launch_pass_c<double, float, PC_RHS>(const PassArgs<double>&, int, cudaStream_t);
-template cudaError_t launch_pass_c<double, double, PC_RES>(const PassArgs<double>&, int, cudaStream_t);
-template cudaError_t launch_pass_c<double, float, PC_RES>(const PassArgs<double>&, int, cudaStream_t);
+
+template <typename T>
+cudaError_t launch_dots(const KryArgs& a, const cx<T>* V, long long vss, const cx<T>* KS, long long kss, int j,
+                        int nslots, cudaStream_t s) {
+  if (nslots <= 0) return cudaSuccess;
+  k_dots<T><<<dim3(a.nchunk, nslots), KR_THREADS, 0, s>>>(a, V, vss, KS, kss, j);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_update(const KryArgs& a, cx<T>* V, long long vss, const cx<T>* KS, long long kss, int j,
+                          int nslots, cudaStream_t s) {
+  if (nslots <= 0) return cudaSuccess;
+  k_update<T><<<dim3(a.nchunk, nslots), KR_THREADS, 0, s>>>(a, V, vss, KS, kss, j);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_xupdate(long long n, int mp1, const int* nsteps, const double* ycoef, const cx<T>* V,
+                           long long vss, cx<double>* X, long long xss, int nslots, cudaStream_t s) {
+  if (nslots <= 0) return cudaSuccess;
+  const int nchunk = (int)((n + KR_CHUNK - 1) / KR_CHUNK);
+  k_xupdate<T><<<dim3(nchunk, nslots), KR_THREADS, 0, s>>>(n, mp1, nsteps, ycoef, V, vss, X, xss);
+  return cudaGetLastError();
+}
+
+#define KR_INST(T)                                                                                     \
+  template cudaError_t launch_dots<T>(const KryArgs&, const cx<T>*, long long, const cx<T>*, long long, int, \
+                                      int, cudaStream_t);                                                 \
+  template cudaError_t launch_update<T>(const KryArgs&, cx<T>*, long long, const cx<T>*, long long, int, int, \
+                                        cudaStream_t);                                                    \
+  template cudaError_t launch_xupdate<T>(long long, int, const int*, const double*, const cx<T>*, long long, \
+                                         cx<double>*, long long, int, cudaStream_t);
+KR_INST(float)
+KR_INST(double)
 
 cudaError_t launch_finalize_h(const KryArgs& a, double* H, int j, int nslots, cudaStream_t s) {
   if (nslots <= 0) return cudaSuccess;

@@ -1,0 +1,74 @@
+// The three pass kernels for one precision (DBAR_T) and one grid size
+// (N = 2^DBAR_LOGN).  The build compiles this file once per (precision, size)
+// so that every FFT is fully unrolled at compile time and the translation
+// units build in parallel.
+#include "launch.cuh"
+#include "passes.cuh"
+
+#ifndef DBAR_T
+#error "DBAR_T (float or double) must be defined"
+#endif
+#ifndef DBAR_LOGN
+#error "DBAR_LOGN must be defined"
+#endif
+
+namespace dbar {
+
+template <typename K>
+static cudaError_t set_smem(K kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename T, int LOGN>
+cudaError_t launch_pass_a_n(const PassArgs<T>& a, int nslots, cudaStream_t s) {
+  using G = RowG<T, LOGN>;
+  const int MA = a.M > 1 ? a.M : 1;
+  constexpr int NSEG = G::TPL >= 32 ? G::TPL / 32 : 1;
+  const size_t sm = align16((size_t)G::LINES * G::P * sizeof(cx<T>)) +
+                    (size_t)G::LINES * NSEG * (MA + 1) * sizeof(cx<double>) +
+                    (size_t)G::LINES * (a.M + 2) * sizeof(cx<double>);
+  cudaError_t e = set_smem(k_pass_a<T, LOGN>, sm);
+  if (e != cudaSuccess) return e;
+  k_pass_a<T, LOGN><<<dim3(G::N / G::LINES, nslots), G::THREADS, sm, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T, int LOGN, int MODE>
+cudaError_t launch_pass_b_n(const PassArgs<T>& a, int nslots, cudaStream_t s) {
+  using G = ColG<T, LOGN>;
+  const size_t sm = align16((size_t)G::COLS * G::P * sizeof(cx<T>)) + (size_t)(a.M + 2) * sizeof(cx<T>);
+  cudaError_t e = set_smem(k_pass_b<T, LOGN, MODE>, sm);
+  if (e != cudaSuccess) return e;
+  k_pass_b<T, LOGN, MODE><<<dim3(G::N / G::COLS, nslots), G::THREADS, sm, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T, typename TO, int LOGN, int MODE>
+cudaError_t launch_pass_c_n(const PassArgs<T>& a, int nslots, cudaStream_t s) {
+  using G = RowG<T, LOGN>;
+  const size_t sm = (size_t)G::LINES * G::P * sizeof(cx<T>);
+  cudaError_t e = set_smem(k_pass_c<T, TO, LOGN, MODE>, sm);
+  if (e != cudaSuccess) return e;
+  k_pass_c<T, TO, LOGN, MODE><<<dim3(G::N / G::LINES, nslots), G::THREADS, sm, s>>>(a);
+  return cudaGetLastError();
+}
+
+typedef DBAR_T TT;
+template cudaError_t launch_pass_a_n<TT, DBAR_LOGN>(const PassArgs<TT>&, int, cudaStream_t);
+template cudaError_t launch_pass_b_n<TT, DBAR_LOGN, PB_MATVEC>(const PassArgs<TT>&, int, cudaStream_t);
+template cudaError_t launch_pass_b_n<TT, DBAR_LOGN, PB_RHS>(const PassArgs<TT>&, int, cudaStream_t);
+template cudaError_t launch_pass_b_n<TT, DBAR_LOGN, PB_HOUT>(const PassArgs<TT>&, int, cudaStream_t);
+template cudaError_t launch_pass_b_n<TT, DBAR_LOGN, PB_FWD>(const PassArgs<TT>&, int, cudaStream_t);
+template cudaError_t launch_pass_b_n<TT, DBAR_LOGN, PB_INV>(const PassArgs<TT>&, int, cudaStream_t);
+template cudaError_t launch_pass_c_n<TT, TT, DBAR_LOGN, PC_KS>(const PassArgs<TT>&, int, cudaStream_t);
+template cudaError_t launch_pass_c_n<TT, TT, DBAR_LOGN, PC_FWD>(const PassArgs<TT>&, int, cudaStream_t);
+template cudaError_t launch_pass_c_n<TT, TT, DBAR_LOGN, PC_INV>(const PassArgs<TT>&, int, cudaStream_t);
+#if DBAR_T_IS_DOUBLE
+template cudaError_t launch_pass_c_n<double, double, DBAR_LOGN, PC_RHS>(const PassArgs<double>&, int, cudaStream_t);
+template cudaError_t launch_pass_c_n<double, float, DBAR_LOGN, PC_RHS>(const PassArgs<double>&, int, cudaStream_t);
+template cudaError_t launch_pass_c_n<double, double, DBAR_LOGN, PC_RES>(const PassArgs<double>&, int, cudaStream_t);
+template cudaError_t launch_pass_c_n<double, float, DBAR_LOGN, PC_RES>(const PassArgs<double>&, int, cudaStream_t);
+#endif
+
+}  // namespace dbar

@@ -200,7 +200,8 @@ static __global__ void k_solve_y(CycleState c, int nslots) {
   c.nsteps[slot] = ns;
 }
 
-// x += sum_i ycoef_i v~_i   (x in FP64, basis in T)
+// x += sum_i ycoef_i v~_i   (x in FP64, basis in T).  The correction is
+// accumulated in T (it carries the precision of the basis) and added to x once.
 template <typename T>
 __global__ void __launch_bounds__(KR_THREADS) k_xupdate(long long n, int mp1, const int* __restrict__ nsteps,
                                                          const double* __restrict__ ycoef,
@@ -211,17 +212,17 @@ __global__ void __launch_bounds__(KR_THREADS) k_xupdate(long long n, int mp1, co
   if (ns == 0) return;
   const long long base = (long long)blockIdx.x * KR_CHUNK + threadIdx.x;
   const cx<T>* Vs = V + (size_t)slot * vss;
-  cx<double> acc[KR_EPT];
+  cx<T> acc[KR_EPT];
 #pragma unroll
-  for (int e = 0; e < KR_EPT; ++e) acc[e] = mkc(0.0, 0.0);
+  for (int e = 0; e < KR_EPT; ++e) acc[e] = mkc((T)0, (T)0);
   for (int i = 0; i < ns; ++i) {
-    const double cf = ycoef[(size_t)slot * mp1 + i];
+    const T cf = (T)ycoef[(size_t)slot * mp1 + i];
 #pragma unroll
     for (int e = 0; e < KR_EPT; ++e) {
       const long long idx = base + (long long)e * KR_THREADS;
       if (idx < n) {
         const cx<T> vi = ldg(Vs + (size_t)i * n + idx);
-        acc[e] = mkc(acc[e].re + cf * (double)vi.re, acc[e].im + cf * (double)vi.im);
+        acc[e] = mkc(acc[e].re + cf * vi.re, acc[e].im + cf * vi.im);
       }
     }
   }
@@ -230,7 +231,7 @@ __global__ void __launch_bounds__(KR_THREADS) k_xupdate(long long n, int mp1, co
     const long long idx = base + (long long)e * KR_THREADS;
     if (idx < n) {
       cx<double>* xp = X + (size_t)slot * xss + idx;
-      *xp = *xp + acc[e];
+      *xp = *xp + ccast<double>(acc[e]);
     }
   }
 }

@@ -6,46 +6,35 @@
 
 namespace dbar {
 
-template <typename T>
-struct Lines {
-  // lines (rows or columns) per block: lines * N/16 threads, lines * N elements of shared memory
-  static int get(int N) {
-    const int cap = sizeof(T) == 4 ? 8192 : 4096;
-    const int l = cap / N;
-    return l < N ? l : N;
-  }
-};
+inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
+inline int ilog2(int N) {
+  int l = 0;
+  while ((1 << l) < N) ++l;
+  return l;
+}
 template <typename T>
 inline Geo make_geo(int N) {
   Geo g;
   g.N = N;
-  g.logN = 0;
-  while ((1 << g.logN) < N) ++g.logN;
+  g.logN = ilog2(N);
   g.tpl = N / 16;
-  g.lines = Lines<T>::get(N);
-  g.P = line_pitch(N);
+  g.lines = row_lines(g.logN);
+  g.P = pitch_of(N);
   return g;
 }
+// blocks per slot of the row passes (A and C): the number of pass-A partial sums
+inline int row_blocks(int N) { return N / row_lines(ilog2(N)); }
 
-inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+// per-size launchers (kern_pass.cu, one translation unit per precision and size)
+template <typename T, int LOGN>
+cudaError_t launch_pass_a_n(const PassArgs<T>& a, int nslots, cudaStream_t s);
+template <typename T, int LOGN, int MODE>
+cudaError_t launch_pass_b_n(const PassArgs<T>& a, int nslots, cudaStream_t s);
+template <typename T, typename TO, int LOGN, int MODE>
+cudaError_t launch_pass_c_n(const PassArgs<T>& a, int nslots, cudaStream_t s);
 
-template <typename T>
-inline size_t smem_pass_a(const Geo& g, int M) {
-  const int MA = M > 1 ? M : 1;
-  const int nseg = g.tpl >= 32 ? g.tpl / 32 : 1;
-  return align16((size_t)g.lines * g.P * sizeof(cx<T>)) + (size_t)g.lines * nseg * (MA + 1) * sizeof(cx<double>) +
-         (size_t)g.lines * (M + 2) * sizeof(cx<double>);
-}
-template <typename T>
-inline size_t smem_pass_b(const Geo& g, int M) {
-  return align16((size_t)g.lines * g.P * sizeof(cx<T>)) + (size_t)(M + 2) * sizeof(cx<T>);
-}
-template <typename T>
-inline size_t smem_pass_c(const Geo& g) {
-  return (size_t)g.lines * g.P * sizeof(cx<T>);
-}
-
+// size dispatch (dispatch.cu)
 template <typename T>
 cudaError_t launch_pass_a(const PassArgs<T>& a, int nslots, cudaStream_t s);
 template <typename T, int MODE>

@@ -33,7 +33,6 @@ namespace dbar {
 
 __device__ __forceinline__ int wavenum(int p, int N) { return p <= (N >> 1) ? p : p - N; }
 
-
 // From the summed row contributions to the coefficients:
 //   n <= M:  c_n = (1/n!) (-i/2)^n N^-2 sum      (eq. fourreeg4, Sec. 4.3 step 4a)
 //   n = M+1: d   = (-i/2) N^-2 sum * fillmul     (fill value dS/dxi(0), scaled)
@@ -48,44 +47,60 @@ __device__ __forceinline__ cx<double> taylor_coef(cx<double> s, int n, int M, in
   return s;
 }
 
+template <typename T, int LOGN>
+struct RowG {
+  static constexpr int N = 1 << LOGN, TPL = N / 16, LINES = row_lines(LOGN), THREADS = LINES * TPL;
+  static constexpr int P = pitch_of(N);
+  static constexpr int MINB = sizeof(T) == 4 ? 4 : 2;
+};
+template <typename T, int LOGN>
+struct ColG {
+  static constexpr int N = 1 << LOGN, TPL = N / 16;
+  static constexpr int CW = col_cw(LOGN, (int)sizeof(cx<T>)), TW = 32 / CW;
+  static constexpr int COLS = col_cols(LOGN, (int)sizeof(cx<T>)), THREADS = COLS * TPL;
+  static constexpr int WPG = TPL / TW;  // warps per group of CW columns
+  static constexpr int P = pitch_of(N);
+  static constexpr int MINB = 2;
+};
+
 // ---------------------------------------------------------------------------
 // Pass A: rows of a Fourier field.
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(KMax<T>::threads) k_pass_a(const PassArgs<T> a) {
+template <typename T, int LOGN>
+__global__ void __launch_bounds__(RowG<T, LOGN>::THREADS, RowG<T, LOGN>::MINB) k_pass_a(const PassArgs<T> a) {
+  using G = RowG<T, LOGN>;
+  constexpr int N = G::N, TPL = G::TPL, LINES = G::LINES, P = G::P;
+  constexpr int SEGW = TPL >= 32 ? 32 : TPL, NSEG = TPL >= 32 ? TPL / 32 : 1;
   extern __shared__ __align__(16) unsigned char smem[];
   const int slot = blockIdx.y;
   if (a.run && !a.run[slot]) return;
-  const int N = a.g.N, TPL = a.g.tpl, P = a.g.P, lines = a.g.lines, M = a.M;
-  const int MA = M > 1 ? M : 1;
+  const int M = a.M, MA = M > 1 ? M : 1;
   const int line = threadIdx.x / TPL, t = threadIdx.x - line * TPL;
-  const int p2 = blockIdx.x * lines + line;
+  const int p2 = blockIdx.x * LINES + line;
   cx<T>* sl = reinterpret_cast<cx<T>*>(smem) + line * P;
   const T sc = a.in_scale ? (T)a.in_scale[(size_t)slot * a.in_scale_ss] : (T)1;
-  const cx<T>* src = a.in + (size_t)slot * a.in_ss + (size_t)p2 * N;
+  const cx<T>* src = a.in + (size_t)slot * a.in_ss + (size_t)p2 * N + t;
   cx<T> v[16];
 #pragma unroll
-  for (int q = 0; q < 16; ++q) v[q] = cscale(ldg(src + t + q * TPL), sc);
+  for (int q = 0; q < 16; ++q) v[q] = cscale(ldg(src + q * TPL), sc);
 
   // Row moments R_a(p2) = sum_p1 (-1)^p1 S D_a(p1), a = 0..MA.
-  const int segw = TPL >= 32 ? 32 : TPL;
-  const int nseg = TPL >= 32 ? TPL / 32 : 1;
-  const int seg = TPL >= 32 ? t / 32 : 0;
-  size_t off = ((size_t)lines * P * sizeof(cx<T>) + 15) & ~(size_t)15;
+  constexpr size_t off = ((size_t)LINES * P * sizeof(cx<T>) + 15) & ~(size_t)15;
   cx<double>* red = reinterpret_cast<cx<double>*>(smem + off);
-  cx<double>* lc = red + lines * nseg * (MA + 1);
+  cx<double>* lc = red + LINES * NSEG * (MA + 1);
+  const int seg = TPL >= 32 ? t / 32 : 0;
   for (int aa = 0; aa <= MA; ++aa) {
     cx<T> acc = mkc((T)0, (T)0);
-    const cx<T>* D = a.Da + (size_t)aa * N;
+    const cx<T>* D = a.Da + (size_t)aa * N + t;
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
-      const int p1 = t + q * TPL;
+      const cx<T> d = ldg(D + q * TPL);
       cx<T> s = v[q];
-      if (p1 & 1) s = mkc(-s.re, -s.im);
-      acc = acc + cmul(s, ldg(D + p1));
+      if ((t + q * TPL) & 1) s = mkc(-s.re, -s.im);
+      acc = acc + cmul(s, d);
     }
-    double re = warp_sum((double)acc.re, segw), im = warp_sum((double)acc.im, segw);
-    if ((t & (segw - 1)) == 0) red[(line * nseg + seg) * (MA + 1) + aa] = mkc(re, im);
+    const double re = warp_sum((double)acc.re, SEGW), im = warp_sum((double)acc.im, SEGW);
+    if ((t & (SEGW - 1)) == 0) red[(line * NSEG + seg) * (MA + 1) + aa] = mkc(re, im);
   }
 
   // S~ (-1)^{p1+p2} / (2 pi L^2) with S~ = S/xi, xi = (m1 + i m2)/L, 0 at xi = 0.
@@ -95,37 +110,32 @@ __global__ void __launch_bounds__(KMax<T>::threads) k_pass_a(const PassArgs<T> a
     const int p1 = t + q * TPL;
     const int m1 = wavenum(p1, N);
     const int den = m1 * m1 + m2 * m2;
-    if (den == 0) {
-      v[q] = mkc((T)0, (T)0);
-    } else {
-      T f = (T)a.inv2piL / (T)den;
-      if ((p1 + p2) & 1) f = -f;
-      v[q] = cmul(v[q], mkc((T)m1 * f, (T)(-m2) * f));
-    }
+    T f = den ? (T)a.inv2piL / (T)den : (T)0;
+    if ((p1 + p2) & 1) f = -f;
+    v[q] = cmul(v[q], mkc((T)m1 * f, (T)(-m2) * f));
   }
-  fft_line<T, true>(v, sl, N, a.g.logN, t, TPL, a.tw);
-  cx<T>* dst = reinterpret_cast<cx<T>*>(a.out) + (size_t)slot * a.out_ss + (size_t)p2 * N;
+  fft_line<T, LOGN, true>(v, sl, t, a.tw);
+  cx<T>* dst = reinterpret_cast<cx<T>*>(a.out) + (size_t)slot * a.out_ss + (size_t)p2 * N + t;
 #pragma unroll
-  for (int q = 0; q < 16; ++q) dst[t + q * TPL] = v[q];
+  for (int q = 0; q < 16; ++q) dst[q * TPL] = v[q];
 
-  // Per-line combination with D_b(p2) (FP64), then the block partial sums.
+  // Per (line, n): combination with D_b(p2) in FP64; then the block partial sums.
   __syncthreads();
-  if ((int)threadIdx.x < lines) {
-    const int ln = threadIdx.x;
-    const int pp2 = blockIdx.x * lines + ln;
-    const double sg = (pp2 & 1) ? -1.0 : 1.0;
-    cx<double> R[17];
-    for (int aa = 0; aa <= MA; ++aa) {
-      cx<double> s = mkc(0.0, 0.0);
-      for (int sgi = 0; sgi < nseg; ++sgi) s = s + red[(ln * nseg + sgi) * (MA + 1) + aa];
-      R[aa] = s;
-    }
-    for (int n = 0; n <= M; ++n) {
-      cx<double> s = mkc(0.0, 0.0);
+  for (int i = threadIdx.x; i < LINES * (M + 2); i += G::THREADS) {
+    const int ln = i / (M + 2), n = i - ln * (M + 2);
+    const int pp2 = blockIdx.x * LINES + ln;
+    const cx<double>* R = red + ln * NSEG * (MA + 1);
+    auto Ra = [&](int aa) {
+      cx<double> s = R[aa];
+      for (int sg = 1; sg < NSEG; ++sg) s = s + R[sg * (MA + 1) + aa];
+      return s;
+    };
+    cx<double> s = mkc(0.0, 0.0);
+    if (n <= M) {
+      // sum_a C(n,a) i^{n-a} D_{n-a}(p2) R_a
       double binom = 1.0;
       for (int aa = 0; aa <= n; ++aa) {
-        // term C(n,a) i^{n-a} D_{n-a}(p2) R_a
-        cx<double> tmp = cmul(a.Da64[(size_t)(n - aa) * N + pp2], R[aa]);
+        cx<double> tmp = cmul(a.Da64[(size_t)(n - aa) * N + pp2], Ra(aa));
         const int e = (n - aa) & 3;
         if (e == 1) tmp = cmuli(tmp);
         else if (e == 2) tmp = mkc(-tmp.re, -tmp.im);
@@ -133,43 +143,46 @@ __global__ void __launch_bounds__(KMax<T>::threads) k_pass_a(const PassArgs<T> a
         s = s + cscale(tmp, binom);
         binom = binom * (double)(n - aa) / (double)(aa + 1);
       }
-      lc[ln * (M + 2) + n] = cscale(s, sg);
+    } else {
+      // fill value: R_1 D_0(p2) - i R_0 D_1(p2)
+      const cx<double> t1 = cmul(Ra(1), a.Da64[pp2]);
+      const cx<double> t2 = cmul(Ra(0), a.Da64[(size_t)N + pp2]);
+      s = mkc(t1.re + t2.im, t1.im - t2.re);
     }
-    // fill value: R_1 D_0(p2) - i R_0 D_1(p2)
-    cx<double> dv = cmul(R[1], a.Da64[pp2]);
-    cx<double> t2 = cmul(R[0], a.Da64[(size_t)N + pp2]);
-    dv = mkc(dv.re + t2.im, dv.im - t2.re);
-    lc[ln * (M + 2) + M + 1] = cscale(dv, sg);
+    lc[ln * (M + 2) + n] = (pp2 & 1) ? mkc(-s.re, -s.im) : s;
   }
   __syncthreads();
-  for (int n = threadIdx.x; n < M + 2; n += blockDim.x) {
+  for (int n = threadIdx.x; n < M + 2; n += G::THREADS) {
     cx<double> s = mkc(0.0, 0.0);
-    for (int ln = 0; ln < lines; ++ln) s = s + lc[ln * (M + 2) + n];
+    for (int ln = 0; ln < LINES; ++ln) s = s + lc[ln * (M + 2) + n];
     a.partA[((size_t)slot * gridDim.x + blockIdx.x) * (M + 2) + n] = s;
   }
 }
 
 // ---------------------------------------------------------------------------
-// Pass B: columns.  MODE 0 operator, 1 right-hand side, 2 h only (m output),
-// 3 raw forward column DFT, 4 raw inverse column DFT.
+// Pass B: columns.  MODE PB_MATVEC operator, PB_RHS right-hand side, PB_HOUT h
+// only (m output), PB_FWD / PB_INV raw column DFTs.  A warp covers CW
+// neighbouring columns x TW consecutive t, so the 16 loads and stores of each
+// thread (rows t + q TPL of column j1) are coalesced row segments.
 // ---------------------------------------------------------------------------
-
-template <typename T, int MODE>
-__global__ void __launch_bounds__(KMax<T>::threads) k_pass_b(const PassArgs<T> a) {
+template <typename T, int LOGN, int MODE>
+__global__ void __launch_bounds__(ColG<T, LOGN>::THREADS, ColG<T, LOGN>::MINB) k_pass_b(const PassArgs<T> a) {
+  using G = ColG<T, LOGN>;
+  constexpr int N = G::N, TPL = G::TPL, P = G::P;
   extern __shared__ __align__(16) unsigned char smem[];
   const int slot = blockIdx.y;
   if (a.run && !a.run[slot]) return;
-  const int N = a.g.N, TPL = a.g.tpl, P = a.g.P, cols = a.g.lines, M = a.M;
-  const int line = threadIdx.x / TPL, t = threadIdx.x - line * TPL;
-  const int c0 = blockIdx.x * cols;
-  const int j1 = c0 + line;
-  cx<T>* tile = reinterpret_cast<cx<T>*>(smem);
-  size_t off = ((size_t)cols * P * sizeof(cx<T>) + 15) & ~(size_t)15;
+  const int M = a.M;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = (warp / G::WPG) * G::CW + lane % G::CW;
+  const int t = (warp % G::WPG) * G::TW + lane / G::CW;
+  const int j1 = blockIdx.x * G::COLS + c;
+  cx<T>* sl = reinterpret_cast<cx<T>*>(smem) + c * P;
+  constexpr size_t off = ((size_t)G::COLS * P * sizeof(cx<T>) + 15) & ~(size_t)15;
   cx<T>* coef = reinterpret_cast<cx<T>*>(smem + off);  // [M+1] c_n, then the fill d'
 
   if (MODE == PB_MATVEC || MODE == PB_HOUT) {
     if (threadIdx.x < 32) {
-      const int lane = threadIdx.x;
       const cx<double>* pa = a.partA + (size_t)slot * a.nblkA * (M + 2);
       for (int n = 0; n < M + 2; ++n) {
         double re = 0.0, im = 0.0;
@@ -184,83 +197,71 @@ __global__ void __launch_bounds__(KMax<T>::threads) k_pass_b(const PassArgs<T> a
       }
     }
   }
-  if (MODE != PB_RHS) {
-    const cx<T>* src = a.in + (size_t)slot * a.in_ss;
-    for (int i = threadIdx.x; i < N * cols; i += blockDim.x) {
-      const int row = i / cols, c = i - row * cols;
-      tile[c * P + padi(row)] = ldg(src + (size_t)row * N + c0 + c);
-    }
-  }
-  __syncthreads();
-  cx<T>* sl = tile + line * P;
   cx<T> v[16];
   if (MODE != PB_RHS) {
+    const cx<T>* src = a.in + (size_t)slot * a.in_ss + (size_t)t * N + j1;
 #pragma unroll
-    for (int q = 0; q < 16; ++q) v[q] = sl[padi(t + q * TPL)];
-    if (MODE == PB_FWD) fft_line<T, false>(v, sl, N, a.g.logN, t, TPL, a.tw);
-    else fft_line<T, true>(v, sl, N, a.g.logN, t, TPL, a.tw);
+    for (int q = 0; q < 16; ++q) v[q] = ldg(src + (size_t)q * TPL * N);
+    if (MODE == PB_FWD) fft_line<T, LOGN, false>(v, sl, t, a.tw);
+    else fft_line<T, LOGN, true>(v, sl, t, a.tw);
   }
-  if (MODE == PB_MATVEC || MODE == PB_RHS || MODE == PB_HOUT) {
-    const cx<T> exv = ldg(a.ex + (size_t)slot * N + j1);
-    const cx<T> fill = (MODE == PB_RHS) ? mkc((T)0, (T)0) : coef[M + 1];
-    const T sw = (T)a.sw;
+  if (MODE == PB_MATVEC || MODE == PB_HOUT) {
+    __syncthreads();  // coefficients visible
+    // h = u + sum_n c_n Delta_n + d'  (n outer, 16 independent loads per n)
+    const cx<T> fill = coef[M + 1];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = v[q] + fill;
+    for (int n = 0; n <= M; ++n) {
+      const cx<T> cn = coef[n];
+      const cx<T>* D = a.DeltaT + ((size_t)n * N + j1) * N + t;
+#pragma unroll
+      for (int q = 0; q < 16; ++q) v[q] = v[q] + cmul(cn, ldg(D + q * TPL));
+    }
+  }
+  if (MODE == PB_MATVEC || MODE == PB_RHS) {
+    // w = (2 pi L^2/N^2) E_k Q conj(h)   (right-hand side: E_k Q)
+    const cx<T> exv = cscale(ldg(a.ex + (size_t)slot * N + j1), (T)a.sw);
+    const cx<T>* EY = a.ey + (size_t)slot * N + t;
+    const cx<T>* QC = a.QT + (size_t)j1 * N + t;
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
-      const int j2 = t + q * TPL;
-      cx<T> h = mkc((T)0, (T)0);
-      if (MODE != PB_RHS) {
-        h = v[q] + fill;
-        for (int n = 0; n <= M; ++n)
-          h = h + cmul(coef[n], ldg(a.DeltaT + ((size_t)n * N + j1) * N + j2));
-      }
-      if (MODE == PB_HOUT) {
-        v[q] = h;
-      } else {
-        const cx<T> eq = cscale(cmul(cmul(exv, ldg(a.ey + (size_t)slot * N + j2)),
-                                     ldg(a.QT + (size_t)j1 * N + j2)), sw);
-        v[q] = (MODE == PB_RHS) ? eq : cmulc(eq, h);
-      }
+      const cx<T> eq = cmul(cmul(exv, ldg(EY + q * TPL)), ldg(QC + q * TPL));
+      v[q] = (MODE == PB_RHS) ? eq : cmulc(eq, v[q]);
     }
-    if (MODE != PB_HOUT) fft_line<T, false>(v, sl, N, a.g.logN, t, TPL, a.tw);
+    fft_line<T, LOGN, false>(v, sl, t, a.tw);
   }
-  __syncthreads();
+  cx<T>* dst = reinterpret_cast<cx<T>*>(a.out) + (size_t)slot * a.out_ss + (size_t)t * N + j1;
 #pragma unroll
-  for (int q = 0; q < 16; ++q) sl[padi(t + q * TPL)] = v[q];
-  __syncthreads();
-  cx<T>* dst = reinterpret_cast<cx<T>*>(a.out) + (size_t)slot * a.out_ss;
-  for (int i = threadIdx.x; i < N * cols; i += blockDim.x) {
-    const int row = i / cols, c = i - row * cols;
-    dst[(size_t)row * N + c0 + c] = tile[c * P + padi(row)];
-  }
+  for (int q = 0; q < 16; ++q) dst[(size_t)q * TPL * N] = v[q];
 }
 
 // ---------------------------------------------------------------------------
-// Pass C: rows.  MODE 0: K S = i (-1)^p DFT(w) -> out (T).
-// MODE 1: b = -i (-1)^p DFT(w) -> out (FP64) and out2 (TO), |b|^2 partials.
-// MODE 2: r = b - x - i (-1)^p DFT(w) -> out2 (TO), |r|^2 partials (T = FP64).
-// MODE 3 / 4: raw forward / inverse row DFT -> out (T).
+// Pass C: rows.  PC_KS: K S = i (-1)^p DFT(w) -> out (T).
+// PC_RHS: b = -i (-1)^p DFT(w) -> out (FP64) and out2 (TO), |b|^2 partials.
+// PC_RES: r = b - x - i (-1)^p DFT(w) -> out2 (TO), |r|^2 partials (T = FP64).
+// PC_FWD / PC_INV: raw row DFTs -> out (T).
 // ---------------------------------------------------------------------------
-
-template <typename T, typename TO, int MODE>
-__global__ void __launch_bounds__(KMax<T>::threads) k_pass_c(const PassArgs<T> a) {
+template <typename T, typename TO, int LOGN, int MODE>
+__global__ void __launch_bounds__(RowG<T, LOGN>::THREADS, RowG<T, LOGN>::MINB) k_pass_c(const PassArgs<T> a) {
+  using G = RowG<T, LOGN>;
+  constexpr int N = G::N, TPL = G::TPL, LINES = G::LINES, P = G::P;
   extern __shared__ __align__(16) unsigned char smem[];
   const int slot = blockIdx.y;
   if (a.run && !a.run[slot]) return;
-  const int N = a.g.N, TPL = a.g.tpl, P = a.g.P, lines = a.g.lines;
   const int line = threadIdx.x / TPL, t = threadIdx.x - line * TPL;
-  const int p2 = blockIdx.x * lines + line;
+  const int p2 = blockIdx.x * LINES + line;
   cx<T>* sl = reinterpret_cast<cx<T>*>(smem) + line * P;
-  const cx<T>* src = a.in + (size_t)slot * a.in_ss + (size_t)p2 * N;
+  const cx<T>* src = a.in + (size_t)slot * a.in_ss + (size_t)p2 * N + t;
   cx<T> v[16];
 #pragma unroll
-  for (int q = 0; q < 16; ++q) v[q] = ldg(src + t + q * TPL);
-  fft_line<T, MODE == PC_INV>(v, sl, N, a.g.logN, t, TPL, a.tw);
+  for (int q = 0; q < 16; ++q) v[q] = ldg(src + q * TPL);
+  fft_line<T, LOGN, MODE == PC_INV>(v, sl, t, a.tw);
   double nrm = 0.0;
-  const size_t rowoff = (size_t)p2 * N;
+  const size_t rowoff = (size_t)p2 * N + t;
 #pragma unroll
   for (int q = 0; q < 16; ++q) {
     const int p1 = t + q * TPL;
-    const size_t idx = rowoff + p1;
+    const size_t idx = rowoff + q * TPL;
     cx<T> y = v[q];
     if (MODE == PC_KS || MODE == PC_RHS || MODE == PC_RES) {
       if ((p1 + p2) & 1) y = mkc(-y.re, -y.im);
@@ -288,7 +289,7 @@ __global__ void __launch_bounds__(KMax<T>::threads) k_pass_c(const PassArgs<T> a
     __syncthreads();
     if (threadIdx.x == 0) {
       double s = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += wred[w];
+      for (int w = 0; w < G::THREADS / 32; ++w) s += wred[w];
       a.part[(size_t)slot * gridDim.x + blockIdx.x] = s;
     }
   }

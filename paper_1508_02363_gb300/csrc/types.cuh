@@ -43,14 +43,6 @@ struct PassArgs {
   double* part;          // [slot][gridDim.x] squared-norm partials (pass C)
 };
 
-template <typename T>
-struct KMax {
-  static constexpr int threads = 512;
-};
-template <>
-struct KMax<double> {
-  static constexpr int threads = 256;
-};
 
 constexpr int KR_THREADS = 256;
 constexpr int KR_EPT = 8;  // complex elements per thread
