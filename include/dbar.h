@@ -42,7 +42,7 @@ extern "C" {
 
 typedef enum {
   DBAR_OK = 0,
-  DBAR_EINVAL = 1,   /* bad argument: N not a power of two in [16, 2048], L <= 0,
+  DBAR_EINVAL = 1,   /* bad argument: N not a power of two in [32, 2048], L <= 0,
                         NaN/Inf in Q or k, null pointer where one is required  */
   DBAR_ENOMEM = 2,   /* a device allocation failed                              */
   DBAR_ENOCONV = 3,  /* some k missed tol within max_iter / max_outer; outputs
@@ -58,8 +58,14 @@ typedef enum {
                         (iterative refinement)                                  */
 } dbar_prec;
 
+typedef enum {
+  DBAR_RESID_DOUBLE_FLOAT = 0, /* float pairs (hi + lo, ~48-bit significand) on the
+                                  FP32 pipes; default                          */
+  DBAR_RESID_FP64 = 1          /* native FP64                                   */
+} dbar_resid_mode;
+
 typedef struct {
-  int N;             /* grid points per axis: power of two, 16 <= N <= 2048    */
+  int N;             /* grid points per axis: power of two, 32 <= N <= 2048    */
   double L;          /* box [-pi L, pi L]^2 (Sec. 4.1, eq. domain), L > 0        */
   int M;             /* Taylor order of G (Sec. 4.2, eq. Gchoice), 0 <= M <= 16 */
   int prec;          /* dbar_prec                                               */
@@ -71,12 +77,15 @@ typedef struct {
   int max_batch;     /* k values solved concurrently; 0 = chosen from memory    */
   double inner_tol;  /* DBAR_MIXED: relative residual reduction per FP32 cycle  */
   int max_outer;     /* cap on cycles (restarts / refinement steps)             */
+  int resid_mode;    /* DBAR_MIXED: arithmetic of the right-hand side and of the
+                        true residual b - A x (dbar_resid_mode)                 */
 } dbar_params;
 
 typedef struct dbar_plan* dbar_plan_t;
 
 /* Defaults for a grid: M = 2, DBAR_MIXED, restart 32, tol 1e-12,
- * inner_tol 1e-6, max_outer 40, max_iter 4000, analytic fill. */
+ * inner_tol 1e-6, max_outer 40, max_iter 4000, analytic fill,
+ * DBAR_RESID_DOUBLE_FLOAT. */
 void dbar_params_init(dbar_params* p, int N, double L);
 
 /* Message describing the calling thread's most recent failure ("" if none). */

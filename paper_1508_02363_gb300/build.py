@@ -20,11 +20,12 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libdbar_gb300.so")
 SIZES = range(5, 12)  # N = 32 .. 2048
 # (source, object name, extra flags): the pass kernels once per precision and size
-UNITS = ([("kern_pass.cu", f"pass_{t}_{l}", [f"-DDBAR_T={t}", f"-DDBAR_LOGN={l}",
-                                              f"-DDBAR_T_IS_DOUBLE={int(t == 'double')}"])
-          for t in ("double", "float") for l in SIZES] +
+UNITS = ([("kern_pass.cu", f"pass_{t}_{l}", [f"-DDBAR_T={t}", f"-DDBAR_LOGN={l}", f"-DDBAR_KIND={kind}"])
+          for t, kind in (("double", 1), ("dd", 2), ("float", 0)) for l in SIZES] +
          [("kern_krylov.cu", "krylov", []), ("dispatch.cu", "dispatch", []), ("plan.cu", "plan", [])])
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# extra nvcc flags (e.g. block-shape macros of csrc/cx.cuh) for tuning builds
+EXTRA = os.environ.get("DBAR_NVCC_FLAGS", "").split()
 
 
 def nvcc() -> str:
@@ -37,7 +38,7 @@ def nvcc() -> str:
 def _compile(unit, verbose: bool) -> str:
     src, name, flags = unit
     obj = os.path.join(BUILD, name + ".o")
-    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", *flags,
+    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", *flags, *EXTRA,
            "-I", os.path.join(ROOT, "include"), "-c", os.path.join(CSRC, src), "-o", obj]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")

@@ -69,6 +69,78 @@ __device__ __forceinline__ double warp_sum(double v, int width) {
 }
 
 // ---------------------------------------------------------------------------
+// Double-float numbers: an unevaluated sum hi + lo of two floats (about 48
+// significant bits).  Sums and products use the error-free transformations
+// of Dekker (1971) and Knuth (TwoSum), as in the double-double arithmetic of
+// Hida, Li and Bailey; every float operation is an explicitly rounded
+// intrinsic so the compiler cannot fuse or reorder it.  On GB300 the FP32
+// pipes are ~64x the FP64 pipe, so FP64-class transforms run several times
+// faster in this form.
+// ---------------------------------------------------------------------------
+struct __align__(8) dd {
+  float hi, lo;
+  dd() = default;
+  __host__ __device__ constexpr dd(float h, float l) : hi(h), lo(l) {}
+  __host__ __device__ dd(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
+  __host__ __device__ constexpr dd(float f) : hi(f), lo(0.f) {}
+  // exact for |i| < 2^24 (grid indices and wavenumbers)
+  __host__ __device__ constexpr dd(int i) : hi((float)i), lo(0.f) {}
+  __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
+  __host__ __device__ explicit operator float() const { return hi + lo; }
+};
+
+__device__ __forceinline__ dd dd_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return dd(s, e);
+}
+__device__ __forceinline__ dd dd_quick_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return dd(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ dd operator+(dd a, dd b) {
+  const dd s = dd_two_sum(a.hi, b.hi);
+  return dd_quick_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ dd operator-(dd a) { return dd(-a.hi, -a.lo); }
+__device__ __forceinline__ dd operator-(dd a, dd b) { return a + (-b); }
+__device__ __forceinline__ dd operator*(dd a, dd b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return dd_quick_two_sum(p, e);
+}
+__device__ __forceinline__ dd operator/(dd a, dd b) {
+  const float q1 = __fdiv_rn(a.hi, b.hi);
+  const dd r = a - dd(q1) * b;
+  return dd_quick_two_sum(q1, __fdiv_rn(r.hi, b.hi));
+}
+__device__ __forceinline__ dd& operator+=(dd& a, dd b) {
+  a = a + b;
+  return a;
+}
+
+template <>
+__device__ __forceinline__ cx<dd> ldg(const cx<dd>* p) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  return mkc(dd(v.x, v.y), dd(v.z, v.w));
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T v, int width) {
+  for (int off = width >> 1; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+template <>
+__device__ __forceinline__ dd warp_sum_t<dd>(dd v, int width) {
+  for (int off = width >> 1; off > 0; off >>= 1)
+    v = v + dd(__shfl_xor_sync(0xffffffffu, v.hi, off), __shfl_xor_sync(0xffffffffu, v.lo, off));
+  return v;
+}
+
+// ---------------------------------------------------------------------------
 // Register DFT of size R in {2,4,8,16}: radix-2 decimation in time after a
 // bit-reversal permutation.  The butterfly twiddles exp(-+ i pi q/8) are the
 // exact values cos(pi q/8), sin(pi q/8) written out.
@@ -226,11 +298,25 @@ __device__ __forceinline__ void fft_line(cx<T> (&v)[16], cx<T>* line, int t, con
 __host__ __device__ constexpr int row_lines(int logN) {
   return (256 / ((1 << logN) / 16)) < (1 << logN) ? (256 / ((1 << logN) / 16)) : (1 << logN);
 }
-__host__ __device__ constexpr int col_cap(int logN, int esz) { return (esz == 8 ? 512 : 256) / ((1 << logN) / 16) > 0 ? (esz == 8 ? 512 : 256) / ((1 << logN) / 16) : 1; }
+// Column-pass shape knobs (bytes of one row segment a warp reads, threads per block).
+#ifndef DBAR_COL_SEG_BYTES
+#define DBAR_COL_SEG_BYTES 64
+#endif
+#ifndef DBAR_COL_THREADS_F32
+#define DBAR_COL_THREADS_F32 512
+#endif
+#ifndef DBAR_COL_THREADS_F64
+#define DBAR_COL_THREADS_F64 256
+#endif
+__host__ __device__ constexpr int col_threads(int esz) { return esz == 8 ? DBAR_COL_THREADS_F32 : DBAR_COL_THREADS_F64; }
+__host__ __device__ constexpr int col_cap(int logN, int esz) {
+  return col_threads(esz) / ((1 << logN) / 16) > 0 ? col_threads(esz) / ((1 << logN) / 16) : 1;
+}
+__host__ __device__ constexpr int col_cwd(int esz) { return DBAR_COL_SEG_BYTES / esz > 0 ? DBAR_COL_SEG_BYTES / esz : 1; }
 __host__ __device__ constexpr int col_cw(int logN, int esz) {
-  // 64-byte row segments when possible; small N: one warp spans all t of CW columns
-  return ((1 << logN) / 16 >= 32 / (esz == 8 ? 8 : 4))
-             ? ((esz == 8 ? 8 : 4) < col_cap(logN, esz) ? (esz == 8 ? 8 : 4) : col_cap(logN, esz))
+  // row segments of DBAR_COL_SEG_BYTES when possible; small N: one warp spans all t of CW columns
+  return ((1 << logN) / 16 >= 32 / col_cwd(esz))
+             ? (col_cwd(esz) < col_cap(logN, esz) ? col_cwd(esz) : col_cap(logN, esz))
              : 32 / ((1 << logN) / 16);
 }
 __host__ __device__ constexpr int col_cols(int logN, int esz) {

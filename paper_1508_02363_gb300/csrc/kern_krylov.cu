@@ -61,46 +61,36 @@ cudaError_t launch_cycle_start(const CycleState& c, const double* part, int nblk
   return cudaGetLastError();
 }
 
-// QT[x][y] = Q[y][x] in both precisions (32x32 tiles through shared memory).
-__global__ void k_transpose_q(const cx<double>* __restrict__ Q, cx<double>* __restrict__ QT64,
-                              cx<float>* __restrict__ QT32, int N) {
-  __shared__ cx<double> tile[32][33];
-  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
-  for (int r = threadIdx.y; r < 32; r += blockDim.y) tile[r][threadIdx.x] = Q[(size_t)(by + r) * N + bx + threadIdx.x];
-  __syncthreads();
-  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-    const cx<double> v = tile[threadIdx.x][r];
-    const size_t o = (size_t)(bx + r) * N + by + threadIdx.x;
-    QT64[o] = v;
-    QT32[o] = ccast<float>(v);
+// Q in both precisions (physical layout [y][x]).
+__global__ void k_load_q(const cx<double>* __restrict__ Q, cx<double>* __restrict__ Q64, cx<float>* __restrict__ Q32,
+                         long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const cx<double> v = Q[i];
+    Q64[i] = v;
+    Q32[i] = ccast<float>(v);
   }
 }
-cudaError_t launch_transpose_q(const cx<double>* Q, cx<double>* QT64, cx<float>* QT32, int N, cudaStream_t s) {
-  k_transpose_q<<<dim3(N / 32, N / 32), dim3(32, 8), 0, s>>>(Q, QT64, QT32, N);
+cudaError_t launch_load_q(const cx<double>* Q, cx<double>* Q64, cx<float>* Q32, int N, cudaStream_t s) {
+  const long long n = (long long)N * N;
+  const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+  k_load_q<<<blocks, 256, 0, s>>>(Q, Q64, Q32, n);
   return cudaGetLastError();
 }
 
-// DT[n][x][y] = W[n][y][x] - V[n][y][x]
+// Delta_n = W_n - V_n in both precisions ([n][y][x]).
 __global__ void k_delta_build(const cx<double>* __restrict__ V, const cx<double>* __restrict__ W,
-                              cx<double>* __restrict__ DT64, cx<float>* __restrict__ DT32, int N) {
-  __shared__ cx<double> tile[32][33];
-  const size_t f = (size_t)blockIdx.z * N * N;
-  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
-  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-    const size_t i = f + (size_t)(by + r) * N + bx + threadIdx.x;
-    tile[r][threadIdx.x] = W[i] - V[i];
-  }
-  __syncthreads();
-  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-    const cx<double> v = tile[threadIdx.x][r];
-    const size_t o = f + (size_t)(bx + r) * N + by + threadIdx.x;
-    DT64[o] = v;
-    DT32[o] = ccast<float>(v);
+                              cx<double>* __restrict__ D64, cx<float>* __restrict__ D32, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const cx<double> v = W[i] - V[i];
+    D64[i] = v;
+    D32[i] = ccast<float>(v);
   }
 }
-cudaError_t launch_delta_build(const cx<double>* V, const cx<double>* W, cx<double>* DT64, cx<float>* DT32, int N,
+cudaError_t launch_delta_build(const cx<double>* V, const cx<double>* W, cx<double>* D64, cx<float>* D32, int N,
                                int nfields, cudaStream_t s) {
-  k_delta_build<<<dim3(N / 32, N / 32, nfields), dim3(32, 8), 0, s>>>(V, W, DT64, DT32, N);
+  const long long n = (long long)N * N * nfields;
+  const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+  k_delta_build<<<blocks, 256, 0, s>>>(V, W, D64, D32, n);
   return cudaGetLastError();
 }
 
@@ -148,6 +138,16 @@ __global__ void k_cast_fields(const cx<double>* __restrict__ in, cx<float>* __re
 cudaError_t launch_cast_fields(const cx<double>* in, cx<float>* out, long long n, cudaStream_t s) {
   const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
   k_cast_fields<<<blocks, 256, 0, s>>>(in, out, n);
+  return cudaGetLastError();
+}
+
+__global__ void k_split_fields(const cx<double>* __restrict__ in, cx<dd>* __restrict__ out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = ccast<dd>(in[i]);
+}
+cudaError_t launch_split_fields(const cx<double>* in, cx<dd>* out, long long n, cudaStream_t s) {
+  const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+  k_split_fields<<<blocks, 256, 0, s>>>(in, out, n);
   return cudaGetLastError();
 }
 

@@ -6,7 +6,10 @@
 #include "passes.cuh"
 
 #ifndef DBAR_T
-#error "DBAR_T (float or double) must be defined"
+#error "DBAR_T (float, double or dd) must be defined"
+#endif
+#ifndef DBAR_KIND
+#error "DBAR_KIND (0 float, 1 double, 2 double-float) must be defined"
 #endif
 #ifndef DBAR_LOGN
 #error "DBAR_LOGN must be defined"
@@ -20,7 +23,7 @@ static cudaError_t set_smem(K kernel, size_t bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-template <typename T, int LOGN>
+template <typename T, int LOGN, bool IN64>
 cudaError_t launch_pass_a_n(const PassArgs<T>& a, int nslots, cudaStream_t s) {
   using G = RowG<T, LOGN>;
   const int MA = a.M > 1 ? a.M : 1;
@@ -28,9 +31,9 @@ cudaError_t launch_pass_a_n(const PassArgs<T>& a, int nslots, cudaStream_t s) {
   const size_t sm = align16((size_t)G::LINES * G::P * sizeof(cx<T>)) +
                     (size_t)G::LINES * NSEG * (MA + 1) * sizeof(cx<double>) +
                     (size_t)G::LINES * (a.M + 2) * sizeof(cx<double>);
-  cudaError_t e = set_smem(k_pass_a<T, LOGN>, sm);
+  cudaError_t e = set_smem(k_pass_a<T, LOGN, IN64>, sm);
   if (e != cudaSuccess) return e;
-  k_pass_a<T, LOGN><<<dim3(G::N / G::LINES, nslots), G::THREADS, sm, s>>>(a);
+  k_pass_a<T, LOGN, IN64><<<dim3(G::N / G::LINES, nslots), G::THREADS, sm, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -55,7 +58,15 @@ cudaError_t launch_pass_c_n(const PassArgs<T>& a, int nslots, cudaStream_t s) {
 }
 
 typedef DBAR_T TT;
-template cudaError_t launch_pass_a_n<TT, DBAR_LOGN>(const PassArgs<TT>&, int, cudaStream_t);
+#if DBAR_KIND == 2
+// double-float: the right-hand side and the true residual of the refinement
+template cudaError_t launch_pass_a_n<dd, DBAR_LOGN, true>(const PassArgs<dd>&, int, cudaStream_t);
+template cudaError_t launch_pass_b_n<dd, DBAR_LOGN, PB_MATVEC>(const PassArgs<dd>&, int, cudaStream_t);
+template cudaError_t launch_pass_b_n<dd, DBAR_LOGN, PB_RHS>(const PassArgs<dd>&, int, cudaStream_t);
+template cudaError_t launch_pass_c_n<dd, float, DBAR_LOGN, PC_RHS>(const PassArgs<dd>&, int, cudaStream_t);
+template cudaError_t launch_pass_c_n<dd, float, DBAR_LOGN, PC_RES>(const PassArgs<dd>&, int, cudaStream_t);
+#else
+template cudaError_t launch_pass_a_n<TT, DBAR_LOGN, false>(const PassArgs<TT>&, int, cudaStream_t);
 template cudaError_t launch_pass_b_n<TT, DBAR_LOGN, PB_MATVEC>(const PassArgs<TT>&, int, cudaStream_t);
 template cudaError_t launch_pass_b_n<TT, DBAR_LOGN, PB_RHS>(const PassArgs<TT>&, int, cudaStream_t);
 template cudaError_t launch_pass_b_n<TT, DBAR_LOGN, PB_HOUT>(const PassArgs<TT>&, int, cudaStream_t);
@@ -64,11 +75,12 @@ template cudaError_t launch_pass_b_n<TT, DBAR_LOGN, PB_INV>(const PassArgs<TT>&,
 template cudaError_t launch_pass_c_n<TT, TT, DBAR_LOGN, PC_KS>(const PassArgs<TT>&, int, cudaStream_t);
 template cudaError_t launch_pass_c_n<TT, TT, DBAR_LOGN, PC_FWD>(const PassArgs<TT>&, int, cudaStream_t);
 template cudaError_t launch_pass_c_n<TT, TT, DBAR_LOGN, PC_INV>(const PassArgs<TT>&, int, cudaStream_t);
-#if DBAR_T_IS_DOUBLE
+#if DBAR_KIND == 1
 template cudaError_t launch_pass_c_n<double, double, DBAR_LOGN, PC_RHS>(const PassArgs<double>&, int, cudaStream_t);
 template cudaError_t launch_pass_c_n<double, float, DBAR_LOGN, PC_RHS>(const PassArgs<double>&, int, cudaStream_t);
 template cudaError_t launch_pass_c_n<double, double, DBAR_LOGN, PC_RES>(const PassArgs<double>&, int, cudaStream_t);
 template cudaError_t launch_pass_c_n<double, float, DBAR_LOGN, PC_RES>(const PassArgs<double>&, int, cudaStream_t);
+#endif
 #endif
 
 }  // namespace dbar

@@ -27,7 +27,7 @@ inline Geo make_geo(int N) {
 inline int row_blocks(int N) { return N / row_lines(ilog2(N)); }
 
 // per-size launchers (kern_pass.cu, one translation unit per precision and size)
-template <typename T, int LOGN>
+template <typename T, int LOGN, bool IN64>
 cudaError_t launch_pass_a_n(const PassArgs<T>& a, int nslots, cudaStream_t s);
 template <typename T, int LOGN, int MODE>
 cudaError_t launch_pass_b_n(const PassArgs<T>& a, int nslots, cudaStream_t s);
@@ -35,7 +35,7 @@ template <typename T, typename TO, int LOGN, int MODE>
 cudaError_t launch_pass_c_n(const PassArgs<T>& a, int nslots, cudaStream_t s);
 
 // size dispatch (dispatch.cu)
-template <typename T>
+template <typename T, bool IN64 = false>
 cudaError_t launch_pass_a(const PassArgs<T>& a, int nslots, cudaStream_t s);
 template <typename T, int MODE>
 cudaError_t launch_pass_b(const PassArgs<T>& a, int nslots, cudaStream_t s);
@@ -59,13 +59,14 @@ cudaError_t launch_cycle_start(const CycleState& c, const double* part, int nblk
                                cudaStream_t s);
 
 // small helpers (kern_f64.cu)
-cudaError_t launch_transpose_q(const cx<double>* Q, cx<double>* QT64, cx<float>* QT32, int N, cudaStream_t s);
-cudaError_t launch_delta_build(const cx<double>* V, const cx<double>* W, cx<double>* DT64, cx<float>* DT32, int N,
+cudaError_t launch_load_q(const cx<double>* Q, cx<double>* Q64, cx<float>* Q32, int N, cudaStream_t s);
+cudaError_t launch_delta_build(const cx<double>* V, const cx<double>* W, cx<double>* D64, cx<float>* D32, int N,
                                int nfields, cudaStream_t s);
 cudaError_t launch_add_fields(const void* S, const void* KS, void* AS, long long n, int fp32, cudaStream_t s);
 cudaError_t launch_taylor_final(const cx<double>* partA, int nblkA, int M, int N, cx<double>* out, int nslots,
                                 cudaStream_t s);
 cudaError_t launch_cast_fields(const cx<double>* in, cx<float>* out, long long n, cudaStream_t s);
+cudaError_t launch_split_fields(const cx<double>* in, cx<dd>* out, long long n, cudaStream_t s);
 cudaError_t launch_check_finite(const double* p, long long n, int* flag, cudaStream_t s);
 
 }  // namespace dbar

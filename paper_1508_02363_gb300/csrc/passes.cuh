@@ -66,7 +66,7 @@ struct ColG {
 // ---------------------------------------------------------------------------
 // Pass A: rows of a Fourier field.
 // ---------------------------------------------------------------------------
-template <typename T, int LOGN>
+template <typename T, int LOGN, bool IN64>
 __global__ void __launch_bounds__(RowG<T, LOGN>::THREADS, RowG<T, LOGN>::MINB) k_pass_a(const PassArgs<T> a) {
   using G = RowG<T, LOGN>;
   constexpr int N = G::N, TPL = G::TPL, LINES = G::LINES, P = G::P;
@@ -79,10 +79,16 @@ __global__ void __launch_bounds__(RowG<T, LOGN>::THREADS, RowG<T, LOGN>::MINB) k
   const int p2 = blockIdx.x * LINES + line;
   cx<T>* sl = reinterpret_cast<cx<T>*>(smem) + line * P;
   const T sc = a.in_scale ? (T)a.in_scale[(size_t)slot * a.in_scale_ss] : (T)1;
-  const cx<T>* src = a.in + (size_t)slot * a.in_ss + (size_t)p2 * N + t;
   cx<T> v[16];
+  if constexpr (IN64) {
+    const cx<double>* src = a.in64 + (size_t)slot * a.in_ss + (size_t)p2 * N + t;
 #pragma unroll
-  for (int q = 0; q < 16; ++q) v[q] = cscale(ldg(src + q * TPL), sc);
+    for (int q = 0; q < 16; ++q) v[q] = cscale(ccast<T>(ldg(src + q * TPL)), sc);
+  } else {
+    const cx<T>* src = a.in + (size_t)slot * a.in_ss + (size_t)p2 * N + t;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = cscale(ldg(src + q * TPL), sc);
+  }
 
   // Row moments R_a(p2) = sum_p1 (-1)^p1 S D_a(p1), a = 0..MA.
   constexpr size_t off = ((size_t)LINES * P * sizeof(cx<T>) + 15) & ~(size_t)15;
@@ -99,8 +105,9 @@ __global__ void __launch_bounds__(RowG<T, LOGN>::THREADS, RowG<T, LOGN>::MINB) k
       if ((t + q * TPL) & 1) s = mkc(-s.re, -s.im);
       acc = acc + cmul(s, d);
     }
-    const double re = warp_sum((double)acc.re, SEGW), im = warp_sum((double)acc.im, SEGW);
-    if ((t & (SEGW - 1)) == 0) red[(line * NSEG + seg) * (MA + 1) + aa] = mkc(re, im);
+    // within a warp segment in T (16 x SEGW terms), across segments in FP64
+    const T re = warp_sum_t(acc.re, SEGW), im = warp_sum_t(acc.im, SEGW);
+    if ((t & (SEGW - 1)) == 0) red[(line * NSEG + seg) * (MA + 1) + aa] = mkc((double)re, (double)im);
   }
 
   // S~ (-1)^{p1+p2} / (2 pi L^2) with S~ = S/xi, xi = (m1 + i m2)/L, 0 at xi = 0.
@@ -213,19 +220,19 @@ __global__ void __launch_bounds__(ColG<T, LOGN>::THREADS, ColG<T, LOGN>::MINB) k
     for (int q = 0; q < 16; ++q) v[q] = v[q] + fill;
     for (int n = 0; n <= M; ++n) {
       const cx<T> cn = coef[n];
-      const cx<T>* D = a.DeltaT + ((size_t)n * N + j1) * N + t;
+      const cx<T>* D = a.Delta + ((size_t)n * N + t) * N + j1;
 #pragma unroll
-      for (int q = 0; q < 16; ++q) v[q] = v[q] + cmul(cn, ldg(D + q * TPL));
+      for (int q = 0; q < 16; ++q) v[q] = v[q] + cmul(cn, ldg(D + (size_t)q * TPL * N));
     }
   }
   if (MODE == PB_MATVEC || MODE == PB_RHS) {
     // w = (2 pi L^2/N^2) E_k Q conj(h)   (right-hand side: E_k Q)
     const cx<T> exv = cscale(ldg(a.ex + (size_t)slot * N + j1), (T)a.sw);
     const cx<T>* EY = a.ey + (size_t)slot * N + t;
-    const cx<T>* QC = a.QT + (size_t)j1 * N + t;
+    const cx<T>* QC = a.Q + (size_t)t * N + j1;
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
-      const cx<T> eq = cmul(cmul(exv, ldg(EY + q * TPL)), ldg(QC + q * TPL));
+      const cx<T> eq = cmul(cmul(exv, ldg(EY + q * TPL)), ldg(QC + (size_t)q * TPL * N));
       v[q] = (MODE == PB_RHS) ? eq : cmulc(eq, v[q]);
     }
     fft_line<T, LOGN, false>(v, sl, t, a.tw);

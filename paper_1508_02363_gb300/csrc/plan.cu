@@ -16,6 +16,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/dbar.h"
@@ -112,15 +113,23 @@ struct dbar_plan {
   cx<float>* tw32 = nullptr;
   cx<double>* Da64 = nullptr;
   cx<float>* Da32 = nullptr;
-  cx<double>* Dt64 = nullptr;  // Delta_n^T
-  cx<float>* Dt32 = nullptr;
-  cx<double>* QT64 = nullptr;
-  cx<float>* QT32 = nullptr;
+  cx<double>* Delta64 = nullptr;  // Delta_n = W_n - V_n, [n][y][x]
+  cx<float>* Delta32 = nullptr;
+  cx<double>* Q64 = nullptr;
+  cx<float>* Q32 = nullptr;
   cx<double>* Qdev = nullptr;  // staging for a host Q
   cx<double>* ex64 = nullptr;
   cx<double>* ey64 = nullptr;
   cx<float>* ex32 = nullptr;
   cx<float>* ey32 = nullptr;
+  // double-float copies for the right-hand side and residual of the mixed path
+  bool resid_dd = false;
+  cx<dd>* tw_dd = nullptr;
+  cx<dd>* Da_dd = nullptr;
+  cx<dd>* Delta_dd = nullptr;
+  cx<dd>* Q_dd = nullptr;
+  cx<dd>* ex_dd = nullptr;
+  cx<dd>* ey_dd = nullptr;
   // workspaces
   cx<double>* x64 = nullptr;
   cx<double>* b64 = nullptr;
@@ -178,6 +187,7 @@ extern "C" void dbar_params_init(dbar_params* p, int N, double L) {
   p->max_batch = 0;
   p->inner_tol = 1e-6;
   p->max_outer = 40;
+  p->resid_mode = DBAR_RESID_DOUBLE_FLOAT;
 }
 
 extern "C" const char* dbar_last_error(void) { return g_last_error.c_str(); }
@@ -264,6 +274,10 @@ static dbar_status upload_ek(dbar_plan* P, const double* k, int nb, cudaStream_t
   }
   CK(timed(P, st, K_OTHER, [&] { return launch_cast_fields(P->ex64, P->ex32, (long long)nb * N, st); }));
   CK(timed(P, st, K_OTHER, [&] { return launch_cast_fields(P->ey64, P->ey32, (long long)nb * N, st); }));
+  if (P->resid_dd) {
+    CK(timed(P, st, K_OTHER, [&] { return launch_split_fields(P->ex64, P->ex_dd, (long long)nb * N, st); }));
+    CK(timed(P, st, K_OTHER, [&] { return launch_split_fields(P->ey64, P->ey_dd, (long long)nb * N, st); }));
+  }
   return DBAR_OK;
 }
 
@@ -279,8 +293,8 @@ PassArgs<double> base_args<double>(const dbar_plan* P) {
   a.tw = P->tw64;
   a.Da = P->Da64;
   a.Da64 = P->Da64;
-  a.DeltaT = P->Dt64;
-  a.QT = P->QT64;
+  a.Delta = P->Delta64;
+  a.Q = P->Q64;
   a.ex = P->ex64;
   a.ey = P->ey64;
   a.inv2piL = P->inv2piL;
@@ -300,10 +314,32 @@ PassArgs<float> base_args<float>(const dbar_plan* P) {
   a.tw = P->tw32;
   a.Da = P->Da32;
   a.Da64 = P->Da64;
-  a.DeltaT = P->Dt32;
-  a.QT = P->QT32;
+  a.Delta = P->Delta32;
+  a.Q = P->Q32;
   a.ex = P->ex32;
   a.ey = P->ey32;
+  a.inv2piL = P->inv2piL;
+  a.sw = P->sw;
+  a.fillscale = P->fillscale;
+  a.partA = P->partA;
+  a.nblkA = P->N / a.g.lines;
+  a.part = P->part2;
+  return a;
+}
+
+template <>
+PassArgs<dd> base_args<dd>(const dbar_plan* P) {
+  PassArgs<dd> a;
+  std::memset(&a, 0, sizeof(a));
+  a.g = make_geo<dd>(P->N);
+  a.M = P->M;
+  a.tw = P->tw_dd;
+  a.Da = P->Da_dd;
+  a.Da64 = P->Da64;
+  a.Delta = P->Delta_dd;
+  a.Q = P->Q_dd;
+  a.ex = P->ex_dd;
+  a.ey = P->ey_dd;
   a.inv2piL = P->inv2piL;
   a.sw = P->sw;
   a.fillscale = P->fillscale;
@@ -355,45 +391,66 @@ static dbar_status h_of_S64(dbar_plan* P, const cx<double>* S, long long s_ss, c
   return DBAR_OK;
 }
 
-// b = -i F(E_k Q) in FP64 -> b64, the Krylov start vector V[slot][0] (TI) and |b|^2 partials.
-template <typename TI>
-static dbar_status build_rhs(dbar_plan* P, int nb, cudaStream_t st) {
-  PassArgs<double> a = base_args<double>(P);
+// b = -i F(E_k Q) computed in TC (FP64 or double-float) -> b64 (FP64 storage),
+// the Krylov start vector V[slot][0] (TI) and |b|^2 partials.
+template <typename TC, typename TI>
+static dbar_status build_rhs_t(dbar_plan* P, int nb, cudaStream_t st) {
+  PassArgs<TC> a = base_args<TC>(P);
   a.out = P->T2;
   a.out_ss = P->n;
-  CK(timed(P, st, K_RHS, [&] { return launch_pass_b<double, PB_RHS>(a, nb, st); }));
-  a.in = reinterpret_cast<const cx<double>*>(P->T2);
+  CK(timed(P, st, K_RHS, [&] { return launch_pass_b<TC, PB_RHS>(a, nb, st); }));
+  a.in = reinterpret_cast<const cx<TC>*>(P->T2);
   a.in_ss = P->n;
   a.out = P->b64;
   a.out_ss = P->n;
   a.out2 = P->V;
   a.out2_ss = (long long)(P->m + 1) * P->n;
-  CK(timed(P, st, K_RHS, [&] { return launch_pass_c<double, TI, PC_RHS>(a, nb, st); }));
+  CK(timed(P, st, K_RHS, [&] { return launch_pass_c<TC, TI, PC_RHS>(a, nb, st); }));
   return DBAR_OK;
 }
 
-// r = b - A x in FP64 -> V[slot][0] (TI) and |r|^2 partials; only active slots.
-template <typename TI>
-static dbar_status true_residual(dbar_plan* P, int nb, cudaStream_t st) {
-  PassArgs<double> a = base_args<double>(P);
+// r = b - A x computed in TC from the FP64 x and b -> V[slot][0] (TI) and |r|^2
+// partials; only active slots.
+template <typename TC, typename TI>
+static dbar_status true_residual_t(dbar_plan* P, int nb, cudaStream_t st) {
+  PassArgs<TC> a = base_args<TC>(P);
   a.run = P->cs.active;
-  a.in = P->x64;
   a.in_ss = P->n;
   a.out = P->T1;
   a.out_ss = P->n;
-  CK(timed(P, st, K_RES_A, [&] { return launch_pass_a<double>(a, nb, st); }));
-  a.in = reinterpret_cast<const cx<double>*>(P->T1);
+  if constexpr (std::is_same<TC, double>::value) {
+    a.in = P->x64;
+    CK(timed(P, st, K_RES_A, [&] { return launch_pass_a<TC, false>(a, nb, st); }));
+  } else {
+    a.in64 = P->x64;
+    CK(timed(P, st, K_RES_A, [&] { return launch_pass_a<TC, true>(a, nb, st); }));
+  }
+  a.in = reinterpret_cast<const cx<TC>*>(P->T1);
   a.out = P->T2;
-  CK(timed(P, st, K_RES_B, [&] { return launch_pass_b<double, PB_MATVEC>(a, nb, st); }));
-  a.in = reinterpret_cast<const cx<double>*>(P->T2);
+  CK(timed(P, st, K_RES_B, [&] { return launch_pass_b<TC, PB_MATVEC>(a, nb, st); }));
+  a.in = reinterpret_cast<const cx<TC>*>(P->T2);
   a.out = nullptr;
   a.out2 = P->V;
   a.out2_ss = (long long)(P->m + 1) * P->n;
   a.b = P->b64;
   a.x = P->x64;
   a.f_ss = P->n;
-  CK(timed(P, st, K_RES_C, [&] { return launch_pass_c<double, TI, PC_RES>(a, nb, st); }));
+  CK(timed(P, st, K_RES_C, [&] { return launch_pass_c<TC, TI, PC_RES>(a, nb, st); }));
   return DBAR_OK;
+}
+
+template <typename TI>
+static dbar_status build_rhs(dbar_plan* P, int nb, cudaStream_t st) {
+  if constexpr (std::is_same<TI, float>::value)
+    if (P->resid_dd) return build_rhs_t<dd, TI>(P, nb, st);
+  return build_rhs_t<double, TI>(P, nb, st);
+}
+
+template <typename TI>
+static dbar_status true_residual(dbar_plan* P, int nb, cudaStream_t st) {
+  if constexpr (std::is_same<TI, float>::value)
+    if (P->resid_dd) return true_residual_t<dd, TI>(P, nb, st);
+  return true_residual_t<double, TI>(P, nb, st);
 }
 
 // Algorithmic bytes of one finished cycle (profiling only): every field the
@@ -520,6 +577,8 @@ static dbar_status check_params(const dbar_params* p) {
   if (p->prec == DBAR_MIXED && !(p->inner_tol > 0.0 && p->inner_tol < 1.0))
     return fail(DBAR_EINVAL, "inner_tol must be in (0, 1)");
   if (p->max_batch < 0 || p->max_batch > 65535) return fail(DBAR_EINVAL, "max_batch must be in [0, 65535]");
+  if (p->resid_mode != DBAR_RESID_DOUBLE_FLOAT && p->resid_mode != DBAR_RESID_FP64)
+    return fail(DBAR_EINVAL, "resid_mode must be DBAR_RESID_DOUBLE_FLOAT or DBAR_RESID_FP64");
   return DBAR_OK;
 }
 
@@ -555,6 +614,13 @@ static dbar_status plan_tables(dbar_plan* P) {
     }
   CK(cudaMemcpy(P->Da64, D.data(), D.size() * sizeof(cx<double>), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(P->Da32, D32.data(), D32.size() * sizeof(cx<float>), cudaMemcpyHostToDevice));
+  if (P->resid_dd) {
+    std::vector<cx<dd>> twd(N), Dd(D.size());
+    for (int t = 0; t < N; ++t) twd[t] = mkc(dd(tw[t].re), dd(tw[t].im));
+    for (size_t i = 0; i < D.size(); ++i) Dd[i] = mkc(dd(D[i].re), dd(D[i].im));
+    CK(cudaMemcpy(P->tw_dd, twd.data(), N * sizeof(cx<dd>), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(P->Da_dd, Dd.data(), Dd.size() * sizeof(cx<dd>), cudaMemcpyHostToDevice));
+  }
 
   // Delta_n = W_n - V_n, V_n = F_d^{-1}(e^{-|xi|^2} conj(xi)^n / xi, 0 at xi = 0)
   //         = (1/(2 pi L^2)) IDFT((-1)^{p1+p2} e^{-|xi|^2} conj(xi)^n / xi).
@@ -614,8 +680,12 @@ static dbar_status plan_tables(dbar_plan* P) {
       if (launch_pass_b<double, PB_INV>(a, cnt, st) != cudaSuccess) { s = fail(DBAR_ECUDA, "pass B"); break; }
     }
     if (s != DBAR_OK) break;
-    if (launch_delta_build(dE, dW, P->Dt64, P->Dt32, N, nf, st) != cudaSuccess) {
+    if (launch_delta_build(dE, dW, P->Delta64, P->Delta32, N, nf, st) != cudaSuccess) {
       s = fail(DBAR_ECUDA, "delta build");
+      break;
+    }
+    if (P->resid_dd && launch_split_fields(P->Delta64, P->Delta_dd, (long long)nf * nn, st) != cudaSuccess) {
+      s = fail(DBAR_ECUDA, "delta split");
       break;
     }
     e = cudaStreamSynchronize(st);
@@ -646,6 +716,7 @@ extern "C" dbar_status dbar_plan_create(const dbar_params* p, dbar_plan_t* out) 
   P->MA = std::max(1, p->M);
   P->m = p->restart;
   P->mixed = (p->prec == DBAR_MIXED);
+  P->resid_dd = P->mixed && p->resid_mode == DBAR_RESID_DOUBLE_FLOAT;
   P->n = (long long)P->N * P->N;
   cudaGetDevice(&P->device);
   const double L = p->L;
@@ -683,15 +754,23 @@ extern "C" dbar_status dbar_plan_create(const dbar_params* p, dbar_plan_t* out) 
   AL(P->tw32, P->N);
   AL(P->Da64, (size_t)(P->MA + 1) * P->N);
   AL(P->Da32, (size_t)(P->MA + 1) * P->N);
-  AL(P->Dt64, (size_t)(P->M + 1) * n);
-  AL(P->Dt32, (size_t)(P->M + 1) * n);
-  AL(P->QT64, n);
-  AL(P->QT32, n);
+  AL(P->Delta64, (size_t)(P->M + 1) * n);
+  AL(P->Delta32, (size_t)(P->M + 1) * n);
+  AL(P->Q64, n);
+  AL(P->Q32, n);
   AL(P->Qdev, n);
   AL(P->ex64, (size_t)B * P->N);
   AL(P->ey64, (size_t)B * P->N);
   AL(P->ex32, (size_t)B * P->N);
   AL(P->ey32, (size_t)B * P->N);
+  if (P->resid_dd) {
+    AL(P->tw_dd, P->N);
+    AL(P->Da_dd, (size_t)(P->MA + 1) * P->N);
+    AL(P->Delta_dd, (size_t)(P->M + 1) * n);
+    AL(P->Q_dd, n);
+    AL(P->ex_dd, (size_t)B * P->N);
+    AL(P->ey_dd, (size_t)B * P->N);
+  }
   AL(P->x64, (size_t)B * n);
   AL(P->b64, (size_t)B * n);
   cx<double>* t1 = nullptr;
@@ -770,11 +849,12 @@ static dbar_status check_k(const double* k, int nk) {
   return DBAR_OK;
 }
 
-// Q (complex128, device) -> QT64 / QT32, with a finiteness check.
+// Q (complex128, device) -> Q64 / Q32 (plan copies), with a finiteness check.
 static dbar_status load_Q_device(dbar_plan* P, const cx<double>* Qd, cudaStream_t st) {
   CK(cudaMemsetAsync(P->flag, 0, sizeof(int), st));
   CK(timed(P, st, K_OTHER, [&] { return launch_check_finite(reinterpret_cast<const double*>(Qd), 2 * P->n, P->flag, st); }));
-  CK(timed(P, st, K_OTHER, [&] { return launch_transpose_q(Qd, P->QT64, P->QT32, P->N, st); }));
+  CK(timed(P, st, K_OTHER, [&] { return launch_load_q(Qd, P->Q64, P->Q32, P->N, st); }));
+  if (P->resid_dd) CK(timed(P, st, K_OTHER, [&] { return launch_split_fields(P->Q64, P->Q_dd, P->n, st); }));
   int bad = 0;
   CK(cudaMemcpyAsync(&bad, P->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));

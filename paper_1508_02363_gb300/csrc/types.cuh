@@ -17,6 +17,7 @@ struct PassArgs {
   long long in_ss;
   const double* in_scale;
   int in_scale_ss;
+  const cx<double>* in64;  // pass A input kept in FP64 storage (double-float residual)
   // outputs
   void* out;
   long long out_ss;
@@ -31,8 +32,8 @@ struct PassArgs {
   const cx<T>* tw;       // [N]   e^{-2 pi i t/N}
   const cx<T>* Da;       // [MA+1][N]
   const cx<double>* Da64;
-  const cx<T>* DeltaT;   // [M+1][N (x index)][N (y index)]
-  const cx<T>* QT;       // [N (x index)][N (y index)]
+  const cx<T>* Delta;    // [M+1][N (y index)][N (x index)]  W_n - V_n
+  const cx<T>* Q;        // [N (y index)][N (x index)]
   const cx<T>* ex;       // [slot][N]  e^{-2 i k2 x_j}
   const cx<T>* ey;       // [slot][N]  e^{-2 i k1 y_j}
   double inv2piL;        // 1/(2 pi L)

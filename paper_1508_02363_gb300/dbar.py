@@ -19,6 +19,7 @@ _lib = ctypes.CDLL(_LIB_PATH)
 
 DBAR_OK, DBAR_EINVAL, DBAR_ENOMEM, DBAR_ENOCONV, DBAR_ETIMEOUT, DBAR_ECUDA, DBAR_EBUSY = range(7)
 DBAR_FP64, DBAR_MIXED = 0, 1
+DBAR_RESID_DOUBLE_FLOAT, DBAR_RESID_FP64 = 0, 1
 STATUS_NAMES = ["DBAR_OK", "DBAR_EINVAL", "DBAR_ENOMEM", "DBAR_ENOCONV", "DBAR_ETIMEOUT", "DBAR_ECUDA",
                 "DBAR_EBUSY"]
 EXPORTED = ["dbar_params_init", "dbar_last_error", "dbar_plan_create", "dbar_plan_destroy", "dbar_plan_info",
@@ -31,7 +32,7 @@ class dbar_params(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int), ("L", ctypes.c_double), ("M", ctypes.c_int), ("prec", ctypes.c_int),
                 ("restart", ctypes.c_int), ("max_iter", ctypes.c_int), ("tol", ctypes.c_double),
                 ("zero_fill", ctypes.c_int), ("max_batch", ctypes.c_int), ("inner_tol", ctypes.c_double),
-                ("max_outer", ctypes.c_int)]
+                ("max_outer", ctypes.c_int), ("resid_mode", ctypes.c_int)]
 
 
 class DbarError(RuntimeError):
@@ -105,6 +106,8 @@ def dbar_params_init(N: int, L: float, **overrides) -> dbar_params:
     for key, v in overrides.items():
         if key == "prec" and isinstance(v, str):
             v = {"fp64": DBAR_FP64, "mixed": DBAR_MIXED}[v]
+        if key == "resid_mode" and isinstance(v, str):
+            v = {"double_float": DBAR_RESID_DOUBLE_FLOAT, "fp64": DBAR_RESID_FP64}[v]
         setattr(p, key, v)
     return p
 

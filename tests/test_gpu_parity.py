@@ -144,9 +144,11 @@ def test_plain_fp64_workload_matches_oracle(dbar):
     assert rel(r["m"][0], o["m"]) < 1e-12
 
 
-def test_mixed_precision_small_grid_matches_oracle(dbar):
+@pytest.mark.parametrize("resid_mode", ["double_float", "fp64"])
+def test_mixed_precision_small_grid_matches_oracle(dbar, resid_mode):
+    # FP32 inner GMRES; right-hand side and true residual in double-float or native FP64
     w = wl.mixed_1024(N=128, nk=4, L=5.0)
-    plan = dbar.Plan(w.N, w.L, M=2, prec="mixed", restart=24, tol=1e-12, max_batch=4)
+    plan = dbar.Plan(w.N, w.L, M=2, prec="mixed", restart=24, tol=1e-12, max_batch=4, resid_mode=resid_mode)
     r = plan.solve(w.Q, w.k)
     assert r["status"] == dbar.DBAR_OK
     for i in range(w.k.size):
