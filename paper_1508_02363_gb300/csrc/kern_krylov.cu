@@ -109,25 +109,10 @@ cudaError_t launch_add_fields(const void* S, const void* KS, void* AS, long long
   return cudaGetLastError();
 }
 
-// Taylor data of one field per slot from the pass-A partial sums: [slot][M+2] = c_0..c_M, d.
-__global__ void k_taylor_final(const cx<double>* __restrict__ partA, int nblkA, int M, int N,
-                               cx<double>* __restrict__ out) {
-  const int slot = blockIdx.x, lane = threadIdx.x;
-  const cx<double>* pa = partA + (size_t)slot * nblkA * (M + 2);
-  for (int n = 0; n < M + 2; ++n) {
-    double re = 0.0, im = 0.0;
-    for (int b = lane; b < nblkA; b += 32) {
-      re += pa[(size_t)b * (M + 2) + n].re;
-      im += pa[(size_t)b * (M + 2) + n].im;
-    }
-    re = warp_sum(re, 32);
-    im = warp_sum(im, 32);
-    if (lane == 0) out[(size_t)slot * (M + 2) + n] = taylor_coef(mkc(re, im), n, M, N, 1.0);
-  }
-}
-cudaError_t launch_taylor_final(const cx<double>* partA, int nblkA, int M, int N, cx<double>* out, int nslots,
-                                cudaStream_t s) {
-  k_taylor_final<<<nslots, 32, 0, s>>>(partA, nblkA, M, N, out);
+cudaError_t launch_coef(const cx<double>* partA, int nblkA, int M, int N, double fillscale, cx<double>* coef,
+                        int nslots, cudaStream_t s) {
+  if (nslots <= 0) return cudaSuccess;
+  k_coef<<<nslots, 256, 0, s>>>(partA, nblkA, M, N, fillscale, coef);
   return cudaGetLastError();
 }
 

@@ -19,8 +19,12 @@
 
 namespace dbar {
 
-__device__ __forceinline__ double block_sum_256(double v, double* sh) {
-  v = warp_sum(v, 32);
+// Block sum of per-thread partials: within each warp in the partials' own
+// precision (FP32 for the inner solve: GB300's FP64 pipe cannot keep up with
+// one FP64 operation per element at HBM speed), across warps in FP64.
+template <typename T>
+__device__ __forceinline__ double block_sum_256(T v, double* sh) {
+  v = warp_sum_t(v, 32);
   const int w = threadIdx.x >> 5;
   __syncthreads();
   if ((threadIdx.x & 31) == 0) sh[w] = v;
@@ -65,8 +69,8 @@ __global__ void __launch_bounds__(KR_THREADS) k_dots(const KryArgs a, const cx<T
         s += vi.re * w[e].re + vi.im * w[e].im;
       }
     }
-    const double d = warp_sum((double)s, 32);
-    if ((threadIdx.x & 31) == 0) red[wid][i] = d;
+    const T d = warp_sum_t(s, 32);
+    if ((threadIdx.x & 31) == 0) red[wid][i] = (double)d;
   }
   __syncthreads();
   for (int i = threadIdx.x; i <= j; i += blockDim.x) {
@@ -137,7 +141,7 @@ __global__ void __launch_bounds__(KR_THREADS) k_update(const KryArgs a, cx<T>* _
       s += w[e].re * w[e].re + w[e].im * w[e].im;
     }
   }
-  const double tot = block_sum_256((double)s, sh);
+  const double tot = block_sum_256(s, sh);
   if (threadIdx.x == 0) a.part2[(size_t)slot * a.nchunk + blockIdx.x] = tot;
 }
 

@@ -63,8 +63,8 @@ cudaError_t launch_load_q(const cx<double>* Q, cx<double>* Q64, cx<float>* Q32, 
 cudaError_t launch_delta_build(const cx<double>* V, const cx<double>* W, cx<double>* D64, cx<float>* D32, int N,
                                int nfields, cudaStream_t s);
 cudaError_t launch_add_fields(const void* S, const void* KS, void* AS, long long n, int fp32, cudaStream_t s);
-cudaError_t launch_taylor_final(const cx<double>* partA, int nblkA, int M, int N, cx<double>* out, int nslots,
-                                cudaStream_t s);
+cudaError_t launch_coef(const cx<double>* partA, int nblkA, int M, int N, double fillscale, cx<double>* coef,
+                        int nslots, cudaStream_t s);
 cudaError_t launch_cast_fields(const cx<double>* in, cx<float>* out, long long n, cudaStream_t s);
 cudaError_t launch_split_fields(const cx<double>* in, cx<dd>* out, long long n, cudaStream_t s);
 cudaError_t launch_check_finite(const double* p, long long n, int* flag, cudaStream_t s);

@@ -188,27 +188,14 @@ __global__ void __launch_bounds__(ColG<T, LOGN>::THREADS, ColG<T, LOGN>::MINB) k
   constexpr size_t off = ((size_t)G::COLS * P * sizeof(cx<T>) + 15) & ~(size_t)15;
   cx<T>* coef = reinterpret_cast<cx<T>*>(smem + off);  // [M+1] c_n, then the fill d'
 
-  if (MODE == PB_MATVEC || MODE == PB_HOUT) {
-    if (threadIdx.x < 32) {
-      const cx<double>* pa = a.partA + (size_t)slot * a.nblkA * (M + 2);
-      for (int n = 0; n < M + 2; ++n) {
-        double re = 0.0, im = 0.0;
-        for (int b = lane; b < a.nblkA; b += 32) {
-          const cx<double> x = pa[(size_t)b * (M + 2) + n];
-          re += x.re;
-          im += x.im;
-        }
-        re = warp_sum(re, 32);
-        im = warp_sum(im, 32);
-        if (lane == 0) coef[n] = ccast<T>(taylor_coef(mkc(re, im), n, M, N, a.fillscale));
-      }
-    }
-  }
   cx<T> v[16];
   if (MODE != PB_RHS) {
     const cx<T>* src = a.in + (size_t)slot * a.in_ss + (size_t)t * N + j1;
 #pragma unroll
     for (int q = 0; q < 16; ++q) v[q] = ldg(src + (size_t)q * TPL * N);
+    // Taylor coefficients of this slot (k_coef), issued after the field loads
+    if ((MODE == PB_MATVEC || MODE == PB_HOUT) && threadIdx.x < M + 2)
+      coef[threadIdx.x] = ccast<T>(a.coef[(size_t)slot * (M + 2) + threadIdx.x]);
     if (MODE == PB_FWD) fft_line<T, LOGN, false>(v, sl, t, a.tw);
     else fft_line<T, LOGN, true>(v, sl, t, a.tw);
   }
@@ -240,6 +227,37 @@ __global__ void __launch_bounds__(ColG<T, LOGN>::THREADS, ColG<T, LOGN>::MINB) k
   cx<T>* dst = reinterpret_cast<cx<T>*>(a.out) + (size_t)slot * a.out_ss + (size_t)t * N + j1;
 #pragma unroll
   for (int q = 0; q < 16; ++q) dst[(size_t)q * TPL * N] = v[q];
+}
+
+// ---------------------------------------------------------------------------
+// Taylor coefficients of each slot from the pass-A block partials, in a fixed
+// order: coef[slot] = c_0..c_M, then the fill d' = d * fillscale.
+// ---------------------------------------------------------------------------
+static __global__ void __launch_bounds__(256) k_coef(const cx<double>* __restrict__ partA, int nblkA, int M, int N,
+                                              double fillscale, cx<double>* __restrict__ coef) {
+  __shared__ double sre[256], sim[256];
+  const int slot = blockIdx.x;
+  const cx<double>* pa = partA + (size_t)slot * nblkA * (M + 2);
+  for (int n = 0; n < M + 2; ++n) {
+    double re = 0.0, im = 0.0;
+    for (int b = threadIdx.x; b < nblkA; b += blockDim.x) {
+      const cx<double> x = pa[(size_t)b * (M + 2) + n];
+      re += x.re;
+      im += x.im;
+    }
+    sre[threadIdx.x] = re;
+    sim[threadIdx.x] = im;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+      if ((int)threadIdx.x < w) {
+        sre[threadIdx.x] += sre[threadIdx.x + w];
+        sim[threadIdx.x] += sim[threadIdx.x + w];
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) coef[(size_t)slot * (M + 2) + n] = taylor_coef(mkc(sre[0], sim[0]), n, M, N, fillscale);
+    __syncthreads();
+  }
 }
 
 // ---------------------------------------------------------------------------

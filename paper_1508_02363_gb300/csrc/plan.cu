@@ -141,6 +141,7 @@ struct dbar_plan {
   double* part = nullptr;
   double* part2 = nullptr;
   double* coef = nullptr;
+  cx<double>* tcoef = nullptr;  // [B][M+2] Taylor coefficients of the field in flight
   int* flag = nullptr;
   CycleState cs;
   // host staging
@@ -302,6 +303,7 @@ PassArgs<double> base_args<double>(const dbar_plan* P) {
   a.fillscale = P->fillscale;
   a.partA = P->partA;
   a.nblkA = P->N / a.g.lines;
+  a.coef = P->tcoef;
   a.part = P->part2;
   return a;
 }
@@ -323,6 +325,7 @@ PassArgs<float> base_args<float>(const dbar_plan* P) {
   a.fillscale = P->fillscale;
   a.partA = P->partA;
   a.nblkA = P->N / a.g.lines;
+  a.coef = P->tcoef;
   a.part = P->part2;
   return a;
 }
@@ -345,8 +348,15 @@ PassArgs<dd> base_args<dd>(const dbar_plan* P) {
   a.fillscale = P->fillscale;
   a.partA = P->partA;
   a.nblkA = P->N / a.g.lines;
+  a.coef = P->tcoef;
   a.part = P->part2;
   return a;
+}
+
+// Taylor coefficients of the fields pass A just read (k_coef), for pass B.
+template <typename T>
+static cudaError_t launch_coef_for(dbar_plan* P, const PassArgs<T>& a, int nb, cudaStream_t st) {
+  return launch_coef(P->partA, a.nblkA, P->M, P->N, P->fillscale, P->tcoef, nb, st);
 }
 
 // One application of K (A S = S + K S) to nb fields: S (T) -> T1 -> T2 -> out (T).
@@ -362,6 +372,7 @@ static dbar_status apply_K(dbar_plan* P, const cx<T>* S, long long s_ss, const d
   a.out = P->T1;
   a.out_ss = P->n;
   CK(timed(P, st, K_PASS_A, [&] { return launch_pass_a<T>(a, nb, st); }));
+  CK(timed(P, st, K_SCALAR, [&] { return launch_coef_for(P, a, nb, st); }));
   a.in = reinterpret_cast<const cx<T>*>(P->T1);
   a.in_ss = P->n;
   a.in_scale = nullptr;
@@ -383,6 +394,7 @@ static dbar_status h_of_S64(dbar_plan* P, const cx<double>* S, long long s_ss, c
   a.out = P->T1;
   a.out_ss = P->n;
   CK(timed(P, st, K_OTHER, [&] { return launch_pass_a<double>(a, nb, st); }));
+  CK(timed(P, st, K_OTHER, [&] { return launch_coef_for(P, a, nb, st); }));
   a.in = reinterpret_cast<const cx<double>*>(P->T1);
   a.in_ss = P->n;
   a.out = out;
@@ -425,6 +437,7 @@ static dbar_status true_residual_t(dbar_plan* P, int nb, cudaStream_t st) {
     a.in64 = P->x64;
     CK(timed(P, st, K_RES_A, [&] { return launch_pass_a<TC, true>(a, nb, st); }));
   }
+  CK(timed(P, st, K_SCALAR, [&] { return launch_coef_for(P, a, nb, st); }));
   a.in = reinterpret_cast<const cx<TC>*>(P->T1);
   a.out = P->T2;
   CK(timed(P, st, K_RES_B, [&] { return launch_pass_b<TC, PB_MATVEC>(a, nb, st); }));
@@ -789,6 +802,7 @@ extern "C" dbar_status dbar_plan_create(const dbar_params* p, dbar_plan_t* out) 
   AL(P->part, (size_t)B * (P->m + 1) * nchunk);
   AL(P->part2, (size_t)B * std::max(std::max(nchunk, P->N), 2 * (P->M + 2)));
   AL(P->coef, (size_t)B * (P->m + 1));
+  AL(P->tcoef, (size_t)B * (P->M + 2));
   AL(P->flag, 4);
   CycleState& c = P->cs;
   const int m = P->m;
@@ -1005,8 +1019,8 @@ extern "C" dbar_status dbar_taylor(dbar_plan_t P, int nk, const void* S, double*
     nblkA = a.nblkA;
     CK(launch_pass_a<double>(a, nk, st));
   }
-  cx<double>* dc = reinterpret_cast<cx<double>*>(P->part2);
-  CK(launch_taylor_final(P->partA, nblkA, P->M, P->N, dc, nk, st));
+  cx<double>* dc = P->tcoef;
+  CK(launch_coef(P->partA, nblkA, P->M, P->N, 1.0, dc, nk, st));
   CK(cudaMemcpyAsync(coef, dc, (size_t)nk * (P->M + 2) * sizeof(cx<double>), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   return DBAR_OK;

@@ -41,6 +41,7 @@ struct PassArgs {
   double fillscale;      // 1/(2 pi L^2), or 0 for the zero-fill reading
   cx<double>* partA;     // [slot][nblkA][M+2]
   int nblkA;
+  const cx<double>* coef;  // [slot][M+2] c_0..c_M, d' (k_coef output, read by pass B)
   double* part;          // [slot][gridDim.x] squared-norm partials (pass C)
 };
 
