@@ -47,6 +47,17 @@ __device__ __forceinline__ cx<double> taylor_coef(cx<double> s, int n, int M, in
   return s;
 }
 
+// 1/(2 pi L (m1^2 + m2^2)): exact division in FP64 and double-float; the
+// fast reciprocal (a few ulp) in the FP32 inner solve.
+template <typename T>
+__device__ __forceinline__ T kappa_scale(double inv2piL, int den) {
+  return (T)inv2piL / (T)den;
+}
+template <>
+__device__ __forceinline__ float kappa_scale<float>(double inv2piL, int den) {
+  return __fdividef((float)inv2piL, (float)den);
+}
+
 template <typename T, int LOGN>
 struct RowG {
   static constexpr int N = 1 << LOGN, TPL = N / 16, LINES = row_lines(LOGN), THREADS = LINES * TPL;
@@ -95,7 +106,13 @@ __global__ void __launch_bounds__(RowG<T, LOGN>::THREADS, RowG<T, LOGN>::MINB) k
   cx<double>* red = reinterpret_cast<cx<double>*>(smem + off);
   cx<double>* lc = red + LINES * NSEG * (MA + 1);
   const int seg = TPL >= 32 ? t / 32 : 0;
-  for (int aa = 0; aa <= MA; ++aa) {
+  // a = 0: D_0(p) = N delta_{p,0}, so R_0 = N S(p1 = 0), held by the thread with t = 0
+  if (t == 0) {
+    const cx<T> s0 = v[0];
+    red[(line * NSEG + seg) * (MA + 1)] = mkc((double)s0.re * N, (double)s0.im * N);
+    for (int sg = 1; sg < NSEG; ++sg) red[(line * NSEG + sg) * (MA + 1)] = mkc(0.0, 0.0);
+  }
+  for (int aa = 1; aa <= MA; ++aa) {
     cx<T> acc = mkc((T)0, (T)0);
     const cx<T>* D = a.Da + (size_t)aa * N + t;
 #pragma unroll
@@ -117,7 +134,7 @@ __global__ void __launch_bounds__(RowG<T, LOGN>::THREADS, RowG<T, LOGN>::MINB) k
     const int p1 = t + q * TPL;
     const int m1 = wavenum(p1, N);
     const int den = m1 * m1 + m2 * m2;
-    T f = den ? (T)a.inv2piL / (T)den : (T)0;
+    T f = den ? kappa_scale<T>(a.inv2piL, den) : (T)0;
     if ((p1 + p2) & 1) f = -f;
     v[q] = cmul(v[q], mkc((T)m1 * f, (T)(-m2) * f));
   }
