@@ -117,9 +117,10 @@ def source_digest():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kind):
-    """DRAM bytes per launch of `kind` from the committed ncu summary, if it was
-    taken on the current kernel sources; else None."""
+def ncu_traffic(kind, algorithmic_bytes_per_launch):
+    """DRAM bytes per launch of `kind`: the DRAM/algorithmic ratio measured by ncu on a
+    smaller capture of the same kernel (profiles/ncu_traffic.json) times this launch's
+    algorithmic bytes, if the capture was taken on the current kernel sources; else None."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(path):
         return None
@@ -127,7 +128,8 @@ def ncu_traffic(kind):
         d = json.load(open(path))
         if d.get("source_digest") != source_digest():
             return None
-        return d.get("kinds", {}).get(kind, {}).get("dram_bytes_per_launch")
+        ratio = d.get("kinds", {}).get(kind, {}).get("dram_over_algorithmic")
+        return None if ratio is None else round(ratio * algorithmic_bytes_per_launch)
     except Exception:
         return None
 
@@ -280,7 +282,7 @@ def run_ours(args):
     dom = max(prof.items(), key=lambda kv: kv[1][0])
     dom_name, (dom_ms, dom_launches, dom_bytes) = dom
     achieved = dom_bytes / (dom_ms / 1e3) / 1e9 if dom_ms > 0 else 0.0
-    traffic = ncu_traffic(dom_name)
+    traffic = ncu_traffic(dom_name, dom_bytes / max(dom_launches, 1))
     all_bytes = sum(v[2] for v in prof.values())
     all_ms = sum(v[0] for v in prof.values())
     roofline = {"bound": "hbm", "kernel": dom_name, "achieved": round(achieved, 1), "peak": peak,
