@@ -151,6 +151,23 @@ dbar_status dbar_taylor(dbar_plan_t plan, int nk, const void* S, double* coef, i
 dbar_status dbar_fft2(dbar_plan_t plan, int nk, const void* in, void* out, int sign, int fp32,
                       void* stream);
 
+/* Allocation-free variant of dbar_fft2, for callers that cannot allocate
+ * device memory when they need a transform: code running while a CUDA graph
+ * is being captured, plugins whose host runtime owns all device memory
+ * through its own pool, latency-critical loops that forbid allocator calls.
+ * (The paper has no counterpart: this is an interface for such callers.)
+ * It needs no plan.  Its intermediate field and twiddle tables live in the
+ * library's own global arrays: every GPU that loads the library keeps 16 MiB
+ * of scratch plus ~100 KiB of tables until the process exits.  Limit:
+ * nk*N*N*sizeof(element) <= 16 MiB (1M complex128 or 2M complex64 values per
+ * call); larger calls return DBAR_EINVAL.  N is a power of two in [32, 2048].
+ * All calls share the scratch, so calls that overlap on the GPU race.  The
+ * first call on a device uploads the twiddle tables and looks up the arrays'
+ * device addresses, so make it before any stream capture.  in and out are
+ * device pointers ([nk][N][N], complex128, or complex64 when fp32 = 1) and may
+ * be equal; sign as in dbar_fft2.  Returns after the stream has drained. */
+dbar_status dbar_fft2_noalloc(int N, int nk, const void* in, void* out, int sign, int fp32, void* stream);
+
 /* --- tracing ------------------------------------------------------------ */
 
 /* Number of kernel kinds the profiler distinguishes, and the name of one. */

@@ -2,7 +2,15 @@
 // instantiated in its own translation unit (kern_f32.cu, kern_f64.cu) so the
 // two compile in parallel.
 #pragma once
+#include <string>
+
+#include "../../include/dbar.h"
 #include "types.cuh"
+
+namespace dbar {}  // namespace dbar
+
+// Records msg as the calling thread's last error (dbar_last_error) and returns st.
+dbar_status dbar_internal_fail(dbar_status st, const std::string& msg);
 
 namespace dbar {
 

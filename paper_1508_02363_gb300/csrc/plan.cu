@@ -32,6 +32,8 @@ static dbar_status fail(dbar_status st, const std::string& msg) {
   return st;
 }
 
+dbar_status dbar_internal_fail(dbar_status st, const std::string& msg) { return fail(st, msg); }
+
 #define CK(call)                                                                              \
   do {                                                                                        \
     cudaError_t e_ = (call);                                                                  \

@@ -25,7 +25,7 @@ STATUS_NAMES = ["DBAR_OK", "DBAR_EINVAL", "DBAR_ENOMEM", "DBAR_ENOCONV", "DBAR_E
 EXPORTED = ["dbar_params_init", "dbar_last_error", "dbar_plan_create", "dbar_plan_destroy", "dbar_plan_info",
             "dbar_solve_cgo", "dbar_apply", "dbar_rhs", "dbar_m_from_S", "dbar_taylor", "dbar_fft2",
             "dbar_profile_nkinds", "dbar_profile_kind_name", "dbar_profile", "dbar_profile_read",
-            "dbar_launch_count"]
+            "dbar_launch_count", "dbar_fft2_noalloc"]
 
 
 class dbar_params(ctypes.Structure):
@@ -55,6 +55,7 @@ _lib.dbar_rhs.argtypes = [_vp, _vp, _int, _dp, _vp, _vp]
 _lib.dbar_m_from_S.argtypes = [_vp, _int, _vp, _vp, _vp]
 _lib.dbar_taylor.argtypes = [_vp, _int, _vp, _dp, _int, _vp]
 _lib.dbar_fft2.argtypes = [_vp, _int, _vp, _vp, _int, _int, _vp]
+_lib.dbar_fft2_noalloc.argtypes = [_int, _int, _vp, _vp, _int, _int, _vp]
 _lib.dbar_profile_nkinds.argtypes = []
 _lib.dbar_profile_kind_name.argtypes = [_int]
 _lib.dbar_profile_kind_name.restype = ctypes.c_char_p
@@ -172,6 +173,11 @@ def dbar_taylor(plan, nk: int, S, M: int, fp32: bool = False, stream=None) -> np
 
 def dbar_fft2(plan, nk: int, x, y, sign: int, fp32: bool = False, stream=None) -> None:
     _check(_lib.dbar_fft2(plan, int(nk), _ptr(x), _ptr(y), int(sign), int(fp32), _stream(stream)))
+
+
+def dbar_fft2_noalloc(N: int, nk: int, x, y, sign: int, fp32: bool = False, stream=None) -> None:
+    """2-D DFT without any device allocation (library-owned 16 MiB scratch); see include/dbar.h."""
+    _check(_lib.dbar_fft2_noalloc(int(N), int(nk), _ptr(x), _ptr(y), int(sign), int(fp32), _stream(stream)))
 
 
 def dbar_profile_nkinds() -> int:
