@@ -329,6 +329,78 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ----------------------------------------------------------------------------- serving workload
+
+def run_serving(args):
+    """Poisson arrivals of CGO requests into the continuous-batching server.
+
+    Each request: N drawn uniformly from {256, 512, 1024, 2048}, raised to the
+    smallest size that resolves its k (N/(2L) >= 2 max(|k1|,|k2|) + XI_Q), L = 6,
+    |k| log-uniform in [0.1, 20], Q a Gaussian mixture of 1-6 terms.  Potentials
+    come from a pool of POOL seeded mixtures per N (generating a fresh 2048^2
+    field per request on the host would outpace the GPU); k is drawn per request.
+    """
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1508_02363_gb300 import dbar
+    import workloads as wl
+
+    L, XI_Q, POOL, KMAX = 6.0, 20.0, 8, 20.0
+    sizes = [256, 512, 1024, 2048]
+    rng = np.random.default_rng(args.seed)
+    pool = {N: [wl.mixture_request(10_000 * N + i, N, L, KMAX)[0] for i in range(POOL)] for N in sizes}
+    nreq = int(args.rate * args.duration)
+    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, size=nreq))
+    plan_reqs = []
+    for i in range(nreq):
+        N0 = int(rng.choice(sizes))
+        k = complex(np.exp(rng.uniform(np.log(0.1), np.log(KMAX))) * np.exp(1j * rng.uniform(0, 2 * np.pi)))
+        N = N0
+        while N < 2048 and N / (2 * L) < 2 * max(abs(k.real), abs(k.imag)) + XI_Q:
+            N *= 2
+        plan_reqs.append((arrivals[i], N, int(rng.integers(POOL)), k))
+    free = torch.cuda.mem_get_info()[0]
+    srv = dbar.Server(int(free * 0.7), prec="mixed", restart=args.restart, tol=1e-12, inner_tol=args.inner_tol,
+                      max_batch=args.serve_batch)
+    tickets = []
+    t0 = time.perf_counter()
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        for (ta, N, qi, k) in plan_reqs:
+            dt = ta - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            tickets.append((srv.submit(N, L, pool[N][qi], k), N, qi, k))
+        results = []
+        for t, N, qi, k in tickets:
+            results.append((srv.wait(t, timeout_s=600, release=True), N, qi, k))
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    # sampled check: 2% of the requests (at least 4) against the plain FP64 GPU solve
+    idx = np.unique(np.linspace(0, len(results) - 1, max(4, len(results) // 50)).astype(int))
+    errs = []
+    for i in idx:
+        r, N, qi, k = results[i]
+        p64 = dbar.Plan(N, L, prec="fp64", restart=args.restart, tol=1e-13, max_batch=1)
+        ref = p64.solve(pool[N][qi], [k], want_m=False)["S"][0]
+        errs.append(float(np.max(np.abs(r["S"] - ref)) / np.max(np.abs(ref))))
+        p64.close()
+    lat = np.array([r["latency_ms"] for r, *_ in results])
+    out = {"metric": "serving: CGO solves/sec and latency under Poisson arrivals", "workload": "serving",
+           "rate_req_s": args.rate, "duration_s": args.duration, "requests": len(results),
+           "solves_per_s": round(st["solves_per_s"], 2), "wall_s": round(wall, 2),
+           "p50_ms": round(float(np.percentile(lat, 50)), 2), "p99_ms": round(float(np.percentile(lat, 99)), 2),
+           "status_ok": int(sum(r["status"] == dbar.DBAR_OK for r, *_ in results)),
+           "resid_max": float(max(r["resid"] for r, *_ in results)),
+           "err_vs_fp64_max": float(max(errs)), "err_sample": len(errs),
+           "n_mix": {str(N): int(sum(1 for _, n, _, _ in tickets if n == N)) for N in sizes},
+           "config": {"L": L, "kmax": KMAX, "xi_q": XI_Q, "pool_per_N": POOL, "restart": args.restart,
+                      "inner_tol": args.inner_tol, "serve_batch": args.serve_batch, "seed": args.seed},
+           "clocks": clk.summary()}
+    print(json.dumps(out))
+
+
 # ----------------------------------------------------------------------------- reference arm
 
 def run_reference(args):
@@ -378,11 +450,17 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nk", type=int, default=0, help="solve only the first nk k values (profiling cases)")
     ap.add_argument("--max-outer", dest="max_outer", type=int, default=40)
+    ap.add_argument("--rate", type=float, default=200.0, help="serving: requests per second")
+    ap.add_argument("--duration", type=float, default=60.0, help="serving: seconds of arrivals")
+    ap.add_argument("--serve-batch", dest="serve_batch", type=int, default=64, help="serving: slots per lane")
+    ap.add_argument("--seed", type=int, default=5)
     ap.add_argument("--quick", action="store_true",
                     help="time the solve only (no FP64 comparison, end-to-end leg or CPU baseline)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_ours(args)
 

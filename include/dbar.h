@@ -168,6 +168,61 @@ dbar_status dbar_fft2(dbar_plan_t plan, int nk, const void* in, void* out, int s
  * be equal; sign as in dbar_fft2.  Returns after the stream has drained. */
 dbar_status dbar_fft2_noalloc(int N, int nk, const void* in, void* out, int sign, int fp32, void* stream);
 
+/* --- serving: continuous batching ------------------------------------- */
+
+/* Many CGO solves are needed per potential and across potentials (Sec. 1;
+ * Sec. 7 outlook).  A server solves requests submitted from any host thread
+ * on one GPU.  Requests of one grid class (N, L) share a batch ("lane") whose
+ * slots each hold one request with its own Q and k; at every GMRES cycle
+ * boundary a lane retires finished slots and admits waiting requests into the
+ * free ones, so new work joins while older work is still iterating.  A
+ * result does not depend on the requests it was batched with.  Device memory
+ * is admitted by mem_budget (bytes): a lane gets the slots the budget leaves
+ * room for; idle lanes are dropped when another grid class needs the memory.
+ * The solver settings (M, prec, restart, tol, ...) come from `defaults`
+ * (its N and L are ignored; max_batch > 0 caps the slots of a lane). */
+typedef struct dbar_server* dbar_server_t;
+
+typedef struct {
+  int N;             /* grid of this request (power of two in [32, 2048])       */
+  double L;          /* box [-pi L, pi L]^2                                      */
+  const double* Q;   /* host, N*N complex128, physical layout; copied at submit  */
+  double k_re, k_im; /* spectral parameter k                                     */
+  int want_m;        /* 1: also return m = h(S) on the x-grid                    */
+} dbar_request;
+
+typedef struct {
+  dbar_status status; /* DBAR_OK, DBAR_ENOCONV (tol missed), or the failure     */
+  int iters;          /* total inner Krylov iterations                          */
+  int cycles;         /* cycles (restarts / refinement steps)                   */
+  double resid;       /* final ||b - A S|| / ||b||                              */
+  double latency_ms;  /* submit -> done                                         */
+  double queue_ms;    /* submit -> admitted into a slot                         */
+  double run_ms;      /* admitted -> done                                       */
+  const double* S;    /* N*N complex128 (Fourier grid); owned by the server     */
+  const double* m;    /* N*N complex128 or NULL; owned by the server            */
+} dbar_result;
+
+dbar_status dbar_serve_create(const dbar_params* defaults, size_t mem_budget, dbar_server_t* out);
+/* Errors: DBAR_EINVAL (bad N, L, NaN/Inf in Q or k), DBAR_ENOMEM (one slot of
+ * this grid cannot fit the budget). */
+dbar_status dbar_serve_submit(dbar_server_t srv, const dbar_request* rq, uint64_t* ticket);
+/* DBAR_EBUSY while the request is pending; DBAR_OK with *out filled when done. */
+dbar_status dbar_serve_poll(dbar_server_t srv, uint64_t ticket, dbar_result* out);
+/* Blocks until done (timeout_s < 0: no limit); DBAR_ETIMEOUT when it runs out. */
+dbar_status dbar_serve_wait(dbar_server_t srv, uint64_t ticket, double timeout_s, dbar_result* out);
+/* Frees a finished request's buffers (its S and m pointers become invalid). */
+dbar_status dbar_serve_release(dbar_server_t srv, uint64_t ticket);
+/* Latency percentiles over finished requests, throughput since the first
+ * submit, finished and pending counts (any pointer may be NULL). */
+dbar_status dbar_serve_stats(dbar_server_t srv, double* p50_ms, double* p99_ms, double* solves_per_s,
+                             uint64_t* completed, uint64_t* pending);
+/* Host-side fault injection for tests: the next lane cycle reports a failure;
+ * its in-flight requests are re-queued once and the lane's plan is rebuilt. */
+dbar_status dbar_serve_inject_fault(dbar_server_t srv);
+/* Stops the worker (pending requests are abandoned) and frees everything. */
+dbar_status dbar_serve_destroy(dbar_server_t srv);
+
 /* --- tracing ------------------------------------------------------------ */
 
 /* Number of kernel kinds the profiler distinguishes, and the name of one. */

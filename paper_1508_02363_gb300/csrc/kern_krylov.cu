@@ -55,9 +55,9 @@ cudaError_t launch_solve_y(const CycleState& c, int nslots, cudaStream_t s) {
   return cudaGetLastError();
 }
 cudaError_t launch_cycle_start(const CycleState& c, const double* part, int nblk, int first, int nslots,
-                               cudaStream_t s) {
+                               cudaStream_t s, const int* mask) {
   if (nslots <= 0) return cudaSuccess;
-  k_cycle_start<<<nslots, KR_THREADS, 0, s>>>(c, part, nblk, first);
+  k_cycle_start<<<nslots, KR_THREADS, 0, s>>>(c, part, nblk, first, mask);
   return cudaGetLastError();
 }
 

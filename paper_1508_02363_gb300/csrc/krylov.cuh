@@ -242,11 +242,13 @@ __global__ void __launch_bounds__(KR_THREADS) k_xupdate(long long n, int mp1, co
 
 // Start of a cycle from a squared-norm partial sum over nblk blocks:
 // beta = ||r||, sigma_0 = 1/beta, g = beta e_1, stop threshold, flags.
-// first != 0: the vector is b itself (records ||b||).
+// first != 0: the vector is b itself (records ||b||).  mask (nullable): only the
+// slots with mask[slot] != 0 (slots being started while others run).
 static __global__ void __launch_bounds__(KR_THREADS) k_cycle_start(CycleState c, const double* part, int nblk,
-                                                             int first) {
+                                                             int first, const int* mask) {
   __shared__ double sh[KR_THREADS / 32];
   const int slot = blockIdx.x;
+  if (mask && !mask[slot]) return;
   if (!first && !c.active[slot]) return;
   double s = 0.0;
   for (int q = threadIdx.x; q < nblk; q += blockDim.x) s += part[(size_t)slot * nblk + q];
@@ -262,7 +264,7 @@ static __global__ void __launch_bounds__(KR_THREADS) k_cycle_start(CycleState c,
   const double bn = c.bnorm[slot];
   const double rel = bn > 0.0 ? beta / bn : 0.0;
   c.resid[slot] = rel;
-  const int act = (bn > 0.0) && (rel > c.tol) && (c.itot[slot] < c.max_iter);
+  const int act = (bn > 0.0) && (rel > c.tol) && (c.itot[slot] < c.max_iter) && (c.ncyc[slot] < c.max_outer);
   c.active[slot] = act;
   c.run[slot] = act;
   c.nsteps[slot] = 0;

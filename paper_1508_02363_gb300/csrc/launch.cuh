@@ -64,7 +64,7 @@ cudaError_t launch_finalize_h(const KryArgs& a, double* H, int j, int nslots, cu
 cudaError_t launch_givens(const KryArgs& a, const CycleState& c, int j, int nslots, cudaStream_t s);
 cudaError_t launch_solve_y(const CycleState& c, int nslots, cudaStream_t s);
 cudaError_t launch_cycle_start(const CycleState& c, const double* part, int nblk, int first, int nslots,
-                               cudaStream_t s);
+                               cudaStream_t s, const int* mask = nullptr);
 
 // small helpers (kern_f64.cu)
 cudaError_t launch_load_q(const cx<double>* Q, cx<double>* Q64, cx<float>* Q32, int N, cudaStream_t s);

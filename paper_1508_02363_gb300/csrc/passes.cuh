@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(ColG<T, LOGN>::THREADS, ColG<T, LOGN>::MINB) k
     // w = (2 pi L^2/N^2) E_k Q conj(h)   (right-hand side: E_k Q)
     const cx<T> exv = cscale(ldg(a.ex + (size_t)slot * N + j1), (T)a.sw);
     const cx<T>* EY = a.ey + (size_t)slot * N + t;
-    const cx<T>* QC = a.Q + (size_t)t * N + j1;
+    const cx<T>* QC = a.Q + (size_t)slot * a.q_ss + (size_t)t * N + j1;
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       const cx<T> eq = cmul(cmul(exv, ldg(EY + q * TPL)), ldg(QC + (size_t)q * TPL * N));

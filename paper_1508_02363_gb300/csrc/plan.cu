@@ -21,6 +21,7 @@
 
 #include "../../include/dbar.h"
 #include "launch.cuh"
+#include "plan_internal.h"
 
 using namespace dbar;
 typedef std::complex<double> zd;
@@ -102,6 +103,9 @@ struct Profiler {
 struct dbar_plan {
   dbar_params p;
   Profiler prof;
+  int per_slot_q = 0;   // 1: every slot has its own potential (serving); 0: one Q for all
+  int* dmask = nullptr;  // [B] device copy of a slot mask
+  int* hmask = nullptr;  // [B] pinned host staging of it
   long long nlaunch = 0;  // kernels launched by this plan
   int N = 0, logN = 0, M = 0, MA = 0, B = 0, m = 0;
   bool mixed = false;
@@ -170,6 +174,7 @@ struct dbar_plan {
     for (void* q : allocs) cudaFree(q);
     if (h_active) cudaFreeHost(h_active);
     if (h_nsteps) cudaFreeHost(h_nsteps);
+    if (hmask) cudaFreeHost(hmask);
     if (h_ek) cudaFreeHost(h_ek);
     cudaSetDevice(cur);
   }
@@ -306,6 +311,7 @@ PassArgs<double> base_args<double>(const dbar_plan* P) {
   a.partA = P->partA;
   a.nblkA = P->N / a.g.lines;
   a.coef = P->tcoef;
+  a.q_ss = P->per_slot_q ? P->n : 0;
   a.part = P->part2;
   return a;
 }
@@ -328,6 +334,7 @@ PassArgs<float> base_args<float>(const dbar_plan* P) {
   a.partA = P->partA;
   a.nblkA = P->N / a.g.lines;
   a.coef = P->tcoef;
+  a.q_ss = P->per_slot_q ? P->n : 0;
   a.part = P->part2;
   return a;
 }
@@ -351,6 +358,7 @@ PassArgs<dd> base_args<dd>(const dbar_plan* P) {
   a.partA = P->partA;
   a.nblkA = P->N / a.g.lines;
   a.coef = P->tcoef;
+  a.q_ss = P->per_slot_q ? P->n : 0;
   a.part = P->part2;
   return a;
 }
@@ -408,8 +416,9 @@ static dbar_status h_of_S64(dbar_plan* P, const cx<double>* S, long long s_ss, c
 // b = -i F(E_k Q) computed in TC (FP64 or double-float) -> b64 (FP64 storage),
 // the Krylov start vector V[slot][0] (TI) and |b|^2 partials.
 template <typename TC, typename TI>
-static dbar_status build_rhs_t(dbar_plan* P, int nb, cudaStream_t st) {
+static dbar_status build_rhs_t(dbar_plan* P, int nb, cudaStream_t st, const int* dmask) {
   PassArgs<TC> a = base_args<TC>(P);
+  a.run = dmask;
   a.out = P->T2;
   a.out_ss = P->n;
   CK(timed(P, st, K_RHS, [&] { return launch_pass_b<TC, PB_RHS>(a, nb, st); }));
@@ -455,10 +464,10 @@ static dbar_status true_residual_t(dbar_plan* P, int nb, cudaStream_t st) {
 }
 
 template <typename TI>
-static dbar_status build_rhs(dbar_plan* P, int nb, cudaStream_t st) {
+static dbar_status build_rhs(dbar_plan* P, int nb, cudaStream_t st, const int* dmask = nullptr) {
   if constexpr (std::is_same<TI, float>::value)
-    if (P->resid_dd) return build_rhs_t<dd, TI>(P, nb, st);
-  return build_rhs_t<double, TI>(P, nb, st);
+    if (P->resid_dd) return build_rhs_t<dd, TI>(P, nb, st, dmask);
+  return build_rhs_t<double, TI>(P, nb, st, dmask);
 }
 
 template <typename TI>
@@ -499,8 +508,42 @@ static void account_cycle(dbar_plan* P, const int* act, const int* ns, int nb, i
   if (nact) by[K_RES_B] += (P->M + 2) * F64;
 }
 
+// Starts slots: x = 0, b = -i F(E_k Q), first cycle state.  hmask == nullptr:
+// all nb slots; else only the slots with hmask[slot] != 0 (the others keep
+// running undisturbed).
 template <typename TI>
-static dbar_status run_cycles(dbar_plan* P, int nb, cudaStream_t st) {
+static dbar_status begin_slots(dbar_plan* P, int nb, const int* hmask, cudaStream_t st) {
+  const long long n = P->n;
+  const int nblkC = row_blocks(P->N);
+  const int* dmask = nullptr;
+  int nnew = nb;
+  if (hmask) {
+    nnew = 0;
+    for (int s = 0; s < nb; ++s) {
+      P->hmask[s] = hmask[s] ? 1 : 0;
+      nnew += P->hmask[s];
+      if (hmask[s]) CK(cudaMemsetAsync(P->x64 + (size_t)s * n, 0, (size_t)n * sizeof(cx<double>), st));
+    }
+    CK(cudaMemcpyAsync(P->dmask, P->hmask, nb * sizeof(int), cudaMemcpyHostToDevice, st));
+    dmask = P->dmask;
+  } else {
+    CK(cudaMemsetAsync(P->x64, 0, (size_t)nb * n * sizeof(cx<double>), st));
+  }
+  dbar_status s = build_rhs<TI>(P, nb, st, dmask);
+  if (s != DBAR_OK) return s;
+  CK(timed(P, st, K_SCALAR, [&] { return launch_cycle_start(P->cs, P->part2, nblkC, 1, nb, st, dmask); }));
+  if (P->prof.on) {
+    const double F = (double)n * P->inner_elem(), F64 = (double)n * sizeof(cx<double>);
+    P->prof.bytes[K_RHS] += nnew * (4.0 * F64 + F) + (P->M + 2) * F64;
+  }
+  return DBAR_OK;
+}
+
+// One cycle for every active slot (FP64: a restarted GMRES cycle; mixed: an FP32
+// correction cycle, x += d, true residual), ending with the next cycle's start.
+// Launches only; *launched_steps receives the Krylov steps launched.
+template <typename TI>
+static dbar_status one_cycle(dbar_plan* P, int nb, cudaStream_t st, int* launched_steps) {
   const long long n = P->n;
   const int m = P->m;
   const long long vss = (long long)(m + 1) * n;
@@ -515,21 +558,45 @@ static dbar_status run_cycles(dbar_plan* P, int nb, cudaStream_t st) {
   ka.coef = P->coef;
   ka.part = P->part;
   ka.part2 = P->part2;
-  const int nblkC = P->N / make_geo<double>(P->N).lines;
-
-  CK(cudaMemsetAsync(P->x64, 0, (size_t)nb * n * sizeof(cx<double>), st));
-  dbar_status s = build_rhs<TI>(P, nb, st);
-  if (s != DBAR_OK) return s;
-  CK(timed(P, st, K_SCALAR, [&] { return launch_cycle_start(P->cs, P->part2, nblkC, 1, nb, st); }));
-  if (P->prof.on) {
-    const double F = (double)n * P->inner_elem(), F64 = (double)n * sizeof(cx<double>);
-    P->prof.bytes[K_RHS] += nb * (4.0 * F64 + F) + (P->M + 2) * F64;
+  const int nblkC = row_blocks(P->N);
+  int launched = 0;
+  dbar_status s;
+  for (int j = 0; j < m; ++j) {
+    s = apply_K<TI>(P, V + (size_t)j * n, vss, P->cs.sigma + j, m + 1, KS, n, P->cs.run, nb, st);
+    if (s != DBAR_OK) return s;
+    CK(timed(P, st, K_DOTS, [&] { return launch_dots<TI>(ka, V, vss, KS, n, j, nb, st); }));
+    CK(timed(P, st, K_SCALAR, [&] { return launch_finalize_h(ka, P->cs.H, j, nb, st); }));
+    CK(timed(P, st, K_UPDATE, [&] { return launch_update<TI>(ka, V, vss, KS, n, j, nb, st); }));
+    CK(timed(P, st, K_SCALAR, [&] { return launch_givens(ka, P->cs, j, nb, st); }));
+    ++launched;
+    if ((j & 7) == 7 && j + 1 < m) {  // stop launching once every slot has finished its cycle
+      CK(cudaMemcpyAsync(P->h_active, P->cs.run, nb * sizeof(int), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      int anyr = 0;
+      for (int i = 0; i < nb; ++i) anyr |= P->h_active[i];
+      if (!anyr) break;
+    }
   }
+  CK(timed(P, st, K_SCALAR, [&] { return launch_solve_y(P->cs, nb, st); }));
+  CK(cudaMemcpyAsync(P->h_nsteps, P->cs.nsteps, nb * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(timed(P, st, K_XUPDATE, [&] {
+    return launch_xupdate<TI>(n, m + 1, P->cs.nsteps, P->cs.ycoef, V, vss, P->x64, n, nb, st);
+  }));
+  s = true_residual<TI>(P, nb, st);
+  if (s != DBAR_OK) return s;
+  CK(timed(P, st, K_SCALAR, [&] { return launch_cycle_start(P->cs, P->part2, nblkC, 0, nb, st); }));
+  *launched_steps = launched;
+  return DBAR_OK;
+}
 
+template <typename TI>
+static dbar_status run_cycles(dbar_plan* P, int nb, cudaStream_t st) {
+  dbar_status s = begin_slots<TI>(P, nb, nullptr, st);
+  if (s != DBAR_OK) return s;
   std::vector<int> prev_act(nb, 0);
   int prev_launched = 0;
   bool pending_account = false;
-  for (int cyc = 0; cyc < P->p.max_outer; ++cyc) {
+  for (int cyc = 0; cyc <= P->p.max_outer; ++cyc) {
     CK(cudaMemcpyAsync(P->h_active, P->cs.active, nb * sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     P->prof.harvest();
@@ -539,38 +606,9 @@ static dbar_status run_cycles(dbar_plan* P, int nb, cudaStream_t st) {
     for (int i = 0; i < nb; ++i) any |= P->h_active[i];
     if (!any) break;
     std::copy(P->h_active, P->h_active + nb, prev_act.begin());
-    int launched = 0;
-    for (int j = 0; j < m; ++j) {
-      s = apply_K<TI>(P, V + (size_t)j * n, vss, P->cs.sigma + j, m + 1, KS, n, P->cs.run, nb, st);
-      if (s != DBAR_OK) return s;
-      CK(timed(P, st, K_DOTS, [&] { return launch_dots<TI>(ka, V, vss, KS, n, j, nb, st); }));
-      CK(timed(P, st, K_SCALAR, [&] { return launch_finalize_h(ka, P->cs.H, j, nb, st); }));
-      CK(timed(P, st, K_UPDATE, [&] { return launch_update<TI>(ka, V, vss, KS, n, j, nb, st); }));
-      CK(timed(P, st, K_SCALAR, [&] { return launch_givens(ka, P->cs, j, nb, st); }));
-      ++launched;
-      if ((j & 7) == 7 && j + 1 < m) {  // stop launching once every slot has finished its cycle
-        CK(cudaMemcpyAsync(P->h_active, P->cs.run, nb * sizeof(int), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        int anyr = 0;
-        for (int i = 0; i < nb; ++i) anyr |= P->h_active[i];
-        if (!anyr) break;
-      }
-    }
-    CK(timed(P, st, K_SCALAR, [&] { return launch_solve_y(P->cs, nb, st); }));
-    CK(cudaMemcpyAsync(P->h_nsteps, P->cs.nsteps, nb * sizeof(int), cudaMemcpyDeviceToHost, st));
-    CK(timed(P, st, K_XUPDATE, [&] {
-      return launch_xupdate<TI>(n, m + 1, P->cs.nsteps, P->cs.ycoef, V, vss, P->x64, n, nb, st);
-    }));
-    s = true_residual<TI>(P, nb, st);
+    s = one_cycle<TI>(P, nb, st, &prev_launched);
     if (s != DBAR_OK) return s;
-    CK(timed(P, st, K_SCALAR, [&] { return launch_cycle_start(P->cs, P->part2, nblkC, 0, nb, st); }));
     pending_account = true;
-    prev_launched = launched;
-  }
-  if (pending_account) {
-    CK(cudaStreamSynchronize(st));
-    P->prof.harvest();
-    account_cycle(P, prev_act.data(), P->h_nsteps, nb, prev_launched);
   }
   return DBAR_OK;
 }
@@ -711,7 +749,21 @@ static dbar_status plan_tables(dbar_plan* P) {
   return s;
 }
 
-extern "C" dbar_status dbar_plan_create(const dbar_params* p, dbar_plan_t* out) {
+size_t plan_slot_bytes(const dbar_params* p, int per_slot_q) {
+  const size_t n = (size_t)p->N * p->N;
+  const size_t F64 = n * sizeof(cx<double>);
+  const size_t Fi = n * (p->prec == DBAR_MIXED ? sizeof(cx<float>) : sizeof(cx<double>));
+  size_t b = 4 * F64 + (size_t)(p->restart + 2) * Fi;  // x, b, T1, T2; basis, K v
+  if (per_slot_q) b += F64 + n * sizeof(cx<float>) + (p->prec == DBAR_MIXED ? F64 : 0);
+  return b;
+}
+
+size_t plan_fixed_bytes(const dbar_params* p) {
+  const size_t n = (size_t)p->N * p->N;
+  return (size_t)(3 * (p->M + 1) + 4) * n * sizeof(cx<double>);
+}
+
+dbar_status plan_create_ex(const dbar_params* p, int per_slot_q, dbar_plan** out) {
   if (!out) return fail(DBAR_EINVAL, "out is NULL");
   *out = nullptr;
   dbar_status s = check_params(p);
@@ -724,6 +776,7 @@ extern "C" dbar_status dbar_plan_create(const dbar_params* p, dbar_plan_t* out) 
   dbar_plan* P = new (std::nothrow) dbar_plan();
   if (!P) return fail(DBAR_ENOMEM, "host allocation failed");
   P->p = *p;
+  P->per_slot_q = per_slot_q ? 1 : 0;
   P->N = p->N;
   P->logN = 0;
   while ((1 << P->logN) < P->N) ++P->logN;
@@ -743,7 +796,7 @@ extern "C" dbar_status dbar_plan_create(const dbar_params* p, dbar_plan_t* out) 
   const size_t Fi = (size_t)P->n * P->inner_elem();
   const int nchunk = (int)((P->n + KR_CHUNK - 1) / KR_CHUNK);
   const int nblkA = P->N / std::min(make_geo<double>(P->N).lines, make_geo<float>(P->N).lines);
-  const size_t per_slot = 4 * F64 + (size_t)(P->m + 2) * Fi;
+  const size_t per_slot = plan_slot_bytes(p, per_slot_q);
   int B = p->max_batch;
   if (B == 0) {
     size_t freeb = 0, totb = 0;
@@ -771,8 +824,9 @@ extern "C" dbar_status dbar_plan_create(const dbar_params* p, dbar_plan_t* out) 
   AL(P->Da32, (size_t)(P->MA + 1) * P->N);
   AL(P->Delta64, (size_t)(P->M + 1) * n);
   AL(P->Delta32, (size_t)(P->M + 1) * n);
-  AL(P->Q64, n);
-  AL(P->Q32, n);
+  const size_t nq = (size_t)(P->per_slot_q ? B : 1) * n;
+  AL(P->Q64, nq);
+  AL(P->Q32, nq);
   AL(P->Qdev, n);
   AL(P->ex64, (size_t)B * P->N);
   AL(P->ey64, (size_t)B * P->N);
@@ -782,7 +836,7 @@ extern "C" dbar_status dbar_plan_create(const dbar_params* p, dbar_plan_t* out) 
     AL(P->tw_dd, P->N);
     AL(P->Da_dd, (size_t)(P->MA + 1) * P->N);
     AL(P->Delta_dd, (size_t)(P->M + 1) * n);
-    AL(P->Q_dd, n);
+    AL(P->Q_dd, nq);
     AL(P->ex_dd, (size_t)B * P->N);
     AL(P->ey_dd, (size_t)B * P->N);
   }
@@ -822,12 +876,15 @@ extern "C" dbar_status dbar_plan_create(const dbar_params* p, dbar_plan_t* out) 
   AL(c.nsteps, B);
   AL(c.itot, B);
   AL(c.ncyc, B);
+  AL(P->dmask, B);
 #undef AL
   c.m = m;
   c.max_iter = p->max_iter;
+  c.max_outer = p->max_outer;
   c.tol = p->tol;
   c.inner_tol = P->mixed ? p->inner_tol : 0.0;
   if (cudaMallocHost(&P->h_active, (size_t)B * sizeof(int)) != cudaSuccess ||
+      cudaMallocHost(&P->hmask, (size_t)B * sizeof(int)) != cudaSuccess ||
       cudaMallocHost(&P->h_nsteps, (size_t)B * sizeof(int)) != cudaSuccess ||
       cudaMallocHost(&P->h_ek, (size_t)B * 2 * P->N * sizeof(cx<double>)) != cudaSuccess) {
     delete P;
@@ -840,6 +897,10 @@ extern "C" dbar_status dbar_plan_create(const dbar_params* p, dbar_plan_t* out) 
   }
   *out = P;
   return DBAR_OK;
+}
+
+extern "C" dbar_status dbar_plan_create(const dbar_params* p, dbar_plan_t* out) {
+  return plan_create_ex(p, 0, out);
 }
 
 extern "C" dbar_status dbar_plan_destroy(dbar_plan_t plan) {
@@ -1058,6 +1119,77 @@ extern "C" dbar_status dbar_fft2(dbar_plan_t P, int nk, const void* in, void* ou
     CK(sign < 0 ? (launch_pass_b<double, PB_FWD>(a, nk, st)) : (launch_pass_b<double, PB_INV>(a, nk, st)));
   }
   CK(cudaStreamSynchronize(st));
+  return DBAR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Slot-level interface (serving).
+// ---------------------------------------------------------------------------
+int plan_batch(const dbar_plan* P) { return P->B; }
+size_t plan_device_bytes(const dbar_plan* P) { return P->bytes; }
+
+dbar_status plan_load_slot(dbar_plan* P, int slot, const double* Q, double k1, double k2, cudaStream_t st) {
+  if (!P || slot < 0 || slot >= P->B || !Q) return fail(DBAR_EINVAL, "plan_load_slot: bad argument");
+  if (!P->per_slot_q) return fail(DBAR_EINVAL, "plan_load_slot: the plan has one shared potential");
+  const long long n = P->n;
+  const int N = P->N;
+  CK(cudaMemcpyAsync(P->Qdev, Q, n * sizeof(cx<double>), cudaMemcpyHostToDevice, st));
+  CK(timed(P, st, K_OTHER, [&] { return launch_load_q(P->Qdev, P->Q64 + slot * n, P->Q32 + slot * n, N, st); }));
+  if (P->resid_dd)
+    CK(timed(P, st, K_OTHER, [&] { return launch_split_fields(P->Q64 + slot * n, P->Q_dd + slot * n, n, st); }));
+  const double k[2] = {k1, k2};
+  cx<double>* h = P->h_ek + (size_t)slot * 2 * N;
+  fill_ek(P, k, 1, h);
+  CK(cudaMemcpyAsync(P->ex64 + (size_t)slot * N, h, N * sizeof(cx<double>), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(P->ey64 + (size_t)slot * N, h + N, N * sizeof(cx<double>), cudaMemcpyHostToDevice, st));
+  CK(launch_cast_fields(P->ex64 + (size_t)slot * N, P->ex32 + (size_t)slot * N, N, st));
+  CK(launch_cast_fields(P->ey64 + (size_t)slot * N, P->ey32 + (size_t)slot * N, N, st));
+  if (P->resid_dd) {
+    CK(launch_split_fields(P->ex64 + (size_t)slot * N, P->ex_dd + (size_t)slot * N, N, st));
+    CK(launch_split_fields(P->ey64 + (size_t)slot * N, P->ey_dd + (size_t)slot * N, N, st));
+  }
+  return DBAR_OK;
+}
+
+dbar_status plan_begin(dbar_plan* P, int nb, const int* hmask, cudaStream_t st) {
+  if (!P || nb < 0 || nb > P->B) return fail(DBAR_EINVAL, "plan_begin: bad argument");
+  return P->mixed ? begin_slots<float>(P, nb, hmask, st) : begin_slots<double>(P, nb, hmask, st);
+}
+
+dbar_status plan_active(dbar_plan* P, int nb, int* active, cudaStream_t st) {
+  if (!P || nb < 0 || nb > P->B || !active) return fail(DBAR_EINVAL, "plan_active: bad argument");
+  CK(cudaMemcpyAsync(P->h_active, P->cs.active, nb * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  P->prof.harvest();
+  std::copy(P->h_active, P->h_active + nb, active);
+  return DBAR_OK;
+}
+
+dbar_status plan_step(dbar_plan* P, int nb, cudaStream_t st) {
+  if (!P || nb < 0 || nb > P->B) return fail(DBAR_EINVAL, "plan_step: bad argument");
+  int launched = 0;
+  return P->mixed ? one_cycle<float>(P, nb, st, &launched) : one_cycle<double>(P, nb, st, &launched);
+}
+
+dbar_status plan_read_slot(dbar_plan* P, int slot, double* S, double* m, int* itot, int* ncyc, double* resid,
+                           cudaStream_t st) {
+  if (!P || slot < 0 || slot >= P->B || !S) return fail(DBAR_EINVAL, "plan_read_slot: bad argument");
+  const long long n = P->n;
+  CK(cudaMemcpyAsync(S, P->x64 + slot * n, n * sizeof(cx<double>), cudaMemcpyDeviceToHost, st));
+  if (m) {
+    dbar_status s = h_of_S64(P, P->x64 + slot * n, n, reinterpret_cast<cx<double>*>(P->T2), n, 1, st);
+    if (s != DBAR_OK) return s;
+    CK(cudaMemcpyAsync(m, P->T2, n * sizeof(cx<double>), cudaMemcpyDeviceToHost, st));
+  }
+  int it = 0, nc = 0;
+  double rs = 0.0;
+  CK(cudaMemcpyAsync(&it, P->cs.itot + slot, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&nc, P->cs.ncyc + slot, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&rs, P->cs.resid + slot, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (itot) *itot = it;
+  if (ncyc) *ncyc = nc;
+  if (resid) *resid = rs;
   return DBAR_OK;
 }
 

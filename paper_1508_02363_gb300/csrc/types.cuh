@@ -33,7 +33,8 @@ struct PassArgs {
   const cx<T>* Da;       // [MA+1][N]
   const cx<double>* Da64;
   const cx<T>* Delta;    // [M+1][N (y index)][N (x index)]  W_n - V_n
-  const cx<T>* Q;        // [N (y index)][N (x index)]
+  const cx<T>* Q;        // [N (y index)][N (x index)], per slot at stride q_ss (0: shared)
+  long long q_ss;
   const cx<T>* ex;       // [slot][N]  e^{-2 i k2 x_j}
   const cx<T>* ey;       // [slot][N]  e^{-2 i k1 y_j}
   double inv2piL;        // 1/(2 pi L)
@@ -78,6 +79,7 @@ struct CycleState {
   int* ncyc;       // [slot]
   int m;
   int max_iter;
+  int max_outer;
   double tol;
   double inner_tol;  // > 0: mixed-precision inner criterion relative to beta
 };

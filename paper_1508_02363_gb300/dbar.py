@@ -25,7 +25,9 @@ STATUS_NAMES = ["DBAR_OK", "DBAR_EINVAL", "DBAR_ENOMEM", "DBAR_ENOCONV", "DBAR_E
 EXPORTED = ["dbar_params_init", "dbar_last_error", "dbar_plan_create", "dbar_plan_destroy", "dbar_plan_info",
             "dbar_solve_cgo", "dbar_apply", "dbar_rhs", "dbar_m_from_S", "dbar_taylor", "dbar_fft2",
             "dbar_profile_nkinds", "dbar_profile_kind_name", "dbar_profile", "dbar_profile_read",
-            "dbar_launch_count", "dbar_fft2_noalloc"]
+            "dbar_launch_count", "dbar_fft2_noalloc", "dbar_serve_create", "dbar_serve_submit",
+            "dbar_serve_poll", "dbar_serve_wait", "dbar_serve_release", "dbar_serve_stats",
+            "dbar_serve_inject_fault", "dbar_serve_destroy"]
 
 
 class dbar_params(ctypes.Structure):
@@ -33,6 +35,17 @@ class dbar_params(ctypes.Structure):
                 ("restart", ctypes.c_int), ("max_iter", ctypes.c_int), ("tol", ctypes.c_double),
                 ("zero_fill", ctypes.c_int), ("max_batch", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("max_outer", ctypes.c_int), ("resid_mode", ctypes.c_int)]
+
+
+class dbar_request(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("L", ctypes.c_double), ("Q", ctypes.c_void_p), ("k_re", ctypes.c_double),
+                ("k_im", ctypes.c_double), ("want_m", ctypes.c_int)]
+
+
+class dbar_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("cycles", ctypes.c_int),
+                ("resid", ctypes.c_double), ("latency_ms", ctypes.c_double), ("queue_ms", ctypes.c_double),
+                ("run_ms", ctypes.c_double), ("S", ctypes.c_void_p), ("m", ctypes.c_void_p)]
 
 
 class DbarError(RuntimeError):
@@ -62,6 +75,15 @@ _lib.dbar_profile_kind_name.restype = ctypes.c_char_p
 _lib.dbar_profile.argtypes = [_vp, _int]
 _lib.dbar_profile_read.argtypes = [_vp, _int, _dp, ctypes.POINTER(ctypes.c_longlong), _dp]
 _lib.dbar_launch_count.argtypes = [_vp, ctypes.POINTER(ctypes.c_longlong)]
+_u64 = ctypes.c_uint64
+_lib.dbar_serve_create.argtypes = [ctypes.POINTER(dbar_params), ctypes.c_size_t, ctypes.POINTER(_vp)]
+_lib.dbar_serve_submit.argtypes = [_vp, ctypes.POINTER(dbar_request), ctypes.POINTER(_u64)]
+_lib.dbar_serve_poll.argtypes = [_vp, _u64, ctypes.POINTER(dbar_result)]
+_lib.dbar_serve_wait.argtypes = [_vp, _u64, ctypes.c_double, ctypes.POINTER(dbar_result)]
+_lib.dbar_serve_release.argtypes = [_vp, _u64]
+_lib.dbar_serve_stats.argtypes = [_vp, _dp, _dp, _dp, ctypes.POINTER(_u64), ctypes.POINTER(_u64)]
+_lib.dbar_serve_inject_fault.argtypes = [_vp]
+_lib.dbar_serve_destroy.argtypes = [_vp]
 for _f in EXPORTED:
     if _f not in ("dbar_params_init", "dbar_last_error", "dbar_profile_kind_name"):
         getattr(_lib, _f).restype = _int
@@ -248,3 +270,107 @@ class Plan:
         resid = np.zeros(k.size, np.float64)
         st = dbar_solve_cgo(self.handle, Q, k, S_out, m_out, iters, resid, io_on_device=True, stream=stream)
         return {"iters": iters, "resid": resid, "status": st}
+
+
+# ----------------------------------------------------------------------------- serving
+
+def dbar_serve_create(params: dbar_params, mem_budget: int):
+    h = ctypes.c_void_p()
+    _check(_lib.dbar_serve_create(ctypes.byref(params), ctypes.c_size_t(int(mem_budget)), ctypes.byref(h)))
+    return h
+
+
+def dbar_serve_submit(srv, N: int, L: float, Q, k: complex, want_m: bool = False) -> int:
+    Q = np.ascontiguousarray(np.asarray(Q, dtype=np.complex128).reshape(N, N))
+    rq = dbar_request(int(N), float(L), Q.ctypes.data, float(np.real(k)), float(np.imag(k)), int(bool(want_m)))
+    t = ctypes.c_uint64()
+    _check(_lib.dbar_serve_submit(srv, ctypes.byref(rq), ctypes.byref(t)))
+    return t.value
+
+
+def _result_dict(res: dbar_result, N: int):
+    def arr(p):
+        if not p:
+            return None
+        buf = (ctypes.c_double * (2 * N * N)).from_address(p)
+        return np.frombuffer(buf, dtype=np.float64).view(np.complex128).reshape(N, N).copy()
+    return {"status": res.status, "iters": res.iters, "cycles": res.cycles, "resid": res.resid,
+            "latency_ms": res.latency_ms, "queue_ms": res.queue_ms, "run_ms": res.run_ms,
+            "S": arr(res.S), "m": arr(res.m)}
+
+
+def dbar_serve_poll(srv, ticket: int, N: int):
+    res = dbar_result()
+    st = _check(_lib.dbar_serve_poll(srv, ticket, ctypes.byref(res)), (DBAR_OK, DBAR_EBUSY))
+    return None if st == DBAR_EBUSY else _result_dict(res, N)
+
+
+def dbar_serve_wait(srv, ticket: int, N: int, timeout_s: float = -1.0):
+    res = dbar_result()
+    _check(_lib.dbar_serve_wait(srv, ticket, float(timeout_s), ctypes.byref(res)))
+    return _result_dict(res, N)
+
+
+def dbar_serve_release(srv, ticket: int) -> None:
+    _check(_lib.dbar_serve_release(srv, ticket))
+
+
+def dbar_serve_stats(srv) -> dict:
+    p50, p99, rate = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    done, pend = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(_lib.dbar_serve_stats(srv, ctypes.byref(p50), ctypes.byref(p99), ctypes.byref(rate), ctypes.byref(done),
+                                 ctypes.byref(pend)))
+    return {"p50_ms": p50.value, "p99_ms": p99.value, "solves_per_s": rate.value, "completed": done.value,
+            "pending": pend.value}
+
+
+def dbar_serve_inject_fault(srv) -> None:
+    _check(_lib.dbar_serve_inject_fault(srv))
+
+
+def dbar_serve_destroy(srv) -> None:
+    _check(_lib.dbar_serve_destroy(srv))
+
+
+class Server:
+    """Continuous-batching CGO server: Server(mem_budget, **solver params)."""
+
+    def __init__(self, mem_budget: int, **params):
+        self.params = dbar_params_init(64, 1.0, **params)
+        self.handle = dbar_serve_create(self.params, mem_budget)
+        self._N = {}
+
+    def submit(self, N: int, L: float, Q, k: complex, want_m: bool = False) -> int:
+        t = dbar_serve_submit(self.handle, N, L, Q, k, want_m)
+        self._N[t] = N
+        return t
+
+    def poll(self, ticket: int):
+        return dbar_serve_poll(self.handle, ticket, self._N[ticket])
+
+    def wait(self, ticket: int, timeout_s: float = -1.0, release: bool = True):
+        r = dbar_serve_wait(self.handle, ticket, self._N[ticket], timeout_s)
+        if release:
+            self.release(ticket)
+        return r
+
+    def release(self, ticket: int) -> None:
+        dbar_serve_release(self.handle, ticket)
+        self._N.pop(ticket, None)
+
+    def stats(self) -> dict:
+        return dbar_serve_stats(self.handle)
+
+    def inject_fault(self) -> None:
+        dbar_serve_inject_fault(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            dbar_serve_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -126,6 +126,16 @@ def resolved(N: int, L: float, k: complex, xi_q: float) -> bool:
     return N / (2.0 * L) >= 2.0 * max(abs(k.real), abs(k.imag)) + xi_q
 
 
+def mixture_request(seed: int, N: int, L: float, kmax: float, nterms_max: int = 6):
+    """One serving request: a Gaussian mixture of 1..nterms_max terms and a k with
+    |k| log-uniform in [0.1, kmax], both drawn from default_rng(seed)."""
+    rng = np.random.default_rng(seed)
+    nterms = int(rng.integers(1, nterms_max + 1))
+    centres, widths, amps = draw_mixture(rng, nterms)
+    k = np.exp(rng.uniform(np.log(0.1), np.log(kmax))) * np.exp(1j * rng.uniform(0.0, 2.0 * np.pi))
+    return gaussian_mixture(N, L, centres, widths, amps), complex(k)
+
+
 BY_NAME = {
     "plain_fp64": plain_fp64,
     "batched_fp64": batched_fp64,
