@@ -329,6 +329,72 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ----------------------------------------------------------------------------- uneven batch
+
+def run_uneven(args):
+    """1000 mixed-size solves grouped by (N, potential), one plan per N, each group
+    one dbar_solve_cgo call; throughput = solves / summed device time."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1508_02363_gb300 import dbar
+    import workloads as wl
+
+    L = 4.0
+    reqs = wl.uneven_batch(n=args.nreq, L=L)
+    groups = {}
+    for idx, (N, pot, k) in enumerate(reqs):
+        groups.setdefault((N, pot), []).append((idx, k))
+    stream = torch.cuda.current_stream()
+    plans, pots = {}, {}
+    for (N, pot) in groups:
+        if N not in plans:
+            nmax = max(len(v) for (n2, _), v in groups.items() if n2 == N)
+            plans[N] = dbar.Plan(N, L, prec="mixed", restart=args.restart, tol=1e-12, inner_tol=args.inner_tol,
+                                 max_batch=min(nmax, 256 if N <= 1024 else 64), autotune=int(args.autotune))
+            pots[N] = [torch.from_numpy(q).cuda() for q in wl.uneven_potentials(N, L)]
+    outS = {key: torch.empty((len(v), key[0], key[0]), dtype=torch.complex128, device="cuda")
+            for key, v in groups.items()}
+
+    def one_pass():
+        res = {}
+        for (N, pot), v in sorted(groups.items()):
+            k = np.array([kk for _, kk in v])
+            res[(N, pot)] = plans[N].solve_device(pots[N][pot], k, outS[(N, pot)], stream=stream)
+        return res
+
+    for _ in range(args.warmup):
+        one_pass()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            res = one_pass()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    resid = max(float(np.max(r["resid"])) for r in res.values())
+    # error vs the plain FP64 GPU solve on a sample of one request per group
+    errs = []
+    for (N, pot), v in sorted(groups.items()):
+        p64 = dbar.Plan(N, L, prec="fp64", restart=args.restart, tol=1e-13, max_batch=1)
+        ref = p64.solve(pots[N][pot].cpu().numpy(), [v[0][1]], want_m=False)["S"][0]
+        got = outS[(N, pot)][0].cpu().numpy()
+        errs.append(float(np.max(np.abs(got - ref)) / np.max(np.abs(ref))))
+        p64.close()
+    out = {"metric": "uneven batch: CGO solves/sec over mixed grid sizes", "workload": "uneven",
+           "solves": len(reqs), "ms_per_pass": round(ms, 2), "solves_per_s": round(len(reqs) / (ms / 1e3), 2),
+           "resid_max": resid, "err_vs_fp64_max": max(errs), "err_sample": len(errs),
+           "groups": {f"{N}/{'ab'[pot]}": len(v) for (N, pot), v in sorted(groups.items())},
+           "autotune": bool(args.autotune),
+           "tiles": {str(N): dict(zip(("column_variant", "ms_v0", "ms_v1"), dbar.dbar_plan_tuning(p.handle)))
+                     for N, p in sorted(plans.items())},
+           "config": {"L": L, "kmax": 12.0, "restart": args.restart, "inner_tol": args.inner_tol},
+           "clocks": clk.summary()}
+    print(json.dumps(out))
+
+
 # ----------------------------------------------------------------------------- serving workload
 
 def run_serving(args):
@@ -454,6 +520,8 @@ def main():
     ap.add_argument("--duration", type=float, default=60.0, help="serving: seconds of arrivals")
     ap.add_argument("--serve-batch", dest="serve_batch", type=int, default=64, help="serving: slots per lane")
     ap.add_argument("--seed", type=int, default=5)
+    ap.add_argument("--nreq", type=int, default=1000, help="uneven: number of solves")
+    ap.add_argument("--autotune", type=int, default=1, help="uneven: autotuned column-pass tiles")
     ap.add_argument("--quick", action="store_true",
                     help="time the solve only (no FP64 comparison, end-to-end leg or CPU baseline)")
     args = ap.parse_args()
@@ -461,6 +529,8 @@ def main():
         run_reference(args)
     elif args.workload == "serving":
         run_serving(args)
+    elif args.workload == "uneven":
+        run_uneven(args)
     else:
         run_ours(args)
 

@@ -79,13 +79,20 @@ typedef struct {
   int max_outer;     /* cap on cycles (restarts / refinement steps)             */
   int resid_mode;    /* DBAR_MIXED: arithmetic of the right-hand side and of the
                         true residual b - A x (dbar_resid_mode)                 */
+  int graphs;        /* 1: each Krylov cycle is captured once as a CUDA graph
+                        and replayed (default); 0: kernels launched one by one  */
+  int autotune;      /* 1 (default): at plan creation, time the compiled tile
+                        shapes of the FP32 column pass on the plan's own
+                        workspaces and keep the faster (results are identical
+                        across shapes); cached per (device, N, M).
+                        0: first shape; 2: second shape (for checks)           */
 } dbar_params;
 
 typedef struct dbar_plan* dbar_plan_t;
 
 /* Defaults for a grid: M = 2, DBAR_MIXED, restart 32, tol 1e-12,
  * inner_tol 1e-6, max_outer 40, max_iter 4000, analytic fill,
- * DBAR_RESID_DOUBLE_FLOAT. */
+ * DBAR_RESID_DOUBLE_FLOAT, graphs on, autotune on. */
 void dbar_params_init(dbar_params* p, int N, double L);
 
 /* Message describing the calling thread's most recent failure ("" if none). */
@@ -239,6 +246,11 @@ dbar_status dbar_profile(dbar_plan_t plan, int enable);
  * launches, and the algorithmic bytes of those launches (every field the
  * method reads or writes counted once per use).  Any pointer may be NULL. */
 dbar_status dbar_profile_read(dbar_plan_t plan, int kind, double* ms, long long* launches, double* bytes);
+
+/* The autotuner's choice: column-pass tile variant in use (0: 64-byte row
+ * segments, 512 threads; 1: 32-byte segments, 256 threads) and the measured ms
+ * per launch of each (0 when not tuned).  Any pointer may be NULL. */
+dbar_status dbar_plan_tuning(dbar_plan_t plan, int* column_variant, double* ms_variant0, double* ms_variant1);
 
 /* Kernels launched by this plan since its creation (profiling on or off). */
 dbar_status dbar_launch_count(dbar_plan_t plan, long long* count);

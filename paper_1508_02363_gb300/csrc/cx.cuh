@@ -298,7 +298,9 @@ __device__ __forceinline__ void fft_line(cx<T> (&v)[16], cx<T>* line, int t, con
 __host__ __device__ constexpr int row_lines(int logN) {
   return (256 / ((1 << logN) / 16)) < (1 << logN) ? (256 / ((1 << logN) / 16)) : (1 << logN);
 }
-// Column-pass shape knobs (bytes of one row segment a warp reads, threads per block).
+// Column-pass tile shapes.  Variant 0: a warp reads DBAR_COL_SEG_BYTES-byte row
+// segments, DBAR_COL_THREADS_F32 / _F64 threads per block.  Variant 1: 32-byte
+// segments and 256 threads.  Plans pick one per grid size by timing (autotune).
 #ifndef DBAR_COL_SEG_BYTES
 #define DBAR_COL_SEG_BYTES 64
 #endif
@@ -308,20 +310,25 @@ __host__ __device__ constexpr int row_lines(int logN) {
 #ifndef DBAR_COL_THREADS_F64
 #define DBAR_COL_THREADS_F64 256
 #endif
-__host__ __device__ constexpr int col_threads(int esz) { return esz == 8 ? DBAR_COL_THREADS_F32 : DBAR_COL_THREADS_F64; }
-__host__ __device__ constexpr int col_cap(int logN, int esz) {
-  return col_threads(esz) / ((1 << logN) / 16) > 0 ? col_threads(esz) / ((1 << logN) / 16) : 1;
+__host__ __device__ constexpr int col_threads(int esz, int cv = 0) {
+  return cv ? 256 : (esz == 8 ? DBAR_COL_THREADS_F32 : DBAR_COL_THREADS_F64);
 }
-__host__ __device__ constexpr int col_cwd(int esz) { return DBAR_COL_SEG_BYTES / esz > 0 ? DBAR_COL_SEG_BYTES / esz : 1; }
-__host__ __device__ constexpr int col_cw(int logN, int esz) {
-  // row segments of DBAR_COL_SEG_BYTES when possible; small N: one warp spans all t of CW columns
-  return ((1 << logN) / 16 >= 32 / col_cwd(esz))
-             ? (col_cwd(esz) < col_cap(logN, esz) ? col_cwd(esz) : col_cap(logN, esz))
+__host__ __device__ constexpr int col_cap(int logN, int esz, int cv = 0) {
+  return col_threads(esz, cv) / ((1 << logN) / 16) > 0 ? col_threads(esz, cv) / ((1 << logN) / 16) : 1;
+}
+__host__ __device__ constexpr int col_cwd(int esz, int cv = 0) {
+  return (cv ? 32 : DBAR_COL_SEG_BYTES) / esz > 0 ? (cv ? 32 : DBAR_COL_SEG_BYTES) / esz : 1;
+}
+__host__ __device__ constexpr int col_cw(int logN, int esz, int cv = 0) {
+  // row segments of the variant's width when possible; small N: one warp spans all t of CW columns
+  return ((1 << logN) / 16 >= 32 / col_cwd(esz, cv))
+             ? (col_cwd(esz, cv) < col_cap(logN, esz, cv) ? col_cwd(esz, cv) : col_cap(logN, esz, cv))
              : 32 / ((1 << logN) / 16);
 }
-__host__ __device__ constexpr int col_cols(int logN, int esz) {
-  return (col_cap(logN, esz) > col_cw(logN, esz) ? col_cap(logN, esz) : col_cw(logN, esz)) < (1 << logN)
-             ? (col_cap(logN, esz) > col_cw(logN, esz) ? col_cap(logN, esz) : col_cw(logN, esz))
+__host__ __device__ constexpr int col_cols(int logN, int esz, int cv = 0) {
+  return (col_cap(logN, esz, cv) > col_cw(logN, esz, cv) ? col_cap(logN, esz, cv) : col_cw(logN, esz, cv)) <
+                 (1 << logN)
+             ? (col_cap(logN, esz, cv) > col_cw(logN, esz, cv) ? col_cap(logN, esz, cv) : col_cw(logN, esz, cv))
              : (1 << logN);
 }
 

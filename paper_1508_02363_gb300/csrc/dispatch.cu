@@ -1,4 +1,6 @@
 // Size dispatch: maps the run-time grid size onto the per-size launchers.
+#include <type_traits>
+
 #include "launch.cuh"
 
 namespace dbar {
@@ -20,9 +22,20 @@ cudaError_t launch_pass_a(const PassArgs<T>& a, int nslots, cudaStream_t s) {
 template <typename T, int MODE>
 cudaError_t launch_pass_b(const PassArgs<T>& a, int nslots, cudaStream_t s) {
   if (nslots <= 0) return cudaSuccess;
+  if constexpr (std::is_same<T, float>::value && MODE == PB_MATVEC) {
+    if (a.colv == 1) {
+      switch (a.g.logN) {
+#define CASE(L) \
+  case L: return launch_pass_b_n<T, L, MODE, 1>(a, nslots, s);
+        DBAR_SIZES(CASE)
+#undef CASE
+      }
+      return cudaErrorInvalidValue;
+    }
+  }
   switch (a.g.logN) {
 #define CASE(L) \
-  case L: return launch_pass_b_n<T, L, MODE>(a, nslots, s);
+  case L: return launch_pass_b_n<T, L, MODE, 0>(a, nslots, s);
     DBAR_SIZES(CASE)
 #undef CASE
   }

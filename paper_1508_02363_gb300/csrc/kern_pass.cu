@@ -37,13 +37,13 @@ cudaError_t launch_pass_a_n(const PassArgs<T>& a, int nslots, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <typename T, int LOGN, int MODE>
+template <typename T, int LOGN, int MODE, int CV>
 cudaError_t launch_pass_b_n(const PassArgs<T>& a, int nslots, cudaStream_t s) {
-  using G = ColG<T, LOGN>;
+  using G = ColG<T, LOGN, CV>;
   const size_t sm = align16((size_t)G::COLS * G::P * sizeof(cx<T>)) + (size_t)(a.M + 2) * sizeof(cx<T>);
-  cudaError_t e = set_smem(k_pass_b<T, LOGN, MODE>, sm);
+  cudaError_t e = set_smem(k_pass_b<T, LOGN, MODE, CV>, sm);
   if (e != cudaSuccess) return e;
-  k_pass_b<T, LOGN, MODE><<<dim3(G::N / G::COLS, nslots), G::THREADS, sm, s>>>(a);
+  k_pass_b<T, LOGN, MODE, CV><<<dim3(G::N / G::COLS, nslots), G::THREADS, sm, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -61,20 +61,23 @@ typedef DBAR_T TT;
 #if DBAR_KIND == 2
 // double-float: the right-hand side and the true residual of the refinement
 template cudaError_t launch_pass_a_n<dd, DBAR_LOGN, true>(const PassArgs<dd>&, int, cudaStream_t);
-template cudaError_t launch_pass_b_n<dd, DBAR_LOGN, PB_MATVEC>(const PassArgs<dd>&, int, cudaStream_t);
-template cudaError_t launch_pass_b_n<dd, DBAR_LOGN, PB_RHS>(const PassArgs<dd>&, int, cudaStream_t);
+template cudaError_t launch_pass_b_n<dd, DBAR_LOGN, PB_MATVEC, 0>(const PassArgs<dd>&, int, cudaStream_t);
+template cudaError_t launch_pass_b_n<dd, DBAR_LOGN, PB_RHS, 0>(const PassArgs<dd>&, int, cudaStream_t);
 template cudaError_t launch_pass_c_n<dd, float, DBAR_LOGN, PC_RHS>(const PassArgs<dd>&, int, cudaStream_t);
 template cudaError_t launch_pass_c_n<dd, float, DBAR_LOGN, PC_RES>(const PassArgs<dd>&, int, cudaStream_t);
 #else
 template cudaError_t launch_pass_a_n<TT, DBAR_LOGN, false>(const PassArgs<TT>&, int, cudaStream_t);
-template cudaError_t launch_pass_b_n<TT, DBAR_LOGN, PB_MATVEC>(const PassArgs<TT>&, int, cudaStream_t);
-template cudaError_t launch_pass_b_n<TT, DBAR_LOGN, PB_RHS>(const PassArgs<TT>&, int, cudaStream_t);
-template cudaError_t launch_pass_b_n<TT, DBAR_LOGN, PB_HOUT>(const PassArgs<TT>&, int, cudaStream_t);
-template cudaError_t launch_pass_b_n<TT, DBAR_LOGN, PB_FWD>(const PassArgs<TT>&, int, cudaStream_t);
-template cudaError_t launch_pass_b_n<TT, DBAR_LOGN, PB_INV>(const PassArgs<TT>&, int, cudaStream_t);
+template cudaError_t launch_pass_b_n<TT, DBAR_LOGN, PB_MATVEC, 0>(const PassArgs<TT>&, int, cudaStream_t);
+template cudaError_t launch_pass_b_n<TT, DBAR_LOGN, PB_RHS, 0>(const PassArgs<TT>&, int, cudaStream_t);
+template cudaError_t launch_pass_b_n<TT, DBAR_LOGN, PB_HOUT, 0>(const PassArgs<TT>&, int, cudaStream_t);
+template cudaError_t launch_pass_b_n<TT, DBAR_LOGN, PB_FWD, 0>(const PassArgs<TT>&, int, cudaStream_t);
+template cudaError_t launch_pass_b_n<TT, DBAR_LOGN, PB_INV, 0>(const PassArgs<TT>&, int, cudaStream_t);
 template cudaError_t launch_pass_c_n<TT, TT, DBAR_LOGN, PC_KS>(const PassArgs<TT>&, int, cudaStream_t);
 template cudaError_t launch_pass_c_n<TT, TT, DBAR_LOGN, PC_FWD>(const PassArgs<TT>&, int, cudaStream_t);
 template cudaError_t launch_pass_c_n<TT, TT, DBAR_LOGN, PC_INV>(const PassArgs<TT>&, int, cudaStream_t);
+#if DBAR_KIND == 0
+template cudaError_t launch_pass_b_n<float, DBAR_LOGN, PB_MATVEC, 1>(const PassArgs<float>&, int, cudaStream_t);
+#endif
 #if DBAR_KIND == 1
 template cudaError_t launch_pass_c_n<double, double, DBAR_LOGN, PC_RHS>(const PassArgs<double>&, int, cudaStream_t);
 template cudaError_t launch_pass_c_n<double, float, DBAR_LOGN, PC_RHS>(const PassArgs<double>&, int, cudaStream_t);

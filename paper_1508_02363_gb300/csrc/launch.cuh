@@ -37,7 +37,7 @@ inline int row_blocks(int N) { return N / row_lines(ilog2(N)); }
 // per-size launchers (kern_pass.cu, one translation unit per precision and size)
 template <typename T, int LOGN, bool IN64>
 cudaError_t launch_pass_a_n(const PassArgs<T>& a, int nslots, cudaStream_t s);
-template <typename T, int LOGN, int MODE>
+template <typename T, int LOGN, int MODE, int CV>
 cudaError_t launch_pass_b_n(const PassArgs<T>& a, int nslots, cudaStream_t s);
 template <typename T, typename TO, int LOGN, int MODE>
 cudaError_t launch_pass_c_n(const PassArgs<T>& a, int nslots, cudaStream_t s);

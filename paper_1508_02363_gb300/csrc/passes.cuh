@@ -64,11 +64,11 @@ struct RowG {
   static constexpr int P = pitch_of(N);
   static constexpr int MINB = sizeof(T) == 4 ? 4 : 2;
 };
-template <typename T, int LOGN>
+template <typename T, int LOGN, int CV = 0>
 struct ColG {
   static constexpr int N = 1 << LOGN, TPL = N / 16;
-  static constexpr int CW = col_cw(LOGN, (int)sizeof(cx<T>)), TW = 32 / CW;
-  static constexpr int COLS = col_cols(LOGN, (int)sizeof(cx<T>)), THREADS = COLS * TPL;
+  static constexpr int CW = col_cw(LOGN, (int)sizeof(cx<T>), CV), TW = 32 / CW;
+  static constexpr int COLS = col_cols(LOGN, (int)sizeof(cx<T>), CV), THREADS = COLS * TPL;
   static constexpr int WPG = TPL / TW;  // warps per group of CW columns
   static constexpr int P = pitch_of(N);
   static constexpr int MINB = 2;
@@ -189,9 +189,9 @@ __global__ void __launch_bounds__(RowG<T, LOGN>::THREADS, RowG<T, LOGN>::MINB) k
 // neighbouring columns x TW consecutive t, so the 16 loads and stores of each
 // thread (rows t + q TPL of column j1) are coalesced row segments.
 // ---------------------------------------------------------------------------
-template <typename T, int LOGN, int MODE>
-__global__ void __launch_bounds__(ColG<T, LOGN>::THREADS, ColG<T, LOGN>::MINB) k_pass_b(const PassArgs<T> a) {
-  using G = ColG<T, LOGN>;
+template <typename T, int LOGN, int MODE, int CV>
+__global__ void __launch_bounds__(ColG<T, LOGN, CV>::THREADS, ColG<T, LOGN, CV>::MINB) k_pass_b(const PassArgs<T> a) {
+  using G = ColG<T, LOGN, CV>;
   constexpr int N = G::N, TPL = G::TPL, P = G::P;
   extern __shared__ __align__(16) unsigned char smem[];
   const int slot = blockIdx.y;

@@ -12,6 +12,9 @@
 #include <algorithm>
 #include <cmath>
 #include <complex>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -100,10 +103,42 @@ struct Profiler {
   }
 };
 
+// A Krylov cycle as CUDA graphs: one graph per chunk of kGraphChunk steps and
+// one for the cycle's tail (solution update, true residual, next start).
+constexpr int kGraphChunk = 8;
+struct GraphPart {
+  cudaGraphExec_t exec = nullptr;
+  int kernels = 0;                      // kernel nodes per replay
+  std::vector<Profiler::Rec> recs;      // event-record pairs captured with the kernels
+};
+struct CycleGraph {
+  int nb = -1;
+  bool prof = false;
+  std::vector<GraphPart> parts;         // chunks 0..nchunks-1, then the tail
+  void clear() {
+    for (GraphPart& g : parts) {
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+      for (const Profiler::Rec& r : g.recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+      }
+    }
+    parts.clear();
+    nb = -1;
+  }
+};
+
 struct dbar_plan {
   dbar_params p;
   Profiler prof;
+  cudaStream_t cap_stream = nullptr;    // stream the cycle graphs are captured on
+  bool capturing = false;
+  GraphPart* cap = nullptr;             // graph part being captured
+  std::vector<GraphPart*> graph_ran;    // parts replayed since the last profile harvest
+  CycleGraph graphs[2];                 // one per batch size in use (full and ragged)
   int per_slot_q = 0;   // 1: every slot has its own potential (serving); 0: one Q for all
+  int colv = 0;         // FP32 column-pass tile variant (autotuned)
+  double tune_ms[2] = {0.0, 0.0};
   int* dmask = nullptr;  // [B] device copy of a slot mask
   int* hmask = nullptr;  // [B] pinned host staging of it
   long long nlaunch = 0;  // kernels launched by this plan
@@ -171,6 +206,8 @@ struct dbar_plan {
     int cur = 0;
     cudaGetDevice(&cur);
     cudaSetDevice(device);
+    for (CycleGraph& g : graphs) g.clear();
+    if (cap_stream) cudaStreamDestroy(cap_stream);
     for (void* q : allocs) cudaFree(q);
     if (h_active) cudaFreeHost(h_active);
     if (h_nsteps) cudaFreeHost(h_nsteps);
@@ -196,6 +233,8 @@ extern "C" void dbar_params_init(dbar_params* p, int N, double L) {
   p->inner_tol = 1e-6;
   p->max_outer = 40;
   p->resid_mode = DBAR_RESID_DOUBLE_FLOAT;
+  p->graphs = 1;
+  p->autotune = 1;
 }
 
 extern "C" const char* dbar_last_error(void) { return g_last_error.c_str(); }
@@ -247,6 +286,18 @@ static double xgrid(int j, int N, double L) { return L * (-M_PI + 2.0 * M_PI * (
 // brackets it with CUDA events on the launching stream.
 template <typename F>
 static cudaError_t timed(dbar_plan* P, cudaStream_t st, int kind, F&& f) {
+  if (P->capturing) {  // recorded into the cycle graph: counted and timed at each replay
+    P->cap->kernels += 1;
+    if (!P->prof.on) return f();
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecordWithFlags(a, st, cudaEventRecordExternal);  // a node that records at each replay
+    cudaError_t e = f();
+    cudaEventRecordWithFlags(b, st, cudaEventRecordExternal);
+    P->cap->recs.push_back({kind, a, b});
+    return e;
+  }
   ++P->nlaunch;
   if (!P->prof.on) return f();
   cudaEvent_t a = P->prof.get(), b = P->prof.get();
@@ -319,6 +370,7 @@ template <>
 PassArgs<float> base_args<float>(const dbar_plan* P) {
   PassArgs<float> a;
   std::memset(&a, 0, sizeof(a));
+  a.colv = P->colv;
   a.g = make_geo<float>(P->N);
   a.M = P->M;
   a.tw = P->tw32;
@@ -539,11 +591,9 @@ static dbar_status begin_slots(dbar_plan* P, int nb, const int* hmask, cudaStrea
   return DBAR_OK;
 }
 
-// One cycle for every active slot (FP64: a restarted GMRES cycle; mixed: an FP32
-// correction cycle, x += d, true residual), ending with the next cycle's start.
-// Launches only; *launched_steps receives the Krylov steps launched.
+// Krylov steps j0 <= j < j1 of the current cycle for every running slot.
 template <typename TI>
-static dbar_status one_cycle(dbar_plan* P, int nb, cudaStream_t st, int* launched_steps) {
+static dbar_status cycle_steps(dbar_plan* P, int nb, int j0, int j1, cudaStream_t st) {
   const long long n = P->n;
   const int m = P->m;
   const long long vss = (long long)(m + 1) * n;
@@ -558,35 +608,140 @@ static dbar_status one_cycle(dbar_plan* P, int nb, cudaStream_t st, int* launche
   ka.coef = P->coef;
   ka.part = P->part;
   ka.part2 = P->part2;
-  const int nblkC = row_blocks(P->N);
-  int launched = 0;
-  dbar_status s;
-  for (int j = 0; j < m; ++j) {
-    s = apply_K<TI>(P, V + (size_t)j * n, vss, P->cs.sigma + j, m + 1, KS, n, P->cs.run, nb, st);
+  for (int j = j0; j < j1; ++j) {
+    dbar_status s = apply_K<TI>(P, V + (size_t)j * n, vss, P->cs.sigma + j, m + 1, KS, n, P->cs.run, nb, st);
     if (s != DBAR_OK) return s;
     CK(timed(P, st, K_DOTS, [&] { return launch_dots<TI>(ka, V, vss, KS, n, j, nb, st); }));
     CK(timed(P, st, K_SCALAR, [&] { return launch_finalize_h(ka, P->cs.H, j, nb, st); }));
     CK(timed(P, st, K_UPDATE, [&] { return launch_update<TI>(ka, V, vss, KS, n, j, nb, st); }));
     CK(timed(P, st, K_SCALAR, [&] { return launch_givens(ka, P->cs, j, nb, st); }));
-    ++launched;
-    if ((j & 7) == 7 && j + 1 < m) {  // stop launching once every slot has finished its cycle
-      CK(cudaMemcpyAsync(P->h_active, P->cs.run, nb * sizeof(int), cudaMemcpyDeviceToHost, st));
-      CK(cudaStreamSynchronize(st));
-      int anyr = 0;
-      for (int i = 0; i < nb; ++i) anyr |= P->h_active[i];
-      if (!anyr) break;
-    }
   }
+  return DBAR_OK;
+}
+
+// End of a cycle: y, x += V y, true residual, start of the next cycle.
+template <typename TI>
+static dbar_status cycle_tail(dbar_plan* P, int nb, cudaStream_t st) {
+  const long long n = P->n;
+  const int m = P->m;
+  const long long vss = (long long)(m + 1) * n;
+  cx<TI>* V = reinterpret_cast<cx<TI>*>(P->V);
   CK(timed(P, st, K_SCALAR, [&] { return launch_solve_y(P->cs, nb, st); }));
   CK(cudaMemcpyAsync(P->h_nsteps, P->cs.nsteps, nb * sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(timed(P, st, K_XUPDATE, [&] {
     return launch_xupdate<TI>(n, m + 1, P->cs.nsteps, P->cs.ycoef, V, vss, P->x64, n, nb, st);
   }));
-  s = true_residual<TI>(P, nb, st);
+  dbar_status s = true_residual<TI>(P, nb, st);
   if (s != DBAR_OK) return s;
-  CK(timed(P, st, K_SCALAR, [&] { return launch_cycle_start(P->cs, P->part2, nblkC, 0, nb, st); }));
+  CK(timed(P, st, K_SCALAR, [&] { return launch_cycle_start(P->cs, P->part2, row_blocks(P->N), 0, nb, st); }));
+  return DBAR_OK;
+}
+
+// true when some slot's cycle is still running (synchronises the stream)
+static bool any_running(dbar_plan* P, int nb, cudaStream_t st) {
+  if (cudaMemcpyAsync(P->h_active, P->cs.run, nb * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return true;
+  int any = 0;
+  for (int i = 0; i < nb; ++i) any |= P->h_active[i];
+  return any != 0;
+}
+
+// One cycle for every active slot (FP64: a restarted GMRES cycle; mixed: an FP32
+// correction cycle, x += d, true residual), ending with the next cycle's start.
+// Between chunks of kGraphChunk steps the host stops launching once every slot
+// has finished its cycle.  *launched_steps receives the Krylov steps launched.
+template <typename TI>
+static dbar_status one_cycle(dbar_plan* P, int nb, cudaStream_t st, int* launched_steps) {
+  int j0 = 0;
+  while (j0 < P->m) {
+    const int j1 = std::min(P->m, j0 + kGraphChunk);
+    dbar_status s = cycle_steps<TI>(P, nb, j0, j1, st);
+    if (s != DBAR_OK) return s;
+    j0 = j1;
+    if (j0 < P->m && !any_running(P, nb, st)) break;
+  }
+  *launched_steps = j0;
+  return cycle_tail<TI>(P, nb, st);
+}
+
+// One cycle as CUDA graphs: each chunk of kGraphChunk Krylov steps and the
+// cycle's tail are captured once per batch size (and profiling state) on the
+// plan's capture stream, then replayed on the caller's stream, with the same
+// host check between chunks as the direct launches.
+template <typename TI, typename F>
+static dbar_status capture_part(dbar_plan* P, GraphPart* g, F&& body) {
+  if (!P->cap_stream) CK(cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking));
+  CK(cudaStreamBeginCapture(P->cap_stream, cudaStreamCaptureModeRelaxed));
+  P->capturing = true;
+  P->cap = g;
+  dbar_status s = body(P->cap_stream);
+  P->capturing = false;
+  P->cap = nullptr;
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(P->cap_stream, &graph);
+  if (s != DBAR_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return s;
+  }
+  if (e != cudaSuccess) return fail(DBAR_ECUDA, std::string("cycle capture: ") + cudaGetErrorString(e));
+  const cudaError_t e2 = cudaGraphInstantiate(&g->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e2 != cudaSuccess) return fail(DBAR_ECUDA, std::string("cycle graph: ") + cudaGetErrorString(e2));
+  return DBAR_OK;
+}
+
+template <typename TI>
+static dbar_status graph_cycle(dbar_plan* P, int nb, cudaStream_t st, int* launched_steps) {
+  CycleGraph* g = nullptr;
+  for (CycleGraph& c : P->graphs)
+    if (!c.parts.empty() && c.nb == nb && c.prof == P->prof.on) g = &c;
+  const int nchunks = (P->m + kGraphChunk - 1) / kGraphChunk;
+  if (!g) {
+    g = (P->graphs[0].nb == nb || P->graphs[0].parts.empty()) ? &P->graphs[0] : &P->graphs[1];
+    g->clear();
+    g->parts.resize(nchunks + 1);
+    for (int c = 0; c <= nchunks; ++c) {
+      dbar_status s = (c < nchunks)
+          ? capture_part<TI>(P, &g->parts[c], [&](cudaStream_t cs) {
+              return cycle_steps<TI>(P, nb, c * kGraphChunk, std::min(P->m, (c + 1) * kGraphChunk), cs);
+            })
+          : capture_part<TI>(P, &g->parts[c], [&](cudaStream_t cs) { return cycle_tail<TI>(P, nb, cs); });
+      if (s != DBAR_OK) {
+        g->clear();
+        return s;
+      }
+    }
+    g->nb = nb;
+    g->prof = P->prof.on;
+  }
+  int launched = 0;
+  for (int c = 0; c < nchunks; ++c) {
+    CK(cudaGraphLaunch(g->parts[c].exec, st));
+    P->nlaunch += g->parts[c].kernels;
+    launched = std::min(P->m, (c + 1) * kGraphChunk);
+    if (P->prof.on) P->graph_ran.push_back(&g->parts[c]);
+    if (c + 1 < nchunks && !any_running(P, nb, st)) break;
+  }
+  CK(cudaGraphLaunch(g->parts[nchunks].exec, st));
+  P->nlaunch += g->parts[nchunks].kernels;
+  if (P->prof.on) P->graph_ran.push_back(&g->parts[nchunks]);
   *launched_steps = launched;
   return DBAR_OK;
+}
+
+// after the graph parts replayed since the last call have completed: fold their
+// event pairs into the profile (a part's events are re-recorded at each replay,
+// so they are read before the part runs again)
+static void harvest_graph(dbar_plan* P) {
+  for (GraphPart* g : P->graph_ran)
+    for (const Profiler::Rec& r : g->recs) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) P->prof.ms[r.kind] += t;
+      P->prof.launches[r.kind] += 1;
+    }
+  P->graph_ran.clear();
+  cudaGetLastError();
 }
 
 template <typename TI>
@@ -600,13 +755,16 @@ static dbar_status run_cycles(dbar_plan* P, int nb, cudaStream_t st) {
     CK(cudaMemcpyAsync(P->h_active, P->cs.active, nb * sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     P->prof.harvest();
-    if (pending_account) account_cycle(P, prev_act.data(), P->h_nsteps, nb, prev_launched);
+    if (pending_account) {
+      if (P->p.graphs) harvest_graph(P);
+      account_cycle(P, prev_act.data(), P->h_nsteps, nb, prev_launched);
+    }
     pending_account = false;
     int any = 0;
     for (int i = 0; i < nb; ++i) any |= P->h_active[i];
     if (!any) break;
     std::copy(P->h_active, P->h_active + nb, prev_act.begin());
-    s = one_cycle<TI>(P, nb, st, &prev_launched);
+    s = P->p.graphs ? graph_cycle<TI>(P, nb, st, &prev_launched) : one_cycle<TI>(P, nb, st, &prev_launched);
     if (s != DBAR_OK) return s;
     pending_account = true;
   }
@@ -630,6 +788,7 @@ static dbar_status check_params(const dbar_params* p) {
   if (p->prec == DBAR_MIXED && !(p->inner_tol > 0.0 && p->inner_tol < 1.0))
     return fail(DBAR_EINVAL, "inner_tol must be in (0, 1)");
   if (p->max_batch < 0 || p->max_batch > 65535) return fail(DBAR_EINVAL, "max_batch must be in [0, 65535]");
+  if (p->autotune < 0 || p->autotune > 2) return fail(DBAR_EINVAL, "autotune must be 0, 1 or 2");
   if (p->resid_mode != DBAR_RESID_DOUBLE_FLOAT && p->resid_mode != DBAR_RESID_FP64)
     return fail(DBAR_EINVAL, "resid_mode must be DBAR_RESID_DOUBLE_FLOAT or DBAR_RESID_FP64");
   return DBAR_OK;
@@ -747,6 +906,67 @@ static dbar_status plan_tables(dbar_plan* P) {
   cudaFree(dE);
   cudaFree(dW);
   return s;
+}
+
+// Column-pass tile autotuner: times each compiled variant of the FP32 column
+// pass on this plan's own workspaces and keeps the faster one.  Results are
+// bit-identical across variants (same arithmetic per column), so the choice
+// only affects speed; it is cached per (device, N, M) for the process.
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int>, std::pair<int, std::pair<double, double>>> g_tune_cache;
+
+static dbar_status autotune_columns(dbar_plan* P) {
+  const auto key = std::make_tuple(P->device, P->N, P->M);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      P->colv = it->second.first;
+      P->tune_ms[0] = it->second.second.first;
+      P->tune_ms[1] = it->second.second.second;
+      return DBAR_OK;
+    }
+  }
+  cudaStream_t st = 0;
+  const int nb = std::min(P->B, 16);
+  const size_t n = (size_t)P->n;
+  CK(cudaMemset(P->T1, 0, (size_t)nb * n * sizeof(cx<float>)));
+  CK(cudaMemset(P->tcoef, 0, (size_t)nb * (P->M + 2) * sizeof(cx<double>)));
+  CK(cudaMemset(P->Q32, 0, n * sizeof(cx<float>)));
+  CK(cudaMemset(P->ex32, 0, (size_t)nb * P->N * sizeof(cx<float>)));
+  CK(cudaMemset(P->ey32, 0, (size_t)nb * P->N * sizeof(cx<float>)));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  double best = 1e300;
+  int choice = 0;
+  for (int cv = 0; cv < 2; ++cv) {
+    PassArgs<float> a = base_args<float>(P);
+    a.colv = cv;
+    a.in = reinterpret_cast<const cx<float>*>(P->T1);
+    a.in_ss = (long long)n;
+    a.out = P->T2;
+    a.out_ss = (long long)n;
+    for (int w = 0; w < 2; ++w) CK((launch_pass_b<float, PB_MATVEC>(a, nb, st)));
+    CK(cudaEventRecord(e0, st));
+    const int reps = 5;
+    for (int r = 0; r < reps; ++r) CK((launch_pass_b<float, PB_MATVEC>(a, nb, st)));
+    CK(cudaEventRecord(e1, st));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    P->tune_ms[cv] = ms / reps;
+    if (ms < best) {
+      best = ms;
+      choice = cv;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  P->colv = choice;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[key] = {choice, {P->tune_ms[0], P->tune_ms[1]}};
+  return DBAR_OK;
 }
 
 size_t plan_slot_bytes(const dbar_params* p, int per_slot_q) {
@@ -891,6 +1111,8 @@ dbar_status plan_create_ex(const dbar_params* p, int per_slot_q, dbar_plan** out
     return fail(DBAR_ENOMEM, "pinned host allocation failed");
   }
   s = plan_tables(P);
+  if (s == DBAR_OK && P->mixed && p->autotune == 1) s = autotune_columns(P);
+  if (P->mixed && p->autotune == 2) P->colv = 1;  // fixed second variant (tests)
   if (s != DBAR_OK) {
     delete P;
     return s;
@@ -1216,6 +1438,15 @@ extern "C" dbar_status dbar_profile_read(dbar_plan_t P, int kind, double* ms, lo
   if (ms) *ms = P->prof.ms[kind];
   if (launches) *launches = P->prof.launches[kind];
   if (bytes) *bytes = P->prof.bytes[kind];
+  return DBAR_OK;
+}
+
+extern "C" dbar_status dbar_plan_tuning(dbar_plan_t P, int* column_variant, double* ms_variant0,
+                                        double* ms_variant1) {
+  if (!P) return fail(DBAR_EINVAL, "plan is NULL");
+  if (column_variant) *column_variant = P->colv;
+  if (ms_variant0) *ms_variant0 = P->tune_ms[0];
+  if (ms_variant1) *ms_variant1 = P->tune_ms[1];
   return DBAR_OK;
 }
 

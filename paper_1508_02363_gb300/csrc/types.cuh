@@ -11,6 +11,7 @@ struct Geo {
 template <typename T>
 struct PassArgs {
   Geo g;
+  int colv;  // column-pass tile variant (autotuned)
   int M;  // Taylor order
   // input field (T), per-slot stride in complex elements; optional per-slot scale
   const cx<T>* in;

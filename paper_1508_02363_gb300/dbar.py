@@ -27,14 +27,15 @@ EXPORTED = ["dbar_params_init", "dbar_last_error", "dbar_plan_create", "dbar_pla
             "dbar_profile_nkinds", "dbar_profile_kind_name", "dbar_profile", "dbar_profile_read",
             "dbar_launch_count", "dbar_fft2_noalloc", "dbar_serve_create", "dbar_serve_submit",
             "dbar_serve_poll", "dbar_serve_wait", "dbar_serve_release", "dbar_serve_stats",
-            "dbar_serve_inject_fault", "dbar_serve_destroy"]
+            "dbar_serve_inject_fault", "dbar_serve_destroy", "dbar_plan_tuning"]
 
 
 class dbar_params(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int), ("L", ctypes.c_double), ("M", ctypes.c_int), ("prec", ctypes.c_int),
                 ("restart", ctypes.c_int), ("max_iter", ctypes.c_int), ("tol", ctypes.c_double),
                 ("zero_fill", ctypes.c_int), ("max_batch", ctypes.c_int), ("inner_tol", ctypes.c_double),
-                ("max_outer", ctypes.c_int), ("resid_mode", ctypes.c_int)]
+                ("max_outer", ctypes.c_int), ("resid_mode", ctypes.c_int), ("graphs", ctypes.c_int),
+                ("autotune", ctypes.c_int)]
 
 
 class dbar_request(ctypes.Structure):
@@ -75,6 +76,7 @@ _lib.dbar_profile_kind_name.restype = ctypes.c_char_p
 _lib.dbar_profile.argtypes = [_vp, _int]
 _lib.dbar_profile_read.argtypes = [_vp, _int, _dp, ctypes.POINTER(ctypes.c_longlong), _dp]
 _lib.dbar_launch_count.argtypes = [_vp, ctypes.POINTER(ctypes.c_longlong)]
+_lib.dbar_plan_tuning.argtypes = [_vp, _ip, _dp, _dp]
 _u64 = ctypes.c_uint64
 _lib.dbar_serve_create.argtypes = [ctypes.POINTER(dbar_params), ctypes.c_size_t, ctypes.POINTER(_vp)]
 _lib.dbar_serve_submit.argtypes = [_vp, ctypes.POINTER(dbar_request), ctypes.POINTER(_u64)]
@@ -218,6 +220,13 @@ def dbar_profile_read(plan, kind: int):
     ms, n, by = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double()
     _check(_lib.dbar_profile_read(plan, int(kind), ctypes.byref(ms), ctypes.byref(n), ctypes.byref(by)))
     return ms.value, n.value, by.value
+
+
+def dbar_plan_tuning(plan):
+    """(column-pass tile variant in use, ms per launch of variant 0, of variant 1)."""
+    v, a, b = ctypes.c_int(), ctypes.c_double(), ctypes.c_double()
+    _check(_lib.dbar_plan_tuning(plan, ctypes.byref(v), ctypes.byref(a), ctypes.byref(b)))
+    return v.value, a.value, b.value
 
 
 def dbar_launch_count(plan) -> int:

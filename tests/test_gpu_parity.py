@@ -216,3 +216,28 @@ def test_full_size_mixed_workload_sampled_k_match_oracle(dbar, torch_cuda):
     for i in (int(np.argmin(abs(w.k))), int(np.argmax(abs(w.k)))):
         o = _oracle(w, i, tol=1e-13)
         assert rel(S[i].cpu().numpy(), o["S"]) < 1e-10, i
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_graph_replayed_cycles_match_direct_launches(dbar, prec):
+    # a Krylov cycle captured once as a CUDA graph and replayed gives the same bits
+    w = wl.batched_fp64(N=64, nk_side=3)
+    res = []
+    for graphs in (1, 0):
+        plan = dbar.Plan(w.N, w.L, M=2, prec=prec, restart=16, tol=1e-12, max_batch=5, graphs=graphs)
+        res.append(plan.solve(w.Q, w.k[:7]))     # batches of 5 and a ragged 2
+    assert np.array_equal(res[0]["S"], res[1]["S"]) and np.array_equal(res[0]["iters"], res[1]["iters"])
+    assert res[0]["status"] == dbar.DBAR_OK
+
+
+def test_autotuned_column_tiles_give_identical_results(dbar):
+    # both compiled tile shapes of the FP32 column pass compute the same numbers
+    w = wl.mixed_1024(N=256, nk=3, L=6.0)
+    res = []
+    for autotune in (0, 2, 1):
+        plan = dbar.Plan(w.N, w.L, M=2, prec="mixed", restart=24, tol=1e-12, max_batch=3, autotune=autotune)
+        res.append(plan.solve(w.Q, w.k, want_m=False))
+        if autotune == 2:
+            assert dbar.dbar_plan_tuning(plan.handle)[0] == 1
+    assert np.array_equal(res[0]["S"], res[1]["S"]) and np.array_equal(res[0]["S"], res[2]["S"])
+    assert res[0]["status"] == dbar.DBAR_OK

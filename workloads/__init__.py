@@ -136,6 +136,42 @@ def mixture_request(seed: int, N: int, L: float, kmax: float, nterms_max: int = 
     return gaussian_mixture(N, L, centres, widths, amps), complex(k)
 
 
+def uneven_potentials(N: int, L: float):
+    """The two potentials of the uneven-batch workload on an N-grid: a Gaussian
+    exp(-(x^2+y^2)) and exp(-(x^2+y^2)^2/4)(1 + 0.3 cos 3x)."""
+    X, Y = mesh(N, L)
+    r2 = X * X + Y * Y
+    qa = np.exp(-r2).astype(np.complex128)
+    qb = (np.exp(-r2 * r2 / 4.0) * (1.0 + 0.3 * np.cos(3.0 * X))).astype(np.complex128)
+    return qa, qb
+
+
+def uneven_batch(n: int = 1000, seed: int = 11, L: float = 4.0, kmax: float = 12.0,
+                 xi_q=(12.5, 18.0)):
+    """Uneven batch: N drawn from {128,256,512,1024,2048} with weights
+    .3/.3/.2/.15/.05; request i uses potential i mod 2; k uniform in the disc
+    |k| <= kmax, rejection-sampled (up to 64 draws) until the N-grid resolves the
+    shifted support of F(E_k Q) (resolved(N, L, k, xi_q[potential])); when no draw
+    fits, N is doubled and the draws continue (2048 resolves every k here)."""
+    rng = np.random.default_rng(seed)
+    sizes = np.array([128, 256, 512, 1024, 2048])
+    Ns = rng.choice(sizes, size=n, p=[0.3, 0.3, 0.2, 0.15, 0.05])
+    out = []
+    for i in range(n):
+        N = int(Ns[i])
+        pot = i % 2
+        tries = 0
+        while True:
+            k = complex(random_k_disc(rng, 1, kmax)[0])
+            if resolved(N, L, k, xi_q[pot]):
+                break
+            tries += 1
+            if tries >= 64 and N < 2048:
+                N, tries = 2 * N, 0
+        out.append((N, pot, k))
+    return out
+
+
 BY_NAME = {
     "plain_fp64": plain_fp64,
     "batched_fp64": batched_fp64,
