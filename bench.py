@@ -518,7 +518,7 @@ def main():
     ap.add_argument("--max-outer", dest="max_outer", type=int, default=40)
     ap.add_argument("--rate", type=float, default=200.0, help="serving: requests per second")
     ap.add_argument("--duration", type=float, default=60.0, help="serving: seconds of arrivals")
-    ap.add_argument("--serve-batch", dest="serve_batch", type=int, default=64, help="serving: slots per lane")
+    ap.add_argument("--serve-batch", dest="serve_batch", type=int, default=128, help="serving: slots per lane")
     ap.add_argument("--seed", type=int, default=5)
     ap.add_argument("--nreq", type=int, default=1000, help="uneven: number of solves")
     ap.add_argument("--autotune", type=int, default=1, help="uneven: autotuned column-pass tiles")

@@ -47,15 +47,15 @@ __device__ __forceinline__ cx<double> taylor_coef(cx<double> s, int n, int M, in
   return s;
 }
 
-// 1/(2 pi L (m1^2 + m2^2)): exact division in FP64 and double-float; the
-// fast reciprocal (a few ulp) in the FP32 inner solve.
+// 1/(2 pi L (m1^2 + m2^2)) from c = 1/(2 pi L) already in T: exact division in
+// FP64 and double-float; the fast reciprocal (a few ulp) in the FP32 inner solve.
 template <typename T>
-__device__ __forceinline__ T kappa_scale(double inv2piL, int den) {
-  return (T)inv2piL / (T)den;
+__device__ __forceinline__ T kappa_scale(T c, int den) {
+  return c / (T)den;
 }
 template <>
-__device__ __forceinline__ float kappa_scale<float>(double inv2piL, int den) {
-  return __fdividef((float)inv2piL, (float)den);
+__device__ __forceinline__ float kappa_scale<float>(float c, int den) {
+  return __fdividef(c, (float)den);
 }
 
 template <typename T, int LOGN>
@@ -129,12 +129,13 @@ __global__ void __launch_bounds__(RowG<T, LOGN>::THREADS, RowG<T, LOGN>::MINB) k
 
   // S~ (-1)^{p1+p2} / (2 pi L^2) with S~ = S/xi, xi = (m1 + i m2)/L, 0 at xi = 0.
   const int m2 = wavenum(p2, N);
+  const T c2piL = (T)a.inv2piL;  // one conversion per thread (FP64 is scarce on GB300)
 #pragma unroll
   for (int q = 0; q < 16; ++q) {
     const int p1 = t + q * TPL;
     const int m1 = wavenum(p1, N);
     const int den = m1 * m1 + m2 * m2;
-    T f = den ? kappa_scale<T>(a.inv2piL, den) : (T)0;
+    T f = den ? kappa_scale<T>(c2piL, den) : (T)0;
     if ((p1 + p2) & 1) f = -f;
     v[q] = cmul(v[q], mkc((T)m1 * f, (T)(-m2) * f));
   }

@@ -652,14 +652,14 @@ static bool any_running(dbar_plan* P, int nb, cudaStream_t st) {
 // Between chunks of kGraphChunk steps the host stops launching once every slot
 // has finished its cycle.  *launched_steps receives the Krylov steps launched.
 template <typename TI>
-static dbar_status one_cycle(dbar_plan* P, int nb, cudaStream_t st, int* launched_steps) {
+static dbar_status one_cycle(dbar_plan* P, int nb, cudaStream_t st, int* launched_steps, bool early_stop = true) {
   int j0 = 0;
   while (j0 < P->m) {
     const int j1 = std::min(P->m, j0 + kGraphChunk);
     dbar_status s = cycle_steps<TI>(P, nb, j0, j1, st);
     if (s != DBAR_OK) return s;
     j0 = j1;
-    if (j0 < P->m && !any_running(P, nb, st)) break;
+    if (early_stop && j0 < P->m && !any_running(P, nb, st)) break;
   }
   *launched_steps = j0;
   return cycle_tail<TI>(P, nb, st);
@@ -692,7 +692,7 @@ static dbar_status capture_part(dbar_plan* P, GraphPart* g, F&& body) {
 }
 
 template <typename TI>
-static dbar_status graph_cycle(dbar_plan* P, int nb, cudaStream_t st, int* launched_steps) {
+static dbar_status graph_cycle(dbar_plan* P, int nb, cudaStream_t st, int* launched_steps, bool early_stop = true) {
   CycleGraph* g = nullptr;
   for (CycleGraph& c : P->graphs)
     if (!c.parts.empty() && c.nb == nb && c.prof == P->prof.on) g = &c;
@@ -721,7 +721,7 @@ static dbar_status graph_cycle(dbar_plan* P, int nb, cudaStream_t st, int* launc
     P->nlaunch += g->parts[c].kernels;
     launched = std::min(P->m, (c + 1) * kGraphChunk);
     if (P->prof.on) P->graph_ran.push_back(&g->parts[c]);
-    if (c + 1 < nchunks && !any_running(P, nb, st)) break;
+    if (early_stop && c + 1 < nchunks && !any_running(P, nb, st)) break;
   }
   CK(cudaGraphLaunch(g->parts[nchunks].exec, st));
   P->nlaunch += g->parts[nchunks].kernels;
@@ -1389,8 +1389,12 @@ dbar_status plan_active(dbar_plan* P, int nb, int* active, cudaStream_t st) {
 
 dbar_status plan_step(dbar_plan* P, int nb, cudaStream_t st) {
   if (!P || nb < 0 || nb > P->B) return fail(DBAR_EINVAL, "plan_step: bad argument");
+  // the whole cycle is launched without host synchronisation, so a server can
+  // service other plans while this one runs
   int launched = 0;
-  return P->mixed ? one_cycle<float>(P, nb, st, &launched) : one_cycle<double>(P, nb, st, &launched);
+  if (P->p.graphs)
+    return P->mixed ? graph_cycle<float>(P, nb, st, &launched, false) : graph_cycle<double>(P, nb, st, &launched, false);
+  return P->mixed ? one_cycle<float>(P, nb, st, &launched, false) : one_cycle<double>(P, nb, st, &launched, false);
 }
 
 dbar_status plan_read_slot(dbar_plan* P, int slot, double* S, double* m, int* itot, int* ncyc, double* resid,

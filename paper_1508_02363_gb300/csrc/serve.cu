@@ -56,6 +56,7 @@ struct Request {
 struct Lane {
   int N = 0;
   double L = 0.0;
+  cudaStream_t stream = nullptr;  // own stream: one lane's cycle runs while others are serviced
   dbar_plan* plan = nullptr;
   int B = 0;
   size_t bytes = 0;
@@ -117,6 +118,7 @@ bool open_lane(dbar_server* S, Lane* ln) {
   if (B < 1) {  // drop idle lanes of other grid classes to make room
     for (Lane* o : S->lanes)
       if (o != ln && o->plan && !o->busy()) {
+        cudaStreamSynchronize(o->stream);
         dbar_plan_destroy(o->plan);
         o->plan = nullptr;
         S->used -= o->bytes;
@@ -128,6 +130,7 @@ bool open_lane(dbar_server* S, Lane* ln) {
   B = std::min<int>(B, (int)std::max<size_t>(1, ln->waiting.size() + 8));
   p.max_batch = B;
   dbar_plan* P = nullptr;
+  if (!ln->stream && cudaStreamCreateWithFlags(&ln->stream, cudaStreamNonBlocking) != cudaSuccess) return false;
   if (plan_create_ex(&p, 1, &P) != DBAR_OK) return false;
   ln->plan = P;
   ln->B = plan_batch(P);
@@ -179,7 +182,7 @@ bool step_lane(dbar_server* S, Lane* ln) {
   const int B = ln->B;
   std::vector<int> act(B, 0), mask(B, 0);
   lk.unlock();
-  dbar_status st = plan_active(ln->plan, B, act.data(), S->stream);
+  dbar_status st = plan_active(ln->plan, B, act.data(), ln->stream);
   lk.lock();
   if (st != DBAR_OK) {
     lane_failed(S, ln, st);
@@ -194,7 +197,7 @@ bool step_lane(dbar_server* S, Lane* ln) {
     if (r->want_m) r->m.resize(n2);
     lk.unlock();
     st = plan_read_slot(ln->plan, s, r->S.data(), r->want_m ? r->m.data() : nullptr, &r->itot, &r->ncyc, &r->resid,
-                        S->stream);
+                        ln->stream);
     lk.lock();
     if (st != DBAR_OK) {
       lane_failed(S, ln, st);
@@ -224,12 +227,12 @@ bool step_lane(dbar_server* S, Lane* ln) {
   lk.unlock();
   st = DBAR_OK;
   for (int s = 0; s < B && st == DBAR_OK; ++s)
-    if (admit[s]) st = plan_load_slot(ln->plan, s, admit[s]->Q.data(), admit[s]->k1, admit[s]->k2, S->stream);
-  if (st == DBAR_OK && nnew) st = plan_begin(ln->plan, B, mask.data(), S->stream);
-  if (st == DBAR_OK && occupied) st = plan_step(ln->plan, B, S->stream);
+    if (admit[s]) st = plan_load_slot(ln->plan, s, admit[s]->Q.data(), admit[s]->k1, admit[s]->k2, ln->stream);
+  if (st == DBAR_OK && nnew) st = plan_begin(ln->plan, B, mask.data(), ln->stream);
+  if (st == DBAR_OK && occupied) st = plan_step(ln->plan, B, ln->stream);
   if (st == DBAR_OK && inject) st = dbar_internal_fail(DBAR_ECUDA, "injected lane failure");
   if (st != DBAR_OK) {
-    cudaStreamSynchronize(S->stream);
+    cudaStreamSynchronize(ln->stream);
     lk.lock();
     lane_failed(S, ln, st);
   }
@@ -427,7 +430,9 @@ extern "C" dbar_status dbar_serve_destroy(dbar_server_t S) {
   if (S->worker.joinable()) S->worker.join();
   cudaSetDevice(S->device);
   for (Lane* l : S->lanes) {
+    if (l->stream) cudaStreamSynchronize(l->stream);
     if (l->plan) dbar_plan_destroy(l->plan);
+    if (l->stream) cudaStreamDestroy(l->stream);
     delete l;
   }
   for (auto& kv : S->reqs) delete kv.second;
