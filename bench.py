@@ -40,6 +40,23 @@ def env_rank():
         int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def rank_units(k, rank, world):
+    """The k values rank `rank` solves: the workload's list rotated by 2 pi rank/world
+    (distinct, statistically equivalent problems per GPU; weak scaling, no data-path
+    collective between ranks)."""
+    return np.asarray(k) * np.exp(2j * np.pi * rank / world)
+
+
+def allreduce_max(x, dist, device="cpu"):
+    """max over ranks of a host float (barrier-free: one all-reduce on a scalar)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -187,6 +204,7 @@ def run_ours(args):
     nk, N = w.k.size, w.N
     if args.nk:
         w.k = w.k[:args.nk]
+    w.k = rank_units(w.k, rank, world)
     nk = w.k.size
     plan = dbar.Plan(N, w.L, M=w.M, prec="mixed" if w.mixed else "fp64", tol=w.tol, restart=args.restart,
                      inner_tol=args.inner_tol, max_batch=nk, max_outer=args.max_outer)
@@ -219,10 +237,7 @@ def run_ours(args):
     total_ms = sum(step_ms)
     prof = dbar.profile_table(plan.handle)
     dbar.dbar_profile(plan.handle, False)
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = allreduce_max(total_ms, dist, device="cuda")
     ms_per_step = total_ms / args.steps
     value = nk * world * args.steps / (total_ms / 1e3)
     last = results[-1]
