@@ -207,7 +207,7 @@ def run_ours(args):
     w.k = rank_units(w.k, rank, world)
     nk = w.k.size
     plan = dbar.Plan(N, w.L, M=w.M, prec="mixed" if w.mixed else "fp64", tol=w.tol, restart=args.restart,
-                     inner_tol=args.inner_tol, max_batch=nk, max_outer=args.max_outer)
+                     inner_tol=args.inner_tol, max_batch=nk, max_outer=args.max_outer, sstep=args.sstep)
     stream = torch.cuda.current_stream()
     Qd = torch.from_numpy(w.Q).cuda()
     Sd = torch.empty((nk, N, N), dtype=torch.complex128, device="cuda")
@@ -318,7 +318,8 @@ def run_ours(args):
            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if w.mixed else "f64",
            "data": "synthetic (seeded Gaussian-mixture potential and k list)",
            "config": {"workload": w.name, "N": N, "L": w.L, "nk": nk, "M": w.M, "tol": w.tol,
-                      "prec": "mixed" if w.mixed else "fp64", "restart": args.restart, "inner_tol": args.inner_tol,
+                      "prec": "mixed" if w.mixed else "fp64", "restart": args.restart, "sstep": args.sstep,
+                      "inner_tol": args.inner_tol,
                       "parallelism": f"replicas over k x{world}",
                       "l2": "inputs larger than L2 (device working set %.1f GB)" % (plan.device_bytes / 1e9)},
            "p50_ms": round(statistics.median(step_ms), 3),
@@ -365,7 +366,8 @@ def run_uneven(args):
     for (N, pot) in groups:
         if N not in plans:
             nmax = max(len(v) for (n2, _), v in groups.items() if n2 == N)
-            plans[N] = dbar.Plan(N, L, prec="mixed", restart=args.restart, tol=1e-12, inner_tol=args.inner_tol,
+            plans[N] = dbar.Plan(N, L, prec="mixed", restart=args.restart, sstep=args.sstep, tol=1e-12,
+                                 inner_tol=args.inner_tol,
                                  max_batch=min(nmax, 256 if N <= 1024 else 64), autotune=int(args.autotune))
             pots[N] = [torch.from_numpy(q).cuda() for q in wl.uneven_potentials(N, L)]
     outS = {key: torch.empty((len(v), key[0], key[0]), dtype=torch.complex128, device="cuda")
@@ -525,6 +527,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="mixed_1024")
     ap.add_argument("--restart", type=int, default=32)
+    ap.add_argument("--sstep", type=int, default=0,
+                    help="Krylov vectors per basis sweep: 1, 2, 4, or 0 = the library's automatic choice")
     ap.add_argument("--inner-tol", dest="inner_tol", type=float, default=1e-6)
     ap.add_argument("--check-k", dest="check_k", type=int, default=4)
     ap.add_argument("--cpu-sample", dest="cpu_sample", type=int, default=16)

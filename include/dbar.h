@@ -86,13 +86,23 @@ typedef struct {
                         workspaces and keep the faster (results are identical
                         across shapes); cached per (device, N, M).
                         0: first shape; 2: second shape (for checks)           */
+  int sstep;         /* Krylov vectors formed per sweep of the stored basis.
+                        2 or 4: s-step blocks -- the chain p, Kp, ..., of
+                        K = A - I is orthogonalised against the basis in one
+                        pass (block Gram-Schmidt + Cholesky QR), which cuts
+                        the basis traffic per Krylov vector about S-fold; the
+                        Krylov space and the minimisation are those of GMRES,
+                        convergence is checked at block ends; restart must be
+                        a multiple of sstep.  1: one vector per sweep
+                        (classical Gram-Schmidt per step).  0 (default): 4
+                        if restart is a multiple of 4, else 2 if even, else 1 */
 } dbar_params;
 
 typedef struct dbar_plan* dbar_plan_t;
 
 /* Defaults for a grid: M = 2, DBAR_MIXED, restart 32, tol 1e-12,
  * inner_tol 1e-6, max_outer 40, max_iter 4000, analytic fill,
- * DBAR_RESID_DOUBLE_FLOAT, graphs on, autotune on. */
+ * DBAR_RESID_DOUBLE_FLOAT, graphs on, autotune on, sstep 0 (automatic). */
 void dbar_params_init(dbar_params* p, int N, double L);
 
 /* Message describing the calling thread's most recent failure ("" if none). */

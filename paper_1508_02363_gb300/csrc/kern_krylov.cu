@@ -39,6 +39,41 @@ cudaError_t launch_xupdate(long long n, int mp1, const int* nsteps, const double
 KR_INST(float)
 KR_INST(double)
 
+template <typename T, int S>
+cudaError_t launch_bdots(const BlockArgs& a, const cx<T>* V, long long vss, int J, int nslots, cudaStream_t s) {
+  if (nslots <= 0) return cudaSuccess;
+  const size_t sm = (size_t)(KR_THREADS / 32) * block_items(J, S) * sizeof(double);
+  k_bdots<T, S><<<dim3(a.nchunk, nslots), KR_THREADS, sm, s>>>(a, V, vss, J);
+  return cudaGetLastError();
+}
+template <int S>
+cudaError_t launch_bscalar(const BlockArgs& a, const CycleState& c, double* Hraw, double* bcoef, int* upd, int J,
+                           int nslots, cudaStream_t s) {
+  if (nslots <= 0) return cudaSuccess;
+  const size_t sm = (size_t)(block_items(J, S) + (J + S) * S) * sizeof(double);
+  k_bscalar<S><<<nslots, KR_THREADS, sm, s>>>(a, c, Hraw, bcoef, upd, J);
+  return cudaGetLastError();
+}
+template <typename T, int S>
+cudaError_t launch_bupdate(const BlockArgs& a, const int* upd, cx<T>* V, long long vss, int J, int nslots,
+                           cudaStream_t s) {
+  if (nslots <= 0) return cudaSuccess;
+  k_bupdate<T, S><<<dim3(a.nchunk, nslots), KR_THREADS, 0, s>>>(a, upd, V, vss, J);
+  return cudaGetLastError();
+}
+#define KB_INST(T, S)                                                                                          \
+  template cudaError_t launch_bdots<T, S>(const BlockArgs&, const cx<T>*, long long, int, int, cudaStream_t);  \
+  template cudaError_t launch_bupdate<T, S>(const BlockArgs&, const int*, cx<T>*, long long, int, int,        \
+                                            cudaStream_t);
+KB_INST(float, 2)
+KB_INST(float, 4)
+KB_INST(double, 2)
+KB_INST(double, 4)
+template cudaError_t launch_bscalar<2>(const BlockArgs&, const CycleState&, double*, double*, int*, int, int,
+                                       cudaStream_t);
+template cudaError_t launch_bscalar<4>(const BlockArgs&, const CycleState&, double*, double*, int*, int, int,
+                                       cudaStream_t);
+
 cudaError_t launch_finalize_h(const KryArgs& a, double* H, int j, int nslots, cudaStream_t s) {
   if (nslots <= 0) return cudaSuccess;
   k_finalize_h<<<nslots, KR_THREADS, 0, s>>>(a, H, j);
@@ -109,10 +144,14 @@ cudaError_t launch_add_fields(const void* S, const void* KS, void* AS, long long
   return cudaGetLastError();
 }
 
-cudaError_t launch_coef(const cx<double>* partA, int nblkA, int M, int N, double fillscale, cx<double>* coef,
-                        int nslots, cudaStream_t s) {
+cudaError_t launch_coef(const cx<double>* partA, int part_fp32, int M, int N, const cx<double>* Da64,
+                        double fillscale, cx<double>* coef, int nslots, cudaStream_t s) {
   if (nslots <= 0) return cudaSuccess;
-  k_coef<<<nslots, 256, 0, s>>>(partA, nblkA, M, N, fillscale, coef);
+  if (part_fp32)
+    k_coef<float><<<nslots, 256, 0, s>>>(reinterpret_cast<const cx<float>*>(partA), seg_count(N), M > 1 ? M : 1, M,
+                                         N, Da64, fillscale, coef);
+  else
+    k_coef<double><<<nslots, 256, 0, s>>>(partA, seg_count(N), M > 1 ? M : 1, M, N, Da64, fillscale, coef);
   return cudaGetLastError();
 }
 

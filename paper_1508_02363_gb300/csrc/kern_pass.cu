@@ -26,11 +26,7 @@ static cudaError_t set_smem(K kernel, size_t bytes) {
 template <typename T, int LOGN, bool IN64>
 cudaError_t launch_pass_a_n(const PassArgs<T>& a, int nslots, cudaStream_t s) {
   using G = RowG<T, LOGN>;
-  const int MA = a.M > 1 ? a.M : 1;
-  constexpr int NSEG = G::TPL >= 32 ? G::TPL / 32 : 1;
-  const size_t sm = align16((size_t)G::LINES * G::P * sizeof(cx<T>)) +
-                    (size_t)G::LINES * NSEG * (MA + 1) * sizeof(cx<double>) +
-                    (size_t)G::LINES * (a.M + 2) * sizeof(cx<double>);
+  const size_t sm = (size_t)G::LINES * G::P * sizeof(cx<T>);
   cudaError_t e = set_smem(k_pass_a<T, LOGN, IN64>, sm);
   if (e != cudaSuccess) return e;
   k_pass_a<T, LOGN, IN64><<<dim3(G::N / G::LINES, nslots), G::THREADS, sm, s>>>(a);

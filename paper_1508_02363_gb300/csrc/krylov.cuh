@@ -146,20 +146,14 @@ __global__ void __launch_bounds__(KR_THREADS) k_update(const KryArgs a, cx<T>* _
 }
 
 
-// Norm of the new vector, Givens rotation of column j, residual estimate.
-static __global__ void __launch_bounds__(KR_THREADS) k_givens(const KryArgs a, CycleState c, int j) {
-  __shared__ double sh[KR_THREADS / 32];
-  const int slot = blockIdx.x;
-  if (!c.run[slot]) return;
-  double s = 0.0;
-  for (int q = threadIdx.x; q < a.nchunk; q += blockDim.x) s += a.part2[(size_t)slot * a.nchunk + q];
-  s = block_sum_256(s, sh);
-  if (threadIdx.x != 0) return;
+// Givens step for Hessenberg column j of a slot whose rows 0..j+1 are in Hc:
+// applies the earlier rotations, forms rotation j, updates g and the step
+// counters; returns true when the slot's cycle stops after this column
+// (residual estimate below the threshold, cycle full, iteration cap, or a
+// zero subdiagonal: the Krylov space is invariant).
+__device__ inline bool givens_column(const CycleState& c, int slot, int j, double* Hc) {
   const int m = c.m;
-  const double nrm = sqrt(s);
-  double* Hc = c.H + ((size_t)slot * m + j) * (m + 1);
-  Hc[j + 1] = nrm;
-  c.sigma[(size_t)slot * (m + 1) + j + 1] = nrm > 0.0 ? 1.0 / nrm : 0.0;
+  const double sub = Hc[j + 1];
   double* cs = c.cs + (size_t)slot * m;
   double* sn = c.sn + (size_t)slot * m;
   double* g = c.g + (size_t)slot * (m + 1);
@@ -182,8 +176,24 @@ static __global__ void __launch_bounds__(KR_THREADS) k_givens(const KryArgs a, C
   g[j] = cj * g[j];
   c.nsteps[slot] = j + 1;
   c.itot[slot] += 1;
-  if (fabs(g[j + 1]) <= c.thr[slot] || j + 1 >= m || nrm == 0.0 || c.itot[slot] >= c.max_iter)
-    c.run[slot] = 0;
+  return fabs(g[j + 1]) <= c.thr[slot] || j + 1 >= m || sub == 0.0 || c.itot[slot] >= c.max_iter;
+}
+
+// Norm of the new vector, Givens rotation of column j, residual estimate.
+static __global__ void __launch_bounds__(KR_THREADS) k_givens(const KryArgs a, CycleState c, int j) {
+  __shared__ double sh[KR_THREADS / 32];
+  const int slot = blockIdx.x;
+  if (!c.run[slot]) return;
+  double s = 0.0;
+  for (int q = threadIdx.x; q < a.nchunk; q += blockDim.x) s += a.part2[(size_t)slot * a.nchunk + q];
+  s = block_sum_256(s, sh);
+  if (threadIdx.x != 0) return;
+  const int m = c.m;
+  const double nrm = sqrt(s);
+  double* Hc = c.H + ((size_t)slot * m + j) * (m + 1);
+  Hc[j + 1] = nrm;
+  c.sigma[(size_t)slot * (m + 1) + j + 1] = nrm > 0.0 ? 1.0 / nrm : 0.0;
+  if (givens_column(c, slot, j, Hc)) c.run[slot] = 0;
 }
 
 // y = R^{-1} g (back substitution), ycoef_i = y_i sigma_i.
@@ -276,6 +286,288 @@ static __global__ void __launch_bounds__(KR_THREADS) k_cycle_start(CycleState c,
   if (c.inner_tol > 0.0) thr = fmax(thr, c.inner_tol * beta);
   c.thr[slot] = thr;
   if (act) c.ncyc[slot] += 1;
+}
+
+// ---------------------------------------------------------------------------
+// s-step (block) Arnoldi.  The Krylov space and the GMRES minimisation are the
+// ones of the step-by-step process above; only the order of the work changes,
+// so that each sweep over the stored basis serves S new directions instead of
+// one (the basis sweeps are HBM-bound).  From the last basis vector
+// v_{J-1} a block forms the monomial chain in K = A - I,
+//     p_0 = v_{J-1},  p_{i+1} = K p_i   (i < S, stored raw in basis slots J+i),
+// so A p_i = p_i + p_{i+1}.  One sweep then yields C = V^T p (J x S) and the
+// Gram matrix p^T p (S x S); a per-slot FP64 step normalises the chain
+// (p^_i = p_i / ||p_i||), forms G = p^T p - C^T C, its Cholesky factor R (the
+// block's orthonormalisation, CholQR), and from A P^ = P^ B (B unit lower
+// bidiagonal up to the normalisation) the S new columns of the Hessenberg
+// matrix,  H_new = (T B - [H_prev Z; 0]) U^{-1},  where T holds the chain's
+// coordinates in the new orthonormal basis, U its part on v_{J-1}..v_{J+S-2}
+// and Z its part on v_0..v_{J-2}.  A second sweep writes the new basis vectors
+// Q = (P^ - V C) R^{-1} over the chain.  A pivot of G below kBlockPivot ends
+// the cycle after the columns it still supports (the outer refinement
+// continues from the true residual).
+// ---------------------------------------------------------------------------
+// Warp reduce-scatter of S = 2 or 4 per-lane values: every lane returns the
+// warp total of value lane / (32 / S).  Each halving step exchanges only the
+// half of the values the partner keeps, so S values cost S - 1 + 5 - log2(S)
+// shuffles instead of 5 S (fixed order: the result does not depend on timing).
+template <int S, typename T>
+__device__ __forceinline__ T warp_reduce_scatter(const T (&s)[S], int lane) {
+  static_assert(S == 2 || S == 4, "S must be 2 or 4");
+  const unsigned full = 0xffffffffu;
+  T k;
+  if constexpr (S == 4) {
+    const bool h = lane & 16;
+    T k0 = h ? s[2] : s[0], k1 = h ? s[3] : s[1];
+    k0 += __shfl_xor_sync(full, h ? s[0] : s[2], 16);
+    k1 += __shfl_xor_sync(full, h ? s[1] : s[3], 16);
+    const bool g = lane & 8;
+    k = g ? k1 : k0;
+    k += __shfl_xor_sync(full, g ? k0 : k1, 8);
+  } else {
+    const bool h = lane & 16;
+    k = h ? s[1] : s[0];
+    k += __shfl_xor_sync(full, h ? s[0] : s[1], 16);
+    k += __shfl_xor_sync(full, k, 8);
+  }
+  k += __shfl_xor_sync(full, k, 4);
+  k += __shfl_xor_sync(full, k, 2);
+  k += __shfl_xor_sync(full, k, 1);
+  return k;
+}
+
+// part[slot][r*S+i][chunk] = <v~_r, p_{i+1}> (r < J); then <p_i, p_l>, i <= l.
+template <typename T, int S>
+__global__ void __launch_bounds__(KR_THREADS) k_bdots(const BlockArgs a, const cx<T>* __restrict__ V, long long vss,
+                                                       int J) {
+  extern __shared__ double red[];  // [KR_THREADS / 32][nit]
+  const int slot = blockIdx.y;
+  if (!a.run[slot]) return;
+  const int nit = block_items(J, S);
+  const long long base = (long long)blockIdx.x * KB_CHUNK + threadIdx.x;
+  const cx<T>* Vs = V + (size_t)slot * vss;
+  cx<T> w[S][KB_EPT];
+#pragma unroll
+  for (int i = 0; i < S; ++i)
+#pragma unroll
+    for (int e = 0; e < KB_EPT; ++e) {
+      const long long idx = base + (long long)e * KR_THREADS;
+      w[i][e] = idx < a.n ? ldg(Vs + (size_t)(J + i) * a.n + idx) : mkc((T)0, (T)0);
+    }
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int r = 0; r < J; ++r) {
+    T s[S];
+#pragma unroll
+    for (int i = 0; i < S; ++i) s[i] = 0;
+#pragma unroll
+    for (int e = 0; e < KB_EPT; ++e) {
+      const long long idx = base + (long long)e * KR_THREADS;
+      if (idx < a.n) {
+        const cx<T> v = ldg(Vs + (size_t)r * a.n + idx);
+#pragma unroll
+        for (int i = 0; i < S; ++i) s[i] += v.re * w[i][e].re + v.im * w[i][e].im;
+      }
+    }
+    const T d = warp_reduce_scatter<S>(s, lane);
+    if ((lane & (32 / S - 1)) == 0) red[wid * nit + r * S + lane / (32 / S)] = (double)d;
+  }
+  int it = J * S;
+#pragma unroll
+  for (int i = 0; i < S; ++i)
+#pragma unroll
+    for (int l = i; l < S; ++l) {
+      T s = 0;
+#pragma unroll
+      for (int e = 0; e < KB_EPT; ++e) s += w[i][e].re * w[l][e].re + w[i][e].im * w[l][e].im;
+      const T d = warp_sum_t(s, 32);
+      if (lane == 0) red[wid * nit + it] = (double)d;
+      ++it;
+    }
+  __syncthreads();
+  for (int q = threadIdx.x; q < nit; q += blockDim.x) {
+    double s = 0.0;
+    for (int w2 = 0; w2 < KR_THREADS / 32; ++w2) s += red[w2 * nit + q];
+    a.part[((size_t)slot * a.nitem + q) * a.nchunk + blockIdx.x] = s;
+  }
+}
+
+// Per-slot FP64 step of a block (one CTA per slot; thread 0 does the small
+// dense algebra).  Writes the block's Hessenberg columns J-1.. (unrotated into
+// Hraw, rotated into c.H with the Givens steps), the sweep coefficients, the
+// scales of the new vectors, and upd[slot] = 1 for every slot that ran the
+// block (its new vectors need the update sweep even when it stops here).
+template <int S>
+static __global__ void __launch_bounds__(KR_THREADS) k_bscalar(BlockArgs a, CycleState c, double* __restrict__ Hraw,
+                                                               double* __restrict__ bcoef, int* __restrict__ upd,
+                                                               int J) {
+  extern __shared__ double sm[];  // val[nit], X[(J + S) * S]
+  const int slot = blockIdx.x;
+  if (!c.run[slot]) {
+    if (threadIdx.x == 0) upd[slot] = 0;
+    return;
+  }
+  const int nit = block_items(J, S);
+  double* val = sm;
+  double* X = sm + nit;
+  for (int q = threadIdx.x; q < nit; q += blockDim.x) {
+    const double* p = a.part + ((size_t)slot * a.nitem + q) * a.nchunk;
+    double s = 0.0;
+    for (int ch = 0; ch < a.nchunk; ++ch) s += p[ch];
+    val[q] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  const int m = c.m, rows = J + S;
+  double* sg = c.sigma + (size_t)slot * (m + 1);
+  // chain norms Sg[i] = ||p_i|| (Sg[0] = 1: v_{J-1} has unit norm)
+  double Sg[S + 1], G[S][S], R[S][S], Ri[S][S];
+  Sg[0] = 1.0;
+  {
+    int it = J * S;
+    for (int i = 0; i < S; ++i)
+      for (int l = i; l < S; ++l, ++it) {
+        G[i][l] = val[it];
+        if (l == i) Sg[i + 1] = sqrt(fmax(val[it], 0.0));
+      }
+  }
+  // C^ = coordinates of p^_{i+1} on v_r (in place in val)
+  for (int r = 0; r < J; ++r)
+    for (int i = 0; i < S; ++i) {
+      const double d = Sg[i + 1];
+      val[r * S + i] = d > 0.0 ? val[r * S + i] * sg[r] / d : 0.0;
+    }
+  // G = p^T p (normalised) - C^T C, Cholesky G = R^T R
+  int nok = S;
+  for (int i = 0; i < S; ++i)
+    for (int l = 0; l < S; ++l) R[i][l] = 0.0;
+  for (int i = 0; i < S && nok == S; ++i) {
+    for (int l = i; l < S; ++l) {
+      const double dd = Sg[i + 1] * Sg[l + 1];
+      double gv = dd > 0.0 ? G[i][l] / dd : 0.0;
+      for (int r = 0; r < J; ++r) gv -= val[r * S + i] * val[r * S + l];
+      for (int q = 0; q < i; ++q) gv -= R[q][i] * R[q][l];
+      if (l == i) {
+        if (!(gv > kBlockPivot) || Sg[i + 1] == 0.0) {
+          nok = i;
+          break;
+        }
+        R[i][i] = sqrt(gv);
+      } else {
+        R[i][l] = gv / R[i][i];
+      }
+    }
+  }
+  const int ncols = nok > 0 ? nok : 1;  // nok = 0: p_1 lies in span(V), a happy breakdown column
+  // R^{-1} on the accepted columns (zero elsewhere)
+  for (int i = 0; i < S; ++i)
+    for (int l = 0; l < S; ++l) Ri[i][l] = 0.0;
+  for (int i = 0; i < nok; ++i) {
+    Ri[i][i] = 1.0 / R[i][i];
+    for (int q = i - 1; q >= 0; --q) {
+      double s = 0.0;
+      for (int l = q + 1; l <= i; ++l) s += R[q][l] * Ri[l][i];
+      Ri[q][i] = -s / R[q][q];
+    }
+  }
+  // T[r][k]: coordinates of p^_k on v_0..v_{J+S-1}
+  auto T = [&](int r, int k) -> double {
+    if (k == 0) return r == J - 1 ? 1.0 : 0.0;
+    if (r < J) return val[r * S + k - 1];
+    const int q = r - J;
+    return q <= k - 1 ? R[q][k - 1] : 0.0;
+  };
+  // H_new = (T B - [H_prev Z; 0]) U^{-1}, column by column
+  for (int i = 0; i < ncols; ++i) {
+    const double bsub = Sg[i + 1] / Sg[i];
+    for (int r = 0; r < rows; ++r) {
+      double v = T(r, i) + T(r, i + 1) * bsub;
+      if (r < J && i > 0)
+        for (int q = (r > 0 ? r - 1 : 0); q < J - 1; ++q)
+          v -= Hraw[((size_t)slot * m + q) * (m + 1) + r] * val[q * S + i - 1];
+      for (int l = 0; l < i; ++l) v -= X[r * S + l] * T(J - 1 + l, i);
+      const double uii = i == 0 ? 1.0 : R[i - 1][i - 1];
+      X[r * S + i] = r <= J + i ? v / uii : 0.0;
+    }
+  }
+  // columns J-1+i: unrotated copy, then the Givens steps
+  bool stop = false;
+  for (int i = 0; i < ncols && !stop; ++i) {
+    const int j = J - 1 + i;
+    double* Hr = Hraw + ((size_t)slot * m + j) * (m + 1);
+    double* Hc = c.H + ((size_t)slot * m + j) * (m + 1);
+    for (int r = 0; r <= j + 1; ++r) Hr[r] = Hc[r] = X[r * S + i];
+    stop = givens_column(c, slot, j, Hc);
+  }
+  if (ncols < S || J - 1 + 2 * S > m) stop = true;
+  // sweep coefficients: Q = P^ R^{-1} - V C^ R^{-1}, on the raw stored vectors
+  double* bc = bcoef + (size_t)slot * (S * S + (m + 1) * S);
+  for (int k = 0; k < S; ++k)
+    for (int i = 0; i < S; ++i) bc[k * S + i] = Sg[k + 1] > 0.0 ? Ri[k][i] / Sg[k + 1] : 0.0;
+  for (int r = 0; r < J; ++r)
+    for (int i = 0; i < S; ++i) {
+      double s = 0.0;
+      for (int k = 0; k <= i; ++k) s += val[r * S + k] * Ri[k][i];
+      bc[S * S + r * S + i] = -s * sg[r];
+    }
+  for (int i = 0; i < S; ++i) sg[J + i] = 1.0;
+  upd[slot] = 1;
+  if (stop) c.run[slot] = 0;
+}
+
+// Q_i = sum_k bcoef_ki p_{k+1} + sum_r bcoef'_ri v~_r, written over the chain
+// (basis slots J..J+S-1); slots with upd[slot] != 0 only.
+template <typename T, int S>
+__global__ void __launch_bounds__(KR_THREADS) k_bupdate(const BlockArgs a, const int* __restrict__ upd,
+                                                         cx<T>* __restrict__ V, long long vss, int J) {
+  __shared__ T cf[S * S + 129 * S];
+  const int slot = blockIdx.y;
+  if (!upd[slot]) return;
+  const double* bc = a.bcoef + (size_t)slot * (S * S + a.mp1 * S);
+  for (int q = threadIdx.x; q < S * S + J * S; q += blockDim.x) cf[q] = (T)bc[q];
+  __syncthreads();
+  const long long base = (long long)blockIdx.x * KB_CHUNK + threadIdx.x;
+  cx<T>* Vs = V + (size_t)slot * vss;
+  cx<T> acc[S][KB_EPT];
+  {
+    cx<T> w[S][KB_EPT];
+#pragma unroll
+    for (int k = 0; k < S; ++k)
+#pragma unroll
+      for (int e = 0; e < KB_EPT; ++e) {
+        const long long idx = base + (long long)e * KR_THREADS;
+        w[k][e] = idx < a.n ? ldg(Vs + (size_t)(J + k) * a.n + idx) : mkc((T)0, (T)0);
+      }
+#pragma unroll
+    for (int i = 0; i < S; ++i)
+#pragma unroll
+      for (int e = 0; e < KB_EPT; ++e) {
+        cx<T> s = mkc((T)0, (T)0);
+#pragma unroll
+        for (int k = 0; k <= i; ++k) s = mkc(s.re + cf[k * S + i] * w[k][e].re, s.im + cf[k * S + i] * w[k][e].im);
+        acc[i][e] = s;
+      }
+  }
+  for (int r = 0; r < J; ++r) {
+#pragma unroll
+    for (int e = 0; e < KB_EPT; ++e) {
+      const long long idx = base + (long long)e * KR_THREADS;
+      if (idx < a.n) {
+        const cx<T> v = ldg(Vs + (size_t)r * a.n + idx);
+#pragma unroll
+        for (int i = 0; i < S; ++i) {
+          const T c = cf[S * S + r * S + i];
+          acc[i][e] = mkc(acc[i][e].re + c * v.re, acc[i][e].im + c * v.im);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < S; ++i)
+#pragma unroll
+    for (int e = 0; e < KB_EPT; ++e) {
+      const long long idx = base + (long long)e * KR_THREADS;
+      if (idx < a.n) Vs[(size_t)(J + i) * a.n + idx] = acc[i][e];
+    }
 }
 
 }  // namespace dbar

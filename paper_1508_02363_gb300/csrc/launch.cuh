@@ -1,6 +1,6 @@
-// Host-side launchers of the pass and Krylov kernels.  Each precision is
-// instantiated in its own translation unit (kern_f32.cu, kern_f64.cu) so the
-// two compile in parallel.
+// Host-side launchers of the pass and Krylov kernels.  The pass kernels are
+// instantiated per precision and grid size in their own translation units
+// (kern_pass.cu compiled once per pair) so they compile in parallel.
 #pragma once
 #include <string>
 
@@ -31,8 +31,11 @@ inline Geo make_geo(int N) {
   g.P = pitch_of(N);
   return g;
 }
-// blocks per slot of the row passes (A and C): the number of pass-A partial sums
+// blocks per slot of the row passes (A and C)
 inline int row_blocks(int N) { return N / row_lines(ilog2(N)); }
+// warp segments of one row line (N/16 threads, at most 32 per segment): the
+// number of row-moment partials pass A writes per row and moment
+inline int seg_count(int N) { return N / 16 >= 32 ? N / 512 : 1; }
 
 // per-size launchers (kern_pass.cu, one translation unit per precision and size)
 template <typename T, int LOGN, bool IN64>
@@ -60,6 +63,15 @@ template <typename T>
 cudaError_t launch_xupdate(long long n, int mp1, const int* nsteps, const double* ycoef, const cx<T>* V,
                            long long vss, cx<double>* X, long long xss, int nslots, cudaStream_t s);
 
+template <typename T, int S>
+cudaError_t launch_bdots(const BlockArgs& a, const cx<T>* V, long long vss, int J, int nslots, cudaStream_t s);
+template <int S>
+cudaError_t launch_bscalar(const BlockArgs& a, const CycleState& c, double* Hraw, double* bcoef, int* upd, int J,
+                           int nslots, cudaStream_t s);
+template <typename T, int S>
+cudaError_t launch_bupdate(const BlockArgs& a, const int* upd, cx<T>* V, long long vss, int J, int nslots,
+                           cudaStream_t s);
+
 cudaError_t launch_finalize_h(const KryArgs& a, double* H, int j, int nslots, cudaStream_t s);
 cudaError_t launch_givens(const KryArgs& a, const CycleState& c, int j, int nslots, cudaStream_t s);
 cudaError_t launch_solve_y(const CycleState& c, int nslots, cudaStream_t s);
@@ -71,8 +83,9 @@ cudaError_t launch_load_q(const cx<double>* Q, cx<double>* Q64, cx<float>* Q32, 
 cudaError_t launch_delta_build(const cx<double>* V, const cx<double>* W, cx<double>* D64, cx<float>* D32, int N,
                                int nfields, cudaStream_t s);
 cudaError_t launch_add_fields(const void* S, const void* KS, void* AS, long long n, int fp32, cudaStream_t s);
-cudaError_t launch_coef(const cx<double>* partA, int nblkA, int M, int N, double fillscale, cx<double>* coef,
-                        int nslots, cudaStream_t s);
+// part_fp32: partials written by the FP32 pass A (cx<float>), else cx<double>
+cudaError_t launch_coef(const cx<double>* partA, int part_fp32, int M, int N, const cx<double>* Da64,
+                        double fillscale, cx<double>* coef, int nslots, cudaStream_t s);
 cudaError_t launch_cast_fields(const cx<double>* in, cx<float>* out, long long n, cudaStream_t s);
 cudaError_t launch_split_fields(const cx<double>* in, cx<dd>* out, long long n, cudaStream_t s);
 cudaError_t launch_check_finite(const double* p, long long n, int* flag, cudaStream_t s);

@@ -50,12 +50,12 @@ __device__ __forceinline__ cx<double> taylor_coef(cx<double> s, int n, int M, in
 // 1/(2 pi L (m1^2 + m2^2)) from c = 1/(2 pi L) already in T: exact division in
 // FP64 and double-float; the fast reciprocal (a few ulp) in the FP32 inner solve.
 template <typename T>
-__device__ __forceinline__ T kappa_scale(T c, int den) {
-  return c / (T)den;
+__device__ __forceinline__ T kappa_scale(T c, T den) {
+  return c / den;
 }
 template <>
-__device__ __forceinline__ float kappa_scale<float>(float c, int den) {
-  return __fdividef(c, (float)den);
+__device__ __forceinline__ float kappa_scale<float>(float c, float den) {
+  return __fdividef(c, den);
 }
 
 template <typename T, int LOGN>
@@ -101,16 +101,18 @@ __global__ void __launch_bounds__(RowG<T, LOGN>::THREADS, RowG<T, LOGN>::MINB) k
     for (int q = 0; q < 16; ++q) v[q] = cscale(ldg(src + q * TPL), sc);
   }
 
-  // Row moments R_a(p2) = sum_p1 (-1)^p1 S D_a(p1), a = 0..MA.
-  constexpr size_t off = ((size_t)LINES * P * sizeof(cx<T>) + 15) & ~(size_t)15;
-  cx<double>* red = reinterpret_cast<cx<double>*>(smem + off);
-  cx<double>* lc = red + LINES * NSEG * (MA + 1);
+  // Row moments R_a(p2) = sum_p1 (-1)^p1 S D_a(p1), a = 0..MA, written as
+  // per-warp-segment partials (FP64) for k_coef, which combines them with
+  // D_b(p2): no block-wide tail and no FP64 arithmetic per element here.
+  // (FP32 partials from the FP32 pass: on GB300 every FP64 conversion issued
+  // per warp occupies the small FP64 pipe for tens of cycles)
+  using PT = typename std::conditional<std::is_same<T, float>::value, float, double>::type;
   const int seg = TPL >= 32 ? t / 32 : 0;
+  cx<PT>* part = reinterpret_cast<cx<PT>*>(a.partA) + ((size_t)slot * N + p2) * NSEG * (MA + 1);
   // a = 0: D_0(p) = N delta_{p,0}, so R_0 = N S(p1 = 0), held by the thread with t = 0
   if (t == 0) {
     const cx<T> s0 = v[0];
-    red[(line * NSEG + seg) * (MA + 1)] = mkc((double)s0.re * N, (double)s0.im * N);
-    for (int sg = 1; sg < NSEG; ++sg) red[(line * NSEG + sg) * (MA + 1)] = mkc(0.0, 0.0);
+    part[0] = mkc((PT)s0.re * N, (PT)s0.im * N);
   }
   for (int aa = 1; aa <= MA; ++aa) {
     cx<T> acc = mkc((T)0, (T)0);
@@ -122,66 +124,36 @@ __global__ void __launch_bounds__(RowG<T, LOGN>::THREADS, RowG<T, LOGN>::MINB) k
       if ((t + q * TPL) & 1) s = mkc(-s.re, -s.im);
       acc = acc + cmul(s, d);
     }
-    // within a warp segment in T (16 x SEGW terms), across segments in FP64
+    // within a warp segment in T (16 x SEGW terms); segments are summed in k_coef
     const T re = warp_sum_t(acc.re, SEGW), im = warp_sum_t(acc.im, SEGW);
-    if ((t & (SEGW - 1)) == 0) red[(line * NSEG + seg) * (MA + 1) + aa] = mkc((double)re, (double)im);
+    if ((t & (SEGW - 1)) == 0) part[seg * (MA + 1) + aa] = mkc((PT)re, (PT)im);
   }
 
   // S~ (-1)^{p1+p2} / (2 pi L^2) with S~ = S/xi, xi = (m1 + i m2)/L, 0 at xi = 0.
-  const int m2 = wavenum(p2, N);
-  const T c2piL = (T)a.inv2piL;  // one conversion per thread (FP64 is scarce on GB300)
+  // The wavenumbers are formed in T from per-thread values (exact: |m| <= N/2,
+  // m1^2 + m2^2 < 2^24), avoiding per-element int->float conversions, which
+  // share GB300's small FP64/conversion pipe.
+  T c2piL;
+  if constexpr (std::is_same<T, float>::value) c2piL = a.inv2piL_f;
+  else c2piL = (T)a.inv2piL;
+  const T m2f = (T)wavenum(p2, N);
+  const T tf = (T)t;
+  const T m2sq = m2f * m2f;
 #pragma unroll
   for (int q = 0; q < 16; ++q) {
     const int p1 = t + q * TPL;
-    const int m1 = wavenum(p1, N);
-    const int den = m1 * m1 + m2 * m2;
-    T f = den ? kappa_scale<T>(c2piL, den) : (T)0;
+    T m1f = tf + (T)(q * TPL);
+    if (p1 > (N >> 1)) m1f = m1f - (T)N;
+    const T den = m1f * m1f + m2sq;
+    T f = (p1 == 0 && p2 == 0) ? (T)0 : kappa_scale<T>(c2piL, den);
     if ((p1 + p2) & 1) f = -f;
-    v[q] = cmul(v[q], mkc((T)m1 * f, (T)(-m2) * f));
+    v[q] = cmul(v[q], mkc(m1f * f, -(m2f * f)));
   }
   fft_line<T, LOGN, true>(v, sl, t, a.tw);
   cx<T>* dst = reinterpret_cast<cx<T>*>(a.out) + (size_t)slot * a.out_ss + (size_t)p2 * N + t;
 #pragma unroll
   for (int q = 0; q < 16; ++q) dst[q * TPL] = v[q];
 
-  // Per (line, n): combination with D_b(p2) in FP64; then the block partial sums.
-  __syncthreads();
-  for (int i = threadIdx.x; i < LINES * (M + 2); i += G::THREADS) {
-    const int ln = i / (M + 2), n = i - ln * (M + 2);
-    const int pp2 = blockIdx.x * LINES + ln;
-    const cx<double>* R = red + ln * NSEG * (MA + 1);
-    auto Ra = [&](int aa) {
-      cx<double> s = R[aa];
-      for (int sg = 1; sg < NSEG; ++sg) s = s + R[sg * (MA + 1) + aa];
-      return s;
-    };
-    cx<double> s = mkc(0.0, 0.0);
-    if (n <= M) {
-      // sum_a C(n,a) i^{n-a} D_{n-a}(p2) R_a
-      double binom = 1.0;
-      for (int aa = 0; aa <= n; ++aa) {
-        cx<double> tmp = cmul(a.Da64[(size_t)(n - aa) * N + pp2], Ra(aa));
-        const int e = (n - aa) & 3;
-        if (e == 1) tmp = cmuli(tmp);
-        else if (e == 2) tmp = mkc(-tmp.re, -tmp.im);
-        else if (e == 3) tmp = mkc(tmp.im, -tmp.re);
-        s = s + cscale(tmp, binom);
-        binom = binom * (double)(n - aa) / (double)(aa + 1);
-      }
-    } else {
-      // fill value: R_1 D_0(p2) - i R_0 D_1(p2)
-      const cx<double> t1 = cmul(Ra(1), a.Da64[pp2]);
-      const cx<double> t2 = cmul(Ra(0), a.Da64[(size_t)N + pp2]);
-      s = mkc(t1.re + t2.im, t1.im - t2.re);
-    }
-    lc[ln * (M + 2) + n] = (pp2 & 1) ? mkc(-s.re, -s.im) : s;
-  }
-  __syncthreads();
-  for (int n = threadIdx.x; n < M + 2; n += G::THREADS) {
-    cx<double> s = mkc(0.0, 0.0);
-    for (int ln = 0; ln < LINES; ++ln) s = s + lc[ln * (M + 2) + n];
-    a.partA[((size_t)slot * gridDim.x + blockIdx.x) * (M + 2) + n] = s;
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -248,20 +220,51 @@ __global__ void __launch_bounds__(ColG<T, LOGN, CV>::THREADS, ColG<T, LOGN, CV>:
 }
 
 // ---------------------------------------------------------------------------
-// Taylor coefficients of each slot from the pass-A block partials, in a fixed
-// order: coef[slot] = c_0..c_M, then the fill d' = d * fillscale.
+// Taylor coefficients of each slot from pass A's row-moment partials, in a
+// fixed order.  Row p2 contributes (-1)^{p2} times
+//   n <= M:  sum_a C(n,a) i^{n-a} D_{n-a}(p2) R_a(p2)      (c_n, Sec. 4.3 step 4a)
+//   n = M+1: R_1(p2) D_0(p2) - i R_0(p2) D_1(p2)          (fill value dS/dxi(0))
+// and coef[slot] = c_0..c_M, then the fill d' = d * fillscale (taylor_coef).
+// partA: [slot][p2][seg][a], the a = 0 moment in segment 0 only.
 // ---------------------------------------------------------------------------
-static __global__ void __launch_bounds__(256) k_coef(const cx<double>* __restrict__ partA, int nblkA, int M, int N,
-                                              double fillscale, cx<double>* __restrict__ coef) {
+template <typename PT>
+static __global__ void __launch_bounds__(256) k_coef(const cx<PT>* __restrict__ partA, int nseg, int MA, int M,
+                                              int N, const cx<double>* __restrict__ Da64, double fillscale,
+                                              cx<double>* __restrict__ coef) {
   __shared__ double sre[256], sim[256];
   const int slot = blockIdx.x;
-  const cx<double>* pa = partA + (size_t)slot * nblkA * (M + 2);
+  const int stride = nseg * (MA + 1);
+  const cx<PT>* pa = partA + (size_t)slot * N * stride;
   for (int n = 0; n < M + 2; ++n) {
     double re = 0.0, im = 0.0;
-    for (int b = threadIdx.x; b < nblkA; b += blockDim.x) {
-      const cx<double> x = pa[(size_t)b * (M + 2) + n];
-      re += x.re;
-      im += x.im;
+    for (int p2 = threadIdx.x; p2 < N; p2 += blockDim.x) {
+      const cx<PT>* R = pa + (size_t)p2 * stride;
+      auto Ra = [&](int aa) {
+        cx<double> s = ccast<double>(R[aa]);
+        if (aa > 0)
+          for (int sg = 1; sg < nseg; ++sg) s = s + ccast<double>(R[sg * (MA + 1) + aa]);
+        return s;
+      };
+      cx<double> s = mkc(0.0, 0.0);
+      if (n <= M) {
+        long long binom = 1;  // C(n, aa), exact for n <= 16
+        for (int aa = 0; aa <= n; ++aa) {
+          cx<double> tmp = cmul(Da64[(size_t)(n - aa) * N + p2], Ra(aa));
+          const int e = (n - aa) & 3;
+          if (e == 1) tmp = cmuli(tmp);
+          else if (e == 2) tmp = mkc(-tmp.re, -tmp.im);
+          else if (e == 3) tmp = mkc(tmp.im, -tmp.re);
+          s = s + cscale(tmp, (double)binom);
+          binom = binom * (n - aa) / (aa + 1);
+        }
+      } else {
+        const cx<double> t1 = cmul(Ra(1), Da64[p2]);
+        const cx<double> t2 = cmul(Ra(0), Da64[(size_t)N + p2]);
+        s = mkc(t1.re + t2.im, t1.im - t2.re);
+      }
+      if (p2 & 1) s = mkc(-s.re, -s.im);
+      re += s.re;
+      im += s.im;
     }
     sre[threadIdx.x] = re;
     sim[threadIdx.x] = im;

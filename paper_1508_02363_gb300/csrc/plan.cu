@@ -185,6 +185,13 @@ struct dbar_plan {
   cx<double>* tcoef = nullptr;  // [B][M+2] Taylor coefficients of the field in flight
   int* flag = nullptr;
   CycleState cs;
+  // s-step blocks (sstep > 1)
+  int sstep = 1;
+  int nchunk_b = 0, nitem_b = 0;
+  double* Hraw = nullptr;   // [B][m][m+1] unrotated Hessenberg columns
+  double* bcoef = nullptr;  // [B][S*S + (m+1)*S] sweep coefficients
+  double* bpart = nullptr;  // [B][nitem_b][nchunk_b] block dot partials
+  int* upd = nullptr;       // [B] slots whose block needs the update sweep
   // host staging
   int* h_active = nullptr;
   int* h_nsteps = nullptr;
@@ -357,10 +364,11 @@ PassArgs<double> base_args<double>(const dbar_plan* P) {
   a.ex = P->ex64;
   a.ey = P->ey64;
   a.inv2piL = P->inv2piL;
+  a.inv2piL_f = (float)P->inv2piL;
   a.sw = P->sw;
   a.fillscale = P->fillscale;
   a.partA = P->partA;
-  a.nblkA = P->N / a.g.lines;
+  a.nseg = seg_count(P->N);
   a.coef = P->tcoef;
   a.q_ss = P->per_slot_q ? P->n : 0;
   a.part = P->part2;
@@ -381,10 +389,11 @@ PassArgs<float> base_args<float>(const dbar_plan* P) {
   a.ex = P->ex32;
   a.ey = P->ey32;
   a.inv2piL = P->inv2piL;
+  a.inv2piL_f = (float)P->inv2piL;
   a.sw = P->sw;
   a.fillscale = P->fillscale;
   a.partA = P->partA;
-  a.nblkA = P->N / a.g.lines;
+  a.nseg = seg_count(P->N);
   a.coef = P->tcoef;
   a.q_ss = P->per_slot_q ? P->n : 0;
   a.part = P->part2;
@@ -405,10 +414,11 @@ PassArgs<dd> base_args<dd>(const dbar_plan* P) {
   a.ex = P->ex_dd;
   a.ey = P->ey_dd;
   a.inv2piL = P->inv2piL;
+  a.inv2piL_f = (float)P->inv2piL;
   a.sw = P->sw;
   a.fillscale = P->fillscale;
   a.partA = P->partA;
-  a.nblkA = P->N / a.g.lines;
+  a.nseg = seg_count(P->N);
   a.coef = P->tcoef;
   a.q_ss = P->per_slot_q ? P->n : 0;
   a.part = P->part2;
@@ -418,7 +428,7 @@ PassArgs<dd> base_args<dd>(const dbar_plan* P) {
 // Taylor coefficients of the fields pass A just read (k_coef), for pass B.
 template <typename T>
 static cudaError_t launch_coef_for(dbar_plan* P, const PassArgs<T>& a, int nb, cudaStream_t st) {
-  return launch_coef(P->partA, a.nblkA, P->M, P->N, P->fillscale, P->tcoef, nb, st);
+  return launch_coef(P->partA, std::is_same<T, float>::value, P->M, P->N, P->Da64, P->fillscale, P->tcoef, nb, st);
 }
 
 // One application of K (A S = S + K S) to nb fields: S (T) -> T1 -> T2 -> out (T).
@@ -546,11 +556,25 @@ static void account_cycle(dbar_plan* P, const int* act, const int* ns, int nb, i
     if (!act[s]) continue;
     ++nact;
     const int k = ns[s];
-    by[K_PASS_A] += 2.0 * F * k;
-    by[K_PASS_B] += 2.0 * F * k;
-    by[K_PASS_C] += 2.0 * F * k;
-    by[K_DOTS] += F * (k * 2.0 + k * (k - 1) / 2.0);
-    by[K_UPDATE] += F * (k * 3.0 + k * (k - 1) / 2.0);
+    if (P->sstep > 1) {
+      // per block at J = b S + 1: S applications of K, dots (J + S) F,
+      // update (J + 2S) F; the last block of the cycle counts in full
+      const int S = P->sstep, nblk = (k + S - 1) / S;
+      for (int b = 0; b < nblk; ++b) {
+        const int J = b * S + 1;
+        by[K_PASS_A] += 2.0 * F * S;
+        by[K_PASS_B] += 2.0 * F * S;
+        by[K_PASS_C] += 2.0 * F * S;
+        by[K_DOTS] += F * (J + S);
+        by[K_UPDATE] += F * (J + 2 * S);
+      }
+    } else {
+      by[K_PASS_A] += 2.0 * F * k;
+      by[K_PASS_B] += 2.0 * F * k;
+      by[K_PASS_C] += 2.0 * F * k;
+      by[K_DOTS] += F * (k * 2.0 + k * (k - 1) / 2.0);
+      by[K_UPDATE] += F * (k * 3.0 + k * (k - 1) / 2.0);
+    }
     by[K_XUPDATE] += F * k + 2.0 * F64;
     by[K_RES_A] += 2.0 * F64;
     by[K_RES_B] += 2.0 * F64;
@@ -591,9 +615,43 @@ static dbar_status begin_slots(dbar_plan* P, int nb, const int* hmask, cudaStrea
   return DBAR_OK;
 }
 
+// s-step blocks covering Krylov steps j0 <= j < j1 (multiples of S): per block,
+// S applications of K along the chain (written into basis slots J..J+S-1),
+// one dot sweep, the per-slot FP64 step, one update sweep.
+template <typename TI, int S>
+static dbar_status block_steps(dbar_plan* P, int nb, int j0, int j1, cudaStream_t st) {
+  const long long n = P->n;
+  const int m = P->m;
+  const long long vss = (long long)(m + 1) * n;
+  cx<TI>* V = reinterpret_cast<cx<TI>*>(P->V);
+  BlockArgs ba;
+  ba.n = n;
+  ba.mp1 = m + 1;
+  ba.nchunk = P->nchunk_b;
+  ba.nitem = P->nitem_b;
+  ba.run = P->cs.run;
+  ba.sigma = P->cs.sigma;
+  ba.bcoef = P->bcoef;
+  ba.part = P->bpart;
+  for (int c0 = j0; c0 < j1; c0 += S) {
+    const int J = c0 + 1;  // basis vectors v_0..v_{J-1} exist
+    for (int i = 0; i < S; ++i) {
+      dbar_status s = apply_K<TI>(P, V + (size_t)(J - 1 + i) * n, vss, i == 0 ? P->cs.sigma + (J - 1) : nullptr,
+                                  m + 1, V + (size_t)(J + i) * n, vss, P->cs.run, nb, st);
+      if (s != DBAR_OK) return s;
+    }
+    CK(timed(P, st, K_DOTS, [&] { return launch_bdots<TI, S>(ba, V, vss, J, nb, st); }));
+    CK(timed(P, st, K_SCALAR, [&] { return launch_bscalar<S>(ba, P->cs, P->Hraw, P->bcoef, P->upd, J, nb, st); }));
+    CK(timed(P, st, K_UPDATE, [&] { return launch_bupdate<TI, S>(ba, P->upd, V, vss, J, nb, st); }));
+  }
+  return DBAR_OK;
+}
+
 // Krylov steps j0 <= j < j1 of the current cycle for every running slot.
 template <typename TI>
 static dbar_status cycle_steps(dbar_plan* P, int nb, int j0, int j1, cudaStream_t st) {
+  if (P->sstep == 4) return block_steps<TI, 4>(P, nb, j0, j1, st);
+  if (P->sstep == 2) return block_steps<TI, 2>(P, nb, j0, j1, st);
   const long long n = P->n;
   const int m = P->m;
   const long long vss = (long long)(m + 1) * n;
@@ -791,6 +849,9 @@ static dbar_status check_params(const dbar_params* p) {
   if (p->autotune < 0 || p->autotune > 2) return fail(DBAR_EINVAL, "autotune must be 0, 1 or 2");
   if (p->resid_mode != DBAR_RESID_DOUBLE_FLOAT && p->resid_mode != DBAR_RESID_FP64)
     return fail(DBAR_EINVAL, "resid_mode must be DBAR_RESID_DOUBLE_FLOAT or DBAR_RESID_FP64");
+  if (p->sstep != 0 && p->sstep != 1 && p->sstep != 2 && p->sstep != 4)
+    return fail(DBAR_EINVAL, "sstep must be 0, 1, 2 or 4");
+  if (p->sstep > 1 && p->restart % p->sstep != 0) return fail(DBAR_EINVAL, "restart must be a multiple of sstep");
   return DBAR_OK;
 }
 
@@ -974,6 +1035,10 @@ size_t plan_slot_bytes(const dbar_params* p, int per_slot_q) {
   const size_t F64 = n * sizeof(cx<double>);
   const size_t Fi = n * (p->prec == DBAR_MIXED ? sizeof(cx<float>) : sizeof(cx<double>));
   size_t b = 4 * F64 + (size_t)(p->restart + 2) * Fi;  // x, b, T1, T2; basis, K v
+  const int S = p->sstep > 0 ? p->sstep : 4;  // upper bound for the automatic choice
+  if (S > 1)  // s-step partials, coefficients, unrotated Hessenberg
+    b += ((size_t)(p->restart + 1) * S + S * (S + 1) / 2) * ((n + KB_CHUNK - 1) / KB_CHUNK) * sizeof(double) +
+         ((size_t)S * (S + p->restart + 1) + (size_t)p->restart * (p->restart + 1)) * sizeof(double);
   if (per_slot_q) b += F64 + n * sizeof(cx<float>) + (p->prec == DBAR_MIXED ? F64 : 0);
   return b;
 }
@@ -1003,6 +1068,7 @@ dbar_status plan_create_ex(const dbar_params* p, int per_slot_q, dbar_plan** out
   P->M = p->M;
   P->MA = std::max(1, p->M);
   P->m = p->restart;
+  P->sstep = p->sstep > 0 ? p->sstep : (p->restart % 4 == 0 ? 4 : (p->restart % 2 == 0 ? 2 : 1));
   P->mixed = (p->prec == DBAR_MIXED);
   P->resid_dd = P->mixed && p->resid_mode == DBAR_RESID_DOUBLE_FLOAT;
   P->n = (long long)P->N * P->N;
@@ -1015,7 +1081,6 @@ dbar_status plan_create_ex(const dbar_params* p, int per_slot_q, dbar_plan** out
   const size_t F64 = (size_t)P->n * sizeof(cx<double>);
   const size_t Fi = (size_t)P->n * P->inner_elem();
   const int nchunk = (int)((P->n + KR_CHUNK - 1) / KR_CHUNK);
-  const int nblkA = P->N / std::min(make_geo<double>(P->N).lines, make_geo<float>(P->N).lines);
   const size_t per_slot = plan_slot_bytes(p, per_slot_q);
   int B = p->max_batch;
   if (B == 0) {
@@ -1074,7 +1139,7 @@ dbar_status plan_create_ex(const dbar_params* p, int per_slot_q, dbar_plan** out
   unsigned char* kb = nullptr;
   AL(kb, (size_t)B * Fi);
   P->KS = kb;
-  AL(P->partA, (size_t)B * nblkA * (P->M + 2));
+  AL(P->partA, (size_t)B * P->N * seg_count(P->N) * (P->MA + 1));
   AL(P->part, (size_t)B * (P->m + 1) * nchunk);
   AL(P->part2, (size_t)B * std::max(std::max(nchunk, P->N), 2 * (P->M + 2)));
   AL(P->coef, (size_t)B * (P->m + 1));
@@ -1097,6 +1162,15 @@ dbar_status plan_create_ex(const dbar_params* p, int per_slot_q, dbar_plan** out
   AL(c.itot, B);
   AL(c.ncyc, B);
   AL(P->dmask, B);
+  if (P->sstep > 1) {
+    const int S = P->sstep;
+    P->nchunk_b = (int)((n + KB_CHUNK - 1) / KB_CHUNK);
+    P->nitem_b = block_items(m + 1, S);
+    AL(P->Hraw, (size_t)B * m * (m + 1));
+    AL(P->bcoef, (size_t)B * (S * S + (m + 1) * S));
+    AL(P->bpart, (size_t)B * P->nitem_b * P->nchunk_b);
+    AL(P->upd, B);
+  }
 #undef AL
   c.m = m;
   c.max_iter = p->max_iter;
@@ -1286,14 +1360,12 @@ extern "C" dbar_status dbar_taylor(dbar_plan_t P, int nk, const void* S, double*
   if (nk == 0) return DBAR_OK;
   if (!S || !coef) return fail(DBAR_EINVAL, "NULL pointer");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  int nblkA;
   if (fp32) {
     PassArgs<float> a = base_args<float>(P);
     a.in = reinterpret_cast<const cx<float>*>(S);
     a.in_ss = P->n;
     a.out = P->T1;
     a.out_ss = P->n;
-    nblkA = a.nblkA;
     CK(launch_pass_a<float>(a, nk, st));
   } else {
     PassArgs<double> a = base_args<double>(P);
@@ -1301,11 +1373,10 @@ extern "C" dbar_status dbar_taylor(dbar_plan_t P, int nk, const void* S, double*
     a.in_ss = P->n;
     a.out = P->T1;
     a.out_ss = P->n;
-    nblkA = a.nblkA;
     CK(launch_pass_a<double>(a, nk, st));
   }
   cx<double>* dc = P->tcoef;
-  CK(launch_coef(P->partA, nblkA, P->M, P->N, 1.0, dc, nk, st));
+  CK(launch_coef(P->partA, fp32, P->M, P->N, P->Da64, 1.0, dc, nk, st));
   CK(cudaMemcpyAsync(coef, dc, (size_t)nk * (P->M + 2) * sizeof(cx<double>), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   return DBAR_OK;

@@ -39,10 +39,12 @@ struct PassArgs {
   const cx<T>* ex;       // [slot][N]  e^{-2 i k2 x_j}
   const cx<T>* ey;       // [slot][N]  e^{-2 i k1 y_j}
   double inv2piL;        // 1/(2 pi L)
+  float inv2piL_f;       // the same, rounded once on the host (FP32 pass A)
   double sw;             // 2 pi L^2 / N^2
   double fillscale;      // 1/(2 pi L^2), or 0 for the zero-fill reading
-  cx<double>* partA;     // [slot][nblkA][M+2]
-  int nblkA;
+  cx<double>* partA;     // [slot][p2][nseg][MA+1] row-moment partials (pass A -> k_coef);
+                         // stored as cx<float> by the FP32 pass A
+  int nseg;              // warp segments per row: seg_count(N)
   const cx<double>* coef;  // [slot][M+2] c_0..c_M, d' (k_coef output, read by pass B)
   double* part;          // [slot][gridDim.x] squared-norm partials (pass C)
 };
@@ -62,6 +64,24 @@ struct KryArgs {
   double* part;         // [slot][mp1][nchunk]
   double* part2;        // [slot][nchunk]
 };
+
+// s-step (block) Arnoldi sweeps (krylov.cuh)
+constexpr int KB_EPT = 4;                      // complex elements per thread (block sweeps)
+constexpr int KB_CHUNK = KR_THREADS * KB_EPT;  // elements per block of a block sweep
+constexpr double kBlockPivot = 1e-5;           // smallest accepted Cholesky pivot of the normalised Gram
+
+struct BlockArgs {
+  long long n;          // complex elements per vector
+  int mp1;              // basis vectors per slot (restart + 1)
+  int nchunk;           // blocks per slot (KB_CHUNK elements each)
+  int nitem;            // partial-sum items per slot (capacity): mp1 * S + S (S + 1) / 2
+  const int* run;       // per-slot flags
+  const double* sigma;  // [slot][mp1] scales of the stored basis vectors
+  const double* bcoef;  // [slot][S*S + mp1*S]: R^{-1} / ||p|| (S x S), then -sigma_r (C R^{-1})_{r,i}
+  double* part;         // [slot][nitem][nchunk]
+};
+
+__host__ __device__ constexpr int block_items(int J, int S) { return J * S + S * (S + 1) / 2; }
 
 struct CycleState {
   double* H;       // [slot][m][m+1]  column j holds rows 0..j+1

@@ -218,13 +218,47 @@ def test_full_size_mixed_workload_sampled_k_match_oracle(dbar, torch_cuda):
         assert rel(S[i].cpu().numpy(), o["S"]) < 1e-10, i
 
 
+@pytest.mark.parametrize("sstep", [2, 4])
+def test_sstep_blocks_match_oracle(dbar, sstep):
+    # s-step Arnoldi (chain of K = A - I per block, block Gram-Schmidt + Cholesky
+    # QR): the same Krylov spaces as one vector per sweep, so the same solution and
+    # about the same inner iterations (rounded up to whole blocks per cycle)
+    w = wl.mixed_1024(N=128, nk=4, L=5.0)
+    kw = dict(M=2, prec="mixed", restart=24, tol=1e-12, max_batch=4)
+    r = dbar.Plan(w.N, w.L, sstep=sstep, **kw).solve(w.Q, w.k)
+    ref = dbar.Plan(w.N, w.L, sstep=1, **kw).solve(w.Q, w.k)
+    assert r["status"] == dbar.DBAR_OK and np.all(r["resid"] <= 1e-12)
+    for i in range(w.k.size):
+        o = _oracle(w, i)
+        assert rel(r["S"][i], o["S"]) < 1e-10, i
+        assert rel(r["m"][i], o["m"]) < 1e-10, i
+    assert np.all(r["iters"][:, 0] <= ref["iters"][:, 0] + 2 * sstep * ref["iters"][:, 1])
+
+
+def test_sstep_fp64_ragged_batches_match_single_solves_and_oracle(dbar):
+    # FP64 s-step cycles; 7 k values through 3 slots (batches 3, 3, 1) and alone
+    w = wl.batched_fp64(N=64, nk_side=3)
+    k = w.k[:7]
+    kw = dict(M=2, prec="fp64", restart=32, tol=1e-13, sstep=4)
+    r = dbar.Plan(w.N, w.L, max_batch=3, **kw).solve(w.Q, k)
+    assert r["status"] == dbar.DBAR_OK
+    alone = dbar.Plan(w.N, w.L, max_batch=1, **kw)
+    for i in range(k.size):
+        ri = alone.solve(w.Q, k[i:i + 1])
+        assert np.array_equal(r["S"][i], ri["S"][0]), i     # slots never mix
+        o = orc.solve_cgo(w.Q, k[i], w.N, w.L, M=2, tol=1e-14)
+        assert rel(r["S"][i], o["S"]) < 1e-12, i
+
+
+@pytest.mark.parametrize("sstep", [1, 4])
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
-def test_graph_replayed_cycles_match_direct_launches(dbar, prec):
+def test_graph_replayed_cycles_match_direct_launches(dbar, prec, sstep):
     # a Krylov cycle captured once as a CUDA graph and replayed gives the same bits
     w = wl.batched_fp64(N=64, nk_side=3)
     res = []
     for graphs in (1, 0):
-        plan = dbar.Plan(w.N, w.L, M=2, prec=prec, restart=16, tol=1e-12, max_batch=5, graphs=graphs)
+        plan = dbar.Plan(w.N, w.L, M=2, prec=prec, restart=16, tol=1e-12, max_batch=5, graphs=graphs,
+                         sstep=sstep)
         res.append(plan.solve(w.Q, w.k[:7]))     # batches of 5 and a ragged 2
     assert np.array_equal(res[0]["S"], res[1]["S"]) and np.array_equal(res[0]["iters"], res[1]["iters"])
     assert res[0]["status"] == dbar.DBAR_OK
