@@ -51,8 +51,14 @@ def _compile(unit, verbose: bool) -> str:
     return obj
 
 
+STAMP = os.path.join(BUILD, "flags.txt")
+
+
 def _stale() -> bool:
     if not os.path.exists(LIB):
+        return True
+    # a change of the extra flags (DBAR_NVCC_FLAGS) rebuilds everything
+    if not os.path.exists(STAMP) or open(STAMP).read() != " ".join(EXTRA):
         return True
     t = os.path.getmtime(LIB)
     for f in os.listdir(CSRC):
@@ -74,6 +80,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as f:
+        f.write(" ".join(EXTRA))
     return LIB
 
 

@@ -124,6 +124,27 @@ __device__ __forceinline__ dd& operator+=(dd& a, dd b) {
   return a;
 }
 
+// Complex double-float sums and products.  With DBAR_DD_CALLS they become
+// out-of-line calls: the fully unrolled double-float transforms are large
+// enough to miss in the instruction cache.
+#ifdef DBAR_DD_CALLS
+#define DBAR_DD_FN __noinline__
+#else
+#define DBAR_DD_FN __forceinline__
+#endif
+template <>
+__device__ DBAR_DD_FN cx<dd> operator+(cx<dd> a, cx<dd> b) {
+  return mkc(a.re + b.re, a.im + b.im);
+}
+template <>
+__device__ DBAR_DD_FN cx<dd> operator-(cx<dd> a, cx<dd> b) {
+  return mkc(a.re - b.re, a.im - b.im);
+}
+template <>
+__device__ DBAR_DD_FN cx<dd> cmul(cx<dd> a, cx<dd> b) {
+  return mkc(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+
 template <>
 __device__ __forceinline__ cx<dd> ldg(const cx<dd>* p) {
   const float4 v = __ldg(reinterpret_cast<const float4*>(p));

@@ -7,12 +7,12 @@ namespace dbar {
 
 #define DBAR_SIZES(X) X(5) X(6) X(7) X(8) X(9) X(10) X(11)
 
-template <typename T, bool IN64>
+template <typename T>
 cudaError_t launch_pass_a(const PassArgs<T>& a, int nslots, cudaStream_t s) {
   if (nslots <= 0) return cudaSuccess;
   switch (a.g.logN) {
 #define CASE(L) \
-  case L: return launch_pass_a_n<T, L, IN64>(a, nslots, s);
+  case L: return launch_pass_a_n<T, L>(a, nslots, s);
     DBAR_SIZES(CASE)
 #undef CASE
   }
@@ -55,7 +55,7 @@ cudaError_t launch_pass_c(const PassArgs<T>& a, int nslots, cudaStream_t s) {
 }
 
 #define INST(T)                                                                         \
-  template cudaError_t launch_pass_a<T, false>(const PassArgs<T>&, int, cudaStream_t);  \
+  template cudaError_t launch_pass_a<T>(const PassArgs<T>&, int, cudaStream_t);  \
   template cudaError_t launch_pass_b<T, PB_MATVEC>(const PassArgs<T>&, int, cudaStream_t); \
   template cudaError_t launch_pass_b<T, PB_RHS>(const PassArgs<T>&, int, cudaStream_t);    \
   template cudaError_t launch_pass_b<T, PB_HOUT>(const PassArgs<T>&, int, cudaStream_t);   \
@@ -70,9 +70,11 @@ template cudaError_t launch_pass_c<double, double, PC_RHS>(const PassArgs<double
 template cudaError_t launch_pass_c<double, float, PC_RHS>(const PassArgs<double>&, int, cudaStream_t);
 template cudaError_t launch_pass_c<double, double, PC_RES>(const PassArgs<double>&, int, cudaStream_t);
 template cudaError_t launch_pass_c<double, float, PC_RES>(const PassArgs<double>&, int, cudaStream_t);
-template cudaError_t launch_pass_a<dd, true>(const PassArgs<dd>&, int, cudaStream_t);
+template cudaError_t launch_pass_a<dd>(const PassArgs<dd>&, int, cudaStream_t);
 template cudaError_t launch_pass_b<dd, PB_MATVEC>(const PassArgs<dd>&, int, cudaStream_t);
 template cudaError_t launch_pass_b<dd, PB_RHS>(const PassArgs<dd>&, int, cudaStream_t);
+template cudaError_t launch_pass_b<dd, PB_W>(const PassArgs<dd>&, int, cudaStream_t);
+template cudaError_t launch_pass_b<dd, PB_FWD>(const PassArgs<dd>&, int, cudaStream_t);
 template cudaError_t launch_pass_c<dd, float, PC_RHS>(const PassArgs<dd>&, int, cudaStream_t);
 template cudaError_t launch_pass_c<dd, float, PC_RES>(const PassArgs<dd>&, int, cudaStream_t);
 

@@ -22,10 +22,23 @@ cudaError_t launch_update(const KryArgs& a, cx<T>* V, long long vss, const cx<T>
 }
 template <typename T>
 cudaError_t launch_xupdate(long long n, int mp1, const int* nsteps, const double* ycoef, const cx<T>* V,
-                           long long vss, cx<double>* X, long long xss, int nslots, cudaStream_t s) {
+                           long long vss, void* X, int x_dd, long long xss, int nslots, cudaStream_t s) {
   if (nslots <= 0) return cudaSuccess;
   const int nchunk = (int)((n + KR_CHUNK - 1) / KR_CHUNK);
-  k_xupdate<T><<<dim3(nchunk, nslots), KR_THREADS, 0, s>>>(n, mp1, nsteps, ycoef, V, vss, X, xss);
+  if constexpr (std::is_same<T, float>::value) {
+    if (x_dd) {
+      k_xupdate<T, dd><<<dim3(nchunk, nslots), KR_THREADS, 0, s>>>(n, mp1, nsteps, ycoef, V, vss,
+                                                                   reinterpret_cast<cx<dd>*>(X), xss);
+      return cudaGetLastError();
+    }
+  }
+  k_xupdate<T, double><<<dim3(nchunk, nslots), KR_THREADS, 0, s>>>(n, mp1, nsteps, ycoef, V, vss,
+                                                                   reinterpret_cast<cx<double>*>(X), xss);
+  return cudaGetLastError();
+}
+cudaError_t launch_dd_to_fp64(const void* in, cx<double>* out, long long n, cudaStream_t s) {
+  const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+  k_dd_to_fp64<<<blocks, 256, 0, s>>>(reinterpret_cast<const cx<dd>*>(in), out, n);
   return cudaGetLastError();
 }
 
@@ -35,14 +48,14 @@ cudaError_t launch_xupdate(long long n, int mp1, const int* nsteps, const double
   template cudaError_t launch_update<T>(const KryArgs&, cx<T>*, long long, const cx<T>*, long long, int, int, \
                                         cudaStream_t);                                                    \
   template cudaError_t launch_xupdate<T>(long long, int, const int*, const double*, const cx<T>*, long long, \
-                                         cx<double>*, long long, int, cudaStream_t);
+                                         void*, int, long long, int, cudaStream_t);
 KR_INST(float)
 KR_INST(double)
 
 template <typename T, int S>
 cudaError_t launch_bdots(const BlockArgs& a, const cx<T>* V, long long vss, int J, int nslots, cudaStream_t s) {
   if (nslots <= 0) return cudaSuccess;
-  const size_t sm = (size_t)(KR_THREADS / 32) * block_items(J, S) * sizeof(double);
+  const size_t sm = (size_t)(KR_THREADS / 32) * block_items(J, S) * sizeof(T);
   k_bdots<T, S><<<dim3(a.nchunk, nslots), KR_THREADS, sm, s>>>(a, V, vss, J);
   return cudaGetLastError();
 }
@@ -145,13 +158,17 @@ cudaError_t launch_add_fields(const void* S, const void* KS, void* AS, long long
 }
 
 cudaError_t launch_coef(const cx<double>* partA, int part_fp32, int M, int N, const cx<double>* Da64,
-                        double fillscale, cx<double>* coef, int nslots, cudaStream_t s) {
+                        double fillscale, cx<double>* coefp, int* ticket, cx<double>* coef, int nslots,
+                        cudaStream_t s) {
   if (nslots <= 0) return cudaSuccess;
+  const int rows = coef_rows(N);
+  const dim3 grid(nslots, N / rows);
   if (part_fp32)
-    k_coef<float><<<nslots, 256, 0, s>>>(reinterpret_cast<const cx<float>*>(partA), seg_count(N), M > 1 ? M : 1, M,
-                                         N, Da64, fillscale, coef);
+    k_coef<float><<<grid, rows, 0, s>>>(reinterpret_cast<const cx<float>*>(partA), seg_count(N), M > 1 ? M : 1, M,
+                                        N, Da64, fillscale, coefp, ticket, coef);
   else
-    k_coef<double><<<nslots, 256, 0, s>>>(partA, seg_count(N), M > 1 ? M : 1, M, N, Da64, fillscale, coef);
+    k_coef<double><<<grid, rows, 0, s>>>(partA, seg_count(N), M > 1 ? M : 1, M, N, Da64, fillscale, coefp, ticket,
+                                         coef);
   return cudaGetLastError();
 }
 

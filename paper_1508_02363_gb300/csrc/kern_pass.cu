@@ -23,13 +23,13 @@ static cudaError_t set_smem(K kernel, size_t bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-template <typename T, int LOGN, bool IN64>
+template <typename T, int LOGN>
 cudaError_t launch_pass_a_n(const PassArgs<T>& a, int nslots, cudaStream_t s) {
   using G = RowG<T, LOGN>;
   const size_t sm = (size_t)G::LINES * G::P * sizeof(cx<T>);
-  cudaError_t e = set_smem(k_pass_a<T, LOGN, IN64>, sm);
+  cudaError_t e = set_smem(k_pass_a<T, LOGN>, sm);
   if (e != cudaSuccess) return e;
-  k_pass_a<T, LOGN, IN64><<<dim3(G::N / G::LINES, nslots), G::THREADS, sm, s>>>(a);
+  k_pass_a<T, LOGN><<<dim3(G::N / G::LINES, nslots), G::THREADS, sm, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -56,13 +56,15 @@ cudaError_t launch_pass_c_n(const PassArgs<T>& a, int nslots, cudaStream_t s) {
 typedef DBAR_T TT;
 #if DBAR_KIND == 2
 // double-float: the right-hand side and the true residual of the refinement
-template cudaError_t launch_pass_a_n<dd, DBAR_LOGN, true>(const PassArgs<dd>&, int, cudaStream_t);
+template cudaError_t launch_pass_a_n<dd, DBAR_LOGN>(const PassArgs<dd>&, int, cudaStream_t);
 template cudaError_t launch_pass_b_n<dd, DBAR_LOGN, PB_MATVEC, 0>(const PassArgs<dd>&, int, cudaStream_t);
 template cudaError_t launch_pass_b_n<dd, DBAR_LOGN, PB_RHS, 0>(const PassArgs<dd>&, int, cudaStream_t);
+template cudaError_t launch_pass_b_n<dd, DBAR_LOGN, PB_W, 0>(const PassArgs<dd>&, int, cudaStream_t);
+template cudaError_t launch_pass_b_n<dd, DBAR_LOGN, PB_FWD, 0>(const PassArgs<dd>&, int, cudaStream_t);
 template cudaError_t launch_pass_c_n<dd, float, DBAR_LOGN, PC_RHS>(const PassArgs<dd>&, int, cudaStream_t);
 template cudaError_t launch_pass_c_n<dd, float, DBAR_LOGN, PC_RES>(const PassArgs<dd>&, int, cudaStream_t);
 #else
-template cudaError_t launch_pass_a_n<TT, DBAR_LOGN, false>(const PassArgs<TT>&, int, cudaStream_t);
+template cudaError_t launch_pass_a_n<TT, DBAR_LOGN>(const PassArgs<TT>&, int, cudaStream_t);
 template cudaError_t launch_pass_b_n<TT, DBAR_LOGN, PB_MATVEC, 0>(const PassArgs<TT>&, int, cudaStream_t);
 template cudaError_t launch_pass_b_n<TT, DBAR_LOGN, PB_RHS, 0>(const PassArgs<TT>&, int, cudaStream_t);
 template cudaError_t launch_pass_b_n<TT, DBAR_LOGN, PB_HOUT, 0>(const PassArgs<TT>&, int, cudaStream_t);

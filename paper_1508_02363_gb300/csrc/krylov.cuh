@@ -214,13 +214,17 @@ static __global__ void k_solve_y(CycleState c, int nslots) {
   c.nsteps[slot] = ns;
 }
 
-// x += sum_i ycoef_i v~_i   (x in FP64, basis in T).  The correction is
+// x += sum_i ycoef_i v~_i   (basis in T; x stored as XS: FP64, or double-float
+// pairs for the mixed path's double-float residual).  The correction is
 // accumulated in T (it carries the precision of the basis) and added to x once.
-template <typename T>
+__device__ __forceinline__ cx<double> xadd(cx<double> x, cx<double> d) { return x + d; }
+__device__ __forceinline__ cx<double> xadd(cx<double> x, cx<float> d) { return x + ccast<double>(d); }
+__device__ __forceinline__ cx<dd> xadd(cx<dd> x, cx<float> d) { return mkc(x.re + dd(d.re), x.im + dd(d.im)); }
+template <typename T, typename XS>
 __global__ void __launch_bounds__(KR_THREADS) k_xupdate(long long n, int mp1, const int* __restrict__ nsteps,
                                                          const double* __restrict__ ycoef,
                                                          const cx<T>* __restrict__ V, long long vss,
-                                                         cx<double>* __restrict__ X, long long xss) {
+                                                         cx<XS>* __restrict__ X, long long xss) {
   const int slot = blockIdx.y;
   const int ns = nsteps[slot];
   if (ns == 0) return;
@@ -244,9 +248,17 @@ __global__ void __launch_bounds__(KR_THREADS) k_xupdate(long long n, int mp1, co
   for (int e = 0; e < KR_EPT; ++e) {
     const long long idx = base + (long long)e * KR_THREADS;
     if (idx < n) {
-      cx<double>* xp = X + (size_t)slot * xss + idx;
-      *xp = *xp + ccast<double>(acc[e]);
+      cx<XS>* xp = X + (size_t)slot * xss + idx;
+      *xp = xadd(*xp, acc[e]);
     }
+  }
+}
+
+// FP64 copy of double-float fields (solution read-out)
+__global__ void k_dd_to_fp64(const cx<dd>* __restrict__ in, cx<double>* __restrict__ out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const cx<dd> v = in[i];
+    out[i] = mkc((double)v.re, (double)v.im);
   }
 }
 
@@ -268,6 +280,7 @@ static __global__ void __launch_bounds__(KR_THREADS) k_cycle_start(CycleState c,
   const double beta = sqrt(s);
   if (first) {
     c.bnorm[slot] = beta;
+    c.nscale[slot] = beta > 0.0 ? (float)exp2(-(double)ilogb(beta)) : 1.f;
     c.itot[slot] = 0;
     c.ncyc[slot] = 0;
   }
@@ -340,7 +353,9 @@ __device__ __forceinline__ T warp_reduce_scatter(const T (&s)[S], int lane) {
 template <typename T, int S>
 __global__ void __launch_bounds__(KR_THREADS) k_bdots(const BlockArgs a, const cx<T>* __restrict__ V, long long vss,
                                                        int J) {
-  extern __shared__ double red[];  // [KR_THREADS / 32][nit]
+  // [KR_THREADS / 32][nit] warp totals in T (FP32 for the inner solve: no FP64 per warp)
+  extern __shared__ __align__(16) unsigned char bd_smem[];
+  T* redf = reinterpret_cast<T*>(bd_smem);
   const int slot = blockIdx.y;
   if (!a.run[slot]) return;
   const int nit = block_items(J, S);
@@ -369,7 +384,7 @@ __global__ void __launch_bounds__(KR_THREADS) k_bdots(const BlockArgs a, const c
       }
     }
     const T d = warp_reduce_scatter<S>(s, lane);
-    if ((lane & (32 / S - 1)) == 0) red[wid * nit + r * S + lane / (32 / S)] = (double)d;
+    if ((lane & (32 / S - 1)) == 0) redf[wid * nit + r * S + lane / (32 / S)] = d;
   }
   int it = J * S;
 #pragma unroll
@@ -380,14 +395,14 @@ __global__ void __launch_bounds__(KR_THREADS) k_bdots(const BlockArgs a, const c
 #pragma unroll
       for (int e = 0; e < KB_EPT; ++e) s += w[i][e].re * w[l][e].re + w[i][e].im * w[l][e].im;
       const T d = warp_sum_t(s, 32);
-      if (lane == 0) red[wid * nit + it] = (double)d;
+      if (lane == 0) redf[wid * nit + it] = d;
       ++it;
     }
   __syncthreads();
   for (int q = threadIdx.x; q < nit; q += blockDim.x) {
-    double s = 0.0;
-    for (int w2 = 0; w2 < KR_THREADS / 32; ++w2) s += red[w2 * nit + q];
-    a.part[((size_t)slot * a.nitem + q) * a.nchunk + blockIdx.x] = s;
+    T s = 0;
+    for (int w2 = 0; w2 < KR_THREADS / 32; ++w2) s += redf[w2 * nit + q];
+    a.part[((size_t)slot * a.nitem + q) * a.nchunk + blockIdx.x] = (double)s;
   }
 }
 

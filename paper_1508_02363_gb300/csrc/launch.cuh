@@ -36,9 +36,11 @@ inline int row_blocks(int N) { return N / row_lines(ilog2(N)); }
 // warp segments of one row line (N/16 threads, at most 32 per segment): the
 // number of row-moment partials pass A writes per row and moment
 inline int seg_count(int N) { return N / 16 >= 32 ? N / 512 : 1; }
+// rows per block of k_coef (one row per thread): N/8, at least 32
+inline int coef_rows(int N) { return N / 8 >= 32 ? N / 8 : 32; }
 
 // per-size launchers (kern_pass.cu, one translation unit per precision and size)
-template <typename T, int LOGN, bool IN64>
+template <typename T, int LOGN>
 cudaError_t launch_pass_a_n(const PassArgs<T>& a, int nslots, cudaStream_t s);
 template <typename T, int LOGN, int MODE, int CV>
 cudaError_t launch_pass_b_n(const PassArgs<T>& a, int nslots, cudaStream_t s);
@@ -46,7 +48,7 @@ template <typename T, typename TO, int LOGN, int MODE>
 cudaError_t launch_pass_c_n(const PassArgs<T>& a, int nslots, cudaStream_t s);
 
 // size dispatch (dispatch.cu)
-template <typename T, bool IN64 = false>
+template <typename T>
 cudaError_t launch_pass_a(const PassArgs<T>& a, int nslots, cudaStream_t s);
 template <typename T, int MODE>
 cudaError_t launch_pass_b(const PassArgs<T>& a, int nslots, cudaStream_t s);
@@ -61,7 +63,9 @@ cudaError_t launch_update(const KryArgs& a, cx<T>* V, long long vss, const cx<T>
                           int nslots, cudaStream_t s);
 template <typename T>
 cudaError_t launch_xupdate(long long n, int mp1, const int* nsteps, const double* ycoef, const cx<T>* V,
-                           long long vss, cx<double>* X, long long xss, int nslots, cudaStream_t s);
+                           long long vss, void* X, int x_dd, long long xss, int nslots, cudaStream_t s);
+// FP64 copy of n double-float complex values
+cudaError_t launch_dd_to_fp64(const void* in, cx<double>* out, long long n, cudaStream_t s);
 
 template <typename T, int S>
 cudaError_t launch_bdots(const BlockArgs& a, const cx<T>* V, long long vss, int J, int nslots, cudaStream_t s);
@@ -83,9 +87,12 @@ cudaError_t launch_load_q(const cx<double>* Q, cx<double>* Q64, cx<float>* Q32, 
 cudaError_t launch_delta_build(const cx<double>* V, const cx<double>* W, cx<double>* D64, cx<float>* D32, int N,
                                int nfields, cudaStream_t s);
 cudaError_t launch_add_fields(const void* S, const void* KS, void* AS, long long n, int fp32, cudaStream_t s);
-// part_fp32: partials written by the FP32 pass A (cx<float>), else cx<double>
+// part_fp32: partials written by the FP32 pass A (cx<float>), else cx<double>.
+// coefp: [slots][N / coef_rows(N)][M+2] block partials; ticket: [slots] zeroed
+// counters (re-armed by the kernel).
 cudaError_t launch_coef(const cx<double>* partA, int part_fp32, int M, int N, const cx<double>* Da64,
-                        double fillscale, cx<double>* coef, int nslots, cudaStream_t s);
+                        double fillscale, cx<double>* coefp, int* ticket, cx<double>* coef, int nslots,
+                        cudaStream_t s);
 cudaError_t launch_cast_fields(const cx<double>* in, cx<float>* out, long long n, cudaStream_t s);
 cudaError_t launch_split_fields(const cx<double>* in, cx<dd>* out, long long n, cudaStream_t s);
 cudaError_t launch_check_finite(const double* p, long long n, int* flag, cudaStream_t s);

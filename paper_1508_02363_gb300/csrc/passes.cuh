@@ -77,7 +77,7 @@ struct ColG {
 // ---------------------------------------------------------------------------
 // Pass A: rows of a Fourier field.
 // ---------------------------------------------------------------------------
-template <typename T, int LOGN, bool IN64>
+template <typename T, int LOGN>
 __global__ void __launch_bounds__(RowG<T, LOGN>::THREADS, RowG<T, LOGN>::MINB) k_pass_a(const PassArgs<T> a) {
   using G = RowG<T, LOGN>;
   constexpr int N = G::N, TPL = G::TPL, LINES = G::LINES, P = G::P;
@@ -91,11 +91,7 @@ __global__ void __launch_bounds__(RowG<T, LOGN>::THREADS, RowG<T, LOGN>::MINB) k
   cx<T>* sl = reinterpret_cast<cx<T>*>(smem) + line * P;
   const T sc = a.in_scale ? (T)a.in_scale[(size_t)slot * a.in_scale_ss] : (T)1;
   cx<T> v[16];
-  if constexpr (IN64) {
-    const cx<double>* src = a.in64 + (size_t)slot * a.in_ss + (size_t)p2 * N + t;
-#pragma unroll
-    for (int q = 0; q < 16; ++q) v[q] = cscale(ccast<T>(ldg(src + q * TPL)), sc);
-  } else {
+  {
     const cx<T>* src = a.in + (size_t)slot * a.in_ss + (size_t)p2 * N + t;
 #pragma unroll
     for (int q = 0; q < 16; ++q) v[q] = cscale(ldg(src + q * TPL), sc);
@@ -184,12 +180,12 @@ __global__ void __launch_bounds__(ColG<T, LOGN, CV>::THREADS, ColG<T, LOGN, CV>:
 #pragma unroll
     for (int q = 0; q < 16; ++q) v[q] = ldg(src + (size_t)q * TPL * N);
     // Taylor coefficients of this slot (k_coef), issued after the field loads
-    if ((MODE == PB_MATVEC || MODE == PB_HOUT) && threadIdx.x < M + 2)
+    if ((MODE == PB_MATVEC || MODE == PB_HOUT || MODE == PB_W) && threadIdx.x < M + 2)
       coef[threadIdx.x] = ccast<T>(a.coef[(size_t)slot * (M + 2) + threadIdx.x]);
     if (MODE == PB_FWD) fft_line<T, LOGN, false>(v, sl, t, a.tw);
     else fft_line<T, LOGN, true>(v, sl, t, a.tw);
   }
-  if (MODE == PB_MATVEC || MODE == PB_HOUT) {
+  if (MODE == PB_MATVEC || MODE == PB_HOUT || MODE == PB_W) {
     __syncthreads();  // coefficients visible
     // h = u + sum_n c_n Delta_n + d'  (n outer, 16 independent loads per n)
     const cx<T> fill = coef[M + 1];
@@ -202,7 +198,7 @@ __global__ void __launch_bounds__(ColG<T, LOGN, CV>::THREADS, ColG<T, LOGN, CV>:
       for (int q = 0; q < 16; ++q) v[q] = v[q] + cmul(cn, ldg(D + (size_t)q * TPL * N));
     }
   }
-  if (MODE == PB_MATVEC || MODE == PB_RHS) {
+  if (MODE == PB_MATVEC || MODE == PB_RHS || MODE == PB_W) {
     // w = (2 pi L^2/N^2) E_k Q conj(h)   (right-hand side: E_k Q)
     const cx<T> exv = cscale(ldg(a.ex + (size_t)slot * N + j1), (T)a.sw);
     const cx<T>* EY = a.ey + (size_t)slot * N + t;
@@ -212,7 +208,7 @@ __global__ void __launch_bounds__(ColG<T, LOGN, CV>::THREADS, ColG<T, LOGN, CV>:
       const cx<T> eq = cmul(cmul(exv, ldg(EY + q * TPL)), ldg(QC + (size_t)q * TPL * N));
       v[q] = (MODE == PB_RHS) ? eq : cmulc(eq, v[q]);
     }
-    fft_line<T, LOGN, false>(v, sl, t, a.tw);
+    if (MODE != PB_W) fft_line<T, LOGN, false>(v, sl, t, a.tw);
   }
   cx<T>* dst = reinterpret_cast<cx<T>*>(a.out) + (size_t)slot * a.out_ss + (size_t)t * N + j1;
 #pragma unroll
@@ -226,48 +222,51 @@ __global__ void __launch_bounds__(ColG<T, LOGN, CV>::THREADS, ColG<T, LOGN, CV>:
 //   n = M+1: R_1(p2) D_0(p2) - i R_0(p2) D_1(p2)          (fill value dS/dxi(0))
 // and coef[slot] = c_0..c_M, then the fill d' = d * fillscale (taylor_coef).
 // partA: [slot][p2][seg][a], the a = 0 moment in segment 0 only.
+// Grid (slots, KC): block b sums rows [b, b+1) * blockDim.x (one row per
+// thread; the FP64 work is spread over many SMs), writes its M+2 partial sums,
+// and the last block of a slot to finish (atomic ticket) adds the KC partials
+// in block order, scales them and re-arms the slot's ticket.
 // ---------------------------------------------------------------------------
+constexpr int KC_MAXM = 16;
 template <typename PT>
 static __global__ void __launch_bounds__(256) k_coef(const cx<PT>* __restrict__ partA, int nseg, int MA, int M,
                                               int N, const cx<double>* __restrict__ Da64, double fillscale,
+                                              cx<double>* __restrict__ coefp, int* __restrict__ ticket,
                                               cx<double>* __restrict__ coef) {
   __shared__ double sre[256], sim[256];
-  const int slot = blockIdx.x;
+  __shared__ bool last;
+  const int slot = blockIdx.x, KC = gridDim.y;
   const int stride = nseg * (MA + 1);
-  const cx<PT>* pa = partA + (size_t)slot * N * stride;
+  const int p2 = blockIdx.y * blockDim.x + threadIdx.x;
+  const cx<PT>* R = partA + ((size_t)slot * N + p2) * stride;
+  auto Ra = [&](int aa) {
+    cx<double> s = ccast<double>(R[aa]);
+    if (aa > 0)
+      for (int sg = 1; sg < nseg; ++sg) s = s + ccast<double>(R[sg * (MA + 1) + aa]);
+    return s;
+  };
+  cx<double>* cp = coefp + ((size_t)slot * KC + blockIdx.y) * (M + 2);
   for (int n = 0; n < M + 2; ++n) {
-    double re = 0.0, im = 0.0;
-    for (int p2 = threadIdx.x; p2 < N; p2 += blockDim.x) {
-      const cx<PT>* R = pa + (size_t)p2 * stride;
-      auto Ra = [&](int aa) {
-        cx<double> s = ccast<double>(R[aa]);
-        if (aa > 0)
-          for (int sg = 1; sg < nseg; ++sg) s = s + ccast<double>(R[sg * (MA + 1) + aa]);
-        return s;
-      };
-      cx<double> s = mkc(0.0, 0.0);
-      if (n <= M) {
-        long long binom = 1;  // C(n, aa), exact for n <= 16
-        for (int aa = 0; aa <= n; ++aa) {
-          cx<double> tmp = cmul(Da64[(size_t)(n - aa) * N + p2], Ra(aa));
-          const int e = (n - aa) & 3;
-          if (e == 1) tmp = cmuli(tmp);
-          else if (e == 2) tmp = mkc(-tmp.re, -tmp.im);
-          else if (e == 3) tmp = mkc(tmp.im, -tmp.re);
-          s = s + cscale(tmp, (double)binom);
-          binom = binom * (n - aa) / (aa + 1);
-        }
-      } else {
-        const cx<double> t1 = cmul(Ra(1), Da64[p2]);
-        const cx<double> t2 = cmul(Ra(0), Da64[(size_t)N + p2]);
-        s = mkc(t1.re + t2.im, t1.im - t2.re);
+    cx<double> s = mkc(0.0, 0.0);
+    if (n <= M) {
+      long long binom = 1;  // C(n, aa), exact for n <= 16
+      for (int aa = 0; aa <= n; ++aa) {
+        cx<double> tmp = cmul(Da64[(size_t)(n - aa) * N + p2], Ra(aa));
+        const int e = (n - aa) & 3;
+        if (e == 1) tmp = cmuli(tmp);
+        else if (e == 2) tmp = mkc(-tmp.re, -tmp.im);
+        else if (e == 3) tmp = mkc(tmp.im, -tmp.re);
+        s = s + cscale(tmp, (double)binom);
+        binom = binom * (n - aa) / (aa + 1);
       }
-      if (p2 & 1) s = mkc(-s.re, -s.im);
-      re += s.re;
-      im += s.im;
+    } else {
+      const cx<double> t1 = cmul(Ra(1), Da64[p2]);
+      const cx<double> t2 = cmul(Ra(0), Da64[(size_t)N + p2]);
+      s = mkc(t1.re + t2.im, t1.im - t2.re);
     }
-    sre[threadIdx.x] = re;
-    sim[threadIdx.x] = im;
+    if (p2 & 1) s = mkc(-s.re, -s.im);
+    sre[threadIdx.x] = s.re;
+    sim[threadIdx.x] = s.im;
     __syncthreads();
     for (int w = blockDim.x / 2; w > 0; w >>= 1) {
       if ((int)threadIdx.x < w) {
@@ -276,9 +275,25 @@ static __global__ void __launch_bounds__(256) k_coef(const cx<PT>* __restrict__ 
       }
       __syncthreads();
     }
-    if (threadIdx.x == 0) coef[(size_t)slot * (M + 2) + n] = taylor_coef(mkc(sre[0], sim[0]), n, M, N, fillscale);
+    if (threadIdx.x == 0) cp[n] = mkc(sre[0], sim[0]);
     __syncthreads();
   }
+  if (threadIdx.x == 0) {
+    __threadfence();  // this block's partials are visible before its ticket
+    last = atomicAdd(ticket + slot, 1) == KC - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int n = threadIdx.x; n < M + 2; n += blockDim.x) {
+    cx<double> s = mkc(0.0, 0.0);
+    for (int b = 0; b < KC; ++b) {
+      const double* q = reinterpret_cast<const double*>(coefp + ((size_t)slot * KC + b) * (M + 2) + n);
+      s = s + mkc(__ldcg(q), __ldcg(q + 1));
+    }
+    coef[(size_t)slot * (M + 2) + n] = taylor_coef(s, n, M, N, fillscale);
+  }
+  if (threadIdx.x == 0) ticket[slot] = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -302,7 +317,14 @@ __global__ void __launch_bounds__(RowG<T, LOGN>::THREADS, RowG<T, LOGN>::MINB) k
 #pragma unroll
   for (int q = 0; q < 16; ++q) v[q] = ldg(src + q * TPL);
   fft_line<T, LOGN, MODE == PC_INV>(v, sl, t, a.tw);
-  double nrm = 0.0;
+  // squared-norm partials.  FP64 for FP64 fields and for the right-hand side
+  // (once per solve); the double-float residual sums FP32 squares of r scaled
+  // by the slot's power-of-two 1/||b|| (no FP64 per element on GB300's small
+  // FP64 pipe, no underflow of small residuals), unscaled once per block.
+  constexpr bool NF32 = !std::is_same<T, double>::value && MODE == PC_RES;
+  using NT = typename std::conditional<NF32, float, double>::type;
+  const float nsc = NF32 ? a.nscale[slot] : 1.f;
+  NT nrm = 0;
   const size_t rowoff = (size_t)p2 * N + t;
 #pragma unroll
   for (int q = 0; q < 16; ++q) {
@@ -316,27 +338,34 @@ __global__ void __launch_bounds__(RowG<T, LOGN>::THREADS, RowG<T, LOGN>::MINB) k
     if (MODE == PC_KS || MODE == PC_FWD || MODE == PC_INV) {
       reinterpret_cast<cx<T>*>(a.out)[(size_t)slot * a.out_ss + idx] = y;
     } else if (MODE == PC_RHS) {
-      reinterpret_cast<cx<double>*>(a.out)[(size_t)slot * a.out_ss + idx] = ccast<double>(y);
+      reinterpret_cast<cx<T>*>(a.out)[(size_t)slot * a.out_ss + idx] = y;
       reinterpret_cast<cx<TO>*>(a.out2)[(size_t)slot * a.out2_ss + idx] = ccast<TO>(y);
-      nrm += (double)y.re * (double)y.re + (double)y.im * (double)y.im;
+      const double yr = (double)y.re, yi = (double)y.im;
+      nrm += yr * yr + yi * yi;
     } else {  // PC_RES
-      const cx<double> bb = a.b[(size_t)slot * a.f_ss + idx];
-      const cx<double> xx = a.x[(size_t)slot * a.f_ss + idx];
-      const cx<double> r = mkc(bb.re - xx.re - (double)y.re, bb.im - xx.im - (double)y.im);
+      const cx<T> bb = a.b[(size_t)slot * a.f_ss + idx];
+      const cx<T> xx = a.x[(size_t)slot * a.f_ss + idx];
+      const cx<T> r = mkc(bb.re - xx.re - y.re, bb.im - xx.im - y.im);
       reinterpret_cast<cx<TO>*>(a.out2)[(size_t)slot * a.out2_ss + idx] = ccast<TO>(r);
-      nrm += r.re * r.re + r.im * r.im;
+      if constexpr (NF32) {
+        const float rr = (float)r.re * nsc, ri = (float)r.im * nsc;
+        nrm += rr * rr + ri * ri;
+      } else {
+        const double rr = (double)r.re, ri = (double)r.im;
+        nrm += rr * rr + ri * ri;
+      }
     }
   }
   if (MODE == PC_RHS || MODE == PC_RES) {
-    __shared__ double wred[32];
-    nrm = warp_sum(nrm, 32);
+    __shared__ NT wred[32];
+    nrm = warp_sum_t(nrm, 32);
     __syncthreads();
     if ((threadIdx.x & 31) == 0) wred[threadIdx.x >> 5] = nrm;
     __syncthreads();
     if (threadIdx.x == 0) {
-      double s = 0.0;
+      NT s = 0;
       for (int w = 0; w < G::THREADS / 32; ++w) s += wred[w];
-      a.part[(size_t)slot * gridDim.x + blockIdx.x] = s;
+      a.part[(size_t)slot * gridDim.x + blockIdx.x] = NF32 ? (double)s / ((double)nsc * (double)nsc) : (double)s;
     }
   }
 }

@@ -172,6 +172,8 @@ struct dbar_plan {
   cx<dd>* ex_dd = nullptr;
   cx<dd>* ey_dd = nullptr;
   // workspaces
+  // x and b: FP64, or double-float pairs (cx<dd>, same size) when the mixed
+  // path's residual runs in double-float (resid_dd) -- see solution_fp64()
   cx<double>* x64 = nullptr;
   cx<double>* b64 = nullptr;
   void* T1 = nullptr;
@@ -183,6 +185,8 @@ struct dbar_plan {
   double* part2 = nullptr;
   double* coef = nullptr;
   cx<double>* tcoef = nullptr;  // [B][M+2] Taylor coefficients of the field in flight
+  cx<double>* coefp = nullptr;  // [B][N / coef_rows(N)][M+2] k_coef block partials
+  int* ticket = nullptr;        // [B] k_coef completion counters (zero between launches)
   int* flag = nullptr;
   CycleState cs;
   // s-step blocks (sstep > 1)
@@ -372,6 +376,7 @@ PassArgs<double> base_args<double>(const dbar_plan* P) {
   a.coef = P->tcoef;
   a.q_ss = P->per_slot_q ? P->n : 0;
   a.part = P->part2;
+  a.nscale = P->cs.nscale;
   return a;
 }
 template <>
@@ -397,6 +402,7 @@ PassArgs<float> base_args<float>(const dbar_plan* P) {
   a.coef = P->tcoef;
   a.q_ss = P->per_slot_q ? P->n : 0;
   a.part = P->part2;
+  a.nscale = P->cs.nscale;
   return a;
 }
 
@@ -422,13 +428,15 @@ PassArgs<dd> base_args<dd>(const dbar_plan* P) {
   a.coef = P->tcoef;
   a.q_ss = P->per_slot_q ? P->n : 0;
   a.part = P->part2;
+  a.nscale = P->cs.nscale;
   return a;
 }
 
 // Taylor coefficients of the fields pass A just read (k_coef), for pass B.
 template <typename T>
 static cudaError_t launch_coef_for(dbar_plan* P, const PassArgs<T>& a, int nb, cudaStream_t st) {
-  return launch_coef(P->partA, std::is_same<T, float>::value, P->M, P->N, P->Da64, P->fillscale, P->tcoef, nb, st);
+  return launch_coef(P->partA, std::is_same<T, float>::value, P->M, P->N, P->Da64, P->fillscale, P->coefp,
+                     P->ticket, P->tcoef, nb, st);
 }
 
 // One application of K (A S = S + K S) to nb fields: S (T) -> T1 -> T2 -> out (T).
@@ -503,23 +511,27 @@ static dbar_status true_residual_t(dbar_plan* P, int nb, cudaStream_t st) {
   a.in_ss = P->n;
   a.out = P->T1;
   a.out_ss = P->n;
-  if constexpr (std::is_same<TC, double>::value) {
-    a.in = P->x64;
-    CK(timed(P, st, K_RES_A, [&] { return launch_pass_a<TC, false>(a, nb, st); }));
-  } else {
-    a.in64 = P->x64;
-    CK(timed(P, st, K_RES_A, [&] { return launch_pass_a<TC, true>(a, nb, st); }));
-  }
+  a.in = reinterpret_cast<const cx<TC>*>(P->x64);  // x stored in TC (FP64 or double-float)
+  CK(timed(P, st, K_RES_A, [&] { return launch_pass_a<TC>(a, nb, st); }));
   CK(timed(P, st, K_SCALAR, [&] { return launch_coef_for(P, a, nb, st); }));
   a.in = reinterpret_cast<const cx<TC>*>(P->T1);
   a.out = P->T2;
-  CK(timed(P, st, K_RES_B, [&] { return launch_pass_b<TC, PB_MATVEC>(a, nb, st); }));
+  if constexpr (std::is_same<TC, dd>::value) {
+    // two launches (column IDFT + pointwise, then column DFT): the fused
+    // double-float column pass is too large for the instruction cache
+    // (the column DFT runs in place: each block owns its columns)
+    CK(timed(P, st, K_RES_B, [&] { return launch_pass_b<TC, PB_W>(a, nb, st); }));
+    a.in = reinterpret_cast<const cx<TC>*>(P->T2);
+    CK(timed(P, st, K_RES_B, [&] { return launch_pass_b<TC, PB_FWD>(a, nb, st); }));
+  } else {
+    CK(timed(P, st, K_RES_B, [&] { return launch_pass_b<TC, PB_MATVEC>(a, nb, st); }));
+  }
   a.in = reinterpret_cast<const cx<TC>*>(P->T2);
   a.out = nullptr;
   a.out2 = P->V;
   a.out2_ss = (long long)(P->m + 1) * P->n;
-  a.b = P->b64;
-  a.x = P->x64;
+  a.b = reinterpret_cast<const cx<TC>*>(P->b64);
+  a.x = reinterpret_cast<const cx<TC>*>(P->x64);
   a.f_ss = P->n;
   CK(timed(P, st, K_RES_C, [&] { return launch_pass_c<TC, TI, PC_RES>(a, nb, st); }));
   return DBAR_OK;
@@ -687,7 +699,7 @@ static dbar_status cycle_tail(dbar_plan* P, int nb, cudaStream_t st) {
   CK(timed(P, st, K_SCALAR, [&] { return launch_solve_y(P->cs, nb, st); }));
   CK(cudaMemcpyAsync(P->h_nsteps, P->cs.nsteps, nb * sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(timed(P, st, K_XUPDATE, [&] {
-    return launch_xupdate<TI>(n, m + 1, P->cs.nsteps, P->cs.ycoef, V, vss, P->x64, n, nb, st);
+    return launch_xupdate<TI>(n, m + 1, P->cs.nsteps, P->cs.ycoef, V, vss, P->x64, P->resid_dd, n, nb, st);
   }));
   dbar_status s = true_residual<TI>(P, nb, st);
   if (s != DBAR_OK) return s;
@@ -1144,6 +1156,8 @@ dbar_status plan_create_ex(const dbar_params* p, int per_slot_q, dbar_plan** out
   AL(P->part2, (size_t)B * std::max(std::max(nchunk, P->N), 2 * (P->M + 2)));
   AL(P->coef, (size_t)B * (P->m + 1));
   AL(P->tcoef, (size_t)B * (P->M + 2));
+  AL(P->coefp, (size_t)B * (P->N / coef_rows(P->N)) * (P->M + 2));
+  AL(P->ticket, B);
   AL(P->flag, 4);
   CycleState& c = P->cs;
   const int m = P->m;
@@ -1155,6 +1169,7 @@ dbar_status plan_create_ex(const dbar_params* p, int per_slot_q, dbar_plan** out
   AL(c.ycoef, (size_t)B * (m + 1));
   AL(c.thr, B);
   AL(c.bnorm, B);
+  AL(c.nscale, B);
   AL(c.resid, B);
   AL(c.run, B);
   AL(c.active, B);
@@ -1172,6 +1187,10 @@ dbar_status plan_create_ex(const dbar_params* p, int per_slot_q, dbar_plan** out
     AL(P->upd, B);
   }
 #undef AL
+  if (cudaMemset(P->ticket, 0, (size_t)B * sizeof(int)) != cudaSuccess) {
+    delete P;
+    return fail(DBAR_ECUDA, "workspace initialisation failed");
+  }
   c.m = m;
   c.max_iter = p->max_iter;
   c.max_outer = p->max_outer;
@@ -1244,6 +1263,21 @@ static dbar_status load_Q(dbar_plan* P, const double* Q, int on_device, cudaStre
   return load_Q_device(P, P->Qdev, st);
 }
 
+// FP64 view of the solutions of slots [s0, s0 + nb): x itself, or, with
+// double-float storage, an FP64 copy written over b (no longer needed once a
+// slot's solve has finished).
+static dbar_status solution_fp64(dbar_plan* P, int s0, int nb, cudaStream_t st, const cx<double>** out) {
+  const long long n = P->n;
+  if (!P->resid_dd) {
+    *out = P->x64 + (size_t)s0 * n;
+    return DBAR_OK;
+  }
+  cx<double>* dst = P->b64 + (size_t)s0 * n;
+  CK(timed(P, st, K_OTHER, [&] { return launch_dd_to_fp64(P->x64 + (size_t)s0 * n, dst, (long long)nb * n, st); }));
+  *out = dst;
+  return DBAR_OK;
+}
+
 extern "C" dbar_status dbar_solve_cgo(dbar_plan_t P, const double* Q, int nk, const double* k, double* S_out,
                                       double* m_out, int* iters, double* resid, int io_on_device, void* stream) {
   if (!P) return fail(DBAR_EINVAL, "plan is NULL");
@@ -1265,9 +1299,12 @@ extern "C" dbar_status dbar_solve_cgo(dbar_plan_t P, const double* Q, int nk, co
     if (s != DBAR_OK) return s;
     s = P->mixed ? run_cycles<float>(P, nb, st) : run_cycles<double>(P, nb, st);
     if (s != DBAR_OK) return s;
-    CK(cudaMemcpyAsync(S_out + (size_t)k0 * n * 2, P->x64, (size_t)nb * n * sizeof(cx<double>), d2o, st));
+    const cx<double>* S64 = nullptr;
+    s = solution_fp64(P, 0, nb, st, &S64);
+    if (s != DBAR_OK) return s;
+    CK(cudaMemcpyAsync(S_out + (size_t)k0 * n * 2, S64, (size_t)nb * n * sizeof(cx<double>), d2o, st));
     if (m_out) {
-      s = h_of_S64(P, P->x64, n, reinterpret_cast<cx<double>*>(P->T2), n, nb, st);
+      s = h_of_S64(P, S64, n, reinterpret_cast<cx<double>*>(P->T2), n, nb, st);
       if (s != DBAR_OK) return s;
       CK(cudaMemcpyAsync(m_out + (size_t)k0 * n * 2, P->T2, (size_t)nb * n * sizeof(cx<double>), d2o, st));
     }
@@ -1337,7 +1374,13 @@ extern "C" dbar_status dbar_rhs(dbar_plan_t P, const double* Q, int nk, const do
   if (s != DBAR_OK) return s;
   s = P->mixed ? build_rhs<float>(P, nk, st) : build_rhs<double>(P, nk, st);
   if (s != DBAR_OK) return s;
-  CK(cudaMemcpyAsync(b, P->b64, (size_t)nk * P->n * sizeof(cx<double>), cudaMemcpyDeviceToDevice, st));
+  const cx<double>* b64 = P->b64;
+  if (P->resid_dd) {  // b is held as double-float pairs
+    cx<double>* t2 = reinterpret_cast<cx<double>*>(P->T2);
+    CK(launch_dd_to_fp64(P->b64, t2, (long long)nk * P->n, st));
+    b64 = t2;
+  }
+  CK(cudaMemcpyAsync(b, b64, (size_t)nk * P->n * sizeof(cx<double>), cudaMemcpyDeviceToDevice, st));
   CK(cudaStreamSynchronize(st));
   return DBAR_OK;
 }
@@ -1376,7 +1419,7 @@ extern "C" dbar_status dbar_taylor(dbar_plan_t P, int nk, const void* S, double*
     CK(launch_pass_a<double>(a, nk, st));
   }
   cx<double>* dc = P->tcoef;
-  CK(launch_coef(P->partA, fp32, P->M, P->N, P->Da64, 1.0, dc, nk, st));
+  CK(launch_coef(P->partA, fp32, P->M, P->N, P->Da64, 1.0, P->coefp, P->ticket, dc, nk, st));
   CK(cudaMemcpyAsync(coef, dc, (size_t)nk * (P->M + 2) * sizeof(cx<double>), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   return DBAR_OK;
@@ -1472,9 +1515,12 @@ dbar_status plan_read_slot(dbar_plan* P, int slot, double* S, double* m, int* it
                            cudaStream_t st) {
   if (!P || slot < 0 || slot >= P->B || !S) return fail(DBAR_EINVAL, "plan_read_slot: bad argument");
   const long long n = P->n;
-  CK(cudaMemcpyAsync(S, P->x64 + slot * n, n * sizeof(cx<double>), cudaMemcpyDeviceToHost, st));
+  const cx<double>* S64 = nullptr;
+  dbar_status s0 = solution_fp64(P, slot, 1, st, &S64);
+  if (s0 != DBAR_OK) return s0;
+  CK(cudaMemcpyAsync(S, S64, n * sizeof(cx<double>), cudaMemcpyDeviceToHost, st));
   if (m) {
-    dbar_status s = h_of_S64(P, P->x64 + slot * n, n, reinterpret_cast<cx<double>*>(P->T2), n, 1, st);
+    dbar_status s = h_of_S64(P, S64, n, reinterpret_cast<cx<double>*>(P->T2), n, 1, st);
     if (s != DBAR_OK) return s;
     CK(cudaMemcpyAsync(m, P->T2, n * sizeof(cx<double>), cudaMemcpyDeviceToHost, st));
   }

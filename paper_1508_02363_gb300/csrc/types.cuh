@@ -18,15 +18,15 @@ struct PassArgs {
   long long in_ss;
   const double* in_scale;
   int in_scale_ss;
-  const cx<double>* in64;  // pass A input kept in FP64 storage (double-float residual)
   // outputs
   void* out;
   long long out_ss;
   void* out2;  // second output (pass C right-hand side / residual: Krylov start vector)
   long long out2_ss;
-  // pass C residual inputs (FP64 fields)
-  const cx<double>* b;
-  const cx<double>* x;
+  // pass C residual inputs, stored in the residual's arithmetic (FP64 or
+  // double-float: x and b of the mixed path never pass through FP64)
+  const cx<T>* b;
+  const cx<T>* x;
   long long f_ss;
   const int* run;  // per-slot flags (nullable)
   // tables
@@ -47,6 +47,7 @@ struct PassArgs {
   int nseg;              // warp segments per row: seg_count(N)
   const cx<double>* coef;  // [slot][M+2] c_0..c_M, d' (k_coef output, read by pass B)
   double* part;          // [slot][gridDim.x] squared-norm partials (pass C)
+  const float* nscale;   // [slot] power-of-two ~1/||b|| (double-float residual norms)
 };
 
 
@@ -92,6 +93,7 @@ struct CycleState {
   double* ycoef;   // [slot][m+1]
   double* thr;     // [slot] stop threshold of the current cycle
   double* bnorm;   // [slot]
+  float* nscale;   // [slot] 2^-e with 2^e ~ ||b|| (scales FP32 squared norms of residuals)
   double* resid;   // [slot] last true relative residual
   int* run;        // [slot]
   int* active;     // [slot]
@@ -105,8 +107,9 @@ struct CycleState {
   double inner_tol;  // > 0: mixed-precision inner criterion relative to beta
 };
 
-// pass B modes: operator, right-hand side, h only, raw column DFTs
-enum { PB_MATVEC = 0, PB_RHS = 1, PB_HOUT = 2, PB_FWD = 3, PB_INV = 4 };
+// pass B modes: operator, right-hand side, h only, raw column DFTs, and the
+// operator's first half (column IDFT, h, w = E_k Q conj(h); no column DFT)
+enum { PB_MATVEC = 0, PB_RHS = 1, PB_HOUT = 2, PB_FWD = 3, PB_INV = 4, PB_W = 5 };
 // pass C modes: K S, right-hand side, FP64 residual, raw row DFTs
 enum { PC_KS = 0, PC_RHS = 1, PC_RES = 2, PC_FWD = 3, PC_INV = 4 };
 
