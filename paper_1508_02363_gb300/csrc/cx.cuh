@@ -246,7 +246,7 @@ __host__ __device__ constexpr int pitch_of(int N) { return N + (N >> 4) + 2; }
 // from the table tw[s] = e^{-2 pi i s/N}, R-point DFT, outputs at
 // ((j - j mod NS) R + j mod NS) + r NS.  The last stage (NS R = N) keeps its
 // outputs in registers: v[q] = X[t + q TPL].
-template <typename T, int N, int R, int NS, bool INV, bool FIRST, bool LAST>
+template <typename T, int N, int R, int NS, bool INV, bool FIRST, bool LAST, bool TWM>
 __device__ __forceinline__ void fft_stage(cx<T> (&v)[16], cx<T>* line, int t, const cx<T>* __restrict__ tw) {
   constexpr int TPL = N / 16, B = 16 / R, NB = N / R;
   static_assert(!FIRST || R == 16, "the first stage is radix 16");
@@ -261,11 +261,32 @@ __device__ __forceinline__ void fft_stage(cx<T> (&v)[16], cx<T>* line, int t, co
     if (NS > 1) {
       constexpr int STEP = N / (NS * R);
       const int k = (t + b * TPL) & (NS - 1);
+      if constexpr (TWM) {
+        // load w^r for r a power of two, form the rest as products (at most
+        // three roundings deep): fewer L1 loads in the FP32 row passes
+        cx<T> wr[R];
 #pragma unroll
-      for (int r = 1; r < R; ++r) {
-        cx<T> w = ldg(tw + r * k * STEP);
-        if (INV) w.im = -w.im;
-        v[b * R + r] = cmul(v[b * R + r], w);
+        for (int r = 1; r < R; ++r) {
+          if ((r & (r - 1)) == 0) {
+            wr[r] = ldg(tw + r * k * STEP);
+          } else {
+            const int hb = 1 << (31 - __clz(r));
+            wr[r] = cmul(wr[hb], wr[r - hb]);
+          }
+        }
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          cx<T> w = wr[r];
+          if (INV) w.im = -w.im;
+          v[b * R + r] = cmul(v[b * R + r], w);
+        }
+      } else {
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          cx<T> w = ldg(tw + r * k * STEP);
+          if (INV) w.im = -w.im;
+          v[b * R + r] = cmul(v[b * R + r], w);
+        }
       }
     }
     dft_reg<T, R, INV>(&v[b * R]);
@@ -296,19 +317,22 @@ __device__ __forceinline__ void fft_stage(cx<T> (&v)[16], cx<T>* line, int t, co
 // Full length-N transform, N = 2^LOGN in [32, 4096]: radix 16 first, then
 // 16 and the remainder.  On entry v[q] = x[t + q TPL]; on exit v[q] = X[t + q TPL],
 // X[p] = sum_j x[j] e^{-+2 pi i p j/N} (unnormalised; + for INV).  Every thread
-// of the block calls this together (it synchronises the block).
-template <typename T, int LOGN, bool INV>
+// of the block calls this together (it synchronises the block).  TWM: stage
+// twiddles w^r formed as products of loaded powers of two (measured faster in
+// the FP32 row passes, slower in the column pass; FP32 only).
+template <typename T, int LOGN, bool INV, bool TWM = false>
 __device__ __forceinline__ void fft_line(cx<T> (&v)[16], cx<T>* line, int t, const cx<T>* __restrict__ tw) {
   constexpr int N = 1 << LOGN;
   constexpr int L1 = LOGN - 4;
   static_assert(L1 >= 1 && L1 <= 8, "N must be in [32, 4096]");
+  static_assert(!TWM || std::is_same<T, float>::value, "twiddle products are for FP32 transforms only");
   if constexpr (L1 <= 4) {
-    fft_stage<T, N, 16, 1, INV, true, false>(v, line, t, tw);
-    fft_stage<T, N, (1 << L1), 16, INV, false, true>(v, line, t, tw);
+    fft_stage<T, N, 16, 1, INV, true, false, TWM>(v, line, t, tw);
+    fft_stage<T, N, (1 << L1), 16, INV, false, true, TWM>(v, line, t, tw);
   } else {
-    fft_stage<T, N, 16, 1, INV, true, false>(v, line, t, tw);
-    fft_stage<T, N, 16, 16, INV, false, false>(v, line, t, tw);
-    fft_stage<T, N, (1 << (L1 - 4)), 256, INV, false, true>(v, line, t, tw);
+    fft_stage<T, N, 16, 1, INV, true, false, TWM>(v, line, t, tw);
+    fft_stage<T, N, 16, 16, INV, false, false, TWM>(v, line, t, tw);
+    fft_stage<T, N, (1 << (L1 - 4)), 256, INV, false, true, TWM>(v, line, t, tw);
   }
 }
 

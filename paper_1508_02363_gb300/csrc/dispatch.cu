@@ -19,6 +19,18 @@ cudaError_t launch_pass_a(const PassArgs<T>& a, int nslots, cudaStream_t s) {
   return cudaErrorInvalidValue;
 }
 
+template <typename T>
+cudaError_t launch_pass_ca(const PassArgs<T>& a, int nslots, cudaStream_t s) {
+  if (nslots <= 0) return cudaSuccess;
+  switch (a.g.logN) {
+#define CASE(L) \
+  case L: return launch_pass_ca_n<T, L>(a, nslots, s);
+    DBAR_SIZES(CASE)
+#undef CASE
+  }
+  return cudaErrorInvalidValue;
+}
+
 template <typename T, int MODE>
 cudaError_t launch_pass_b(const PassArgs<T>& a, int nslots, cudaStream_t s) {
   if (nslots <= 0) return cudaSuccess;
@@ -56,6 +68,7 @@ cudaError_t launch_pass_c(const PassArgs<T>& a, int nslots, cudaStream_t s) {
 
 #define INST(T)                                                                         \
   template cudaError_t launch_pass_a<T>(const PassArgs<T>&, int, cudaStream_t);  \
+  template cudaError_t launch_pass_ca<T>(const PassArgs<T>&, int, cudaStream_t);  \
   template cudaError_t launch_pass_b<T, PB_MATVEC>(const PassArgs<T>&, int, cudaStream_t); \
   template cudaError_t launch_pass_b<T, PB_RHS>(const PassArgs<T>&, int, cudaStream_t);    \
   template cudaError_t launch_pass_b<T, PB_HOUT>(const PassArgs<T>&, int, cudaStream_t);   \

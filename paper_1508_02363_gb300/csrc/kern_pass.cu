@@ -43,6 +43,16 @@ cudaError_t launch_pass_b_n(const PassArgs<T>& a, int nslots, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <typename T, int LOGN>
+cudaError_t launch_pass_ca_n(const PassArgs<T>& a, int nslots, cudaStream_t s) {
+  using G = RowG<T, LOGN>;
+  const size_t sm = (size_t)G::LINES * G::P * sizeof(cx<T>);
+  cudaError_t e = set_smem(k_pass_ca<T, LOGN>, sm);
+  if (e != cudaSuccess) return e;
+  k_pass_ca<T, LOGN><<<dim3(G::N / G::LINES, nslots), G::THREADS, sm, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <typename T, typename TO, int LOGN, int MODE>
 cudaError_t launch_pass_c_n(const PassArgs<T>& a, int nslots, cudaStream_t s) {
   using G = RowG<T, LOGN>;
@@ -76,6 +86,7 @@ template cudaError_t launch_pass_c_n<TT, TT, DBAR_LOGN, PC_INV>(const PassArgs<T
 #if DBAR_KIND == 0
 template cudaError_t launch_pass_b_n<float, DBAR_LOGN, PB_MATVEC, 1>(const PassArgs<float>&, int, cudaStream_t);
 #endif
+template cudaError_t launch_pass_ca_n<TT, DBAR_LOGN>(const PassArgs<TT>&, int, cudaStream_t);
 #if DBAR_KIND == 1
 template cudaError_t launch_pass_c_n<double, double, DBAR_LOGN, PC_RHS>(const PassArgs<double>&, int, cudaStream_t);
 template cudaError_t launch_pass_c_n<double, float, DBAR_LOGN, PC_RHS>(const PassArgs<double>&, int, cudaStream_t);

@@ -46,10 +46,16 @@ template <typename T, int LOGN, int MODE, int CV>
 cudaError_t launch_pass_b_n(const PassArgs<T>& a, int nslots, cudaStream_t s);
 template <typename T, typename TO, int LOGN, int MODE>
 cudaError_t launch_pass_c_n(const PassArgs<T>& a, int nslots, cudaStream_t s);
+template <typename T, int LOGN>
+cudaError_t launch_pass_ca_n(const PassArgs<T>& a, int nslots, cudaStream_t s);
 
 // size dispatch (dispatch.cu)
 template <typename T>
 cudaError_t launch_pass_a(const PassArgs<T>& a, int nslots, cudaStream_t s);
+// fused chain step rows: pass C of the column-pass output -> out (K p), then
+// pass A of K p -> out2 (and the Taylor moment partials)
+template <typename T>
+cudaError_t launch_pass_ca(const PassArgs<T>& a, int nslots, cudaStream_t s);
 template <typename T, int MODE>
 cudaError_t launch_pass_b(const PassArgs<T>& a, int nslots, cudaStream_t s);
 template <typename T, typename TO, int MODE>

@@ -62,7 +62,10 @@ template <typename T, int LOGN>
 struct RowG {
   static constexpr int N = 1 << LOGN, TPL = N / 16, LINES = row_lines(LOGN), THREADS = LINES * TPL;
   static constexpr int P = pitch_of(N);
-  static constexpr int MINB = sizeof(T) == 4 ? 4 : 2;
+#ifndef DBAR_ROW_MINB_F32
+#define DBAR_ROW_MINB_F32 4
+#endif
+  static constexpr int MINB = sizeof(T) == 4 ? DBAR_ROW_MINB_F32 : 2;
 };
 template <typename T, int LOGN, int CV = 0>
 struct ColG {
@@ -75,33 +78,24 @@ struct ColG {
 };
 
 // ---------------------------------------------------------------------------
-// Pass A: rows of a Fourier field.
+// Pass A: rows of a Fourier field.  row_a() is the work on one row once its
+// 16 values per thread are in registers (v[q] = S[p2][t + q TPL]): the
+// Taylor row moments, S~ (-1)^p / (2 pi L^2), the row IDFT and the store to
+// dst (this thread's first element of the row).  Used by k_pass_a and by the
+// fused row pass k_pass_ca.
 // ---------------------------------------------------------------------------
 template <typename T, int LOGN>
-__global__ void __launch_bounds__(RowG<T, LOGN>::THREADS, RowG<T, LOGN>::MINB) k_pass_a(const PassArgs<T> a) {
+__device__ __forceinline__ void row_a(const PassArgs<T>& a, cx<T> (&v)[16], int slot, int p2, int t, cx<T>* sl,
+                                      cx<T>* dst) {
   using G = RowG<T, LOGN>;
-  constexpr int N = G::N, TPL = G::TPL, LINES = G::LINES, P = G::P;
+  constexpr int N = G::N, TPL = G::TPL;
   constexpr int SEGW = TPL >= 32 ? 32 : TPL, NSEG = TPL >= 32 ? TPL / 32 : 1;
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int slot = blockIdx.y;
-  if (a.run && !a.run[slot]) return;
   const int M = a.M, MA = M > 1 ? M : 1;
-  const int line = threadIdx.x / TPL, t = threadIdx.x - line * TPL;
-  const int p2 = blockIdx.x * LINES + line;
-  cx<T>* sl = reinterpret_cast<cx<T>*>(smem) + line * P;
-  const T sc = a.in_scale ? (T)a.in_scale[(size_t)slot * a.in_scale_ss] : (T)1;
-  cx<T> v[16];
-  {
-    const cx<T>* src = a.in + (size_t)slot * a.in_ss + (size_t)p2 * N + t;
-#pragma unroll
-    for (int q = 0; q < 16; ++q) v[q] = cscale(ldg(src + q * TPL), sc);
-  }
-
   // Row moments R_a(p2) = sum_p1 (-1)^p1 S D_a(p1), a = 0..MA, written as
-  // per-warp-segment partials (FP64) for k_coef, which combines them with
-  // D_b(p2): no block-wide tail and no FP64 arithmetic per element here.
-  // (FP32 partials from the FP32 pass: on GB300 every FP64 conversion issued
-  // per warp occupies the small FP64 pipe for tens of cycles)
+  // per-warp-segment partials for k_coef, which combines them with D_b(p2)
+  // in FP64: no block-wide tail here.  The FP32 pass writes FP32 partials (on
+  // GB300 every FP64 conversion issued per warp occupies the small FP64 pipe
+  // for tens of cycles).
   using PT = typename std::conditional<std::is_same<T, float>::value, float, double>::type;
   const int seg = TPL >= 32 ? t / 32 : 0;
   cx<PT>* part = reinterpret_cast<cx<PT>*>(a.partA) + ((size_t)slot * N + p2) * NSEG * (MA + 1);
@@ -145,11 +139,62 @@ __global__ void __launch_bounds__(RowG<T, LOGN>::THREADS, RowG<T, LOGN>::MINB) k
     if ((p1 + p2) & 1) f = -f;
     v[q] = cmul(v[q], mkc(m1f * f, -(m2f * f)));
   }
-  fft_line<T, LOGN, true>(v, sl, t, a.tw);
-  cx<T>* dst = reinterpret_cast<cx<T>*>(a.out) + (size_t)slot * a.out_ss + (size_t)p2 * N + t;
+  fft_line<T, LOGN, true, std::is_same<T, float>::value>(v, sl, t, a.tw);
 #pragma unroll
   for (int q = 0; q < 16; ++q) dst[q * TPL] = v[q];
+}
 
+template <typename T, int LOGN>
+__global__ void __launch_bounds__(RowG<T, LOGN>::THREADS, RowG<T, LOGN>::MINB) k_pass_a(const PassArgs<T> a) {
+  using G = RowG<T, LOGN>;
+  constexpr int N = G::N, TPL = G::TPL, LINES = G::LINES, P = G::P;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int slot = blockIdx.y;
+  if (a.run && !a.run[slot]) return;
+  const int line = threadIdx.x / TPL, t = threadIdx.x - line * TPL;
+  const int p2 = blockIdx.x * LINES + line;
+  cx<T>* sl = reinterpret_cast<cx<T>*>(smem) + line * P;
+  const T sc = a.in_scale ? (T)a.in_scale[(size_t)slot * a.in_scale_ss] : (T)1;
+  cx<T> v[16];
+  const cx<T>* src = a.in + (size_t)slot * a.in_ss + (size_t)p2 * N + t;
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = cscale(ldg(src + q * TPL), sc);
+  row_a<T, LOGN>(a, v, slot, p2, t, sl, reinterpret_cast<cx<T>*>(a.out) + (size_t)slot * a.out_ss + (size_t)p2 * N + t);
+}
+
+// ---------------------------------------------------------------------------
+// Fused row pass of a Krylov chain step: pass C of K p_i (row DFT of the
+// column pass output, K p_i = i (-1)^p DFT(w) -> out, the next chain vector)
+// followed, on the same rows still in registers, by pass A of K p_i (-> out2).
+// Saves the re-read of p_{i+1} and one launch per chain step.
+// ---------------------------------------------------------------------------
+template <typename T, int LOGN>
+__global__ void __launch_bounds__(RowG<T, LOGN>::THREADS, RowG<T, LOGN>::MINB) k_pass_ca(const PassArgs<T> a) {
+  using G = RowG<T, LOGN>;
+  constexpr int N = G::N, TPL = G::TPL, LINES = G::LINES, P = G::P;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int slot = blockIdx.y;
+  if (a.run && !a.run[slot]) return;
+  const int line = threadIdx.x / TPL, t = threadIdx.x - line * TPL;
+  const int p2 = blockIdx.x * LINES + line;
+  cx<T>* sl = reinterpret_cast<cx<T>*>(smem) + line * P;
+  cx<T> v[16];
+  const cx<T>* src = a.in + (size_t)slot * a.in_ss + (size_t)p2 * N + t;
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = ldg(src + q * TPL);
+  fft_line<T, LOGN, false, std::is_same<T, float>::value>(v, sl, t, a.tw);
+  cx<T>* kp = reinterpret_cast<cx<T>*>(a.out) + (size_t)slot * a.out_ss + (size_t)p2 * N + t;
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    cx<T> y = v[q];
+    if ((t + q * TPL + p2) & 1) y = mkc(-y.re, -y.im);
+    y = cmuli(y);
+    kp[q * TPL] = y;
+    v[q] = y;
+  }
+  // (the inverse transform's first stage synchronises before it reuses the line buffer)
+  row_a<T, LOGN>(a, v, slot, p2, t, sl,
+                 reinterpret_cast<cx<T>*>(a.out2) + (size_t)slot * a.out2_ss + (size_t)p2 * N + t);
 }
 
 // ---------------------------------------------------------------------------
@@ -191,6 +236,19 @@ __global__ void __launch_bounds__(ColG<T, LOGN, CV>::THREADS, ColG<T, LOGN, CV>:
     const cx<T> fill = coef[M + 1];
 #pragma unroll
     for (int q = 0; q < 16; ++q) v[q] = v[q] + fill;
+#ifdef DBAR_PB_M2
+    if (M == 2) {  // the common order: the three tables' loads of a row issued together
+      const cx<T> c0 = coef[0], c1 = coef[1], c2 = coef[2];
+      const cx<T>* D = a.Delta + (size_t)t * N + j1;
+      const size_t fs = (size_t)N * N;
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const size_t o = (size_t)q * TPL * N;
+        const cx<T> d0 = ldg(D + o), d1 = ldg(D + fs + o), d2 = ldg(D + 2 * fs + o);
+        v[q] = v[q] + cmul(c0, d0) + cmul(c1, d1) + cmul(c2, d2);
+      }
+    } else
+#endif
     for (int n = 0; n <= M; ++n) {
       const cx<T> cn = coef[n];
       const cx<T>* D = a.Delta + ((size_t)n * N + t) * N + j1;
@@ -316,7 +374,7 @@ __global__ void __launch_bounds__(RowG<T, LOGN>::THREADS, RowG<T, LOGN>::MINB) k
   cx<T> v[16];
 #pragma unroll
   for (int q = 0; q < 16; ++q) v[q] = ldg(src + q * TPL);
-  fft_line<T, LOGN, MODE == PC_INV>(v, sl, t, a.tw);
+  fft_line<T, LOGN, MODE == PC_INV, std::is_same<T, float>::value>(v, sl, t, a.tw);
   // squared-norm partials.  FP64 for FP64 fields and for the right-hand side
   // (once per solve); the double-float residual sums FP32 squares of r scaled
   // by the slot's power-of-two 1/||b|| (no FP64 per element on GB300's small

@@ -49,12 +49,12 @@ dbar_status dbar_internal_fail(dbar_status st, const std::string& msg) { return 
 // Kernel kinds for the event profiler (dbar_profile_*).
 enum {
   K_PASS_A, K_PASS_B, K_PASS_C, K_DOTS, K_UPDATE, K_SCALAR, K_XUPDATE,
-  K_RES_A, K_RES_B, K_RES_C, K_RHS, K_OTHER, K_NKINDS
+  K_RES_A, K_RES_B, K_RES_C, K_RHS, K_OTHER, K_PASS_CA, K_NKINDS
 };
 static const char* const kKindNames[K_NKINDS] = {
     "inner_pass_a_rows", "inner_pass_b_cols", "inner_pass_c_rows", "arnoldi_dots", "arnoldi_update",
     "krylov_scalar", "solution_update", "fp64_residual_pass_a", "fp64_residual_pass_b",
-    "fp64_residual_pass_c", "rhs", "other"};
+    "fp64_residual_pass_c", "rhs", "other", "inner_pass_ca_rows"};
 
 // CUDA-event timing of every launch of the solve, grouped by kind, plus the
 // algorithmic bytes of each kind (fields read and written once per use).
@@ -557,8 +557,11 @@ static dbar_status true_residual(dbar_plan* P, int nb, cudaStream_t st) {
 // write T1), pass B 2F (read T1, write T2), pass C 2F (read T2, write K v_j),
 // dots (j+2)F (v_0..v_j and K v_j), update (j+3)F (the same, plus the new
 // vector); per launch of pass B the shared tables Q and Delta_0..Delta_M,
-// (M+2)F.  Per cycle and slot: solution update (ns F + 2 F64), FP64 residual
-// passes 2 F64 + 2 F64 + (3 F64 + F), plus (M+2) F64 of tables per pass-B launch.
+// (M+2)F.  s-step blocks (J basis vectors, S chain steps): pass A 2F, S pass B
+// 2F, S-1 fused row passes 3F (read T2, write K p_i and T1), one pass C 2F,
+// block dots (J+S)F, block update (J+2S)F.  Per cycle and slot: solution
+// update (ns F + 2 F64), residual passes 2 F64 + 2 F64 + (3 F64 + F), plus
+// (M+2) F64 of tables per pass-B launch.
 static void account_cycle(dbar_plan* P, const int* act, const int* ns, int nb, int launched_steps) {
   if (!P->prof.on) return;
   const double F = (double)P->n * P->inner_elem(), F64 = (double)P->n * sizeof(cx<double>);
@@ -574,9 +577,10 @@ static void account_cycle(dbar_plan* P, const int* act, const int* ns, int nb, i
       const int S = P->sstep, nblk = (k + S - 1) / S;
       for (int b = 0; b < nblk; ++b) {
         const int J = b * S + 1;
-        by[K_PASS_A] += 2.0 * F * S;
+        by[K_PASS_A] += 2.0 * F;            // v_{J-1} -> T1
         by[K_PASS_B] += 2.0 * F * S;
-        by[K_PASS_C] += 2.0 * F * S;
+        by[K_PASS_CA] += 3.0 * F * (S - 1);  // T2 -> K p_i and T1
+        by[K_PASS_C] += 2.0 * F;
         by[K_DOTS] += F * (J + S);
         by[K_UPDATE] += F * (J + 2 * S);
       }
@@ -647,10 +651,36 @@ static dbar_status block_steps(dbar_plan* P, int nb, int j0, int j1, cudaStream_
   ba.part = P->bpart;
   for (int c0 = j0; c0 < j1; c0 += S) {
     const int J = c0 + 1;  // basis vectors v_0..v_{J-1} exist
+    // the chain p_{i+1} = K p_i into basis slots J..J+S-1: pass A of v_{J-1};
+    // per step the coefficients and pass B, then pass C fused with the next
+    // step's pass A (the last step: pass C alone)
+    PassArgs<TI> a = base_args<TI>(P);
+    a.run = P->cs.run;
+    a.in = V + (size_t)(J - 1) * n;
+    a.in_ss = vss;
+    a.in_scale = P->cs.sigma + (J - 1);
+    a.in_scale_ss = m + 1;
+    a.out = P->T1;
+    a.out_ss = n;
+    CK(timed(P, st, K_PASS_A, [&] { return launch_pass_a<TI>(a, nb, st); }));
+    a.in_scale = nullptr;
     for (int i = 0; i < S; ++i) {
-      dbar_status s = apply_K<TI>(P, V + (size_t)(J - 1 + i) * n, vss, i == 0 ? P->cs.sigma + (J - 1) : nullptr,
-                                  m + 1, V + (size_t)(J + i) * n, vss, P->cs.run, nb, st);
-      if (s != DBAR_OK) return s;
+      CK(timed(P, st, K_SCALAR, [&] { return launch_coef_for(P, a, nb, st); }));
+      a.in = reinterpret_cast<const cx<TI>*>(P->T1);
+      a.in_ss = n;
+      a.out = P->T2;
+      a.out_ss = n;
+      CK(timed(P, st, K_PASS_B, [&] { return launch_pass_b<TI, PB_MATVEC>(a, nb, st); }));
+      a.in = reinterpret_cast<const cx<TI>*>(P->T2);
+      a.out = V + (size_t)(J + i) * n;
+      a.out_ss = vss;
+      if (i + 1 < S) {
+        a.out2 = P->T1;
+        a.out2_ss = n;
+        CK(timed(P, st, K_PASS_CA, [&] { return launch_pass_ca<TI>(a, nb, st); }));
+      } else {
+        CK(timed(P, st, K_PASS_C, [&] { return launch_pass_c<TI, TI, PC_KS>(a, nb, st); }));
+      }
     }
     CK(timed(P, st, K_DOTS, [&] { return launch_bdots<TI, S>(ba, V, vss, J, nb, st); }));
     CK(timed(P, st, K_SCALAR, [&] { return launch_bscalar<S>(ba, P->cs, P->Hraw, P->bcoef, P->upd, J, nb, st); }));
