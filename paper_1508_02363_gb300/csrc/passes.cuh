@@ -236,19 +236,6 @@ __global__ void __launch_bounds__(ColG<T, LOGN, CV>::THREADS, ColG<T, LOGN, CV>:
     const cx<T> fill = coef[M + 1];
 #pragma unroll
     for (int q = 0; q < 16; ++q) v[q] = v[q] + fill;
-#ifdef DBAR_PB_M2
-    if (M == 2) {  // the common order: the three tables' loads of a row issued together
-      const cx<T> c0 = coef[0], c1 = coef[1], c2 = coef[2];
-      const cx<T>* D = a.Delta + (size_t)t * N + j1;
-      const size_t fs = (size_t)N * N;
-#pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const size_t o = (size_t)q * TPL * N;
-        const cx<T> d0 = ldg(D + o), d1 = ldg(D + fs + o), d2 = ldg(D + 2 * fs + o);
-        v[q] = v[q] + cmul(c0, d0) + cmul(c1, d1) + cmul(c2, d2);
-      }
-    } else
-#endif
     for (int n = 0; n <= M; ++n) {
       const cx<T> cn = coef[n];
       const cx<T>* D = a.Delta + ((size_t)n * N + t) * N + j1;
