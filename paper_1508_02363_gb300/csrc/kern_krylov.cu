@@ -71,7 +71,7 @@ template <typename T, int S>
 cudaError_t launch_bupdate(const BlockArgs& a, const int* upd, cx<T>* V, long long vss, int J, int nslots,
                            cudaStream_t s) {
   if (nslots <= 0) return cudaSuccess;
-  k_bupdate<T, S><<<dim3(a.nchunk, nslots), KR_THREADS, 0, s>>>(a, upd, V, vss, J);
+  k_bupdate<T, S><<<dim3(a.nwork, nslots), KR_THREADS, 0, s>>>(a, upd, V, vss, J);
   return cudaGetLastError();
 }
 #define KB_INST(T, S)                                                                                          \
@@ -158,17 +158,17 @@ cudaError_t launch_add_fields(const void* S, const void* KS, void* AS, long long
 }
 
 cudaError_t launch_coef(const cx<double>* partA, int part_fp32, int M, int N, const cx<double>* Da64,
-                        double fillscale, cx<double>* coefp, int* ticket, cx<double>* coef, int nslots,
-                        cudaStream_t s) {
+                        const cx<float>* Da32, double fillscale, cx<double>* coefp, int* ticket, cx<double>* coef,
+                        int nslots, cudaStream_t s) {
   if (nslots <= 0) return cudaSuccess;
   const int rows = coef_rows(N);
   const dim3 grid(nslots, N / rows);
   if (part_fp32)
     k_coef<float><<<grid, rows, 0, s>>>(reinterpret_cast<const cx<float>*>(partA), seg_count(N), M > 1 ? M : 1, M,
-                                        N, Da64, fillscale, coefp, ticket, coef);
+                                        N, Da64, Da32, fillscale, coefp, ticket, coef);
   else
-    k_coef<double><<<grid, rows, 0, s>>>(partA, seg_count(N), M > 1 ? M : 1, M, N, Da64, fillscale, coefp, ticket,
-                                         coef);
+    k_coef<double><<<grid, rows, 0, s>>>(partA, seg_count(N), M > 1 ? M : 1, M, N, Da64, Da32, fillscale, coefp,
+                                         ticket, coef);
   return cudaGetLastError();
 }
 

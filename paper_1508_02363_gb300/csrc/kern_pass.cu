@@ -39,7 +39,7 @@ cudaError_t launch_pass_b_n(const PassArgs<T>& a, int nslots, cudaStream_t s) {
   const size_t sm = align16((size_t)G::COLS * G::P * sizeof(cx<T>)) + (size_t)(a.M + 2) * sizeof(cx<T>);
   cudaError_t e = set_smem(k_pass_b<T, LOGN, MODE, CV>, sm);
   if (e != cudaSuccess) return e;
-  k_pass_b<T, LOGN, MODE, CV><<<dim3(G::N / G::COLS, nslots), G::THREADS, sm, s>>>(a);
+  k_pass_b<T, LOGN, MODE, CV><<<dim3(nslots, G::N / G::COLS), G::THREADS, sm, s>>>(a);
   return cudaGetLastError();
 }
 

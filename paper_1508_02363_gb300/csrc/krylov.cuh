@@ -359,45 +359,50 @@ __global__ void __launch_bounds__(KR_THREADS) k_bdots(const BlockArgs a, const c
   const int slot = blockIdx.y;
   if (!a.run[slot]) return;
   const int nit = block_items(J, S);
-  const long long base = (long long)blockIdx.x * KB_CHUNK + threadIdx.x;
   const cx<T>* Vs = V + (size_t)slot * vss;
-  cx<T> w[S][KB_EPT];
-#pragma unroll
-  for (int i = 0; i < S; ++i)
-#pragma unroll
-    for (int e = 0; e < KB_EPT; ++e) {
-      const long long idx = base + (long long)e * KR_THREADS;
-      w[i][e] = idx < a.n ? ldg(Vs + (size_t)(J + i) * a.n + idx) : mkc((T)0, (T)0);
-    }
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int r = 0; r < J; ++r) {
-    T s[S];
+  // each warp accumulates its own row of red over the block's chunks
+  for (int q = threadIdx.x; q < (KR_THREADS / 32) * nit; q += blockDim.x) redf[q] = 0;
+  __syncthreads();
+  for (int ch = blockIdx.x; ch < a.nwork; ch += gridDim.x) {
+    const long long base = (long long)ch * KB_CHUNK + threadIdx.x;
+    cx<T> w[S][KB_EPT];
 #pragma unroll
-    for (int i = 0; i < S; ++i) s[i] = 0;
+    for (int i = 0; i < S; ++i)
 #pragma unroll
-    for (int e = 0; e < KB_EPT; ++e) {
-      const long long idx = base + (long long)e * KR_THREADS;
-      if (idx < a.n) {
-        const cx<T> v = ldg(Vs + (size_t)r * a.n + idx);
-#pragma unroll
-        for (int i = 0; i < S; ++i) s[i] += v.re * w[i][e].re + v.im * w[i][e].im;
+      for (int e = 0; e < KB_EPT; ++e) {
+        const long long idx = base + (long long)e * KR_THREADS;
+        w[i][e] = idx < a.n ? ldg(Vs + (size_t)(J + i) * a.n + idx) : mkc((T)0, (T)0);
       }
+    for (int r = 0; r < J; ++r) {
+      T s[S];
+#pragma unroll
+      for (int i = 0; i < S; ++i) s[i] = 0;
+#pragma unroll
+      for (int e = 0; e < KB_EPT; ++e) {
+        const long long idx = base + (long long)e * KR_THREADS;
+        if (idx < a.n) {
+          const cx<T> v = ldg(Vs + (size_t)r * a.n + idx);
+#pragma unroll
+          for (int i = 0; i < S; ++i) s[i] += v.re * w[i][e].re + v.im * w[i][e].im;
+        }
+      }
+      const T d = warp_reduce_scatter<S>(s, lane);
+      if ((lane & (32 / S - 1)) == 0) redf[wid * nit + r * S + lane / (32 / S)] += d;
     }
-    const T d = warp_reduce_scatter<S>(s, lane);
-    if ((lane & (32 / S - 1)) == 0) redf[wid * nit + r * S + lane / (32 / S)] = d;
+    int it = J * S;
+#pragma unroll
+    for (int i = 0; i < S; ++i)
+#pragma unroll
+      for (int l = i; l < S; ++l) {
+        T s = 0;
+#pragma unroll
+        for (int e = 0; e < KB_EPT; ++e) s += w[i][e].re * w[l][e].re + w[i][e].im * w[l][e].im;
+        const T d = warp_sum_t(s, 32);
+        if (lane == 0) redf[wid * nit + it] += d;
+        ++it;
+      }
   }
-  int it = J * S;
-#pragma unroll
-  for (int i = 0; i < S; ++i)
-#pragma unroll
-    for (int l = i; l < S; ++l) {
-      T s = 0;
-#pragma unroll
-      for (int e = 0; e < KB_EPT; ++e) s += w[i][e].re * w[l][e].re + w[i][e].im * w[l][e].im;
-      const T d = warp_sum_t(s, 32);
-      if (lane == 0) redf[wid * nit + it] = d;
-      ++it;
-    }
   __syncthreads();
   for (int q = threadIdx.x; q < nit; q += blockDim.x) {
     T s = 0;

@@ -97,8 +97,8 @@ cudaError_t launch_add_fields(const void* S, const void* KS, void* AS, long long
 // coefp: [slots][N / coef_rows(N)][M+2] block partials; ticket: [slots] zeroed
 // counters (re-armed by the kernel).
 cudaError_t launch_coef(const cx<double>* partA, int part_fp32, int M, int N, const cx<double>* Da64,
-                        double fillscale, cx<double>* coefp, int* ticket, cx<double>* coef, int nslots,
-                        cudaStream_t s);
+                        const cx<float>* Da32, double fillscale, cx<double>* coefp, int* ticket, cx<double>* coef,
+                        int nslots, cudaStream_t s);
 cudaError_t launch_cast_fields(const cx<double>* in, cx<float>* out, long long n, cudaStream_t s);
 cudaError_t launch_split_fields(const cx<double>* in, cx<dd>* out, long long n, cudaStream_t s);
 cudaError_t launch_check_finite(const double* p, long long n, int* flag, cudaStream_t s);

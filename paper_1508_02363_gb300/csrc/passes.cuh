@@ -208,13 +208,15 @@ __global__ void __launch_bounds__(ColG<T, LOGN, CV>::THREADS, ColG<T, LOGN, CV>:
   using G = ColG<T, LOGN, CV>;
   constexpr int N = G::N, TPL = G::TPL, P = G::P;
   extern __shared__ __align__(16) unsigned char smem[];
-  const int slot = blockIdx.y;
+  // slot-major block order: the blocks resident together work on the same column
+  // tiles of different slots and share the Q / Delta_n table tiles in L2 and L1
+  const int slot = blockIdx.x;
   if (a.run && !a.run[slot]) return;
   const int M = a.M;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int c = (warp / G::WPG) * G::CW + lane % G::CW;
   const int t = (warp % G::WPG) * G::TW + lane / G::CW;
-  const int j1 = blockIdx.x * G::COLS + c;
+  const int j1 = blockIdx.y * G::COLS + c;
   cx<T>* sl = reinterpret_cast<cx<T>*>(smem) + c * P;
   constexpr size_t off = ((size_t)G::COLS * P * sizeof(cx<T>) + 15) & ~(size_t)15;
   cx<T>* coef = reinterpret_cast<cx<T>*>(smem + off);  // [M+1] c_n, then the fill d'
@@ -275,52 +277,65 @@ __global__ void __launch_bounds__(ColG<T, LOGN, CV>::THREADS, ColG<T, LOGN, CV>:
 constexpr int KC_MAXM = 16;
 template <typename PT>
 static __global__ void __launch_bounds__(256) k_coef(const cx<PT>* __restrict__ partA, int nseg, int MA, int M,
-                                              int N, const cx<double>* __restrict__ Da64, double fillscale,
+                                              int N, const cx<double>* __restrict__ Da64,
+                                              const cx<float>* __restrict__ Da32, double fillscale,
                                               cx<double>* __restrict__ coefp, int* __restrict__ ticket,
                                               cx<double>* __restrict__ coef) {
-  __shared__ double sre[256], sim[256];
+  // FP64 partials (FP64 and double-float passes): FP64 products and sums.
+  // FP32 partials (the FP32 inner pass): FP32 products, double-float sums
+  // over rows -- no FP64 per row on GB300's small FP64 pipe; the products
+  // carry the FP32 precision the moments already have.
+  constexpr bool F32 = std::is_same<PT, float>::value;
+  using AT = typename std::conditional<F32, float, double>::type;  // product arithmetic
+  using ST = typename std::conditional<F32, dd, double>::type;     // row-sum arithmetic
+  __shared__ ST sre[256], sim[256];
   __shared__ bool last;
   const int slot = blockIdx.x, KC = gridDim.y;
   const int stride = nseg * (MA + 1);
   const int p2 = blockIdx.y * blockDim.x + threadIdx.x;
   const cx<PT>* R = partA + ((size_t)slot * N + p2) * stride;
-  auto Ra = [&](int aa) {
-    cx<double> s = ccast<double>(R[aa]);
+  cx<AT> Rv[KC_MAXM + 1];  // R_a(p2), a = 0..MA (MA <= 16)
+  for (int aa = 0; aa <= MA; ++aa) {
+    cx<PT> s = R[aa];
     if (aa > 0)
-      for (int sg = 1; sg < nseg; ++sg) s = s + ccast<double>(R[sg * (MA + 1) + aa]);
-    return s;
+      for (int sg = 1; sg < nseg; ++sg) s = s + R[sg * (MA + 1) + aa];
+    Rv[aa] = ccast<AT>(s);
+  }
+  auto Dv = [&](int b) -> cx<AT> {
+    if constexpr (F32) return Da32[(size_t)b * N + p2];
+    else return Da64[(size_t)b * N + p2];
   };
   cx<double>* cp = coefp + ((size_t)slot * KC + blockIdx.y) * (M + 2);
   for (int n = 0; n < M + 2; ++n) {
-    cx<double> s = mkc(0.0, 0.0);
+    cx<AT> s = mkc((AT)0, (AT)0);
     if (n <= M) {
-      long long binom = 1;  // C(n, aa), exact for n <= 16
+      int binom = 1;  // C(n, aa), exact for n <= 16
       for (int aa = 0; aa <= n; ++aa) {
-        cx<double> tmp = cmul(Da64[(size_t)(n - aa) * N + p2], Ra(aa));
+        cx<AT> tmp = cmul(Dv(n - aa), Rv[aa]);
         const int e = (n - aa) & 3;
         if (e == 1) tmp = cmuli(tmp);
         else if (e == 2) tmp = mkc(-tmp.re, -tmp.im);
         else if (e == 3) tmp = mkc(tmp.im, -tmp.re);
-        s = s + cscale(tmp, (double)binom);
+        s = s + cscale(tmp, (AT)binom);
         binom = binom * (n - aa) / (aa + 1);
       }
     } else {
-      const cx<double> t1 = cmul(Ra(1), Da64[p2]);
-      const cx<double> t2 = cmul(Ra(0), Da64[(size_t)N + p2]);
+      const cx<AT> t1 = cmul(Rv[1], Dv(0));
+      const cx<AT> t2 = cmul(Rv[0], Dv(1));
       s = mkc(t1.re + t2.im, t1.im - t2.re);
     }
     if (p2 & 1) s = mkc(-s.re, -s.im);
-    sre[threadIdx.x] = s.re;
-    sim[threadIdx.x] = s.im;
+    sre[threadIdx.x] = ST(s.re);
+    sim[threadIdx.x] = ST(s.im);
     __syncthreads();
     for (int w = blockDim.x / 2; w > 0; w >>= 1) {
       if ((int)threadIdx.x < w) {
-        sre[threadIdx.x] += sre[threadIdx.x + w];
-        sim[threadIdx.x] += sim[threadIdx.x + w];
+        sre[threadIdx.x] = sre[threadIdx.x] + sre[threadIdx.x + w];
+        sim[threadIdx.x] = sim[threadIdx.x] + sim[threadIdx.x + w];
       }
       __syncthreads();
     }
-    if (threadIdx.x == 0) cp[n] = mkc(sre[0], sim[0]);
+    if (threadIdx.x == 0) cp[n] = mkc((double)sre[0], (double)sim[0]);
     __syncthreads();
   }
   if (threadIdx.x == 0) {

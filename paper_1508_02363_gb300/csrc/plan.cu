@@ -194,7 +194,7 @@ struct dbar_plan {
   int nchunk_b = 0, nitem_b = 0;
   double* Hraw = nullptr;   // [B][m][m+1] unrotated Hessenberg columns
   double* bcoef = nullptr;  // [B][S*S + (m+1)*S] sweep coefficients
-  double* bpart = nullptr;  // [B][nitem_b][nchunk_b] block dot partials
+  double* bpart = nullptr;  // [B][nitem_b][min(nchunk_b, kBlockDotBlocks)] block dot partials
   int* upd = nullptr;       // [B] slots whose block needs the update sweep
   // host staging
   int* h_active = nullptr;
@@ -435,8 +435,8 @@ PassArgs<dd> base_args<dd>(const dbar_plan* P) {
 // Taylor coefficients of the fields pass A just read (k_coef), for pass B.
 template <typename T>
 static cudaError_t launch_coef_for(dbar_plan* P, const PassArgs<T>& a, int nb, cudaStream_t st) {
-  return launch_coef(P->partA, std::is_same<T, float>::value, P->M, P->N, P->Da64, P->fillscale, P->coefp,
-                     P->ticket, P->tcoef, nb, st);
+  return launch_coef(P->partA, std::is_same<T, float>::value, P->M, P->N, P->Da64, P->Da32, P->fillscale,
+                     P->coefp, P->ticket, P->tcoef, nb, st);
 }
 
 // One application of K (A S = S + K S) to nb fields: S (T) -> T1 -> T2 -> out (T).
@@ -643,7 +643,8 @@ static dbar_status block_steps(dbar_plan* P, int nb, int j0, int j1, cudaStream_
   BlockArgs ba;
   ba.n = n;
   ba.mp1 = m + 1;
-  ba.nchunk = P->nchunk_b;
+  ba.nwork = P->nchunk_b;
+  ba.nchunk = std::min(P->nchunk_b, kBlockDotBlocks);
   ba.nitem = P->nitem_b;
   ba.run = P->cs.run;
   ba.sigma = P->cs.sigma;
@@ -1079,7 +1080,8 @@ size_t plan_slot_bytes(const dbar_params* p, int per_slot_q) {
   size_t b = 4 * F64 + (size_t)(p->restart + 2) * Fi;  // x, b, T1, T2; basis, K v
   const int S = p->sstep > 0 ? p->sstep : 4;  // upper bound for the automatic choice
   if (S > 1)  // s-step partials, coefficients, unrotated Hessenberg
-    b += ((size_t)(p->restart + 1) * S + S * (S + 1) / 2) * ((n + KB_CHUNK - 1) / KB_CHUNK) * sizeof(double) +
+    b += ((size_t)(p->restart + 1) * S + S * (S + 1) / 2) *
+             std::min<size_t>((n + KB_CHUNK - 1) / KB_CHUNK, kBlockDotBlocks) * sizeof(double) +
          ((size_t)S * (S + p->restart + 1) + (size_t)p->restart * (p->restart + 1)) * sizeof(double);
   if (per_slot_q) b += F64 + n * sizeof(cx<float>) + (p->prec == DBAR_MIXED ? F64 : 0);
   return b;
@@ -1213,7 +1215,7 @@ dbar_status plan_create_ex(const dbar_params* p, int per_slot_q, dbar_plan** out
     P->nitem_b = block_items(m + 1, S);
     AL(P->Hraw, (size_t)B * m * (m + 1));
     AL(P->bcoef, (size_t)B * (S * S + (m + 1) * S));
-    AL(P->bpart, (size_t)B * P->nitem_b * P->nchunk_b);
+    AL(P->bpart, (size_t)B * P->nitem_b * std::min(P->nchunk_b, kBlockDotBlocks));
     AL(P->upd, B);
   }
 #undef AL
@@ -1449,7 +1451,7 @@ extern "C" dbar_status dbar_taylor(dbar_plan_t P, int nk, const void* S, double*
     CK(launch_pass_a<double>(a, nk, st));
   }
   cx<double>* dc = P->tcoef;
-  CK(launch_coef(P->partA, fp32, P->M, P->N, P->Da64, 1.0, P->coefp, P->ticket, dc, nk, st));
+  CK(launch_coef(P->partA, fp32, P->M, P->N, P->Da64, P->Da32, 1.0, P->coefp, P->ticket, dc, nk, st));
   CK(cudaMemcpyAsync(coef, dc, (size_t)nk * (P->M + 2) * sizeof(cx<double>), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   return DBAR_OK;

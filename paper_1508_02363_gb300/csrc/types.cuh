@@ -70,11 +70,13 @@ struct KryArgs {
 constexpr int KB_EPT = 4;                      // complex elements per thread (block sweeps)
 constexpr int KB_CHUNK = KR_THREADS * KB_EPT;  // elements per block of a block sweep
 constexpr double kBlockPivot = 1e-5;           // smallest accepted Cholesky pivot of the normalised Gram
+constexpr int kBlockDotBlocks = 128;           // dot-sweep blocks per slot (fewer partials to fold in FP64)
 
 struct BlockArgs {
   long long n;          // complex elements per vector
   int mp1;              // basis vectors per slot (restart + 1)
-  int nchunk;           // blocks per slot (KB_CHUNK elements each)
+  int nwork;            // KB_CHUNK-element chunks per vector (update sweep: one block each)
+  int nchunk;           // dot-sweep blocks per slot (each sums several chunks): partials per item
   int nitem;            // partial-sum items per slot (capacity): mp1 * S + S (S + 1) / 2
   const int* run;       // per-slot flags
   const double* sigma;  // [slot][mp1] scales of the stored basis vectors
