@@ -107,12 +107,16 @@ __device__ __forceinline__ dd operator+(dd a, dd b) {
 }
 __device__ __forceinline__ dd operator-(dd a) { return dd(-a.hi, -a.lo); }
 __device__ __forceinline__ dd operator-(dd a, dd b) { return a + (-b); }
+// Product: p = rn(a.hi b.hi) and e = its exact error (FMA) + the cross terms.
+// The pair is left unrenormalised (|e| stays within about one ulp of p):
+// sums renormalise through TwoSum, and a product only ever multiplies e by
+// a hi part, so the skipped QuickTwoSum changes nothing beyond ~2^-46.
 __device__ __forceinline__ dd operator*(dd a, dd b) {
   const float p = __fmul_rn(a.hi, b.hi);
   float e = __fmaf_rn(a.hi, b.hi, -p);
   e = __fmaf_rn(a.hi, b.lo, e);
   e = __fmaf_rn(a.lo, b.hi, e);
-  return dd_quick_two_sum(p, e);
+  return dd(p, e);
 }
 __device__ __forceinline__ dd operator/(dd a, dd b) {
   const float q1 = __fdiv_rn(a.hi, b.hi);
@@ -318,8 +322,8 @@ __device__ __forceinline__ void fft_stage(cx<T> (&v)[16], cx<T>* line, int t, co
 // 16 and the remainder.  On entry v[q] = x[t + q TPL]; on exit v[q] = X[t + q TPL],
 // X[p] = sum_j x[j] e^{-+2 pi i p j/N} (unnormalised; + for INV).  Every thread
 // of the block calls this together (it synchronises the block).  TWM: stage
-// twiddles w^r formed as products of loaded powers of two (measured faster in
-// the FP32 row passes, slower in the column pass; FP32 only).
+// twiddles w^r formed as products of loaded powers of two (fewer L1 loads;
+// measured faster in every FP32 pass; FP32 only).
 template <typename T, int LOGN, bool INV, bool TWM = false>
 __device__ __forceinline__ void fft_line(cx<T> (&v)[16], cx<T>* line, int t, const cx<T>* __restrict__ tw) {
   constexpr int N = 1 << LOGN;

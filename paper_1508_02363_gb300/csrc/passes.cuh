@@ -57,6 +57,15 @@ template <>
 __device__ __forceinline__ float kappa_scale<float>(float c, float den) {
   return __fdividef(c, den);
 }
+// double-float: den is an exact integer in float (m1^2 + m2^2 < 2^24); its
+// reciprocal y = rn(1/den) is corrected by one Newton step with the exact FMA
+// residual e = 1 - den y (1/den = y (1 + e + ...), ~2^-48 relative), then c * (1/den).
+template <>
+__device__ __forceinline__ dd kappa_scale<dd>(dd c, dd den) {
+  const float y = __frcp_rn(den.hi);
+  const float e = __fmaf_rn(-den.hi, y, 1.0f);
+  return c * dd_quick_two_sum(y, __fmul_rn(y, e));
+}
 
 template <typename T, int LOGN>
 struct RowG {
@@ -229,8 +238,8 @@ __global__ void __launch_bounds__(ColG<T, LOGN, CV>::THREADS, ColG<T, LOGN, CV>:
     // Taylor coefficients of this slot (k_coef), issued after the field loads
     if ((MODE == PB_MATVEC || MODE == PB_HOUT || MODE == PB_W) && threadIdx.x < M + 2)
       coef[threadIdx.x] = ccast<T>(a.coef[(size_t)slot * (M + 2) + threadIdx.x]);
-    if (MODE == PB_FWD) fft_line<T, LOGN, false>(v, sl, t, a.tw);
-    else fft_line<T, LOGN, true>(v, sl, t, a.tw);
+    if (MODE == PB_FWD) fft_line<T, LOGN, false, std::is_same<T, float>::value>(v, sl, t, a.tw);
+    else fft_line<T, LOGN, true, std::is_same<T, float>::value>(v, sl, t, a.tw);
   }
   if (MODE == PB_MATVEC || MODE == PB_HOUT || MODE == PB_W) {
     __syncthreads();  // coefficients visible
@@ -255,7 +264,7 @@ __global__ void __launch_bounds__(ColG<T, LOGN, CV>::THREADS, ColG<T, LOGN, CV>:
       const cx<T> eq = cmul(cmul(exv, ldg(EY + q * TPL)), ldg(QC + (size_t)q * TPL * N));
       v[q] = (MODE == PB_RHS) ? eq : cmulc(eq, v[q]);
     }
-    if (MODE != PB_W) fft_line<T, LOGN, false>(v, sl, t, a.tw);
+    if (MODE != PB_W) fft_line<T, LOGN, false, std::is_same<T, float>::value>(v, sl, t, a.tw);
   }
   cx<T>* dst = reinterpret_cast<cx<T>*>(a.out) + (size_t)slot * a.out_ss + (size_t)t * N + j1;
 #pragma unroll
