@@ -71,7 +71,8 @@ template <typename T, int S>
 cudaError_t launch_bupdate(const BlockArgs& a, const int* upd, cx<T>* V, long long vss, int J, int nslots,
                            cudaStream_t s) {
   if (nslots <= 0) return cudaSuccess;
-  k_bupdate<T, S><<<dim3(a.nwork, nslots), KR_THREADS, 0, s>>>(a, upd, V, vss, J);
+  k_bupdate<T, S, false><<<dim3(a.nwork, nslots), KR_THREADS, 0, s>>>(a, upd, V, vss, J);
+  k_bupdate<T, S, true><<<dim3(a.nwork, nslots), KR_THREADS, 0, s>>>(a, upd, V, vss, J);
   return cudaGetLastError();
 }
 #define KB_INST(T, S)                                                                                          \

@@ -531,19 +531,44 @@ static __global__ void __launch_bounds__(KR_THREADS) k_bscalar(BlockArgs a, Cycl
     }
   for (int i = 0; i < S; ++i) sg[J + i] = 1.0;
   upd[slot] = 1;
-  if (stop) c.run[slot] = 0;
+  if (stop) {
+    // last block of this slot's cycle: y = R^{-1} g on the rotated columns, and
+    // ycoef_i = y_i sigma_i, so that the update sweep also adds V y to x
+    const int ns = c.nsteps[slot];
+    double* y = c.ycoef + (size_t)slot * (m + 1);
+    const double* g = c.g + (size_t)slot * (m + 1);
+    for (int i = ns - 1; i >= 0; --i) {
+      double s = g[i];
+      for (int l = i + 1; l < ns; ++l) s -= c.H[((size_t)slot * m + l) * (m + 1) + i] * y[l];
+      const double d = c.H[((size_t)slot * m + i) * (m + 1) + i];
+      y[i] = d != 0.0 ? s / d : 0.0;
+    }
+    for (int i = 0; i < ns; ++i) y[i] *= sg[i];
+    for (int i = ns; i <= m; ++i) y[i] = 0.0;
+    upd[slot] = 2;
+    c.run[slot] = 0;
+  }
 }
 
 // Q_i = sum_k bcoef_ki p_{k+1} + sum_r bcoef'_ri v~_r, written over the chain
-// (basis slots J..J+S-1); slots with upd[slot] != 0 only.
-template <typename T, int S>
+// (basis slots J..J+S-1); slots with upd[slot] != 0 only.  upd[slot] == 2 (the
+// slot's last block of the cycle): also x += sum_r ycoef_r v~_r + sum_i
+// ycoef_{J+i} Q_i, accumulated in T and added to x once (no separate pass
+// over the basis).
+template <typename T, int S, bool XU>
 __global__ void __launch_bounds__(KR_THREADS) k_bupdate(const BlockArgs a, const int* __restrict__ upd,
                                                          cx<T>* __restrict__ V, long long vss, int J) {
   __shared__ T cf[S * S + 129 * S];
+  __shared__ T yc[129 + S];
   const int slot = blockIdx.y;
-  if (!upd[slot]) return;
+  // XU: the launch for slots in their last block (upd == 2); the other launch
+  // (upd == 1) keeps the lean register budget of the plain sweep
+  const int u = upd[slot];
+  if (u != (XU ? 2 : 1)) return;
   const double* bc = a.bcoef + (size_t)slot * (S * S + a.mp1 * S);
   for (int q = threadIdx.x; q < S * S + J * S; q += blockDim.x) cf[q] = (T)bc[q];
+  if (XU)
+    for (int q = threadIdx.x; q < J + S; q += blockDim.x) yc[q] = (T)a.ycoef[(size_t)slot * a.mp1 + q];
   __syncthreads();
   const long long base = (long long)blockIdx.x * KB_CHUNK + threadIdx.x;
   cx<T>* Vs = V + (size_t)slot * vss;
@@ -567,7 +592,11 @@ __global__ void __launch_bounds__(KR_THREADS) k_bupdate(const BlockArgs a, const
         acc[i][e] = s;
       }
   }
+  cx<T> dx[KB_EPT];
+#pragma unroll
+  for (int e = 0; e < KB_EPT; ++e) dx[e] = mkc((T)0, (T)0);
   for (int r = 0; r < J; ++r) {
+    const T yr = XU ? yc[r] : (T)0;
 #pragma unroll
     for (int e = 0; e < KB_EPT; ++e) {
       const long long idx = base + (long long)e * KR_THREADS;
@@ -578,6 +607,7 @@ __global__ void __launch_bounds__(KR_THREADS) k_bupdate(const BlockArgs a, const
           const T c = cf[S * S + r * S + i];
           acc[i][e] = mkc(acc[i][e].re + c * v.re, acc[i][e].im + c * v.im);
         }
+        if (XU) dx[e] = mkc(dx[e].re + yr * v.re, dx[e].im + yr * v.im);
       }
     }
   }
@@ -588,6 +618,25 @@ __global__ void __launch_bounds__(KR_THREADS) k_bupdate(const BlockArgs a, const
       const long long idx = base + (long long)e * KR_THREADS;
       if (idx < a.n) Vs[(size_t)(J + i) * a.n + idx] = acc[i][e];
     }
+  if (XU) {
+#pragma unroll
+    for (int e = 0; e < KB_EPT; ++e) {
+      const long long idx = base + (long long)e * KR_THREADS;
+      if (idx >= a.n) continue;
+      cx<T> d = dx[e];
+#pragma unroll
+      for (int i = 0; i < S; ++i) d = mkc(d.re + yc[J + i] * acc[i][e].re, d.im + yc[J + i] * acc[i][e].im);
+      if constexpr (std::is_same<T, float>::value) {
+        if (a.x_dd) {
+          cx<dd>* xp = reinterpret_cast<cx<dd>*>(a.X) + (size_t)slot * a.xss + idx;
+          *xp = xadd(*xp, d);
+          continue;
+        }
+      }
+      cx<double>* xp = reinterpret_cast<cx<double>*>(a.X) + (size_t)slot * a.xss + idx;
+      *xp = xadd(*xp, d);
+    }
+  }
 }
 
 }  // namespace dbar

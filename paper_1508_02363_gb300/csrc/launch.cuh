@@ -79,6 +79,8 @@ template <int S>
 cudaError_t launch_bscalar(const BlockArgs& a, const CycleState& c, double* Hraw, double* bcoef, int* upd, int J,
                            int nslots, cudaStream_t s);
 template <typename T, int S>
+// two launches: slots continuing their cycle (upd 1), slots in their last
+// block (upd 2, which also add V y to x)
 cudaError_t launch_bupdate(const BlockArgs& a, const int* upd, cx<T>* V, long long vss, int J, int nslots,
                            cudaStream_t s);
 

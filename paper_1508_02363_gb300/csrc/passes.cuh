@@ -394,6 +394,19 @@ __global__ void __launch_bounds__(RowG<T, LOGN>::THREADS, RowG<T, LOGN>::MINB) k
   using NT = typename std::conditional<NF32, float, double>::type;
   const float nsc = NF32 ? a.nscale[slot] : 1.f;
   NT nrm = 0;
+  // double-float right-hand side (||b|| not known yet): FP32 squares scaled by
+  // a power of two near 1 / (this thread's largest |value|), unscaled in FP64
+  // once per thread
+  constexpr bool RHS32 = !std::is_same<T, double>::value && MODE == PC_RHS;
+  float rsc = 1.f, nrm32 = 0.f;
+  if constexpr (RHS32) {
+    float mx = 0.f;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) mx = fmaxf(mx, fmaxf(fabsf((float)v[q].re), fabsf((float)v[q].im)));
+    int e = (__float_as_int(mx) >> 23) & 0xff;  // biased exponent
+    e = e < 1 ? 1 : (e > 253 ? 253 : e);
+    rsc = __int_as_float((254 - e) << 23);  // 2^(127 - e)
+  }
   const size_t rowoff = (size_t)p2 * N + t;
 #pragma unroll
   for (int q = 0; q < 16; ++q) {
@@ -409,8 +422,13 @@ __global__ void __launch_bounds__(RowG<T, LOGN>::THREADS, RowG<T, LOGN>::MINB) k
     } else if (MODE == PC_RHS) {
       reinterpret_cast<cx<T>*>(a.out)[(size_t)slot * a.out_ss + idx] = y;
       reinterpret_cast<cx<TO>*>(a.out2)[(size_t)slot * a.out2_ss + idx] = ccast<TO>(y);
-      const double yr = (double)y.re, yi = (double)y.im;
-      nrm += yr * yr + yi * yi;
+      if constexpr (RHS32) {
+        const float yr = (float)y.re * rsc, yi = (float)y.im * rsc;
+        nrm32 += yr * yr + yi * yi;
+      } else {
+        const double yr = (double)y.re, yi = (double)y.im;
+        nrm += yr * yr + yi * yi;
+      }
     } else {  // PC_RES
       const cx<T> bb = a.b[(size_t)slot * a.f_ss + idx];
       const cx<T> xx = a.x[(size_t)slot * a.f_ss + idx];
@@ -424,6 +442,10 @@ __global__ void __launch_bounds__(RowG<T, LOGN>::THREADS, RowG<T, LOGN>::MINB) k
         nrm += rr * rr + ri * ri;
       }
     }
+  }
+  if constexpr (RHS32) {
+    const double inv = (double)(1.0f / rsc);  // 2^(e - 127), exact
+    nrm = (double)nrm32 * inv * inv;
   }
   if (MODE == PC_RHS || MODE == PC_RES) {
     __shared__ NT wred[32];

@@ -295,10 +295,11 @@ static double xgrid(int j, int N, double L) { return L * (-M_PI + 2.0 * M_PI * (
 
 // Launch through the profiler: counts the launch and, when profiling is on,
 // brackets it with CUDA events on the launching stream.
+// f launches nk kernels (counted in dbar_launch_count)
 template <typename F>
-static cudaError_t timed(dbar_plan* P, cudaStream_t st, int kind, F&& f) {
+static cudaError_t timed(dbar_plan* P, cudaStream_t st, int kind, F&& f, int nk = 1) {
   if (P->capturing) {  // recorded into the cycle graph: counted and timed at each replay
-    P->cap->kernels += 1;
+    P->cap->kernels += nk;
     if (!P->prof.on) return f();
     cudaEvent_t a, b;
     cudaEventCreate(&a);
@@ -309,7 +310,7 @@ static cudaError_t timed(dbar_plan* P, cudaStream_t st, int kind, F&& f) {
     P->cap->recs.push_back({kind, a, b});
     return e;
   }
-  ++P->nlaunch;
+  P->nlaunch += nk;
   if (!P->prof.on) return f();
   cudaEvent_t a = P->prof.get(), b = P->prof.get();
   cudaEventRecord(a, st);
@@ -559,8 +560,9 @@ static dbar_status true_residual(dbar_plan* P, int nb, cudaStream_t st) {
 // vector); per launch of pass B the shared tables Q and Delta_0..Delta_M,
 // (M+2)F.  s-step blocks (J basis vectors, S chain steps): pass A 2F, S pass B
 // 2F, S-1 fused row passes 3F (read T2, write K p_i and T1), one pass C 2F,
-// block dots (J+S)F, block update (J+2S)F.  Per cycle and slot: solution
-// update (ns F + 2 F64), residual passes 2 F64 + 2 F64 + (3 F64 + F), plus
+// block dots (J+S)F, block update (J+2S)F, plus x read and written (2 F64) by
+// the last block's update sweep.  Per cycle and slot: solution update (one
+// vector per sweep: ns F + 2 F64), residual passes 2 F64 + 2 F64 + (3 F64 + F), plus
 // (M+2) F64 of tables per pass-B launch.
 static void account_cycle(dbar_plan* P, const int* act, const int* ns, int nb, int launched_steps) {
   if (!P->prof.on) return;
@@ -584,6 +586,7 @@ static void account_cycle(dbar_plan* P, const int* act, const int* ns, int nb, i
         by[K_DOTS] += F * (J + S);
         by[K_UPDATE] += F * (J + 2 * S);
       }
+      by[K_UPDATE] += 2.0 * F64;  // x read and written by the slot's last update sweep
     } else {
       by[K_PASS_A] += 2.0 * F * k;
       by[K_PASS_B] += 2.0 * F * k;
@@ -591,7 +594,7 @@ static void account_cycle(dbar_plan* P, const int* act, const int* ns, int nb, i
       by[K_DOTS] += F * (k * 2.0 + k * (k - 1) / 2.0);
       by[K_UPDATE] += F * (k * 3.0 + k * (k - 1) / 2.0);
     }
-    by[K_XUPDATE] += F * k + 2.0 * F64;
+    if (P->sstep <= 1) by[K_XUPDATE] += F * k + 2.0 * F64;
     by[K_RES_A] += 2.0 * F64;
     by[K_RES_B] += 2.0 * F64;
     by[K_RES_C] += 3.0 * F64 + F;
@@ -650,6 +653,10 @@ static dbar_status block_steps(dbar_plan* P, int nb, int j0, int j1, cudaStream_
   ba.sigma = P->cs.sigma;
   ba.bcoef = P->bcoef;
   ba.part = P->bpart;
+  ba.ycoef = P->cs.ycoef;
+  ba.X = P->x64;
+  ba.xss = n;
+  ba.x_dd = P->resid_dd ? 1 : 0;
   for (int c0 = j0; c0 < j1; c0 += S) {
     const int J = c0 + 1;  // basis vectors v_0..v_{J-1} exist
     // the chain p_{i+1} = K p_i into basis slots J..J+S-1: pass A of v_{J-1};
@@ -685,7 +692,7 @@ static dbar_status block_steps(dbar_plan* P, int nb, int j0, int j1, cudaStream_
     }
     CK(timed(P, st, K_DOTS, [&] { return launch_bdots<TI, S>(ba, V, vss, J, nb, st); }));
     CK(timed(P, st, K_SCALAR, [&] { return launch_bscalar<S>(ba, P->cs, P->Hraw, P->bcoef, P->upd, J, nb, st); }));
-    CK(timed(P, st, K_UPDATE, [&] { return launch_bupdate<TI, S>(ba, P->upd, V, vss, J, nb, st); }));
+    CK(timed(P, st, K_UPDATE, [&] { return launch_bupdate<TI, S>(ba, P->upd, V, vss, J, nb, st); }, 2));
   }
   return DBAR_OK;
 }
@@ -727,11 +734,16 @@ static dbar_status cycle_tail(dbar_plan* P, int nb, cudaStream_t st) {
   const int m = P->m;
   const long long vss = (long long)(m + 1) * n;
   cx<TI>* V = reinterpret_cast<cx<TI>*>(P->V);
-  CK(timed(P, st, K_SCALAR, [&] { return launch_solve_y(P->cs, nb, st); }));
-  CK(cudaMemcpyAsync(P->h_nsteps, P->cs.nsteps, nb * sizeof(int), cudaMemcpyDeviceToHost, st));
-  CK(timed(P, st, K_XUPDATE, [&] {
-    return launch_xupdate<TI>(n, m + 1, P->cs.nsteps, P->cs.ycoef, V, vss, P->x64, P->resid_dd, n, nb, st);
-  }));
+  if (P->sstep > 1) {
+    // s-step cycles: each slot's last block already solved for y and added V y to x
+    CK(cudaMemcpyAsync(P->h_nsteps, P->cs.nsteps, nb * sizeof(int), cudaMemcpyDeviceToHost, st));
+  } else {
+    CK(timed(P, st, K_SCALAR, [&] { return launch_solve_y(P->cs, nb, st); }));
+    CK(cudaMemcpyAsync(P->h_nsteps, P->cs.nsteps, nb * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(timed(P, st, K_XUPDATE, [&] {
+      return launch_xupdate<TI>(n, m + 1, P->cs.nsteps, P->cs.ycoef, V, vss, P->x64, P->resid_dd, n, nb, st);
+    }));
+  }
   dbar_status s = true_residual<TI>(P, nb, st);
   if (s != DBAR_OK) return s;
   CK(timed(P, st, K_SCALAR, [&] { return launch_cycle_start(P->cs, P->part2, row_blocks(P->N), 0, nb, st); }));

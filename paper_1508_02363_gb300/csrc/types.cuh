@@ -82,6 +82,11 @@ struct BlockArgs {
   const double* sigma;  // [slot][mp1] scales of the stored basis vectors
   const double* bcoef;  // [slot][S*S + mp1*S]: R^{-1} / ||p|| (S x S), then -sigma_r (C R^{-1})_{r,i}
   double* part;         // [slot][nitem][nchunk]
+  // solution update fused into a slot's last block: x += sum_i ycoef_i v~_i
+  const double* ycoef;  // [slot][mp1] y_i sigma_i (written by the block's scalar step)
+  void* X;              // [slot][n] at stride xss: cx<double>, or cx<dd> when x_dd
+  long long xss;
+  int x_dd;
 };
 
 __host__ __device__ constexpr int block_items(int J, int S) { return J * S + S * (S + 1) / 2; }
