@@ -28,6 +28,10 @@ What it computes (paper notation):
   summation at xi = 0, (b) G and sum c_n W_n, (c) h = F^{-1}((S-G)/xi) +
   sum c_n W_n, (d) A S = S + i F(E_k Q conj(h)): three 2-D FFTs.
 
+* DS II reflection coefficient (Sec. 6.1, eq. MainEQDSpm, rviah, m1def, rt):
+  r(k, t) = (i/2)(S_+(0) - S_-(0)) exp(-i t (k^2 + conj(k)^2)/4), S_pm the CGO
+  solutions at the parameter k/2 with the potentials +Q and -Q (reflection()).
+
 Discretisation (Sec. 4.1, eq. domain, xidomain):
   x_j = L(-pi + 2 pi j/N), xi_m = m/L with m in [-N/2+1, N/2] (Nyquist on
   the positive side).  With h = 2 pi L/N the Riemann sums give
@@ -355,3 +359,29 @@ def solve_cgo(Q, k, N, L, M=2, tol=1e-13, restart=40, maxiter=2000, fill="analyt
     S, it, res = P.solve_gmres(tol=tol, restart=restart, maxiter=maxiter)
     m = P.h(S)
     return {"S": S, "m": m, "m1": 1j * S[0, 0], "iters": it, "resid": res}
+
+
+# ---------------------------------------------------------------------------
+# DS II reflection coefficient (Sec. 6.1, eq. MainEQDSpm, hpmdef, rviah,
+# m1def; time dependence eq. rt).
+# ---------------------------------------------------------------------------
+
+
+def reflection(Q, k, N, L, M=2, t=0.0, tol=1e-13, restart=40, maxiter=2000):
+    """r(k, t) for the potential Q (sampled on the x-grid), Sec. 6's convention
+    (k replaced by k/2, so the exponential is e^{(conj(k z) - k z)/2} = E_{k/2}).
+
+    The two equations eq. MainEQDSpm are the CGO equation of Sec. 5.1 at the
+    parameter k/2 with the potentials +Q (S_+) and -Q (S_-).  By eq. m1def,
+    m^(1)_pm = i S_pm(0); by eq. Sform / hpmdef, S_pm(0) = f(0) pm h(i conj k)
+    with f common, so eq. rviah gives
+        r(k) = i h(i conj k) = (m^(1)_+ - m^(1)_-)/2 = (i/2)(S_+(0) - S_-(0)),
+    and eq. rt gives r(k, t) = r(k) exp(-i t (k^2 + conj(k)^2) / 4).
+    Returns dict(r, Sp0, Sm0, iters, resid)."""
+    k = complex(k)
+    sp = solve_cgo(Q, k / 2.0, N, L, M=M, tol=tol, restart=restart, maxiter=maxiter)
+    sm = solve_cgo(-np.asarray(Q), k / 2.0, N, L, M=M, tol=tol, restart=restart, maxiter=maxiter)
+    r0 = 0.5j * (sp["S"][0, 0] - sm["S"][0, 0])
+    r = r0 * np.exp(-1j * t * (k * k + np.conj(k) ** 2) / 4.0)
+    return {"r": complex(r), "Sp0": complex(sp["S"][0, 0]), "Sm0": complex(sm["S"][0, 0]),
+            "iters": (sp["iters"], sm["iters"]), "resid": max(sp["resid"], sm["resid"])}

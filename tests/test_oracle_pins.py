@@ -280,3 +280,36 @@ def test_dbar_equation_holds_on_a_refined_grid():
     assert abs(lhs - rhs).max() < 1e-13
     # coarse-grid points of the refined m agree with the solved m
     assert abs(h2[::2, ::2] - r["m"]).max() < 1e-13
+
+
+# --------------------------------------------------------------------------- reflection coefficient
+
+@pytest.mark.parametrize("k", [0.7 + 0.4j, 2.0 - 1.0j, -1.5j])
+def test_reflection_born_limit_is_the_gaussian_closed_form(k):
+    # Sec. 6.1: for Q = eps exp(-|z|^2), S_pm = mp i eps F(E_{k/2} e^{-|z|^2}) + O(eps^2), and the
+    # second-order terms of S_+ and S_- are equal (the conjugated term flips sign twice), so
+    # r(k) = eps F(e^{-|z|^2} e^{-i(k2 x + k1 y)})(0) + O(eps^3) = (eps/2) e^{-|k|^2/4} + O(eps^3)
+    # (the Gaussian integral; the Fourier convention carries 1/(2 pi)).
+    N, L = 64, 3.0
+    X, Y = wl.mesh(N, L)
+    born = 0.5 * np.exp(-abs(k) ** 2 / 4.0)
+    dev = []
+    for eps in (1e-3, 2e-3):
+        r = orc.reflection(eps * np.exp(-(X * X + Y * Y)), k, N, L)["r"]
+        dev.append(r / eps - born)
+        assert abs(r / eps - born) < 50 * eps * eps, (eps, r / eps, born)
+    # the deviation is O(eps^2) in r/eps (no O(eps) term): doubling eps multiplies it by 4
+    assert abs(dev[1] / dev[0] - 4.0) < 0.2, dev
+
+
+def test_reflection_time_dependence_is_a_unimodular_factor():
+    # eq. rt: r(k, t) = r(k, 0) exp(-i t (k^2 + conj(k)^2)/4), |r| conserved in time
+    N, L = 32, 2.5
+    X, Y = wl.mesh(N, L)
+    Q = 0.8 * np.exp(-(X * X + Y * Y)) * (1 + 0.2j * X)
+    k = 1.2 - 0.7j
+    r0 = orc.reflection(Q, k, N, L, t=0.0)["r"]
+    r1 = orc.reflection(Q, k, N, L, t=0.3)["r"]
+    assert abs(abs(r1) - abs(r0)) < 1e-13 * abs(r0)
+    ang = np.angle(r1 / r0)
+    np.testing.assert_allclose(ang, -0.3 * (k * k + np.conj(k) ** 2).real / 4.0, atol=1e-12)
