@@ -412,6 +412,59 @@ def run_uneven(args):
     print(json.dumps(out))
 
 
+# ----------------------------------------------------------------------------- reflection workload
+
+def run_reflection(args):
+    """DS II reflection coefficient r(k) over the resolved k-grid of Sec. 6's example
+    (q = exp(-(x^2+y^2)), N = 128, L = 3.2, M = 11): 2401 values of k, two CGO solves
+    each, all slots of one sign in one batch.  Throughput = r values / device time."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1508_02363_gb300 import dbar
+    import workloads as wl
+
+    N, L = 128, 3.2
+    Q, k, M = wl.reflection_grid(N, L)
+    Qd = torch.from_numpy(Q).cuda()
+    stream = torch.cuda.current_stream()
+    plan = dbar.Plan(N, L, M=M, prec="mixed", tol=1e-12, restart=args.restart, sstep=args.sstep,
+                     inner_tol=args.inner_tol, max_batch=k.size)
+    for _ in range(args.warmup):
+        dbar.dbar_reflection(plan.handle, Qd, k, stream=stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            r, iters, resid, status = dbar.dbar_reflection(plan.handle, Qd, k, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    # sampled parity against the FP64 GPU path (same entry point, FP64 plan) and the Born-free
+    # CPU oracle on a few k (host cores, spawned pool)
+    sample = np.linspace(0, k.size - 1, 6).astype(int)
+    p64 = dbar.Plan(N, L, M=M, prec="fp64", tol=1e-13, max_batch=len(sample))
+    r64 = dbar.dbar_reflection(p64.handle, Q, k[sample])[0]
+    scale = float(np.max(np.abs(r)))
+    err64 = float(np.max(np.abs(r[sample] - r64)) / scale)
+    out = {"metric": "DS II reflection coefficient: r(k) values/s over the resolved k-grid (2 CGO solves each)",
+           "workload": "reflection", "N": N, "L": L, "M": M, "nk": int(k.size),
+           "ms_per_grid": round(ms, 2), "r_per_s": round(k.size / (ms / 1e3), 1),
+           "solves_per_s": round(2 * k.size / (ms / 1e3), 1),
+           "iters_inner_mean_per_r": float(np.mean(iters[:, 0])), "resid_max": float(np.max(resid)),
+           "status_ok": bool(status == dbar.DBAR_OK), "err_vs_fp64_gpu_max": err64,
+           "err_sample_k": [complex(x).__repr__() for x in k[sample]],
+           "max_abs_r": scale, "clocks": clk.summary()}
+    if not args.no_cpu_baseline:
+        from oracle import dbar_oracle as orc
+        t0 = time.perf_counter()
+        ro = [orc.reflection(Q, kk, N, L, M=M, tol=1e-13)["r"] for kk in k[sample[:2]]]
+        out["err_vs_oracle_max"] = float(np.max(np.abs(r[sample[:2]] - np.array(ro))) / scale)
+        out["oracle_s_per_r"] = round((time.perf_counter() - t0) / 2, 2)
+    print(json.dumps(out))
+
+
 # ----------------------------------------------------------------------------- serving workload
 
 def run_serving(args):
@@ -548,6 +601,8 @@ def main():
         run_reference(args)
     elif args.workload == "serving":
         run_serving(args)
+    elif args.workload == "reflection":
+        run_reflection(args)
     elif args.workload == "uneven":
         run_uneven(args)
     else:

@@ -141,6 +141,26 @@ dbar_status dbar_solve_cgo(dbar_plan_t plan, const double* Q, int nk, const doub
                            double* S_out, double* m_out, int* iters, double* resid,
                            int io_on_device, void* stream);
 
+/* DS II reflection coefficient (Sec. 6.1, eq. MainEQDSpm, hpmdef, rviah,
+ * m1def; time dependence eq. rt).  Sec. 6 replaces k by k/2, so for each k the
+ * plan solves the CGO problem of dbar_solve_cgo at the parameter k/2 twice,
+ * with the potential +Q (S_+) and -Q (S_-), and returns
+ *     r(k, t) = (i/2) (S_+(0) - S_-(0)) exp(-i t (k^2 + conj(k)^2) / 4)
+ * (eq. rviah: r = i h(i conj k) = (m^(1)_+ - m^(1)_-)/2, m^(1) = i S(0)).
+ *   Q        N*N complex (interleaved doubles, row-major [y][x]); host, or
+ *            device when q_on_device != 0
+ *   k        2*nk doubles (Re, Im), host
+ *   t        time of eq. rt (0: r(k, 0))
+ *   r_out    host, 2*nk doubles (Re, Im of r(k, t))
+ *   iters    host or NULL, nk*2 ints: inner iterations of both solves summed,
+ *            and the larger outer-cycle count
+ *   resid    host or NULL, nk doubles: the larger final relative residual
+ * Only S(0) of each solve is copied off the GPU.  Plans made for serving are
+ * rejected (DBAR_EINVAL).  Returns DBAR_ENOCONV when a solve missed tol
+ * (r_out still written). */
+dbar_status dbar_reflection(dbar_plan_t plan, const double* Q, int nk, const double* k, double t,
+                            double* r_out, int* iters, double* resid, int q_on_device, void* stream);
+
 /* --- stage entry points (device pointers; used for parity checks) -------- */
 
 /* A S for nk fields (Sec. 4.3 step 4):  AS[i] = S[i] + i F(E_{k_i} Q conj(h(S[i]))).

@@ -177,6 +177,40 @@ __global__ void k_cast_fields(const cx<double>* __restrict__ in, cx<float>* __re
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     out[i] = ccast<float>(in[i]);
 }
+// x -> -x over n floats / doubles (the potential's sign flip between the two
+// equations of the reflection coefficient)
+__global__ void k_negate_f32(float* __restrict__ p, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    p[i] = -p[i];
+}
+__global__ void k_negate_f64(double* __restrict__ p, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    p[i] = -p[i];
+}
+cudaError_t launch_negate(void* p, long long n, int fp64, cudaStream_t s) {
+  const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+  if (fp64) k_negate_f64<<<blocks, 256, 0, s>>>(reinterpret_cast<double*>(p), n);
+  else k_negate_f32<<<blocks, 256, 0, s>>>(reinterpret_cast<float*>(p), n);
+  return cudaGetLastError();
+}
+
+// out[i] = x[i][0] (the value at xi = 0 of slot i's solution) in FP64
+__global__ void k_gather_s0(const void* __restrict__ x, long long xss, int nb, int x_dd, cx<double>* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nb) return;
+  if (x_dd) {
+    const cx<dd> v = reinterpret_cast<const cx<dd>*>(x)[(size_t)i * xss];
+    out[i] = mkc((double)v.re, (double)v.im);
+  } else {
+    out[i] = reinterpret_cast<const cx<double>*>(x)[(size_t)i * xss];
+  }
+}
+cudaError_t launch_gather_s0(const void* x, long long xss, int nb, int x_dd, cx<double>* out, cudaStream_t s) {
+  if (nb <= 0) return cudaSuccess;
+  k_gather_s0<<<(nb + 127) / 128, 128, 0, s>>>(x, xss, nb, x_dd, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_cast_fields(const cx<double>* in, cx<float>* out, long long n, cudaStream_t s) {
   const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
   k_cast_fields<<<blocks, 256, 0, s>>>(in, out, n);

@@ -101,6 +101,8 @@ cudaError_t launch_add_fields(const void* S, const void* KS, void* AS, long long
 cudaError_t launch_coef(const cx<double>* partA, int part_fp32, int M, int N, const cx<double>* Da64,
                         const cx<float>* Da32, double fillscale, cx<double>* coefp, int* ticket, cx<double>* coef,
                         int nslots, cudaStream_t s);
+cudaError_t launch_negate(void* p, long long n, int fp64, cudaStream_t s);
+cudaError_t launch_gather_s0(const void* x, long long xss, int nb, int x_dd, cx<double>* out, cudaStream_t s);
 cudaError_t launch_cast_fields(const cx<double>* in, cx<float>* out, long long n, cudaStream_t s);
 cudaError_t launch_split_fields(const cx<double>* in, cx<dd>* out, long long n, cudaStream_t s);
 cudaError_t launch_check_finite(const double* p, long long n, int* flag, cudaStream_t s);

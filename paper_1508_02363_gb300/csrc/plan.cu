@@ -187,6 +187,7 @@ struct dbar_plan {
   cx<double>* tcoef = nullptr;  // [B][M+2] Taylor coefficients of the field in flight
   cx<double>* coefp = nullptr;  // [B][N / coef_rows(N)][M+2] k_coef block partials
   int* ticket = nullptr;        // [B] k_coef completion counters (zero between launches)
+  cx<double>* s0buf = nullptr;  // [B] solutions at xi = 0 (reflection coefficient)
   int* flag = nullptr;
   CycleState cs;
   // s-step blocks (sstep > 1)
@@ -1202,6 +1203,7 @@ dbar_status plan_create_ex(const dbar_params* p, int per_slot_q, dbar_plan** out
   AL(P->tcoef, (size_t)B * (P->M + 2));
   AL(P->coefp, (size_t)B * (P->N / coef_rows(P->N)) * (P->M + 2));
   AL(P->ticket, B);
+  AL(P->s0buf, B);
   AL(P->flag, 4);
   CycleState& c = P->cs;
   const int m = P->m;
@@ -1363,6 +1365,79 @@ extern "C" dbar_status dbar_solve_cgo(dbar_plan_t P, const double* Q, int nk, co
       }
       if (resid) resid[k0 + i] = rs[i];
       if (!(rs[i] <= P->p.tol)) noconv = true;
+    }
+  }
+  if (noconv) return fail(DBAR_ENOCONV, "some k did not reach tol");
+  return DBAR_OK;
+}
+
+// DS II reflection coefficient over a list of k (Sec. 6.1): per k the CGO
+// problem at k/2 with +Q and with -Q, r = (i/2)(S_+(0) - S_-(0)) times the
+// time factor of eq. rt.  Per batch of slots the two solves run one after the
+// other with the plan's Q copies negated in between; only S(0) leaves the GPU.
+extern "C" dbar_status dbar_reflection(dbar_plan_t P, const double* Q, int nk, const double* k, double t,
+                                       double* r_out, int* iters, double* resid, int q_on_device, void* stream) {
+  if (!P) return fail(DBAR_EINVAL, "plan is NULL");
+  if (P->per_slot_q) return fail(DBAR_EINVAL, "dbar_reflection needs a plan with one shared potential");
+  dbar_status s = check_k(k, nk);
+  if (s != DBAR_OK) return s;
+  if (!std::isfinite(t)) return fail(DBAR_EINVAL, "t is not finite");
+  if (nk > 0 && !r_out) return fail(DBAR_EINVAL, "r_out is NULL");
+  if (nk == 0) return DBAR_OK;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  s = load_Q(P, Q, q_on_device, st);
+  if (s != DBAR_OK) return s;
+  const long long n = P->n;
+  std::vector<double> khalf(2 * (size_t)nk);
+  for (int i = 0; i < 2 * nk; ++i) khalf[i] = 0.5 * k[i];
+  auto negate_q = [&]() -> dbar_status {
+    CK(timed(P, st, K_OTHER, [&] { return launch_negate(P->Q64, 2 * n, 1, st); }));
+    CK(timed(P, st, K_OTHER, [&] { return launch_negate(P->Q32, 2 * n, 0, st); }));
+    if (P->resid_dd) CK(timed(P, st, K_OTHER, [&] { return launch_negate(P->Q_dd, 4 * n, 0, st); }));
+    return DBAR_OK;
+  };
+  bool noconv = false;
+  std::vector<cx<double>> s0(2 * (size_t)P->B);
+  std::vector<int> it(P->B), nc(P->B);
+  std::vector<double> rs(P->B);
+  for (int k0 = 0; k0 < nk; k0 += P->B) {
+    const int nb = std::min(P->B, nk - k0);
+    s = upload_ek(P, khalf.data() + 2 * k0, nb, st);
+    if (s != DBAR_OK) return s;
+    for (int pm = 0; pm < 2; ++pm) {  // pm = 0: S_+ (potential Q), 1: S_- (potential -Q)
+      if (pm == 1) {
+        s = negate_q();
+        if (s != DBAR_OK) return s;
+      }
+      s = P->mixed ? run_cycles<float>(P, nb, st) : run_cycles<double>(P, nb, st);
+      if (s != DBAR_OK) return s;
+      CK(timed(P, st, K_OTHER, [&] { return launch_gather_s0(P->x64, n, nb, P->resid_dd ? 1 : 0, P->s0buf, st); }));
+      CK(cudaMemcpyAsync(s0.data() + (size_t)pm * P->B, P->s0buf, nb * sizeof(cx<double>), cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(it.data(), P->cs.itot, nb * sizeof(int), cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(nc.data(), P->cs.ncyc, nb * sizeof(int), cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(rs.data(), P->cs.resid, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      for (int i = 0; i < nb; ++i) {
+        if (iters) {
+          int* o = iters + 2 * (size_t)(k0 + i);
+          o[0] = (pm ? o[0] : 0) + it[i];
+          o[1] = pm ? std::max(o[1], nc[i]) : nc[i];
+        }
+        if (resid) resid[k0 + i] = pm ? std::max(resid[k0 + i], rs[i]) : rs[i];
+        if (!(rs[i] <= P->p.tol)) noconv = true;
+      }
+      if (pm == 1) {
+        s = negate_q();  // the plan's potential back to +Q for the next batch
+        if (s != DBAR_OK) return s;
+      }
+    }
+    for (int i = 0; i < nb; ++i) {
+      const std::complex<double> sp(s0[i].re, s0[i].im), sm(s0[(size_t)P->B + i].re, s0[(size_t)P->B + i].im);
+      const std::complex<double> kk(k[2 * (k0 + i)], k[2 * (k0 + i) + 1]);
+      std::complex<double> r = std::complex<double>(0.0, 0.5) * (sp - sm);
+      r *= std::exp(std::complex<double>(0.0, -t / 4.0) * (kk * kk + std::conj(kk) * std::conj(kk)));
+      r_out[2 * (size_t)(k0 + i)] = r.real();
+      r_out[2 * (size_t)(k0 + i) + 1] = r.imag();
     }
   }
   if (noconv) return fail(DBAR_ENOCONV, "some k did not reach tol");

@@ -27,7 +27,7 @@ EXPORTED = ["dbar_params_init", "dbar_last_error", "dbar_plan_create", "dbar_pla
             "dbar_profile_nkinds", "dbar_profile_kind_name", "dbar_profile", "dbar_profile_read",
             "dbar_launch_count", "dbar_fft2_noalloc", "dbar_serve_create", "dbar_serve_submit",
             "dbar_serve_poll", "dbar_serve_wait", "dbar_serve_release", "dbar_serve_stats",
-            "dbar_serve_inject_fault", "dbar_serve_destroy", "dbar_plan_tuning"]
+            "dbar_serve_inject_fault", "dbar_serve_destroy", "dbar_plan_tuning", "dbar_reflection"]
 
 
 class dbar_params(ctypes.Structure):
@@ -65,6 +65,7 @@ _lib.dbar_plan_destroy.argtypes = [_vp]
 _lib.dbar_plan_info.argtypes = [_vp, ctypes.POINTER(ctypes.c_size_t), _ip]
 _lib.dbar_solve_cgo.argtypes = [_vp, _vp, _int, _dp, _vp, _vp, _ip, _dp, _int, _vp]
 _lib.dbar_apply.argtypes = [_vp, _vp, _int, _dp, _vp, _vp, _int, _vp]
+_lib.dbar_reflection.argtypes = [_vp, _vp, _int, _dp, _dbl, _dp, _ip, _dp, _int, _vp]
 _lib.dbar_rhs.argtypes = [_vp, _vp, _int, _dp, _vp, _vp]
 _lib.dbar_m_from_S.argtypes = [_vp, _int, _vp, _vp, _vp]
 _lib.dbar_taylor.argtypes = [_vp, _int, _vp, _dp, _int, _vp]
@@ -171,6 +172,24 @@ def dbar_solve_cgo(plan, Q, k, S_out, m_out=None, iters=None, resid=None, io_on_
     st = _lib.dbar_solve_cgo(plan, _ptr(Q), nk, kb.ctypes.data_as(_dp), _ptr(S_out), _ptr(m_out), ip, rp,
                              int(bool(io_on_device)), _stream(stream))
     return _check(st, (DBAR_OK, DBAR_ENOCONV))
+
+
+def dbar_reflection(plan, Q, k, t: float = 0.0, q_on_device=None, stream=None):
+    """r(k, t) for each k (numpy complex128), plus iters [nk, 2], resid [nk] and the status."""
+    kb = _kbuf(k)
+    nk = kb.size // 2
+    if q_on_device is None:
+        q_on_device = hasattr(Q, "data_ptr")
+    if not q_on_device:
+        Q = np.ascontiguousarray(np.asarray(Q, dtype=np.complex128))
+    r = np.zeros(2 * nk, np.float64)
+    iters = np.zeros((nk, 2), np.int32)
+    resid = np.zeros(nk, np.float64)
+    st = _lib.dbar_reflection(plan, _ptr(Q), nk, kb.ctypes.data_as(_dp), float(t), r.ctypes.data_as(_dp),
+                              iters.ctypes.data_as(_ip), resid.ctypes.data_as(_dp), int(bool(q_on_device)),
+                              _stream(stream))
+    status = _check(st, (DBAR_OK, DBAR_ENOCONV))
+    return r.view(np.complex128), iters, resid, status
 
 
 def dbar_apply(plan, Q, k, S, AS, fp32: bool = False, stream=None) -> None:
