@@ -32,6 +32,11 @@ What it computes (paper notation):
   r(k, t) = (i/2)(S_+(0) - S_-(0)) exp(-i t (k^2 + conj(k)^2)/4), S_pm the CGO
   solutions at the parameter k/2 with the potentials +Q and -Q (reflection()).
 
+* Iterated integral equation (Sec. 5.2-5.3, eq. eqh2 with the shifted
+  regularisation eq. dbarinvShift): h - K_0(H(h)) = -i F(q), 2k on the xi-grid
+  (IteratedProblem, solve_iterated); reflection_iterated() gives r = i h(i conj k)
+  from one solve per k.
+
 Discretisation (Sec. 4.1, eq. domain, xidomain):
   x_j = L(-pi + 2 pi j/N), xi_m = m/L with m in [-N/2+1, N/2] (Nyquist on
   the positive side).  With h = 2 pi L/N the Riemann sums give
@@ -385,3 +390,85 @@ def reflection(Q, k, N, L, M=2, t=0.0, tol=1e-13, restart=40, maxiter=2000):
     r = r0 * np.exp(-1j * t * (k * k + np.conj(k) ** 2) / 4.0)
     return {"r": complex(r), "Sp0": complex(sp["S"][0, 0]), "Sm0": complex(sm["S"][0, 0]),
             "iters": (sp["iters"], sm["iters"]), "resid": max(sp["resid"], sm["resid"])}
+
+
+# ---------------------------------------------------------------------------
+# Iterated integral equation (Sec. 5.2-5.3, eq. eqh2, dbarinvShift): the
+# unknown h, supported near the origin for every k, with 2k on the xi-grid.
+# ---------------------------------------------------------------------------
+
+
+def shift_index(k, L):
+    """Grid offset (m1, m2) of xi0 = 2i conj(k) = 2 k2 + 2i k1, i.e. xi0 = (m1 + i m2)/L;
+    Sec. 5.3 requires 2k on the xi-grid."""
+    m1, m2 = 2.0 * k.imag * L, 2.0 * k.real * L
+    r1, r2 = int(round(m1)), int(round(m2))
+    if abs(m1 - r1) > 1e-9 or abs(m2 - r2) > 1e-9:
+        raise ValueError("2k must lie on the xi-grid (2 k L integer in both components)")
+    return r1, r2
+
+
+class IteratedProblem:
+    """h - K_0(H(h)) = -i F(q) (eq. eqh2) with
+        H(h) = -i F(q conj(F^{-1}(h / (xi - xi0)))),  xi0 = 2i conj(k)   (Sec. 5.3 step 1)
+        K_0(S) = -i F(q conj(F^{-1}(S / xi)))                            (eq. shift)
+    F^{-1}(h/(xi - xi0)) by the shifting argument eq. dbarinvShift: with
+    h~(eta) = h(eta + xi0) (a circular shift on the grid, exact for the periodic
+    discretisation), F^{-1}[g(. - xi0)] = e^{i xi0.x} F^{-1}[g], so
+        F^{-1}(h/(xi - xi0)) = e^{i xi0.x} F^{-1}(h~/eta),
+    the last term regularised exactly as in Sec. 4 (h_of_S)."""
+
+    def __init__(self, q, k, N, L, M=2, fill="analytic"):
+        self.g = Grid(N, L)
+        self.q = np.asarray(q, dtype=np.complex128)
+        self.k = complex(k)
+        self.M, self.fill = M, fill
+        self.m0 = shift_index(self.k, L)
+        xi0 = self.m0[0] / L + 1j * self.m0[1] / L
+        self.mod = np.exp(1j * (xi0.real * self.g.X + xi0.imag * self.g.Y))   # e^{i xi0.x}
+        self.Wn = [W(n, self.g.z) for n in range(M + 1)]
+
+    def shifted(self, h):
+        """h~[m] = h[m + m0] on the periodic grid ([m2][m1] layout)."""
+        return np.roll(h, shift=(-self.m0[1], -self.m0[0]), axis=(-2, -1))
+
+    def H(self, h):
+        u = self.mod * h_of_S(self.shifted(h), self.g, self.M, self.fill, self.Wn)
+        return -1j * self.g.F(self.q * np.conj(u))
+
+    def K0(self, S):
+        return -1j * self.g.F(self.q * np.conj(h_of_S(S, self.g, self.M, self.fill, self.Wn)))
+
+    def rhs(self):
+        return -1j * self.g.F(self.q)
+
+    def apply(self, h):
+        return h - self.K0(self.H(h))
+
+    def solve_gmres(self, tol=1e-13, restart=40, maxiter=2000):
+        to_real = lambda S: np.ascontiguousarray(S).view(np.float64).reshape(-1)
+        N = self.g.N
+        from_real = lambda x: np.ascontiguousarray(x).view(np.complex128).reshape(N, N)
+        b = to_real(self.rhs())
+        x, it, res = gmres(lambda v: to_real(self.apply(from_real(v))), b, tol=tol, restart=restart,
+                           maxiter=maxiter)
+        return from_real(x), it, res
+
+
+def solve_iterated(q, k, N, L, M=2, tol=1e-13, restart=40, maxiter=2000):
+    """h of eq. eqh2 at parameter k: dict(h, iters, resid)."""
+    P = IteratedProblem(q, k, N, L, M)
+    h, it, res = P.solve_gmres(tol=tol, restart=restart, maxiter=maxiter)
+    return {"h": h, "iters": it, "resid": res}
+
+
+def reflection_iterated(q, k, N, L, M=2, t=0.0, tol=1e-13):
+    """r(k, t) through the iterated equation (Sec. 6.1 with Sec. 5.3): in Sec. 6's
+    convention the equation is taken at k/2, so xi0 = i conj(k), and eq. rviah reads
+    r = i h(i conj k) -- one solve per k.  Needs k on the xi-grid (k L integer)."""
+    k = complex(k)
+    sol = solve_iterated(q, k / 2.0, N, L, M=M, tol=tol)
+    m1, m2 = shift_index(k / 2.0, L)
+    h0 = sol["h"][m2 % N, m1 % N]
+    r = 1j * h0 * np.exp(-1j * t * (k * k + np.conj(k) ** 2) / 4.0)
+    return {"r": complex(r), "iters": sol["iters"], "resid": sol["resid"]}

@@ -313,3 +313,46 @@ def test_reflection_time_dependence_is_a_unimodular_factor():
     assert abs(abs(r1) - abs(r0)) < 1e-13 * abs(r0)
     ang = np.angle(r1 / r0)
     np.testing.assert_allclose(ang, -0.3 * (k * k + np.conj(k) ** 2).real / 4.0, atol=1e-12)
+
+
+# --------------------------------------------------------------------------- iterated equation (Sec. 5)
+
+def _mixture(N, L):
+    X, Y = wl.mesh(N, L)
+    return (1.3 * np.exp(-(X * X + Y * Y)) + (0.4 + 0.6j) * np.exp(-((X - 0.5) ** 2 + (Y + 0.3) ** 2) / 0.7)
+            ).astype(np.complex128)
+
+
+@pytest.mark.parametrize("m", [(0, 0), (1, 2), (-3, 1), (4, -5)])
+def test_iterated_equation_reflection_matches_the_direct_route(m):
+    # Sec. 6.1: r = i h(i conj k) from the single iterated solve (eq. eqh2, shifted regularisation
+    # eq. dbarinvShift) equals (i/2)(S_+(0) - S_-(0)) from the two solves of the Sec. 4 method,
+    # wherever the latter resolves the problem (small k): two different discrete operators
+    N, L = 64, 3.0
+    Q = _mixture(N, L)
+    k = (m[0] + 1j * m[1]) / L
+    a = orc.reflection(Q, k, N, L)["r"]
+    b = orc.reflection_iterated(Q, k, N, L)["r"]
+    assert abs(a - b) < 1e-12 * abs(a)
+
+
+@pytest.mark.parametrize("m", [(10, 6), (-8, -12), (14, 0)])
+def test_iterated_equation_born_limit_at_large_k(m):
+    # the Gaussian Born limit r = (eps/2) e^{-|k|^2/4} + O(eps^3) through the iterated equation at
+    # |k| = 3.6 .. 4.5, where E_{k/2} Q already reaches the edge of the xi-box (Nyquist 10)
+    N, L = 64, 3.2
+    X, Y = wl.mesh(N, L)
+    k = (m[0] + 1j * m[1]) / L
+    born = 0.5 * np.exp(-abs(k) ** 2 / 4.0)
+    dev = []
+    for eps in (1e-3, 2e-3):
+        r = orc.reflection_iterated(eps * np.exp(-(X * X + Y * Y)), k, N, L)["r"]
+        dev.append(r / eps - born)
+        assert abs(r / eps - born) < 50 * eps * eps * born + 1e-11, (eps, r / eps, born)
+    assert abs(dev[1] / dev[0] - 4.0) < 0.3, dev
+
+
+def test_iterated_shift_requires_2k_on_the_grid():
+    with pytest.raises(ValueError):
+        orc.shift_index(0.1 + 0.0j, 3.0)
+    assert orc.shift_index((1.5 + 2.0j) / 3.0, 3.0) == (4, 3)
