@@ -96,6 +96,14 @@ typedef struct {
                         a multiple of sstep.  1: one vector per sweep
                         (classical Gram-Schmidt per step).  0 (default): 4
                         if restart is a multiple of 4, else 2 if even, else 1 */
+  int iterated;      /* 1: the plan solves the iterated integral equation of
+                        Sec. 5.2-5.3 (eq. eqh2, shifted regularisation eq.
+                        dbarinvShift) for h instead of the Sec. 4 equation for
+                        S: h - K_0(H(h)) = -i F(Q), supported near the origin
+                        for every k; 2k must lie on the xi-grid (2 k L integer
+                        in both components).  One vector per sweep (sstep 0
+                        or 1); dbar_solve_cgo returns h in S_out and takes no
+                        m_out.  0 (default): the Sec. 4 equation              */
 } dbar_params;
 
 typedef struct dbar_plan* dbar_plan_t;

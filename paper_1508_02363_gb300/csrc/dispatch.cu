@@ -90,5 +90,6 @@ template cudaError_t launch_pass_b<dd, PB_W>(const PassArgs<dd>&, int, cudaStrea
 template cudaError_t launch_pass_b<dd, PB_FWD>(const PassArgs<dd>&, int, cudaStream_t);
 template cudaError_t launch_pass_c<dd, float, PC_RHS>(const PassArgs<dd>&, int, cudaStream_t);
 template cudaError_t launch_pass_c<dd, float, PC_RES>(const PassArgs<dd>&, int, cudaStream_t);
+template cudaError_t launch_pass_c<dd, dd, PC_KS>(const PassArgs<dd>&, int, cudaStream_t);
 
 }  // namespace dbar

@@ -194,20 +194,58 @@ cudaError_t launch_negate(void* p, long long n, int fp64, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// out[i] = x[i][0] (the value at xi = 0 of slot i's solution) in FP64
-__global__ void k_gather_s0(const void* __restrict__ x, long long xss, int nb, int x_dd, cx<double>* __restrict__ out) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nb) return;
-  if (x_dd) {
-    const cx<dd> v = reinterpret_cast<const cx<dd>*>(x)[(size_t)i * xss];
-    out[i] = mkc((double)v.re, (double)v.im);
-  } else {
-    out[i] = reinterpret_cast<const cx<double>*>(x)[(size_t)i * xss];
+// out[slot][p2][p1] = scale_slot * in[slot][(p2 + s2) mod N][(p1 + s1) mod N],
+// (s1, s2) = shift[slot]: h~(eta) = h(eta + xi0) on the periodic grid (the
+// shifted regularisation of Sec. 5).  scale may be NULL (1).
+template <typename T>
+__global__ void k_roll(const cx<T>* __restrict__ in, long long in_ss, const double* __restrict__ scale, int scale_ss,
+                       const int* __restrict__ shift, const int* __restrict__ run, int N, cx<T>* __restrict__ out,
+                       long long out_ss) {
+  const int slot = blockIdx.y;
+  if (run && !run[slot]) return;
+  const long long n = (long long)N * N;
+  const int s1 = shift[2 * slot], s2 = shift[2 * slot + 1];
+  const T sc = scale ? (T)scale[(size_t)slot * scale_ss] : (T)1;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int p2 = (int)(i / N), p1 = (int)(i - (long long)p2 * N);
+    const cx<T> v = in[(size_t)slot * in_ss + (size_t)((p2 + s2) & (N - 1)) * N + ((p1 + s1) & (N - 1))];
+    out[(size_t)slot * out_ss + i] = mkc(sc * v.re, sc * v.im);
   }
 }
-cudaError_t launch_gather_s0(const void* x, long long xss, int nb, int x_dd, cx<double>* out, cudaStream_t s) {
+template <typename T>
+cudaError_t launch_roll(const cx<T>* in, long long in_ss, const double* scale, int scale_ss, const int* shift,
+                        const int* run, int N, cx<T>* out, long long out_ss, int nslots, cudaStream_t s) {
+  if (nslots <= 0) return cudaSuccess;
+  const long long n = (long long)N * N;
+  const int bx = (int)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024);
+  k_roll<T><<<dim3(bx, nslots), 256, 0, s>>>(in, in_ss, scale, scale_ss, shift, run, N, out, out_ss);
+  return cudaGetLastError();
+}
+template cudaError_t launch_roll<float>(const cx<float>*, long long, const double*, int, const int*, const int*, int,
+                                        cx<float>*, long long, int, cudaStream_t);
+template cudaError_t launch_roll<double>(const cx<double>*, long long, const double*, int, const int*, const int*, int,
+                                         cx<double>*, long long, int, cudaStream_t);
+template cudaError_t launch_roll<dd>(const cx<dd>*, long long, const double*, int, const int*, const int*, int,
+                                     cx<dd>*, long long, int, cudaStream_t);
+
+// out[i] = x[i][0] (the value at xi = 0 of slot i's solution) in FP64
+// (at = NULL) or at the per-slot element index at[i]
+__global__ void k_gather_s0(const void* __restrict__ x, long long xss, int nb, int x_dd, const long long* __restrict__ at,
+                            cx<double>* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nb) return;
+  const size_t e = (size_t)i * xss + (at ? (size_t)at[i] : 0);
+  if (x_dd) {
+    const cx<dd> v = reinterpret_cast<const cx<dd>*>(x)[e];
+    out[i] = mkc((double)v.re, (double)v.im);
+  } else {
+    out[i] = reinterpret_cast<const cx<double>*>(x)[e];
+  }
+}
+cudaError_t launch_gather_s0(const void* x, long long xss, int nb, int x_dd, const long long* at, cx<double>* out,
+                             cudaStream_t s) {
   if (nb <= 0) return cudaSuccess;
-  k_gather_s0<<<(nb + 127) / 128, 128, 0, s>>>(x, xss, nb, x_dd, out);
+  k_gather_s0<<<(nb + 127) / 128, 128, 0, s>>>(x, xss, nb, x_dd, at, out);
   return cudaGetLastError();
 }
 

@@ -73,6 +73,7 @@ template cudaError_t launch_pass_b_n<dd, DBAR_LOGN, PB_W, 0>(const PassArgs<dd>&
 template cudaError_t launch_pass_b_n<dd, DBAR_LOGN, PB_FWD, 0>(const PassArgs<dd>&, int, cudaStream_t);
 template cudaError_t launch_pass_c_n<dd, float, DBAR_LOGN, PC_RHS>(const PassArgs<dd>&, int, cudaStream_t);
 template cudaError_t launch_pass_c_n<dd, float, DBAR_LOGN, PC_RES>(const PassArgs<dd>&, int, cudaStream_t);
+template cudaError_t launch_pass_c_n<dd, dd, DBAR_LOGN, PC_KS>(const PassArgs<dd>&, int, cudaStream_t);
 #else
 template cudaError_t launch_pass_a_n<TT, DBAR_LOGN>(const PassArgs<TT>&, int, cudaStream_t);
 template cudaError_t launch_pass_b_n<TT, DBAR_LOGN, PB_MATVEC, 0>(const PassArgs<TT>&, int, cudaStream_t);

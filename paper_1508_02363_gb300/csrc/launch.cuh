@@ -102,7 +102,11 @@ cudaError_t launch_coef(const cx<double>* partA, int part_fp32, int M, int N, co
                         const cx<float>* Da32, double fillscale, cx<double>* coefp, int* ticket, cx<double>* coef,
                         int nslots, cudaStream_t s);
 cudaError_t launch_negate(void* p, long long n, int fp64, cudaStream_t s);
-cudaError_t launch_gather_s0(const void* x, long long xss, int nb, int x_dd, cx<double>* out, cudaStream_t s);
+cudaError_t launch_gather_s0(const void* x, long long xss, int nb, int x_dd, const long long* at, cx<double>* out,
+                             cudaStream_t s);
+template <typename T>
+cudaError_t launch_roll(const cx<T>* in, long long in_ss, const double* scale, int scale_ss, const int* shift,
+                        const int* run, int N, cx<T>* out, long long out_ss, int nslots, cudaStream_t s);
 cudaError_t launch_cast_fields(const cx<double>* in, cx<float>* out, long long n, cudaStream_t s);
 cudaError_t launch_split_fields(const cx<double>* in, cx<dd>* out, long long n, cudaStream_t s);
 cudaError_t launch_check_finite(const double* p, long long n, int* flag, cudaStream_t s);

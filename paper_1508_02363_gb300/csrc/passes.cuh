@@ -414,7 +414,7 @@ __global__ void __launch_bounds__(RowG<T, LOGN>::THREADS, RowG<T, LOGN>::MINB) k
     const size_t idx = rowoff + q * TPL;
     cx<T> y = v[q];
     if (MODE == PC_KS || MODE == PC_RHS || MODE == PC_RES) {
-      if ((p1 + p2) & 1) y = mkc(-y.re, -y.im);
+      if (((p1 + p2) & 1) != (a.neg != 0)) y = mkc(-y.re, -y.im);
       y = (MODE == PC_RHS) ? mkc(y.im, -y.re) : cmuli(y);
     }
     if (MODE == PC_KS || MODE == PC_FWD || MODE == PC_INV) {

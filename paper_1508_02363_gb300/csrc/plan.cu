@@ -188,6 +188,16 @@ struct dbar_plan {
   cx<double>* coefp = nullptr;  // [B][N / coef_rows(N)][M+2] k_coef block partials
   int* ticket = nullptr;        // [B] k_coef completion counters (zero between launches)
   cx<double>* s0buf = nullptr;  // [B] solutions at xi = 0 (reflection coefficient)
+  // iterated equation of Sec. 5 (params.iterated)
+  bool iter = false;
+  int* rolls = nullptr;         // [B][2] grid offset of xi0 = 2i conj(k) per slot (device)
+  int* h_rolls = nullptr;       // [B][2] host staging
+  void* It1 = nullptr;          // [B][n] rolled field (FP64-sized)
+  void* It2 = nullptr;          // [B][n] first operator application (FP64-sized)
+  long long* gat = nullptr;     // [B] per-slot element index for the S(0) / h(xi0) gather
+  cx<double>* ones64 = nullptr;  // [B][N] ones (E = 1), in each arithmetic
+  cx<float>* ones32 = nullptr;
+  cx<dd>* ones_dd = nullptr;
   int* flag = nullptr;
   CycleState cs;
   // s-step blocks (sstep > 1)
@@ -223,6 +233,7 @@ struct dbar_plan {
     for (void* q : allocs) cudaFree(q);
     if (h_active) cudaFreeHost(h_active);
     if (h_nsteps) cudaFreeHost(h_nsteps);
+    if (h_rolls) cudaFreeHost(h_rolls);
     if (hmask) cudaFreeHost(hmask);
     if (h_ek) cudaFreeHost(h_ek);
     cudaSetDevice(cur);
@@ -337,6 +348,18 @@ static void fill_ek(const dbar_plan* P, const double* k, int nb, cx<double>* dst
 
 static dbar_status upload_ek(dbar_plan* P, const double* k, int nb, cudaStream_t st) {
   const int N = P->N;
+  if (P->iter) {
+    // Sec. 5.3: xi0 = 2i conj(k) = 2 k2 + 2i k1 must be a grid point, offset (2 k2 L, 2 k1 L)
+    for (int s = 0; s < nb; ++s) {
+      const double m1 = 2.0 * k[2 * s + 1] * P->p.L, m2 = 2.0 * k[2 * s] * P->p.L;
+      const double r1 = std::nearbyint(m1), r2 = std::nearbyint(m2);
+      if (std::fabs(m1 - r1) > 1e-9 || std::fabs(m2 - r2) > 1e-9)
+        return fail(DBAR_EINVAL, "iterated plan: 2k must lie on the xi-grid (2 k L integer in both components)");
+      P->h_rolls[2 * s] = (int)(((long long)r1 % N + N) % N);
+      P->h_rolls[2 * s + 1] = (int)(((long long)r2 % N + N) % N);
+    }
+    CK(cudaMemcpyAsync(P->rolls, P->h_rolls, 2 * nb * sizeof(int), cudaMemcpyHostToDevice, st));
+  }
   fill_ek(P, k, nb, P->h_ek);
   for (int s = 0; s < nb; ++s) {
     CK(cudaMemcpyAsync(P->ex64 + (size_t)s * N, P->h_ek + (size_t)s * 2 * N, N * sizeof(cx<double>),
@@ -434,6 +457,16 @@ PassArgs<dd> base_args<dd>(const dbar_plan* P) {
   return a;
 }
 
+// E = 1 in the column pass: per-slot rows of ones in place of the slot's E_k
+// factors (K_0 of the iterated equation, its right-hand side); the same layout
+// keeps the column pass's indexing unchanged
+template <typename T>
+static void set_unit_e(const dbar_plan* P, PassArgs<T>& a) {
+  if constexpr (std::is_same<T, float>::value) a.ex = a.ey = P->ones32;
+  else if constexpr (std::is_same<T, double>::value) a.ex = a.ey = P->ones64;
+  else a.ex = a.ey = P->ones_dd;
+}
+
 // Taylor coefficients of the fields pass A just read (k_coef), for pass B.
 template <typename T>
 static cudaError_t launch_coef_for(dbar_plan* P, const PassArgs<T>& a, int nb, cudaStream_t st) {
@@ -444,9 +477,12 @@ static cudaError_t launch_coef_for(dbar_plan* P, const PassArgs<T>& a, int nb, c
 // One application of K (A S = S + K S) to nb fields: S (T) -> T1 -> T2 -> out (T).
 template <typename T>
 static dbar_status apply_K(dbar_plan* P, const cx<T>* S, long long s_ss, const double* scale, int scale_ss,
-                           cx<T>* out, long long o_ss, const int* run, int nb, cudaStream_t st) {
+                           cx<T>* out, long long o_ss, const int* run, int nb, cudaStream_t st, int unitE = 0,
+                           int neg = 0) {
   PassArgs<T> a = base_args<T>(P);
   a.run = run;
+  if (unitE) set_unit_e(P, a);
+  a.neg = neg;
   a.in = S;
   a.in_ss = s_ss;
   a.in_scale = scale;
@@ -465,6 +501,26 @@ static dbar_status apply_K(dbar_plan* P, const cx<T>* S, long long s_ss, const d
   a.out_ss = o_ss;
   CK(timed(P, st, K_PASS_C, [&] { return launch_pass_c<T, T, PC_KS>(a, nb, st); }));
   return DBAR_OK;
+}
+
+// The operator's K on nb fields: A = I + K.  Sec. 4 method: K = apply_K with
+// E_k.  Iterated equation of Sec. 5 (eq. eqh2): A h = h - K_0(H(h)) with
+// H(h) = -i F(q conj(F^{-1}(h/(xi - xi0)))) and K_0(S) = -i F(q conj(F^{-1}(S/xi))).
+// By the shifted regularisation (eq. dbarinvShift), F^{-1}(h/(xi - xi0)) =
+// e^{i xi0.x} F^{-1}(h~/eta) with h~ = h(. + xi0) and e^{-i xi0.x} = E_k, so
+// H(h) = -K_{E_k}(h~), K_0(S) = -K_1(S) and K_it(h) = -K_1(K_{E_k}(h~)):
+// a circular shift, one application with E_k, one with E = 1 and the sign.
+template <typename T>
+static dbar_status apply_op(dbar_plan* P, const cx<T>* S, long long s_ss, const double* scale, int scale_ss,
+                            cx<T>* out, long long o_ss, const int* run, int nb, cudaStream_t st) {
+  if (!P->iter) return apply_K<T>(P, S, s_ss, scale, scale_ss, out, o_ss, run, nb, st);
+  const long long n = P->n;
+  cx<T>* R = reinterpret_cast<cx<T>*>(P->It1);
+  cx<T>* H = reinterpret_cast<cx<T>*>(P->It2);
+  CK(timed(P, st, K_OTHER, [&] { return launch_roll<T>(S, s_ss, scale, scale_ss, P->rolls, run, P->N, R, n, nb, st); }));
+  dbar_status s = apply_K<T>(P, R, n, nullptr, 0, H, n, run, nb, st);
+  if (s != DBAR_OK) return s;
+  return apply_K<T>(P, H, n, nullptr, 0, out, o_ss, run, nb, st, 1, 1);
 }
 
 // h(S) for FP64 fields (m output): pass A then pass B without the forward transform.
@@ -491,6 +547,7 @@ template <typename TC, typename TI>
 static dbar_status build_rhs_t(dbar_plan* P, int nb, cudaStream_t st, const int* dmask) {
   PassArgs<TC> a = base_args<TC>(P);
   a.run = dmask;
+  if (P->iter) set_unit_e(P, a);  // iterated equation: b = -i F(q)
   a.out = P->T2;
   a.out_ss = P->n;
   CK(timed(P, st, K_RHS, [&] { return launch_pass_b<TC, PB_RHS>(a, nb, st); }));
@@ -508,34 +565,62 @@ static dbar_status build_rhs_t(dbar_plan* P, int nb, cudaStream_t st, const int*
 // partials; only active slots.
 template <typename TC, typename TI>
 static dbar_status true_residual_t(dbar_plan* P, int nb, cudaStream_t st) {
-  PassArgs<TC> a = base_args<TC>(P);
-  a.run = P->cs.active;
-  a.in_ss = P->n;
-  a.out = P->T1;
-  a.out_ss = P->n;
-  a.in = reinterpret_cast<const cx<TC>*>(P->x64);  // x stored in TC (FP64 or double-float)
-  CK(timed(P, st, K_RES_A, [&] { return launch_pass_a<TC>(a, nb, st); }));
-  CK(timed(P, st, K_SCALAR, [&] { return launch_coef_for(P, a, nb, st); }));
-  a.in = reinterpret_cast<const cx<TC>*>(P->T1);
-  a.out = P->T2;
-  if constexpr (std::is_same<TC, dd>::value) {
-    // two launches (column IDFT + pointwise, then column DFT): the fused
-    // double-float column pass is too large for the instruction cache
-    // (the column DFT runs in place: each block owns its columns)
-    CK(timed(P, st, K_RES_B, [&] { return launch_pass_b<TC, PB_W>(a, nb, st); }));
-    a.in = reinterpret_cast<const cx<TC>*>(P->T2);
-    CK(timed(P, st, K_RES_B, [&] { return launch_pass_b<TC, PB_FWD>(a, nb, st); }));
+  const long long n = P->n;
+  // pass A, Taylor coefficients and the column pass on `in` -> T2
+  auto passes_ab = [&](const cx<TC>* in, int unitE) -> dbar_status {
+    PassArgs<TC> a = base_args<TC>(P);
+    a.run = P->cs.active;
+    if (unitE) set_unit_e(P, a);
+    a.in = in;
+    a.in_ss = n;
+    a.out = P->T1;
+    a.out_ss = n;
+    CK(timed(P, st, K_RES_A, [&] { return launch_pass_a<TC>(a, nb, st); }));
+    CK(timed(P, st, K_SCALAR, [&] { return launch_coef_for(P, a, nb, st); }));
+    a.in = reinterpret_cast<const cx<TC>*>(P->T1);
+    a.out = P->T2;
+    if constexpr (std::is_same<TC, dd>::value) {
+      // two launches (column IDFT + pointwise, then column DFT): the fused
+      // double-float column pass is too large for the instruction cache
+      // (the column DFT runs in place: each block owns its columns)
+      CK(timed(P, st, K_RES_B, [&] { return launch_pass_b<TC, PB_W>(a, nb, st); }));
+      a.in = reinterpret_cast<const cx<TC>*>(P->T2);
+      CK(timed(P, st, K_RES_B, [&] { return launch_pass_b<TC, PB_FWD>(a, nb, st); }));
+    } else {
+      CK(timed(P, st, K_RES_B, [&] { return launch_pass_b<TC, PB_MATVEC>(a, nb, st); }));
+    }
+    return DBAR_OK;
+  };
+  const cx<TC>* x = reinterpret_cast<const cx<TC>*>(P->x64);  // x stored in TC (FP64 or double-float)
+  dbar_status s;
+  PassArgs<TC> c = base_args<TC>(P);
+  c.run = P->cs.active;
+  c.in_ss = n;
+  if (P->iter) {
+    // K_it x = -K_1(K_{E_k}(x~)): shift, one application with E_k (-> It2), then E = 1 and the sign
+    cx<TC>* R = reinterpret_cast<cx<TC>*>(P->It1);
+    cx<TC>* H = reinterpret_cast<cx<TC>*>(P->It2);
+    CK(timed(P, st, K_OTHER, [&] {
+      return launch_roll<TC>(x, n, nullptr, 0, P->rolls, P->cs.active, P->N, R, n, nb, st);
+    }));
+    if ((s = passes_ab(R, 0)) != DBAR_OK) return s;
+    c.in = reinterpret_cast<const cx<TC>*>(P->T2);
+    c.out = H;
+    c.out_ss = n;
+    CK(timed(P, st, K_RES_C, [&] { return launch_pass_c<TC, TC, PC_KS>(c, nb, st); }));
+    if ((s = passes_ab(H, 1)) != DBAR_OK) return s;
+    c.neg = 1;
   } else {
-    CK(timed(P, st, K_RES_B, [&] { return launch_pass_b<TC, PB_MATVEC>(a, nb, st); }));
+    if ((s = passes_ab(x, 0)) != DBAR_OK) return s;
   }
-  a.in = reinterpret_cast<const cx<TC>*>(P->T2);
-  a.out = nullptr;
-  a.out2 = P->V;
-  a.out2_ss = (long long)(P->m + 1) * P->n;
-  a.b = reinterpret_cast<const cx<TC>*>(P->b64);
-  a.x = reinterpret_cast<const cx<TC>*>(P->x64);
-  a.f_ss = P->n;
-  CK(timed(P, st, K_RES_C, [&] { return launch_pass_c<TC, TI, PC_RES>(a, nb, st); }));
+  c.in = reinterpret_cast<const cx<TC>*>(P->T2);
+  c.out = nullptr;
+  c.out2 = P->V;
+  c.out2_ss = (long long)(P->m + 1) * n;
+  c.b = reinterpret_cast<const cx<TC>*>(P->b64);
+  c.x = x;
+  c.f_ss = n;
+  CK(timed(P, st, K_RES_C, [&] { return launch_pass_c<TC, TI, PC_RES>(c, nb, st); }));
   return DBAR_OK;
 }
 
@@ -718,7 +803,7 @@ static dbar_status cycle_steps(dbar_plan* P, int nb, int j0, int j1, cudaStream_
   ka.part = P->part;
   ka.part2 = P->part2;
   for (int j = j0; j < j1; ++j) {
-    dbar_status s = apply_K<TI>(P, V + (size_t)j * n, vss, P->cs.sigma + j, m + 1, KS, n, P->cs.run, nb, st);
+    dbar_status s = apply_op<TI>(P, V + (size_t)j * n, vss, P->cs.sigma + j, m + 1, KS, n, P->cs.run, nb, st);
     if (s != DBAR_OK) return s;
     CK(timed(P, st, K_DOTS, [&] { return launch_dots<TI>(ka, V, vss, KS, n, j, nb, st); }));
     CK(timed(P, st, K_SCALAR, [&] { return launch_finalize_h(ka, P->cs.H, j, nb, st); }));
@@ -908,6 +993,8 @@ static dbar_status check_params(const dbar_params* p) {
   if (p->sstep != 0 && p->sstep != 1 && p->sstep != 2 && p->sstep != 4)
     return fail(DBAR_EINVAL, "sstep must be 0, 1, 2 or 4");
   if (p->sstep > 1 && p->restart % p->sstep != 0) return fail(DBAR_EINVAL, "restart must be a multiple of sstep");
+  if (p->iterated != 0 && p->iterated != 1) return fail(DBAR_EINVAL, "iterated must be 0 or 1");
+  if (p->iterated && p->sstep > 1) return fail(DBAR_EINVAL, "the iterated equation runs one Krylov vector per sweep");
   return DBAR_OK;
 }
 
@@ -925,6 +1012,15 @@ static dbar_status plan_tables(dbar_plan* P) {
   }
   CK(cudaMemcpy(P->tw64, tw.data(), N * sizeof(cx<double>), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(P->tw32, tw32.data(), N * sizeof(cx<float>), cudaMemcpyHostToDevice));
+  {
+    const size_t cnt = (size_t)P->B * N;
+    std::vector<cx<double>> o64(cnt, mkc(1.0, 0.0));
+    std::vector<cx<float>> o32(cnt, mkc(1.0f, 0.0f));
+    std::vector<cx<dd>> odd(cnt, mkc(dd(1.0f), dd(0.0f)));
+    CK(cudaMemcpy(P->ones64, o64.data(), cnt * sizeof(cx<double>), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(P->ones32, o32.data(), cnt * sizeof(cx<float>), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(P->ones_dd, odd.data(), cnt * sizeof(cx<dd>), cudaMemcpyHostToDevice));
+  }
   // D_a(p) = sum_j x_j^a e^{+2 pi i p j/N}
   const int MA = P->MA;
   std::vector<cx<double>> D((size_t)(MA + 1) * N);
@@ -1097,6 +1193,7 @@ size_t plan_slot_bytes(const dbar_params* p, int per_slot_q) {
              std::min<size_t>((n + KB_CHUNK - 1) / KB_CHUNK, kBlockDotBlocks) * sizeof(double) +
          ((size_t)S * (S + p->restart + 1) + (size_t)p->restart * (p->restart + 1)) * sizeof(double);
   if (per_slot_q) b += F64 + n * sizeof(cx<float>) + (p->prec == DBAR_MIXED ? F64 : 0);
+  if (p->iterated) b += 2 * F64;  // shifted field and first operator application
   return b;
 }
 
@@ -1125,7 +1222,8 @@ dbar_status plan_create_ex(const dbar_params* p, int per_slot_q, dbar_plan** out
   P->M = p->M;
   P->MA = std::max(1, p->M);
   P->m = p->restart;
-  P->sstep = p->sstep > 0 ? p->sstep : (p->restart % 4 == 0 ? 4 : (p->restart % 2 == 0 ? 2 : 1));
+  P->iter = p->iterated != 0;
+  P->sstep = P->iter ? 1 : (p->sstep > 0 ? p->sstep : (p->restart % 4 == 0 ? 4 : (p->restart % 2 == 0 ? 2 : 1)));
   P->mixed = (p->prec == DBAR_MIXED);
   P->resid_dd = P->mixed && p->resid_mode == DBAR_RESID_DOUBLE_FLOAT;
   P->n = (long long)P->N * P->N;
@@ -1161,6 +1259,9 @@ dbar_status plan_create_ex(const dbar_params* p, int per_slot_q, dbar_plan** out
   } while (0)
   const size_t n = (size_t)P->n;
   AL(P->tw64, P->N);
+  AL(P->ones64, (size_t)B * P->N);
+  AL(P->ones32, (size_t)B * P->N);
+  AL(P->ones_dd, (size_t)B * P->N);
   AL(P->tw32, P->N);
   AL(P->Da64, (size_t)(P->MA + 1) * P->N);
   AL(P->Da32, (size_t)(P->MA + 1) * P->N);
@@ -1204,6 +1305,16 @@ dbar_status plan_create_ex(const dbar_params* p, int per_slot_q, dbar_plan** out
   AL(P->coefp, (size_t)B * (P->N / coef_rows(P->N)) * (P->M + 2));
   AL(P->ticket, B);
   AL(P->s0buf, B);
+  AL(P->gat, B);
+  if (P->iter) {
+    AL(P->rolls, 2 * (size_t)B);
+    cx<double>* i1 = nullptr;
+    cx<double>* i2 = nullptr;
+    AL(i1, (size_t)B * n);
+    AL(i2, (size_t)B * n);
+    P->It1 = i1;
+    P->It2 = i2;
+  }
   AL(P->flag, 4);
   CycleState& c = P->cs;
   const int m = P->m;
@@ -1245,6 +1356,7 @@ dbar_status plan_create_ex(const dbar_params* p, int per_slot_q, dbar_plan** out
   if (cudaMallocHost(&P->h_active, (size_t)B * sizeof(int)) != cudaSuccess ||
       cudaMallocHost(&P->hmask, (size_t)B * sizeof(int)) != cudaSuccess ||
       cudaMallocHost(&P->h_nsteps, (size_t)B * sizeof(int)) != cudaSuccess ||
+      cudaMallocHost(&P->h_rolls, 2 * (size_t)B * sizeof(int)) != cudaSuccess ||
       cudaMallocHost(&P->h_ek, (size_t)B * 2 * P->N * sizeof(cx<double>)) != cudaSuccess) {
     delete P;
     return fail(DBAR_ENOMEM, "pinned host allocation failed");
@@ -1330,6 +1442,7 @@ extern "C" dbar_status dbar_solve_cgo(dbar_plan_t P, const double* Q, int nk, co
   dbar_status s = check_k(k, nk);
   if (s != DBAR_OK) return s;
   if (nk > 0 && !S_out) return fail(DBAR_EINVAL, "S_out is NULL");
+  if (P->iter && m_out) return fail(DBAR_EINVAL, "an iterated plan returns h only (m_out must be NULL)");
   if (nk == 0) return DBAR_OK;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   s = load_Q(P, Q, io_on_device, st);
@@ -1400,6 +1513,42 @@ extern "C" dbar_status dbar_reflection(dbar_plan_t P, const double* Q, int nk, c
   std::vector<cx<double>> s0(2 * (size_t)P->B);
   std::vector<int> it(P->B), nc(P->B);
   std::vector<double> rs(P->B);
+  if (P->iter) {
+    // Sec. 5.3 route: one solve of eq. eqh2 per k (at k/2), r = i h(i conj k),
+    // the value of h at the grid offset of xi0 = i conj(k)
+    std::vector<long long> at(P->B);
+    for (int k0 = 0; k0 < nk; k0 += P->B) {
+      const int nb = std::min(P->B, nk - k0);
+      s = upload_ek(P, khalf.data() + 2 * k0, nb, st);
+      if (s != DBAR_OK) return s;
+      for (int i = 0; i < nb; ++i) at[i] = (long long)P->h_rolls[2 * i + 1] * P->N + P->h_rolls[2 * i];
+      CK(cudaMemcpyAsync(P->gat, at.data(), nb * sizeof(long long), cudaMemcpyHostToDevice, st));
+      s = P->mixed ? run_cycles<float>(P, nb, st) : run_cycles<double>(P, nb, st);
+      if (s != DBAR_OK) return s;
+      CK(timed(P, st, K_OTHER, [&] { return launch_gather_s0(P->x64, n, nb, P->resid_dd ? 1 : 0, P->gat, P->s0buf, st); }));
+      CK(cudaMemcpyAsync(s0.data(), P->s0buf, nb * sizeof(cx<double>), cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(it.data(), P->cs.itot, nb * sizeof(int), cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(nc.data(), P->cs.ncyc, nb * sizeof(int), cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(rs.data(), P->cs.resid, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      for (int i = 0; i < nb; ++i) {
+        if (iters) {
+          iters[2 * (size_t)(k0 + i)] = it[i];
+          iters[2 * (size_t)(k0 + i) + 1] = nc[i];
+        }
+        if (resid) resid[k0 + i] = rs[i];
+        if (!(rs[i] <= P->p.tol)) noconv = true;
+        const std::complex<double> h0(s0[i].re, s0[i].im);
+        const std::complex<double> kk(k[2 * (k0 + i)], k[2 * (k0 + i) + 1]);
+        std::complex<double> r = std::complex<double>(0.0, 1.0) * h0;
+        r *= std::exp(std::complex<double>(0.0, -t / 4.0) * (kk * kk + std::conj(kk) * std::conj(kk)));
+        r_out[2 * (size_t)(k0 + i)] = r.real();
+        r_out[2 * (size_t)(k0 + i) + 1] = r.imag();
+      }
+    }
+    if (noconv) return fail(DBAR_ENOCONV, "some k did not reach tol");
+    return DBAR_OK;
+  }
   for (int k0 = 0; k0 < nk; k0 += P->B) {
     const int nb = std::min(P->B, nk - k0);
     s = upload_ek(P, khalf.data() + 2 * k0, nb, st);
@@ -1411,7 +1560,7 @@ extern "C" dbar_status dbar_reflection(dbar_plan_t P, const double* Q, int nk, c
       }
       s = P->mixed ? run_cycles<float>(P, nb, st) : run_cycles<double>(P, nb, st);
       if (s != DBAR_OK) return s;
-      CK(timed(P, st, K_OTHER, [&] { return launch_gather_s0(P->x64, n, nb, P->resid_dd ? 1 : 0, P->s0buf, st); }));
+      CK(timed(P, st, K_OTHER, [&] { return launch_gather_s0(P->x64, n, nb, P->resid_dd ? 1 : 0, nullptr, P->s0buf, st); }));
       CK(cudaMemcpyAsync(s0.data() + (size_t)pm * P->B, P->s0buf, nb * sizeof(cx<double>), cudaMemcpyDeviceToHost, st));
       CK(cudaMemcpyAsync(it.data(), P->cs.itot, nb * sizeof(int), cudaMemcpyDeviceToHost, st));
       CK(cudaMemcpyAsync(nc.data(), P->cs.ncyc, nb * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1468,11 +1617,11 @@ extern "C" dbar_status dbar_apply(dbar_plan_t P, const void* Q, int nk, const do
   if (s != DBAR_OK) return s;
   const long long n = P->n;
   if (fp32)
-    s = apply_K<float>(P, reinterpret_cast<const cx<float>*>(S), n, nullptr, 0, reinterpret_cast<cx<float>*>(P->KS), n,
-                       nullptr, nk, st);
+    s = apply_op<float>(P, reinterpret_cast<const cx<float>*>(S), n, nullptr, 0, reinterpret_cast<cx<float>*>(P->KS),
+                        n, nullptr, nk, st);
   else
-    s = apply_K<double>(P, reinterpret_cast<const cx<double>*>(S), n, nullptr, 0,
-                        reinterpret_cast<cx<double>*>(P->b64), n, nullptr, nk, st);
+    s = apply_op<double>(P, reinterpret_cast<const cx<double>*>(S), n, nullptr, 0,
+                         reinterpret_cast<cx<double>*>(P->b64), n, nullptr, nk, st);
   if (s != DBAR_OK) return s;
   CK(launch_add_fields(S, fp32 ? P->KS : (void*)P->b64, AS, (long long)nk * n, fp32, st));
   CK(cudaStreamSynchronize(st));

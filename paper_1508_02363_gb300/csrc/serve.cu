@@ -285,6 +285,8 @@ void fill_result(const dbar_server* S, const Request* r, dbar_result* out) {
 extern "C" dbar_status dbar_serve_create(const dbar_params* defaults, size_t mem_budget, dbar_server_t* out) {
   if (!out || !defaults) return dbar_internal_fail(DBAR_EINVAL, "dbar_serve_create: NULL argument");
   *out = nullptr;
+  if (defaults->iterated)
+    return dbar_internal_fail(DBAR_EINVAL, "dbar_serve_create: the server solves the Sec. 4 equation (iterated = 0)");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
     cudaGetLastError();

@@ -48,6 +48,7 @@ struct PassArgs {
   const cx<double>* coef;  // [slot][M+2] c_0..c_M, d' (k_coef output, read by pass B)
   double* part;          // [slot][gridDim.x] squared-norm partials (pass C)
   const float* nscale;   // [slot] power-of-two ~1/||b|| (double-float residual norms)
+  int neg;               // row pass C: the transform's output negated (K of the iterated equation)
 };
 
 

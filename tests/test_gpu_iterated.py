@@ -1,0 +1,89 @@
+"""The iterated integral equation of Sec. 5 (eq. eqh2, shifted regularisation)
+through the C ABI against the CPU oracle's literal implementation."""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import dbar_oracle as orc
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dbar():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1508_02363_gb300 import dbar as d
+    return d
+
+
+def rel(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def _mixture(N, L):
+    X, Y = wl.mesh(N, L)
+    return (1.3 * np.exp(-(X * X + Y * Y)) + (0.4 + 0.6j) * np.exp(-((X - 0.5) ** 2 + (Y + 0.3) ** 2) / 0.7)
+            ).astype(np.complex128)
+
+
+def test_iterated_operator_matches_oracle(dbar):
+    torch = pytest.importorskip("torch")
+    N, L = 64, 3.0
+    Q = _mixture(N, L)
+    k = np.array([(2 + 1j) / (2 * L), (-3 + 5j) / (2 * L)])      # 2k on the xi-grid
+    plan = dbar.Plan(N, L, M=2, prec="fp64", iterated=1, max_batch=2)
+    rng = np.random.default_rng(3)
+    g = orc.Grid(N, L)
+    h = np.stack([g.F(np.exp(-((g.X - 0.3) ** 2 + g.Y ** 2)) * (1 + 0.5j * rng.standard_normal()))
+                  for _ in range(2)])
+    Qd = torch.from_numpy(Q).cuda()
+    hd = torch.from_numpy(h).cuda()
+    out = torch.empty_like(hd)
+    dbar.dbar_apply(plan.handle, Qd, k, hd, out)
+    for i in range(2):
+        ref = orc.IteratedProblem(Q, k[i], N, L).apply(h[i])
+        assert rel(out[i].cpu().numpy(), ref) < 1e-13, i
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("mixed", 1e-10)])
+def test_iterated_solve_matches_oracle(dbar, prec, tol):
+    N, L = 64, 3.2
+    Q = _mixture(N, L)
+    k = np.array([0.0, (4 + 2j) / (2 * L), (-6 - 10j) / (2 * L), (12 + 0j) / (2 * L)])
+    plan = dbar.Plan(N, L, M=2, prec=prec, iterated=1, tol=1e-13 if prec == "fp64" else 1e-12, max_batch=4)
+    r = plan.solve(Q, k, want_m=False)
+    assert r["status"] == dbar.DBAR_OK
+    for i in range(k.size):
+        ref = orc.solve_iterated(Q, k[i], N, L, tol=1e-14)["h"]
+        assert rel(r["S"][i], ref) < tol, i
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_reflection_through_the_iterated_equation(dbar, prec):
+    # one solve per k; agrees with the two-solve route and the oracle, also at |k| where the
+    # two-solve route no longer resolves E_{k/2} q
+    N, L = 64, 3.2
+    Q = _mixture(N, L)
+    k = np.array([0.0, (3 - 2j) / L, (-8 + 6j) / L, (12 + 12j) / L])
+    it = dbar.Plan(N, L, M=2, prec=prec, iterated=1, tol=1e-13 if prec == "fp64" else 1e-12, max_batch=4)
+    r, iters, resid, status = dbar.dbar_reflection(it.handle, Q, k)
+    assert status == dbar.DBAR_OK
+    ref = np.array([orc.reflection_iterated(Q, kk, N, L, tol=1e-14)["r"] for kk in k])
+    assert np.max(np.abs(r - ref)) < (1e-12 if prec == "fp64" else 1e-10) * np.max(np.abs(ref))
+    direct = dbar.Plan(N, L, M=2, prec="fp64", tol=1e-13, max_batch=4)
+    r2 = dbar.dbar_reflection(direct.handle, Q, k[:2])[0]
+    assert np.max(np.abs(r[:2] - r2)) < 1e-10 * np.max(np.abs(ref))
+
+
+def test_iterated_plan_rejects_k_off_the_grid_and_m_output(dbar):
+    N, L = 32, 2.5
+    Q = _mixture(N, L)
+    plan = dbar.Plan(N, L, prec="fp64", iterated=1, max_batch=2)
+    with pytest.raises(dbar.DbarError) as e:
+        plan.solve(Q, [0.1234 + 0.0j], want_m=False)
+    assert e.value.status == dbar.DBAR_EINVAL
+    with pytest.raises(dbar.DbarError) as e:
+        plan.solve(Q, [0.0], want_m=True)
+    assert e.value.status == dbar.DBAR_EINVAL

@@ -172,17 +172,20 @@ def uneven_batch(n: int = 1000, seed: int = 11, L: float = 4.0, kmax: float = 12
     return out
 
 
-def reflection_grid(N: int = 128, L: float = 3.2, xi_q: float = 12.5):
+def reflection_grid(N: int = 128, L: float = 3.2, xi_q: float = 12.5, full: bool = False):
     """DS II reflection-coefficient workload (Sec. 6): initial data q = exp(-(x^2+y^2))
     (the paper's Sec. 6 example, N = 128 and L = 3.2 as in its reconstruction table)
     and k on the xi-grid (k and xi are dual in Sec. 6's k/2 convention), restricted to
     the k the grid resolves: E_{k/2} shifts the Fourier support of q by (k2, k1), so
     max(|k1|, |k2|) + xi_q <= N/(2L) with xi_q = 12.5 (beyond it |q^| < 1e-16 max).
-    Returns (Q [N][N] complex128, k [nk] complex128, M = 11)."""
+    full=True: every k of the xi-grid (N^2 values; the iterated equation of Sec. 5
+    resolves them all).  Returns (Q [N][N] complex128, k [nk] complex128, M = 11)."""
     X, Y = mesh(N, L)
     Q = np.exp(-(X * X + Y * Y)).astype(np.complex128)
     mmax = int(math.floor((N / (2.0 * L) - xi_q) * L))
     m = np.arange(-mmax, mmax + 1)
+    if full:
+        m = np.arange(-N // 2 + 1, N // 2 + 1)
     K1, K2 = np.meshgrid(m / L, m / L, indexing="xy")
     return Q, (K1 + 1j * K2).ravel(), 11
 
