@@ -37,6 +37,11 @@ What it computes (paper notation):
   (IteratedProblem, solve_iterated); reflection_iterated() gives r = i h(i conj k)
   from one solve per k.
 
+* DS II potential from r (Sec. 1 eq. dbarrecA/B, qRec, rt; Sec. 6.2): the same
+  formula with z and k exchanged on the k-grid of the box L' = N/(2 pi L)
+  (reflection_on_grid, ds2_potential); the round trip q -> r -> q is pinned by the
+  paper's reconstruction table.
+
 Discretisation (Sec. 4.1, eq. domain, xidomain):
   x_j = L(-pi + 2 pi j/N), xi_m = m/L with m in [-N/2+1, N/2] (Nyquist on
   the positive side).  With h = 2 pi L/N the Riemann sums give
@@ -472,3 +477,38 @@ def reflection_iterated(q, k, N, L, M=2, t=0.0, tol=1e-13):
     h0 = sol["h"][m2 % N, m1 % N]
     r = 1j * h0 * np.exp(-1j * t * (k * k + np.conj(k) ** 2) / 4.0)
     return {"r": complex(r), "iters": sol["iters"], "resid": sol["resid"]}
+
+
+# ---------------------------------------------------------------------------
+# DS II potential from the reflection coefficient (Sec. 1 eq. dbarrecA/B,
+# qRec, rt; Sec. 6.2).  In Sec. 6's convention (k and xi dual) r lives on the
+# points m/L of a problem of box L, i.e. on the x-grid of the box
+# L' = N/(2 pi L), and the D-bar problem in k is the CGO problem in the
+# variable k with the potential conj(r(k, t)) at the parameter z/2:
+# q(z, t) = (m~^(1)_+ - m~^(1)_-)/2, the same formula as r with z and k exchanged.
+# ---------------------------------------------------------------------------
+
+
+def inverse_box(N, L):
+    """L' such that the x-grid of the box L' is the grid m/L of Sec. 6's k."""
+    return N / (2.0 * math.pi * L)
+
+
+def reflection_on_grid(q, N, L, M=2, tol=1e-13):
+    """r(k, 0) at every point k of the x-grid of the box L' = inverse_box(N, L),
+    [k2][k1] layout (one iterated solve per k)."""
+    g = Grid(N, inverse_box(N, L))
+    R = np.empty((N, N), dtype=np.complex128)
+    for a in range(N):
+        for b in range(N):
+            R[a, b] = reflection_iterated(q, g.z[a, b], N, L, M=M, tol=tol)["r"]
+    return R
+
+
+def ds2_potential(R, z, N, L, M=2, t=0.0, tol=1e-13):
+    """q(z, t) from r(k, 0) = R on the k-grid of the box L' = inverse_box(N, L)."""
+    Lp = inverse_box(N, L)
+    g = Grid(N, Lp)
+    k = g.z
+    Qk = np.conj(R * np.exp(-1j * t * (k * k + np.conj(k) ** 2) / 4.0))
+    return reflection_iterated(Qk, complex(z), N, Lp, M=M, tol=tol)["r"]

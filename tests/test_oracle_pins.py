@@ -356,3 +356,21 @@ def test_iterated_shift_requires_2k_on_the_grid():
     with pytest.raises(ValueError):
         orc.shift_index(0.1 + 0.0j, 3.0)
     assert orc.shift_index((1.5 + 2.0j) / 3.0, 3.0) == (4, 3)
+
+
+# --------------------------------------------------------------------------- DS II round trip (Sec. 6.2)
+
+@pytest.mark.parametrize("row", [0, 1])
+def test_ds2_round_trip_reproduces_the_papers_reconstruction_errors(row):
+    # q -> r (one iterated solve per k) -> q (one per z) for q = exp(-x^2-y^2), M = 11, at the
+    # paper's (N, L) pairs; the error must not exceed the printed one and stays within a factor 10
+    t = json.load(open(os.path.join(GOLDEN, "ds2_reconstruction.json")))
+    N, L, err_paper = t["rows"][row]
+    M = t["M"]
+    X, Y = wl.mesh(N, L)
+    q = np.exp(-(X * X + Y * Y)).astype(np.complex128)
+    R = orc.reflection_on_grid(q, N, L, M=M, tol=1e-14)
+    qr = np.array([[orc.ds2_potential(R, X[a, b] + 1j * Y[a, b], N, L, M=M, tol=1e-14) for b in range(N)]
+                   for a in range(N)])
+    err = np.max(np.abs(qr - q))
+    assert err_paper / 10 <= err <= err_paper, (N, L, err, err_paper)
