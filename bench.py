@@ -473,6 +473,59 @@ def run_reflection(args):
     print(json.dumps(out))
 
 
+# ----------------------------------------------------------------------------- DS II round trip workload
+
+def run_ds2(args):
+    """Sec. 6.2: q(x,y,0) = exp(-x^2-y^2) -> r(k) on the whole k-grid (one iterated solve per k)
+    -> q on the whole x-grid (one iterated solve per point), at the paper's (N, L) = (128, 3.2)
+    and (256, 4.2), M = 11; the reconstruction error against q and the paper's printed error,
+    and q at t = 0.1 (eq. rt) with its L2 norm (conserved by DS II)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1508_02363_gb300 import dbar
+    import workloads as wl
+
+    table = json.load(open(os.path.join(ROOT, "tests", "golden", "ds2_reconstruction.json")))
+    M = table["M"]
+    stream = torch.cuda.current_stream()
+    rows = []
+    for N, L, err_paper in table["rows"][4:]:
+        X, Y = wl.mesh(N, L)
+        q = np.exp(-(X * X + Y * Y)).astype(np.complex128)
+        Lp = N / (2.0 * np.pi * L)
+        j = np.arange(N)
+        kg = Lp * (-np.pi + 2.0 * np.pi * j / N)
+        K1, K2 = np.meshgrid(kg, kg, indexing="xy")
+        k = (K1 + 1j * K2).ravel()
+        z = (X + 1j * Y).ravel()
+        mb = min(N * N, 4096)
+        kw = dict(M=M, prec=args.ds2_prec, iterated=1, restart=16, tol=args.ds2_tol, max_batch=mb)
+        fwd, inv = dbar.Plan(N, L, **kw), dbar.Plan(N, Lp, **kw)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e[0].record(stream)
+        r, it_r, res_r, st_r = dbar.dbar_reflection(fwd.handle, q, k, stream=stream)
+        e[1].record(stream)
+        qr, it_q, res_q, st_q = dbar.dbar_ds2_potential(inv.handle, r.reshape(N, N), z, stream=stream)
+        e[2].record(stream)
+        qt = dbar.dbar_ds2_potential(inv.handle, r.reshape(N, N), z, t=0.1, stream=stream)[0]
+        e[3].record(stream)
+        torch.cuda.synchronize()
+        err = float(np.max(np.abs(qr.reshape(N, N) - q)))
+        rows.append({"N": N, "L": L, "solves": 3 * N * N, "ms_r": round(e[0].elapsed_time(e[1]), 1),
+                     "ms_q": round(e[1].elapsed_time(e[2]), 1), "ms_q_t": round(e[2].elapsed_time(e[3]), 1),
+                     "err_reconstruction": err, "err_paper": err_paper,
+                     "iters_mean": float(np.mean(np.concatenate([it_r[:, 0], it_q[:, 0]]))),
+                     "resid_max": float(max(np.max(res_r), np.max(res_q))),
+                     "status_ok": bool(st_r == dbar.DBAR_OK and st_q == dbar.DBAR_OK),
+                     "l2_ratio_t0.1": float(np.linalg.norm(qt) / np.linalg.norm(qr))})
+        fwd.close()
+        inv.close()
+    out = {"metric": "DS II round trip q -> r -> q over whole grids (Sec. 6.2), error vs the paper's table",
+           "workload": "ds2", "M": M, "prec": args.ds2_prec, "tol": args.ds2_tol, "rows": rows}
+    print(json.dumps(out))
+
+
 # ----------------------------------------------------------------------------- serving workload
 
 def run_serving(args):
@@ -588,6 +641,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="mixed_1024")
     ap.add_argument("--restart", type=int, default=32)
+    ap.add_argument("--ds2-prec", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--ds2-tol", type=float, default=1e-13)
     ap.add_argument("--iterated", action="store_true",
                     help="reflection workload: the iterated equation of Sec. 5 over the whole k-grid")
     ap.add_argument("--sstep", type=int, default=0,
@@ -613,6 +668,8 @@ def main():
         run_serving(args)
     elif args.workload == "reflection":
         run_reflection(args)
+    elif args.workload == "ds2":
+        run_ds2(args)
     elif args.workload == "uneven":
         run_uneven(args)
     else:

@@ -169,6 +169,26 @@ dbar_status dbar_solve_cgo(dbar_plan_t plan, const double* Q, int nk, const doub
 dbar_status dbar_reflection(dbar_plan_t plan, const double* Q, int nk, const double* k, double t,
                             double* r_out, int* iters, double* resid, int q_on_device, void* stream);
 
+/* DS II potential q(x, y, t) from the reflection coefficient (Sec. 1 eq.
+ * dbarrecA/B and qRec with the time dependence eq. rt; Sec. 6.2).  The
+ * D-bar problem in k is a CGO problem in the variable k: the plan's grid is
+ * the k-grid (with Sec. 6's convention the reflection coefficient computed on
+ * a plan of box L lives on the points m/L, i.e. on the grid of a plan with
+ * box L' = N/(2 pi L)), its potential is conj(r(k) e^{-i t (k^2 + conj(k)^2)/4})
+ * and its parameter is z/2, so that
+ *     q(z, t) = (m~^(1)_+ - m~^(1)_-)/2,
+ * the quantity dbar_reflection returns with the roles of z and k exchanged.
+ *   r        N*N complex r(k, 0) on the plan's grid, row-major [k2][k1];
+ *            host, or device when r_on_device != 0
+ *   z        2*nz doubles (x, y) of the points where q is wanted, host; an
+ *            iterated plan needs z L' integer in both components (the x-grid
+ *            of the box L)
+ *   q_out    host, 2*nz doubles (Re, Im of q(z, t))
+ *   iters, resid as in dbar_reflection.  Returns DBAR_ENOCONV when a solve
+ *   missed tol (q_out still written). */
+dbar_status dbar_ds2_potential(dbar_plan_t plan, const double* r, double t, int nz, const double* z,
+                               double* q_out, int* iters, double* resid, int r_on_device, void* stream);
+
 /* --- stage entry points (device pointers; used for parity checks) -------- */
 
 /* A S for nk fields (Sec. 4.3 step 4):  AS[i] = S[i] + i F(E_{k_i} Q conj(h(S[i]))).

@@ -228,6 +228,29 @@ template cudaError_t launch_roll<double>(const cx<double>*, long long, const dou
 template cudaError_t launch_roll<dd>(const cx<dd>*, long long, const double*, int, const int*, const int*, int,
                                      cx<dd>*, long long, int, cudaStream_t);
 
+// out[p2][p1] = conj(r[p2][p1] e^{-i t (k^2 + conj(k)^2)/4}), k = x_{p1} + i y_{p2} on the
+// grid x_j = L(-pi + 2 pi j/N): the potential of the D-bar problem in k at time t
+// (eq. rt; k^2 + conj(k)^2 = 2 (x^2 - y^2)).  Once per call, FP64.
+__global__ void k_ds2_kernel_potential(const cx<double>* __restrict__ r, int N, double L, double t,
+                                       cx<double>* __restrict__ out) {
+  const long long n = (long long)N * N;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int p2 = (int)(i / N), p1 = (int)(i - (long long)p2 * N);
+    const double x = L * (-M_PI + 2.0 * M_PI * p1 / N), y = L * (-M_PI + 2.0 * M_PI * p2 / N);
+    double sn, cs;
+    sincos(-0.5 * t * (x * x - y * y), &sn, &cs);
+    const cx<double> v = r[i];
+    out[i] = mkc(v.re * cs - v.im * sn, -(v.re * sn + v.im * cs));
+  }
+}
+cudaError_t launch_ds2_kernel_potential(const cx<double>* r, int N, double L, double t, cx<double>* out,
+                                        cudaStream_t s) {
+  const long long n = (long long)N * N;
+  const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+  k_ds2_kernel_potential<<<blocks, 256, 0, s>>>(r, N, L, t, out);
+  return cudaGetLastError();
+}
+
 // out[i] = x[i][0] (the value at xi = 0 of slot i's solution) in FP64
 // (at = NULL) or at the per-slot element index at[i]
 __global__ void k_gather_s0(const void* __restrict__ x, long long xss, int nb, int x_dd, const long long* __restrict__ at,

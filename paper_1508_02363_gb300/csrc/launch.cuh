@@ -102,6 +102,8 @@ cudaError_t launch_coef(const cx<double>* partA, int part_fp32, int M, int N, co
                         const cx<float>* Da32, double fillscale, cx<double>* coefp, int* ticket, cx<double>* coef,
                         int nslots, cudaStream_t s);
 cudaError_t launch_negate(void* p, long long n, int fp64, cudaStream_t s);
+cudaError_t launch_ds2_kernel_potential(const cx<double>* r, int N, double L, double t, cx<double>* out,
+                                        cudaStream_t s);
 cudaError_t launch_gather_s0(const void* x, long long xss, int nb, int x_dd, const long long* at, cx<double>* out,
                              cudaStream_t s);
 template <typename T>

@@ -1488,18 +1488,14 @@ extern "C" dbar_status dbar_solve_cgo(dbar_plan_t P, const double* Q, int nk, co
 // problem at k/2 with +Q and with -Q, r = (i/2)(S_+(0) - S_-(0)) times the
 // time factor of eq. rt.  Per batch of slots the two solves run one after the
 // other with the plan's Q copies negated in between; only S(0) leaves the GPU.
-extern "C" dbar_status dbar_reflection(dbar_plan_t P, const double* Q, int nk, const double* k, double t,
-                                       double* r_out, int* iters, double* resid, int q_on_device, void* stream) {
-  if (!P) return fail(DBAR_EINVAL, "plan is NULL");
-  if (P->per_slot_q) return fail(DBAR_EINVAL, "dbar_reflection needs a plan with one shared potential");
-  dbar_status s = check_k(k, nk);
-  if (s != DBAR_OK) return s;
-  if (!std::isfinite(t)) return fail(DBAR_EINVAL, "t is not finite");
-  if (nk > 0 && !r_out) return fail(DBAR_EINVAL, "r_out is NULL");
-  if (nk == 0) return DBAR_OK;
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  s = load_Q(P, Q, q_on_device, st);
-  if (s != DBAR_OK) return s;
+// (m^(1)_+ - m^(1)_-)/2 for each k, Sec. 6's convention (the CGO problems at k/2
+// with the plan's potential +Q and -Q, m^(1) = i S(0)), times the time factor
+// of eq. rt at t; the plan's potential is loaded.  The DS II reflection
+// coefficient (eq. rviah) and, with the roles of z and k exchanged, the
+// reconstructed potential (eq. qRec) are both this quantity.
+static dbar_status m1_half_difference(dbar_plan* P, int nk, const double* k, double t, double* r_out, int* iters,
+                                      double* resid, cudaStream_t st) {
+  dbar_status s = DBAR_OK;
   const long long n = P->n;
   std::vector<double> khalf(2 * (size_t)nk);
   for (int i = 0; i < 2 * nk; ++i) khalf[i] = 0.5 * k[i];
@@ -1591,6 +1587,51 @@ extern "C" dbar_status dbar_reflection(dbar_plan_t P, const double* Q, int nk, c
   }
   if (noconv) return fail(DBAR_ENOCONV, "some k did not reach tol");
   return DBAR_OK;
+}
+
+extern "C" dbar_status dbar_reflection(dbar_plan_t P, const double* Q, int nk, const double* k, double t,
+                                       double* r_out, int* iters, double* resid, int q_on_device, void* stream) {
+  if (!P) return fail(DBAR_EINVAL, "plan is NULL");
+  if (P->per_slot_q) return fail(DBAR_EINVAL, "dbar_reflection needs a plan with one shared potential");
+  dbar_status s = check_k(k, nk);
+  if (s != DBAR_OK) return s;
+  if (!std::isfinite(t)) return fail(DBAR_EINVAL, "t is not finite");
+  if (nk > 0 && !r_out) return fail(DBAR_EINVAL, "r_out is NULL");
+  if (nk == 0) return DBAR_OK;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  s = load_Q(P, Q, q_on_device, st);
+  if (s != DBAR_OK) return s;
+  return m1_half_difference(P, nk, k, t, r_out, iters, resid, st);
+}
+
+// DS II potential from the reflection coefficient (Sec. 1 eq. dbarrecA/B, qRec;
+// time dependence eq. rt; Sec. 6.2): with Sec. 6's k/2 convention the D-bar
+// problem in k is the CGO problem in the variable k with the potential
+// conj(r(k, t)) and the parameter z/2, and q(z, t) = (m~^(1)_+ - m~^(1)_-)/2.
+extern "C" dbar_status dbar_ds2_potential(dbar_plan_t P, const double* r, double t, int nz, const double* z,
+                                          double* q_out, int* iters, double* resid, int r_on_device, void* stream) {
+  if (!P) return fail(DBAR_EINVAL, "plan is NULL");
+  if (P->per_slot_q) return fail(DBAR_EINVAL, "dbar_ds2_potential needs a plan with one shared potential");
+  dbar_status s = check_k(z, nz);
+  if (s != DBAR_OK) return s;
+  if (!std::isfinite(t)) return fail(DBAR_EINVAL, "t is not finite");
+  if (!r) return fail(DBAR_EINVAL, "r is NULL");
+  if (nz > 0 && !q_out) return fail(DBAR_EINVAL, "q_out is NULL");
+  if (nz == 0) return DBAR_OK;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const long long n = P->n;
+  const cx<double>* rd = reinterpret_cast<const cx<double>*>(r);
+  if (!r_on_device) {
+    for (long long i = 0; i < 2 * n; ++i)
+      if (!std::isfinite(r[i])) return fail(DBAR_EINVAL, "r has a non-finite entry");
+    CK(cudaMemcpyAsync(P->T1, r, n * sizeof(cx<double>), cudaMemcpyHostToDevice, st));
+    rd = reinterpret_cast<const cx<double>*>(P->T1);
+  }
+  // potential of the problem in k: conj(r(k) e^{-i t (k^2 + conj(k)^2)/4}) on the plan's grid
+  CK(timed(P, st, K_OTHER, [&] { return launch_ds2_kernel_potential(rd, P->N, P->p.L, t, P->Qdev, st); }));
+  s = load_Q_device(P, P->Qdev, st);
+  if (s != DBAR_OK) return s;
+  return m1_half_difference(P, nz, z, 0.0, q_out, iters, resid, st);
 }
 
 // ---------------------------------------------------------------------------

@@ -27,7 +27,8 @@ EXPORTED = ["dbar_params_init", "dbar_last_error", "dbar_plan_create", "dbar_pla
             "dbar_profile_nkinds", "dbar_profile_kind_name", "dbar_profile", "dbar_profile_read",
             "dbar_launch_count", "dbar_fft2_noalloc", "dbar_serve_create", "dbar_serve_submit",
             "dbar_serve_poll", "dbar_serve_wait", "dbar_serve_release", "dbar_serve_stats",
-            "dbar_serve_inject_fault", "dbar_serve_destroy", "dbar_plan_tuning", "dbar_reflection"]
+            "dbar_serve_inject_fault", "dbar_serve_destroy", "dbar_plan_tuning", "dbar_reflection",
+            "dbar_ds2_potential"]
 
 
 class dbar_params(ctypes.Structure):
@@ -66,6 +67,7 @@ _lib.dbar_plan_info.argtypes = [_vp, ctypes.POINTER(ctypes.c_size_t), _ip]
 _lib.dbar_solve_cgo.argtypes = [_vp, _vp, _int, _dp, _vp, _vp, _ip, _dp, _int, _vp]
 _lib.dbar_apply.argtypes = [_vp, _vp, _int, _dp, _vp, _vp, _int, _vp]
 _lib.dbar_reflection.argtypes = [_vp, _vp, _int, _dp, _dbl, _dp, _ip, _dp, _int, _vp]
+_lib.dbar_ds2_potential.argtypes = [_vp, _vp, _dbl, _int, _dp, _dp, _ip, _dp, _int, _vp]
 _lib.dbar_rhs.argtypes = [_vp, _vp, _int, _dp, _vp, _vp]
 _lib.dbar_m_from_S.argtypes = [_vp, _int, _vp, _vp, _vp]
 _lib.dbar_taylor.argtypes = [_vp, _int, _vp, _dp, _int, _vp]
@@ -190,6 +192,25 @@ def dbar_reflection(plan, Q, k, t: float = 0.0, q_on_device=None, stream=None):
                               _stream(stream))
     status = _check(st, (DBAR_OK, DBAR_ENOCONV))
     return r.view(np.complex128), iters, resid, status
+
+
+def dbar_ds2_potential(plan, r, z, t: float = 0.0, r_on_device=None, stream=None):
+    """q(z, t) at the points z (numpy complex128) from r(k, 0) on the plan's grid, plus
+    iters [nz, 2], resid [nz] and the status."""
+    zb = _kbuf(z)
+    nz = zb.size // 2
+    if r_on_device is None:
+        r_on_device = hasattr(r, "data_ptr")
+    if not r_on_device:
+        r = np.ascontiguousarray(np.asarray(r, dtype=np.complex128))
+    q = np.zeros(2 * nz, np.float64)
+    iters = np.zeros((nz, 2), np.int32)
+    resid = np.zeros(nz, np.float64)
+    st = _lib.dbar_ds2_potential(plan, _ptr(r), float(t), nz, zb.ctypes.data_as(_dp), q.ctypes.data_as(_dp),
+                                 iters.ctypes.data_as(_ip), resid.ctypes.data_as(_dp), int(bool(r_on_device)),
+                                 _stream(stream))
+    status = _check(st, (DBAR_OK, DBAR_ENOCONV))
+    return q.view(np.complex128), iters, resid, status
 
 
 def dbar_apply(plan, Q, k, S, AS, fp32: bool = False, stream=None) -> None:

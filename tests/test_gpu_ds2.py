@@ -1,0 +1,68 @@
+"""DS II round trip through the C ABI (Sec. 6.2): q -> r (dbar_reflection on an iterated
+plan) -> q (dbar_ds2_potential), against the paper's reconstruction table and the CPU oracle."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import dbar_oracle as orc
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def dbar():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1508_02363_gb300 import dbar as d
+    return d
+
+
+def _round_trip(dbar, N, L, M, prec, t=0.0):
+    X, Y = wl.mesh(N, L)
+    q = np.exp(-(X * X + Y * Y)).astype(np.complex128)
+    Lp = orc.inverse_box(N, L)
+    g = orc.Grid(N, Lp)
+    tol = 1e-13 if prec == "fp64" else 1e-12
+    fwd = dbar.Plan(N, L, M=M, prec=prec, iterated=1, restart=16, tol=tol, max_batch=min(N * N, 1024))
+    r, _, _, st = dbar.dbar_reflection(fwd.handle, q, g.z.ravel())
+    assert st == dbar.DBAR_OK
+    inv = dbar.Plan(N, Lp, M=M, prec=prec, iterated=1, restart=16, tol=tol, max_batch=min(N * N, 1024))
+    z = (X + 1j * Y).ravel()
+    qr, _, _, st = dbar.dbar_ds2_potential(inv.handle, r.reshape(N, N), z, t=t)
+    assert st == dbar.DBAR_OK
+    return q, qr.reshape(N, N), r.reshape(N, N)
+
+
+@pytest.mark.parametrize("row,prec", [(2, "fp64"), (3, "fp64"), (3, "mixed")])
+def test_round_trip_reproduces_the_papers_reconstruction_errors(dbar, row, prec):
+    t = json.load(open(os.path.join(GOLDEN, "ds2_reconstruction.json")))
+    N, L, err_paper = t["rows"][row]
+    q, qr, _ = _round_trip(dbar, N, L, t["M"], prec)
+    err = float(np.max(np.abs(qr - q)))
+    assert err_paper / 10 <= err <= err_paper, (N, L, prec, err, err_paper)
+
+
+def test_round_trip_matches_the_oracle(dbar):
+    # r at sampled k against the oracle; q from the GPU's r against the oracle's formula on the
+    # same r (the oracle needs one solve per point, so r is not recomputed on the whole grid)
+    N, L, M = 32, 1.5, 11
+    q, qr, r = _round_trip(dbar, N, L, M, "fp64")
+    g = orc.Grid(N, orc.inverse_box(N, L))
+    for a, b in ((0, 0), (7, 21), (16, 16), (31, 4)):
+        ro = orc.reflection_iterated(q, g.z[a, b], N, L, M=M, tol=1e-14)["r"]
+        assert abs(r[a, b] - ro) < 1e-12 * np.max(np.abs(r)), (a, b)
+    X, Y = wl.mesh(N, L)
+    for a, b in ((0, 0), (5, 9), (16, 16), (30, 3)):
+        qo = orc.ds2_potential(r, X[a, b] + 1j * Y[a, b], N, L, M=M, tol=1e-14)
+        assert abs(qr[a, b] - qo) < 1e-12, (a, b)
+    # time evolution (eq. rt) through both
+    z = X[16, 16] + 1j * Y[16, 16]
+    Lp = orc.inverse_box(N, L)
+    inv = dbar.Plan(N, Lp, M=M, prec="fp64", iterated=1, restart=16, tol=1e-13, max_batch=4)
+    qt = dbar.dbar_ds2_potential(inv.handle, r, np.array([z]), t=0.3)[0][0]
+    assert abs(qt - orc.ds2_potential(r, z, N, L, M=M, t=0.3, tol=1e-14)) < 1e-12
