@@ -42,6 +42,13 @@ What it computes (paper notation):
   (reflection_on_grid, ds2_potential); the round trip q -> r -> q is pinned by the
   paper's reconstruction table.
 
+* Convolution regularisation (Sec. 4.2, remark after eq. fourreg5a): G = S e^{-|xi|^2},
+  so (S - G)/xi = S (1 - e^{-|xi|^2})/xi is smooth (0 at xi = 0) and goes through the
+  FFT, while F^{-1}(G/xi) = (1/2pi) int F^{-1}(S)(z') W_0(z - z') d^2z' is summed
+  directly over the grid, a four-dimensional sum (h_of_S_conv, ConvProblem,
+  solve_cgo_conv).  The paper keeps this variant as an independent test of the
+  Taylor-Gaussian code.
+
 Discretisation (Sec. 4.1, eq. domain, xidomain):
   x_j = L(-pi + 2 pi j/N), xi_m = m/L with m in [-N/2+1, N/2] (Nyquist on
   the positive side).  With h = 2 pi L/N the Riemann sums give
@@ -369,6 +376,77 @@ def solve_cgo(Q, k, N, L, M=2, tol=1e-13, restart=40, maxiter=2000, fill="analyt
     S, it, res = P.solve_gmres(tol=tol, restart=restart, maxiter=maxiter)
     m = P.h(S)
     return {"S": S, "m": m, "m1": 1j * S[0, 0], "iters": it, "resid": res}
+
+
+# ---------------------------------------------------------------------------
+# Convolution regularisation (Sec. 4.2, remark after eq. fourreg5a).
+# ---------------------------------------------------------------------------
+
+
+def conv_kernel_table(g: Grid):
+    """W_0(z_j - z_j') at every difference of two grid points: [dy + N-1][dx + N-1]
+    with z_j - z_j' = h (dx + i dy), h = 2 pi L/N, dx, dy in [-(N-1), N-1]."""
+    N = g.N
+    h = 2.0 * np.pi * g.L / N
+    d = np.arange(-(N - 1), N)
+    DX, DY = np.meshgrid(d, d, indexing="xy")
+    return W(0, h * (DX + 1j * DY))
+
+
+def gauss_convolution(s, g: Grid, K=None):
+    """(1/2pi) int s(z') W_0(z - z') d^2z' by the trapezoidal rule on the x-grid (the
+    periodic box's quadrature, area h^2 per point), summed directly over every pair of
+    grid points -- the four-dimensional sum of the remark after eq. fourreg5a:
+        out[y][x] = (h^2/2pi) sum_{y', x'} s[y'][x'] K[y - y' + N-1][x - x' + N-1].
+    s may carry leading batch axes."""
+    N = g.N
+    if K is None:
+        K = conv_kernel_table(g)
+    h = 2.0 * np.pi * g.L / N
+    s = np.asarray(s, dtype=np.complex128)
+    # win[a][b][y][x] = K[a + y][b + x]; the pair (y', x') uses a = N-1-y', b = N-1-x'
+    win = np.lib.stride_tricks.sliding_window_view(K, (N, N))
+    s_rev = s[..., ::-1, ::-1]
+    out = np.einsum("...ab,abyx->...yx", s_rev, win)
+    return out * (h * h / (2.0 * np.pi))
+
+
+def h_of_S_conv(S, g: Grid, K=None):
+    """h = F^{-1}(S/xi) with G = S e^{-|xi|^2} (eq. Sreg):
+        F^{-1}((S - G)/xi) = F^{-1}(S (1 - e^{-|xi|^2})/xi)   (smooth; 0 at xi = 0)
+        F^{-1}(G/xi)       = (1/2pi) int F^{-1}(S)(z') W_0(z - z') d^2z'."""
+    xi = g.xi.copy()
+    r2 = (xi * np.conj(xi)).real
+    xi[0, 0] = 1.0                                # placeholder, the factor is 0 there
+    mult = -np.expm1(-r2) / xi
+    mult[0, 0] = 0.0
+    u = g.Finv(S * mult)
+    s = g.Finv(S)
+    return u + gauss_convolution(s, g, K)
+
+
+def dbar_inverse_conv(f, g: Grid):
+    """dbar^{-1} f = F^{-1}(-2i/xi F f) (Sec. 3 lemma) through the convolution regularisation."""
+    return h_of_S_conv(-2j * g.F(f), g)
+
+
+class ConvProblem(CGOProblem):
+    """The CGO operator of Sec. 4.3 (Q -> E_k Q) with h(S) from the convolution
+    regularisation instead of the Taylor-Gaussian G; same right-hand side."""
+
+    def __init__(self, Q, k: complex, N: int, L: float):
+        super().__init__(Q, k, N, L, M=0)
+        self.K = conv_kernel_table(self.g)
+
+    def h(self, S):
+        return h_of_S_conv(S, self.g, self.K)
+
+
+def solve_cgo_conv(Q, k, N, L, tol=1e-13, restart=40, maxiter=2000):
+    """One CGO solve with the convolution regularisation: dict(S, m, m1, iters, resid)."""
+    P = ConvProblem(Q, k, N, L)
+    S, it, res = P.solve_gmres(tol=tol, restart=restart, maxiter=maxiter)
+    return {"S": S, "m": P.h(S), "m1": 1j * S[0, 0], "iters": it, "resid": res}
 
 
 # ---------------------------------------------------------------------------

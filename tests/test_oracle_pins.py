@@ -374,3 +374,74 @@ def test_ds2_round_trip_reproduces_the_papers_reconstruction_errors(row):
                    for a in range(N)])
     err = np.max(np.abs(qr - q))
     assert err_paper / 10 <= err <= err_paper, (N, L, err, err_paper)
+
+
+# --------------------------------------------------------------------------- convolution regularisation
+
+def test_gaussian_convolution_is_the_closed_form():
+    # F s = (1/2) e^{-|xi|^2/4} e^{-i xi.z0} for s = e^{-|z - z0|^2}, so
+    # F^{-1}(F(s) e^{-|xi|^2}/xi) = (1/2) F^{-1}(e^{-(5/4)|xi|^2}/xi)(z - z0)
+    #                             = (1/2) (i/(z - z0)) (1 - e^{-|z - z0|^2/5}),
+    # the lemma of Sec. 3 with 1/(4 * 5/4); the direct grid sum must reach it.
+    z0 = 0.4 - 0.3j
+    g = orc.Grid(32, 2.0)
+    w = g.z - z0
+    r2 = (w * np.conj(w)).real
+    s = np.exp(-r2)
+    with np.errstate(all="ignore"):
+        exact = 0.5j / w * (-np.expm1(-r2 / 5.0))
+    exact[r2 == 0] = 0.0
+    out = orc.gauss_convolution(s, g)
+    assert abs(out - exact).max() < 1e-14
+    # batch axes are summed independently
+    out2 = orc.gauss_convolution(np.stack([s, 2j * s]), g)
+    assert abs(out2[1] - 2j * exact).max() < 2e-14
+
+
+def test_conv_kernel_is_W0_at_grid_differences():
+    # W_0 is odd and vanishes at 0; the table's centre row is W_0 on the x-axis
+    g = orc.Grid(16, 1.0)
+    K = orc.conv_kernel_table(g)
+    assert K.shape == (31, 31)
+    assert K[15, 15] == 0
+    assert abs(K + K[::-1, ::-1]).max() < 1e-15
+    h = 2 * np.pi / 16
+    x = h * np.arange(1, 16)
+    assert abs(K[15, 16:] - 1j / x * (-np.expm1(-x * x / 4))).max() < 1e-15
+
+
+def test_dbar_inverse_conv_worked_example():
+    # dbartest (a = 1/2, b = 1, c = i) through G = S e^{-|xi|^2}: the smooth remainder's
+    # x-space tail decays only like e^{-|z|^2/(4 + 1/a)}, so it needs the larger box
+    g = orc.Grid(128, 5.0)
+    f, exact = _dbartest(g, 0.5, 1.0, 1j)
+    assert abs(orc.dbar_inverse_conv(f, g) - exact).max() < 1e-13
+    g = orc.Grid(64, 4.0)
+    f, exact = _dbartest(g, 0.5, 1.0, 1j)
+    assert abs(orc.dbar_inverse_conv(f, g) - exact).max() < 1e-10
+
+
+def test_conv_and_taylor_regularisations_give_the_same_cgo_solution():
+    # the paper's use of the convolution code: an independent test of the Taylor-Gaussian one
+    N, L, k = 64, 4.0, 0.7 + 0.4j
+    g = orc.Grid(N, L)
+    Q = np.exp(-(g.z * np.conj(g.z)).real).astype(np.complex128)
+    a = orc.solve_cgo_conv(Q, k, N, L)
+    b = orc.solve_cgo(Q, k, N, L, M=11)
+    assert a["resid"] < 1e-13 and b["resid"] < 1e-13
+    assert abs(a["S"] - b["S"]).max() < 1e-13 * abs(b["S"]).max()
+    assert abs(a["m"] - b["m"]).max() < 1e-13
+    # with M = 0 the Taylor route is only algebraically accurate: the agreement is lost
+    c = orc.solve_cgo(Q, k, N, L, M=0)
+    assert abs(c["m"] - a["m"]).max() > 1e-9
+
+
+def test_conv_operator_krylov_agrees_with_dense_solve():
+    N, L, k = 16, 2.0, -0.5 + 0.9j
+    g = orc.Grid(N, L)
+    Q = (1.5 - 0.5j) * np.exp(-(g.z * np.conj(g.z)).real)
+    P = orc.ConvProblem(Q, k, N, L)
+    Sd = P.solve_dense()
+    Sg, it, res = P.solve_gmres(tol=1e-14)
+    assert abs(Sd - Sg).max() < 1e-12 * abs(Sd).max()
+    assert P.residual(Sd) < 1e-13
