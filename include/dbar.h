@@ -64,6 +64,23 @@ typedef enum {
   DBAR_RESID_FP64 = 1          /* native FP64                                   */
 } dbar_resid_mode;
 
+/* How F^{-1}(S/xi) is regularised at xi = 0 (eq. Sreg: S/xi = (S - G)/xi + G/xi). */
+typedef enum {
+  DBAR_REG_TAYLOR = 0, /* G = e^{-|xi|^2} sum_{n<=M} c_n conj(xi)^n (Sec. 4.2, eq.
+                          Gchoice), F^{-1}(G/xi) = sum c_n W_n in closed form;
+                          the method of the paper (default)                    */
+  DBAR_REG_CONV = 1    /* G = S e^{-|xi|^2} (Sec. 4.2, remark after eq.
+                          fourreg5a): (S - G)/xi = S (1 - e^{-|xi|^2})/xi is
+                          smooth and goes through the FFT, and
+                          F^{-1}(G/xi) = (1/2pi) int F^{-1}(S)(z') W_0(z - z') d^2z'
+                          is summed directly over every pair of grid points
+                          (N^4 complex multiply-adds per field).  The paper
+                          keeps it as an independent test of the Taylor code.
+                          FP64 only (prec = DBAR_FP64), N <= 256, one Krylov
+                          vector per sweep, not with iterated; M is unused and
+                          dbar_taylor returns DBAR_EINVAL                     */
+} dbar_regularisation;
+
 typedef struct {
   int N;             /* grid points per axis: power of two, 32 <= N <= 2048    */
   double L;          /* box [-pi L, pi L]^2 (Sec. 4.1, eq. domain), L > 0        */
@@ -104,6 +121,7 @@ typedef struct {
                         in both components).  One vector per sweep (sstep 0
                         or 1); dbar_solve_cgo returns h in S_out and takes no
                         m_out.  0 (default): the Sec. 4 equation              */
+  int regularisation; /* dbar_regularisation; 0 (DBAR_REG_TAYLOR) by default */
 } dbar_params;
 
 typedef struct dbar_plan* dbar_plan_t;
@@ -302,7 +320,10 @@ dbar_status dbar_profile(dbar_plan_t plan, int enable);
 
 /* Totals of one kind since dbar_profile(plan, 1): summed event time in ms,
  * launches, and the algorithmic bytes of those launches (every field the
- * method reads or writes counted once per use).  Any pointer may be NULL. */
+ * method reads or writes counted once per use).  For the kind
+ * "conv_direct_sum" (the direct sum of DBAR_REG_CONV, bound by FP64
+ * arithmetic) the last value counts floating-point operations instead:
+ * 8 N^4 per field and operator application.  Any pointer may be NULL. */
 dbar_status dbar_profile_read(dbar_plan_t plan, int kind, double* ms, long long* launches, double* bytes);
 
 /* The autotuner's choice: column-pass tile variant in use (0: 64-byte row

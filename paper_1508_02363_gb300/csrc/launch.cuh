@@ -109,6 +109,18 @@ cudaError_t launch_gather_s0(const void* x, long long xss, int nb, int x_dd, con
 template <typename T>
 cudaError_t launch_roll(const cx<T>* in, long long in_ss, const double* scale, int scale_ss, const int* shift,
                         const int* run, int N, cx<T>* out, long long out_ss, int nslots, cudaStream_t s);
+// convolution regularisation (conv.cu; Sec. 4.2, remark after eq. fourreg5a), FP64.
+// Once per device before the first launch (shared-memory opt-in of the direct sum).
+cudaError_t launch_conv_prepare();
+// out[slot][0] = sigma S Mu, out[slot][1] = sigma (-1)^{p1+p2} S / (2 pi L^2)  ([slot][2][N*N])
+cudaError_t launch_conv_split(const cx<double>* S, long long s_ss, const double* scale, int scale_ss, const int* run,
+                              const cx<double>* Mu, double inv2piL2, int N, cx<double>* out, int nslots,
+                              cudaStream_t s);
+// h = f[slot][0] + direct sum of f[slot][1] against Kt ([2N-1][2N], h^2/(2 pi) W_0 at the
+// grid differences); w_out = 0: out = h, 1: out = sw E_k Q conj(h).  N a multiple of 32.
+cudaError_t launch_conv_sum(const cx<double>* f, const cx<double>* Kt, int N, const int* run, const cx<double>* Q,
+                            long long q_ss, const cx<double>* ex, const cx<double>* ey, double sw, int w_out,
+                            cx<double>* out, long long o_ss, int nslots, cudaStream_t s);
 cudaError_t launch_cast_fields(const cx<double>* in, cx<float>* out, long long n, cudaStream_t s);
 cudaError_t launch_split_fields(const cx<double>* in, cx<dd>* out, long long n, cudaStream_t s);
 cudaError_t launch_check_finite(const double* p, long long n, int* flag, cudaStream_t s);

@@ -49,12 +49,12 @@ dbar_status dbar_internal_fail(dbar_status st, const std::string& msg) { return 
 // Kernel kinds for the event profiler (dbar_profile_*).
 enum {
   K_PASS_A, K_PASS_B, K_PASS_C, K_DOTS, K_UPDATE, K_SCALAR, K_XUPDATE,
-  K_RES_A, K_RES_B, K_RES_C, K_RHS, K_OTHER, K_PASS_CA, K_NKINDS
+  K_RES_A, K_RES_B, K_RES_C, K_RHS, K_OTHER, K_PASS_CA, K_CONV, K_NKINDS
 };
 static const char* const kKindNames[K_NKINDS] = {
     "inner_pass_a_rows", "inner_pass_b_cols", "inner_pass_c_rows", "arnoldi_dots", "arnoldi_update",
     "krylov_scalar", "solution_update", "fp64_residual_pass_a", "fp64_residual_pass_b",
-    "fp64_residual_pass_c", "rhs", "other", "inner_pass_ca_rows"};
+    "fp64_residual_pass_c", "rhs", "other", "inner_pass_ca_rows", "conv_direct_sum"};
 
 // CUDA-event timing of every launch of the solve, grouped by kind, plus the
 // algorithmic bytes of each kind (fields read and written once per use).
@@ -194,6 +194,12 @@ struct dbar_plan {
   int* h_rolls = nullptr;       // [B][2] host staging
   void* It1 = nullptr;          // [B][n] rolled field (FP64-sized)
   void* It2 = nullptr;          // [B][n] first operator application (FP64-sized)
+  // convolution regularisation (params.regularisation = DBAR_REG_CONV), FP64
+  bool conv = false;
+  cx<double>* Kt = nullptr;     // [2N-1][2N] (h^2/2pi) W_0(h(dx + i dy)) at [dy + N-1][dx + N-1]
+  cx<double>* Mu = nullptr;     // [N][N] (-1)^{p1+p2} (1 - e^{-|xi|^2})/(xi 2 pi L^2), 0 at xi = 0
+  cx<double>* Cv1 = nullptr;    // [B][2][n] smooth part and F^{-1} S (two fields per slot)
+  cx<double>* Cv2 = nullptr;    // [B][2][n] their row transforms
   long long* gat = nullptr;     // [B] per-slot element index for the S(0) / h(xi0) gather
   cx<double>* ones64 = nullptr;  // [B][N] ones (E = 1), in each arithmetic
   cx<float>* ones32 = nullptr;
@@ -474,6 +480,50 @@ static cudaError_t launch_coef_for(dbar_plan* P, const PassArgs<T>& a, int nb, c
                      P->coefp, P->ticket, P->tcoef, nb, st);
 }
 
+// Convolution regularisation (Sec. 4.2, remark after eq. fourreg5a), FP64:
+// h(S) = F^{-1}(S (1 - e^{-|xi|^2})/xi) + (1/2pi) sum over the grid of F^{-1}(S)(z') W_0(z - z') h^2.
+// Split S into the two fields, inverse-transform both (2 nb fields through the raw
+// row and column transforms), then the direct sum: out = h (w_out = 0) or
+// out = sw E_k Q conj(h) (w_out = 1, the field the operator's forward transform takes).
+static dbar_status conv_h(dbar_plan* P, const cx<double>* S, long long s_ss, const double* scale, int scale_ss,
+                          const int* run, int w_out, cx<double>* out, long long o_ss, int nb, cudaStream_t st) {
+  const long long n = P->n;
+  const double inv2piL2 = 1.0 / (2.0 * M_PI * P->p.L * P->p.L);
+  CK(timed(P, st, K_OTHER, [&] {
+    return launch_conv_split(S, s_ss, scale, scale_ss, run, P->Mu, inv2piL2, P->N, P->Cv1, nb, st);
+  }));
+  PassArgs<double> a = base_args<double>(P);
+  a.in = P->Cv1;
+  a.in_ss = n;
+  a.out = P->Cv2;
+  a.out_ss = n;
+  CK(timed(P, st, K_OTHER, [&] { return launch_pass_c<double, double, PC_INV>(a, 2 * nb, st); }));
+  a.in = P->Cv2;
+  a.out = P->Cv1;
+  CK(timed(P, st, K_OTHER, [&] { return launch_pass_b<double, PB_INV>(a, 2 * nb, st); }));
+  CK(timed(P, st, K_CONV, [&] {
+    return launch_conv_sum(P->Cv1, P->Kt, P->N, run, P->Q64, a.q_ss, P->ex64, P->ey64, P->sw, w_out, out, o_ss, nb,
+                           st);
+  }));
+  return DBAR_OK;
+}
+
+// The convolution route up to the state the fused column pass leaves in T2:
+// w = sw E_k Q conj(h(S)) in T1, then its column DFT -> T2.
+static dbar_status conv_to_T2(dbar_plan* P, const cx<double>* S, long long s_ss, const double* scale, int scale_ss,
+                              const int* run, int nb, cudaStream_t st) {
+  dbar_status s = conv_h(P, S, s_ss, scale, scale_ss, run, 1, reinterpret_cast<cx<double>*>(P->T1), P->n, nb, st);
+  if (s != DBAR_OK) return s;
+  PassArgs<double> a = base_args<double>(P);
+  a.run = run;
+  a.in = reinterpret_cast<const cx<double>*>(P->T1);
+  a.in_ss = P->n;
+  a.out = P->T2;
+  a.out_ss = P->n;
+  CK(timed(P, st, K_OTHER, [&] { return launch_pass_b<double, PB_FWD>(a, nb, st); }));
+  return DBAR_OK;
+}
+
 // One application of K (A S = S + K S) to nb fields: S (T) -> T1 -> T2 -> out (T).
 template <typename T>
 static dbar_status apply_K(dbar_plan* P, const cx<T>* S, long long s_ss, const double* scale, int scale_ss,
@@ -483,6 +533,18 @@ static dbar_status apply_K(dbar_plan* P, const cx<T>* S, long long s_ss, const d
   a.run = run;
   if (unitE) set_unit_e(P, a);
   a.neg = neg;
+  if constexpr (std::is_same<T, double>::value) {
+    if (P->conv) {  // convolution regularisation: T2 from the direct-sum route, then pass C
+      dbar_status s = conv_to_T2(P, S, s_ss, scale, scale_ss, run, nb, st);
+      if (s != DBAR_OK) return s;
+      a.in = reinterpret_cast<const cx<T>*>(P->T2);
+      a.in_ss = P->n;
+      a.out = out;
+      a.out_ss = o_ss;
+      CK(timed(P, st, K_PASS_C, [&] { return launch_pass_c<T, T, PC_KS>(a, nb, st); }));
+      return DBAR_OK;
+    }
+  }
   a.in = S;
   a.in_ss = s_ss;
   a.in_scale = scale;
@@ -526,6 +588,7 @@ static dbar_status apply_op(dbar_plan* P, const cx<T>* S, long long s_ss, const 
 // h(S) for FP64 fields (m output): pass A then pass B without the forward transform.
 static dbar_status h_of_S64(dbar_plan* P, const cx<double>* S, long long s_ss, cx<double>* out, long long o_ss,
                             int nb, cudaStream_t st) {
+  if (P->conv) return conv_h(P, S, s_ss, nullptr, 0, nullptr, 0, out, o_ss, nb, st);
   PassArgs<double> a = base_args<double>(P);
   a.in = S;
   a.in_ss = s_ss;
@@ -568,6 +631,8 @@ static dbar_status true_residual_t(dbar_plan* P, int nb, cudaStream_t st) {
   const long long n = P->n;
   // pass A, Taylor coefficients and the column pass on `in` -> T2
   auto passes_ab = [&](const cx<TC>* in, int unitE) -> dbar_status {
+    if constexpr (std::is_same<TC, double>::value)
+      if (P->conv) return conv_to_T2(P, in, n, nullptr, 0, P->cs.active, nb, st);
     PassArgs<TC> a = base_args<TC>(P);
     a.run = P->cs.active;
     if (unitE) set_unit_e(P, a);
@@ -659,6 +724,18 @@ static void account_cycle(dbar_plan* P, const int* act, const int* ns, int nb, i
     if (!act[s]) continue;
     ++nact;
     const int k = ns[s];
+    if (P->conv) {
+      // direct sum: N^4 complex multiply-adds (8 N^4 flops) per field, for the
+      // k Krylov steps and the cycle's true residual (this kind counts flops)
+      const double NN = (double)P->n;
+      by[K_CONV] += 8.0 * NN * NN * (k + 1);
+      by[K_PASS_C] += 2.0 * F * k;
+      by[K_DOTS] += F * (k * 2.0 + k * (k - 1) / 2.0);
+      by[K_UPDATE] += F * (k * 3.0 + k * (k - 1) / 2.0);
+      by[K_XUPDATE] += F * k + 2.0 * F64;
+      by[K_RES_C] += 3.0 * F64 + F;
+      continue;
+    }
     if (P->sstep > 1) {
       // per block at J = b S + 1: S applications of K, dots (J + S) F,
       // update (J + 2S) F; the last block of the cycle counts in full
@@ -685,6 +762,7 @@ static void account_cycle(dbar_plan* P, const int* act, const int* ns, int nb, i
     by[K_RES_B] += 2.0 * F64;
     by[K_RES_C] += 3.0 * F64 + F;
   }
+  if (P->conv) return;
   by[K_PASS_B] += (double)launched_steps * (P->M + 2) * F;
   if (nact) by[K_RES_B] += (P->M + 2) * F64;
 }
@@ -995,6 +1073,15 @@ static dbar_status check_params(const dbar_params* p) {
   if (p->sstep > 1 && p->restart % p->sstep != 0) return fail(DBAR_EINVAL, "restart must be a multiple of sstep");
   if (p->iterated != 0 && p->iterated != 1) return fail(DBAR_EINVAL, "iterated must be 0 or 1");
   if (p->iterated && p->sstep > 1) return fail(DBAR_EINVAL, "the iterated equation runs one Krylov vector per sweep");
+  if (p->regularisation != DBAR_REG_TAYLOR && p->regularisation != DBAR_REG_CONV)
+    return fail(DBAR_EINVAL, "regularisation must be DBAR_REG_TAYLOR or DBAR_REG_CONV");
+  if (p->regularisation == DBAR_REG_CONV) {
+    if (p->prec != DBAR_FP64) return fail(DBAR_EINVAL, "the convolution regularisation runs in FP64 only (DBAR_FP64)");
+    if (p->N > 256) return fail(DBAR_EINVAL, "the convolution regularisation needs N <= 256 (its direct sum costs N^4)");
+    if (p->iterated) return fail(DBAR_EINVAL, "the convolution regularisation is not combined with the iterated equation");
+    if (p->sstep > 1) return fail(DBAR_EINVAL, "the convolution regularisation runs one Krylov vector per sweep");
+    if (p->max_batch > 4096) return fail(DBAR_EINVAL, "the convolution regularisation takes max_batch <= 4096");
+  }
   return DBAR_OK;
 }
 
@@ -1045,6 +1132,32 @@ static dbar_status plan_tables(dbar_plan* P) {
     for (size_t i = 0; i < D.size(); ++i) Dd[i] = mkc(dd(D[i].re), dd(D[i].im));
     CK(cudaMemcpy(P->tw_dd, twd.data(), N * sizeof(cx<dd>), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(P->Da_dd, Dd.data(), Dd.size() * sizeof(cx<dd>), cudaMemcpyHostToDevice));
+  }
+
+  if (P->conv) {
+    // convolution regularisation: the direct-sum kernel table and the smooth multiplier
+    const double h = 2.0 * M_PI * L / N, w = h * h / (2.0 * M_PI);
+    std::vector<cx<double>> kt((size_t)(2 * N - 1) * 2 * N, mkc(0.0, 0.0));
+    for (int dy = -(N - 1); dy <= N - 1; ++dy)
+      for (int dx = -(N - 1); dx <= N - 1; ++dx) {
+        const zd v = W_host(0, zd(h * dx, h * dy)) * w;
+        kt[(size_t)(dy + N - 1) * 2 * N + dx + N - 1] = mkc(v.real(), v.imag());
+      }
+    std::vector<cx<double>> mu((size_t)N * N);
+    for (int p2 = 0; p2 < N; ++p2) {
+      const int m2 = p2 <= N / 2 ? p2 : p2 - N;
+      for (int p1 = 0; p1 < N; ++p1) {
+        const int m1 = p1 <= N / 2 ? p1 : p1 - N;
+        const zd xi((double)m1 / L, (double)m2 / L);
+        const double sg = ((p1 + p2) & 1) ? -1.0 : 1.0;
+        zd f(0.0, 0.0);
+        if (m1 != 0 || m2 != 0) f = -std::expm1(-std::norm(xi)) / xi * sg / (2.0 * M_PI * L * L);
+        mu[(size_t)p2 * N + p1] = mkc(f.real(), f.imag());
+      }
+    }
+    CK(cudaMemcpy(P->Kt, kt.data(), kt.size() * sizeof(cx<double>), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(P->Mu, mu.data(), mu.size() * sizeof(cx<double>), cudaMemcpyHostToDevice));
+    CK(launch_conv_prepare());
   }
 
   // Delta_n = W_n - V_n, V_n = F_d^{-1}(e^{-|xi|^2} conj(xi)^n / xi, 0 at xi = 0)
@@ -1194,12 +1307,15 @@ size_t plan_slot_bytes(const dbar_params* p, int per_slot_q) {
          ((size_t)S * (S + p->restart + 1) + (size_t)p->restart * (p->restart + 1)) * sizeof(double);
   if (per_slot_q) b += F64 + n * sizeof(cx<float>) + (p->prec == DBAR_MIXED ? F64 : 0);
   if (p->iterated) b += 2 * F64;  // shifted field and first operator application
+  if (p->regularisation == DBAR_REG_CONV) b += 4 * F64;  // two fields per slot, twice
   return b;
 }
 
 size_t plan_fixed_bytes(const dbar_params* p) {
   const size_t n = (size_t)p->N * p->N;
-  return (size_t)(3 * (p->M + 1) + 4) * n * sizeof(cx<double>);
+  size_t b = (size_t)(3 * (p->M + 1) + 4) * n * sizeof(cx<double>);
+  if (p->regularisation == DBAR_REG_CONV) b += ((size_t)(2 * p->N - 1) * 2 * p->N + n) * sizeof(cx<double>);
+  return b;
 }
 
 dbar_status plan_create_ex(const dbar_params* p, int per_slot_q, dbar_plan** out) {
@@ -1223,7 +1339,8 @@ dbar_status plan_create_ex(const dbar_params* p, int per_slot_q, dbar_plan** out
   P->MA = std::max(1, p->M);
   P->m = p->restart;
   P->iter = p->iterated != 0;
-  P->sstep = P->iter ? 1 : (p->sstep > 0 ? p->sstep : (p->restart % 4 == 0 ? 4 : (p->restart % 2 == 0 ? 2 : 1)));
+  P->conv = p->regularisation == DBAR_REG_CONV;
+  P->sstep = (P->iter || P->conv) ? 1 : (p->sstep > 0 ? p->sstep : (p->restart % 4 == 0 ? 4 : (p->restart % 2 == 0 ? 2 : 1)));
   P->mixed = (p->prec == DBAR_MIXED);
   P->resid_dd = P->mixed && p->resid_mode == DBAR_RESID_DOUBLE_FLOAT;
   P->n = (long long)P->N * P->N;
@@ -1245,6 +1362,7 @@ dbar_status plan_create_ex(const dbar_params* p, int per_slot_q, dbar_plan** out
     size_t avail = freeb > fixed ? (freeb - fixed) / 2 : 0;
     B = (int)std::min<size_t>(256, std::max<size_t>(1, avail / per_slot));
   }
+  if (P->conv) B = std::min(B, 4096);  // the raw transforms take 2 B fields per launch
   P->B = B;
   cudaError_t e = cudaSuccess;
 #define AL(ptr, cnt)                                                          \
@@ -1314,6 +1432,12 @@ dbar_status plan_create_ex(const dbar_params* p, int per_slot_q, dbar_plan** out
     AL(i2, (size_t)B * n);
     P->It1 = i1;
     P->It2 = i2;
+  }
+  if (P->conv) {
+    AL(P->Kt, (size_t)(2 * P->N - 1) * 2 * P->N);
+    AL(P->Mu, n);
+    AL(P->Cv1, (size_t)B * 2 * n);
+    AL(P->Cv2, (size_t)B * 2 * n);
   }
   AL(P->flag, 4);
   CycleState& c = P->cs;
@@ -1651,6 +1775,7 @@ extern "C" dbar_status dbar_apply(dbar_plan_t P, const void* Q, int nk, const do
   if (s != DBAR_OK) return s;
   if (nk == 0) return DBAR_OK;
   if (!Q || !S || !AS) return fail(DBAR_EINVAL, "NULL pointer");
+  if (fp32 && P->conv) return fail(DBAR_EINVAL, "the convolution regularisation has FP64 kernels only");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   s = load_Q_device(P, reinterpret_cast<const cx<double>*>(Q), st);
   if (s != DBAR_OK) return s;
@@ -1711,6 +1836,7 @@ extern "C" dbar_status dbar_taylor(dbar_plan_t P, int nk, const void* S, double*
   if (s != DBAR_OK) return s;
   if (nk == 0) return DBAR_OK;
   if (!S || !coef) return fail(DBAR_EINVAL, "NULL pointer");
+  if (P->conv) return fail(DBAR_EINVAL, "the convolution regularisation has no Taylor coefficients");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (fp32) {
     PassArgs<float> a = base_args<float>(P);

@@ -287,6 +287,8 @@ extern "C" dbar_status dbar_serve_create(const dbar_params* defaults, size_t mem
   *out = nullptr;
   if (defaults->iterated)
     return dbar_internal_fail(DBAR_EINVAL, "dbar_serve_create: the server solves the Sec. 4 equation (iterated = 0)");
+  if (defaults->regularisation != DBAR_REG_TAYLOR)
+    return dbar_internal_fail(DBAR_EINVAL, "dbar_serve_create: the server uses the Taylor-Gaussian regularisation");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
     cudaGetLastError();

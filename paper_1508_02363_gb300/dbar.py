@@ -20,6 +20,7 @@ _lib = ctypes.CDLL(_LIB_PATH)
 DBAR_OK, DBAR_EINVAL, DBAR_ENOMEM, DBAR_ENOCONV, DBAR_ETIMEOUT, DBAR_ECUDA, DBAR_EBUSY = range(7)
 DBAR_FP64, DBAR_MIXED = 0, 1
 DBAR_RESID_DOUBLE_FLOAT, DBAR_RESID_FP64 = 0, 1
+DBAR_REG_TAYLOR, DBAR_REG_CONV = 0, 1
 STATUS_NAMES = ["DBAR_OK", "DBAR_EINVAL", "DBAR_ENOMEM", "DBAR_ENOCONV", "DBAR_ETIMEOUT", "DBAR_ECUDA",
                 "DBAR_EBUSY"]
 EXPORTED = ["dbar_params_init", "dbar_last_error", "dbar_plan_create", "dbar_plan_destroy", "dbar_plan_info",
@@ -36,7 +37,8 @@ class dbar_params(ctypes.Structure):
                 ("restart", ctypes.c_int), ("max_iter", ctypes.c_int), ("tol", ctypes.c_double),
                 ("zero_fill", ctypes.c_int), ("max_batch", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("max_outer", ctypes.c_int), ("resid_mode", ctypes.c_int), ("graphs", ctypes.c_int),
-                ("autotune", ctypes.c_int), ("sstep", ctypes.c_int), ("iterated", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("sstep", ctypes.c_int), ("iterated", ctypes.c_int),
+                ("regularisation", ctypes.c_int)]
 
 
 class dbar_request(ctypes.Structure):
@@ -136,6 +138,8 @@ def dbar_params_init(N: int, L: float, **overrides) -> dbar_params:
             v = {"fp64": DBAR_FP64, "mixed": DBAR_MIXED}[v]
         if key == "resid_mode" and isinstance(v, str):
             v = {"double_float": DBAR_RESID_DOUBLE_FLOAT, "fp64": DBAR_RESID_FP64}[v]
+        if key == "regularisation" and isinstance(v, str):
+            v = {"taylor": DBAR_REG_TAYLOR, "conv": DBAR_REG_CONV}[v]
         setattr(p, key, v)
     return p
 
