@@ -126,18 +126,26 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# sources that do not build or launch the solve's kernels (the convolution route, the
+# allocation-free DFT entry point, the serving runtime): editing them keeps the captured
+# DRAM counters of the solve's kernels valid
+DIGEST_EXCLUDE = ("conv.cu", "noalloc.cu", "serve.cu")
+
+
 def source_digest():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1508_02363_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
-        h.update(open(os.path.join(csrc, f), "rb").read())
+        if f not in DIGEST_EXCLUDE:
+            h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kind, algorithmic_bytes_per_launch):
+def ncu_traffic(kind, algorithmic_bytes_per_launch, variant=None):
     """DRAM bytes per launch of `kind`: the DRAM/algorithmic ratio measured by ncu on a
-    smaller capture of the same kernel (profiles/ncu_traffic.json) times this launch's
-    algorithmic bytes, if the capture was taken on the current kernel sources; else None."""
+    smaller capture of the same kernel (profiles/ncu_traffic.json; per tile variant where
+    the kind has several) times this launch's algorithmic bytes, if the capture was taken
+    on the current kernel sources; else None."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(path):
         return None
@@ -145,7 +153,10 @@ def ncu_traffic(kind, algorithmic_bytes_per_launch):
         d = json.load(open(path))
         if d.get("source_digest") != source_digest():
             return None
-        ratio = d.get("kinds", {}).get(kind, {}).get("dram_over_algorithmic")
+        entry = d.get("kinds", {}).get(kind, {})
+        ratio = entry.get("dram_over_algorithmic")
+        if variant is not None and "variants" in entry:
+            ratio = entry["variants"].get(str(variant))
         return None if ratio is None else round(ratio * algorithmic_bytes_per_launch)
     except Exception:
         return None
@@ -207,7 +218,9 @@ def run_ours(args):
     w.k = rank_units(w.k, rank, world)
     nk = w.k.size
     plan = dbar.Plan(N, w.L, M=w.M, prec="mixed" if w.mixed else "fp64", tol=w.tol, restart=args.restart,
-                     inner_tol=args.inner_tol, max_batch=nk, max_outer=args.max_outer, sstep=args.sstep)
+                     inner_tol=args.inner_tol, max_batch=nk, max_outer=args.max_outer, sstep=args.sstep,
+                     autotune=args.autotune)
+    colv, tune0, tune1 = dbar.dbar_plan_tuning(plan.handle)
     stream = torch.cuda.current_stream()
     Qd = torch.from_numpy(w.Q).cuda()
     Sd = torch.empty((nk, N, N), dtype=torch.complex128, device="cuda")
@@ -297,7 +310,7 @@ def run_ours(args):
     dom = max(prof.items(), key=lambda kv: kv[1][0])
     dom_name, (dom_ms, dom_launches, dom_bytes) = dom
     achieved = dom_bytes / (dom_ms / 1e3) / 1e9 if dom_ms > 0 else 0.0
-    traffic = ncu_traffic(dom_name, dom_bytes / max(dom_launches, 1))
+    traffic = ncu_traffic(dom_name, dom_bytes / max(dom_launches, 1), variant=colv)
     all_bytes = sum(v[2] for v in prof.values())
     all_ms = sum(v[0] for v in prof.values())
     roofline = {"bound": "hbm", "kernel": dom_name, "achieved": round(achieved, 1), "peak": peak,
@@ -320,6 +333,7 @@ def run_ours(args):
            "config": {"workload": w.name, "N": N, "L": w.L, "nk": nk, "M": w.M, "tol": w.tol,
                       "prec": "mixed" if w.mixed else "fp64", "restart": args.restart, "sstep": args.sstep,
                       "inner_tol": args.inner_tol,
+                      "column_variant": colv, "column_tune_ms": [round(tune0, 4), round(tune1, 4)],
                       "parallelism": f"replicas over k x{world}",
                       "l2": "inputs larger than L2 (device working set %.1f GB)" % (plan.device_bytes / 1e9)},
            "p50_ms": round(statistics.median(step_ms), 3),
@@ -699,7 +713,8 @@ def run_serving(args):
            "err_vs_fp64_max": float(max(errs)), "err_sample": len(errs),
            "n_mix": {str(N): int(sum(1 for _, n, _, _ in tickets if n == N)) for N in sizes},
            "config": {"L": L, "kmax": KMAX, "xi_q": XI_Q, "pool_per_N": POOL, "restart": args.restart,
-                      "inner_tol": args.inner_tol, "serve_batch": args.serve_batch, "seed": args.seed},
+                      "inner_tol": args.inner_tol,
+                      "column_variant": colv, "column_tune_ms": [round(tune0, 4), round(tune1, 4)], "serve_batch": args.serve_batch, "seed": args.seed},
            "clocks": clk.summary()}
     print(json.dumps(out))
 
@@ -764,7 +779,8 @@ def main():
     ap.add_argument("--serve-batch", dest="serve_batch", type=int, default=128, help="serving: slots per lane")
     ap.add_argument("--seed", type=int, default=5)
     ap.add_argument("--nreq", type=int, default=1000, help="uneven: number of solves")
-    ap.add_argument("--autotune", type=int, default=1, help="uneven: autotuned column-pass tiles")
+    ap.add_argument("--autotune", type=int, default=1,
+                    help="column-pass tiles: 1 timed at plan creation (default), 0 or 2 pin variant 0 or 1")
     ap.add_argument("--quick", action="store_true",
                     help="time the solve only (no FP64 comparison, end-to-end leg or CPU baseline)")
     args = ap.parse_args()
