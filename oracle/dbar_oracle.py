@@ -245,6 +245,42 @@ def h_of_S(S, g: Grid, M: int, fill: str = "analytic", Wn=None):
     return h
 
 
+def h_of_S_at(S, g: Grid, m0, M: int, fill: str = "analytic", Wn=None):
+    """F^{-1}(S/(xi - xi0)) with the shifted regularisation eq. dbarinvShift, xi0 = (m0[0] + i m0[1])/L
+    a grid point:
+      * S's quotient by xi - xi0 is formed at the grid points as they are (no periodic wrap of
+        xi - xi0: S lives near the origin, xi0 may lie near the edge of the box);
+      * G = e^{-|xi - xi0|^2} sum_n c_n conj(xi - xi0)^n with n! c_n = d^n_{conj xi} S(xi0)
+        = (-i/2)^n F(z^n e^{-i xi0.x} F^{-1} S)(0) is Sec. 4's G moved to xi0 on the grid's torus:
+        its difference xi - xi0 is taken periodically (reading: the paper is silent on a G that
+        reaches the edge of the box; there its coefficients are those of S far from its support);
+      * the analytic limit d = d_xi S(xi0) at xi0, and F^{-1}(G/(xi - xi0)) = e^{i xi0.x} sum_n c_n W_n.
+    m0 = (0, 0) is h_of_S."""
+    N = g.N
+    xi0 = (m0[0] + 1j * m0[1]) / g.L
+    s = g.Finv(S)
+    ph = np.exp(-1j * (xi0.real * g.X + xi0.imag * g.Y))          # e^{-i xi0.x}
+    c = [(-0.5j) ** n / math.factorial(n) * g.F_at0(g.z ** n * s * ph) for n in range(M + 1)]
+    d = -0.5j * g.F_at0(np.conj(g.z) * s * ph)
+    if Wn is None:
+        Wn = [W(n, g.z) for n in range(M + 1)]
+    at = (m0[1] % N, m0[0] % N)                                   # the grid point xi0
+    dxi = g.xi - xi0                                              # plain difference
+    dxi_t = np.roll(g.xi, shift=at, axis=(0, 1))                  # periodic difference on the torus
+    gauss = np.exp(-(dxi_t * np.conj(dxi_t)).real)
+    den, den_t = dxi.copy(), dxi_t.copy()
+    den[at] = den_t[at] = 1.0                                     # placeholders, xi0 overwritten below
+    U = S / den
+    for n in range(M + 1):
+        U = U - np.asarray(c[n])[..., None, None] * gauss * np.conj(dxi_t) ** n / den_t
+    U[(Ellipsis,) + at] = d if fill == "analytic" else 0.0
+    h = g.Finv(U)
+    mod = np.conj(ph)                                             # e^{i xi0.x}
+    for n in range(M + 1):
+        h = h + np.asarray(c[n])[..., None, None] * mod * Wn[n]
+    return h
+
+
 def dbar_inverse(f, g: Grid, M: int, fill: str = "analytic"):
     """dbar^{-1} f = F^{-1}(-2i/xi F f) (Sec. 3 lemma), through the same regularisation."""
     return h_of_S(-2j * g.F(f), g, M, fill)
@@ -495,28 +531,26 @@ class IteratedProblem:
     """h - K_0(H(h)) = -i F(q) (eq. eqh2) with
         H(h) = -i F(q conj(F^{-1}(h / (xi - xi0)))),  xi0 = 2i conj(k)   (Sec. 5.3 step 1)
         K_0(S) = -i F(q conj(F^{-1}(S / xi)))                            (eq. shift)
-    F^{-1}(h/(xi - xi0)) by the shifting argument eq. dbarinvShift: with
-    h~(eta) = h(eta + xi0) (a circular shift on the grid, exact for the periodic
-    discretisation), F^{-1}[g(. - xi0)] = e^{i xi0.x} F^{-1}[g], so
-        F^{-1}(h/(xi - xi0)) = e^{i xi0.x} F^{-1}(h~/eta),
-    the last term regularised exactly as in Sec. 4 (h_of_S)."""
+    F^{-1}(h/(xi - xi0)) by the shifted regularisation eq. dbarinvShift (h_of_S_at):
+    h is supported near the origin, the quotient by xi - xi0 is formed at the grid
+    points, and the singular point xi0 (which may lie near the edge of the box) is
+    regularised by a Gaussian G centred there."""
 
     def __init__(self, q, k, N, L, M=2, fill="analytic"):
         self.g = Grid(N, L)
         self.q = np.asarray(q, dtype=np.complex128)
         self.k = complex(k)
         self.M, self.fill = M, fill
-        self.m0 = shift_index(self.k, L)
-        xi0 = self.m0[0] / L + 1j * self.m0[1] / L
-        self.mod = np.exp(1j * (xi0.real * self.g.X + xi0.imag * self.g.Y))   # e^{i xi0.x}
+        # xi0 on the grid's wavenumbers (-N/2, N/2]; -N/2 is the Nyquist point, which the
+        # grid holds on the positive side (eq. xidomain)
+        m0 = shift_index(self.k, L)
+        if not all(-N // 2 <= m <= N // 2 for m in m0):
+            raise ValueError("2k L must lie within the grid's wavenumbers [-N/2, N/2]")
+        self.m0 = tuple(N // 2 if m == -N // 2 else m for m in m0)
         self.Wn = [W(n, self.g.z) for n in range(M + 1)]
 
-    def shifted(self, h):
-        """h~[m] = h[m + m0] on the periodic grid ([m2][m1] layout)."""
-        return np.roll(h, shift=(-self.m0[1], -self.m0[0]), axis=(-2, -1))
-
     def H(self, h):
-        u = self.mod * h_of_S(self.shifted(h), self.g, self.M, self.fill, self.Wn)
+        u = h_of_S_at(h, self.g, self.m0, self.M, self.fill, self.Wn)
         return -1j * self.g.F(self.q * np.conj(u))
 
     def K0(self, S):

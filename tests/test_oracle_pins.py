@@ -327,13 +327,14 @@ def _mixture(N, L):
 def test_iterated_equation_reflection_matches_the_direct_route(m):
     # Sec. 6.1: r = i h(i conj k) from the single iterated solve (eq. eqh2, shifted regularisation
     # eq. dbarinvShift) equals (i/2)(S_+(0) - S_-(0)) from the two solves of the Sec. 4 method,
-    # wherever the latter resolves the problem (small k): two different discrete operators
-    N, L = 64, 3.0
+    # wherever the latter resolves the problem (small k): two different discrete operators.  The
+    # grid resolves h to the box edge (Q's widest transform ~e^{-0.175|xi|^2} at xi_max = 21)
+    N, L = 128, 3.0
     Q = _mixture(N, L)
     k = (m[0] + 1j * m[1]) / L
     a = orc.reflection(Q, k, N, L)["r"]
     b = orc.reflection_iterated(Q, k, N, L)["r"]
-    assert abs(a - b) < 1e-12 * abs(a)
+    assert abs(a - b) < 1e-13 * abs(a)
 
 
 @pytest.mark.parametrize("m", [(10, 6), (-8, -12), (14, 0)])
@@ -352,6 +353,79 @@ def test_iterated_equation_born_limit_at_large_k(m):
     assert abs(dev[1] / dev[0] - 4.0) < 0.3, dev
 
 
+def _shifted_gaussian_quotient(g, xi0):
+    # F^{-1}(h/(xi - xi0)) for h = F e^{-|z|^2} = (1/2) e^{-|xi|^2/4}: with the shift theorem and
+    # F^{-1}(F(f)/xi) = (i/2) dbar^{-1} f,  = e^{i xi0.x} (i/2) dbar^{-1}(e^{-i xi0.x} e^{-|z|^2}),
+    # and e^{-i xi0.x} e^{-|z|^2} = e^{-|xi0|^2/4} e^{-(z-b)(conj z-c)}, b = -i xi0/2, c = -i conj(xi0)/2
+    b, c = -0.5j * xi0, -0.5j * np.conj(xi0)
+    w = g.z - b
+    with np.errstate(all="ignore"):
+        inv = (1 / w) * (1 - np.exp(-w * (np.conj(g.z) - c)))
+    at = abs(w) < 1e-13
+    inv[at] = (np.conj(g.z) - c)[at]
+    return np.exp(1j * (xi0.real * g.X + xi0.imag * g.Y)) * 0.5j * np.exp(-abs(xi0) ** 2 / 4) * inv
+
+
+@pytest.mark.parametrize("m0", [(0, 0), (10, 0), (30, -20), (64, 0), (50, 50), (-63, 40), (64, 64)])
+def test_shifted_quotient_is_the_closed_form_up_to_the_box_edge(m0):
+    # eq. dbarinvShift: h centred at the origin divided by xi - xi0, xi0 anywhere on the grid up to
+    # its edge (xi_max = N/(2L) = 16 here), against the closed form above
+    g = orc.Grid(128, 4.0)
+    h = g.F(np.exp(-(g.z * np.conj(g.z)).real))
+    xi0 = (m0[0] + 1j * m0[1]) / g.L
+    exact = _shifted_gaussian_quotient(g, xi0)
+    assert abs(orc.h_of_S_at(h, g, m0, 11) - exact).max() < 5e-14
+
+
+def test_shifted_quotient_is_not_a_circular_shift_of_the_unshifted_one():
+    # reading of eq. dbarinvShift: the quotient is formed at the grid points as they are.  Rolling h
+    # by xi0 and dividing by xi instead wraps xi - xi0 periodically; near the edge of the box that
+    # is a different (and wrong) operator, while it agrees where h's shifted support stays inside
+    g = orc.Grid(128, 4.0)
+    h = g.F(np.exp(-(g.z * np.conj(g.z)).real))
+    for m0, agree in (((10, 0), True), ((64, 0), False)):
+        xi0 = (m0[0] + 1j * m0[1]) / g.L
+        rolled = np.exp(1j * (xi0.real * g.X + xi0.imag * g.Y)) * orc.h_of_S(
+            np.roll(h, shift=(-m0[1], -m0[0]), axis=(0, 1)), g, 11)
+        err = abs(rolled - _shifted_gaussian_quotient(g, xi0)).max()
+        assert (err < 1e-13) == agree, (m0, err)
+    # at xi0 = 0 the shifted route is the unshifted one
+    S = g.F(np.exp(-((g.X - 0.4) ** 2 + (g.Y + 0.2) ** 2)) * (1 + 0.3j))
+    assert abs(orc.h_of_S_at(S, g, (0, 0), 11) - orc.h_of_S(S, g, 11)).max() < 1e-15
+
+
+def test_shift_table_of_sec5_unshifted_slow_shifted_spectral():
+    # Sec. 5.1, the figure and table of the shifting argument: dbar^{-1} of a test function (eq.
+    # dbartest, a = 1/2) whose transform sits at -2i conj(k) for the table's (N, L, k).  Reading:
+    # f = E_k e^{-a|z|^2}, i.e. eq. dbartest with b = conj(k)/a, c = -k/a scaled by e^{-|k|^2/a}, so
+    # dbar^{-1} f = (e^{-|k|^2/a} - f)/(a (z - b)).  Without the shift the error falls only like 1/N
+    # (the k of the table grow with N); with it (phi = F(e^{i xi0.x} f), eq. dbarinvShift) it falls
+    # spectrally to machine precision.
+    t = json.load(open(os.path.join(GOLDEN, "shift_table.json")))
+    a = 0.5
+    for col in (2, 3):
+        unshifted, shifted = [], []
+        for row in t["rows"]:
+            N, L, k = row[0], row[1], complex(*row[col])
+            g = orc.Grid(N, L)
+            f = g.E(k) * np.exp(-a * (g.z * np.conj(g.z)).real)
+            b = np.conj(k) / a
+            with np.errstate(all="ignore"):
+                exact = (np.exp(-abs(k) ** 2 / a) - f) / (a * (g.z - b))
+            at = abs(g.z - b) < 1e-12
+            exact[at] = np.exp(-abs(k) ** 2 / a) * (np.conj(b) + k / a)
+            unshifted.append(abs(orc.dbar_inverse(f, g, 11) - exact).max())
+            m0 = orc.shift_index(k, L)
+            xi0 = (m0[0] + 1j * m0[1]) / L
+            mod = np.exp(1j * (xi0.real * g.X + xi0.imag * g.Y))
+            sh = -2j * np.conj(mod) * orc.h_of_S_at(g.F(mod * f), g, m0, 11)
+            shifted.append(abs(sh - exact).max())
+        assert all(u > 0.04 for u in unshifted), unshifted
+        assert all(1.7 < u1 / u2 < 2.3 for u1, u2 in zip(unshifted[2:], unshifted[3:])), unshifted
+        assert all(s2 < s1 for s1, s2 in zip(shifted[:4], shifted[1:4])), shifted
+        assert max(shifted[3:]) < 1e-13, shifted
+
+
 def test_iterated_shift_requires_2k_on_the_grid():
     with pytest.raises(ValueError):
         orc.shift_index(0.1 + 0.0j, 3.0)
@@ -363,7 +437,9 @@ def test_iterated_shift_requires_2k_on_the_grid():
 @pytest.mark.parametrize("row", [0, 1])
 def test_ds2_round_trip_reproduces_the_papers_reconstruction_errors(row):
     # q -> r (one iterated solve per k) -> q (one per z) for q = exp(-x^2-y^2), M = 11, at the
-    # paper's (N, L) pairs; the error must not exceed the printed one and stays within a factor 10
+    # paper's (N, L) pairs: at these coarse grids the error is the method's discretisation error,
+    # so it must reproduce the printed value itself (within 10 %; 7.47e-3 vs 7.09e-3 and
+    # 3.193e-4 vs 3.187e-4 with the shifted regularisation read as in eq. dbarinvShift)
     t = json.load(open(os.path.join(GOLDEN, "ds2_reconstruction.json")))
     N, L, err_paper = t["rows"][row]
     M = t["M"]
@@ -373,7 +449,7 @@ def test_ds2_round_trip_reproduces_the_papers_reconstruction_errors(row):
     qr = np.array([[orc.ds2_potential(R, X[a, b] + 1j * Y[a, b], N, L, M=M, tol=1e-14) for b in range(N)]
                    for a in range(N)])
     err = np.max(np.abs(qr - q))
-    assert err_paper / 10 <= err <= err_paper, (N, L, err, err_paper)
+    assert abs(err / err_paper - 1.0) < 0.1, (N, L, err, err_paper)
 
 
 # --------------------------------------------------------------------------- convolution regularisation
