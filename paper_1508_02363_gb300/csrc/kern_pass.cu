@@ -27,9 +27,15 @@ template <typename T, int LOGN>
 cudaError_t launch_pass_a_n(const PassArgs<T>& a, int nslots, cudaStream_t s) {
   using G = RowG<T, LOGN>;
   const size_t sm = (size_t)G::LINES * G::P * sizeof(cx<T>);
-  cudaError_t e = set_smem(k_pass_a<T, LOGN>, sm);
-  if (e != cudaSuccess) return e;
-  k_pass_a<T, LOGN><<<dim3(G::N / G::LINES, nslots), G::THREADS, sm, s>>>(a);
+  if (a.dshift) {  // shifted quotient of the iterated equation
+    cudaError_t e = set_smem(k_pass_a<T, LOGN, true>, sm);
+    if (e != cudaSuccess) return e;
+    k_pass_a<T, LOGN, true><<<dim3(G::N / G::LINES, nslots), G::THREADS, sm, s>>>(a);
+  } else {
+    cudaError_t e = set_smem(k_pass_a<T, LOGN, false>, sm);
+    if (e != cudaSuccess) return e;
+    k_pass_a<T, LOGN, false><<<dim3(G::N / G::LINES, nslots), G::THREADS, sm, s>>>(a);
+  }
   return cudaGetLastError();
 }
 

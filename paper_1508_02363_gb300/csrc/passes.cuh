@@ -93,7 +93,7 @@ struct ColG {
 // dst (this thread's first element of the row).  Used by k_pass_a and by the
 // fused row pass k_pass_ca.
 // ---------------------------------------------------------------------------
-template <typename T, int LOGN>
+template <typename T, int LOGN, bool SH = false>
 __device__ __forceinline__ void row_a(const PassArgs<T>& a, cx<T> (&v)[16], int slot, int p2, int t, cx<T>* sl,
                                       cx<T>* dst) {
   using G = RowG<T, LOGN>;
@@ -135,25 +135,55 @@ __device__ __forceinline__ void row_a(const PassArgs<T>& a, cx<T> (&v)[16], int 
   T c2piL;
   if constexpr (std::is_same<T, float>::value) c2piL = a.inv2piL_f;
   else c2piL = (T)a.inv2piL;
-  const T m2f = (T)wavenum(p2, N);
   const T tf = (T)t;
-  const T m2sq = m2f * m2f;
+  // Shifted quotient (iterated equation): the field was rolled by s, so element p holds the
+  // value at p + s and its divisor is the unwrapped wavenumber m(p + s) - s, i.e. the
+  // representative of p in [-N/2 + 1 - s, N/2 - s] (eq. dbarinvShift: no periodic wrap of
+  // xi - xi0).  Exact in T: |m| <= N.
+  auto scale_row = [&](int s1, int s2) {
+    int m2 = wavenum(p2, N);
+    if (m2 > (N >> 1) - s2) m2 -= N;
+    else if (m2 < -(N >> 1) + 1 - s2) m2 += N;
+    const T m2f = (T)m2;
+    const T m2sq = m2f * m2f;
+    const int hi1 = (N >> 1) - s1, lo1 = -(N >> 1) + 1 - s1;
 #pragma unroll
-  for (int q = 0; q < 16; ++q) {
-    const int p1 = t + q * TPL;
-    T m1f = tf + (T)(q * TPL);
-    if (p1 > (N >> 1)) m1f = m1f - (T)N;
-    const T den = m1f * m1f + m2sq;
-    T f = (p1 == 0 && p2 == 0) ? (T)0 : kappa_scale<T>(c2piL, den);
-    if ((p1 + p2) & 1) f = -f;
-    v[q] = cmul(v[q], mkc(m1f * f, -(m2f * f)));
+    for (int q = 0; q < 16; ++q) {
+      const int p1 = t + q * TPL;
+      const int m1 = wavenum(p1, N);
+      T m1f = tf + (T)(q * TPL);
+      if (p1 > (N >> 1)) m1f = m1f - (T)N;
+      if (m1 > hi1) m1f = m1f - (T)N;
+      else if (m1 < lo1) m1f = m1f + (T)N;
+      const T den = m1f * m1f + m2sq;
+      T f = (p1 == 0 && p2 == 0) ? (T)0 : kappa_scale<T>(c2piL, den);
+      if ((p1 + p2) & 1) f = -f;
+      v[q] = cmul(v[q], mkc(m1f * f, -(m2f * f)));
+    }
+  };
+  if constexpr (SH) {
+    scale_row(a.dshift[2 * slot], a.dshift[2 * slot + 1]);
+  } else {
+    const T m2f = (T)wavenum(p2, N);
+    const T m2sq = m2f * m2f;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int p1 = t + q * TPL;
+      T m1f = tf + (T)(q * TPL);
+      if (p1 > (N >> 1)) m1f = m1f - (T)N;
+      const T den = m1f * m1f + m2sq;
+      T f = (p1 == 0 && p2 == 0) ? (T)0 : kappa_scale<T>(c2piL, den);
+      if ((p1 + p2) & 1) f = -f;
+      v[q] = cmul(v[q], mkc(m1f * f, -(m2f * f)));
+    }
   }
   fft_line<T, LOGN, true, std::is_same<T, float>::value>(v, sl, t, a.tw);
 #pragma unroll
   for (int q = 0; q < 16; ++q) dst[q * TPL] = v[q];
 }
 
-template <typename T, int LOGN>
+// SH: the shifted quotient of the iterated equation (a.dshift set)
+template <typename T, int LOGN, bool SH>
 __global__ void __launch_bounds__(RowG<T, LOGN>::THREADS, RowG<T, LOGN>::MINB) k_pass_a(const PassArgs<T> a) {
   using G = RowG<T, LOGN>;
   constexpr int N = G::N, TPL = G::TPL, LINES = G::LINES, P = G::P;
@@ -168,7 +198,8 @@ __global__ void __launch_bounds__(RowG<T, LOGN>::THREADS, RowG<T, LOGN>::MINB) k
   const cx<T>* src = a.in + (size_t)slot * a.in_ss + (size_t)p2 * N + t;
 #pragma unroll
   for (int q = 0; q < 16; ++q) v[q] = cscale(ldg(src + q * TPL), sc);
-  row_a<T, LOGN>(a, v, slot, p2, t, sl, reinterpret_cast<cx<T>*>(a.out) + (size_t)slot * a.out_ss + (size_t)p2 * N + t);
+  row_a<T, LOGN, SH>(a, v, slot, p2, t, sl,
+                     reinterpret_cast<cx<T>*>(a.out) + (size_t)slot * a.out_ss + (size_t)p2 * N + t);
 }
 
 // ---------------------------------------------------------------------------

@@ -190,8 +190,10 @@ struct dbar_plan {
   cx<double>* s0buf = nullptr;  // [B] solutions at xi = 0 (reflection coefficient)
   // iterated equation of Sec. 5 (params.iterated)
   bool iter = false;
-  int* rolls = nullptr;         // [B][2] grid offset of xi0 = 2i conj(k) per slot (device)
+  int* rolls = nullptr;         // [B][2] grid offset of xi0 = 2i conj(k) per slot, mod N (device)
   int* h_rolls = nullptr;       // [B][2] host staging
+  int* dshift = nullptr;        // [B][2] the same offsets signed, in (-N/2, N/2] (pass A's divisor)
+  int* h_dshift = nullptr;      // [B][2] host staging
   void* It1 = nullptr;          // [B][n] rolled field (FP64-sized)
   void* It2 = nullptr;          // [B][n] first operator application (FP64-sized)
   // convolution regularisation (params.regularisation = DBAR_REG_CONV), FP64
@@ -240,6 +242,7 @@ struct dbar_plan {
     if (h_active) cudaFreeHost(h_active);
     if (h_nsteps) cudaFreeHost(h_nsteps);
     if (h_rolls) cudaFreeHost(h_rolls);
+    if (h_dshift) cudaFreeHost(h_dshift);
     if (hmask) cudaFreeHost(hmask);
     if (h_ek) cudaFreeHost(h_ek);
     cudaSetDevice(cur);
@@ -361,10 +364,16 @@ static dbar_status upload_ek(dbar_plan* P, const double* k, int nb, cudaStream_t
       const double r1 = std::nearbyint(m1), r2 = std::nearbyint(m2);
       if (std::fabs(m1 - r1) > 1e-9 || std::fabs(m2 - r2) > 1e-9)
         return fail(DBAR_EINVAL, "iterated plan: 2k must lie on the xi-grid (2 k L integer in both components)");
+      if (std::fabs(r1) > N / 2 || std::fabs(r2) > N / 2)
+        return fail(DBAR_EINVAL, "iterated plan: 2 k L must lie within the grid's wavenumbers [-N/2, N/2]");
       P->h_rolls[2 * s] = (int)(((long long)r1 % N + N) % N);
       P->h_rolls[2 * s + 1] = (int)(((long long)r2 % N + N) % N);
+      // signed offsets in (-N/2, N/2]: -N/2 is the Nyquist point, held on the positive side
+      P->h_dshift[2 * s] = P->h_rolls[2 * s] > N / 2 ? P->h_rolls[2 * s] - N : P->h_rolls[2 * s];
+      P->h_dshift[2 * s + 1] = P->h_rolls[2 * s + 1] > N / 2 ? P->h_rolls[2 * s + 1] - N : P->h_rolls[2 * s + 1];
     }
     CK(cudaMemcpyAsync(P->rolls, P->h_rolls, 2 * nb * sizeof(int), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(P->dshift, P->h_dshift, 2 * nb * sizeof(int), cudaMemcpyHostToDevice, st));
   }
   fill_ek(P, k, nb, P->h_ek);
   for (int s = 0; s < nb; ++s) {
@@ -528,9 +537,10 @@ static dbar_status conv_to_T2(dbar_plan* P, const cx<double>* S, long long s_ss,
 template <typename T>
 static dbar_status apply_K(dbar_plan* P, const cx<T>* S, long long s_ss, const double* scale, int scale_ss,
                            cx<T>* out, long long o_ss, const int* run, int nb, cudaStream_t st, int unitE = 0,
-                           int neg = 0) {
+                           int neg = 0, const int* dshift = nullptr) {
   PassArgs<T> a = base_args<T>(P);
   a.run = run;
+  a.dshift = dshift;
   if (unitE) set_unit_e(P, a);
   a.neg = neg;
   if constexpr (std::is_same<T, double>::value) {
@@ -569,7 +579,9 @@ static dbar_status apply_K(dbar_plan* P, const cx<T>* S, long long s_ss, const d
 // E_k.  Iterated equation of Sec. 5 (eq. eqh2): A h = h - K_0(H(h)) with
 // H(h) = -i F(q conj(F^{-1}(h/(xi - xi0)))) and K_0(S) = -i F(q conj(F^{-1}(S/xi))).
 // By the shifted regularisation (eq. dbarinvShift), F^{-1}(h/(xi - xi0)) =
-// e^{i xi0.x} F^{-1}(h~/eta) with h~ = h(. + xi0) and e^{-i xi0.x} = E_k, so
+// e^{i xi0.x} F^{-1}(h~/(xi - xi0)~) with h~ = h(. + xi0) (a circular shift, which
+// moves the Taylor data at xi0 to the origin) and the divisor taken at the unshifted
+// points (no periodic wrap of xi - xi0: pass A's dshift); e^{-i xi0.x} = E_k, so
 // H(h) = -K_{E_k}(h~), K_0(S) = -K_1(S) and K_it(h) = -K_1(K_{E_k}(h~)):
 // a circular shift, one application with E_k, one with E = 1 and the sign.
 template <typename T>
@@ -580,7 +592,7 @@ static dbar_status apply_op(dbar_plan* P, const cx<T>* S, long long s_ss, const 
   cx<T>* R = reinterpret_cast<cx<T>*>(P->It1);
   cx<T>* H = reinterpret_cast<cx<T>*>(P->It2);
   CK(timed(P, st, K_OTHER, [&] { return launch_roll<T>(S, s_ss, scale, scale_ss, P->rolls, run, P->N, R, n, nb, st); }));
-  dbar_status s = apply_K<T>(P, R, n, nullptr, 0, H, n, run, nb, st);
+  dbar_status s = apply_K<T>(P, R, n, nullptr, 0, H, n, run, nb, st, 0, 0, P->dshift);
   if (s != DBAR_OK) return s;
   return apply_K<T>(P, H, n, nullptr, 0, out, o_ss, run, nb, st, 1, 1);
 }
@@ -630,11 +642,12 @@ template <typename TC, typename TI>
 static dbar_status true_residual_t(dbar_plan* P, int nb, cudaStream_t st) {
   const long long n = P->n;
   // pass A, Taylor coefficients and the column pass on `in` -> T2
-  auto passes_ab = [&](const cx<TC>* in, int unitE) -> dbar_status {
+  auto passes_ab = [&](const cx<TC>* in, int unitE, const int* dshift) -> dbar_status {
     if constexpr (std::is_same<TC, double>::value)
       if (P->conv) return conv_to_T2(P, in, n, nullptr, 0, P->cs.active, nb, st);
     PassArgs<TC> a = base_args<TC>(P);
     a.run = P->cs.active;
+    a.dshift = dshift;
     if (unitE) set_unit_e(P, a);
     a.in = in;
     a.in_ss = n;
@@ -668,15 +681,15 @@ static dbar_status true_residual_t(dbar_plan* P, int nb, cudaStream_t st) {
     CK(timed(P, st, K_OTHER, [&] {
       return launch_roll<TC>(x, n, nullptr, 0, P->rolls, P->cs.active, P->N, R, n, nb, st);
     }));
-    if ((s = passes_ab(R, 0)) != DBAR_OK) return s;
+    if ((s = passes_ab(R, 0, P->dshift)) != DBAR_OK) return s;
     c.in = reinterpret_cast<const cx<TC>*>(P->T2);
     c.out = H;
     c.out_ss = n;
     CK(timed(P, st, K_RES_C, [&] { return launch_pass_c<TC, TC, PC_KS>(c, nb, st); }));
-    if ((s = passes_ab(H, 1)) != DBAR_OK) return s;
+    if ((s = passes_ab(H, 1, nullptr)) != DBAR_OK) return s;
     c.neg = 1;
   } else {
-    if ((s = passes_ab(x, 0)) != DBAR_OK) return s;
+    if ((s = passes_ab(x, 0, nullptr)) != DBAR_OK) return s;
   }
   c.in = reinterpret_cast<const cx<TC>*>(P->T2);
   c.out = nullptr;
@@ -1426,6 +1439,7 @@ dbar_status plan_create_ex(const dbar_params* p, int per_slot_q, dbar_plan** out
   AL(P->gat, B);
   if (P->iter) {
     AL(P->rolls, 2 * (size_t)B);
+    AL(P->dshift, 2 * (size_t)B);
     cx<double>* i1 = nullptr;
     cx<double>* i2 = nullptr;
     AL(i1, (size_t)B * n);
@@ -1481,6 +1495,7 @@ dbar_status plan_create_ex(const dbar_params* p, int per_slot_q, dbar_plan** out
       cudaMallocHost(&P->hmask, (size_t)B * sizeof(int)) != cudaSuccess ||
       cudaMallocHost(&P->h_nsteps, (size_t)B * sizeof(int)) != cudaSuccess ||
       cudaMallocHost(&P->h_rolls, 2 * (size_t)B * sizeof(int)) != cudaSuccess ||
+      cudaMallocHost(&P->h_dshift, 2 * (size_t)B * sizeof(int)) != cudaSuccess ||
       cudaMallocHost(&P->h_ek, (size_t)B * 2 * P->N * sizeof(cx<double>)) != cudaSuccess) {
     delete P;
     return fail(DBAR_ENOMEM, "pinned host allocation failed");

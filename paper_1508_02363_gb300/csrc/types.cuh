@@ -49,6 +49,10 @@ struct PassArgs {
   double* part;          // [slot][gridDim.x] squared-norm partials (pass C)
   const float* nscale;   // [slot] power-of-two ~1/||b|| (double-float residual norms)
   int neg;               // row pass C: the transform's output negated (K of the iterated equation)
+  // pass A of the iterated equation's shifted quotient (eq. dbarinvShift): per slot the signed
+  // grid offset (s1, s2) of xi0 by which the input was rolled, so that the divisor of rolled
+  // element p is the unwrapped xi_{p + s} - xi0 (nullable: the plain divisor xi_p)
+  const int* dshift;
 };
 
 

@@ -22,12 +22,13 @@ def dbar():
     return d
 
 
-def _round_trip(dbar, N, L, M, prec, t=0.0):
+def _round_trip(dbar, N, L, M, prec, t=0.0, tol=None):
     X, Y = wl.mesh(N, L)
     q = np.exp(-(X * X + Y * Y)).astype(np.complex128)
     Lp = orc.inverse_box(N, L)
     g = orc.Grid(N, Lp)
-    tol = 1e-13 if prec == "fp64" else 1e-12
+    if tol is None:
+        tol = 1e-13 if prec == "fp64" else 1e-12
     fwd = dbar.Plan(N, L, M=M, prec=prec, iterated=1, restart=16, tol=tol, max_batch=min(N * N, 1024))
     r, _, _, st = dbar.dbar_reflection(fwd.handle, q, g.z.ravel())
     assert st == dbar.DBAR_OK
@@ -44,14 +45,16 @@ def test_round_trip_reproduces_the_papers_reconstruction_errors(dbar, row, prec)
     N, L, err_paper = t["rows"][row]
     q, qr, _ = _round_trip(dbar, N, L, t["M"], prec)
     err = float(np.max(np.abs(qr - q)))
-    assert err_paper / 10 <= err <= err_paper, (N, L, prec, err, err_paper)
+    # the method's own discretisation error at these grids: it reproduces the printed value
+    assert abs(err / err_paper - 1.0) < 0.1, (N, L, prec, err, err_paper)
 
 
 def test_round_trip_matches_the_oracle(dbar):
     # r at sampled k against the oracle; q from the GPU's r against the oracle's formula on the
     # same r (the oracle needs one solve per point, so r is not recomputed on the whole grid)
+    # (both solved to 1e-14: the pointwise comparison below is at 1e-12 of max |r|)
     N, L, M = 32, 1.5, 11
-    q, qr, r = _round_trip(dbar, N, L, M, "fp64")
+    q, qr, r = _round_trip(dbar, N, L, M, "fp64", tol=1e-14)
     g = orc.Grid(N, orc.inverse_box(N, L))
     for a, b in ((0, 0), (7, 21), (16, 16), (31, 4)):
         ro = orc.reflection_iterated(q, g.z[a, b], N, L, M=M, tol=1e-14)["r"]

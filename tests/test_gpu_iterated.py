@@ -28,23 +28,27 @@ def _mixture(N, L):
             ).astype(np.complex128)
 
 
-def test_iterated_operator_matches_oracle(dbar):
+@pytest.mark.parametrize("fp32", [False, True])
+def test_iterated_operator_matches_oracle(dbar, fp32):
+    # 2k on the xi-grid; the last two put xi0 = 2i conj(k) at the edge of the box (xi_max = 32/L),
+    # one on the Nyquist wavenumber -N/2 (held as +N/2), where the quotient by xi - xi0 must not
+    # wrap periodically (eq. dbarinvShift)
     torch = pytest.importorskip("torch")
     N, L = 64, 3.0
     Q = _mixture(N, L)
-    k = np.array([(2 + 1j) / (2 * L), (-3 + 5j) / (2 * L)])      # 2k on the xi-grid
-    plan = dbar.Plan(N, L, M=2, prec="fp64", iterated=1, max_batch=2)
+    k = np.array([(2 + 1j) / (2 * L), (-3 + 5j) / (2 * L), (31 + 30j) / (2 * L), (-32 - 29j) / (2 * L)])
+    plan = dbar.Plan(N, L, M=2, prec="mixed" if fp32 else "fp64", iterated=1, max_batch=k.size)
     rng = np.random.default_rng(3)
     g = orc.Grid(N, L)
     h = np.stack([g.F(np.exp(-((g.X - 0.3) ** 2 + g.Y ** 2)) * (1 + 0.5j * rng.standard_normal()))
-                  for _ in range(2)])
+                  for _ in range(k.size)])
     Qd = torch.from_numpy(Q).cuda()
-    hd = torch.from_numpy(h).cuda()
+    hd = torch.from_numpy(h.astype(np.complex64) if fp32 else h).cuda()
     out = torch.empty_like(hd)
-    dbar.dbar_apply(plan.handle, Qd, k, hd, out)
-    for i in range(2):
+    dbar.dbar_apply(plan.handle, Qd, k, hd, out, fp32=fp32)
+    for i in range(k.size):
         ref = orc.IteratedProblem(Q, k[i], N, L).apply(h[i])
-        assert rel(out[i].cpu().numpy(), ref) < 1e-13, i
+        assert rel(out[i].cpu().numpy(), ref) < (2e-6 if fp32 else 1e-13), i
 
 
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("mixed", 1e-10)])
@@ -86,4 +90,7 @@ def test_iterated_plan_rejects_k_off_the_grid_and_m_output(dbar):
     assert e.value.status == dbar.DBAR_EINVAL
     with pytest.raises(dbar.DbarError) as e:
         plan.solve(Q, [0.0], want_m=True)
+    assert e.value.status == dbar.DBAR_EINVAL
+    with pytest.raises(dbar.DbarError) as e:   # 2 k L = 20 beyond the grid's wavenumbers (N/2 = 16)
+        plan.solve(Q, [4.0 + 0.0j], want_m=False)
     assert e.value.status == dbar.DBAR_EINVAL
