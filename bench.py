@@ -525,6 +525,17 @@ def run_ds2(args):
         qt = dbar.dbar_ds2_potential(inv.handle, r.reshape(N, N), z, t=0.1, stream=stream)[0]
         e[3].record(stream)
         torch.cuda.synchronize()
+        routes = None
+        if args.ds2_routes:
+            # remark of Sec. 6 (time dependence): q(., t) from the same r through the Sec. 4 route
+            # (two solves per point) against the iterated route, L-infinity difference
+            direct = dbar.Plan(N, Lp, M=M, prec=args.ds2_prec, restart=32, tol=args.ds2_tol, max_batch=mb)
+            routes = {}
+            for tt in (0.1, 0.8):
+                qi = dbar.dbar_ds2_potential(inv.handle, r.reshape(N, N), z, t=tt, stream=stream)[0]
+                qd = dbar.dbar_ds2_potential(direct.handle, r.reshape(N, N), z, t=tt, stream=stream)[0]
+                routes[f"t{tt}"] = float(np.max(np.abs(qi - qd)))
+            direct.close()
         err = float(np.max(np.abs(qr.reshape(N, N) - q)))
         rows.append({"N": N, "L": L, "solves": 3 * N * N, "ms_r": round(e[0].elapsed_time(e[1]), 1),
                      "ms_q": round(e[1].elapsed_time(e[2]), 1), "ms_q_t": round(e[2].elapsed_time(e[3]), 1),
@@ -532,7 +543,8 @@ def run_ds2(args):
                      "iters_mean": float(np.mean(np.concatenate([it_r[:, 0], it_q[:, 0]]))),
                      "resid_max": float(max(np.max(res_r), np.max(res_q))),
                      "status_ok": bool(st_r == dbar.DBAR_OK and st_q == dbar.DBAR_OK),
-                     "l2_ratio_t0.1": float(np.linalg.norm(qt) / np.linalg.norm(qr))})
+                     "l2_ratio_t0.1": float(np.linalg.norm(qt) / np.linalg.norm(qr)),
+                     "route_difference": routes})
         fwd.close()
         inv.close()
     out = {"metric": "DS II round trip q -> r -> q over whole grids (Sec. 6.2), error vs the paper's table",
@@ -764,6 +776,8 @@ def main():
     ap.add_argument("--restart", type=int, default=32)
     ap.add_argument("--ds2-prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--ds2-tol", type=float, default=1e-13)
+    ap.add_argument("--ds2-routes", action="store_true",
+                    help="ds2: also q(., t) through the Sec. 4 route, difference to the iterated one")
     ap.add_argument("--iterated", action="store_true",
                     help="reflection workload: the iterated equation of Sec. 5 over the whole k-grid")
     ap.add_argument("--sstep", type=int, default=0,
