@@ -94,3 +94,25 @@ def test_iterated_plan_rejects_k_off_the_grid_and_m_output(dbar):
     with pytest.raises(dbar.DbarError) as e:   # 2 k L = 20 beyond the grid's wavenumbers (N/2 = 16)
         plan.solve(Q, [4.0 + 0.0j], want_m=False)
     assert e.value.status == dbar.DBAR_EINVAL
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("mixed", 1e-11)])
+def test_iterated_solve_at_the_papers_large_k(dbar, prec, tol):
+    # Sec. 5: k = 8.5936 ~ 55/6.4 at L = 3.2 (2kL = 55, xi0 at 86 % of the box edge at N = 128):
+    # the GPU's h at N = 128 equals the oracle's, and refining to N = 256 leaves it unchanged
+    L, k = 3.2, 55 / 6.4
+    pts = [(0, 0), (3, -2), (-5, 7), (10, 0)]
+    vals = {}
+    for N in (128, 256):
+        X, Y = wl.mesh(N, L)
+        q = np.exp(-(X * X + Y * Y)).astype(np.complex128)
+        plan = dbar.Plan(N, L, M=11, prec=prec, iterated=1, restart=16,
+                         tol=1e-14 if prec == "fp64" else 1e-12, max_batch=1)
+        r = plan.solve(q, [k], want_m=False)
+        assert r["status"] == dbar.DBAR_OK
+        h = r["S"][0]
+        vals[N] = np.array([h[m2 % N, m1 % N] for m1, m2 in pts])
+        if N == 128:
+            ref = orc.solve_iterated(q, k, N, L, M=11, tol=1e-14)["h"]
+            assert rel(h, ref) < tol
+    assert np.max(np.abs(vals[128] - vals[256])) < tol

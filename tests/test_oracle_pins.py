@@ -426,6 +426,26 @@ def test_shift_table_of_sec5_unshifted_slow_shifted_spectral():
         assert max(shifted[3:]) < 1e-13, shifted
 
 
+def test_iterated_equation_reaches_machine_precision_at_the_papers_large_k():
+    # Sec. 5: the paper's large-k case k = 8.5936, L = 3.2, N = 128 (its figure of the first two
+    # Born iterates); 2kL = 55.0 to 1e-3, i.e. 2k on the xi-grid (k = 55/6.4).  Refining the grid
+    # N = 128 -> 256 must not change the iterated equation's h (machine precision at N = 128 for
+    # this k, as Sec. 5.3 states), while the Sec. 4 equation's S still moves by ~1e-4 there
+    L, k = 3.2, 55 / 6.4
+    assert abs(2 * 8.5936 * L - 55) < 1e-3
+    pts = [(0, 0), (3, -2), (-5, 7), (10, 0)]
+    h, S = {}, {}
+    for N in (128, 256):
+        X, Y = wl.mesh(N, L)
+        q = np.exp(-(X * X + Y * Y)).astype(np.complex128)
+        hh = orc.solve_iterated(q, k, N, L, M=11, tol=1e-14)["h"]
+        SS = orc.solve_cgo(q, k, N, L, M=11, tol=1e-14)["S"]
+        h[N] = np.array([hh[m2 % N, m1 % N] for m1, m2 in pts])
+        S[N] = np.array([SS[m2 % N, m1 % N] for m1, m2 in pts])
+    assert np.max(np.abs(h[128] - h[256])) < 1e-14
+    assert np.max(np.abs(S[128] - S[256])) > 1e-5
+
+
 def test_iterated_shift_requires_2k_on_the_grid():
     with pytest.raises(ValueError):
         orc.shift_index(0.1 + 0.0j, 3.0)
