@@ -70,6 +70,22 @@ def peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
+def hbm_roofline(prof, variant=None, traffic_ok=False):
+    """Roofline object of the dominant kernel kind of a profile_table() (largest summed
+    CUDA-event time): algorithmic bytes / event time against the measured HBM copy rate.
+    traffic_ok: the workload's kernels are the captured ones (headline grid), else null."""
+    peak, peak_kind = peaks()
+    name, (ms, launches, nbytes) = max(prof.items(), key=lambda kv: kv[1][0])
+    achieved = nbytes / (ms / 1e3) / 1e9 if ms > 0 else 0.0
+    return {"bound": "hbm", "kernel": name, "achieved": round(achieved, 1), "peak": peak,
+            "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+            "traffic": ncu_traffic(name, nbytes / max(launches, 1), variant=variant) if traffic_ok else None,
+            "algorithmic_bytes_per_launch": nbytes / max(launches, 1), "avg_launch_ms": ms / max(launches, 1),
+            "kinds": {k: {"ms": round(v[0], 3), "launches": v[1],
+                          "GBs": round(v[2] / (v[0] / 1e3) / 1e9, 1) if v[0] > 0 else 0.0}
+                      for k, v in prof.items() if v[1]}}
+
+
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
 
@@ -444,7 +460,7 @@ def run_reflection(args):
     stream = torch.cuda.current_stream()
     if args.iterated:   # Sec. 5.3 route: one solve per k, every k of the xi-grid
         plan = dbar.Plan(N, L, M=M, prec="mixed", tol=1e-12, restart=16, iterated=1, inner_tol=args.inner_tol,
-                         max_batch=min(k.size, 4096))
+                         max_batch=min(k.size, 4096), sstep=args.sstep)
     else:               # Sec. 4 route: two solves per k, the k the grid resolves
         plan = dbar.Plan(N, L, M=M, prec="mixed", tol=1e-12, restart=args.restart, sstep=args.sstep,
                          inner_tol=args.inner_tol, max_batch=k.size)
@@ -452,12 +468,15 @@ def run_reflection(args):
         dbar.dbar_reflection(plan.handle, Qd, k, stream=stream)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dbar.dbar_profile(plan.handle, True)
     with ClockSampler(0) as clk:
         e0.record(stream)
         for _ in range(args.steps):
             r, iters, resid, status = dbar.dbar_reflection(plan.handle, Qd, k, stream=stream)
         e1.record(stream)
         torch.cuda.synchronize()
+    roofline = hbm_roofline(dbar.profile_table(plan.handle))
+    dbar.dbar_profile(plan.handle, False)
     ms = e0.elapsed_time(e1) / args.steps
     # sampled parity against the FP64 GPU path (same entry point, FP64 plan) and the Born-free
     # CPU oracle on a few k (host cores, spawned pool)
@@ -476,14 +495,16 @@ def run_reflection(args):
            "iters_inner_mean_per_r": float(np.mean(iters[:, 0])), "resid_max": float(np.max(resid)),
            "status_ok": bool(status == dbar.DBAR_OK), "err_vs_fp64_gpu_max": err64,
            "err_sample_k": [complex(x).__repr__() for x in k[sample]],
-           "max_abs_r": scale, "clocks": clk.summary()}
+           "max_abs_r": scale, "roofline": roofline, "clocks": clk.summary()}
     if not args.no_cpu_baseline:
         from oracle import dbar_oracle as orc
         t0 = time.perf_counter()
         fn = orc.reflection_iterated if args.iterated else orc.reflection
         ro = [fn(Q, kk, N, L, M=M, tol=1e-13)["r"] for kk in k[sample[:2]]]
+        dt = time.perf_counter() - t0
         out["err_vs_oracle_max"] = float(np.max(np.abs(r[sample[:2]] - np.array(ro))) / scale)
-        out["oracle_s_per_r"] = round((time.perf_counter() - t0) / 2, 2)
+        out["cpu_baseline"] = {"value": round(2 / dt, 4), "unit": "r/s", "cores": 1, "kind": "oracle",
+                               "sample": f"r at 2 of the {k.size} k by the FP64 CPU oracle on one core, {dt:.1f} s"}
     print(json.dumps(out))
 
 
@@ -517,9 +538,13 @@ def run_ds2(args):
         kw = dict(M=M, prec=args.ds2_prec, iterated=1, restart=16, tol=args.ds2_tol, max_batch=mb)
         fwd, inv = dbar.Plan(N, L, **kw), dbar.Plan(N, Lp, **kw)
         e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        dbar.dbar_profile(fwd.handle, True)
         e[0].record(stream)
         r, it_r, res_r, st_r = dbar.dbar_reflection(fwd.handle, q, k, stream=stream)
         e[1].record(stream)
+        torch.cuda.synchronize()
+        roofline = hbm_roofline(dbar.profile_table(fwd.handle))
+        dbar.dbar_profile(fwd.handle, False)
         qr, it_q, res_q, st_q = dbar.dbar_ds2_potential(inv.handle, r.reshape(N, N), z, stream=stream)
         e[2].record(stream)
         qt = dbar.dbar_ds2_potential(inv.handle, r.reshape(N, N), z, t=0.1, stream=stream)[0]
@@ -544,7 +569,19 @@ def run_ds2(args):
                      "resid_max": float(max(np.max(res_r), np.max(res_q))),
                      "status_ok": bool(st_r == dbar.DBAR_OK and st_q == dbar.DBAR_OK),
                      "l2_ratio_t0.1": float(np.linalg.norm(qt) / np.linalg.norm(qr)),
-                     "route_difference": routes})
+                     "route_difference": routes, "roofline_r_direction": roofline})
+        if N == table["rows"][4][0] and not args.no_cpu_baseline:
+            # the FP64 CPU oracle on two points of q (one iterated solve each), from the GPU's r
+            from oracle import dbar_oracle as orc
+            t0 = time.perf_counter()
+            pts = [(N // 2, N // 2), (N // 3, 2 * N // 3)]
+            qo = [orc.ds2_potential(r.reshape(N, N), X[a, b] + 1j * Y[a, b], N, L, M=M, tol=1e-13) for a, b in pts]
+            dt = time.perf_counter() - t0
+            rows[-1]["cpu_baseline"] = {"value": round(len(pts) / dt, 4), "unit": "q values/s", "cores": 1,
+                                        "kind": "oracle",
+                                        "sample": f"q at 2 of the {N * N} points by the FP64 CPU oracle on one core, "
+                                                  f"{dt:.1f} s"}
+            rows[-1]["err_vs_oracle_max"] = float(max(abs(qr.reshape(N, N)[a, b] - v) for (a, b), v in zip(pts, qo)))
         fwd.close()
         inv.close()
     out = {"metric": "DS II round trip q -> r -> q over whole grids (Sec. 6.2), error vs the paper's table",

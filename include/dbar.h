@@ -76,8 +76,8 @@ typedef enum {
                           is summed directly over every pair of grid points
                           (N^4 complex multiply-adds per field).  The paper
                           keeps it as an independent test of the Taylor code.
-                          FP64 only (prec = DBAR_FP64), N <= 256, one Krylov
-                          vector per sweep, not with iterated; M is unused and
+                          FP64 only (prec = DBAR_FP64), N <= 256, not with
+                          iterated, sstep 0 means 1 here; M is unused and
                           dbar_taylor returns DBAR_EINVAL                     */
 } dbar_regularisation;
 
@@ -118,9 +118,12 @@ typedef struct {
                         dbarinvShift) for h instead of the Sec. 4 equation for
                         S: h - K_0(H(h)) = -i F(Q), supported near the origin
                         for every k; 2k must lie on the xi-grid (2 k L integer
-                        in both components).  One vector per sweep (sstep 0
-                        or 1); dbar_solve_cgo returns h in S_out and takes no
-                        m_out.  0 (default): the Sec. 4 equation              */
+                        in both components, within [-N/2, N/2]).  sstep 0
+                        means 1 here (solves of a few iterations, which
+                        blocks overshoot); sstep 2 or 4 chain whole
+                        applications of its operator in a block;
+                        dbar_solve_cgo returns h in S_out and takes no m_out.
+                        0 (default): the Sec. 4 equation                      */
   int regularisation; /* dbar_regularisation; 0 (DBAR_REG_TAYLOR) by default */
 } dbar_params;
 

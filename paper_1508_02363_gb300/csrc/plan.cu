@@ -836,6 +836,16 @@ static dbar_status block_steps(dbar_plan* P, int nb, int j0, int j1, cudaStream_
   ba.x_dd = P->resid_dd ? 1 : 0;
   for (int c0 = j0; c0 < j1; c0 += S) {
     const int J = c0 + 1;  // basis vectors v_0..v_{J-1} exist
+    if (P->iter || P->conv) {
+      // operators made of several applications (iterated equation, convolution
+      // route): the chain p_{i+1} = K p_i one whole application at a time
+      for (int i = 0; i < S; ++i) {
+        const cx<TI>* pin = V + (size_t)(J - 1 + i) * n;
+        dbar_status s = apply_op<TI>(P, pin, vss, i == 0 ? P->cs.sigma + (J - 1) : nullptr, i == 0 ? m + 1 : 0,
+                                     V + (size_t)(J + i) * n, vss, P->cs.run, nb, st);
+        if (s != DBAR_OK) return s;
+      }
+    } else {
     // the chain p_{i+1} = K p_i into basis slots J..J+S-1: pass A of v_{J-1};
     // per step the coefficients and pass B, then pass C fused with the next
     // step's pass A (the last step: pass C alone)
@@ -866,6 +876,7 @@ static dbar_status block_steps(dbar_plan* P, int nb, int j0, int j1, cudaStream_
       } else {
         CK(timed(P, st, K_PASS_C, [&] { return launch_pass_c<TI, TI, PC_KS>(a, nb, st); }));
       }
+    }
     }
     CK(timed(P, st, K_DOTS, [&] { return launch_bdots<TI, S>(ba, V, vss, J, nb, st); }));
     CK(timed(P, st, K_SCALAR, [&] { return launch_bscalar<S>(ba, P->cs, P->Hraw, P->bcoef, P->upd, J, nb, st); }));
@@ -1085,14 +1096,12 @@ static dbar_status check_params(const dbar_params* p) {
     return fail(DBAR_EINVAL, "sstep must be 0, 1, 2 or 4");
   if (p->sstep > 1 && p->restart % p->sstep != 0) return fail(DBAR_EINVAL, "restart must be a multiple of sstep");
   if (p->iterated != 0 && p->iterated != 1) return fail(DBAR_EINVAL, "iterated must be 0 or 1");
-  if (p->iterated && p->sstep > 1) return fail(DBAR_EINVAL, "the iterated equation runs one Krylov vector per sweep");
   if (p->regularisation != DBAR_REG_TAYLOR && p->regularisation != DBAR_REG_CONV)
     return fail(DBAR_EINVAL, "regularisation must be DBAR_REG_TAYLOR or DBAR_REG_CONV");
   if (p->regularisation == DBAR_REG_CONV) {
     if (p->prec != DBAR_FP64) return fail(DBAR_EINVAL, "the convolution regularisation runs in FP64 only (DBAR_FP64)");
     if (p->N > 256) return fail(DBAR_EINVAL, "the convolution regularisation needs N <= 256 (its direct sum costs N^4)");
     if (p->iterated) return fail(DBAR_EINVAL, "the convolution regularisation is not combined with the iterated equation");
-    if (p->sstep > 1) return fail(DBAR_EINVAL, "the convolution regularisation runs one Krylov vector per sweep");
     if (p->max_batch > 4096) return fail(DBAR_EINVAL, "the convolution regularisation takes max_batch <= 4096");
   }
   return DBAR_OK;
@@ -1353,7 +1362,9 @@ dbar_status plan_create_ex(const dbar_params* p, int per_slot_q, dbar_plan** out
   P->m = p->restart;
   P->iter = p->iterated != 0;
   P->conv = p->regularisation == DBAR_REG_CONV;
-  P->sstep = (P->iter || P->conv) ? 1 : (p->sstep > 0 ? p->sstep : (p->restart % 4 == 0 ? 4 : (p->restart % 2 == 0 ? 2 : 1)));
+  // automatic choice: blocks of 4 for the Sec. 4 operator; one vector per sweep for the
+  // multi-application operators (their solves take few iterations, which blocks overshoot)
+  P->sstep = ((P->conv || P->iter) && p->sstep == 0) ? 1 : (p->sstep > 0 ? p->sstep : (p->restart % 4 == 0 ? 4 : (p->restart % 2 == 0 ? 2 : 1)));
   P->mixed = (p->prec == DBAR_MIXED);
   P->resid_dd = P->mixed && p->resid_mode == DBAR_RESID_DOUBLE_FLOAT;
   P->n = (long long)P->N * P->N;

@@ -44,9 +44,9 @@ def test_parameter_validation_is_host_side(lib):
     from paper_1508_02363_gb300 import dbar
     for bad in (dict(N=48), dict(N=16), dict(N=4096), dict(L=0.0), dict(M=17), dict(restart=0),
                 dict(tol=0.0), dict(prec=7), dict(sstep=3), dict(sstep=8), dict(sstep=4, restart=30),
-                dict(iterated=2), dict(iterated=1, sstep=4), dict(regularisation=2),
+                dict(iterated=2), dict(regularisation=2),
                 dict(regularisation=1), dict(regularisation=1, prec=0, N=512),
-                dict(regularisation=1, prec=0, iterated=1), dict(regularisation=1, prec=0, sstep=4),
+                dict(regularisation=1, prec=0, iterated=1),
                 dict(regularisation=1, prec=0, max_batch=5000)):
         args = dict(N=64, L=4.0)
         args.update(bad)

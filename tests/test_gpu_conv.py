@@ -70,13 +70,15 @@ def test_conv_operator_matches_oracle(dbar, N, L):
         assert rel(out[i].cpu().numpy(), ref) < 1e-13, i
 
 
-@pytest.mark.parametrize("graphs", [0, 1])
-def test_conv_solve_matches_oracle(dbar, graphs):
-    # 5 k values on a 2-slot plan: two full batches and a ragged one
+@pytest.mark.parametrize("graphs,sstep", [(0, 0), (1, 0), (1, 4)])
+def test_conv_solve_matches_oracle(dbar, graphs, sstep):
+    # 5 k values on a 2-slot plan: two full batches and a ragged one; one vector per sweep
+    # (sstep 0 means 1 on this route) and s-step blocks of whole applications
     N, L = 64, 4.0
     Q = _potential(N, L)
     k = np.array([0.0, 0.7 + 0.4j, -1.5 + 2.0j, 2.5 - 0.5j, -0.3 - 1.1j])
-    plan = dbar.Plan(N, L, prec="fp64", regularisation="conv", tol=1e-13, restart=16, max_batch=2, graphs=graphs)
+    plan = dbar.Plan(N, L, prec="fp64", regularisation="conv", tol=1e-13, restart=16, max_batch=2, graphs=graphs,
+                     sstep=sstep)
     r = plan.solve(Q, k)
     assert r["status"] == dbar.DBAR_OK
     assert np.all(r["resid"] < 1e-13)

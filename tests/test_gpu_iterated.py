@@ -51,12 +51,15 @@ def test_iterated_operator_matches_oracle(dbar, fp32):
         assert rel(out[i].cpu().numpy(), ref) < (2e-6 if fp32 else 1e-13), i
 
 
+@pytest.mark.parametrize("sstep", [1, 4])
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("mixed", 1e-10)])
-def test_iterated_solve_matches_oracle(dbar, prec, tol):
+def test_iterated_solve_matches_oracle(dbar, prec, tol, sstep):
+    # one vector per sweep, and s-step blocks chaining whole applications of the operator
     N, L = 64, 3.2
     Q = _mixture(N, L)
     k = np.array([0.0, (4 + 2j) / (2 * L), (-6 - 10j) / (2 * L), (12 + 0j) / (2 * L)])
-    plan = dbar.Plan(N, L, M=2, prec=prec, iterated=1, tol=1e-13 if prec == "fp64" else 1e-12, max_batch=4)
+    plan = dbar.Plan(N, L, M=2, prec=prec, iterated=1, tol=1e-13 if prec == "fp64" else 1e-12, max_batch=4,
+                     sstep=sstep)
     r = plan.solve(Q, k, want_m=False)
     assert r["status"] == dbar.DBAR_OK
     for i in range(k.size):
