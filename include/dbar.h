@@ -47,7 +47,7 @@ typedef enum {
   DBAR_ENOMEM = 2,   /* a device allocation failed                              */
   DBAR_ENOCONV = 3,  /* some k missed tol within max_iter / max_outer; outputs
                         are still written (best iterate and its residual)       */
-  DBAR_ETIMEOUT = 4, /* reserved: a bounded device wait ran out                 */
+  DBAR_ETIMEOUT = 4, /* a bounded device wait ran out (kernel-side limit)     */
   DBAR_ECUDA = 5,    /* a CUDA call failed; see dbar_last_error()               */
   DBAR_EBUSY = 6     /* reserved for asynchronous interfaces                    */
 } dbar_status;

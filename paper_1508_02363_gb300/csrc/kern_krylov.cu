@@ -4,6 +4,11 @@
 #include "launch.cuh"
 #include "passes.cuh"
 
+// 1: the block update streams the basis through shared memory by bulk asynchronous copies
+#ifndef DBAR_BUPD_BULK
+#define DBAR_BUPD_BULK 1
+#endif
+
 namespace dbar {
 
 template <typename T>
@@ -71,6 +76,14 @@ template <typename T, int S>
 cudaError_t launch_bupdate(const BlockArgs& a, const int* upd, cx<T>* V, long long vss, int J, int nslots,
                            cudaStream_t s) {
   if (nslots <= 0) return cudaSuccess;
+#if DBAR_BUPD_BULK
+  if (a.n % KB_CHUNK == 0) {  // whole chunks: the basis streamed by bulk asynchronous copies
+    const size_t sm = (size_t)KBStages<T>::value * KB_CHUNK * sizeof(cx<T>);
+    k_bupdate_bulk<T, S, false><<<dim3(a.nwork, nslots), KR_THREADS, sm, s>>>(a, upd, V, vss, J);
+    k_bupdate_bulk<T, S, true><<<dim3(a.nwork, nslots), KR_THREADS, sm, s>>>(a, upd, V, vss, J);
+    return cudaGetLastError();
+  }
+#endif
   k_bupdate<T, S, false><<<dim3(a.nwork, nslots), KR_THREADS, 0, s>>>(a, upd, V, vss, J);
   k_bupdate<T, S, true><<<dim3(a.nwork, nslots), KR_THREADS, 0, s>>>(a, upd, V, vss, J);
   return cudaGetLastError();

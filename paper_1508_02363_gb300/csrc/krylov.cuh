@@ -639,4 +639,165 @@ __global__ void __launch_bounds__(KR_THREADS) k_bupdate(const BlockArgs a, const
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Block update with the basis streamed through shared memory by bulk
+// asynchronous copies (cp.async.bulk, completion counted on an mbarrier):
+// KB_STAGES chunks of basis vectors are in flight per CTA while the threads
+// work on an earlier one, so a CTA keeps ~KB_STAGES x 8 KB of reads
+// outstanding with no registers held for them.  Same arithmetic, order and
+// results as k_bupdate.  Every wait is bounded: when one runs out the CTA
+// sets *a.err, stops computing, drains its own copies (bounded) and returns.
+// Needs n to be a multiple of KB_CHUNK (chunks of whole 16-byte units).
+// ---------------------------------------------------------------------------
+// stages per CTA: 32 KB of shared memory for either element size
+template <typename T>
+struct KBStages {
+  static constexpr int value = sizeof(cx<T>) == 8 ? 4 : 2;
+};
+constexpr int kWaitLimit = 1 << 20;  // try_wait rounds before a wait is declared lost
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// one arrival that also announces the bytes the next copy will deliver
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+// true once the barrier's phase with the given parity has completed; false after kWaitLimit rounds
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t addr = smem_u32(bar);
+  for (int i = 0; i < kWaitLimit; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+template <typename T, int S, bool XU>
+__global__ void __launch_bounds__(KR_THREADS) k_bupdate_bulk(const BlockArgs a, const int* __restrict__ upd,
+                                                              cx<T>* __restrict__ V, long long vss, int J) {
+  constexpr int KB_STAGES = KBStages<T>::value;
+  extern __shared__ __align__(128) unsigned char kb_stage_raw[];
+  cx<T>* stage = reinterpret_cast<cx<T>*>(kb_stage_raw);  // [KB_STAGES][KB_CHUNK]
+  __shared__ __align__(8) uint64_t bar[KB_STAGES];
+  __shared__ T cf[S * S + 129 * S];
+  __shared__ T yc[129 + S];
+  __shared__ int lost;
+  const int slot = blockIdx.y;
+  const int u = upd[slot];
+  if (u != (XU ? 2 : 1)) return;
+  constexpr uint32_t kBytes = KB_CHUNK * sizeof(cx<T>);
+  cx<T>* Vs = V + (size_t)slot * vss;
+  const long long c0 = (long long)blockIdx.x * KB_CHUNK;  // this CTA's chunk: elements c0 .. c0 + KB_CHUNK - 1
+  if (threadIdx.x == 0) {
+    lost = 0;
+    for (int s = 0; s < KB_STAGES; ++s) mbar_init(&bar[s], 1);
+    mbar_fence_init();
+    // the first KB_STAGES basis vectors of the sweep
+    for (int r = 0; r < KB_STAGES && r < J; ++r) {
+      mbar_expect_tx(&bar[r], kBytes);
+      bulk_g2s(stage + (size_t)r * KB_CHUNK, Vs + (size_t)r * a.n + c0, kBytes, &bar[r]);
+    }
+  }
+  const double* bc = a.bcoef + (size_t)slot * (S * S + a.mp1 * S);
+  for (int q = threadIdx.x; q < S * S + J * S; q += blockDim.x) cf[q] = (T)bc[q];
+  if (XU)
+    for (int q = threadIdx.x; q < J + S; q += blockDim.x) yc[q] = (T)a.ycoef[(size_t)slot * a.mp1 + q];
+  __syncthreads();
+  cx<T> acc[S][KB_EPT];
+  {
+    cx<T> w[S][KB_EPT];
+#pragma unroll
+    for (int k = 0; k < S; ++k)
+#pragma unroll
+      for (int e = 0; e < KB_EPT; ++e) w[k][e] = ldg(Vs + (size_t)(J + k) * a.n + c0 + threadIdx.x + e * KR_THREADS);
+#pragma unroll
+    for (int i = 0; i < S; ++i)
+#pragma unroll
+      for (int e = 0; e < KB_EPT; ++e) {
+        cx<T> s = mkc((T)0, (T)0);
+#pragma unroll
+        for (int k = 0; k <= i; ++k) s = mkc(s.re + cf[k * S + i] * w[k][e].re, s.im + cf[k * S + i] * w[k][e].im);
+        acc[i][e] = s;
+      }
+  }
+  cx<T> dx[KB_EPT];
+#pragma unroll
+  for (int e = 0; e < KB_EPT; ++e) dx[e] = mkc((T)0, (T)0);
+  int r = 0;
+  for (; r < J; ++r) {
+    const int st = r % KB_STAGES;
+    if (!mbar_wait(&bar[st], (uint32_t)((r / KB_STAGES) & 1))) lost = 1;
+    __syncthreads();  // every thread has waited (and sees `lost`)
+    if (lost) break;
+    const T yr = XU ? yc[r] : (T)0;
+    const cx<T>* src = stage + (size_t)st * KB_CHUNK + threadIdx.x;
+#pragma unroll
+    for (int e = 0; e < KB_EPT; ++e) {
+      const cx<T> v = src[e * KR_THREADS];
+#pragma unroll
+      for (int i = 0; i < S; ++i) {
+        const T c = cf[S * S + r * S + i];
+        acc[i][e] = mkc(acc[i][e].re + c * v.re, acc[i][e].im + c * v.im);
+      }
+      if (XU) dx[e] = mkc(dx[e].re + yr * v.re, dx[e].im + yr * v.im);
+    }
+    __syncthreads();  // stage st has been read by every thread: refill it
+    if (threadIdx.x == 0 && r + KB_STAGES < J) {
+      mbar_expect_tx(&bar[st], kBytes);
+      bulk_g2s(stage + (size_t)st * KB_CHUNK, Vs + (size_t)(r + KB_STAGES) * a.n + c0, kBytes, &bar[st]);
+    }
+  }
+  if (r < J) {
+    // a wait ran out: report it, drain this CTA's copies still in flight (bounded), return
+    if (threadIdx.x == 0) {
+      if (a.err) atomicExch(a.err, 1);
+      const int issued = J < r + KB_STAGES ? J : r + KB_STAGES;
+      for (int q = r; q < issued; ++q) mbar_wait(&bar[q % KB_STAGES], (uint32_t)((q / KB_STAGES) & 1));
+    }
+    return;
+  }
+#pragma unroll
+  for (int i = 0; i < S; ++i)
+#pragma unroll
+    for (int e = 0; e < KB_EPT; ++e) Vs[(size_t)(J + i) * a.n + c0 + threadIdx.x + e * KR_THREADS] = acc[i][e];
+  if (XU) {
+#pragma unroll
+    for (int e = 0; e < KB_EPT; ++e) {
+      const long long idx = c0 + threadIdx.x + e * KR_THREADS;
+      cx<T> d = dx[e];
+#pragma unroll
+      for (int i = 0; i < S; ++i) d = mkc(d.re + yc[J + i] * acc[i][e].re, d.im + yc[J + i] * acc[i][e].im);
+      if constexpr (std::is_same<T, float>::value) {
+        if (a.x_dd) {
+          cx<dd>* xp = reinterpret_cast<cx<dd>*>(a.X) + (size_t)slot * a.xss + idx;
+          *xp = xadd(*xp, d);
+          continue;
+        }
+      }
+      cx<double>* xp = reinterpret_cast<cx<double>*>(a.X) + (size_t)slot * a.xss + idx;
+      *xp = xadd(*xp, d);
+    }
+  }
+}
+
 }  // namespace dbar

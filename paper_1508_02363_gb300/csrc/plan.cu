@@ -194,6 +194,7 @@ struct dbar_plan {
   int* h_rolls = nullptr;       // [B][2] host staging
   int* dshift = nullptr;        // [B][2] the same offsets signed, in (-N/2, N/2] (pass A's divisor)
   int* h_dshift = nullptr;      // [B][2] host staging
+  int* h_err = nullptr;         // pinned copy of flag[1]: a bounded device wait ran out
   void* It1 = nullptr;          // [B][n] rolled field (FP64-sized)
   void* It2 = nullptr;          // [B][n] first operator application (FP64-sized)
   // convolution regularisation (params.regularisation = DBAR_REG_CONV), FP64
@@ -243,6 +244,7 @@ struct dbar_plan {
     if (h_nsteps) cudaFreeHost(h_nsteps);
     if (h_rolls) cudaFreeHost(h_rolls);
     if (h_dshift) cudaFreeHost(h_dshift);
+    if (h_err) cudaFreeHost(h_err);
     if (hmask) cudaFreeHost(hmask);
     if (h_ek) cudaFreeHost(h_ek);
     cudaSetDevice(cur);
@@ -834,6 +836,7 @@ static dbar_status block_steps(dbar_plan* P, int nb, int j0, int j1, cudaStream_
   ba.X = P->x64;
   ba.xss = n;
   ba.x_dd = P->resid_dd ? 1 : 0;
+  ba.err = P->flag + 1;
   for (int c0 = j0; c0 < j1; c0 += S) {
     const int J = c0 + 1;  // basis vectors v_0..v_{J-1} exist
     if (P->iter || P->conv) {
@@ -1054,7 +1057,13 @@ static dbar_status run_cycles(dbar_plan* P, int nb, cudaStream_t st) {
   bool pending_account = false;
   for (int cyc = 0; cyc <= P->p.max_outer; ++cyc) {
     CK(cudaMemcpyAsync(P->h_active, P->cs.active, nb * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(P->h_err, P->flag + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    if (*P->h_err) {
+      cudaMemsetAsync(P->flag + 1, 0, sizeof(int), st);
+      cudaStreamSynchronize(st);
+      return fail(DBAR_ETIMEOUT, "a bounded device wait ran out (bulk copies of the block update)");
+    }
     P->prof.harvest();
     if (pending_account) {
       if (P->p.graphs) harvest_graph(P);
@@ -1493,7 +1502,8 @@ dbar_status plan_create_ex(const dbar_params* p, int per_slot_q, dbar_plan** out
     AL(P->upd, B);
   }
 #undef AL
-  if (cudaMemset(P->ticket, 0, (size_t)B * sizeof(int)) != cudaSuccess) {
+  if (cudaMemset(P->ticket, 0, (size_t)B * sizeof(int)) != cudaSuccess ||
+      cudaMemset(P->flag, 0, 4 * sizeof(int)) != cudaSuccess) {
     delete P;
     return fail(DBAR_ECUDA, "workspace initialisation failed");
   }
@@ -1507,6 +1517,7 @@ dbar_status plan_create_ex(const dbar_params* p, int per_slot_q, dbar_plan** out
       cudaMallocHost(&P->h_nsteps, (size_t)B * sizeof(int)) != cudaSuccess ||
       cudaMallocHost(&P->h_rolls, 2 * (size_t)B * sizeof(int)) != cudaSuccess ||
       cudaMallocHost(&P->h_dshift, 2 * (size_t)B * sizeof(int)) != cudaSuccess ||
+      cudaMallocHost(&P->h_err, sizeof(int)) != cudaSuccess ||
       cudaMallocHost(&P->h_ek, (size_t)B * 2 * P->N * sizeof(cx<double>)) != cudaSuccess) {
     delete P;
     return fail(DBAR_ENOMEM, "pinned host allocation failed");

@@ -92,6 +92,7 @@ struct BlockArgs {
   void* X;              // [slot][n] at stride xss: cx<double>, or cx<dd> when x_dd
   long long xss;
   int x_dd;
+  int* err;             // set to 1 when a bounded device wait runs out (nullable)
 };
 
 __host__ __device__ constexpr int block_items(int J, int S) { return J * S + S * (S + 1) / 2; }
