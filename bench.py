@@ -764,7 +764,7 @@ def run_serving(args):
            "n_mix": {str(N): int(sum(1 for _, n, _, _ in tickets if n == N)) for N in sizes},
            "config": {"L": L, "kmax": KMAX, "xi_q": XI_Q, "pool_per_N": POOL, "restart": args.restart,
                       "inner_tol": args.inner_tol,
-                      "column_variant": colv, "column_tune_ms": [round(tune0, 4), round(tune1, 4)], "serve_batch": args.serve_batch, "seed": args.seed},
+                      "serve_batch": args.serve_batch, "seed": args.seed},
            "clocks": clk.summary()}
     print(json.dumps(out))
 
