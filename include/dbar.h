@@ -112,7 +112,8 @@ typedef struct {
                         convergence is checked at block ends; restart must be
                         a multiple of sstep.  1: one vector per sweep
                         (classical Gram-Schmidt per step).  0 (default): 4
-                        if restart is a multiple of 4, else 2 if even, else 1 */
+                        if restart is a multiple of 4, else 2 if even, else 1;
+                        1 for iterated and convolution plans               */
   int iterated;      /* 1: the plan solves the iterated integral equation of
                         Sec. 5.2-5.3 (eq. eqh2, shifted regularisation eq.
                         dbarinvShift) for h instead of the Sec. 4 equation for
