@@ -220,6 +220,8 @@ struct dbar_plan {
   int* h_active = nullptr;
   int* h_nsteps = nullptr;
   cx<double>* h_ek = nullptr;  // pinned [B][2N]
+  double* h_k = nullptr;       // pinned [B][2] k values of the batch being loaded
+  double* kdev = nullptr;      // [B][2] the same on the device (E_k tables built there)
 
   double inv2piL = 0, sw = 0, fillscale = 0;
 
@@ -247,6 +249,7 @@ struct dbar_plan {
     if (h_err) cudaFreeHost(h_err);
     if (hmask) cudaFreeHost(hmask);
     if (h_ek) cudaFreeHost(h_ek);
+    if (h_k) cudaFreeHost(h_k);
     cudaSetDevice(cur);
   }
   size_t inner_elem() const { return mixed ? sizeof(cx<float>) : sizeof(cx<double>); }
@@ -377,13 +380,11 @@ static dbar_status upload_ek(dbar_plan* P, const double* k, int nb, cudaStream_t
     CK(cudaMemcpyAsync(P->rolls, P->h_rolls, 2 * nb * sizeof(int), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(P->dshift, P->h_dshift, 2 * nb * sizeof(int), cudaMemcpyHostToDevice, st));
   }
-  fill_ek(P, k, nb, P->h_ek);
-  for (int s = 0; s < nb; ++s) {
-    CK(cudaMemcpyAsync(P->ex64 + (size_t)s * N, P->h_ek + (size_t)s * 2 * N, N * sizeof(cx<double>),
-                       cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(P->ey64 + (size_t)s * N, P->h_ek + (size_t)s * 2 * N + N, N * sizeof(cx<double>),
-                       cudaMemcpyHostToDevice, st));
-  }
+  // E_k tables of the batch built on the device from its k values (one copy of 16 bytes per k;
+  // the previous batch's copy has completed: every cycle loop ends with a stream synchronisation)
+  std::memcpy(P->h_k, k, 2 * (size_t)nb * sizeof(double));
+  CK(cudaMemcpyAsync(P->kdev, P->h_k, 2 * (size_t)nb * sizeof(double), cudaMemcpyHostToDevice, st));
+  CK(timed(P, st, K_OTHER, [&] { return launch_fill_ek(P->kdev, nb, N, P->p.L, P->ex64, P->ey64, st); }));
   CK(timed(P, st, K_OTHER, [&] { return launch_cast_fields(P->ex64, P->ex32, (long long)nb * N, st); }));
   CK(timed(P, st, K_OTHER, [&] { return launch_cast_fields(P->ey64, P->ey32, (long long)nb * N, st); }));
   if (P->resid_dd) {
@@ -1474,6 +1475,7 @@ dbar_status plan_create_ex(const dbar_params* p, int per_slot_q, dbar_plan** out
     AL(P->Cv2, (size_t)B * 2 * n);
   }
   AL(P->flag, 4);
+  AL(P->kdev, 2 * (size_t)B);
   CycleState& c = P->cs;
   const int m = P->m;
   AL(c.H, (size_t)B * m * (m + 1));
@@ -1518,7 +1520,8 @@ dbar_status plan_create_ex(const dbar_params* p, int per_slot_q, dbar_plan** out
       cudaMallocHost(&P->h_rolls, 2 * (size_t)B * sizeof(int)) != cudaSuccess ||
       cudaMallocHost(&P->h_dshift, 2 * (size_t)B * sizeof(int)) != cudaSuccess ||
       cudaMallocHost(&P->h_err, sizeof(int)) != cudaSuccess ||
-      cudaMallocHost(&P->h_ek, (size_t)B * 2 * P->N * sizeof(cx<double>)) != cudaSuccess) {
+      cudaMallocHost(&P->h_ek, (size_t)B * 2 * P->N * sizeof(cx<double>)) != cudaSuccess ||
+      cudaMallocHost(&P->h_k, (size_t)B * 2 * sizeof(double)) != cudaSuccess) {
     delete P;
     return fail(DBAR_ENOMEM, "pinned host allocation failed");
   }
