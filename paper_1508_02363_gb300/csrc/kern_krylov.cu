@@ -241,31 +241,6 @@ template cudaError_t launch_roll<double>(const cx<double>*, long long, const dou
 template cudaError_t launch_roll<dd>(const cx<dd>*, long long, const double*, int, const int*, const int*, int,
                                      cx<dd>*, long long, int, cudaStream_t);
 
-// E_k = exp(conj(kz) - kz) = exp(-2i (k2 x + k1 y)) = ex(x) ey(y) on the grid
-// x_j = L(-pi + 2 pi j/N) for nb values k = k[2s] + i k[2s+1] (Sec. 5.1), FP64:
-// ex[s][j] = e^{-2i k2 x_j}, ey[s][j] = e^{-2i k1 x_j}.
-__global__ void k_fill_ek(const double* __restrict__ k, int nb, int N, double L, cx<double>* __restrict__ ex,
-                          cx<double>* __restrict__ ey) {
-  const long long total = (long long)nb * N;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int s = (int)(i / N), j = (int)(i - (long long)s * N);
-    const double x = L * (-M_PI + 2.0 * M_PI * (double)j / (double)N);
-    double sn, cs;
-    sincos(2.0 * k[2 * s + 1] * x, &sn, &cs);
-    ex[i] = mkc(cs, -sn);
-    sincos(2.0 * k[2 * s] * x, &sn, &cs);
-    ey[i] = mkc(cs, -sn);
-  }
-}
-cudaError_t launch_fill_ek(const double* k, int nb, int N, double L, cx<double>* ex, cx<double>* ey, cudaStream_t s) {
-  if (nb <= 0) return cudaSuccess;
-  const long long total = (long long)nb * N;
-  const int blocks = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
-  k_fill_ek<<<blocks, 256, 0, s>>>(k, nb, N, L, ex, ey);
-  return cudaGetLastError();
-}
-
 // out[p2][p1] = conj(r[p2][p1] e^{-i t (k^2 + conj(k)^2)/4}), k = x_{p1} + i y_{p2} on the
 // grid x_j = L(-pi + 2 pi j/N): the potential of the D-bar problem in k at time t
 // (eq. rt; k^2 + conj(k)^2 = 2 (x^2 - y^2)).  Once per call, FP64.

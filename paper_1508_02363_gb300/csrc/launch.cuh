@@ -121,8 +121,6 @@ cudaError_t launch_conv_split(const cx<double>* S, long long s_ss, const double*
 cudaError_t launch_conv_sum(const cx<double>* f, const cx<double>* Kt, int N, const int* run, const cx<double>* Q,
                             long long q_ss, const cx<double>* ex, const cx<double>* ey, double sw, int w_out,
                             cx<double>* out, long long o_ss, int nslots, cudaStream_t s);
-// ex[s][j] = e^{-2i k2 x_j}, ey[s][j] = e^{-2i k1 x_j} for k (device, [nb][2]) on the grid of box L
-cudaError_t launch_fill_ek(const double* k, int nb, int N, double L, cx<double>* ex, cx<double>* ey, cudaStream_t s);
 cudaError_t launch_cast_fields(const cx<double>* in, cx<float>* out, long long n, cudaStream_t s);
 cudaError_t launch_split_fields(const cx<double>* in, cx<dd>* out, long long n, cudaStream_t s);
 cudaError_t launch_check_finite(const double* p, long long n, int* flag, cudaStream_t s);
