@@ -16,6 +16,7 @@
 #include <mutex>
 #include <tuple>
 #include <cstdio>
+#include <cstdint>
 #include <cstring>
 #include <new>
 #include <string>
@@ -1628,9 +1629,16 @@ extern "C" dbar_status dbar_solve_cgo(dbar_plan_t P, const double* Q, int nk, co
     s = P->mixed ? run_cycles<float>(P, nb, st) : run_cycles<double>(P, nb, st);
     if (s != DBAR_OK) return s;
     const cx<double>* S64 = nullptr;
-    s = solution_fp64(P, 0, nb, st, &S64);
-    if (s != DBAR_OK) return s;
-    CK(cudaMemcpyAsync(S_out + (size_t)k0 * n * 2, S64, (size_t)nb * n * sizeof(cx<double>), d2o, st));
+    if (io_on_device && P->resid_dd && reinterpret_cast<uintptr_t>(S_out) % 16 == 0) {
+      // double-float solution converted straight into the caller's (16-byte aligned) device buffer
+      cx<double>* dst = reinterpret_cast<cx<double>*>(S_out) + (size_t)k0 * n;
+      CK(timed(P, st, K_OTHER, [&] { return launch_dd_to_fp64(P->x64, dst, (long long)nb * n, st); }));
+      S64 = dst;
+    } else {
+      s = solution_fp64(P, 0, nb, st, &S64);
+      if (s != DBAR_OK) return s;
+      CK(cudaMemcpyAsync(S_out + (size_t)k0 * n * 2, S64, (size_t)nb * n * sizeof(cx<double>), d2o, st));
+    }
     if (m_out) {
       s = h_of_S64(P, S64, n, reinterpret_cast<cx<double>*>(P->T2), n, nb, st);
       if (s != DBAR_OK) return s;
