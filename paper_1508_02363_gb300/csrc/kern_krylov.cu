@@ -41,11 +41,6 @@ cudaError_t launch_xupdate(long long n, int mp1, const int* nsteps, const double
                                                                    reinterpret_cast<cx<double>*>(X), xss);
   return cudaGetLastError();
 }
-cudaError_t launch_dd_to_fp64(const void* in, cx<double>* out, long long n, cudaStream_t s) {
-  const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
-  k_dd_to_fp64<<<blocks, 256, 0, s>>>(reinterpret_cast<const cx<dd>*>(in), out, n);
-  return cudaGetLastError();
-}
 
 #define KR_INST(T)                                                                                     \
   template cudaError_t launch_dots<T>(const KryArgs&, const cx<T>*, long long, const cx<T>*, long long, int, \

@@ -255,27 +255,6 @@ __global__ void __launch_bounds__(KR_THREADS) k_xupdate(long long n, int mp1, co
 }
 
 // FP64 copy of double-float fields (solution read-out)
-// float -> double by bit manipulation on the integer pipes (exact, like the conversion
-// instruction, which on GB300 occupies the small FP64 pipe): sign, exponent rebiased by
-// 1023 - 127, mantissa shifted into place; zeros, subnormals, infinities and NaNs take
-// the conversion instruction.
-__device__ __forceinline__ double f2d_bits(float f) {
-  const unsigned int u = __float_as_uint(f);
-  const unsigned int e = (u >> 23) & 0xffu;
-  if (e == 0u || e == 0xffu) return (double)f;
-  const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
-                               ((unsigned long long)(e + 896u) << 52) |
-                               ((unsigned long long)(u & 0x7fffffu) << 29);
-  return __longlong_as_double((long long)b);
-}
-
-__global__ void k_dd_to_fp64(const cx<dd>* __restrict__ in, cx<double>* __restrict__ out, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const cx<dd> v = in[i];
-    out[i] = mkc(f2d_bits(v.re.hi) + f2d_bits(v.re.lo), f2d_bits(v.im.hi) + f2d_bits(v.im.lo));
-  }
-}
-
 // Start of a cycle from a squared-norm partial sum over nblk blocks:
 // beta = ||r||, sigma_0 = 1/beta, g = beta e_1, stop threshold, flags.
 // first != 0: the vector is b itself (records ||b||).  mask (nullable): only the

@@ -31,7 +31,7 @@ using namespace dbar;
 typedef std::complex<double> zd;
 
 namespace dbar {
-// kern_ek.cu: ex[s][j] = e^{-2i k2 x_j}, ey[s][j] = e^{-2i k1 x_j} for k (device, [nb][2]) on the grid of box L
+// kern_aux.cu: ex[s][j] = e^{-2i k2 x_j}, ey[s][j] = e^{-2i k1 x_j} for k (device, [nb][2]) on the grid of box L
 cudaError_t launch_fill_ek(const double* k, int nb, int N, double L, cx<double>* ex, cx<double>* ey, cudaStream_t s);
 }  // namespace dbar
 
