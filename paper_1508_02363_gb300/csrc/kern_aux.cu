@@ -46,13 +46,26 @@ __device__ __forceinline__ double f2d_bits(float f) {
 }
 
 __global__ void k_dd_to_fp64(const cx<dd>* __restrict__ in, cx<double>* __restrict__ out, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    // one 16-byte load and one 16-byte store per element (both buffers 16-byte aligned)
-    const float4 v = __ldg(reinterpret_cast<const float4*>(in) + i);
-    reinterpret_cast<double2*>(out)[i] = make_double2(f2d_bits(v.x) + f2d_bits(v.y), f2d_bits(v.z) + f2d_bits(v.w));
+  // four independent 16-byte loads in flight per thread before the conversions; both
+  // buffers 16-byte aligned
+  const float4* src = reinterpret_cast<const float4*>(in);
+  double2* dst = reinterpret_cast<double2*>(out);
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; i0 < n; i0 += 4 * stride) {
+    float4 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const long long i = i0 + u * stride;
+      if (i < n) v[u] = __ldg(src + i);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const long long i = i0 + u * stride;
+      if (i < n)
+        dst[i] = make_double2(f2d_bits(v[u].x) + f2d_bits(v[u].y), f2d_bits(v[u].z) + f2d_bits(v[u].w));
+    }
   }
 }
-
 cudaError_t launch_dd_to_fp64(const void* in, cx<double>* out, long long n, cudaStream_t s) {
   const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
   k_dd_to_fp64<<<blocks, 256, 0, s>>>(reinterpret_cast<const cx<dd>*>(in), out, n);
