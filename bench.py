@@ -461,10 +461,10 @@ def run_reflection(args):
     stream = torch.cuda.current_stream()
     if args.iterated:   # Sec. 5.3 route: one solve per k, every k of the xi-grid
         plan = dbar.Plan(N, L, M=M, prec="mixed", tol=1e-12, restart=16, iterated=1, inner_tol=args.inner_tol,
-                         max_batch=min(k.size, 4096), sstep=args.sstep)
+                         max_batch=min(k.size, 4096), sstep=args.sstep, inner_M=args.inner_m)
     else:               # Sec. 4 route: two solves per k, the k the grid resolves
         plan = dbar.Plan(N, L, M=M, prec="mixed", tol=1e-12, restart=args.restart, sstep=args.sstep,
-                         inner_tol=args.inner_tol, max_batch=k.size)
+                         inner_tol=args.inner_tol, max_batch=k.size, inner_M=args.inner_m)
     for _ in range(args.warmup):
         dbar.dbar_reflection(plan.handle, Qd, k, stream=stream)
     torch.cuda.synchronize()
@@ -490,7 +490,7 @@ def run_reflection(args):
     out = {"metric": "DS II reflection coefficient: r(k) values/s over the k-grid",
            "workload": "reflection", "route": "iterated equation (Sec. 5.3), one solve per k, whole xi-grid"
            if args.iterated else "Sec. 4 equation, two solves per k, the k the grid resolves",
-           "N": N, "L": L, "M": M, "nk": int(k.size),
+           "N": N, "L": L, "M": M, "inner_M": args.inner_m or M, "nk": int(k.size),
            "ms_per_grid": round(ms, 2), "r_per_s": round(k.size / (ms / 1e3), 1),
            "solves_per_s": round(per_r * k.size / (ms / 1e3), 1),
            "iters_inner_mean_per_r": float(np.mean(iters[:, 0])), "resid_max": float(np.max(resid)),
@@ -536,7 +536,8 @@ def run_ds2(args):
         k = (K1 + 1j * K2).ravel()
         z = (X + 1j * Y).ravel()
         mb = min(N * N, 4096)
-        kw = dict(M=M, prec=args.ds2_prec, iterated=1, restart=16, tol=args.ds2_tol, max_batch=mb)
+        kw = dict(M=M, prec=args.ds2_prec, iterated=1, restart=16, tol=args.ds2_tol, max_batch=mb,
+                  inner_M=args.inner_m if args.ds2_prec == "mixed" else 0)
         fwd, inv = dbar.Plan(N, L, **kw), dbar.Plan(N, Lp, **kw)
         e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         dbar.dbar_profile(fwd.handle, True)
@@ -555,7 +556,8 @@ def run_ds2(args):
         if args.ds2_routes:
             # remark of Sec. 6 (time dependence): q(., t) from the same r through the Sec. 4 route
             # (two solves per point) against the iterated route, L-infinity difference
-            direct = dbar.Plan(N, Lp, M=M, prec=args.ds2_prec, restart=32, tol=args.ds2_tol, max_batch=mb)
+            direct = dbar.Plan(N, Lp, M=M, prec=args.ds2_prec, restart=32, tol=args.ds2_tol, max_batch=mb,
+                               inner_M=kw["inner_M"])
             routes = {}
             for tt in (0.1, 0.8):
                 qi = dbar.dbar_ds2_potential(inv.handle, r.reshape(N, N), z, t=tt, stream=stream)[0]
@@ -586,7 +588,8 @@ def run_ds2(args):
         fwd.close()
         inv.close()
     out = {"metric": "DS II round trip q -> r -> q over whole grids (Sec. 6.2), error vs the paper's table",
-           "workload": "ds2", "M": M, "prec": args.ds2_prec, "tol": args.ds2_tol, "rows": rows}
+           "workload": "ds2", "M": M, "inner_M": args.inner_m if args.ds2_prec == "mixed" else M,
+           "prec": args.ds2_prec, "tol": args.ds2_tol, "rows": rows}
     print(json.dumps(out))
 
 
@@ -821,6 +824,8 @@ def main():
     ap.add_argument("--sstep", type=int, default=0,
                     help="Krylov vectors per basis sweep: 1, 2, 4, or 0 = the library's automatic choice")
     ap.add_argument("--inner-tol", dest="inner_tol", type=float, default=1e-6)
+    ap.add_argument("--inner-m", dest="inner_m", type=int, default=0,
+                    help="reflection / ds2 (M = 11, mixed): Taylor order of the FP32 inner operator (0: M)")
     ap.add_argument("--check-k", dest="check_k", type=int, default=4)
     ap.add_argument("--cpu-sample", dest="cpu_sample", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")

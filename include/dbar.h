@@ -126,6 +126,13 @@ typedef struct {
                         dbar_solve_cgo returns h in S_out and takes no m_out.
                         0 (default): the Sec. 4 equation                      */
   int regularisation; /* dbar_regularisation; 0 (DBAR_REG_TAYLOR) by default */
+  int inner_M;       /* DBAR_MIXED: Taylor order of the FP32 inner operator,
+                        0 <= inner_M <= M; 0 (default) means M.  The right-hand
+                        side and the true residual always use M, so the result
+                        is the M solution; a smaller inner order only changes
+                        the correction solves (the M = 2 and M = 11 operators
+                        differ by ~1e-8 relative, below FP32 rounding) and
+                        saves their table reads and moments                  */
 } dbar_params;
 
 typedef struct dbar_plan* dbar_plan_t;

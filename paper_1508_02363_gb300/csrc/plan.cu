@@ -149,6 +149,7 @@ struct dbar_plan {
   int* hmask = nullptr;  // [B] pinned host staging of it
   long long nlaunch = 0;  // kernels launched by this plan
   int N = 0, logN = 0, M = 0, MA = 0, B = 0, m = 0;
+  int Min = 0;          // Taylor order of the FP32 inner passes (params.inner_M, else M)
   bool mixed = false;
   int device = 0;
   long long n = 0;  // N*N
@@ -434,7 +435,7 @@ PassArgs<float> base_args<float>(const dbar_plan* P) {
   std::memset(&a, 0, sizeof(a));
   a.colv = P->colv;
   a.g = make_geo<float>(P->N);
-  a.M = P->M;
+  a.M = P->Min;
   a.tw = P->tw32;
   a.Da = P->Da32;
   a.Da64 = P->Da64;
@@ -494,7 +495,7 @@ static void set_unit_e(const dbar_plan* P, PassArgs<T>& a) {
 // Taylor coefficients of the fields pass A just read (k_coef), for pass B.
 template <typename T>
 static cudaError_t launch_coef_for(dbar_plan* P, const PassArgs<T>& a, int nb, cudaStream_t st) {
-  return launch_coef(P->partA, std::is_same<T, float>::value, P->M, P->N, P->Da64, P->Da32, P->fillscale,
+  return launch_coef(P->partA, std::is_same<T, float>::value, a.M, P->N, P->Da64, P->Da32, P->fillscale,
                      P->coefp, P->ticket, P->tcoef, nb, st);
 }
 
@@ -785,7 +786,7 @@ static void account_cycle(dbar_plan* P, const int* act, const int* ns, int nb, i
     by[K_RES_C] += 3.0 * F64 + F;
   }
   if (P->conv) return;
-  by[K_PASS_B] += (double)launched_steps * (P->M + 2) * F;
+  by[K_PASS_B] += (double)launched_steps * ((P->mixed ? P->Min : P->M) + 2) * F;
   if (nact) by[K_RES_B] += (P->M + 2) * F64;
 }
 
@@ -1112,6 +1113,7 @@ static dbar_status check_params(const dbar_params* p) {
     return fail(DBAR_EINVAL, "sstep must be 0, 1, 2 or 4");
   if (p->sstep > 1 && p->restart % p->sstep != 0) return fail(DBAR_EINVAL, "restart must be a multiple of sstep");
   if (p->iterated != 0 && p->iterated != 1) return fail(DBAR_EINVAL, "iterated must be 0 or 1");
+  if (p->inner_M < 0 || p->inner_M > p->M) return fail(DBAR_EINVAL, "inner_M must be in [0, M]");
   if (p->regularisation != DBAR_REG_TAYLOR && p->regularisation != DBAR_REG_CONV)
     return fail(DBAR_EINVAL, "regularisation must be DBAR_REG_TAYLOR or DBAR_REG_CONV");
   if (p->regularisation == DBAR_REG_CONV) {
@@ -1280,7 +1282,7 @@ static std::mutex g_tune_mu;
 static std::map<std::tuple<int, int, int>, std::pair<int, std::pair<double, double>>> g_tune_cache;
 
 static dbar_status autotune_columns(dbar_plan* P) {
-  const auto key = std::make_tuple(P->device, P->N, P->M);
+  const auto key = std::make_tuple(P->device, P->N, P->Min);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
@@ -1375,6 +1377,7 @@ dbar_status plan_create_ex(const dbar_params* p, int per_slot_q, dbar_plan** out
   while ((1 << P->logN) < P->N) ++P->logN;
   P->M = p->M;
   P->MA = std::max(1, p->M);
+  P->Min = (p->prec == DBAR_MIXED && p->inner_M > 0) ? p->inner_M : p->M;
   P->m = p->restart;
   P->iter = p->iterated != 0;
   P->conv = p->regularisation == DBAR_REG_CONV;
@@ -1893,6 +1896,7 @@ extern "C" dbar_status dbar_taylor(dbar_plan_t P, int nk, const void* S, double*
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (fp32) {
     PassArgs<float> a = base_args<float>(P);
+    a.M = P->M;  // the plan's order, whatever the inner solve uses
     a.in = reinterpret_cast<const cx<float>*>(S);
     a.in_ss = P->n;
     a.out = P->T1;

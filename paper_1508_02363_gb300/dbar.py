@@ -38,7 +38,7 @@ class dbar_params(ctypes.Structure):
                 ("zero_fill", ctypes.c_int), ("max_batch", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("max_outer", ctypes.c_int), ("resid_mode", ctypes.c_int), ("graphs", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("sstep", ctypes.c_int), ("iterated", ctypes.c_int),
-                ("regularisation", ctypes.c_int)]
+                ("regularisation", ctypes.c_int), ("inner_M", ctypes.c_int)]
 
 
 class dbar_request(ctypes.Structure):

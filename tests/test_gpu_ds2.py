@@ -69,3 +69,23 @@ def test_round_trip_matches_the_oracle(dbar):
     inv = dbar.Plan(N, Lp, M=M, prec="fp64", iterated=1, restart=16, tol=1e-13, max_batch=4)
     qt = dbar.dbar_ds2_potential(inv.handle, r, np.array([z]), t=0.3)[0][0]
     assert abs(qt - orc.ds2_potential(r, z, N, L, M=M, t=0.3, tol=1e-14)) < 1e-12
+
+
+def test_round_trip_with_a_lower_inner_taylor_order(dbar):
+    # mixed precision with the FP32 correction solves at Taylor order 2 (params.inner_M) while the
+    # right-hand side and the true residual use M = 11: the same reconstruction error
+    t = json.load(open(os.path.join(GOLDEN, "ds2_reconstruction.json")))
+    N, L, err_paper = t["rows"][3]
+    X, Y = wl.mesh(N, L)
+    q = np.exp(-(X * X + Y * Y)).astype(np.complex128)
+    Lp = orc.inverse_box(N, L)
+    g = orc.Grid(N, Lp)
+    kw = dict(M=t["M"], prec="mixed", iterated=1, restart=16, tol=1e-12, max_batch=N * N, inner_M=2)
+    fwd = dbar.Plan(N, L, **kw)
+    r, it_r, res_r, st = dbar.dbar_reflection(fwd.handle, q, g.z.ravel())
+    assert st == dbar.DBAR_OK and np.all(res_r <= 1e-12)
+    inv = dbar.Plan(N, Lp, **kw)
+    qr, it_q, res_q, st = dbar.dbar_ds2_potential(inv.handle, r.reshape(N, N), (X + 1j * Y).ravel())
+    assert st == dbar.DBAR_OK and np.all(res_q <= 1e-12)
+    err = float(np.max(np.abs(qr.reshape(N, N) - q)))
+    assert abs(err / err_paper - 1.0) < 0.1, (err, err_paper)

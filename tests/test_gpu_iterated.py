@@ -119,3 +119,19 @@ def test_iterated_solve_at_the_papers_large_k(dbar, prec, tol):
             ref = orc.solve_iterated(q, k, N, L, M=11, tol=1e-14)["h"]
             assert rel(h, ref) < tol
     assert np.max(np.abs(vals[128] - vals[256])) < tol
+
+
+def test_lower_inner_taylor_order_gives_the_same_solution(dbar):
+    # params.inner_M: FP32 correction solves at M = 2 under an M = 11 right-hand side and residual
+    N, L = 64, 3.2
+    Q = _mixture(N, L)
+    k = np.array([0.0, (4 + 2j) / (2 * L), (-6 - 10j) / (2 * L)])
+    full = dbar.Plan(N, L, M=11, prec="mixed", iterated=1, tol=1e-12, max_batch=3).solve(Q, k, want_m=False)
+    low = dbar.Plan(N, L, M=11, prec="mixed", iterated=1, tol=1e-12, max_batch=3, inner_M=2).solve(Q, k,
+                                                                                                   want_m=False)
+    assert full["status"] == dbar.DBAR_OK and low["status"] == dbar.DBAR_OK
+    for i in range(k.size):
+        ref = orc.solve_iterated(Q, k[i], N, L, M=11, tol=1e-14)["h"]
+        assert rel(low["S"][i], ref) < 1e-10, i
+        assert rel(full["S"][i], ref) < 1e-10, i
+    assert np.all(low["iters"][:, 1] <= full["iters"][:, 1] + 1)
