@@ -98,12 +98,14 @@ template cudaError_t launch_bscalar<4>(const BlockArgs&, const CycleState&, doub
 
 cudaError_t launch_finalize_h(const KryArgs& a, double* H, int j, int nslots, cudaStream_t s) {
   if (nslots <= 0) return cudaSuccess;
-  k_finalize_h<<<nslots, KR_THREADS, 0, s>>>(a, H, j);
+  constexpr int per = KR_THREADS / 32;
+  k_finalize_h<<<(nslots + per - 1) / per, KR_THREADS, 0, s>>>(a, H, j, nslots);
   return cudaGetLastError();
 }
 cudaError_t launch_givens(const KryArgs& a, const CycleState& c, int j, int nslots, cudaStream_t s) {
   if (nslots <= 0) return cudaSuccess;
-  k_givens<<<nslots, KR_THREADS, 0, s>>>(a, c, j);
+  constexpr int per = KR_THREADS / 32;
+  k_givens<<<(nslots + per - 1) / per, KR_THREADS, 0, s>>>(a, c, j, nslots);
   return cudaGetLastError();
 }
 cudaError_t launch_solve_y(const CycleState& c, int nslots, cudaStream_t s) {

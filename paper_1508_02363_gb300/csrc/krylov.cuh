@@ -81,16 +81,17 @@ __global__ void __launch_bounds__(KR_THREADS) k_dots(const KryArgs a, const cx<T
 }
 
 // H[slot][j][i] = h_i = sigma_i sum_chunks part;  coef[slot][i] = h_i sigma_i
-static __global__ void __launch_bounds__(KR_THREADS) k_finalize_h(const KryArgs a, double* H, int j) {
-  __shared__ double sh[KR_THREADS / 32];
-  const int slot = blockIdx.x;
-  if (!a.run[slot]) return;
+// One warp per slot (KR_THREADS / 32 slots per block): the j + 1 reductions are
+// warp shuffles, not block barriers, and thousands of small slots share blocks.
+static __global__ void __launch_bounds__(KR_THREADS) k_finalize_h(const KryArgs a, double* H, int j, int nslots) {
+  const int slot = blockIdx.x * (KR_THREADS / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (slot >= nslots || !a.run[slot]) return;
   for (int i = 0; i <= j; ++i) {
     double s = 0.0;
     const double* p = a.part + ((size_t)slot * a.mp1 + i) * a.nchunk;
-    for (int c = threadIdx.x; c < a.nchunk; c += blockDim.x) s += p[c];
-    s = block_sum_256(s, sh);
-    if (threadIdx.x == 0) {
+    for (int c = lane; c < a.nchunk; c += 32) s += p[c];
+    s = warp_sum(s, 32);
+    if (lane == 0) {
       const double sg = a.sigma[(size_t)slot * a.mp1 + i];
       const double h = s * sg;
       H[((size_t)slot * (a.mp1 - 1) + j) * a.mp1 + i] = h;
@@ -180,14 +181,14 @@ __device__ inline bool givens_column(const CycleState& c, int slot, int j, doubl
 }
 
 // Norm of the new vector, Givens rotation of column j, residual estimate.
-static __global__ void __launch_bounds__(KR_THREADS) k_givens(const KryArgs a, CycleState c, int j) {
-  __shared__ double sh[KR_THREADS / 32];
-  const int slot = blockIdx.x;
-  if (!c.run[slot]) return;
+// One warp per slot, as k_finalize_h.
+static __global__ void __launch_bounds__(KR_THREADS) k_givens(const KryArgs a, CycleState c, int j, int nslots) {
+  const int slot = blockIdx.x * (KR_THREADS / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (slot >= nslots || !c.run[slot]) return;
   double s = 0.0;
-  for (int q = threadIdx.x; q < a.nchunk; q += blockDim.x) s += a.part2[(size_t)slot * a.nchunk + q];
-  s = block_sum_256(s, sh);
-  if (threadIdx.x != 0) return;
+  for (int q = lane; q < a.nchunk; q += 32) s += a.part2[(size_t)slot * a.nchunk + q];
+  s = warp_sum(s, 32);
+  if (lane != 0) return;
   const int m = c.m;
   const double nrm = sqrt(s);
   double* Hc = c.H + ((size_t)slot * m + j) * (m + 1);

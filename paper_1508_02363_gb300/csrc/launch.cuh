@@ -36,8 +36,9 @@ inline int row_blocks(int N) { return N / row_lines(ilog2(N)); }
 // warp segments of one row line (N/16 threads, at most 32 per segment): the
 // number of row-moment partials pass A writes per row and moment
 inline int seg_count(int N) { return N / 16 >= 32 ? N / 512 : 1; }
-// rows per block of k_coef (one row per thread): N/8, at least 32
-inline int coef_rows(int N) { return N / 8 >= 32 ? N / 8 : 32; }
+// rows per block of k_coef (one row per thread): the whole row set for N <= 256 (one block
+// per slot: no cross-block combination; small grids come in large batches), else N/8
+inline int coef_rows(int N) { return N <= 256 ? N : N / 8; }
 
 // per-size launchers (kern_pass.cu, one translation unit per precision and size)
 template <typename T, int LOGN>

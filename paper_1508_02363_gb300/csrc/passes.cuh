@@ -365,17 +365,22 @@ static __global__ void __launch_bounds__(256) k_coef(const cx<PT>* __restrict__ 
       s = mkc(t1.re + t2.im, t1.im - t2.re);
     }
     if (p2 & 1) s = mkc(-s.re, -s.im);
-    sre[threadIdx.x] = ST(s.re);
-    sim[threadIdx.x] = ST(s.im);
-    __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-      if ((int)threadIdx.x < w) {
-        sre[threadIdx.x] = sre[threadIdx.x] + sre[threadIdx.x + w];
-        sim[threadIdx.x] = sim[threadIdx.x] + sim[threadIdx.x + w];
-      }
-      __syncthreads();
+    // warp sums by shuffles, then the warps' sums (one barrier pair per coefficient)
+    const ST wr = warp_sum_t(ST(s.re), 32), wi = warp_sum_t(ST(s.im), 32);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+      sre[wid] = wr;
+      sim[wid] = wi;
     }
-    if (threadIdx.x == 0) cp[n] = mkc((double)sre[0], (double)sim[0]);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      ST tr = sre[0], ti = sim[0];
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+        tr = tr + sre[w];
+        ti = ti + sim[w];
+      }
+      cp[n] = mkc((double)tr, (double)ti);
+    }
     __syncthreads();
   }
   if (threadIdx.x == 0) {
