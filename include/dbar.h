@@ -165,7 +165,10 @@ dbar_status dbar_plan_info(dbar_plan_t plan, size_t* device_bytes, int* max_batc
  *   Q        N*N complex (2*N*N doubles), physical layout; host or device
  *   nk       number of k values (0 is accepted and does nothing)
  *   k        2*nk doubles (Re k, Im k), host memory
- *   S_out    nk*N*N complex: S = xi m^ on the Fourier grid; host or device
+ *   S_out    nk*N*N complex: S = xi m^ on the Fourier grid; host or device.
+ *            A page-locked host S_out (cudaHostAlloc / cudaHostRegister, mapped
+ *            into the device's address space) of a mixed plan is written by
+ *            the device directly when m_out is NULL (no device staging copy)
  *   m_out    nk*N*N complex: m on the x-grid (Sec. 4.3, eq. S0Taylor: m = h);
  *            may be NULL
  *   iters    2*nk ints, host, may be NULL: (total inner iterations, cycles)

@@ -1585,13 +1585,25 @@ static dbar_status load_Q_device(dbar_plan* P, const cx<double>* Qd, cudaStream_
   return DBAR_OK;
 }
 
+// A host Q is copied as it is; the device-side check of load_Q_device rejects
+// non-finite entries (the same DBAR_EINVAL as for a device Q).
 static dbar_status load_Q(dbar_plan* P, const double* Q, int on_device, cudaStream_t st) {
   if (!Q) return fail(DBAR_EINVAL, "Q is NULL");
   if (on_device) return load_Q_device(P, reinterpret_cast<const cx<double>*>(Q), st);
-  for (long long i = 0; i < 2 * P->n; ++i)
-    if (!std::isfinite(Q[i])) return fail(DBAR_EINVAL, "Q has a non-finite entry");
   CK(cudaMemcpyAsync(P->Qdev, Q, P->n * sizeof(cx<double>), cudaMemcpyHostToDevice, st));
   return load_Q_device(P, P->Qdev, st);
+}
+
+// Device address of a host buffer that kernels may write (page-locked and
+// mapped into the device's address space, e.g. cudaHostAlloc memory), else
+// nullptr (pageable memory: the solution goes out by cudaMemcpyAsync).
+static cx<double>* mapped_host(void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();  // clear the query's error state
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? reinterpret_cast<cx<double>*>(at.devicePointer) : nullptr;
 }
 
 // FP64 view of the solutions of slots [s0, s0 + nb): x itself, or, with
@@ -1622,6 +1634,13 @@ extern "C" dbar_status dbar_solve_cgo(dbar_plan_t P, const double* Q, int nk, co
   if (s != DBAR_OK) return s;
   const long long n = P->n;
   const cudaMemcpyKind d2o = io_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  // where the conversion kernel can write S itself: a device S_out, or a mapped
+  // host S_out when m_out (computed from S on the device) is not requested;
+  // 16-byte aligned for its vector stores
+  cx<double>* direct = nullptr;
+  if (P->resid_dd && nk > 0)
+    direct = io_on_device ? reinterpret_cast<cx<double>*>(S_out) : (m_out ? nullptr : mapped_host(S_out));
+  if (reinterpret_cast<uintptr_t>(direct) % 16 != 0) direct = nullptr;
   bool noconv = false;
   std::vector<int> it(2 * P->B), nc(P->B);
   std::vector<double> rs(P->B);
@@ -1632,9 +1651,10 @@ extern "C" dbar_status dbar_solve_cgo(dbar_plan_t P, const double* Q, int nk, co
     s = P->mixed ? run_cycles<float>(P, nb, st) : run_cycles<double>(P, nb, st);
     if (s != DBAR_OK) return s;
     const cx<double>* S64 = nullptr;
-    if (io_on_device && P->resid_dd && reinterpret_cast<uintptr_t>(S_out) % 16 == 0) {
-      // double-float solution converted straight into the caller's (16-byte aligned) device buffer
-      cx<double>* dst = reinterpret_cast<cx<double>*>(S_out) + (size_t)k0 * n;
+    if (direct) {
+      // double-float solution converted straight into the caller's buffer (device
+      // memory, or mapped host memory written over the host link by the kernel)
+      cx<double>* dst = direct + (size_t)k0 * n;
       CK(timed(P, st, K_OTHER, [&] { return launch_dd_to_fp64(P->x64, dst, (long long)nb * n, st); }));
       S64 = dst;
     } else {

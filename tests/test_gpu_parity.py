@@ -198,6 +198,31 @@ def test_invalid_inputs_are_rejected(dbar):
     assert e.value.status == dbar.DBAR_EINVAL
 
 
+def test_page_locked_host_output_matches_device_and_pageable_outputs(dbar, torch_cuda):
+    # A page-locked host S_out of a mixed plan is written by the conversion kernel
+    # itself; pageable host memory goes through a copy, device memory is written
+    # in place: all three give the same bits.  With m_out requested the
+    # page-locked S_out takes the copy route.
+    torch = torch_cuda
+    w = wl.mixed_1024(N=128, nk=3, L=5.0)
+    plan = dbar.Plan(w.N, w.L, M=2, prec="mixed", tol=1e-12, max_batch=2)  # two batches: 2 + 1 k
+    shape = (w.k.size, w.N, w.N)
+    Sd = torch.empty(shape, dtype=torch.complex128, device="cuda")
+    assert plan.solve_device(dev(torch, w.Q), w.k, Sd)["status"] == dbar.DBAR_OK
+    Sp = torch.full(shape, np.nan, dtype=torch.complex128).pin_memory()
+    Qp = torch.from_numpy(np.ascontiguousarray(w.Q, dtype=np.complex128)).pin_memory()
+    st = dbar.dbar_solve_cgo(plan.handle, Qp.numpy(), w.k, Sp.numpy(), io_on_device=False)
+    assert st == dbar.DBAR_OK
+    r = plan.solve(w.Q, w.k)
+    assert np.array_equal(Sp.numpy(), Sd.cpu().numpy())
+    assert np.array_equal(r["S"], Sd.cpu().numpy())
+    Sp2 = torch.full(shape, np.nan, dtype=torch.complex128).pin_memory()
+    mp = np.zeros(shape, np.complex128)
+    st = dbar.dbar_solve_cgo(plan.handle, w.Q, w.k, Sp2.numpy(), mp, io_on_device=False)
+    assert st == dbar.DBAR_OK
+    assert np.array_equal(Sp2.numpy(), Sd.cpu().numpy()) and np.array_equal(mp, r["m"])
+
+
 def test_iteration_cap_reports_no_convergence(dbar):
     w = wl.plain_fp64()
     plan = dbar.Plan(w.N, w.L, prec="fp64", restart=4, max_iter=4, max_outer=1, tol=1e-13)
