@@ -157,6 +157,16 @@ dbar_status dbar_plan_create(const dbar_params* p, dbar_plan_t* out);
 /* Frees every device resource of the plan (NULL is accepted). */
 dbar_status dbar_plan_destroy(dbar_plan_t plan);
 
+/* Check of the bounded device-side wait (no plan needed): one CTA on the
+ * current device runs an mbarrier wait of the kind the bulk-copy block update
+ * uses, at most `rounds` try_wait rounds (1 <= rounds <= the sweeps' own limit,
+ * 2^18, about a second).  complete = 1: a 16-byte bulk copy completes the awaited phase and the
+ * call returns DBAR_OK; complete = 0: nothing completes it, the wait runs out
+ * and the call returns DBAR_ETIMEOUT with the context still usable.  seconds
+ * (may be NULL) receives the kernel's duration.  Synchronous on stream.
+ * Errors: DBAR_EINVAL (rounds), DBAR_ETIMEOUT, DBAR_ECUDA. */
+dbar_status dbar_check_bounded_wait(int complete, int rounds, double* seconds, void* stream);
+
 /* Bytes of device memory the plan holds, and the batch size it uses. */
 dbar_status dbar_plan_info(dbar_plan_t plan, size_t* device_bytes, int* max_batch);
 

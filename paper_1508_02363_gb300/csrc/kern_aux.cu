@@ -1,7 +1,9 @@
 // Small helper kernels outside the solve's sweeps: the per-slot factors of E_k
-// (Sec. 5.1) for a batch of k values, and the FP64 read-out of double-float fields.
+// (Sec. 5.1) for a batch of k values, the FP64 read-out of double-float fields,
+// and a check of the bounded mbarrier wait the bulk-copy sweeps rely on.
 #include <cuda_runtime.h>
 
+#include "krylov.cuh"
 #include "launch.cuh"
 
 namespace dbar {
@@ -69,6 +71,43 @@ __global__ void k_dd_to_fp64(const cx<dd>* __restrict__ in, cx<double>* __restri
 cudaError_t launch_dd_to_fp64(const void* in, cx<double>* out, long long n, cudaStream_t s) {
   const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
   k_dd_to_fp64<<<blocks, 256, 0, s>>>(reinterpret_cast<const cx<dd>*>(in), out, n);
+  return cudaGetLastError();
+}
+
+// One mbarrier wait of the kind the bulk-copy block update uses (mbarrier
+// try_wait rounds, at most `rounds` of them).  complete = 1: a 16-byte bulk copy
+// of src delivers the bytes the phase announces; complete = 0: the phase
+// announces 16 bytes that no copy delivers, so the wait runs out.  out[0] = 1 if
+// the phase completed, out[1] = the copied word, out[2] = rounds taken.  With a
+// copy issued, a wait that runs out waits once more (bounded) for that copy to
+// land before the CTA exits.
+__global__ void k_wait_check(int complete, int rounds, const int4* __restrict__ src, int* __restrict__ out) {
+  __shared__ __align__(16) int4 buf;
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  mbar_fence_init();
+  mbar_expect_tx(&bar, (uint32_t)sizeof(int4));
+  if (complete) bulk_g2s(&buf, src, (uint32_t)sizeof(int4), &bar);
+  const uint32_t addr = smem_u32(&bar);
+  int done = 0, i = 0;
+  for (; i < rounds && !done; ++i) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(addr)
+        : "memory");
+  }
+  if (!done && complete) mbar_wait(&bar, 0);  // drain the copy in flight
+  out[0] = done;
+  out[1] = done ? buf.x : 0;
+  out[2] = i;
+}
+int wait_limit_rounds() { return kWaitLimit; }
+cudaError_t launch_wait_check(int complete, int rounds, const int4* src, int* out, cudaStream_t s) {
+  k_wait_check<<<1, 32, 0, s>>>(complete, rounds, src, out);
   return cudaGetLastError();
 }
 

@@ -649,7 +649,7 @@ template <typename T>
 struct KBStages {
   static constexpr int value = sizeof(cx<T>) == 8 ? 4 : 2;
 };
-constexpr int kWaitLimit = 1 << 20;  // try_wait rounds before a wait is declared lost
+constexpr int kWaitLimit = 1 << 18;  // try_wait rounds before a wait is declared lost (~1 s on GB300)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));

@@ -33,6 +33,9 @@ typedef std::complex<double> zd;
 namespace dbar {
 // kern_aux.cu: ex[s][j] = e^{-2i k2 x_j}, ey[s][j] = e^{-2i k1 x_j} for k (device, [nb][2]) on the grid of box L
 cudaError_t launch_fill_ek(const double* k, int nb, int N, double L, cx<double>* ex, cx<double>* ey, cudaStream_t s);
+// kern_aux.cu: one bounded mbarrier wait (out[0] completed, out[1] copied word, out[2] rounds)
+cudaError_t launch_wait_check(int complete, int rounds, const int4* src, int* out, cudaStream_t s);
+int wait_limit_rounds();
 }  // namespace dbar
 
 static thread_local std::string g_last_error;
@@ -1551,6 +1554,42 @@ extern "C" dbar_status dbar_plan_create(const dbar_params* p, dbar_plan_t* out) 
 
 extern "C" dbar_status dbar_plan_destroy(dbar_plan_t plan) {
   delete plan;
+  return DBAR_OK;
+}
+
+extern "C" dbar_status dbar_check_bounded_wait(int complete, int rounds, double* seconds, void* stream) {
+  if (rounds < 1 || rounds > wait_limit_rounds()) return fail(DBAR_EINVAL, "rounds must be in [1, the sweeps' limit]");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int magic = 0x5eed;
+  const int h_src[4] = {magic, 1, 2, 3};
+  int h_out[3] = {0, 0, 0};
+  void* mem = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto cleanup = [&] {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (mem) cudaFree(mem);
+  };
+  if (cudaMalloc(&mem, 32) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+      cudaEventCreate(&e1) != cudaSuccess ||
+      cudaMemcpyAsync(mem, h_src, sizeof(h_src), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemsetAsync(static_cast<char*>(mem) + 16, 0, 16, st) != cudaSuccess ||
+      cudaEventRecord(e0, st) != cudaSuccess ||
+      launch_wait_check(complete, rounds, static_cast<const int4*>(mem), reinterpret_cast<int*>(static_cast<char*>(mem) + 16),
+                        st) != cudaSuccess ||
+      cudaEventRecord(e1, st) != cudaSuccess ||
+      cudaMemcpyAsync(h_out, static_cast<char*>(mem) + 16, sizeof(h_out), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    const cudaError_t e = cudaGetLastError();
+    cleanup();
+    return fail(DBAR_ECUDA, std::string("bounded-wait check: ") + cudaGetErrorString(e));
+  }
+  float ms = 0.0f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cleanup();
+  if (seconds) *seconds = ms / 1e3;
+  if (!h_out[0]) return fail(DBAR_ETIMEOUT, "bounded-wait check: the wait ran out after " + std::to_string(h_out[2]) + " rounds");
+  if (h_out[1] != magic) return fail(DBAR_ECUDA, "bounded-wait check: the copied word is wrong");
   return DBAR_OK;
 }
 

@@ -75,6 +75,7 @@ _lib.dbar_m_from_S.argtypes = [_vp, _int, _vp, _vp, _vp]
 _lib.dbar_taylor.argtypes = [_vp, _int, _vp, _dp, _int, _vp]
 _lib.dbar_fft2.argtypes = [_vp, _int, _vp, _vp, _int, _int, _vp]
 _lib.dbar_fft2_noalloc.argtypes = [_int, _int, _vp, _vp, _int, _int, _vp]
+_lib.dbar_check_bounded_wait.argtypes = [_int, _int, _dp, _vp]
 _lib.dbar_profile_nkinds.argtypes = []
 _lib.dbar_profile_kind_name.argtypes = [_int]
 _lib.dbar_profile_kind_name.restype = ctypes.c_char_p
@@ -178,6 +179,15 @@ def dbar_solve_cgo(plan, Q, k, S_out, m_out=None, iters=None, resid=None, io_on_
     st = _lib.dbar_solve_cgo(plan, _ptr(Q), nk, kb.ctypes.data_as(_dp), _ptr(S_out), _ptr(m_out), ip, rp,
                              int(bool(io_on_device)), _stream(stream))
     return _check(st, (DBAR_OK, DBAR_ENOCONV))
+
+
+def dbar_check_bounded_wait(complete: bool, rounds: int, stream=None) -> float:
+    """One bounded mbarrier wait on the device (see include/dbar.h); returns the
+    kernel's seconds.  complete=False makes the wait run out: DbarError with
+    status DBAR_ETIMEOUT."""
+    sec = ctypes.c_double(0.0)
+    _check(_lib.dbar_check_bounded_wait(int(bool(complete)), int(rounds), ctypes.byref(sec), _stream(stream)))
+    return sec.value
 
 
 def dbar_reflection(plan, Q, k, t: float = 0.0, q_on_device=None, stream=None):
