@@ -237,7 +237,7 @@ def run_ours(args):
     plan = dbar.Plan(N, w.L, M=w.M, prec="mixed" if w.mixed else "fp64", tol=w.tol, restart=args.restart,
                      inner_tol=args.inner_tol, max_batch=nk, max_outer=args.max_outer, sstep=args.sstep,
                      autotune=args.autotune)
-    colv, tune0, tune1 = dbar.dbar_plan_tuning(plan.handle)
+    colv, tune = dbar.dbar_plan_tuning(plan.handle)
     stream = torch.cuda.current_stream()
     Qd = torch.from_numpy(w.Q).cuda()
     Sd = torch.empty((nk, N, N), dtype=torch.complex128, device="cuda")
@@ -350,7 +350,7 @@ def run_ours(args):
            "config": {"workload": w.name, "N": N, "L": w.L, "nk": nk, "M": w.M, "tol": w.tol,
                       "prec": "mixed" if w.mixed else "fp64", "restart": args.restart, "sstep": args.sstep,
                       "inner_tol": args.inner_tol,
-                      "column_variant": colv, "column_tune_ms": [round(tune0, 4), round(tune1, 4)],
+                      "column_variant": colv, "column_tune_ms": [round(x, 4) for x in tune],
                       "parallelism": f"replicas over k x{world}",
                       "l2": "inputs larger than L2 (device working set %.1f GB)" % (plan.device_bytes / 1e9)},
            "p50_ms": round(statistics.median(step_ms), 3),
@@ -436,7 +436,7 @@ def run_uneven(args):
            "resid_max": resid, "err_vs_fp64_max": max(errs), "err_sample": len(errs),
            "groups": {f"{N}/{'ab'[pot]}": len(v) for (N, pot), v in sorted(groups.items())},
            "autotune": bool(args.autotune),
-           "tiles": {str(N): dict(zip(("column_variant", "ms_v0", "ms_v1"), dbar.dbar_plan_tuning(p.handle)))
+           "tiles": {str(N): dict(zip(("column_variant", "ms_per_variant"), dbar.dbar_plan_tuning(p.handle)))
                      for N, p in sorted(plans.items())},
            "config": {"L": L, "kmax": 12.0, "restart": args.restart, "inner_tol": args.inner_tol},
            "clocks": clk.summary()}

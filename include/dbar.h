@@ -102,7 +102,7 @@ typedef struct {
                         shapes of the FP32 column pass on the plan's own
                         workspaces and keep the faster (results are identical
                         across shapes); cached per (device, N, M).
-                        0: first shape; 2: second shape (for checks)           */
+                        0: first shape; 2: second; 3: third (for checks)       */
   int sstep;         /* Krylov vectors formed per sweep of the stored basis.
                         2 or 4: s-step blocks -- the chain p, Kp, ..., of
                         K = A - I is orthogonalised against the basis in one
@@ -350,10 +350,16 @@ dbar_status dbar_profile(dbar_plan_t plan, int enable);
  * 8 N^4 per field and operator application.  Any pointer may be NULL. */
 dbar_status dbar_profile_read(dbar_plan_t plan, int kind, double* ms, long long* launches, double* bytes);
 
-/* The autotuner's choice: column-pass tile variant in use (0: 64-byte row
- * segments, 512 threads; 1: 32-byte segments, 256 threads) and the measured ms
- * per launch of each (0 when not tuned).  Any pointer may be NULL. */
-dbar_status dbar_plan_tuning(dbar_plan_t plan, int* column_variant, double* ms_variant0, double* ms_variant1);
+/* Tile variants of the FP32 operator column pass: 0: 64-byte row segments,
+ * 512 threads per block (N = 1024); 1: 32-byte segments, 256 threads; 2: the
+ * shape of 0 with two k values per block (shared table tiles, the two slots'
+ * transforms in lockstep). */
+#define DBAR_COLUMN_VARIANTS 3
+
+/* The autotuner's choice: column-pass tile variant in use, and the measured ms
+ * per launch of each variant in ms_per_variant[DBAR_COLUMN_VARIANTS] (0 when
+ * not tuned).  Any pointer may be NULL. */
+dbar_status dbar_plan_tuning(dbar_plan_t plan, int* column_variant, double* ms_per_variant);
 
 /* Kernels launched by this plan since its creation (profiling on or off). */
 dbar_status dbar_launch_count(dbar_plan_t plan, long long* count);

@@ -340,6 +340,103 @@ __device__ __forceinline__ void fft_line(cx<T> (&v)[16], cx<T>* line, int t, con
   }
 }
 
+// Register part of one Stockham stage (twiddles, R-point DFTs, and the last
+// stage's reordering), as in fft_stage.
+template <typename T, int N, int R, int NS, bool INV, bool LAST, bool TWM>
+__device__ __forceinline__ void fft_stage_regs(cx<T> (&v)[16], int t, const cx<T>* __restrict__ tw) {
+  constexpr int TPL = N / 16, B = 16 / R;
+#pragma unroll
+  for (int b = 0; b < B; ++b) {
+    if (NS > 1) {
+      constexpr int STEP = N / (NS * R);
+      const int k = (t + b * TPL) & (NS - 1);
+      if constexpr (TWM) {
+        cx<T> wr[R];
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          if ((r & (r - 1)) == 0) {
+            wr[r] = ldg(tw + r * k * STEP);
+          } else {
+            const int hb = 1 << (31 - __clz(r));
+            wr[r] = cmul(wr[hb], wr[r - hb]);
+          }
+        }
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          cx<T> w = wr[r];
+          if (INV) w.im = -w.im;
+          v[b * R + r] = cmul(v[b * R + r], w);
+        }
+      } else {
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          cx<T> w = ldg(tw + r * k * STEP);
+          if (INV) w.im = -w.im;
+          v[b * R + r] = cmul(v[b * R + r], w);
+        }
+      }
+    }
+    dft_reg<T, R, INV>(&v[b * R]);
+  }
+  if (LAST) {
+    cx<T> u[16];
+#pragma unroll
+    for (int b = 0; b < B; ++b)
+#pragma unroll
+      for (int r = 0; r < R; ++r) u[b + r * B] = v[b * R + r];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = u[i];
+  }
+}
+// One stage on two lines at once (same t, separate line buffers): one pair of
+// barriers serves both, and each thread carries two independent butterfly chains.
+template <typename T, int N, int R, int NS, bool INV, bool FIRST, bool LAST, bool TWM>
+__device__ __forceinline__ void fft_stage2(cx<T> (&va)[16], cx<T> (&vb)[16], cx<T>* la, cx<T>* lb, int t,
+                                           const cx<T>* __restrict__ tw) {
+  constexpr int TPL = N / 16, B = 16 / R, NB = N / R;
+  if (!FIRST) {
+#pragma unroll
+    for (int b = 0; b < B; ++b)
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        va[b * R + r] = la[padi(t + b * TPL + r * NB)];
+        vb[b * R + r] = lb[padi(t + b * TPL + r * NB)];
+      }
+  }
+  fft_stage_regs<T, N, R, NS, INV, LAST, TWM>(va, t, tw);
+  fft_stage_regs<T, N, R, NS, INV, LAST, TWM>(vb, t, tw);
+  if (!LAST) {
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int j = t + b * TPL;
+      const int k = j & (NS - 1);
+      const int base = (j - k) * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        la[padi(base + r * NS)] = va[b * R + r];
+        lb[padi(base + r * NS)] = vb[b * R + r];
+      }
+    }
+    __syncthreads();
+  }
+}
+// fft_line on two lines in lockstep.
+template <typename T, int LOGN, bool INV, bool TWM = false>
+__device__ __forceinline__ void fft_line2(cx<T> (&va)[16], cx<T> (&vb)[16], cx<T>* la, cx<T>* lb, int t,
+                                          const cx<T>* __restrict__ tw) {
+  constexpr int N = 1 << LOGN;
+  constexpr int L1 = LOGN - 4;
+  if constexpr (L1 <= 4) {
+    fft_stage2<T, N, 16, 1, INV, true, false, TWM>(va, vb, la, lb, t, tw);
+    fft_stage2<T, N, (1 << L1), 16, INV, false, true, TWM>(va, vb, la, lb, t, tw);
+  } else {
+    fft_stage2<T, N, 16, 1, INV, true, false, TWM>(va, vb, la, lb, t, tw);
+    fft_stage2<T, N, 16, 16, INV, false, false, TWM>(va, vb, la, lb, t, tw);
+    fft_stage2<T, N, (1 << (L1 - 4)), 256, INV, false, true, TWM>(va, vb, la, lb, t, tw);
+  }
+}
+
 // Block shapes (shared by the kernels and the host launchers).
 //  rows:    LINES lines of TPL = N/16 consecutive threads, 256 threads at most.
 //  columns: COLS columns; a warp covers CW neighbouring columns x 32/CW

@@ -44,6 +44,15 @@ cudaError_t launch_pass_b(const PassArgs<T>& a, int nslots, cudaStream_t s) {
       }
       return cudaErrorInvalidValue;
     }
+    if (a.colv == 2) {
+      switch (a.g.logN) {
+#define CASE(L) \
+  case L: return launch_pass_b_n<T, L, MODE, 2>(a, nslots, s);
+        DBAR_SIZES(CASE)
+#undef CASE
+      }
+      return cudaErrorInvalidValue;
+    }
   }
   switch (a.g.logN) {
 #define CASE(L) \

@@ -41,6 +41,14 @@ cudaError_t launch_pass_a_n(const PassArgs<T>& a, int nslots, cudaStream_t s) {
 
 template <typename T, int LOGN, int MODE, int CV>
 cudaError_t launch_pass_b_n(const PassArgs<T>& a, int nslots, cudaStream_t s) {
+  if constexpr (CV == 2) {  // two slots per block (operator mode)
+    using G = ColG<T, LOGN, 0>;
+    const size_t sm = align16((size_t)2 * G::COLS * G::P * sizeof(cx<T>)) + (size_t)2 * (a.M + 2) * sizeof(cx<T>);
+    cudaError_t e = set_smem(k_pass_b2<T, LOGN>, sm);
+    if (e != cudaSuccess) return e;
+    k_pass_b2<T, LOGN><<<dim3((nslots + 1) / 2, G::N / G::COLS), G::THREADS, sm, s>>>(a, nslots);
+    return cudaGetLastError();
+  }
   using G = ColG<T, LOGN, CV>;
   const size_t sm = align16((size_t)G::COLS * G::P * sizeof(cx<T>)) + (size_t)(a.M + 2) * sizeof(cx<T>);
   cudaError_t e = set_smem(k_pass_b<T, LOGN, MODE, CV>, sm);
@@ -92,6 +100,7 @@ template cudaError_t launch_pass_c_n<TT, TT, DBAR_LOGN, PC_FWD>(const PassArgs<T
 template cudaError_t launch_pass_c_n<TT, TT, DBAR_LOGN, PC_INV>(const PassArgs<TT>&, int, cudaStream_t);
 #if DBAR_KIND == 0
 template cudaError_t launch_pass_b_n<float, DBAR_LOGN, PB_MATVEC, 1>(const PassArgs<float>&, int, cudaStream_t);
+template cudaError_t launch_pass_b_n<float, DBAR_LOGN, PB_MATVEC, 2>(const PassArgs<float>&, int, cudaStream_t);
 #endif
 template cudaError_t launch_pass_ca_n<TT, DBAR_LOGN>(const PassArgs<TT>&, int, cudaStream_t);
 #if DBAR_KIND == 1

@@ -303,6 +303,93 @@ __global__ void __launch_bounds__(ColG<T, LOGN, CV>::THREADS, ColG<T, LOGN, CV>:
 }
 
 // ---------------------------------------------------------------------------
+// Pass B, operator mode, two slots per block: slots 2b and 2b+1 on the same
+// column tile (the Q / Delta_n tiles are read once for both), their transforms
+// in lockstep.  Same arithmetic per element as k_pass_b<T, LOGN, PB_MATVEC, 0>.
+// ---------------------------------------------------------------------------
+template <typename T, int LOGN>
+__global__ void __launch_bounds__(ColG<T, LOGN, 0>::THREADS, 1) k_pass_b2(const PassArgs<T> a, int nslots) {
+  using G = ColG<T, LOGN, 0>;
+  constexpr int N = G::N, TPL = G::TPL, P = G::P;
+  constexpr bool TWM = std::is_same<T, float>::value;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int s0 = 2 * blockIdx.x, s1 = s0 + 1 < nslots ? s0 + 1 : s0;
+  const bool r0 = !a.run || a.run[s0];
+  const bool r1 = s1 != s0 && (!a.run || a.run[s1]);
+  if (!r0 && !r1) return;
+  const int M = a.M;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = (warp / G::WPG) * G::CW + lane % G::CW;
+  const int t = (warp % G::WPG) * G::TW + lane / G::CW;
+  const int j1 = blockIdx.y * G::COLS + c;
+  cx<T>* la = reinterpret_cast<cx<T>*>(smem) + c * P;
+  cx<T>* lb = la + G::COLS * P;
+  constexpr size_t off = ((size_t)2 * G::COLS * P * sizeof(cx<T>) + 15) & ~(size_t)15;
+  cx<T>* coef = reinterpret_cast<cx<T>*>(smem + off);  // [2][M+2]
+
+  cx<T> va[16], vb[16];
+  {
+    const cx<T>* sa = a.in + (size_t)s0 * a.in_ss + (size_t)t * N + j1;
+    const cx<T>* sb = a.in + (size_t)s1 * a.in_ss + (size_t)t * N + j1;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      va[q] = ldg(sa + (size_t)q * TPL * N);
+      vb[q] = ldg(sb + (size_t)q * TPL * N);
+    }
+  }
+  if (threadIdx.x < 2 * (M + 2)) {
+    const int h = threadIdx.x >= M + 2, i = threadIdx.x - h * (M + 2);
+    coef[threadIdx.x] = ccast<T>(a.coef[(size_t)(h ? s1 : s0) * (M + 2) + i]);
+  }
+  fft_line2<T, LOGN, true, TWM>(va, vb, la, lb, t, a.tw);
+  __syncthreads();  // coefficients visible
+  {
+    const cx<T> fa = coef[M + 1], fb = coef[2 * M + 3];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      va[q] = va[q] + fa;
+      vb[q] = vb[q] + fb;
+    }
+  }
+  for (int n = 0; n <= M; ++n) {
+    const cx<T> ca = coef[n], cb = coef[M + 2 + n];
+    const cx<T>* D = a.Delta + ((size_t)n * N + t) * N + j1;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const cx<T> d = ldg(D + (size_t)q * TPL * N);
+      va[q] = va[q] + cmul(ca, d);
+      vb[q] = vb[q] + cmul(cb, d);
+    }
+  }
+  {
+    const cx<T> xa = cscale(ldg(a.ex + (size_t)s0 * N + j1), (T)a.sw);
+    const cx<T> xb = cscale(ldg(a.ex + (size_t)s1 * N + j1), (T)a.sw);
+    const cx<T>* EA = a.ey + (size_t)s0 * N + t;
+    const cx<T>* EB = a.ey + (size_t)s1 * N + t;
+    const cx<T>* QA = a.Q + (size_t)s0 * a.q_ss + (size_t)t * N + j1;
+    const cx<T>* QB = a.Q + (size_t)s1 * a.q_ss + (size_t)t * N + j1;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const cx<T> qa = ldg(QA + (size_t)q * TPL * N);
+      const cx<T> qb = a.q_ss ? ldg(QB + (size_t)q * TPL * N) : qa;
+      va[q] = cmulc(cmul(cmul(xa, ldg(EA + q * TPL)), qa), va[q]);
+      vb[q] = cmulc(cmul(cmul(xb, ldg(EB + q * TPL)), qb), vb[q]);
+    }
+  }
+  fft_line2<T, LOGN, false, TWM>(va, vb, la, lb, t, a.tw);
+  cx<T>* da = reinterpret_cast<cx<T>*>(a.out) + (size_t)s0 * a.out_ss + (size_t)t * N + j1;
+  cx<T>* db = reinterpret_cast<cx<T>*>(a.out) + (size_t)s1 * a.out_ss + (size_t)t * N + j1;
+  if (r0) {
+#pragma unroll
+    for (int q = 0; q < 16; ++q) da[(size_t)q * TPL * N] = va[q];
+  }
+  if (r1) {
+#pragma unroll
+    for (int q = 0; q < 16; ++q) db[(size_t)q * TPL * N] = vb[q];
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Taylor coefficients of each slot from pass A's row-moment partials, in a
 // fixed order.  Row p2 contributes (-1)^{p2} times
 //   n <= M:  sum_a C(n,a) i^{n-a} D_{n-a}(p2) R_a(p2)      (c_n, Sec. 4.3 step 4a)

@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <cmath>
 #include <complex>
+#include <array>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -147,7 +148,7 @@ struct dbar_plan {
   CycleGraph graphs[2];                 // one per batch size in use (full and ragged)
   int per_slot_q = 0;   // 1: every slot has its own potential (serving); 0: one Q for all
   int colv = 0;         // FP32 column-pass tile variant (autotuned)
-  double tune_ms[2] = {0.0, 0.0};
+  double tune_ms[DBAR_COLUMN_VARIANTS] = {0.0, 0.0, 0.0};
   int* dmask = nullptr;  // [B] device copy of a slot mask
   int* hmask = nullptr;  // [B] pinned host staging of it
   long long nlaunch = 0;  // kernels launched by this plan
@@ -1109,7 +1110,7 @@ static dbar_status check_params(const dbar_params* p) {
   if (p->prec == DBAR_MIXED && !(p->inner_tol > 0.0 && p->inner_tol < 1.0))
     return fail(DBAR_EINVAL, "inner_tol must be in (0, 1)");
   if (p->max_batch < 0 || p->max_batch > 65535) return fail(DBAR_EINVAL, "max_batch must be in [0, 65535]");
-  if (p->autotune < 0 || p->autotune > 2) return fail(DBAR_EINVAL, "autotune must be 0, 1 or 2");
+  if (p->autotune < 0 || p->autotune > 3) return fail(DBAR_EINVAL, "autotune must be 0, 1, 2 or 3");
   if (p->resid_mode != DBAR_RESID_DOUBLE_FLOAT && p->resid_mode != DBAR_RESID_FP64)
     return fail(DBAR_EINVAL, "resid_mode must be DBAR_RESID_DOUBLE_FLOAT or DBAR_RESID_FP64");
   if (p->sstep != 0 && p->sstep != 1 && p->sstep != 2 && p->sstep != 4)
@@ -1282,7 +1283,7 @@ static dbar_status plan_tables(dbar_plan* P) {
 // bit-identical across variants (same arithmetic per column), so the choice
 // only affects speed; it is cached per (device, N, M) for the process.
 static std::mutex g_tune_mu;
-static std::map<std::tuple<int, int, int>, std::pair<int, std::pair<double, double>>> g_tune_cache;
+static std::map<std::tuple<int, int, int>, std::pair<int, std::array<double, DBAR_COLUMN_VARIANTS>>> g_tune_cache;
 
 static dbar_status autotune_columns(dbar_plan* P) {
   const auto key = std::make_tuple(P->device, P->N, P->Min);
@@ -1291,8 +1292,7 @@ static dbar_status autotune_columns(dbar_plan* P) {
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) {
       P->colv = it->second.first;
-      P->tune_ms[0] = it->second.second.first;
-      P->tune_ms[1] = it->second.second.second;
+      for (int v = 0; v < DBAR_COLUMN_VARIANTS; ++v) P->tune_ms[v] = it->second.second[v];
       return DBAR_OK;
     }
   }
@@ -1309,7 +1309,7 @@ static dbar_status autotune_columns(dbar_plan* P) {
   CK(cudaEventCreate(&e1));
   double best = 1e300;
   int choice = 0;
-  for (int cv = 0; cv < 2; ++cv) {
+  for (int cv = 0; cv < DBAR_COLUMN_VARIANTS; ++cv) {
     PassArgs<float> a = base_args<float>(P);
     a.colv = cv;
     a.in = reinterpret_cast<const cx<float>*>(P->T1);
@@ -1334,7 +1334,9 @@ static dbar_status autotune_columns(dbar_plan* P) {
   cudaEventDestroy(e1);
   P->colv = choice;
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_tune_cache[key] = {choice, {P->tune_ms[0], P->tune_ms[1]}};
+  std::array<double, DBAR_COLUMN_VARIANTS> t;
+  for (int v = 0; v < DBAR_COLUMN_VARIANTS; ++v) t[v] = P->tune_ms[v];
+  g_tune_cache[key] = {choice, t};
   return DBAR_OK;
 }
 
@@ -1540,6 +1542,7 @@ dbar_status plan_create_ex(const dbar_params* p, int per_slot_q, dbar_plan** out
   s = plan_tables(P);
   if (s == DBAR_OK && P->mixed && p->autotune == 1) s = autotune_columns(P);
   if (P->mixed && p->autotune == 2) P->colv = 1;  // fixed second variant (tests)
+  if (P->mixed && p->autotune == 3) P->colv = 2;  // fixed third variant (tests)
   if (s != DBAR_OK) {
     delete P;
     return s;
@@ -2113,12 +2116,11 @@ extern "C" dbar_status dbar_profile_read(dbar_plan_t P, int kind, double* ms, lo
   return DBAR_OK;
 }
 
-extern "C" dbar_status dbar_plan_tuning(dbar_plan_t P, int* column_variant, double* ms_variant0,
-                                        double* ms_variant1) {
+extern "C" dbar_status dbar_plan_tuning(dbar_plan_t P, int* column_variant, double* ms_per_variant) {
   if (!P) return fail(DBAR_EINVAL, "plan is NULL");
   if (column_variant) *column_variant = P->colv;
-  if (ms_variant0) *ms_variant0 = P->tune_ms[0];
-  if (ms_variant1) *ms_variant1 = P->tune_ms[1];
+  if (ms_per_variant)
+    for (int v = 0; v < DBAR_COLUMN_VARIANTS; ++v) ms_per_variant[v] = P->tune_ms[v];
   return DBAR_OK;
 }
 

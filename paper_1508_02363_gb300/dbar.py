@@ -82,7 +82,7 @@ _lib.dbar_profile_kind_name.restype = ctypes.c_char_p
 _lib.dbar_profile.argtypes = [_vp, _int]
 _lib.dbar_profile_read.argtypes = [_vp, _int, _dp, ctypes.POINTER(ctypes.c_longlong), _dp]
 _lib.dbar_launch_count.argtypes = [_vp, ctypes.POINTER(ctypes.c_longlong)]
-_lib.dbar_plan_tuning.argtypes = [_vp, _ip, _dp, _dp]
+_lib.dbar_plan_tuning.argtypes = [_vp, _ip, _dp]
 _u64 = ctypes.c_uint64
 _lib.dbar_serve_create.argtypes = [ctypes.POINTER(dbar_params), ctypes.c_size_t, ctypes.POINTER(_vp)]
 _lib.dbar_serve_submit.argtypes = [_vp, ctypes.POINTER(dbar_request), ctypes.POINTER(_u64)]
@@ -276,11 +276,14 @@ def dbar_profile_read(plan, kind: int):
     return ms.value, n.value, by.value
 
 
+COLUMN_VARIANTS = 3
+
+
 def dbar_plan_tuning(plan):
-    """(column-pass tile variant in use, ms per launch of variant 0, of variant 1)."""
-    v, a, b = ctypes.c_int(), ctypes.c_double(), ctypes.c_double()
-    _check(_lib.dbar_plan_tuning(plan, ctypes.byref(v), ctypes.byref(a), ctypes.byref(b)))
-    return v.value, a.value, b.value
+    """(column-pass tile variant in use, [ms per launch of each variant])."""
+    v, ms = ctypes.c_int(), (ctypes.c_double * COLUMN_VARIANTS)()
+    _check(_lib.dbar_plan_tuning(plan, ctypes.byref(v), ms))
+    return v.value, list(ms)
 
 
 def dbar_launch_count(plan) -> int:

@@ -293,13 +293,18 @@ def test_graph_replayed_cycles_match_direct_launches(dbar, prec, sstep):
 
 
 def test_autotuned_column_tiles_give_identical_results(dbar):
-    # both compiled tile shapes of the FP32 column pass compute the same numbers
+    # every compiled tile shape of the FP32 column pass computes the same numbers
+    # (an odd batch: the two-slot variant's last block holds one k)
     w = wl.mixed_1024(N=256, nk=3, L=6.0)
     res = []
-    for autotune in (0, 2, 1):
+    for autotune, variant in ((0, 0), (2, 1), (3, 2), (1, None)):
         plan = dbar.Plan(w.N, w.L, M=2, prec="mixed", restart=24, tol=1e-12, max_batch=3, autotune=autotune)
         res.append(plan.solve(w.Q, w.k, want_m=False))
-        if autotune == 2:
-            assert dbar.dbar_plan_tuning(plan.handle)[0] == 1
-    assert np.array_equal(res[0]["S"], res[1]["S"]) and np.array_equal(res[0]["S"], res[2]["S"])
+        v, ms = dbar.dbar_plan_tuning(plan.handle)
+        if variant is not None:
+            assert v == variant
+        else:
+            assert v in (0, 1, 2) and len(ms) == dbar.COLUMN_VARIANTS and min(ms) > 0
+    for r in res[1:]:
+        assert np.array_equal(res[0]["S"], r["S"])
     assert res[0]["status"] == dbar.DBAR_OK
