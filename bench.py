@@ -837,7 +837,7 @@ def main():
     ap.add_argument("--seed", type=int, default=5)
     ap.add_argument("--nreq", type=int, default=1000, help="uneven: number of solves")
     ap.add_argument("--autotune", type=int, default=1,
-                    help="column-pass tiles: 1 timed at plan creation (default), 0 or 2 pin variant 0 or 1")
+                    help="column-pass tiles: 1 timed at plan creation (default); 0, 2 or 3 pin variant 0, 1 or 2")
     ap.add_argument("--quick", action="store_true",
                     help="time the solve only (no FP64 comparison, end-to-end leg or CPU baseline)")
     args = ap.parse_args()
