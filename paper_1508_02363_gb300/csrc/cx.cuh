@@ -243,23 +243,11 @@ __device__ __forceinline__ void dft_reg(cx<T>* v) {
 __device__ __forceinline__ int padi(int i) { return i + (i >> 4); }
 __host__ __device__ constexpr int pitch_of(int N) { return N + (N >> 4) + 2; }
 
-// One Stockham stage of radix R on a line of length N held by TPL = N/16
-// threads; each thread owns 16 elements, i.e. 16/R butterflies j = t + b TPL.
-// Inputs x[j + r N/R] (already in registers in the first stage: v[r] =
-// x[t + r TPL]), twiddle w^{r (j mod NS)} with w = e^{-+2 pi i/(NS R)} read
-// from the table tw[s] = e^{-2 pi i s/N}, R-point DFT, outputs at
-// ((j - j mod NS) R + j mod NS) + r NS.  The last stage (NS R = N) keeps its
-// outputs in registers: v[q] = X[t + q TPL].
-template <typename T, int N, int R, int NS, bool INV, bool FIRST, bool LAST, bool TWM>
-__device__ __forceinline__ void fft_stage(cx<T> (&v)[16], cx<T>* line, int t, const cx<T>* __restrict__ tw) {
-  constexpr int TPL = N / 16, B = 16 / R, NB = N / R;
-  static_assert(!FIRST || R == 16, "the first stage is radix 16");
-  if (!FIRST) {
-#pragma unroll
-    for (int b = 0; b < B; ++b)
-#pragma unroll
-      for (int r = 0; r < R; ++r) v[b * R + r] = line[padi(t + b * TPL + r * NB)];
-  }
+// Register part of one Stockham stage (see fft_stage): twiddles, the R-point
+// DFTs and, in the last stage, the reordering to v[q] = X[t + q TPL].
+template <typename T, int N, int R, int NS, bool INV, bool LAST, bool TWM>
+__device__ __forceinline__ void fft_stage_regs(cx<T> (&v)[16], int t, const cx<T>* __restrict__ tw) {
+  constexpr int TPL = N / 16, B = 16 / R;
 #pragma unroll
   for (int b = 0; b < B; ++b) {
     if (NS > 1) {
@@ -267,7 +255,7 @@ __device__ __forceinline__ void fft_stage(cx<T> (&v)[16], cx<T>* line, int t, co
       const int k = (t + b * TPL) & (NS - 1);
       if constexpr (TWM) {
         // load w^r for r a power of two, form the rest as products (at most
-        // three roundings deep): fewer L1 loads in the FP32 row passes
+        // three roundings deep): fewer L1 loads in the FP32 passes
         cx<T> wr[R];
 #pragma unroll
         for (int r = 1; r < R; ++r) {
@@ -296,7 +284,6 @@ __device__ __forceinline__ void fft_stage(cx<T> (&v)[16], cx<T>* line, int t, co
     dft_reg<T, R, INV>(&v[b * R]);
   }
   if (LAST) {
-    static_assert(!LAST || NS * R == N, "the last stage completes the transform");
     cx<T> u[16];
 #pragma unroll
     for (int b = 0; b < B; ++b)
@@ -304,7 +291,28 @@ __device__ __forceinline__ void fft_stage(cx<T> (&v)[16], cx<T>* line, int t, co
       for (int r = 0; r < R; ++r) u[b + r * B] = v[b * R + r];
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = u[i];
-  } else {
+  }
+}
+// One Stockham stage of radix R on a line of length N held by TPL = N/16
+// threads; each thread owns 16 elements, i.e. 16/R butterflies j = t + b TPL.
+// Inputs x[j + r N/R] (already in registers in the first stage: v[r] =
+// x[t + r TPL]), twiddle w^{r (j mod NS)} with w = e^{-+2 pi i/(NS R)} read
+// from the table tw[s] = e^{-2 pi i s/N}, R-point DFT, outputs at
+// ((j - j mod NS) R + j mod NS) + r NS.  The last stage (NS R = N) keeps its
+// outputs in registers: v[q] = X[t + q TPL].
+template <typename T, int N, int R, int NS, bool INV, bool FIRST, bool LAST, bool TWM>
+__device__ __forceinline__ void fft_stage(cx<T> (&v)[16], cx<T>* line, int t, const cx<T>* __restrict__ tw) {
+  constexpr int TPL = N / 16, B = 16 / R, NB = N / R;
+  static_assert(!FIRST || R == 16, "the first stage is radix 16");
+  static_assert(!LAST || NS * R == N, "the last stage completes the transform");
+  if (!FIRST) {
+#pragma unroll
+    for (int b = 0; b < B; ++b)
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[b * R + r] = line[padi(t + b * TPL + r * NB)];
+  }
+  fft_stage_regs<T, N, R, NS, INV, LAST, TWM>(v, t, tw);
+  if (!LAST) {
     __syncthreads();  // every thread has read the inputs of this stage
 #pragma unroll
     for (int b = 0; b < B; ++b) {
@@ -340,54 +348,6 @@ __device__ __forceinline__ void fft_line(cx<T> (&v)[16], cx<T>* line, int t, con
   }
 }
 
-// Register part of one Stockham stage (twiddles, R-point DFTs, and the last
-// stage's reordering), as in fft_stage.
-template <typename T, int N, int R, int NS, bool INV, bool LAST, bool TWM>
-__device__ __forceinline__ void fft_stage_regs(cx<T> (&v)[16], int t, const cx<T>* __restrict__ tw) {
-  constexpr int TPL = N / 16, B = 16 / R;
-#pragma unroll
-  for (int b = 0; b < B; ++b) {
-    if (NS > 1) {
-      constexpr int STEP = N / (NS * R);
-      const int k = (t + b * TPL) & (NS - 1);
-      if constexpr (TWM) {
-        cx<T> wr[R];
-#pragma unroll
-        for (int r = 1; r < R; ++r) {
-          if ((r & (r - 1)) == 0) {
-            wr[r] = ldg(tw + r * k * STEP);
-          } else {
-            const int hb = 1 << (31 - __clz(r));
-            wr[r] = cmul(wr[hb], wr[r - hb]);
-          }
-        }
-#pragma unroll
-        for (int r = 1; r < R; ++r) {
-          cx<T> w = wr[r];
-          if (INV) w.im = -w.im;
-          v[b * R + r] = cmul(v[b * R + r], w);
-        }
-      } else {
-#pragma unroll
-        for (int r = 1; r < R; ++r) {
-          cx<T> w = ldg(tw + r * k * STEP);
-          if (INV) w.im = -w.im;
-          v[b * R + r] = cmul(v[b * R + r], w);
-        }
-      }
-    }
-    dft_reg<T, R, INV>(&v[b * R]);
-  }
-  if (LAST) {
-    cx<T> u[16];
-#pragma unroll
-    for (int b = 0; b < B; ++b)
-#pragma unroll
-      for (int r = 0; r < R; ++r) u[b + r * B] = v[b * R + r];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = u[i];
-  }
-}
 // One stage on two lines at once (same t, separate line buffers): one pair of
 // barriers serves both, and each thread carries two independent butterfly chains.
 template <typename T, int N, int R, int NS, bool INV, bool FIRST, bool LAST, bool TWM>
