@@ -259,9 +259,10 @@ dbar_status dbar_fft2(dbar_plan_t plan, int nk, const void* in, void* out, int s
                       void* stream);
 
 /* Allocation-free variant of dbar_fft2, for callers that cannot allocate
- * device memory when they need a transform: code running while a CUDA graph
- * is being captured, plugins whose host runtime owns all device memory
- * through its own pool, latency-critical loops that forbid allocator calls.
+ * device memory when they need a transform: plugins whose host runtime owns
+ * all device memory through its own pool (a cudaMalloc would bypass its
+ * accounting or fail against its reservation), and latency-critical loops
+ * that forbid allocator calls (cudaMalloc/cudaFree may synchronise the device).
  * (The paper has no counterpart: this is an interface for such callers.)
  * It needs no plan.  Its intermediate field and twiddle tables live in the
  * library's own global arrays: every GPU that loads the library keeps 16 MiB
@@ -270,9 +271,12 @@ dbar_status dbar_fft2(dbar_plan_t plan, int nk, const void* in, void* out, int s
  * call); larger calls return DBAR_EINVAL.  N is a power of two in [32, 2048].
  * All calls share the scratch, so calls that overlap on the GPU race.  The
  * first call on a device uploads the twiddle tables and looks up the arrays'
- * device addresses, so make it before any stream capture.  in and out are
+ * device addresses with that device current.  in and out are
  * device pointers ([nk][N][N], complex128, or complex64 when fp32 = 1) and may
- * be equal; sign as in dbar_fft2.  Returns after the stream has drained. */
+ * be equal; sign as in dbar_fft2.  Returns after the stream has drained
+ * (the call ends with a synchronisation of `stream`).
+ * Errors: DBAR_EINVAL (N, nk, sign, NULL pointers, size beyond the scratch),
+ * DBAR_ECUDA. */
 dbar_status dbar_fft2_noalloc(int N, int nk, const void* in, void* out, int sign, int fp32, void* stream);
 
 /* --- serving: continuous batching ------------------------------------- */

@@ -1,9 +1,11 @@
 // Allocation-free 2-D DFT: dbar_fft2_noalloc.
 //
 // Some callers cannot allocate device memory at the point where they need a
-// transform: code running while a CUDA graph is being captured, kernels-only
-// plugins whose host runtime owns every byte of device memory through its
-// own pool, and latency-critical loops that forbid allocator calls.  For them
+// transform: kernels-only plugins whose host runtime owns every byte of device
+// memory through its own pool (a cudaMalloc there would bypass the pool's
+// accounting or fail against its reservation), and latency-critical loops
+// that forbid allocator calls (cudaMalloc/cudaFree can synchronise the device
+// and take milliseconds).  For them
 // this entry point runs the same row and column transform kernels as
 // dbar_fft2, but keeps its intermediate field and its twiddle tables in
 // global arrays that belong to the library image itself, so a call allocates
@@ -15,8 +17,10 @@
 //  * All calls share the one scratch array: calls that overlap on the GPU
 //    (different host threads, or different streams without ordering) race.
 //  * The first call on a device copies the twiddle tables there and looks up
-//    the arrays' device addresses (cudaMemcpyToSymbol, cudaGetSymbolAddress);
-//    make that first call before any stream capture.
+//    the arrays' device addresses (cudaMemcpyToSymbol, cudaGetSymbolAddress)
+//    with that device current.
+//  * Each call returns after the caller's stream has drained (it ends with a
+//    cudaStreamSynchronize, like the library's other entry points).
 #include <cuda_runtime.h>
 
 #include <cmath>
