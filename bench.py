@@ -185,7 +185,7 @@ def _oracle_solve(args):
     N, L, M, tol, Q, k = args
     from oracle import dbar_oracle as orc
     r = orc.solve_cgo(Q, k, N, L, M=M, tol=tol, restart=40)
-    return r["iters"], r["resid"]
+    return r["iters"], r["resid"], r["S"]
 
 
 def cpu_oracle_step(w, ks, cores):
@@ -306,6 +306,30 @@ def run_ours(args):
     torch.cuda.synchronize()
     fp64_single_rate = nrep / (e0.elapsed_time(e1) / 1e3)
 
+    # the same workload with the refinement's residual and right-hand side in native FP64
+    # (resid_mode = fp64) instead of double-float: its rate, and its solutions for the
+    # oracle comparison below
+    S64r = None
+    if w.mixed and not args.no_fp64_resid:
+        pr = dbar.Plan(N, w.L, M=w.M, prec="mixed", tol=w.tol, restart=args.restart, inner_tol=args.inner_tol,
+                       max_batch=nk, max_outer=args.max_outer, sstep=args.sstep, autotune=args.autotune,
+                       resid_mode="fp64")
+        S64r = torch.empty_like(Sd)
+        pr.solve_device(Qd, w.k, S64r, stream=stream)   # warm
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        nrep_r = 2
+        for _ in range(nrep_r):
+            r64r = pr.solve_device(Qd, w.k, S64r, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fp64_resid = {"solves_per_s": round(nrep_r * nk / (e0.elapsed_time(e1) / 1e3), 3),
+                      "resid_max": float(np.max(r64r["resid"])),
+                      "iters_inner_mean": float(np.mean(r64r["iters"][:, 0]))}
+        pr.close()
+        del pr
+
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     Qh = torch.from_numpy(w.Q).pin_memory()
     Sh = torch.empty((nk, N, N), dtype=torch.complex128).pin_memory()
@@ -345,7 +369,10 @@ def run_ours(args):
 
     out = {"metric": METRIC, "value": round(value, 3), "unit": "solves/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if w.mixed else "f64",
+           "scaling": "weak", "vs_baseline": None,
+           # mixed: FP32 inner GMRES; right-hand side, true residual, x and b in double-float
+           # (float pairs, ~48-bit significand); read-out to FP64
+           "dtype": "f32+df32x2" if w.mixed else "f64",
            "data": "synthetic (seeded Gaussian-mixture potential and k list)",
            "config": {"workload": w.name, "N": N, "L": w.L, "nk": nk, "M": w.M, "tol": w.tol,
                       "prec": "mixed" if w.mixed else "fp64", "restart": args.restart, "sstep": args.sstep,
@@ -353,23 +380,47 @@ def run_ours(args):
                       "column_variant": colv, "column_tune_ms": [round(x, 4) for x in tune],
                       "parallelism": f"replicas over k x{world}",
                       "l2": "inputs larger than L2 (device working set %.1f GB)" % (plan.device_bytes / 1e9)},
-           "p50_ms": round(statistics.median(step_ms), 3),
-           "p99_ms": round(float(np.percentile(step_ms, 99)), 3),
+           "step_p50_ms": round(statistics.median(step_ms), 3),
+           "step_p99_ms": round(float(np.percentile(step_ms, 99)), 3),
            "iters_inner_mean": float(np.mean(iters[:, 0])), "cycles_max": int(np.max(iters[:, 1])),
            "resid_max": float(np.max(resid)), "err_vs_fp64_max": float(max(errs)),
            "err_vs_fp64_sampled_k": [int(i) for i in sample],
            "fp64_plain_single_k_solves_per_s": round(fp64_single_rate, 3),
+           "fp64_plain_single_k_latency_ms": round(1e3 / fp64_single_rate, 3),
            "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline, "clocks": clk.summary()}
 
+    if w.mixed and S64r is not None:
+        out["fp64_resid"] = fp64_resid
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = cpu_cores()
         ncpu = min(cores, args.cpu_sample)
-        ks = w.k[np.linspace(0, nk - 1, ncpu).astype(int)]
+        idx = np.linspace(0, nk - 1, ncpu).astype(int)
+        ks = w.k[idx]
         dt, res = cpu_oracle_step(w, ks, cores)
         out["cpu_baseline"] = {"value": round(len(ks) / dt, 4), "unit": "solves/s", "cores": min(cores, len(ks)),
                                "kind": "oracle",
                                "sample": f"{len(ks)} of the {nk} k values solved once each by the FP64 CPU "
                                          f"oracle, one process per core, wall {dt:.1f} s"}
+        # the headline's accuracy: the timed solutions against the oracle's, element by element
+        def err_vs(Sx):
+            return float(max(np.max(np.abs(Sx[i].cpu().numpy() - So)) / np.max(np.abs(So))
+                             for i, (_, _, So) in zip(idx, res)))
+        out["err_vs_oracle_max"] = err_vs(Sd)
+        out["err_vs_oracle_sampled_k"] = [int(i) for i in idx]
+        if S64r is not None:
+            out["fp64_resid"]["err_vs_oracle_max"] = err_vs(S64r)
+    if rank == 0 and world == 1 and not args.no_serving and args.workload == "mixed_1024":
+        # request-level latency under continuous batching (the metric's p50/p99), with the
+        # plain single-k FP64 solve's latency beside it
+        plan.close()
+        p64.close()
+        p1.close()
+        del Sd, S64, S1, Sh, Qh, S64r
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        sv = serving_leg(args, dbar, torch, local)
+        out["serving"] = sv
+        out["p50_ms"], out["p99_ms"] = sv["p50_ms"], sv["p99_ms"]
     if rank == 0:
         print(json.dumps(out))
     if dist is not None:
@@ -701,74 +752,148 @@ def run_conv(args):
 
 # ----------------------------------------------------------------------------- serving workload
 
-def run_serving(args):
+def _oracle_serving(args):
+    N, L, mixture, k = args
+    import workloads as wl
+    from oracle import dbar_oracle as orc
+    r = orc.solve_cgo(wl.gaussian_mixture(N, L, *mixture), k, N, L, M=2, tol=1e-13, restart=40)
+    return r["S"]
+
+
+def serving_leg(args, dbar, torch, clock_gpu=0):
     """Poisson arrivals of CGO requests into the continuous-batching server.
 
-    Each request: N drawn uniformly from {256, 512, 1024, 2048}, raised to the
-    smallest size that resolves its k (N/(2L) >= 2 max(|k1|,|k2|) + XI_Q), L = 6,
-    |k| log-uniform in [0.1, 20], Q a Gaussian mixture of 1-6 terms.  Potentials
-    come from a pool of POOL seeded mixtures per N (generating a fresh 2048^2
-    field per request on the host would outpace the GPU); k is drawn per request.
-    """
+    Request i is drawn from default_rng(seed + i) (workloads.serving_request): N uniform
+    over {256, 512, 1024, 2048}, raised to the smallest size that resolves its k
+    (N/(2L) >= 2 max(|k1|,|k2|) + 20, L = 6); its own Gaussian mixture of 1-6 terms;
+    |k| log-uniform in [0.1, 20].  Each potential is generated on the host just ahead of
+    its arrival by a thread pool (one matrix product of separable factors), submitted at
+    its arrival time (the server copies it), and its result released as soon as it is
+    done.  Device memory is admitted by the server's budget.  2 % of the requests (every
+    50th) are checked against the plain FP64 GPU solve, and those of them with N <= 512
+    (at most `serve_oracle`) against the FP64 CPU oracle (solved in a spawned process
+    pool; larger grids take the oracle minutes per solve)."""
+    import concurrent.futures as cf
+    import workloads as wl
+
+    L, XI_Q, KMAX = 6.0, 20.0, 20.0
+    arrivals = wl.poisson_arrivals(args.rate, args.duration, seed=args.seed)
+    reqs = [wl.serving_request(i, base_seed=args.seed, L=L, kmax=KMAX, xi_q=XI_Q) for i in range(arrivals.size)]
+    sampled = set(range(0, len(reqs), 50))
+    free = torch.cuda.mem_get_info()[0]
+    srv = dbar.Server(int(free * 0.7), prec="mixed", restart=args.restart, tol=1e-12, inner_tol=args.inner_tol,
+                      max_batch=args.serve_batch)
+    gen = cf.ThreadPoolExecutor(max_workers=6)
+    futs = {}
+    LOOK = 64
+    kept_Q, kept_S, lat = {}, {}, []
+    status, resid = [], []
+    tickets = []
+    tickets_ready = threading.Condition()
+    late = [0]
+
+    def generate(i):
+        N, k, mix = reqs[i]
+        return wl.gaussian_mixture(N, L, *mix)
+
+    def collect():
+        j = 0
+        while True:
+            with tickets_ready:
+                while j >= len(tickets):
+                    tickets_ready.wait()
+                item = tickets[j]
+            if item is None:
+                return
+            i, t = item
+            r = srv.wait(t, timeout_s=600, release=True, copy=i in sampled)
+            lat.append(r["latency_ms"])
+            status.append(r["status"])
+            resid.append(r["resid"])
+            if i in sampled:
+                kept_S[i] = r["S"]
+            j += 1
+
+    collector = threading.Thread(target=collect, daemon=True)
+    collector.start()
+    for i in range(min(LOOK, len(reqs))):
+        futs[i] = gen.submit(generate, i)
+    with ClockSampler(clock_gpu) as clk:
+        t0 = time.perf_counter()
+        for i, ta in enumerate(arrivals):
+            if i + LOOK < len(reqs):
+                futs[i + LOOK] = gen.submit(generate, i + LOOK)
+            Q = futs.pop(i).result()
+            dt = ta - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            elif dt < -0.005:
+                late[0] += 1
+            N, k, _ = reqs[i]
+            t = srv.submit(N, L, Q, k)
+            if i in sampled:
+                kept_Q[i] = Q
+            with tickets_ready:
+                tickets.append((i, t))
+                tickets_ready.notify()
+        with tickets_ready:
+            tickets.append(None)
+            tickets_ready.notify()
+        collector.join()
+        wall = time.perf_counter() - t0
+    gen.shutdown()
+    st = srv.stats()
+    srv.close()
+    torch.cuda.empty_cache()
+    # checks: the oracle on the sampled requests with N <= 512 (spawned pool, CPU), while the
+    # GPU solves every sampled request with a plain FP64 plan per grid
+    orc_idx = [i for i in sorted(sampled) if reqs[i][0] <= 512][:args.serve_oracle]
+    cores = cpu_cores()
+    ctx = mp.get_context("spawn")
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ.setdefault(v, "1")
+    pool = ctx.Pool(processes=max(1, min(cores, len(orc_idx)))) if orc_idx else None
+    pending = pool.map_async(_oracle_serving, [(reqs[i][0], L, reqs[i][2], reqs[i][1]) for i in orc_idx]) \
+        if pool else None
+    plans64, err64 = {}, []
+    for i in sorted(sampled):
+        N, k, _ = reqs[i]
+        if N not in plans64:
+            plans64[N] = dbar.Plan(N, L, prec="fp64", restart=args.restart, tol=1e-13, max_batch=1)
+        ref = plans64[N].solve(kept_Q[i], [k], want_m=False)["S"][0]
+        err64.append(float(np.max(np.abs(kept_S[i] - ref)) / np.max(np.abs(ref))))
+    for p in plans64.values():
+        p.close()
+    err_orc = []
+    if pool:
+        for i, So in zip(orc_idx, pending.get()):
+            err_orc.append(float(np.max(np.abs(kept_S[i] - So)) / np.max(np.abs(So))))
+        pool.close()
+        pool.join()
+    lat = np.array(lat)
+    nmix = {str(N): int(sum(1 for r in reqs if r[0] == N)) for N in wl.SERVING_SIZES}
+    return {"rate_req_s": args.rate, "duration_s": args.duration, "requests": len(reqs),
+            "solves_per_s": round(st["solves_per_s"], 2), "wall_s": round(wall, 2),
+            "p50_ms": round(float(np.percentile(lat, 50)), 2), "p99_ms": round(float(np.percentile(lat, 99)), 2),
+            "status_ok": int(sum(s_ == dbar.DBAR_OK for s_ in status)), "resid_max": float(max(resid)),
+            "err_vs_fp64_gpu_max": float(max(err64)), "err_vs_fp64_gpu_sample": len(err64),
+            "err_vs_oracle_max": float(max(err_orc)) if err_orc else None,
+            "err_vs_oracle_sample": f"{len(err_orc)} requests with N <= 512 of the 2% sample "
+                                    f"(N of the sample: {sorted(set(reqs[i][0] for i in orc_idx))})",
+            "late_submits": late[0], "n_mix": nmix,
+            "config": {"L": L, "kmax": KMAX, "xi_q": XI_Q, "per_request_seed": f"{args.seed} + request index",
+                       "terms": "1-6 per request", "restart": args.restart, "inner_tol": args.inner_tol,
+                       "serve_batch": args.serve_batch, "budget_bytes": int(free * 0.7)},
+            "clocks": clk.summary()}
+
+
+def run_serving(args):
     import torch
     import __graft_entry__
     __graft_entry__.build()
     from paper_1508_02363_gb300 import dbar
-    import workloads as wl
-
-    L, XI_Q, POOL, KMAX = 6.0, 20.0, 8, 20.0
-    sizes = [256, 512, 1024, 2048]
-    rng = np.random.default_rng(args.seed)
-    pool = {N: [wl.mixture_request(10_000 * N + i, N, L, KMAX)[0] for i in range(POOL)] for N in sizes}
-    nreq = int(args.rate * args.duration)
-    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, size=nreq))
-    plan_reqs = []
-    for i in range(nreq):
-        N0 = int(rng.choice(sizes))
-        k = complex(np.exp(rng.uniform(np.log(0.1), np.log(KMAX))) * np.exp(1j * rng.uniform(0, 2 * np.pi)))
-        N = N0
-        while N < 2048 and N / (2 * L) < 2 * max(abs(k.real), abs(k.imag)) + XI_Q:
-            N *= 2
-        plan_reqs.append((arrivals[i], N, int(rng.integers(POOL)), k))
-    free = torch.cuda.mem_get_info()[0]
-    srv = dbar.Server(int(free * 0.7), prec="mixed", restart=args.restart, tol=1e-12, inner_tol=args.inner_tol,
-                      max_batch=args.serve_batch)
-    tickets = []
-    t0 = time.perf_counter()
-    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
-        for (ta, N, qi, k) in plan_reqs:
-            dt = ta - (time.perf_counter() - t0)
-            if dt > 0:
-                time.sleep(dt)
-            tickets.append((srv.submit(N, L, pool[N][qi], k), N, qi, k))
-        results = []
-        for t, N, qi, k in tickets:
-            results.append((srv.wait(t, timeout_s=600, release=True), N, qi, k))
-    wall = time.perf_counter() - t0
-    st = srv.stats()
-    srv.close()
-    # sampled check: 2% of the requests (at least 4) against the plain FP64 GPU solve
-    idx = np.unique(np.linspace(0, len(results) - 1, max(4, len(results) // 50)).astype(int))
-    errs = []
-    for i in idx:
-        r, N, qi, k = results[i]
-        p64 = dbar.Plan(N, L, prec="fp64", restart=args.restart, tol=1e-13, max_batch=1)
-        ref = p64.solve(pool[N][qi], [k], want_m=False)["S"][0]
-        errs.append(float(np.max(np.abs(r["S"] - ref)) / np.max(np.abs(ref))))
-        p64.close()
-    lat = np.array([r["latency_ms"] for r, *_ in results])
-    out = {"metric": "serving: CGO solves/sec and latency under Poisson arrivals", "workload": "serving",
-           "rate_req_s": args.rate, "duration_s": args.duration, "requests": len(results),
-           "solves_per_s": round(st["solves_per_s"], 2), "wall_s": round(wall, 2),
-           "p50_ms": round(float(np.percentile(lat, 50)), 2), "p99_ms": round(float(np.percentile(lat, 99)), 2),
-           "status_ok": int(sum(r["status"] == dbar.DBAR_OK for r, *_ in results)),
-           "resid_max": float(max(r["resid"] for r, *_ in results)),
-           "err_vs_fp64_max": float(max(errs)), "err_sample": len(errs),
-           "n_mix": {str(N): int(sum(1 for _, n, _, _ in tickets if n == N)) for N in sizes},
-           "config": {"L": L, "kmax": KMAX, "xi_q": XI_Q, "pool_per_N": POOL, "restart": args.restart,
-                      "inner_tol": args.inner_tol,
-                      "serve_batch": args.serve_batch, "seed": args.seed},
-           "clocks": clk.summary()}
+    out = {"metric": "serving: CGO solves/sec and latency under Poisson arrivals", "workload": "serving"}
+    out.update(serving_leg(args, dbar, torch, int(os.environ.get("LOCAL_RANK", "0"))))
     print(json.dumps(out))
 
 
@@ -834,6 +959,11 @@ def main():
     ap.add_argument("--rate", type=float, default=200.0, help="serving: requests per second")
     ap.add_argument("--duration", type=float, default=60.0, help="serving: seconds of arrivals")
     ap.add_argument("--serve-batch", dest="serve_batch", type=int, default=128, help="serving: slots per lane")
+    ap.add_argument("--serve-oracle", dest="serve_oracle", type=int, default=32,
+                    help="serving: at most this many sampled requests (N <= 512) checked against the CPU oracle")
+    ap.add_argument("--no-serving", action="store_true", help="default workload: skip the serving leg")
+    ap.add_argument("--no-fp64-resid", dest="no_fp64_resid", action="store_true",
+                    help="default workload: skip the leg with the refinement in native FP64")
     ap.add_argument("--seed", type=int, default=5)
     ap.add_argument("--nreq", type=int, default=1000, help="uneven: number of solves")
     ap.add_argument("--autotune", type=int, default=1,

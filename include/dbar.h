@@ -133,13 +133,26 @@ typedef struct {
                         the correction solves (the M = 2 and M = 11 operators
                         differ by ~1e-8 relative, below FP32 rounding) and
                         saves their table reads and moments                  */
+  double gauss_w;    /* width w of the Gaussian of G (Sec. 4.2, eq. Gchoice with
+                        e^{-|xi|^2} read as e^{-|xi|^2/w^2}); w > 0, 1 (default)
+                        is the paper's choice.  The Taylor data c_n and the fill
+                        value do not depend on w; the closed-form part becomes
+                        F^{-1}(G/xi) = sum_n c_n w^{n+1} W_n(w z) (eq. fourreg5
+                        at w z).  With DBAR_REG_CONV: G = S e^{-|xi|^2/w^2}    */
+  size_t mem_budget; /* device bytes the plan may hold once created; 0 (default)
+                        = no limit.  With max_batch = 0 the batch is the largest
+                        that fits (at most 256); a plan that cannot fit
+                        max_batch slots (or one slot) fails with DBAR_ENOMEM.
+                        Plan creation briefly takes 2(M+1) FP64 fields more
+                        for building its tables                               */
 } dbar_params;
 
 typedef struct dbar_plan* dbar_plan_t;
 
 /* Defaults for a grid: M = 2, DBAR_MIXED, restart 32, tol 1e-12,
  * inner_tol 1e-6, max_outer 40, max_iter 4000, analytic fill,
- * DBAR_RESID_DOUBLE_FLOAT, graphs on, autotune on, sstep 0 (automatic). */
+ * DBAR_RESID_DOUBLE_FLOAT, graphs on, autotune on, sstep 0 (automatic),
+ * gauss_w 1, no memory budget. */
 void dbar_params_init(dbar_params* p, int N, double L);
 
 /* Message describing the calling thread's most recent failure ("" if none). */
@@ -175,6 +188,15 @@ dbar_status dbar_plan_info(dbar_plan_t plan, size_t* device_bytes, int* max_batc
  *   Q        N*N complex (2*N*N doubles), physical layout; host or device
  *   nk       number of k values (0 is accepted and does nothing)
  *   k        2*nk doubles (Re k, Im k), host memory
+ *   x0       NULL, or nk*N*N complex: initial guess of S per k (Fourier grid;
+ *            host or device like S_out).  GMRES (Sec. 4.1) leaves the start
+ *            vector open; NULL starts from S = 0.  With x0 the first cycle
+ *            starts from the true residual b - A x0 (FP64, or double-float on
+ *            a mixed plan), tol stays relative to ||b||, and the iteration and
+ *            cycle counts restart from 0.  Resuming an interrupted batch: pass
+ *            the S_out of a call that returned DBAR_ENOCONV (e.g. capped by
+ *            max_outer) as x0.  Non-finite entries give DBAR_EINVAL.  x0 may
+ *            be the same buffer as S_out
  *   S_out    nk*N*N complex: S = xi m^ on the Fourier grid; host or device.
  *            A page-locked host S_out (cudaHostAlloc / cudaHostRegister, mapped
  *            into the device's address space) of a mixed plan is written by
@@ -183,13 +205,13 @@ dbar_status dbar_plan_info(dbar_plan_t plan, size_t* device_bytes, int* max_batc
  *            may be NULL
  *   iters    2*nk ints, host, may be NULL: (total inner iterations, cycles)
  *   resid    nk doubles, host, may be NULL: final ||b - A S||/||b|| in FP64
- *   io_on_device  1: Q, S_out, m_out are device pointers; 0: host pointers
+ *   io_on_device  1: Q, x0, S_out, m_out are device pointers; 0: host pointers
  *   stream   cudaStream_t or NULL
  * m^(1) = i S(0) (the 1/z coefficient, Sec. 6 eq:m1def) is S_out[k][0][0]*i.
  * Returns DBAR_ENOCONV when some k missed tol (outputs still written). */
 dbar_status dbar_solve_cgo(dbar_plan_t plan, const double* Q, int nk, const double* k,
-                           double* S_out, double* m_out, int* iters, double* resid,
-                           int io_on_device, void* stream);
+                           const double* x0, double* S_out, double* m_out, int* iters,
+                           double* resid, int io_on_device, void* stream);
 
 /* DS II reflection coefficient (Sec. 6.1, eq. MainEQDSpm, hpmdef, rviah,
  * m1def; time dependence eq. rt).  Sec. 6 replaces k by k/2, so for each k the

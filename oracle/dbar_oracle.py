@@ -22,6 +22,10 @@ What it computes (paper notation):
   fourreg5a): G = e^{-|xi|^2} sum_{n<=M} c_n conj(xi)^n with
   n! c_n = (-i/2)^n F(z^n F^{-1} S)(0), and
   F^{-1}(G/xi) = sum c_n W_n, W_n = F^{-1}(conj(xi)^n/xi e^{-|xi|^2}).
+  A Gaussian of width w (e^{-|xi|^2/w^2}; w = 1 is the paper's) changes only
+  G and the closed form: substituting xi = w eta in the transform gives
+  F^{-1}(conj(xi)^n/xi e^{-|xi|^2/w^2})(z) = w^{n+1} W_n(w z) (W_width); the
+  c_n (Taylor data of S at 0) do not depend on w.
 * The algorithm of Sec. 4.3 (for k = 0, used with Q -> E_k Q for k != 0 as
   in Sec. 5.1): GMRES on the stacked real and imaginary parts, each matrix
   application doing (a) Taylor coefficients via one inverse FFT and a
@@ -209,6 +213,13 @@ def W(n: int, z):
     return out
 
 
+def W_width(n: int, z, w: float = 1.0):
+    """F^{-1}(conj(xi)^n/xi e^{-|xi|^2/w^2}) = w^{n+1} W_n(w z) (the substitution xi = w eta
+    in the inverse transform); w = 1 is W_n."""
+    w = float(w)
+    return w ** (n + 1) * W(n, w * np.asarray(z, dtype=np.complex128))
+
+
 # ---------------------------------------------------------------------------
 # The regularised F^{-1}(S/xi) (Sec. 4.3, steps 4a-4c).
 # ---------------------------------------------------------------------------
@@ -224,14 +235,15 @@ def taylor_coeffs(S, g: Grid, M: int):
     return c, d
 
 
-def h_of_S(S, g: Grid, M: int, fill: str = "analytic", Wn=None):
-    """h = F^{-1}(S/xi) = F^{-1}((S - G)/xi) + sum_n c_n W_n   (eq. Sreg, S0Taylor).
+def h_of_S(S, g: Grid, M: int, fill: str = "analytic", Wn=None, width: float = 1.0):
+    """h = F^{-1}(S/xi) = F^{-1}((S - G)/xi) + sum_n c_n W_n   (eq. Sreg, S0Taylor),
+    with the Gaussian of G of the given width (e^{-|xi|^2/width^2}).
 
     S may carry leading batch axes.  Returns h on the x-grid."""
     c, d = taylor_coeffs(S, g, M)
     if Wn is None:
-        Wn = [W(n, g.z) for n in range(M + 1)]
-    gauss = np.exp(-(g.xi * np.conj(g.xi)).real)
+        Wn = [W_width(n, g.z, width) for n in range(M + 1)]
+    gauss = np.exp(-(g.xi * np.conj(g.xi)).real / width ** 2)
     G = np.zeros_like(S)
     for n in range(M + 1):
         G = G + np.asarray(c[n])[..., None, None] * gauss * np.conj(g.xi) ** n
@@ -245,7 +257,7 @@ def h_of_S(S, g: Grid, M: int, fill: str = "analytic", Wn=None):
     return h
 
 
-def h_of_S_at(S, g: Grid, m0, M: int, fill: str = "analytic", Wn=None):
+def h_of_S_at(S, g: Grid, m0, M: int, fill: str = "analytic", Wn=None, width: float = 1.0):
     """F^{-1}(S/(xi - xi0)) with the shifted regularisation eq. dbarinvShift, xi0 = (m0[0] + i m0[1])/L
     a grid point:
       * S's quotient by xi - xi0 is formed at the grid points as they are (no periodic wrap of
@@ -255,7 +267,7 @@ def h_of_S_at(S, g: Grid, m0, M: int, fill: str = "analytic", Wn=None):
         its difference xi - xi0 is taken periodically (reading: the paper is silent on a G that
         reaches the edge of the box; there its coefficients are those of S far from its support);
       * the analytic limit d = d_xi S(xi0) at xi0, and F^{-1}(G/(xi - xi0)) = e^{i xi0.x} sum_n c_n W_n.
-    m0 = (0, 0) is h_of_S."""
+    m0 = (0, 0) is h_of_S.  width: that of the Gaussian of G, as in h_of_S."""
     N = g.N
     xi0 = (m0[0] + 1j * m0[1]) / g.L
     s = g.Finv(S)
@@ -263,11 +275,11 @@ def h_of_S_at(S, g: Grid, m0, M: int, fill: str = "analytic", Wn=None):
     c = [(-0.5j) ** n / math.factorial(n) * g.F_at0(g.z ** n * s * ph) for n in range(M + 1)]
     d = -0.5j * g.F_at0(np.conj(g.z) * s * ph)
     if Wn is None:
-        Wn = [W(n, g.z) for n in range(M + 1)]
+        Wn = [W_width(n, g.z, width) for n in range(M + 1)]
     at = (m0[1] % N, m0[0] % N)                                   # the grid point xi0
     dxi = g.xi - xi0                                              # plain difference
     dxi_t = np.roll(g.xi, shift=at, axis=(0, 1))                  # periodic difference on the torus
-    gauss = np.exp(-(dxi_t * np.conj(dxi_t)).real)
+    gauss = np.exp(-(dxi_t * np.conj(dxi_t)).real / width ** 2)
     den, den_t = dxi.copy(), dxi_t.copy()
     den[at] = den_t[at] = 1.0                                     # placeholders, xi0 overwritten below
     U = S / den
@@ -281,9 +293,9 @@ def h_of_S_at(S, g: Grid, m0, M: int, fill: str = "analytic", Wn=None):
     return h
 
 
-def dbar_inverse(f, g: Grid, M: int, fill: str = "analytic"):
+def dbar_inverse(f, g: Grid, M: int, fill: str = "analytic", width: float = 1.0):
     """dbar^{-1} f = F^{-1}(-2i/xi F f) (Sec. 3 lemma), through the same regularisation."""
-    return h_of_S(-2j * g.F(f), g, M, fill)
+    return h_of_S(-2j * g.F(f), g, M, fill, width=width)
 
 
 # ---------------------------------------------------------------------------
@@ -292,21 +304,22 @@ def dbar_inverse(f, g: Grid, M: int, fill: str = "analytic"):
 
 
 class CGOProblem:
-    def __init__(self, Q, k: complex, N: int, L: float, M: int = 2, fill: str = "analytic"):
+    def __init__(self, Q, k: complex, N: int, L: float, M: int = 2, fill: str = "analytic", width: float = 1.0):
         self.g = Grid(N, L)
         self.Q = np.asarray(Q, dtype=np.complex128)
         self.k = complex(k)
         self.M = M
         self.fill = fill
+        self.width = float(width)
         self.EQ = self.g.E(self.k) * self.Q
-        self.Wn = [W(n, self.g.z) for n in range(M + 1)]
+        self.Wn = [W_width(n, self.g.z, width) for n in range(M + 1)]
 
     def rhs(self):
         """b = -i F(E_k Q)  (Sec. 4.3 step 3; eq. S0)."""
         return -1j * self.g.F(self.EQ)
 
     def h(self, S):
-        return h_of_S(S, self.g, self.M, self.fill, self.Wn)
+        return h_of_S(S, self.g, self.M, self.fill, self.Wn, self.width)
 
     def apply(self, S):
         """A S = S + i F(E_k Q conj(h(S)))  (Sec. 4.3 step 4d)."""
@@ -341,9 +354,10 @@ class CGOProblem:
         x = np.linalg.solve(A, self.to_real(self.rhs()))
         return self.from_real(x)
 
-    def solve_gmres(self, tol=1e-13, restart=40, maxiter=2000):
+    def solve_gmres(self, tol=1e-13, restart=40, maxiter=2000, x0=None):
         b = self.to_real(self.rhs())
-        x, it, res = gmres(self.apply_real, b, tol=tol, restart=restart, maxiter=maxiter)
+        x0 = None if x0 is None else self.to_real(np.asarray(x0, dtype=np.complex128))
+        x, it, res = gmres(self.apply_real, b, tol=tol, restart=restart, maxiter=maxiter, x0=x0)
         return self.from_real(x), it, res
 
     def residual(self, S):
@@ -406,10 +420,11 @@ def gmres(apply, b, tol=1e-13, restart=40, maxiter=2000, x0=None):
         x = x + V[:j_done].T @ y
 
 
-def solve_cgo(Q, k, N, L, M=2, tol=1e-13, restart=40, maxiter=2000, fill="analytic"):
-    """One CGO solve: returns dict(S, m, m1, iters, resid)."""
-    P = CGOProblem(Q, k, N, L, M, fill)
-    S, it, res = P.solve_gmres(tol=tol, restart=restart, maxiter=maxiter)
+def solve_cgo(Q, k, N, L, M=2, tol=1e-13, restart=40, maxiter=2000, fill="analytic", width=1.0, x0=None):
+    """One CGO solve: returns dict(S, m, m1, iters, resid).  width: that of the
+    Gaussian of G; x0: initial guess of S (None: S = 0)."""
+    P = CGOProblem(Q, k, N, L, M, fill, width)
+    S, it, res = P.solve_gmres(tol=tol, restart=restart, maxiter=maxiter, x0=x0)
     m = P.h(S)
     return {"S": S, "m": m, "m1": 1j * S[0, 0], "iters": it, "resid": res}
 
@@ -419,14 +434,15 @@ def solve_cgo(Q, k, N, L, M=2, tol=1e-13, restart=40, maxiter=2000, fill="analyt
 # ---------------------------------------------------------------------------
 
 
-def conv_kernel_table(g: Grid):
+def conv_kernel_table(g: Grid, width: float = 1.0):
     """W_0(z_j - z_j') at every difference of two grid points: [dy + N-1][dx + N-1]
-    with z_j - z_j' = h (dx + i dy), h = 2 pi L/N, dx, dy in [-(N-1), N-1]."""
+    with z_j - z_j' = h (dx + i dy), h = 2 pi L/N, dx, dy in [-(N-1), N-1]
+    (W_0 of the Gaussian of the given width)."""
     N = g.N
     h = 2.0 * np.pi * g.L / N
     d = np.arange(-(N - 1), N)
     DX, DY = np.meshgrid(d, d, indexing="xy")
-    return W(0, h * (DX + 1j * DY))
+    return W_width(0, h * (DX + 1j * DY), width)
 
 
 def gauss_convolution(s, g: Grid, K=None):
@@ -447,17 +463,20 @@ def gauss_convolution(s, g: Grid, K=None):
     return out * (h * h / (2.0 * np.pi))
 
 
-def h_of_S_conv(S, g: Grid, K=None):
+def h_of_S_conv(S, g: Grid, K=None, width: float = 1.0):
     """h = F^{-1}(S/xi) with G = S e^{-|xi|^2} (eq. Sreg):
         F^{-1}((S - G)/xi) = F^{-1}(S (1 - e^{-|xi|^2})/xi)   (smooth; 0 at xi = 0)
-        F^{-1}(G/xi)       = (1/2pi) int F^{-1}(S)(z') W_0(z - z') d^2z'."""
+        F^{-1}(G/xi)       = (1/2pi) int F^{-1}(S)(z') W_0(z - z') d^2z'
+    (with a width: e^{-|xi|^2/width^2} and W_0 of that Gaussian)."""
     xi = g.xi.copy()
-    r2 = (xi * np.conj(xi)).real
+    r2 = (xi * np.conj(xi)).real / width ** 2
     xi[0, 0] = 1.0                                # placeholder, the factor is 0 there
     mult = -np.expm1(-r2) / xi
     mult[0, 0] = 0.0
     u = g.Finv(S * mult)
     s = g.Finv(S)
+    if K is None:
+        K = conv_kernel_table(g, width)
     return u + gauss_convolution(s, g, K)
 
 
@@ -470,17 +489,17 @@ class ConvProblem(CGOProblem):
     """The CGO operator of Sec. 4.3 (Q -> E_k Q) with h(S) from the convolution
     regularisation instead of the Taylor-Gaussian G; same right-hand side."""
 
-    def __init__(self, Q, k: complex, N: int, L: float):
-        super().__init__(Q, k, N, L, M=0)
-        self.K = conv_kernel_table(self.g)
+    def __init__(self, Q, k: complex, N: int, L: float, width: float = 1.0):
+        super().__init__(Q, k, N, L, M=0, width=width)
+        self.K = conv_kernel_table(self.g, width)
 
     def h(self, S):
-        return h_of_S_conv(S, self.g, self.K)
+        return h_of_S_conv(S, self.g, self.K, self.width)
 
 
-def solve_cgo_conv(Q, k, N, L, tol=1e-13, restart=40, maxiter=2000):
+def solve_cgo_conv(Q, k, N, L, tol=1e-13, restart=40, maxiter=2000, width=1.0):
     """One CGO solve with the convolution regularisation: dict(S, m, m1, iters, resid)."""
-    P = ConvProblem(Q, k, N, L)
+    P = ConvProblem(Q, k, N, L, width)
     S, it, res = P.solve_gmres(tol=tol, restart=restart, maxiter=maxiter)
     return {"S": S, "m": P.h(S), "m1": 1j * S[0, 0], "iters": it, "resid": res}
 
@@ -536,25 +555,25 @@ class IteratedProblem:
     points, and the singular point xi0 (which may lie near the edge of the box) is
     regularised by a Gaussian G centred there."""
 
-    def __init__(self, q, k, N, L, M=2, fill="analytic"):
+    def __init__(self, q, k, N, L, M=2, fill="analytic", width=1.0):
         self.g = Grid(N, L)
         self.q = np.asarray(q, dtype=np.complex128)
         self.k = complex(k)
-        self.M, self.fill = M, fill
+        self.M, self.fill, self.width = M, fill, float(width)
         # xi0 on the grid's wavenumbers (-N/2, N/2]; -N/2 is the Nyquist point, which the
         # grid holds on the positive side (eq. xidomain)
         m0 = shift_index(self.k, L)
         if not all(-N // 2 <= m <= N // 2 for m in m0):
             raise ValueError("2k L must lie within the grid's wavenumbers [-N/2, N/2]")
         self.m0 = tuple(N // 2 if m == -N // 2 else m for m in m0)
-        self.Wn = [W(n, self.g.z) for n in range(M + 1)]
+        self.Wn = [W_width(n, self.g.z, width) for n in range(M + 1)]
 
     def H(self, h):
-        u = h_of_S_at(h, self.g, self.m0, self.M, self.fill, self.Wn)
+        u = h_of_S_at(h, self.g, self.m0, self.M, self.fill, self.Wn, self.width)
         return -1j * self.g.F(self.q * np.conj(u))
 
     def K0(self, S):
-        return -1j * self.g.F(self.q * np.conj(h_of_S(S, self.g, self.M, self.fill, self.Wn)))
+        return -1j * self.g.F(self.q * np.conj(h_of_S(S, self.g, self.M, self.fill, self.Wn, self.width)))
 
     def rhs(self):
         return -1j * self.g.F(self.q)

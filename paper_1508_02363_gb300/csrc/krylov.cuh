@@ -260,19 +260,23 @@ __global__ void __launch_bounds__(KR_THREADS) k_xupdate(long long n, int mp1, co
 // beta = ||r||, sigma_0 = 1/beta, g = beta e_1, stop threshold, flags.
 // first != 0: the vector is b itself (records ||b||).  mask (nullable): only the
 // slots with mask[slot] != 0 (slots being started while others run).
+// first = 1: a new solve from x = 0 (part holds |b|^2: sets ||b|| and the
+// counters); 0: the next cycle of a running solve; 2: a new solve from a given
+// x (after a first = 1 launch on b; part holds |b - A x|^2: the counters stay
+// as that launch set them).
 static __global__ void __launch_bounds__(KR_THREADS) k_cycle_start(CycleState c, const double* part, int nblk,
                                                              int first, const int* mask) {
   __shared__ double sh[KR_THREADS / 32];
   const int slot = blockIdx.x;
   if (mask && !mask[slot]) return;
-  if (!first && !c.active[slot]) return;
+  if (first != 1 && !c.active[slot]) return;
   double s = 0.0;
   for (int q = threadIdx.x; q < nblk; q += blockDim.x) s += part[(size_t)slot * nblk + q];
   s = block_sum_256(s, sh);
   if (threadIdx.x != 0) return;
   const int m = c.m;
   const double beta = sqrt(s);
-  if (first) {
+  if (first == 1) {
     c.bnorm[slot] = beta;
     c.nscale[slot] = beta > 0.0 ? (float)exp2(-(double)ilogb(beta)) : 1.f;
     c.itot[slot] = 0;
@@ -292,7 +296,8 @@ static __global__ void __launch_bounds__(KR_THREADS) k_cycle_start(CycleState c,
   double thr = 0.5 * c.tol * bn;
   if (c.inner_tol > 0.0) thr = fmax(thr, c.inner_tol * beta);
   c.thr[slot] = thr;
-  if (act) c.ncyc[slot] += 1;
+  if (act && first != 2) c.ncyc[slot] += 1;
+  if (first == 2 && !act) c.ncyc[slot] = 0;  // x already meets tol: no cycle runs
 }
 
 // ---------------------------------------------------------------------------

@@ -206,6 +206,7 @@ struct dbar_plan {
   int* dshift = nullptr;        // [B][2] the same offsets signed, in (-N/2, N/2] (pass A's divisor)
   int* h_dshift = nullptr;      // [B][2] host staging
   int* h_err = nullptr;         // pinned copy of flag[1]: a bounded device wait ran out
+  const cx<double>* x0d = nullptr;  // FP64 initial guesses of the batch being started (device), or none
   void* It1 = nullptr;          // [B][n] rolled field (FP64-sized)
   void* It2 = nullptr;          // [B][n] first operator application (FP64-sized)
   // convolution regularisation (params.regularisation = DBAR_REG_CONV), FP64
@@ -236,8 +237,14 @@ struct dbar_plan {
 
   double inv2piL = 0, sw = 0, fillscale = 0;
 
+  bool dry = false;  // alloc() only counts bytes (the footprint of a mem_budget check)
   template <typename X>
   cudaError_t alloc(X** ptr, size_t count) {
+    if (dry) {
+      bytes += count * sizeof(X);
+      *ptr = nullptr;
+      return cudaSuccess;
+    }
     void* q = nullptr;
     cudaError_t e = cudaMalloc(&q, count * sizeof(X));
     if (e != cudaSuccess) return e;
@@ -283,6 +290,8 @@ extern "C" void dbar_params_init(dbar_params* p, int N, double L) {
   p->resid_mode = DBAR_RESID_DOUBLE_FLOAT;
   p->graphs = 1;
   p->autotune = 1;
+  p->gauss_w = 1.0;
+  p->mem_budget = 0;
 }
 
 extern "C" const char* dbar_last_error(void) { return g_last_error.c_str(); }
@@ -812,12 +821,24 @@ static dbar_status begin_slots(dbar_plan* P, int nb, const int* hmask, cudaStrea
     }
     CK(cudaMemcpyAsync(P->dmask, P->hmask, nb * sizeof(int), cudaMemcpyHostToDevice, st));
     dmask = P->dmask;
+  } else if (P->x0d) {
+    // the caller's initial guess (FP64 on the device) in x's storage format
+    if (P->resid_dd)
+      CK(timed(P, st, K_OTHER, [&] { return launch_split_fields(P->x0d, reinterpret_cast<cx<dd>*>(P->x64), (long long)nb * n, st); }));
+    else
+      CK(cudaMemcpyAsync(P->x64, P->x0d, (size_t)nb * n * sizeof(cx<double>), cudaMemcpyDeviceToDevice, st));
   } else {
     CK(cudaMemsetAsync(P->x64, 0, (size_t)nb * n * sizeof(cx<double>), st));
   }
   dbar_status s = build_rhs<TI>(P, nb, st, dmask);
   if (s != DBAR_OK) return s;
   CK(timed(P, st, K_SCALAR, [&] { return launch_cycle_start(P->cs, P->part2, nblkC, 1, nb, st, dmask); }));
+  if (!hmask && P->x0d) {
+    // start from the true residual b - A x0; ||b|| (set above) stays the reference
+    s = true_residual<TI>(P, nb, st);
+    if (s != DBAR_OK) return s;
+    CK(timed(P, st, K_SCALAR, [&] { return launch_cycle_start(P->cs, P->part2, nblkC, 2, nb, st); }));
+  }
   if (P->prof.on) {
     const double F = (double)n * P->inner_elem(), F64 = (double)n * sizeof(cx<double>);
     P->prof.bytes[K_RHS] += nnew * (4.0 * F64 + F) + (P->M + 2) * F64;
@@ -1118,6 +1139,7 @@ static dbar_status check_params(const dbar_params* p) {
   if (p->sstep > 1 && p->restart % p->sstep != 0) return fail(DBAR_EINVAL, "restart must be a multiple of sstep");
   if (p->iterated != 0 && p->iterated != 1) return fail(DBAR_EINVAL, "iterated must be 0 or 1");
   if (p->inner_M < 0 || p->inner_M > p->M) return fail(DBAR_EINVAL, "inner_M must be in [0, M]");
+  if (!(p->gauss_w > 0.0) || !std::isfinite(p->gauss_w)) return fail(DBAR_EINVAL, "gauss_w must be finite and > 0");
   if (p->regularisation != DBAR_REG_TAYLOR && p->regularisation != DBAR_REG_CONV)
     return fail(DBAR_EINVAL, "regularisation must be DBAR_REG_TAYLOR or DBAR_REG_CONV");
   if (p->regularisation == DBAR_REG_CONV) {
@@ -1180,11 +1202,12 @@ static dbar_status plan_tables(dbar_plan* P) {
 
   if (P->conv) {
     // convolution regularisation: the direct-sum kernel table and the smooth multiplier
-    const double h = 2.0 * M_PI * L / N, w = h * h / (2.0 * M_PI);
+    // W_0 of the Gaussian of width gw: gw W_0(gw z)
+    const double h = 2.0 * M_PI * L / N, w = h * h / (2.0 * M_PI), gw = P->p.gauss_w;
     std::vector<cx<double>> kt((size_t)(2 * N - 1) * 2 * N, mkc(0.0, 0.0));
     for (int dy = -(N - 1); dy <= N - 1; ++dy)
       for (int dx = -(N - 1); dx <= N - 1; ++dx) {
-        const zd v = W_host(0, zd(h * dx, h * dy)) * w;
+        const zd v = W_host(0, zd(gw * h * dx, gw * h * dy)) * (gw * w);
         kt[(size_t)(dy + N - 1) * 2 * N + dx + N - 1] = mkc(v.real(), v.imag());
       }
     std::vector<cx<double>> mu((size_t)N * N);
@@ -1195,7 +1218,7 @@ static dbar_status plan_tables(dbar_plan* P) {
         const zd xi((double)m1 / L, (double)m2 / L);
         const double sg = ((p1 + p2) & 1) ? -1.0 : 1.0;
         zd f(0.0, 0.0);
-        if (m1 != 0 || m2 != 0) f = -std::expm1(-std::norm(xi)) / xi * sg / (2.0 * M_PI * L * L);
+        if (m1 != 0 || m2 != 0) f = -std::expm1(-std::norm(xi) / (gw * gw)) / xi * sg / (2.0 * M_PI * L * L);
         mu[(size_t)p2 * N + p1] = mkc(f.real(), f.imag());
       }
     }
@@ -1206,6 +1229,8 @@ static dbar_status plan_tables(dbar_plan* P) {
 
   // Delta_n = W_n - V_n, V_n = F_d^{-1}(e^{-|xi|^2} conj(xi)^n / xi, 0 at xi = 0)
   //         = (1/(2 pi L^2)) IDFT((-1)^{p1+p2} e^{-|xi|^2} conj(xi)^n / xi).
+  // A Gaussian of width gw (e^{-|xi|^2/gw^2}) scales the closed form: gw^{n+1} W_n(gw z).
+  const double gw = P->p.gauss_w;
   const int nf = P->M + 1;
   const size_t nn = (size_t)N * N;
   std::vector<cx<double>> hE(nf * nn), hW(nf * nn);
@@ -1216,7 +1241,7 @@ static dbar_status plan_tables(dbar_plan* P) {
       const zd xi((double)m1 / L, (double)m2 / L);
       const double sg = ((p1 + p2) & 1) ? -1.0 : 1.0;
       zd f(0.0, 0.0);
-      if (m1 != 0 || m2 != 0) f = std::exp(-std::norm(xi)) / xi * sg / (2.0 * M_PI * L * L);
+      if (m1 != 0 || m2 != 0) f = std::exp(-std::norm(xi) / (gw * gw)) / xi * sg / (2.0 * M_PI * L * L);
       for (int nn_ = 0; nn_ < nf; ++nn_) {
         hE[nn_ * nn + (size_t)p2 * N + p1] = mkc(f.real(), f.imag());
         f *= std::conj(xi);
@@ -1226,8 +1251,9 @@ static dbar_status plan_tables(dbar_plan* P) {
   for (int j2 = 0; j2 < N; ++j2)
     for (int j1 = 0; j1 < N; ++j1) {
       const zd z(xgrid(j1, N, L), xgrid(j2, N, L));
-      for (int nn_ = 0; nn_ < nf; ++nn_) {
-        const zd w = W_host(nn_, z);
+      double sc = gw;  // gw^{n+1}
+      for (int nn_ = 0; nn_ < nf; ++nn_, sc *= gw) {
+        const zd w = W_host(nn_, gw * z) * sc;
         hW[nn_ * nn + (size_t)j2 * N + j1] = mkc(w.real(), w.imag());
       }
     }
@@ -1363,65 +1389,19 @@ size_t plan_fixed_bytes(const dbar_params* p) {
   return b;
 }
 
-dbar_status plan_create_ex(const dbar_params* p, int per_slot_q, dbar_plan** out) {
-  if (!out) return fail(DBAR_EINVAL, "out is NULL");
-  *out = nullptr;
-  dbar_status s = check_params(p);
-  if (s != DBAR_OK) return s;
-  int ndev = 0;
-  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
-    cudaGetLastError();
-    return fail(DBAR_ECUDA, "no CUDA device is available");
-  }
-  dbar_plan* P = new (std::nothrow) dbar_plan();
-  if (!P) return fail(DBAR_ENOMEM, "host allocation failed");
-  P->p = *p;
-  P->per_slot_q = per_slot_q ? 1 : 0;
-  P->N = p->N;
-  P->logN = 0;
-  while ((1 << P->logN) < P->N) ++P->logN;
-  P->M = p->M;
-  P->MA = std::max(1, p->M);
-  P->Min = (p->prec == DBAR_MIXED && p->inner_M > 0) ? p->inner_M : p->M;
-  P->m = p->restart;
-  P->iter = p->iterated != 0;
-  P->conv = p->regularisation == DBAR_REG_CONV;
-  // automatic choice: blocks of 4 for the Sec. 4 operator; one vector per sweep for the
-  // multi-application operators (their solves take few iterations, which blocks overshoot)
-  P->sstep = ((P->conv || P->iter) && p->sstep == 0) ? 1 : (p->sstep > 0 ? p->sstep : (p->restart % 4 == 0 ? 4 : (p->restart % 2 == 0 ? 2 : 1)));
-  P->mixed = (p->prec == DBAR_MIXED);
-  P->resid_dd = P->mixed && p->resid_mode == DBAR_RESID_DOUBLE_FLOAT;
-  P->n = (long long)P->N * P->N;
-  cudaGetDevice(&P->device);
-  const double L = p->L;
-  P->inv2piL = 1.0 / (2.0 * M_PI * L);
-  P->sw = 2.0 * M_PI * L * L / ((double)P->N * P->N);
-  P->fillscale = p->zero_fill ? 0.0 : 1.0 / (2.0 * M_PI * L * L);
-
-  const size_t F64 = (size_t)P->n * sizeof(cx<double>);
+// Every device workspace of a plan of B slots.  With P->dry set nothing is
+// allocated and only P->bytes grows (the exact size, for mem_budget).
+static cudaError_t alloc_workspaces(dbar_plan* P, int B, const char** what) {
+  cudaError_t e = cudaSuccess;
   const size_t Fi = (size_t)P->n * P->inner_elem();
   const int nchunk = (int)((P->n + KR_CHUNK - 1) / KR_CHUNK);
-  const size_t per_slot = plan_slot_bytes(p, per_slot_q);
-  int B = p->max_batch;
-  if (B == 0) {
-    size_t freeb = 0, totb = 0;
-    cudaMemGetInfo(&freeb, &totb);
-    const size_t fixed = (size_t)(2 * (P->M + 1) + 3) * F64;
-    size_t avail = freeb > fixed ? (freeb - fixed) / 2 : 0;
-    B = (int)std::min<size_t>(256, std::max<size_t>(1, avail / per_slot));
-  }
-  if (P->conv) B = std::min(B, 4096);  // the raw transforms take 2 B fields per launch
-  P->B = B;
-  cudaError_t e = cudaSuccess;
-#define AL(ptr, cnt)                                                          \
-  do {                                                                        \
-    e = P->alloc(&(ptr), (cnt));                                              \
-    if (e != cudaSuccess) {                                                   \
-      delete P;                                                               \
-      return fail(e == cudaErrorMemoryAllocation ? DBAR_ENOMEM : DBAR_ECUDA,  \
-                  std::string("cudaMalloc failed for " #ptr ": ") +           \
-                      cudaGetErrorString(e));                                 \
-    }                                                                         \
+#define AL(ptr, cnt)                     \
+  do {                                   \
+    e = P->alloc(&(ptr), (cnt));         \
+    if (e != cudaSuccess) {              \
+      *what = #ptr;                      \
+      return e;                          \
+    }                                    \
   } while (0)
   const size_t n = (size_t)P->n;
   AL(P->tw64, P->N);
@@ -1518,6 +1498,94 @@ dbar_status plan_create_ex(const dbar_params* p, int per_slot_q, dbar_plan** out
     AL(P->upd, B);
   }
 #undef AL
+  return cudaSuccess;
+}
+
+dbar_status plan_create_ex(const dbar_params* p, int per_slot_q, dbar_plan** out) {
+  if (!out) return fail(DBAR_EINVAL, "out is NULL");
+  *out = nullptr;
+  dbar_status s = check_params(p);
+  if (s != DBAR_OK) return s;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return fail(DBAR_ECUDA, "no CUDA device is available");
+  }
+  dbar_plan* P = new (std::nothrow) dbar_plan();
+  if (!P) return fail(DBAR_ENOMEM, "host allocation failed");
+  P->p = *p;
+  P->per_slot_q = per_slot_q ? 1 : 0;
+  P->N = p->N;
+  P->logN = 0;
+  while ((1 << P->logN) < P->N) ++P->logN;
+  P->M = p->M;
+  P->MA = std::max(1, p->M);
+  P->Min = (p->prec == DBAR_MIXED && p->inner_M > 0) ? p->inner_M : p->M;
+  P->m = p->restart;
+  P->iter = p->iterated != 0;
+  P->conv = p->regularisation == DBAR_REG_CONV;
+  // automatic choice: blocks of 4 for the Sec. 4 operator; one vector per sweep for the
+  // multi-application operators (their solves take few iterations, which blocks overshoot)
+  P->sstep = ((P->conv || P->iter) && p->sstep == 0) ? 1 : (p->sstep > 0 ? p->sstep : (p->restart % 4 == 0 ? 4 : (p->restart % 2 == 0 ? 2 : 1)));
+  P->mixed = (p->prec == DBAR_MIXED);
+  P->resid_dd = P->mixed && p->resid_mode == DBAR_RESID_DOUBLE_FLOAT;
+  P->n = (long long)P->N * P->N;
+  cudaGetDevice(&P->device);
+  const double L = p->L;
+  P->inv2piL = 1.0 / (2.0 * M_PI * L);
+  P->sw = 2.0 * M_PI * L * L / ((double)P->N * P->N);
+  P->fillscale = p->zero_fill ? 0.0 : 1.0 / (2.0 * M_PI * L * L);
+
+  const size_t F64 = (size_t)P->n * sizeof(cx<double>);
+  const size_t per_slot = plan_slot_bytes(p, per_slot_q);
+  int B = p->max_batch;
+  if (B == 0) {
+    size_t freeb = 0, totb = 0;
+    cudaMemGetInfo(&freeb, &totb);
+    const size_t fixed = (size_t)(2 * (P->M + 1) + 3) * F64;
+    size_t avail = freeb > fixed ? (freeb - fixed) / 2 : 0;
+    B = (int)std::min<size_t>(256, std::max<size_t>(1, avail / per_slot));
+  }
+  if (P->conv) B = std::min(B, 4096);  // the raw transforms take 2 B fields per launch
+  if (p->mem_budget > 0) {
+    // the plan's exact footprint is affine in the batch size: bytes(1), bytes(2)
+    const char* what = nullptr;
+    P->dry = true;
+    alloc_workspaces(P, 1, &what);
+    const size_t b1 = P->bytes;
+    P->bytes = 0;
+    alloc_workspaces(P, 2, &what);
+    const size_t b2 = P->bytes;
+    P->bytes = 0;
+    P->dry = false;
+    const size_t per = b2 - b1, fixed = b1 - per;
+    if (b1 > p->mem_budget) {
+      delete P;
+      return fail(DBAR_ENOMEM, "mem_budget " + std::to_string(p->mem_budget) + " bytes is below one slot's plan (" +
+                                   std::to_string(b1) + " bytes)");
+    }
+    const size_t fit = (p->mem_budget - fixed) / per;
+    if (p->max_batch == 0) {
+      B = (int)std::min<size_t>((size_t)B, fit);
+    } else if ((size_t)B > fit) {
+      delete P;
+      return fail(DBAR_ENOMEM, "max_batch " + std::to_string(B) + " needs " + std::to_string(fixed + per * B) +
+                                   " bytes, above mem_budget " + std::to_string(p->mem_budget));
+    }
+  }
+  P->B = B;
+  const size_t n = (size_t)P->n;
+  const int m = P->m;
+  CycleState& c = P->cs;
+  {
+    const char* what = "";
+    const cudaError_t e = alloc_workspaces(P, B, &what);
+    if (e != cudaSuccess) {
+      delete P;
+      return fail(e == cudaErrorMemoryAllocation ? DBAR_ENOMEM : DBAR_ECUDA,
+                  std::string("cudaMalloc failed for ") + what + ": " + cudaGetErrorString(e));
+    }
+  }
   if (cudaMemset(P->ticket, 0, (size_t)B * sizeof(int)) != cudaSuccess ||
       cudaMemset(P->flag, 0, 4 * sizeof(int)) != cudaSuccess) {
     delete P;
@@ -1663,8 +1731,26 @@ static dbar_status solution_fp64(dbar_plan* P, int s0, int nb, cudaStream_t st, 
   return DBAR_OK;
 }
 
-extern "C" dbar_status dbar_solve_cgo(dbar_plan_t P, const double* Q, int nk, const double* k, double* S_out,
-                                      double* m_out, int* iters, double* resid, int io_on_device, void* stream) {
+// The caller's initial guesses of slots [k0, k0 + nb) (host or device, any
+// alignment) staged into T1, checked for non-finite entries; P->x0d points there.
+static dbar_status load_x0(dbar_plan* P, const double* x0, int k0, int nb, int on_device, cudaStream_t st) {
+  const size_t cnt = (size_t)nb * P->n;
+  cx<double>* dst = reinterpret_cast<cx<double>*>(P->T1);
+  CK(cudaMemcpyAsync(dst, x0 + (size_t)k0 * P->n * 2, cnt * sizeof(cx<double>),
+                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(P->flag, 0, sizeof(int), st));
+  CK(timed(P, st, K_OTHER, [&] { return launch_check_finite(reinterpret_cast<const double*>(dst), 2 * (long long)cnt, P->flag, st); }));
+  int bad = 0;
+  CK(cudaMemcpyAsync(&bad, P->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (bad) return fail(DBAR_EINVAL, "x0 has a non-finite entry");
+  P->x0d = dst;
+  return DBAR_OK;
+}
+
+extern "C" dbar_status dbar_solve_cgo(dbar_plan_t P, const double* Q, int nk, const double* k, const double* x0,
+                                      double* S_out, double* m_out, int* iters, double* resid, int io_on_device,
+                                      void* stream) {
   if (!P) return fail(DBAR_EINVAL, "plan is NULL");
   dbar_status s = check_k(k, nk);
   if (s != DBAR_OK) return s;
@@ -1690,7 +1776,9 @@ extern "C" dbar_status dbar_solve_cgo(dbar_plan_t P, const double* Q, int nk, co
     const int nb = std::min(P->B, nk - k0);
     s = upload_ek(P, k + 2 * k0, nb, st);
     if (s != DBAR_OK) return s;
+    if (x0 && (s = load_x0(P, x0, k0, nb, io_on_device, st)) != DBAR_OK) return s;
     s = P->mixed ? run_cycles<float>(P, nb, st) : run_cycles<double>(P, nb, st);
+    P->x0d = nullptr;
     if (s != DBAR_OK) return s;
     const cx<double>* S64 = nullptr;
     if (direct) {

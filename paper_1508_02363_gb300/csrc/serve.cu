@@ -101,6 +101,7 @@ dbar_params lane_params(const dbar_server* S, int N, double L, int B) {
   p.N = N;
   p.L = L;
   p.max_batch = B;
+  p.mem_budget = 0;  // the server's own budget decides B
   return p;
 }
 

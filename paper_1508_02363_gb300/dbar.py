@@ -38,7 +38,8 @@ class dbar_params(ctypes.Structure):
                 ("zero_fill", ctypes.c_int), ("max_batch", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("max_outer", ctypes.c_int), ("resid_mode", ctypes.c_int), ("graphs", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("sstep", ctypes.c_int), ("iterated", ctypes.c_int),
-                ("regularisation", ctypes.c_int), ("inner_M", ctypes.c_int)]
+                ("regularisation", ctypes.c_int), ("inner_M", ctypes.c_int), ("gauss_w", ctypes.c_double),
+                ("mem_budget", ctypes.c_size_t)]
 
 
 class dbar_request(ctypes.Structure):
@@ -66,7 +67,7 @@ _lib.dbar_last_error.restype = ctypes.c_char_p
 _lib.dbar_plan_create.argtypes = [ctypes.POINTER(dbar_params), ctypes.POINTER(_vp)]
 _lib.dbar_plan_destroy.argtypes = [_vp]
 _lib.dbar_plan_info.argtypes = [_vp, ctypes.POINTER(ctypes.c_size_t), _ip]
-_lib.dbar_solve_cgo.argtypes = [_vp, _vp, _int, _dp, _vp, _vp, _ip, _dp, _int, _vp]
+_lib.dbar_solve_cgo.argtypes = [_vp, _vp, _int, _dp, _vp, _vp, _vp, _ip, _dp, _int, _vp]
 _lib.dbar_apply.argtypes = [_vp, _vp, _int, _dp, _vp, _vp, _int, _vp]
 _lib.dbar_reflection.argtypes = [_vp, _vp, _int, _dp, _dbl, _dp, _ip, _dp, _int, _vp]
 _lib.dbar_ds2_potential.argtypes = [_vp, _vp, _dbl, _int, _dp, _dp, _ip, _dp, _int, _vp]
@@ -166,18 +167,20 @@ def dbar_plan_info(plan):
     return b.value, mb.value
 
 
-def dbar_solve_cgo(plan, Q, k, S_out, m_out=None, iters=None, resid=None, io_on_device=None, stream=None) -> int:
-    """Q, S_out, m_out: numpy complex128 arrays (host) or torch complex128 CUDA tensors.
-    iters: numpy int32 [nk, 2]; resid: numpy float64 [nk].  Returns the status
-    (DBAR_OK or DBAR_ENOCONV); other failures raise DbarError."""
+def dbar_solve_cgo(plan, Q, k, S_out, m_out=None, iters=None, resid=None, io_on_device=None, stream=None,
+                   x0=None) -> int:
+    """Q, x0, S_out, m_out: numpy complex128 arrays (host) or torch complex128 CUDA tensors.
+    x0 (optional): initial guess of S per k.  iters: numpy int32 [nk, 2]; resid:
+    numpy float64 [nk].  Returns the status (DBAR_OK or DBAR_ENOCONV); other
+    failures raise DbarError."""
     kb = _kbuf(k)
     nk = kb.size // 2
     if io_on_device is None:
         io_on_device = hasattr(Q, "data_ptr")
     ip = iters.ctypes.data_as(_ip) if iters is not None else None
     rp = resid.ctypes.data_as(_dp) if resid is not None else None
-    st = _lib.dbar_solve_cgo(plan, _ptr(Q), nk, kb.ctypes.data_as(_dp), _ptr(S_out), _ptr(m_out), ip, rp,
-                             int(bool(io_on_device)), _stream(stream))
+    st = _lib.dbar_solve_cgo(plan, _ptr(Q), nk, kb.ctypes.data_as(_dp), _ptr(x0), _ptr(S_out), _ptr(m_out), ip,
+                             rp, int(bool(io_on_device)), _stream(stream))
     return _check(st, (DBAR_OK, DBAR_ENOCONV))
 
 
@@ -317,24 +320,27 @@ class Plan:
         except Exception:
             pass
 
-    def solve(self, Q, k, want_m: bool = True, stream=None):
-        """Host in, host out: returns dict(S, m, iters, resid, status)."""
+    def solve(self, Q, k, want_m: bool = True, stream=None, x0=None):
+        """Host in, host out: returns dict(S, m, iters, resid, status).  x0: optional
+        initial guess of S ([nk, N, N] complex128), e.g. the S of an interrupted solve."""
         k = np.atleast_1d(np.asarray(k, dtype=np.complex128))
         nk, N = k.size, self.N
         Q = np.ascontiguousarray(np.asarray(Q, dtype=np.complex128).reshape(N, N))
+        if x0 is not None:
+            x0 = np.ascontiguousarray(np.asarray(x0, dtype=np.complex128).reshape(nk, N, N))
         S = np.zeros((nk, N, N), np.complex128)
         m = np.zeros((nk, N, N), np.complex128) if want_m else None
         iters = np.zeros((nk, 2), np.int32)
         resid = np.zeros(nk, np.float64)
-        st = dbar_solve_cgo(self.handle, Q, k, S, m, iters, resid, io_on_device=False, stream=stream)
+        st = dbar_solve_cgo(self.handle, Q, k, S, m, iters, resid, io_on_device=False, stream=stream, x0=x0)
         return {"S": S, "m": m, "iters": iters, "resid": resid, "status": st}
 
-    def solve_device(self, Q, k, S_out, m_out=None, stream=None):
-        """Device in, device out (torch complex128 CUDA tensors)."""
+    def solve_device(self, Q, k, S_out, m_out=None, stream=None, x0=None):
+        """Device in, device out (torch complex128 CUDA tensors; x0 optional)."""
         k = np.atleast_1d(np.asarray(k, dtype=np.complex128))
         iters = np.zeros((k.size, 2), np.int32)
         resid = np.zeros(k.size, np.float64)
-        st = dbar_solve_cgo(self.handle, Q, k, S_out, m_out, iters, resid, io_on_device=True, stream=stream)
+        st = dbar_solve_cgo(self.handle, Q, k, S_out, m_out, iters, resid, io_on_device=True, stream=stream, x0=x0)
         return {"iters": iters, "resid": resid, "status": st}
 
 
@@ -354,9 +360,9 @@ def dbar_serve_submit(srv, N: int, L: float, Q, k: complex, want_m: bool = False
     return t.value
 
 
-def _result_dict(res: dbar_result, N: int):
+def _result_dict(res: dbar_result, N: int, copy: bool = True):
     def arr(p):
-        if not p:
+        if not p or not copy:
             return None
         buf = (ctypes.c_double * (2 * N * N)).from_address(p)
         return np.frombuffer(buf, dtype=np.float64).view(np.complex128).reshape(N, N).copy()
@@ -371,10 +377,11 @@ def dbar_serve_poll(srv, ticket: int, N: int):
     return None if st == DBAR_EBUSY else _result_dict(res, N)
 
 
-def dbar_serve_wait(srv, ticket: int, N: int, timeout_s: float = -1.0):
+def dbar_serve_wait(srv, ticket: int, N: int, timeout_s: float = -1.0, copy: bool = True):
+    """Blocks until the request is done; copy=False leaves S and m out of the dict."""
     res = dbar_result()
     _check(_lib.dbar_serve_wait(srv, ticket, float(timeout_s), ctypes.byref(res)))
-    return _result_dict(res, N)
+    return _result_dict(res, N, copy)
 
 
 def dbar_serve_release(srv, ticket: int) -> None:
@@ -414,8 +421,8 @@ class Server:
     def poll(self, ticket: int):
         return dbar_serve_poll(self.handle, ticket, self._N[ticket])
 
-    def wait(self, ticket: int, timeout_s: float = -1.0, release: bool = True):
-        r = dbar_serve_wait(self.handle, ticket, self._N[ticket], timeout_s)
+    def wait(self, ticket: int, timeout_s: float = -1.0, release: bool = True, copy: bool = True):
+        r = dbar_serve_wait(self.handle, ticket, self._N[ticket], timeout_s, copy)
         if release:
             self.release(ticket)
         return r

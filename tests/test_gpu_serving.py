@@ -108,3 +108,36 @@ def test_invalid_requests_are_rejected_at_submit(dbar):
             srv.submit(*args)
         assert e.value.status == dbar.DBAR_EINVAL
     srv.close()
+
+
+def _oracle_S(args):
+    N, L, Q, k = args
+    from oracle import dbar_oracle as orc
+    return orc.solve_cgo(Q, k, N, L, M=2, tol=1e-13, restart=40)["S"]
+
+
+def test_served_results_match_the_oracle_at_the_serving_k_range(dbar):
+    # The serving workload's grid classes and k range (L = 6, N raised until
+    # N/(2L) >= 2 max(|k1|, |k2|) + 20): N = 256 at small |k|, N = 512 up to
+    # max(|k1|, |k2|) = 11, N = 1024 at |k| = 20; each request its own Gaussian mixture
+    # of 1-6 terms, all submitted together so that they share lanes.  Every served S
+    # is compared with the FP64 CPU oracle (mixed-precision bar 1e-10).
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    L = 6.0
+    cases = [(256, 0.12 + 0.05j), (256, -0.3 + 0.5j), (512, 3.7 + 2.1j), (512, -8.5 + 6.0j),
+             (512, 11.0 - 10.8j), (1024, 20.0 + 0.0j)]
+    reqs = []
+    srv = dbar.Server(16 << 30, prec="mixed", restart=32, tol=1e-12)
+    for i, (N, k) in enumerate(cases):
+        rng = np.random.default_rng(900 + i)
+        Q = wl.gaussian_mixture(N, L, *wl.draw_mixture(rng, int(rng.integers(1, 7))))
+        reqs.append((N, Q, k, srv.submit(N, L, Q, k)))
+    with cf.ProcessPoolExecutor(max_workers=len(cases), mp_context=mp.get_context("spawn")) as ex:
+        futs = [ex.submit(_oracle_S, (N, L, Q, k)) for N, Q, k, _ in reqs]
+        served = [srv.wait(t, timeout_s=300) for *_, t in reqs]
+        oracle = [f.result() for f in futs]
+    srv.close()
+    for i, (r, So) in enumerate(zip(served, oracle)):
+        assert r["status"] == dbar.DBAR_OK and r["resid"] <= 1e-12, i
+        assert rel(r["S"], So) <= 1e-10, (i, cases[i], rel(r["S"], So))

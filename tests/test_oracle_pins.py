@@ -109,6 +109,20 @@ def test_W_matches_bessel_quadrature(n):
         assert abs(orc.W(n, np.array([z]))[0] - ref) <= 1e-12 * max(1.0, abs(ref))
 
 
+@pytest.mark.parametrize("n", [0, 2, 5])
+@pytest.mark.parametrize("w", [0.6, 1.7])
+def test_W_of_a_wider_or_narrower_gaussian_matches_bessel_quadrature(n, w):
+    # The defining integral with e^{-|xi|^2/w^2}, in polar form:
+    # i^{n+1} e^{-i(n+1) arg z} int_0^inf r^n e^{-r^2/w^2} J_{n+1}(|z| r) dr.
+    from scipy import integrate, special
+    for z in [0.4 + 0.3j, -1.7 + 0.9j, 3.0 - 2.5j]:
+        rho, phi = abs(z), np.angle(z)
+        val, _ = integrate.quad(lambda r: r ** n * np.exp(-r * r / (w * w)) * special.jv(n + 1, rho * r),
+                                0, 12 * w, epsabs=1e-15, epsrel=1e-13, limit=400)
+        ref = (1j) ** (n + 1) * np.exp(-1j * (n + 1) * phi) * val
+        assert abs(orc.W_width(n, np.array([z]), w)[0] - ref) <= 1e-12 * max(1.0, abs(ref))
+
+
 # --------------------------------------------------------------------------- Taylor data
 
 def test_taylor_coefficients_of_a_shifted_gaussian():
@@ -142,6 +156,19 @@ def test_dbar_inverse_worked_example_reaches_machine_precision():
     g = orc.Grid(p["N"], p["L"])
     f, exact = _dbartest(g, p["a"], p["b"], complex(p["c_re"], p["c_im"]))
     err = abs(orc.dbar_inverse(f, g, p["M"]) - exact).max()
+    assert err < gold["claims"]["linf_error_below"], err
+
+
+@pytest.mark.parametrize("w", [1.5, 2.0])
+def test_dbar_inverse_worked_example_with_another_gaussian_width(w):
+    # The regularisation is exact for any width of the Gaussian of G: the eq. dbartest
+    # example keeps machine precision at the golden parameters with w = 1.5 and 2.
+    with open(os.path.join(GOLDEN, "dbartest.json")) as fh:
+        gold = json.load(fh)
+    p = gold["parameters"]
+    g = orc.Grid(p["N"], p["L"])
+    f, exact = _dbartest(g, p["a"], p["b"], complex(p["c_re"], p["c_im"]))
+    err = abs(orc.dbar_inverse(f, g, p["M"], width=w) - exact).max()
     assert err < gold["claims"]["linf_error_below"], err
 
 
@@ -203,6 +230,20 @@ def test_krylov_agrees_with_dense_direct_solve(N):
     Sk, it, res = P.solve_gmres(tol=1e-14)
     assert res < 1e-13
     assert abs(Sk - Sd).max() <= 1e-12 * abs(Sd).max()
+
+
+def test_gmres_resumes_from_an_initial_guess():
+    # GMRES (Sec. 4.1) from a given start: the converged solution is a fixed point (no
+    # iteration), and a solve capped early resumes from its iterate to the same solution.
+    w = wl.small_gaussian(16, 2.0, 0.5 + 0.3j, amp=1.0)
+    P = orc.CGOProblem(w.Q, w.k[0], w.N, w.L)
+    Sd = P.solve_dense()
+    S1, it1, res1 = P.solve_gmres(tol=1e-14, restart=4, maxiter=4)
+    assert res1 > 1e-6 and it1 == 4
+    S2, it2, res2 = P.solve_gmres(tol=1e-14, restart=8, x0=S1)
+    assert res2 <= 1e-14 and abs(S2 - Sd).max() <= 1e-12 * abs(Sd).max()
+    S3, it3, res3 = P.solve_gmres(tol=1e-12, x0=Sd)
+    assert it3 == 0 and np.array_equal(S3, Sd)
 
 
 @pytest.mark.slow

@@ -57,12 +57,16 @@ def mesh(N: int, L: float):
 
 
 def gaussian_mixture(N, L, centres, widths, amps):
-    """Q = sum_j c_j exp(-|z - z_j|^2 / w_j^2) sampled on the grid."""
-    X, Y = mesh(N, L)
-    Q = np.zeros((N, N), dtype=np.complex128)
-    for (cx, cy), w, c in zip(centres, widths, amps):
-        Q += c * np.exp(-((X - cx) ** 2 + (Y - cy) ** 2) / (w * w))
-    return Q
+    """Q = sum_j c_j exp(-|z - z_j|^2 / w_j^2) sampled on the grid.  Each term is the
+    outer product exp(-(y - y_j)^2/w_j^2) exp(-(x - x_j)^2/w_j^2), so Q is one matrix
+    product over the terms ([N][t] times [t][N])."""
+    x = x_grid(N, L)
+    centres = np.asarray(centres, dtype=np.float64).reshape(-1, 2)
+    w2 = np.asarray(widths, dtype=np.float64).reshape(-1, 1) ** 2
+    gx = np.exp(-((x[None, :] - centres[:, 0:1]) ** 2) / w2)      # [t][N], along x
+    gy = np.exp(-((x[None, :] - centres[:, 1:2]) ** 2) / w2)      # [t][N], along y
+    amps = np.asarray(amps, dtype=np.complex128).reshape(-1)
+    return np.ascontiguousarray((gy.T * amps[None, :]) @ gx.astype(np.complex128))
 
 
 def draw_mixture(rng: np.random.Generator, nterms: int):
@@ -134,6 +138,34 @@ def mixture_request(seed: int, N: int, L: float, kmax: float, nterms_max: int = 
     centres, widths, amps = draw_mixture(rng, nterms)
     k = np.exp(rng.uniform(np.log(0.1), np.log(kmax))) * np.exp(1j * rng.uniform(0.0, 2.0 * np.pi))
     return gaussian_mixture(N, L, centres, widths, amps), complex(k)
+
+
+SERVING_SIZES = (256, 512, 1024, 2048)
+
+
+def serving_request(i: int, base_seed: int = 5, L: float = 6.0, kmax: float = 20.0, xi_q: float = 20.0,
+                    sizes=SERVING_SIZES):
+    """Request i of the serving stream, drawn from default_rng(base_seed + i): N uniform
+    over `sizes`, then 1-6 Gaussian terms (drawn as in draw_mixture), then k with |k|
+    log-uniform in [0.1, kmax] and arg k U[0, 2pi).  N is raised to the smallest size
+    that resolves E_k Q: N/(2L) >= 2 max(|k1|, |k2|) + xi_q.  Returns (N, k, mixture),
+    mixture = (centres, widths, amps) for gaussian_mixture."""
+    rng = np.random.default_rng(base_seed + i)
+    N = int(rng.choice(np.asarray(sizes)))
+    nterms = int(rng.integers(1, 7))
+    mixture = draw_mixture(rng, nterms)
+    k = complex(np.exp(rng.uniform(np.log(0.1), np.log(kmax))) * np.exp(1j * rng.uniform(0.0, 2.0 * np.pi)))
+    while N < max(sizes) and N / (2.0 * L) < 2.0 * max(abs(k.real), abs(k.imag)) + xi_q:
+        N *= 2
+    return N, k, mixture
+
+
+def poisson_arrivals(rate: float, duration: float, seed: int = 5) -> np.ndarray:
+    """Arrival times (s) of a Poisson stream of `rate` per second over `duration` s."""
+    rng = np.random.default_rng(seed)
+    n = int(rate * duration * 1.5) + 16
+    t = np.cumsum(rng.exponential(1.0 / rate, size=n))
+    return t[t < duration]
 
 
 def uneven_potentials(N: int, L: float):
