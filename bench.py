@@ -24,7 +24,12 @@ import sys
 import threading
 import time
 
-import numpy as np
+# one BLAS thread per caller: the serving leg generates potentials in a thread pool, and a
+# multi-threaded BLAS inside each of its matrix products oversubscribes the host cores
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+os.environ.setdefault("OMP_NUM_THREADS", "1")
+
+import numpy as np  # noqa: E402
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)

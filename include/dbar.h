@@ -287,10 +287,11 @@ dbar_status dbar_fft2(dbar_plan_t plan, int nk, const void* in, void* out, int s
  * that forbid allocator calls (cudaMalloc/cudaFree may synchronise the device).
  * (The paper has no counterpart: this is an interface for such callers.)
  * It needs no plan.  Its intermediate field and twiddle tables live in the
- * library's own global arrays: every GPU that loads the library keeps 16 MiB
+ * library's own global arrays: every GPU that loads the library keeps 32 MiB
  * of scratch plus ~100 KiB of tables until the process exits.  Limit:
- * nk*N*N*sizeof(element) <= 16 MiB (1M complex128 or 2M complex64 values per
- * call); larger calls return DBAR_EINVAL.  N is a power of two in [32, 2048].
+ * nk*N*N*sizeof(element) <= 32 MiB (2M complex128 or 4M complex64 values per
+ * call: one 2048^2 complex64 field, two 1024^2 complex128 fields); larger
+ * calls return DBAR_EINVAL.  N is a power of two in [32, 2048].
  * All calls share the scratch, so calls that overlap on the GPU race.  The
  * first call on a device uploads the twiddle tables and looks up the arrays'
  * device addresses with that device current.  in and out are

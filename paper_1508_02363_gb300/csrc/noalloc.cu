@@ -12,8 +12,9 @@
 // nothing.
 //
 // Costs and rules of that choice:
-//  * Every GPU that loads the library holds kScratchBytes (16 MiB) plus the
-//    twiddle tables (about 100 KiB) until the process exits.
+//  * Every GPU that loads the library holds kScratchBytes (32 MiB: one 2048^2
+//    complex64 field, the largest grid's FP32 transform) plus the twiddle
+//    tables (about 100 KiB) until the process exits.
 //  * All calls share the one scratch array: calls that overlap on the GPU
 //    (different host threads, or different streams without ordering) race.
 //  * The first call on a device copies the twiddle tables there and looks up
@@ -35,7 +36,7 @@ using namespace dbar;
 
 namespace {
 
-constexpr size_t kScratchBytes = (size_t)16 << 20;  // 16 MiB
+constexpr size_t kScratchBytes = (size_t)32 << 20;  // 32 MiB
 constexpr int kMinLog = 5, kMaxLog = 11;              // N = 32 .. 2048
 constexpr int kTableLen = (1 << (kMaxLog + 1)) - (1 << kMinLog);  // sum of all supported N
 constexpr int kMaxDevices = 64;
@@ -119,8 +120,8 @@ extern "C" dbar_status dbar_fft2_noalloc(int N, int nk, const void* in, void* ou
   if (!in || !out) return dbar_internal_fail(DBAR_EINVAL, "dbar_fft2_noalloc: NULL pointer");
   const size_t bytes = (size_t)nk * N * N * (fp32 ? sizeof(cx<float>) : sizeof(cx<double>));
   if (bytes > kScratchBytes)
-    return dbar_internal_fail(DBAR_EINVAL, "dbar_fft2_noalloc: nk*N*N fields exceed the 16 MiB scratch "
-                                           "(at most 1M complex128 or 2M complex64 values per call)");
+    return dbar_internal_fail(DBAR_EINVAL, "dbar_fft2_noalloc: nk*N*N fields exceed the 32 MiB scratch "
+                                           "(at most 2M complex128 or 4M complex64 values per call)");
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return dbar_internal_fail(DBAR_ECUDA, "dbar_fft2_noalloc: no device");
   DeviceState* d = nullptr;

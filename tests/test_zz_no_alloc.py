@@ -27,9 +27,9 @@ def env():
     return torch, dbar
 
 
-# (2048, 1, True): 2048^2 complex64 is exactly the 16 MiB limit; 32 is the smallest grid
+# (2048, 1, True) and (1024, 2, False) are exactly the 32 MiB limit; 32 is the smallest grid
 @pytest.mark.parametrize("N,nk,fp32", [(256, 4, False), (1024, 2, True), (64, 3, False),
-                                       (32, 1, True), (2048, 1, True)])
+                                       (32, 1, True), (2048, 1, True), (1024, 2, False)])
 def test_noalloc_fft2_matches_planned_fft2_on_calls_in_a_row(env, N, nk, fp32):
     torch, dbar = env
     plan = dbar.Plan(N, 4.0, prec="mixed", max_batch=nk, restart=4)
@@ -56,14 +56,16 @@ def test_noalloc_fft2_matches_planned_fft2_on_calls_in_a_row(env, N, nk, fp32):
 
 def test_noalloc_fft2_rejects_sizes_beyond_its_scratch(env):
     torch, dbar = env
-    N, nk = 1024, 2                                           # 2 x 1024^2 complex128 = 32 MiB > 16 MiB
+    N, nk = 1024, 3                                           # 3 x 1024^2 complex128 = 48 MiB > 32 MiB
     x = torch.zeros((nk, N, N), dtype=torch.complex128, device="cuda")
     with pytest.raises(dbar.DbarError) as e:
         dbar.dbar_fft2_noalloc(N, nk, x, x, -1, False)
     assert e.value.status == dbar.DBAR_EINVAL
 
 
-@pytest.mark.parametrize("N,nk,fp32", [(2048, 2, True), (2048, 1, False), (96, 1, True), (4096, 1, True)])
+# 64 MiB, 64 MiB, 36 MiB: just above the limit; then grids outside [32, 2048] or not powers of two
+@pytest.mark.parametrize("N,nk,fp32", [(2048, 2, True), (2048, 1, False), (512, 9, False), (96, 1, True),
+                                       (4096, 1, True), (16, 1, True)])
 def test_noalloc_fft2_rejects_bad_sizes(env, N, nk, fp32):
     torch, dbar = env
     x = torch.zeros(16, dtype=torch.complex64, device="cuda")  # never touched: rejected before launch
