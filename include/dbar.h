@@ -145,6 +145,12 @@ typedef struct {
                         max_batch slots (or one slot) fails with DBAR_ENOMEM.
                         Plan creation briefly takes 2(M+1) FP64 fields more
                         for building its tables                               */
+  int support_skip;  /* DBAR_MIXED, one potential per plan, Sec. 4 equation: 1
+                        (default): the FP32 inner operator skips the grid
+                        columns (and its column pass the rows) on which Q is
+                        exactly zero in FP32, where w = E_k Q conj(h) is exactly
+                        zero -- the same values, less work and traffic for a
+                        potential concentrated near the origin; 0: every column */
 } dbar_params;
 
 typedef struct dbar_plan* dbar_plan_t;
@@ -152,7 +158,7 @@ typedef struct dbar_plan* dbar_plan_t;
 /* Defaults for a grid: M = 2, DBAR_MIXED, restart 32, tol 1e-12,
  * inner_tol 1e-6, max_outer 40, max_iter 4000, analytic fill,
  * DBAR_RESID_DOUBLE_FLOAT, graphs on, autotune on, sstep 0 (automatic),
- * gauss_w 1, no memory budget. */
+ * gauss_w 1, no memory budget, support_skip 1. */
 void dbar_params_init(dbar_params* p, int N, double L);
 
 /* Message describing the calling thread's most recent failure ("" if none). */

@@ -288,6 +288,25 @@ cudaError_t launch_cast_fields(const cx<double>* in, cx<float>* out, long long n
   return cudaGetLastError();
 }
 
+// Support of an FP32 potential: colf[x] = 1 if some Q[y][x] != 0, rowf[y] = 1 if some
+// Q[y][x] != 0 (flags zeroed beforehand; concurrent writes store the same 1).
+__global__ void k_q_support(const cx<float>* __restrict__ Q, int N, int* colf, int* rowf) {
+  const long long n = (long long)N * N;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const cx<float> v = Q[i];
+    if (v.re != 0.f || v.im != 0.f) {
+      colf[i % N] = 1;
+      rowf[i / N] = 1;
+    }
+  }
+}
+cudaError_t launch_q_support(const cx<float>* Q, int N, int* flags, cudaStream_t s) {
+  const long long n = (long long)N * N;
+  const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+  k_q_support<<<blocks, 256, 0, s>>>(Q, N, flags, flags + N);
+  return cudaGetLastError();
+}
+
 __global__ void k_split_fields(const cx<double>* __restrict__ in, cx<dd>* __restrict__ out, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     out[i] = ccast<dd>(in[i]);

@@ -46,14 +46,18 @@ cudaError_t launch_pass_b_n(const PassArgs<T>& a, int nslots, cudaStream_t s) {
     const size_t sm = align16((size_t)2 * G::COLS * G::P * sizeof(cx<T>)) + (size_t)2 * (a.M + 2) * sizeof(cx<T>);
     cudaError_t e = set_smem(k_pass_b2<T, LOGN>, sm);
     if (e != cudaSuccess) return e;
-    k_pass_b2<T, LOGN><<<dim3((nslots + 1) / 2, G::N / G::COLS), G::THREADS, sm, s>>>(a, nslots);
+    const int ntile = (a.sx1 - a.sx0) / G::COLS;  // column tiles of the potential's support
+    if (ntile <= 0) return cudaSuccess;
+    k_pass_b2<T, LOGN><<<dim3((nslots + 1) / 2, ntile), G::THREADS, sm, s>>>(a, nslots);
     return cudaGetLastError();
   }
   using G = ColG<T, LOGN, CV>;
   const size_t sm = align16((size_t)G::COLS * G::P * sizeof(cx<T>)) + (size_t)(a.M + 2) * sizeof(cx<T>);
   cudaError_t e = set_smem(k_pass_b<T, LOGN, MODE, CV>, sm);
   if (e != cudaSuccess) return e;
-  k_pass_b<T, LOGN, MODE, CV><<<dim3(nslots, G::N / G::COLS), G::THREADS, sm, s>>>(a);
+  const int ntile = (a.sx1 - a.sx0) / G::COLS;  // column tiles of the potential's support
+  if (ntile <= 0) return cudaSuccess;
+  k_pass_b<T, LOGN, MODE, CV><<<dim3(nslots, ntile), G::THREADS, sm, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -125,5 +125,13 @@ cudaError_t launch_conv_sum(const cx<double>* f, const cx<double>* Kt, int N, co
 cudaError_t launch_cast_fields(const cx<double>* in, cx<float>* out, long long n, cudaStream_t s);
 cudaError_t launch_split_fields(const cx<double>* in, cx<dd>* out, long long n, cudaStream_t s);
 cudaError_t launch_check_finite(const double* p, long long n, int* flag, cudaStream_t s);
+// flags[x] = 1 where column x of Q has a nonzero entry, flags[N + y] = 1 where row y has
+// one ([2N], zeroed beforehand)
+cudaError_t launch_q_support(const cx<float>* Q, int N, int* flags, cudaStream_t s);
+// column-pass tiles of every variant at N are aligned to this many columns
+inline int col_align(int N) {
+  const int l = ilog2(N), c0 = col_cols(l, 8, 0), c1 = col_cols(l, 8, 1);
+  return c0 > c1 ? c0 : c1;
+}
 
 }  // namespace dbar

@@ -92,6 +92,7 @@ dbar_status run(int N, int nk, const void* in, void* out, int sign, void* scratc
   PassArgs<T> a;
   std::memset(&a, 0, sizeof(a));
   a.g = make_geo<T>(N);
+  a.sx1 = a.sy1 = N;  // every column and row
   a.tw = tw + (N - (1 << kMinLog));
   a.in = reinterpret_cast<const cx<T>*>(in);
   a.in_ss = (long long)N * N;

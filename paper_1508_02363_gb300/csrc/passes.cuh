@@ -178,8 +178,12 @@ __device__ __forceinline__ void row_a(const PassArgs<T>& a, cx<T> (&v)[16], int 
     }
   }
   fft_line<T, LOGN, true, std::is_same<T, float>::value>(v, sl, t, a.tw);
+  // only the columns the column pass reads (those where Q is not zero)
 #pragma unroll
-  for (int q = 0; q < 16; ++q) dst[q * TPL] = v[q];
+  for (int q = 0; q < 16; ++q) {
+    const int x = t + q * TPL;
+    if (x >= a.sx0 && x < a.sx1) dst[q * TPL] = v[q];
+  }
 }
 
 // SH: the shifted quotient of the iterated equation (a.dshift set)
@@ -220,8 +224,12 @@ __global__ void __launch_bounds__(RowG<T, LOGN>::THREADS, RowG<T, LOGN>::MINB) k
   cx<T>* sl = reinterpret_cast<cx<T>*>(smem) + line * P;
   cx<T> v[16];
   const cx<T>* src = a.in + (size_t)slot * a.in_ss + (size_t)p2 * N + t;
+  // columns outside the potential's support are exactly zero (not stored by the column pass)
 #pragma unroll
-  for (int q = 0; q < 16; ++q) v[q] = ldg(src + q * TPL);
+  for (int q = 0; q < 16; ++q) {
+    const int x = t + q * TPL;
+    v[q] = (x >= a.sx0 && x < a.sx1) ? ldg(src + q * TPL) : mkc((T)0, (T)0);
+  }
   fft_line<T, LOGN, false, std::is_same<T, float>::value>(v, sl, t, a.tw);
   cx<T>* kp = reinterpret_cast<cx<T>*>(a.out) + (size_t)slot * a.out_ss + (size_t)p2 * N + t;
 #pragma unroll
@@ -256,7 +264,7 @@ __global__ void __launch_bounds__(ColG<T, LOGN, CV>::THREADS, ColG<T, LOGN, CV>:
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int c = (warp / G::WPG) * G::CW + lane % G::CW;
   const int t = (warp % G::WPG) * G::TW + lane / G::CW;
-  const int j1 = blockIdx.y * G::COLS + c;
+  const int j1 = a.sx0 + blockIdx.y * G::COLS + c;  // the column tiles of the potential's support
   cx<T>* sl = reinterpret_cast<cx<T>*>(smem) + c * P;
   constexpr size_t off = ((size_t)G::COLS * P * sizeof(cx<T>) + 15) & ~(size_t)15;
   cx<T>* coef = reinterpret_cast<cx<T>*>(smem + off);  // [M+1] c_n, then the fill d'
@@ -282,7 +290,10 @@ __global__ void __launch_bounds__(ColG<T, LOGN, CV>::THREADS, ColG<T, LOGN, CV>:
       const cx<T> cn = coef[n];
       const cx<T>* D = a.Delta + ((size_t)n * N + t) * N + j1;
 #pragma unroll
-      for (int q = 0; q < 16; ++q) v[q] = v[q] + cmul(cn, ldg(D + (size_t)q * TPL * N));
+      for (int q = 0; q < 16; ++q) {
+        const int y = t + q * TPL;  // operator: rows where Q = 0 give w = 0 below
+        if (MODE != PB_MATVEC || (y >= a.sy0 && y < a.sy1)) v[q] = v[q] + cmul(cn, ldg(D + (size_t)q * TPL * N));
+      }
     }
   }
   if (MODE == PB_MATVEC || MODE == PB_RHS || MODE == PB_W) {
@@ -292,6 +303,11 @@ __global__ void __launch_bounds__(ColG<T, LOGN, CV>::THREADS, ColG<T, LOGN, CV>:
     const cx<T>* QC = a.Q + (size_t)slot * a.q_ss + (size_t)t * N + j1;
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
+      const int y = t + q * TPL;
+      if (MODE == PB_MATVEC && !(y >= a.sy0 && y < a.sy1)) {
+        v[q] = mkc((T)0, (T)0);  // Q = 0 on this row: w = 0 exactly
+        continue;
+      }
       const cx<T> eq = cmul(cmul(exv, ldg(EY + q * TPL)), ldg(QC + (size_t)q * TPL * N));
       v[q] = (MODE == PB_RHS) ? eq : cmulc(eq, v[q]);
     }
@@ -321,7 +337,7 @@ __global__ void __launch_bounds__(ColG<T, LOGN, 0>::THREADS, 1) k_pass_b2(const 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int c = (warp / G::WPG) * G::CW + lane % G::CW;
   const int t = (warp % G::WPG) * G::TW + lane / G::CW;
-  const int j1 = blockIdx.y * G::COLS + c;
+  const int j1 = a.sx0 + blockIdx.y * G::COLS + c;  // the column tiles of the potential's support
   cx<T>* la = reinterpret_cast<cx<T>*>(smem) + c * P;
   cx<T>* lb = la + G::COLS * P;
   constexpr size_t off = ((size_t)2 * G::COLS * P * sizeof(cx<T>) + 15) & ~(size_t)15;
@@ -356,9 +372,12 @@ __global__ void __launch_bounds__(ColG<T, LOGN, 0>::THREADS, 1) k_pass_b2(const 
     const cx<T>* D = a.Delta + ((size_t)n * N + t) * N + j1;
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
-      const cx<T> d = ldg(D + (size_t)q * TPL * N);
-      va[q] = va[q] + cmul(ca, d);
-      vb[q] = vb[q] + cmul(cb, d);
+      const int y = t + q * TPL;  // rows where Q = 0 give w = 0 below
+      if (y >= a.sy0 && y < a.sy1) {
+        const cx<T> d = ldg(D + (size_t)q * TPL * N);
+        va[q] = va[q] + cmul(ca, d);
+        vb[q] = vb[q] + cmul(cb, d);
+      }
     }
   }
   {
@@ -370,6 +389,12 @@ __global__ void __launch_bounds__(ColG<T, LOGN, 0>::THREADS, 1) k_pass_b2(const 
     const cx<T>* QB = a.Q + (size_t)s1 * a.q_ss + (size_t)t * N + j1;
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
+      const int y = t + q * TPL;
+      if (!(y >= a.sy0 && y < a.sy1)) {  // Q = 0 on this row: w = 0 exactly
+        va[q] = mkc((T)0, (T)0);
+        vb[q] = mkc((T)0, (T)0);
+        continue;
+      }
       const cx<T> qa = ldg(QA + (size_t)q * TPL * N);
       const cx<T> qb = a.q_ss ? ldg(QB + (size_t)q * TPL * N) : qa;
       va[q] = cmulc(cmul(cmul(xa, ldg(EA + q * TPL)), qa), va[q]);
@@ -506,8 +531,12 @@ __global__ void __launch_bounds__(RowG<T, LOGN>::THREADS, RowG<T, LOGN>::MINB) k
   cx<T>* sl = reinterpret_cast<cx<T>*>(smem) + line * P;
   const cx<T>* src = a.in + (size_t)slot * a.in_ss + (size_t)p2 * N + t;
   cx<T> v[16];
+  // columns outside the potential's support are exactly zero (not stored by the column pass)
 #pragma unroll
-  for (int q = 0; q < 16; ++q) v[q] = ldg(src + q * TPL);
+  for (int q = 0; q < 16; ++q) {
+    const int x = t + q * TPL;
+    v[q] = (x >= a.sx0 && x < a.sx1) ? ldg(src + q * TPL) : mkc((T)0, (T)0);
+  }
   fft_line<T, LOGN, MODE == PC_INV, std::is_same<T, float>::value>(v, sl, t, a.tw);
   // squared-norm partials.  FP64 for FP64 fields and for the right-hand side
   // (once per solve); the double-float residual sums FP32 squares of r scaled

@@ -206,6 +206,11 @@ struct dbar_plan {
   int* dshift = nullptr;        // [B][2] the same offsets signed, in (-N/2, N/2] (pass A's divisor)
   int* h_dshift = nullptr;      // [B][2] host staging
   int* h_err = nullptr;         // pinned copy of flag[1]: a bounded device wait ran out
+  // support of the potential in FP32 (Q32 exactly zero outside): columns [sx0, sx1), aligned
+  // to every column-pass tile width, and rows [sy0, sy1); used by the FP32 inner operator
+  bool sup = false;
+  int sx0 = 0, sx1 = 0, sy0 = 0, sy1 = 0;
+  int* supflag = nullptr;       // [2N] device: column, then row flags of the support scan
   const cx<double>* x0d = nullptr;  // FP64 initial guesses of the batch being started (device), or none
   void* It1 = nullptr;          // [B][n] rolled field (FP64-sized)
   void* It2 = nullptr;          // [B][n] first operator application (FP64-sized)
@@ -292,6 +297,7 @@ extern "C" void dbar_params_init(dbar_params* p, int N, double L) {
   p->autotune = 1;
   p->gauss_w = 1.0;
   p->mem_budget = 0;
+  p->support_skip = 1;
 }
 
 extern "C" const char* dbar_last_error(void) { return g_last_error.c_str(); }
@@ -422,6 +428,7 @@ PassArgs<double> base_args<double>(const dbar_plan* P) {
   PassArgs<double> a;
   std::memset(&a, 0, sizeof(a));
   a.g = make_geo<double>(P->N);
+  a.sx1 = a.sy1 = P->N;
   a.M = P->M;
   a.tw = P->tw64;
   a.Da = P->Da64;
@@ -448,6 +455,7 @@ PassArgs<float> base_args<float>(const dbar_plan* P) {
   std::memset(&a, 0, sizeof(a));
   a.colv = P->colv;
   a.g = make_geo<float>(P->N);
+  a.sx1 = a.sy1 = P->N;
   a.M = P->Min;
   a.tw = P->tw32;
   a.Da = P->Da32;
@@ -474,6 +482,7 @@ PassArgs<dd> base_args<dd>(const dbar_plan* P) {
   PassArgs<dd> a;
   std::memset(&a, 0, sizeof(a));
   a.g = make_geo<dd>(P->N);
+  a.sx1 = a.sy1 = P->N;
   a.M = P->M;
   a.tw = P->tw_dd;
   a.Da = P->Da_dd;
@@ -498,6 +507,21 @@ PassArgs<dd> base_args<dd>(const dbar_plan* P) {
 // E = 1 in the column pass: per-slot rows of ones in place of the slot's E_k
 // factors (K_0 of the iterated equation, its right-hand side); the same layout
 // keeps the column pass's indexing unchanged
+// The FP32 inner operator's passes skip the columns (and pass B the rows) where the
+// potential is exactly zero in FP32: there w = E_k Q conj(h) = 0, so the skipped work
+// is exactly zero (the same values as the full passes).
+template <typename T>
+static void set_support(const dbar_plan* P, PassArgs<T>& a) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (P->sup) {
+      a.sx0 = P->sx0;
+      a.sx1 = P->sx1;
+      a.sy0 = P->sy0;
+      a.sy1 = P->sy1;
+    }
+  }
+}
+
 template <typename T>
 static void set_unit_e(const dbar_plan* P, PassArgs<T>& a) {
   if constexpr (std::is_same<T, float>::value) a.ex = a.ey = P->ones32;
@@ -566,6 +590,7 @@ static dbar_status apply_K(dbar_plan* P, const cx<T>* S, long long s_ss, const d
   a.dshift = dshift;
   if (unitE) set_unit_e(P, a);
   a.neg = neg;
+  set_support(P, a);
   if constexpr (std::is_same<T, double>::value) {
     if (P->conv) {  // convolution regularisation: T2 from the direct-sum route, then pass C
       dbar_status s = conv_to_T2(P, S, s_ss, scale, scale_ss, run, nb, st);
@@ -740,7 +765,8 @@ static dbar_status true_residual(dbar_plan* P, int nb, cudaStream_t st) {
 }
 
 // Algorithmic bytes of one finished cycle (profiling only): every field the
-// method reads or writes counted once per use, F = one inner-precision field,
+// method reads or writes counted once per use (the FP32 pass intermediates T1
+// and T2 on the potential's support columns only), F = one inner-precision field,
 // F64 = one FP64 field.  Per Krylov step j of a slot: pass A 2F (read v_j,
 // write T1), pass B 2F (read T1, write T2), pass C 2F (read T2, write K v_j),
 // dots (j+2)F (v_0..v_j and K v_j), update (j+3)F (the same, plus the new
@@ -754,6 +780,8 @@ static dbar_status true_residual(dbar_plan* P, int nb, cudaStream_t st) {
 static void account_cycle(dbar_plan* P, const int* act, const int* ns, int nb, int launched_steps) {
   if (!P->prof.on) return;
   const double F = (double)P->n * P->inner_elem(), F64 = (double)P->n * sizeof(cx<double>);
+  const double fx = P->sup ? (double)(P->sx1 - P->sx0) / P->N : 1.0;
+  const double fy = P->sup ? (double)(P->sy1 - P->sy0) / P->N : 1.0;
   double* by = P->prof.bytes;
   int nact = 0;
   for (int s = 0; s < nb; ++s) {
@@ -772,24 +800,25 @@ static void account_cycle(dbar_plan* P, const int* act, const int* ns, int nb, i
       by[K_RES_C] += 3.0 * F64 + F;
       continue;
     }
+    // the pass intermediates T1, T2 hold only the support's columns (fraction fx)
     if (P->sstep > 1) {
       // per block at J = b S + 1: S applications of K, dots (J + S) F,
       // update (J + 2S) F; the last block of the cycle counts in full
       const int S = P->sstep, nblk = (k + S - 1) / S;
       for (int b = 0; b < nblk; ++b) {
         const int J = b * S + 1;
-        by[K_PASS_A] += 2.0 * F;            // v_{J-1} -> T1
-        by[K_PASS_B] += 2.0 * F * S;
-        by[K_PASS_CA] += 3.0 * F * (S - 1);  // T2 -> K p_i and T1
-        by[K_PASS_C] += 2.0 * F;
+        by[K_PASS_A] += (1.0 + fx) * F;            // v_{J-1} -> T1
+        by[K_PASS_B] += 2.0 * fx * F * S;
+        by[K_PASS_CA] += (1.0 + 2.0 * fx) * F * (S - 1);  // T2 -> K p_i and T1
+        by[K_PASS_C] += (1.0 + fx) * F;
         by[K_DOTS] += F * (J + S);
         by[K_UPDATE] += F * (J + 2 * S);
       }
       by[K_UPDATE] += 2.0 * F64;  // x read and written by the slot's last update sweep
     } else {
-      by[K_PASS_A] += 2.0 * F * k;
-      by[K_PASS_B] += 2.0 * F * k;
-      by[K_PASS_C] += 2.0 * F * k;
+      by[K_PASS_A] += (1.0 + fx) * F * k;
+      by[K_PASS_B] += 2.0 * fx * F * k;
+      by[K_PASS_C] += (1.0 + fx) * F * k;
       by[K_DOTS] += F * (k * 2.0 + k * (k - 1) / 2.0);
       by[K_UPDATE] += F * (k * 3.0 + k * (k - 1) / 2.0);
     }
@@ -799,7 +828,8 @@ static void account_cycle(dbar_plan* P, const int* act, const int* ns, int nb, i
     by[K_RES_C] += 3.0 * F64 + F;
   }
   if (P->conv) return;
-  by[K_PASS_B] += (double)launched_steps * ((P->mixed ? P->Min : P->M) + 2) * F;
+  // shared tables Q, Delta_n per launch, on the support's columns and rows
+  by[K_PASS_B] += (double)launched_steps * ((P->mixed ? P->Min : P->M) + 2) * F * fx * fy;
   if (nact) by[K_RES_B] += (P->M + 2) * F64;
 }
 
@@ -886,6 +916,7 @@ static dbar_status block_steps(dbar_plan* P, int nb, int j0, int j1, cudaStream_
     // per step the coefficients and pass B, then pass C fused with the next
     // step's pass A (the last step: pass C alone)
     PassArgs<TI> a = base_args<TI>(P);
+    set_support(P, a);
     a.run = P->cs.run;
     a.in = V + (size_t)(J - 1) * n;
     a.in_ss = vss;
@@ -1140,6 +1171,7 @@ static dbar_status check_params(const dbar_params* p) {
   if (p->iterated != 0 && p->iterated != 1) return fail(DBAR_EINVAL, "iterated must be 0 or 1");
   if (p->inner_M < 0 || p->inner_M > p->M) return fail(DBAR_EINVAL, "inner_M must be in [0, M]");
   if (!(p->gauss_w > 0.0) || !std::isfinite(p->gauss_w)) return fail(DBAR_EINVAL, "gauss_w must be finite and > 0");
+  if (p->support_skip != 0 && p->support_skip != 1) return fail(DBAR_EINVAL, "support_skip must be 0 or 1");
   if (p->regularisation != DBAR_REG_TAYLOR && p->regularisation != DBAR_REG_CONV)
     return fail(DBAR_EINVAL, "regularisation must be DBAR_REG_TAYLOR or DBAR_REG_CONV");
   if (p->regularisation == DBAR_REG_CONV) {
@@ -1469,6 +1501,7 @@ static cudaError_t alloc_workspaces(dbar_plan* P, int B, const char** what) {
     AL(P->Cv2, (size_t)B * 2 * n);
   }
   AL(P->flag, 4);
+  AL(P->supflag, 2 * (size_t)P->N);
   AL(P->kdev, 2 * (size_t)B);
   CycleState& c = P->cs;
   const int m = P->m;
@@ -1688,10 +1721,35 @@ static dbar_status load_Q_device(dbar_plan* P, const cx<double>* Qd, cudaStream_
   CK(timed(P, st, K_OTHER, [&] { return launch_check_finite(reinterpret_cast<const double*>(Qd), 2 * P->n, P->flag, st); }));
   CK(timed(P, st, K_OTHER, [&] { return launch_load_q(Qd, P->Q64, P->Q32, P->N, st); }));
   if (P->resid_dd) CK(timed(P, st, K_OTHER, [&] { return launch_split_fields(P->Q64, P->Q_dd, P->n, st); }));
+  // support of the FP32 potential (the inner operator skips the columns and rows where it is zero)
+  const bool scan = P->mixed && !P->per_slot_q && !P->iter && !P->conv && P->p.support_skip;
+  std::vector<int> fl(scan ? 2 * P->N : 0);
+  if (scan) {
+    CK(cudaMemsetAsync(P->supflag, 0, 2 * (size_t)P->N * sizeof(int), st));
+    CK(timed(P, st, K_OTHER, [&] { return launch_q_support(P->Q32, P->N, P->supflag, st); }));
+    CK(cudaMemcpyAsync(fl.data(), P->supflag, 2 * (size_t)P->N * sizeof(int), cudaMemcpyDeviceToHost, st));
+  }
   int bad = 0;
   CK(cudaMemcpyAsync(&bad, P->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   if (bad) return fail(DBAR_EINVAL, "Q has a non-finite entry");
+  P->sup = scan;
+  if (scan) {
+    const int N = P->N, A = col_align(N);
+    int x0 = N, x1 = -1, y0 = N, y1 = -1;
+    for (int i = 0; i < N; ++i) {
+      if (fl[i]) x0 = std::min(x0, i), x1 = i;
+      if (fl[N + i]) y0 = std::min(y0, i), y1 = i;
+    }
+    if (x1 < 0) {  // Q = 0 in FP32: the inner operator is zero
+      P->sx0 = P->sx1 = P->sy0 = P->sy1 = 0;
+    } else {
+      P->sx0 = (x0 / A) * A;
+      P->sx1 = std::min(N, ((x1 + A) / A) * A);
+      P->sy0 = y0;
+      P->sy1 = y1 + 1;
+    }
+  }
   return DBAR_OK;
 }
 

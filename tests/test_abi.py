@@ -48,7 +48,7 @@ def test_parameter_validation_is_host_side(lib):
                 dict(regularisation=1), dict(regularisation=1, prec=0, N=512),
                 dict(regularisation=1, prec=0, iterated=1),
                 dict(regularisation=1, prec=0, max_batch=5000), dict(inner_M=3), dict(inner_M=-1), dict(autotune=4),
-                dict(gauss_w=0.0), dict(gauss_w=-1.0), dict(gauss_w=float("nan"))):
+                dict(gauss_w=0.0), dict(gauss_w=-1.0), dict(gauss_w=float("nan")), dict(support_skip=2)):
         args = dict(N=64, L=4.0)
         args.update(bad)
         p = dbar.dbar_params_init(args.pop("N"), args.pop("L"), **args)
@@ -63,7 +63,7 @@ def test_params_defaults_and_solve_signature(lib):
     # the struct as the header lays it out, filled by the library's own defaults
     from paper_1508_02363_gb300 import dbar
     p = dbar.dbar_params_init(128, 5.0)
-    assert (p.N, p.L, p.M, p.restart, p.gauss_w, p.mem_budget) == (128, 5.0, 2, 32, 1.0, 0)
+    assert (p.N, p.L, p.M, p.restart, p.gauss_w, p.mem_budget, p.support_skip) == (128, 5.0, 2, 32, 1.0, 0, 1)
     # dbar_solve_cgo(plan, Q, nk, k, x0, S_out, m_out, iters, resid, io_on_device, stream):
     # eleven arguments, a NULL plan answered on the host
     assert len(lib.dbar_solve_cgo.argtypes or dbar._lib.dbar_solve_cgo.argtypes) == 11

@@ -145,3 +145,26 @@ def test_memory_budget_bounds_the_plan(dbar):
         with pytest.raises(dbar.DbarError) as e:
             dbar.Plan(w.N, w.L, M=2, prec="mixed", restart=16, **bad)
         assert e.value.status == dbar.DBAR_ENOMEM, bad
+
+
+@pytest.mark.parametrize("N,L,nk", [(256, 8.0, 5), (1024, 10.0, 3)])
+def test_support_skip_gives_the_same_solution(dbar, N, L, nk):
+    # A potential concentrated near the origin (narrow Gaussians): Q is exactly zero in
+    # FP32 on most columns and rows of the box, where the FP32 inner operator skips its
+    # work; the solution is the same as with every column processed, value for value
+    rng = np.random.default_rng(31)
+    Q = wl.gaussian_mixture(N, L, rng.uniform(-1.5, 1.5, (3, 2)), rng.uniform(0.4, 0.8, 3),
+                            rng.uniform(1, 3, 3) * np.exp(2j * np.pi * rng.uniform(size=3)))
+    Q32 = Q.astype(np.complex64)
+    cols = np.flatnonzero(np.any(Q32 != 0, axis=0))
+    assert cols.size < 0.6 * N                     # the skip is in effect
+    k = wl.random_k_disc(rng, nk, 3.0)
+    kw = dict(M=2, prec="mixed", restart=16, tol=1e-12, max_batch=nk)
+    r = dbar.Plan(N, L, **kw).solve(Q, k, want_m=False)
+    r0 = dbar.Plan(N, L, support_skip=0, **kw).solve(Q, k, want_m=False)
+    assert r["status"] == dbar.DBAR_OK
+    assert np.array_equal(r["S"], r0["S"]) and np.array_equal(r["iters"], r0["iters"])
+    if N <= 256:
+        for i in range(nk):
+            o = orc.solve_cgo(Q, k[i], N, L, M=2, tol=1e-14, restart=60)
+            assert rel(r["S"][i], o["S"]) < 1e-10, i
