@@ -291,8 +291,8 @@ __global__ void __launch_bounds__(ColG<T, LOGN, CV>::THREADS, ColG<T, LOGN, CV>:
       const cx<T>* D = a.Delta + ((size_t)n * N + t) * N + j1;
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
-        const int y = t + q * TPL;  // operator: rows where Q = 0 give w = 0 below
-        if (MODE != PB_MATVEC || (y >= a.sy0 && y < a.sy1)) v[q] = v[q] + cmul(cn, ldg(D + (size_t)q * TPL * N));
+        const int y = t + q * TPL;  // operator and its first half: rows where Q = 0 give w = 0 below
+        if (MODE == PB_HOUT || (y >= a.sy0 && y < a.sy1)) v[q] = v[q] + cmul(cn, ldg(D + (size_t)q * TPL * N));
       }
     }
   }
@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(ColG<T, LOGN, CV>::THREADS, ColG<T, LOGN, CV>:
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       const int y = t + q * TPL;
-      if (MODE == PB_MATVEC && !(y >= a.sy0 && y < a.sy1)) {
+      if (!(y >= a.sy0 && y < a.sy1)) {
         v[q] = mkc((T)0, (T)0);  // Q = 0 on this row: w = 0 exactly
         continue;
       }

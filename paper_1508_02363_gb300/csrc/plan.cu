@@ -509,10 +509,12 @@ PassArgs<dd> base_args<dd>(const dbar_plan* P) {
 // keeps the column pass's indexing unchanged
 // The FP32 inner operator's passes skip the columns (and pass B the rows) where the
 // potential is exactly zero in FP32: there w = E_k Q conj(h) = 0, so the skipped work
-// is exactly zero (the same values as the full passes).
+// is exactly zero (the same values as the full passes).  The double-float copy of Q
+// is a pair of floats, zero exactly where the FP32 copy is, so the double-float
+// right-hand side and residual passes skip the same columns and rows.
 template <typename T>
 static void set_support(const dbar_plan* P, PassArgs<T>& a) {
-  if constexpr (std::is_same<T, float>::value) {
+  if constexpr (std::is_same<T, float>::value || std::is_same<T, dd>::value) {
     if (P->sup) {
       a.sx0 = P->sx0;
       a.sx1 = P->sx1;
@@ -669,6 +671,7 @@ static dbar_status h_of_S64(dbar_plan* P, const cx<double>* S, long long s_ss, c
 template <typename TC, typename TI>
 static dbar_status build_rhs_t(dbar_plan* P, int nb, cudaStream_t st, const int* dmask) {
   PassArgs<TC> a = base_args<TC>(P);
+  set_support(P, a);
   a.run = dmask;
   if (P->iter) set_unit_e(P, a);  // iterated equation: b = -i F(q)
   a.out = P->T2;
@@ -694,6 +697,7 @@ static dbar_status true_residual_t(dbar_plan* P, int nb, cudaStream_t st) {
     if constexpr (std::is_same<TC, double>::value)
       if (P->conv) return conv_to_T2(P, in, n, nullptr, 0, P->cs.active, nb, st);
     PassArgs<TC> a = base_args<TC>(P);
+    set_support(P, a);
     a.run = P->cs.active;
     a.dshift = dshift;
     if (unitE) set_unit_e(P, a);
@@ -720,6 +724,7 @@ static dbar_status true_residual_t(dbar_plan* P, int nb, cudaStream_t st) {
   const cx<TC>* x = reinterpret_cast<const cx<TC>*>(P->x64);  // x stored in TC (FP64 or double-float)
   dbar_status s;
   PassArgs<TC> c = base_args<TC>(P);
+  set_support(P, c);
   c.run = P->cs.active;
   c.in_ss = n;
   if (P->iter) {
@@ -782,6 +787,8 @@ static void account_cycle(dbar_plan* P, const int* act, const int* ns, int nb, i
   const double F = (double)P->n * P->inner_elem(), F64 = (double)P->n * sizeof(cx<double>);
   const double fx = P->sup ? (double)(P->sx1 - P->sx0) / P->N : 1.0;
   const double fy = P->sup ? (double)(P->sy1 - P->sy0) / P->N : 1.0;
+  // the double-float residual passes skip the same columns and rows (FP64 ones do not)
+  const double rx = P->resid_dd ? fx : 1.0, ry = P->resid_dd ? fy : 1.0;
   double* by = P->prof.bytes;
   int nact = 0;
   for (int s = 0; s < nb; ++s) {
@@ -823,14 +830,14 @@ static void account_cycle(dbar_plan* P, const int* act, const int* ns, int nb, i
       by[K_UPDATE] += F * (k * 3.0 + k * (k - 1) / 2.0);
     }
     if (P->sstep <= 1) by[K_XUPDATE] += F * k + 2.0 * F64;
-    by[K_RES_A] += 2.0 * F64;
-    by[K_RES_B] += 2.0 * F64;
-    by[K_RES_C] += 3.0 * F64 + F;
+    by[K_RES_A] += (1.0 + rx) * F64;
+    by[K_RES_B] += 2.0 * rx * F64;
+    by[K_RES_C] += (2.0 + rx) * F64 + F;
   }
   if (P->conv) return;
   // shared tables Q, Delta_n per launch, on the support's columns and rows
   by[K_PASS_B] += (double)launched_steps * ((P->mixed ? P->Min : P->M) + 2) * F * fx * fy;
-  if (nact) by[K_RES_B] += (P->M + 2) * F64;
+  if (nact) by[K_RES_B] += (P->M + 2) * F64 * rx * ry;
 }
 
 // Starts slots: x = 0, b = -i F(E_k Q), first cycle state.  hmask == nullptr:
