@@ -219,6 +219,31 @@ dbar_status dbar_solve_cgo(dbar_plan_t plan, const double* Q, int nk, const doub
                            const double* x0, double* S_out, double* m_out, int* iters,
                            double* resid, int io_on_device, void* stream);
 
+/* Uneven batches: many CGO solves (Sec. 4.3 with Q -> E_k Q, Sec. 5.1) on
+ * grids of different sizes or with different potentials, one plan per grid.
+ * Each batch is one dbar_solve_cgo call (same arguments, same results); the
+ * batches of different plans run at the same time, one host thread and one
+ * CUDA stream per plan, so that the launches of different grids overlap on
+ * the GPU; batches of the same plan run in list order.  Work queued on
+ * `stream` before the call finishes first; the call returns when every batch
+ * is done.  Each batch's own status is written to its `status`; the call
+ * returns the first failure in list order, else DBAR_ENOCONV if a batch missed
+ * tol, else DBAR_OK.  A plan must not be used by another thread meanwhile. */
+typedef struct {
+  dbar_plan_t plan;   /* the grid (and settings) of this batch                     */
+  const double* Q;    /* as dbar_solve_cgo                                          */
+  int nk;
+  const double* k;
+  const double* x0;
+  double* S_out;
+  double* m_out;
+  int* iters;
+  double* resid;
+  int io_on_device;
+  dbar_status status; /* out: this batch's result                                   */
+} dbar_batch;
+dbar_status dbar_solve_batches(dbar_batch* batches, int nbatch, void* stream);
+
 /* DS II reflection coefficient (Sec. 6.1, eq. MainEQDSpm, hpmdef, rviah,
  * m1def; time dependence eq. rt).  Sec. 6 replaces k by k/2, so for each k the
  * plan solves the CGO problem of dbar_solve_cgo at the parameter k/2 twice,
@@ -393,6 +418,17 @@ dbar_status dbar_profile_read(dbar_plan_t plan, int kind, double* ms, long long*
  * per launch of each variant in ms_per_variant[DBAR_COLUMN_VARIANTS] (0 when
  * not tuned).  Any pointer may be NULL. */
 dbar_status dbar_plan_tuning(dbar_plan_t plan, int* column_variant, double* ms_per_variant);
+
+/* Test hook for the device-side bounded waits (no counterpart in the paper):
+ * the next block-update launch of this plan announces 16 bytes more on its
+ * first bulk-copy stage than the copy delivers, so that stage's mbarrier phase
+ * cannot complete and every wait on it runs out (2^18 try_wait rounds, about
+ * a second, then as long again while the block drains its copies).  The solve
+ * in progress returns DBAR_ETIMEOUT at its next cycle boundary; the plan drops
+ * its captured cycle graphs and solves normally afterwards.  Nothing faults or
+ * hangs.  Plans with s-step blocks only (sstep > 1, Sec. 4 equation); else
+ * DBAR_EINVAL. */
+dbar_status dbar_plan_inject_wait_timeout(dbar_plan_t plan);
 
 /* Kernels launched by this plan since its creation (profiling on or off). */
 dbar_status dbar_launch_count(dbar_plan_t plan, long long* count);

@@ -24,6 +24,7 @@ UNITS = ([("kern_pass.cu", f"pass_{t}_{l}", [f"-DDBAR_T={t}", f"-DDBAR_LOGN={l}"
           for t, kind in (("double", 1), ("dd", 2), ("float", 0)) for l in SIZES] +
          [("kern_krylov.cu", "krylov", []), ("dispatch.cu", "dispatch", []), ("plan.cu", "plan", []),
           ("serve.cu", "serve", []), ("noalloc.cu", "noalloc", []), ("conv.cu", "conv", []),
+          ("batches.cu", "batches", []),
           ("kern_aux.cu", "kern_aux", [])])
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # extra nvcc flags (e.g. block-shape macros of csrc/cx.cuh) for tuning builds

@@ -713,7 +713,8 @@ __global__ void __launch_bounds__(KR_THREADS) k_bupdate_bulk(const BlockArgs a, 
     mbar_fence_init();
     // the first KB_STAGES basis vectors of the sweep
     for (int r = 0; r < KB_STAGES && r < J; ++r) {
-      mbar_expect_tx(&bar[r], kBytes);
+      // (a.tx_extra > 0 only under the test hook: that stage's phase cannot complete)
+      mbar_expect_tx(&bar[r], kBytes + (r == 0 ? (uint32_t)a.tx_extra : 0u));
       bulk_g2s(stage + (size_t)r * KB_CHUNK, Vs + (size_t)r * a.n + c0, kBytes, &bar[r]);
     }
   }

@@ -212,6 +212,7 @@ struct dbar_plan {
   int sx0 = 0, sx1 = 0, sy0 = 0, sy1 = 0;
   int* supflag = nullptr;       // [2N] device: column, then row flags of the support scan
   const cx<double>* x0d = nullptr;  // FP64 initial guesses of the batch being started (device), or none
+  int inject_tx = 0;            // test hook: extra bytes announced by the next block-update launch
   void* It1 = nullptr;          // [B][n] rolled field (FP64-sized)
   void* It2 = nullptr;          // [B][n] first operator application (FP64-sized)
   // convolution regularisation (params.regularisation = DBAR_REG_CONV), FP64
@@ -907,6 +908,7 @@ static dbar_status block_steps(dbar_plan* P, int nb, int j0, int j1, cudaStream_
   ba.xss = n;
   ba.x_dd = P->resid_dd ? 1 : 0;
   ba.err = P->flag + 1;
+  ba.tx_extra = 0;
   for (int c0 = j0; c0 < j1; c0 += S) {
     const int J = c0 + 1;  // basis vectors v_0..v_{J-1} exist
     if (P->iter || P->conv) {
@@ -954,7 +956,10 @@ static dbar_status block_steps(dbar_plan* P, int nb, int j0, int j1, cudaStream_
     }
     CK(timed(P, st, K_DOTS, [&] { return launch_bdots<TI, S>(ba, V, vss, J, nb, st); }));
     CK(timed(P, st, K_SCALAR, [&] { return launch_bscalar<S>(ba, P->cs, P->Hraw, P->bcoef, P->upd, J, nb, st); }));
+    ba.tx_extra = P->inject_tx;  // the test hook fires on one launch
+    P->inject_tx = 0;
     CK(timed(P, st, K_UPDATE, [&] { return launch_bupdate<TI, S>(ba, P->upd, V, vss, J, nb, st); }, 2));
+    ba.tx_extra = 0;
   }
   return DBAR_OK;
 }
@@ -1133,6 +1138,9 @@ static dbar_status run_cycles(dbar_plan* P, int nb, cudaStream_t st) {
     if (*P->h_err) {
       cudaMemsetAsync(P->flag + 1, 0, sizeof(int), st);
       cudaStreamSynchronize(st);
+      // cycle graphs captured around the launch that ran out are not replayed again
+      for (CycleGraph& g : P->graphs) g.clear();
+      P->inject_tx = 0;
       return fail(DBAR_ETIMEOUT, "a bounded device wait ran out (bulk copies of the block update)");
     }
     P->prof.harvest();
@@ -2274,6 +2282,15 @@ extern "C" dbar_status dbar_plan_tuning(dbar_plan_t P, int* column_variant, doub
   if (column_variant) *column_variant = P->colv;
   if (ms_per_variant)
     for (int v = 0; v < DBAR_COLUMN_VARIANTS; ++v) ms_per_variant[v] = P->tune_ms[v];
+  return DBAR_OK;
+}
+
+extern "C" dbar_status dbar_plan_inject_wait_timeout(dbar_plan_t P) {
+  if (!P) return fail(DBAR_EINVAL, "plan is NULL");
+  if (P->sstep <= 1 || P->iter || P->conv)
+    return fail(DBAR_EINVAL, "the plan has no block-update sweeps (sstep > 1, Sec. 4 equation)");
+  P->inject_tx = 16;
+  for (CycleGraph& g : P->graphs) g.clear();  // the next cycle is captured with the hook in place
   return DBAR_OK;
 }
 

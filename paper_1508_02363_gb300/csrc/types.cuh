@@ -99,6 +99,7 @@ struct BlockArgs {
   long long xss;
   int x_dd;
   int* err;             // set to 1 when a bounded device wait runs out (nullable)
+  int tx_extra;         // bytes the first bulk-copy stage announces beyond its copy (test hook; 0)
 };
 
 __host__ __device__ constexpr int block_items(int J, int S) { return J * S + S * (S + 1) / 2; }

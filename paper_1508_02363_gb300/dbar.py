@@ -29,7 +29,7 @@ EXPORTED = ["dbar_params_init", "dbar_last_error", "dbar_plan_create", "dbar_pla
             "dbar_launch_count", "dbar_fft2_noalloc", "dbar_serve_create", "dbar_serve_submit",
             "dbar_serve_poll", "dbar_serve_wait", "dbar_serve_release", "dbar_serve_stats",
             "dbar_serve_inject_fault", "dbar_serve_destroy", "dbar_plan_tuning", "dbar_reflection",
-            "dbar_ds2_potential"]
+            "dbar_ds2_potential", "dbar_plan_inject_wait_timeout", "dbar_solve_batches"]
 
 
 class dbar_params(ctypes.Structure):
@@ -45,6 +45,13 @@ class dbar_params(ctypes.Structure):
 class dbar_request(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int), ("L", ctypes.c_double), ("Q", ctypes.c_void_p), ("k_re", ctypes.c_double),
                 ("k_im", ctypes.c_double), ("want_m", ctypes.c_int)]
+
+
+class dbar_batch(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("Q", ctypes.c_void_p), ("nk", ctypes.c_int), ("k", ctypes.c_void_p),
+                ("x0", ctypes.c_void_p), ("S_out", ctypes.c_void_p), ("m_out", ctypes.c_void_p),
+                ("iters", ctypes.c_void_p), ("resid", ctypes.c_void_p), ("io_on_device", ctypes.c_int),
+                ("status", ctypes.c_int)]
 
 
 class dbar_result(ctypes.Structure):
@@ -83,6 +90,8 @@ _lib.dbar_profile_kind_name.restype = ctypes.c_char_p
 _lib.dbar_profile.argtypes = [_vp, _int]
 _lib.dbar_profile_read.argtypes = [_vp, _int, _dp, ctypes.POINTER(ctypes.c_longlong), _dp]
 _lib.dbar_launch_count.argtypes = [_vp, ctypes.POINTER(ctypes.c_longlong)]
+_lib.dbar_plan_inject_wait_timeout.argtypes = [_vp]
+_lib.dbar_solve_batches.argtypes = [ctypes.POINTER(dbar_batch), _int, _vp]
 _lib.dbar_plan_tuning.argtypes = [_vp, _ip, _dp]
 _u64 = ctypes.c_uint64
 _lib.dbar_serve_create.argtypes = [ctypes.POINTER(dbar_params), ctypes.c_size_t, ctypes.POINTER(_vp)]
@@ -182,6 +191,32 @@ def dbar_solve_cgo(plan, Q, k, S_out, m_out=None, iters=None, resid=None, io_on_
     st = _lib.dbar_solve_cgo(plan, _ptr(Q), nk, kb.ctypes.data_as(_dp), _ptr(x0), _ptr(S_out), _ptr(m_out), ip,
                              rp, int(bool(io_on_device)), _stream(stream))
     return _check(st, (DBAR_OK, DBAR_ENOCONV))
+
+
+def dbar_solve_batches(batches, stream=None):
+    """batches: list of dicts with keys plan (a Plan handle), Q, k, S_out and optionally
+    m_out, x0, io_on_device (device tensors or host arrays as in dbar_solve_cgo).  Runs the
+    batches of different plans concurrently (see include/dbar.h).  Returns (status,
+    per-batch statuses, per-batch iters [nk, 2], per-batch resid [nk])."""
+    arr = (dbar_batch * len(batches))()
+    keep = []
+    out_iters, out_resid = [], []
+    for i, bt in enumerate(batches):
+        kb = _kbuf(bt["k"])
+        nk = kb.size // 2
+        it = np.zeros((nk, 2), np.int32)
+        rs = np.zeros(nk, np.float64)
+        keep += [kb, it, rs]
+        dev = bt.get("io_on_device", hasattr(bt["Q"], "data_ptr"))
+        arr[i] = dbar_batch(bt["plan"].value if hasattr(bt["plan"], "value") else bt["plan"],
+                            _ptr(bt["Q"]).value, nk, kb.ctypes.data, _ptr(bt.get("x0")).value if bt.get("x0") is not None
+                            else None, _ptr(bt["S_out"]).value, _ptr(bt.get("m_out")).value
+                            if bt.get("m_out") is not None else None, it.ctypes.data, rs.ctypes.data, int(bool(dev)), 0)
+        out_iters.append(it)
+        out_resid.append(rs)
+    st = _lib.dbar_solve_batches(arr, len(batches), _stream(stream))
+    status = _check(st, (DBAR_OK, DBAR_ENOCONV))
+    return status, [arr[i].status for i in range(len(batches))], out_iters, out_resid
 
 
 def dbar_check_bounded_wait(complete: bool, rounds: int, stream=None) -> float:
@@ -287,6 +322,12 @@ def dbar_plan_tuning(plan):
     v, ms = ctypes.c_int(), (ctypes.c_double * COLUMN_VARIANTS)()
     _check(_lib.dbar_plan_tuning(plan, ctypes.byref(v), ms))
     return v.value, list(ms)
+
+
+def dbar_plan_inject_wait_timeout(plan) -> None:
+    """Test hook: the plan's next block-update launch cannot complete its first bulk-copy
+    stage, so its bounded waits run out and the solve returns DBAR_ETIMEOUT."""
+    _check(_lib.dbar_plan_inject_wait_timeout(plan))
 
 
 def dbar_launch_count(plan) -> int:

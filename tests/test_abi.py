@@ -70,3 +70,19 @@ def test_params_defaults_and_solve_signature(lib):
     k = (ctypes.c_double * 2)(0.1, 0.0)
     st = dbar._lib.dbar_solve_cgo(None, None, 1, k, None, None, None, None, None, 0, None)
     assert st == dbar.DBAR_EINVAL and "plan" in dbar.dbar_last_error()
+
+
+def test_wait_hook_rejects_a_null_plan(lib):
+    from paper_1508_02363_gb300 import dbar
+    with pytest.raises(dbar.DbarError) as e:
+        dbar.dbar_plan_inject_wait_timeout(None)
+    assert e.value.status == dbar.DBAR_EINVAL
+
+
+def test_batches_reject_a_missing_plan(lib):
+    from paper_1508_02363_gb300 import dbar
+    import numpy as np
+    with pytest.raises(dbar.DbarError) as e:
+        dbar.dbar_solve_batches([{"plan": None, "Q": np.zeros((32, 32), complex), "k": [0.1],
+                                  "S_out": np.zeros((1, 32, 32), complex)}], stream=0)
+    assert e.value.status == dbar.DBAR_EINVAL

@@ -168,3 +168,44 @@ def test_support_skip_gives_the_same_solution(dbar, N, L, nk):
         for i in range(nk):
             o = orc.solve_cgo(Q, k[i], N, L, M=2, tol=1e-14, restart=60)
             assert rel(r["S"][i], o["S"]) < 1e-10, i
+
+
+def test_uneven_batches_run_concurrently_with_the_same_results(dbar, torch_cuda):
+    # three grids (three plans), two potentials on one of them: one dbar_solve_batches
+    # call gives each batch the bits of its own dbar_solve_cgo call
+    torch = torch_cuda
+    L = 4.0
+    specs = [(64, 0, [0.3 + 0.1j, -0.2j, 0.5]), (128, 0, [1.1 - 0.4j, 0.2 + 0.9j]), (128, 1, [0.7j]),
+             (256, 1, [2.0 + 1.0j, -1.5 + 0.5j, 0.1])]
+    plans = {N: dbar.Plan(N, L, prec="mixed", restart=16, tol=1e-12, max_batch=3) for N in (64, 128, 256)}
+    batch, ref = [], []
+    for N, pot, k in specs:
+        Q = torch.from_numpy(wl.uneven_potentials(N, L)[pot]).cuda()
+        S = torch.empty((len(k), N, N), dtype=torch.complex128, device="cuda")
+        batch.append({"plan": plans[N].handle, "Q": Q, "k": np.array(k), "S_out": S})
+    st, sts, iters, resid = dbar.dbar_solve_batches(batch)
+    assert st == dbar.DBAR_OK and all(x == dbar.DBAR_OK for x in sts)
+    for (N, pot, k), bt, it, rs in zip(specs, batch, iters, resid):
+        alone = torch.empty_like(bt["S_out"])
+        r = plans[N].solve_device(bt["Q"], np.array(k), alone)
+        assert torch.equal(alone, bt["S_out"]), (N, pot)
+        assert np.array_equal(r["iters"], it) and np.all(rs <= 1e-12)
+
+
+def test_uneven_batches_report_each_status(dbar, torch_cuda):
+    torch = torch_cuda
+    w = wl.plain_fp64()
+    ok = dbar.Plan(w.N, w.L, prec="fp64", tol=1e-13, max_batch=1)
+    capped = dbar.Plan(w.N, w.L, prec="fp64", tol=1e-13, restart=4, max_iter=4, max_outer=1, max_batch=1)
+    Q = torch.from_numpy(w.Q).cuda()
+    S1 = torch.empty((1, w.N, w.N), dtype=torch.complex128, device="cuda")
+    S2 = torch.empty_like(S1)
+    st, sts, _, _ = dbar.dbar_solve_batches([{"plan": ok.handle, "Q": Q, "k": w.k, "S_out": S1},
+                                              {"plan": capped.handle, "Q": Q, "k": w.k, "S_out": S2}])
+    assert st == dbar.DBAR_ENOCONV and sts == [dbar.DBAR_OK, dbar.DBAR_ENOCONV]
+    bad = Q.clone()
+    bad[3, 3] = float("nan")
+    with pytest.raises(dbar.DbarError) as e:
+        dbar.dbar_solve_batches([{"plan": ok.handle, "Q": Q, "k": w.k, "S_out": S1},
+                                 {"plan": capped.handle, "Q": bad, "k": w.k, "S_out": S2}])
+    assert e.value.status == dbar.DBAR_EINVAL and "batch 1" in str(e.value)

@@ -58,3 +58,35 @@ def test_rounds_are_validated(dbar):
         with pytest.raises(dbar.DbarError) as e:
             dbar.dbar_check_bounded_wait(True, bad)
         assert e.value.status == dbar.DBAR_EINVAL
+
+
+@pytest.mark.parametrize("prec,graphs", [("fp64", 1), ("mixed", 0)])
+def test_block_update_wait_runs_out_inside_a_solve(dbar, prec, graphs):
+    # The solve-level path: one block-update launch announces 16 bytes more on its first
+    # bulk-copy stage than the copy delivers (a phase nothing completes); its waits run
+    # out, the block reports through the plan's error flag and drains its copies, and
+    # dbar_solve_cgo returns DBAR_ETIMEOUT.  The next solve on the same plan is correct.
+    from oracle import dbar_oracle as orc
+    w = wl.plain_fp64()
+    tol = 1e-13 if prec == "fp64" else 1e-12
+    plan = dbar.Plan(w.N, w.L, M=w.M, prec=prec, restart=8, sstep=4, tol=tol, max_batch=1, graphs=graphs)
+    assert plan.solve(w.Q, w.k)["status"] == dbar.DBAR_OK      # cycle graphs (if any) captured
+    dbar.dbar_plan_inject_wait_timeout(plan.handle)
+    t0 = time.perf_counter()
+    with pytest.raises(dbar.DbarError) as e:
+        plan.solve(w.Q, w.k)
+    elapsed = time.perf_counter() - t0
+    assert e.value.status == dbar.DBAR_ETIMEOUT and "bounded device wait" in str(e.value)
+    assert elapsed < 20.0, elapsed
+    r = plan.solve(w.Q, w.k)
+    assert r["status"] == dbar.DBAR_OK and r["resid"][0] <= tol
+    o = orc.solve_cgo(w.Q, w.k[0], w.N, w.L, M=w.M, tol=1e-14)
+    err = float(abs(r["S"][0] - o["S"]).max() / abs(o["S"]).max())
+    assert err < (1e-12 if prec == "fp64" else 1e-10), err
+
+
+def test_wait_hook_needs_block_sweeps(dbar):
+    w = wl.plain_fp64()
+    with pytest.raises(dbar.DbarError) as e:
+        dbar.dbar_plan_inject_wait_timeout(dbar.Plan(w.N, w.L, prec="fp64", sstep=1, max_batch=1).handle)
+    assert e.value.status == dbar.DBAR_EINVAL
