@@ -243,6 +243,7 @@ def run_ours(args):
                      inner_tol=args.inner_tol, max_batch=nk, max_outer=args.max_outer, sstep=args.sstep,
                      autotune=args.autotune)
     colv, tune = dbar.dbar_plan_tuning(plan.handle)
+    rowv, rtune = dbar.dbar_plan_row_tuning(plan.handle)
     stream = torch.cuda.current_stream()
     Qd = torch.from_numpy(w.Q).cuda()
     Sd = torch.empty((nk, N, N), dtype=torch.complex128, device="cuda")
@@ -383,6 +384,7 @@ def run_ours(args):
                       "prec": "mixed" if w.mixed else "fp64", "restart": args.restart, "sstep": args.sstep,
                       "inner_tol": args.inner_tol,
                       "column_variant": colv, "column_tune_ms": [round(x, 4) for x in tune],
+                      "row_shape": rowv, "row_tune_ms": [round(x, 4) for x in rtune],
                       "parallelism": f"replicas over k x{world}",
                       "l2": "inputs larger than L2 (device working set %.1f GB)" % (plan.device_bytes / 1e9)},
            "step_p50_ms": round(statistics.median(step_ms), 3),
@@ -506,7 +508,8 @@ def run_uneven(args):
            "resid_max": resid_max, "err_vs_fp64_max": max(errs), "err_sample": len(errs),
            "groups": {f"{N}/{'ab'[pot]}": len(v) for (N, pot), v in sorted(groups.items())},
            "autotune": bool(args.autotune),
-           "tiles": {str(N): dict(zip(("column_variant", "ms_per_variant"), dbar.dbar_plan_tuning(p.handle)))
+           "tiles": {str(N): dict(zip(("column_variant", "ms_per_variant", "row_shape", "ms_per_row_shape"),
+                                      dbar.dbar_plan_tuning(p.handle) + dbar.dbar_plan_row_tuning(p.handle)))
                      for N, p in sorted(plans.items())},
            "config": {"L": L, "kmax": 12.0, "restart": args.restart, "inner_tol": args.inner_tol},
            "clocks": clk.summary()}

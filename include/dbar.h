@@ -151,6 +151,12 @@ typedef struct {
                         exactly zero in FP32, where w = E_k Q conj(h) is exactly
                         zero -- the same values, less work and traffic for a
                         potential concentrated near the origin; 0: every column */
+  int row_shape;     /* DBAR_MIXED: lines per block of the FP32 operator's row
+                        passes.  0 (default): timed at plan creation with
+                        autotune = 1 (else the first shape); 1, 2, 3: the
+                        first (256 threads at N = 1024), second (half as many
+                        lines) or third shape (twice as many).  The arithmetic
+                        per line is the same in every shape                  */
 } dbar_params;
 
 typedef struct dbar_plan* dbar_plan_t;
@@ -414,10 +420,18 @@ dbar_status dbar_profile_read(dbar_plan_t plan, int kind, double* ms, long long*
  * transforms in lockstep). */
 #define DBAR_COLUMN_VARIANTS 3
 
-/* The autotuner's choice: column-pass tile variant in use, and the measured ms
- * per launch of each variant in ms_per_variant[DBAR_COLUMN_VARIANTS] (0 when
- * not tuned).  Any pointer may be NULL. */
-dbar_status dbar_plan_tuning(dbar_plan_t plan, int* column_variant, double* ms_per_variant);
+/* Row-pass shapes of the FP32 operator (row_shape). */
+#define DBAR_ROW_VARIANTS 3
+
+/* The autotuner's choices: column-pass tile variant in use and the measured ms
+ * per launch of each variant in ms_per_variant[DBAR_COLUMN_VARIANTS]; row-pass
+ * shape in use (0-based) and the ms per fused row-pass launch of each shape in
+ * ms_per_row_shape[DBAR_ROW_VARIANTS] (0 when not tuned).  The FFT radix
+ * schedule is fixed per N (radix 16 stages, then the remainder): a different
+ * split would change the rounding, and so the results, from one tuning to
+ * the next.  Any pointer may be NULL. */
+dbar_status dbar_plan_tuning(dbar_plan_t plan, int* column_variant, double* ms_per_variant, int* row_shape,
+                             double* ms_per_row_shape);
 
 /* Test hook for the device-side bounded waits (no counterpart in the paper):
  * the next block-update launch of this plan announces 16 bytes more on its

@@ -403,8 +403,17 @@ __device__ __forceinline__ void fft_line2(cx<T> (&va)[16], cx<T> (&vb)[16], cx<T
 //           consecutive t, so each load of the 16 elements of a thread is a
 //           set of 32*sizeof(cx)/CW-byte row segments (coalesced straight
 //           from/to registers).
+// Row-pass shapes of the FP32 inner passes (autotuned): lines per block of shape rv
+// (0: row_lines, 1: half as many, 2: twice as many; within [1, N] and 1024 threads).
+__host__ __device__ constexpr int row_lines_v(int logN, int rv);
 __host__ __device__ constexpr int row_lines(int logN) {
   return (256 / ((1 << logN) / 16)) < (1 << logN) ? (256 / ((1 << logN) / 16)) : (1 << logN);
+}
+__host__ __device__ constexpr int row_lines_v(int logN, int rv) {
+  return rv == 1 ? (row_lines(logN) / 2 > 0 ? row_lines(logN) / 2 : 1)
+       : rv == 2 ? ((row_lines(logN) * 2 <= (1 << logN) && row_lines(logN) * 2 * ((1 << logN) / 16) <= 1024)
+                        ? row_lines(logN) * 2 : row_lines(logN))
+                 : row_lines(logN);
 }
 // Column-pass tile shapes.  Variant 0: a warp reads DBAR_COL_SEG_BYTES-byte row
 // segments, DBAR_COL_THREADS_F32 / _F64 threads per block.  Variant 1: 32-byte

@@ -23,20 +23,24 @@ static cudaError_t set_smem(K kernel, size_t bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+template <typename T, int LOGN, bool SH, int RV>
+static cudaError_t launch_a_shape(const PassArgs<T>& a, int nslots, cudaStream_t s) {
+  using G = RowG<T, LOGN, RV>;
+  const size_t sm = (size_t)G::LINES * G::P * sizeof(cx<T>);
+  cudaError_t e = set_smem(k_pass_a<T, LOGN, SH, RV>, sm);
+  if (e != cudaSuccess) return e;
+  k_pass_a<T, LOGN, SH, RV><<<dim3(G::N / G::LINES, nslots), G::THREADS, sm, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <typename T, int LOGN>
 cudaError_t launch_pass_a_n(const PassArgs<T>& a, int nslots, cudaStream_t s) {
-  using G = RowG<T, LOGN>;
-  const size_t sm = (size_t)G::LINES * G::P * sizeof(cx<T>);
-  if (a.dshift) {  // shifted quotient of the iterated equation
-    cudaError_t e = set_smem(k_pass_a<T, LOGN, true>, sm);
-    if (e != cudaSuccess) return e;
-    k_pass_a<T, LOGN, true><<<dim3(G::N / G::LINES, nslots), G::THREADS, sm, s>>>(a);
-  } else {
-    cudaError_t e = set_smem(k_pass_a<T, LOGN, false>, sm);
-    if (e != cudaSuccess) return e;
-    k_pass_a<T, LOGN, false><<<dim3(G::N / G::LINES, nslots), G::THREADS, sm, s>>>(a);
+  if (a.dshift) return launch_a_shape<T, LOGN, true, 0>(a, nslots, s);  // shifted quotient (iterated equation)
+  if constexpr (std::is_same<T, float>::value) {
+    if (a.rowv == 1) return launch_a_shape<T, LOGN, false, 1>(a, nslots, s);
+    if (a.rowv == 2) return launch_a_shape<T, LOGN, false, 2>(a, nslots, s);
   }
-  return cudaGetLastError();
+  return launch_a_shape<T, LOGN, false, 0>(a, nslots, s);
 }
 
 template <typename T, int LOGN, int MODE, int CV>
@@ -61,24 +65,43 @@ cudaError_t launch_pass_b_n(const PassArgs<T>& a, int nslots, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <typename T, int LOGN, int RV>
+static cudaError_t launch_ca_shape(const PassArgs<T>& a, int nslots, cudaStream_t s) {
+  using G = RowG<T, LOGN, RV>;
+  const size_t sm = (size_t)G::LINES * G::P * sizeof(cx<T>);
+  cudaError_t e = set_smem(k_pass_ca<T, LOGN, RV>, sm);
+  if (e != cudaSuccess) return e;
+  k_pass_ca<T, LOGN, RV><<<dim3(G::N / G::LINES, nslots), G::THREADS, sm, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <typename T, int LOGN>
 cudaError_t launch_pass_ca_n(const PassArgs<T>& a, int nslots, cudaStream_t s) {
-  using G = RowG<T, LOGN>;
+  if constexpr (std::is_same<T, float>::value) {
+    if (a.rowv == 1) return launch_ca_shape<T, LOGN, 1>(a, nslots, s);
+    if (a.rowv == 2) return launch_ca_shape<T, LOGN, 2>(a, nslots, s);
+  }
+  return launch_ca_shape<T, LOGN, 0>(a, nslots, s);
+}
+
+template <typename T, typename TO, int LOGN, int MODE, int RV>
+static cudaError_t launch_c_shape(const PassArgs<T>& a, int nslots, cudaStream_t s) {
+  using G = RowG<T, LOGN, RV>;
   const size_t sm = (size_t)G::LINES * G::P * sizeof(cx<T>);
-  cudaError_t e = set_smem(k_pass_ca<T, LOGN>, sm);
+  cudaError_t e = set_smem(k_pass_c<T, TO, LOGN, MODE, RV>, sm);
   if (e != cudaSuccess) return e;
-  k_pass_ca<T, LOGN><<<dim3(G::N / G::LINES, nslots), G::THREADS, sm, s>>>(a);
+  k_pass_c<T, TO, LOGN, MODE, RV><<<dim3(G::N / G::LINES, nslots), G::THREADS, sm, s>>>(a);
   return cudaGetLastError();
 }
 
 template <typename T, typename TO, int LOGN, int MODE>
 cudaError_t launch_pass_c_n(const PassArgs<T>& a, int nslots, cudaStream_t s) {
-  using G = RowG<T, LOGN>;
-  const size_t sm = (size_t)G::LINES * G::P * sizeof(cx<T>);
-  cudaError_t e = set_smem(k_pass_c<T, TO, LOGN, MODE>, sm);
-  if (e != cudaSuccess) return e;
-  k_pass_c<T, TO, LOGN, MODE><<<dim3(G::N / G::LINES, nslots), G::THREADS, sm, s>>>(a);
-  return cudaGetLastError();
+  // the operator's K S (no per-block partial sums): the autotuned shape
+  if constexpr (std::is_same<T, float>::value && MODE == PC_KS) {
+    if (a.rowv == 1) return launch_c_shape<T, TO, LOGN, MODE, 1>(a, nslots, s);
+    if (a.rowv == 2) return launch_c_shape<T, TO, LOGN, MODE, 2>(a, nslots, s);
+  }
+  return launch_c_shape<T, TO, LOGN, MODE, 0>(a, nslots, s);
 }
 
 typedef DBAR_T TT;

@@ -67,14 +67,17 @@ __device__ __forceinline__ dd kappa_scale<dd>(dd c, dd den) {
   return c * dd_quick_two_sum(y, __fmul_rn(y, e));
 }
 
-template <typename T, int LOGN>
+// RV: row shape (row_lines_v); the blocks an SM keeps scale with 1/LINES so that the
+// register budget per thread is the same for every shape.
+template <typename T, int LOGN, int RV = 0>
 struct RowG {
-  static constexpr int N = 1 << LOGN, TPL = N / 16, LINES = row_lines(LOGN), THREADS = LINES * TPL;
+  static constexpr int N = 1 << LOGN, TPL = N / 16, LINES = row_lines_v(LOGN, RV), THREADS = LINES * TPL;
   static constexpr int P = pitch_of(N);
 #ifndef DBAR_ROW_MINB_F32
 #define DBAR_ROW_MINB_F32 4
 #endif
-  static constexpr int MINB = sizeof(T) == 4 ? DBAR_ROW_MINB_F32 : 2;
+  static constexpr int MINB0 = sizeof(T) == 4 ? DBAR_ROW_MINB_F32 : 2;
+  static constexpr int MINB = MINB0 * row_lines(LOGN) / LINES > 0 ? MINB0 * row_lines(LOGN) / LINES : 1;
 };
 template <typename T, int LOGN, int CV = 0>
 struct ColG {
@@ -187,9 +190,9 @@ __device__ __forceinline__ void row_a(const PassArgs<T>& a, cx<T> (&v)[16], int 
 }
 
 // SH: the shifted quotient of the iterated equation (a.dshift set)
-template <typename T, int LOGN, bool SH>
-__global__ void __launch_bounds__(RowG<T, LOGN>::THREADS, RowG<T, LOGN>::MINB) k_pass_a(const PassArgs<T> a) {
-  using G = RowG<T, LOGN>;
+template <typename T, int LOGN, bool SH, int RV = 0>
+__global__ void __launch_bounds__(RowG<T, LOGN, RV>::THREADS, RowG<T, LOGN, RV>::MINB) k_pass_a(const PassArgs<T> a) {
+  using G = RowG<T, LOGN, RV>;
   constexpr int N = G::N, TPL = G::TPL, LINES = G::LINES, P = G::P;
   extern __shared__ __align__(16) unsigned char smem[];
   const int slot = blockIdx.y;
@@ -212,9 +215,9 @@ __global__ void __launch_bounds__(RowG<T, LOGN>::THREADS, RowG<T, LOGN>::MINB) k
 // followed, on the same rows still in registers, by pass A of K p_i (-> out2).
 // Saves the re-read of p_{i+1} and one launch per chain step.
 // ---------------------------------------------------------------------------
-template <typename T, int LOGN>
-__global__ void __launch_bounds__(RowG<T, LOGN>::THREADS, RowG<T, LOGN>::MINB) k_pass_ca(const PassArgs<T> a) {
-  using G = RowG<T, LOGN>;
+template <typename T, int LOGN, int RV = 0>
+__global__ void __launch_bounds__(RowG<T, LOGN, RV>::THREADS, RowG<T, LOGN, RV>::MINB) k_pass_ca(const PassArgs<T> a) {
+  using G = RowG<T, LOGN, RV>;
   constexpr int N = G::N, TPL = G::TPL, LINES = G::LINES, P = G::P;
   extern __shared__ __align__(16) unsigned char smem[];
   const int slot = blockIdx.y;
@@ -519,9 +522,9 @@ static __global__ void __launch_bounds__(256) k_coef(const cx<PT>* __restrict__ 
 // PC_RES: r = b - x - i (-1)^p DFT(w) -> out2 (TO), |r|^2 partials (T = FP64).
 // PC_FWD / PC_INV: raw row DFTs -> out (T).
 // ---------------------------------------------------------------------------
-template <typename T, typename TO, int LOGN, int MODE>
-__global__ void __launch_bounds__(RowG<T, LOGN>::THREADS, RowG<T, LOGN>::MINB) k_pass_c(const PassArgs<T> a) {
-  using G = RowG<T, LOGN>;
+template <typename T, typename TO, int LOGN, int MODE, int RV = 0>
+__global__ void __launch_bounds__(RowG<T, LOGN, RV>::THREADS, RowG<T, LOGN, RV>::MINB) k_pass_c(const PassArgs<T> a) {
+  using G = RowG<T, LOGN, RV>;
   constexpr int N = G::N, TPL = G::TPL, LINES = G::LINES, P = G::P;
   extern __shared__ __align__(16) unsigned char smem[];
   const int slot = blockIdx.y;

@@ -149,6 +149,8 @@ struct dbar_plan {
   int per_slot_q = 0;   // 1: every slot has its own potential (serving); 0: one Q for all
   int colv = 0;         // FP32 column-pass tile variant (autotuned)
   double tune_ms[DBAR_COLUMN_VARIANTS] = {0.0, 0.0, 0.0};
+  int rowv = 0;         // row-pass shape of the FP32 operator's row passes (autotuned)
+  double row_ms[DBAR_ROW_VARIANTS] = {0.0, 0.0, 0.0};
   int* dmask = nullptr;  // [B] device copy of a slot mask
   int* hmask = nullptr;  // [B] pinned host staging of it
   long long nlaunch = 0;  // kernels launched by this plan
@@ -455,6 +457,7 @@ PassArgs<float> base_args<float>(const dbar_plan* P) {
   PassArgs<float> a;
   std::memset(&a, 0, sizeof(a));
   a.colv = P->colv;
+  a.rowv = P->rowv;
   a.g = make_geo<float>(P->N);
   a.sx1 = a.sy1 = P->N;
   a.M = P->Min;
@@ -1187,6 +1190,7 @@ static dbar_status check_params(const dbar_params* p) {
   if (p->inner_M < 0 || p->inner_M > p->M) return fail(DBAR_EINVAL, "inner_M must be in [0, M]");
   if (!(p->gauss_w > 0.0) || !std::isfinite(p->gauss_w)) return fail(DBAR_EINVAL, "gauss_w must be finite and > 0");
   if (p->support_skip != 0 && p->support_skip != 1) return fail(DBAR_EINVAL, "support_skip must be 0 or 1");
+  if (p->row_shape < 0 || p->row_shape > DBAR_ROW_VARIANTS) return fail(DBAR_EINVAL, "row_shape must be in [0, 3]");
   if (p->regularisation != DBAR_REG_TAYLOR && p->regularisation != DBAR_REG_CONV)
     return fail(DBAR_EINVAL, "regularisation must be DBAR_REG_TAYLOR or DBAR_REG_CONV");
   if (p->regularisation == DBAR_REG_CONV) {
@@ -1356,7 +1360,12 @@ static dbar_status plan_tables(dbar_plan* P) {
 // bit-identical across variants (same arithmetic per column), so the choice
 // only affects speed; it is cached per (device, N, M) for the process.
 static std::mutex g_tune_mu;
-static std::map<std::tuple<int, int, int>, std::pair<int, std::array<double, DBAR_COLUMN_VARIANTS>>> g_tune_cache;
+struct TuneResult {
+  int colv, rowv;
+  std::array<double, DBAR_COLUMN_VARIANTS> col_ms;
+  std::array<double, DBAR_ROW_VARIANTS> row_ms;
+};
+static std::map<std::tuple<int, int, int>, TuneResult> g_tune_cache;
 
 static dbar_status autotune_columns(dbar_plan* P) {
   const auto key = std::make_tuple(P->device, P->N, P->Min);
@@ -1364,8 +1373,10 @@ static dbar_status autotune_columns(dbar_plan* P) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) {
-      P->colv = it->second.first;
-      for (int v = 0; v < DBAR_COLUMN_VARIANTS; ++v) P->tune_ms[v] = it->second.second[v];
+      P->colv = it->second.colv;
+      P->rowv = it->second.rowv;
+      for (int v = 0; v < DBAR_COLUMN_VARIANTS; ++v) P->tune_ms[v] = it->second.col_ms[v];
+      for (int v = 0; v < DBAR_ROW_VARIANTS; ++v) P->row_ms[v] = it->second.row_ms[v];
       return DBAR_OK;
     }
   }
@@ -1373,6 +1384,7 @@ static dbar_status autotune_columns(dbar_plan* P) {
   const int nb = std::min(P->B, 16);
   const size_t n = (size_t)P->n;
   CK(cudaMemset(P->T1, 0, (size_t)nb * n * sizeof(cx<float>)));
+  CK(cudaMemset(P->T2, 0, (size_t)nb * n * sizeof(cx<float>)));
   CK(cudaMemset(P->tcoef, 0, (size_t)nb * (P->M + 2) * sizeof(cx<double>)));
   CK(cudaMemset(P->Q32, 0, n * sizeof(cx<float>)));
   CK(cudaMemset(P->ex32, 0, (size_t)nb * P->N * sizeof(cx<float>)));
@@ -1403,13 +1415,43 @@ static dbar_status autotune_columns(dbar_plan* P) {
       choice = cv;
     }
   }
+  P->colv = choice;
+  // row-pass shapes, timed on the fused row pass (the inner operator's largest row pass)
+  best = 1e300;
+  int rchoice = 0;
+  for (int rv = 0; rv < DBAR_ROW_VARIANTS; ++rv) {
+    PassArgs<float> a = base_args<float>(P);
+    a.rowv = rv;
+    a.in = reinterpret_cast<const cx<float>*>(P->T2);
+    a.in_ss = (long long)n;
+    a.out = P->KS;
+    a.out_ss = (long long)n;
+    a.out2 = P->T1;
+    a.out2_ss = (long long)n;
+    for (int w = 0; w < 2; ++w) CK(launch_pass_ca<float>(a, nb, st));
+    CK(cudaEventRecord(e0, st));
+    const int reps = 5;
+    for (int r = 0; r < reps; ++r) CK(launch_pass_ca<float>(a, nb, st));
+    CK(cudaEventRecord(e1, st));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    P->row_ms[rv] = ms / reps;
+    if (ms < best) {
+      best = ms;
+      rchoice = rv;
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  P->colv = choice;
+  P->rowv = rchoice;
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  std::array<double, DBAR_COLUMN_VARIANTS> t;
-  for (int v = 0; v < DBAR_COLUMN_VARIANTS; ++v) t[v] = P->tune_ms[v];
-  g_tune_cache[key] = {choice, t};
+  TuneResult t;
+  t.colv = choice;
+  t.rowv = rchoice;
+  for (int v = 0; v < DBAR_COLUMN_VARIANTS; ++v) t.col_ms[v] = P->tune_ms[v];
+  for (int v = 0; v < DBAR_ROW_VARIANTS; ++v) t.row_ms[v] = P->row_ms[v];
+  g_tune_cache[key] = t;
   return DBAR_OK;
 }
 
@@ -1659,6 +1701,7 @@ dbar_status plan_create_ex(const dbar_params* p, int per_slot_q, dbar_plan** out
   if (s == DBAR_OK && P->mixed && p->autotune == 1) s = autotune_columns(P);
   if (P->mixed && p->autotune == 2) P->colv = 1;  // fixed second variant (tests)
   if (P->mixed && p->autotune == 3) P->colv = 2;  // fixed third variant (tests)
+  if (P->mixed && p->row_shape > 0) P->rowv = p->row_shape - 1;  // fixed row-pass shape
   if (s != DBAR_OK) {
     delete P;
     return s;
@@ -2277,11 +2320,15 @@ extern "C" dbar_status dbar_profile_read(dbar_plan_t P, int kind, double* ms, lo
   return DBAR_OK;
 }
 
-extern "C" dbar_status dbar_plan_tuning(dbar_plan_t P, int* column_variant, double* ms_per_variant) {
+extern "C" dbar_status dbar_plan_tuning(dbar_plan_t P, int* column_variant, double* ms_per_variant,
+                                        int* row_shape, double* ms_per_row_shape) {
   if (!P) return fail(DBAR_EINVAL, "plan is NULL");
   if (column_variant) *column_variant = P->colv;
   if (ms_per_variant)
     for (int v = 0; v < DBAR_COLUMN_VARIANTS; ++v) ms_per_variant[v] = P->tune_ms[v];
+  if (row_shape) *row_shape = P->rowv;
+  if (ms_per_row_shape)
+    for (int v = 0; v < DBAR_ROW_VARIANTS; ++v) ms_per_row_shape[v] = P->row_ms[v];
   return DBAR_OK;
 }
 

@@ -12,6 +12,7 @@ template <typename T>
 struct PassArgs {
   Geo g;
   int colv;  // column-pass tile variant (autotuned)
+  int rowv;  // row-pass shape of the FP32 operator's row passes (autotuned; 0 elsewhere)
   int M;  // Taylor order
   // input field (T), per-slot stride in complex elements; optional per-slot scale
   const cx<T>* in;

@@ -39,7 +39,7 @@ class dbar_params(ctypes.Structure):
                 ("max_outer", ctypes.c_int), ("resid_mode", ctypes.c_int), ("graphs", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("sstep", ctypes.c_int), ("iterated", ctypes.c_int),
                 ("regularisation", ctypes.c_int), ("inner_M", ctypes.c_int), ("gauss_w", ctypes.c_double),
-                ("mem_budget", ctypes.c_size_t), ("support_skip", ctypes.c_int)]
+                ("mem_budget", ctypes.c_size_t), ("support_skip", ctypes.c_int), ("row_shape", ctypes.c_int)]
 
 
 class dbar_request(ctypes.Structure):
@@ -92,7 +92,7 @@ _lib.dbar_profile_read.argtypes = [_vp, _int, _dp, ctypes.POINTER(ctypes.c_longl
 _lib.dbar_launch_count.argtypes = [_vp, ctypes.POINTER(ctypes.c_longlong)]
 _lib.dbar_plan_inject_wait_timeout.argtypes = [_vp]
 _lib.dbar_solve_batches.argtypes = [ctypes.POINTER(dbar_batch), _int, _vp]
-_lib.dbar_plan_tuning.argtypes = [_vp, _ip, _dp]
+_lib.dbar_plan_tuning.argtypes = [_vp, _ip, _dp, _ip, _dp]
 _u64 = ctypes.c_uint64
 _lib.dbar_serve_create.argtypes = [ctypes.POINTER(dbar_params), ctypes.c_size_t, ctypes.POINTER(_vp)]
 _lib.dbar_serve_submit.argtypes = [_vp, ctypes.POINTER(dbar_request), ctypes.POINTER(_u64)]
@@ -315,12 +315,20 @@ def dbar_profile_read(plan, kind: int):
 
 
 COLUMN_VARIANTS = 3
+ROW_VARIANTS = 3
 
 
 def dbar_plan_tuning(plan):
     """(column-pass tile variant in use, [ms per launch of each variant])."""
     v, ms = ctypes.c_int(), (ctypes.c_double * COLUMN_VARIANTS)()
-    _check(_lib.dbar_plan_tuning(plan, ctypes.byref(v), ms))
+    _check(_lib.dbar_plan_tuning(plan, ctypes.byref(v), ms, None, None))
+    return v.value, list(ms)
+
+
+def dbar_plan_row_tuning(plan):
+    """(row-pass shape in use, [ms per fused row-pass launch of each shape])."""
+    v, ms = ctypes.c_int(), (ctypes.c_double * ROW_VARIANTS)()
+    _check(_lib.dbar_plan_tuning(plan, None, None, ctypes.byref(v), ms))
     return v.value, list(ms)
 
 

@@ -308,3 +308,22 @@ def test_autotuned_column_tiles_give_identical_results(dbar):
     for r in res[1:]:
         assert np.array_equal(res[0]["S"], r["S"])
     assert res[0]["status"] == dbar.DBAR_OK
+
+
+@pytest.mark.parametrize("N,nk,L", [(256, 3, 6.0), (1024, 2, 10.0)])
+def test_row_pass_shapes_give_identical_results(dbar, N, nk, L):
+    # every row-pass shape of the FP32 operator computes the same numbers; the autotuner
+    # times them all and records its choice
+    w = wl.mixed_1024(N=N, nk=nk, L=L)
+    res = []
+    for shape in (1, 2, 3, 0):
+        plan = dbar.Plan(w.N, w.L, M=2, prec="mixed", restart=24, tol=1e-12, max_batch=nk, row_shape=shape)
+        res.append(plan.solve(w.Q, w.k, want_m=False))
+        rv, ms = dbar.dbar_plan_row_tuning(plan.handle)
+        if shape:
+            assert rv == shape - 1
+        else:
+            assert rv in (0, 1, 2) and len(ms) == dbar.ROW_VARIANTS and min(ms) > 0
+    for r in res[1:]:
+        assert np.array_equal(res[0]["S"], r["S"]) and np.array_equal(res[0]["iters"], r["iters"])
+    assert res[0]["status"] == dbar.DBAR_OK
