@@ -153,10 +153,12 @@ typedef struct {
                         potential concentrated near the origin; 0: every column */
   int row_shape;     /* DBAR_MIXED: lines per block of the FP32 operator's row
                         passes.  0 (default): timed at plan creation with
-                        autotune = 1 (else the first shape); 1, 2, 3: the
-                        first (256 threads at N = 1024), second (half as many
-                        lines) or third shape (twice as many).  The arithmetic
-                        per line is the same in every shape                  */
+                        autotune = 1 (else the first shape); 1..5: the first
+                        (256 threads at N = 1024), second (half as many lines)
+                        or third shape (twice as many), and the first two with
+                        a larger register budget per thread (three quarters
+                        of the threads resident per SM).  The arithmetic per
+                        line is the same in every shape                       */
 } dbar_params;
 
 typedef struct dbar_plan* dbar_plan_t;
@@ -421,7 +423,7 @@ dbar_status dbar_profile_read(dbar_plan_t plan, int kind, double* ms, long long*
 #define DBAR_COLUMN_VARIANTS 3
 
 /* Row-pass shapes of the FP32 operator (row_shape). */
-#define DBAR_ROW_VARIANTS 3
+#define DBAR_ROW_VARIANTS 5
 
 /* The autotuner's choices: column-pass tile variant in use and the measured ms
  * per launch of each variant in ms_per_variant[DBAR_COLUMN_VARIANTS]; row-pass

@@ -404,13 +404,14 @@ __device__ __forceinline__ void fft_line2(cx<T> (&va)[16], cx<T> (&vb)[16], cx<T
 //           set of 32*sizeof(cx)/CW-byte row segments (coalesced straight
 //           from/to registers).
 // Row-pass shapes of the FP32 inner passes (autotuned): lines per block of shape rv
-// (0: row_lines, 1: half as many, 2: twice as many; within [1, N] and 1024 threads).
+// (0: row_lines, 1: half as many, 2: twice as many; within [1, N] and 1024 threads;
+// 3 and 4: the lines of 0 and 1 with a larger register budget, see RowG).
 __host__ __device__ constexpr int row_lines_v(int logN, int rv);
 __host__ __device__ constexpr int row_lines(int logN) {
   return (256 / ((1 << logN) / 16)) < (1 << logN) ? (256 / ((1 << logN) / 16)) : (1 << logN);
 }
 __host__ __device__ constexpr int row_lines_v(int logN, int rv) {
-  return rv == 1 ? (row_lines(logN) / 2 > 0 ? row_lines(logN) / 2 : 1)
+  return (rv == 1 || rv == 4) ? (row_lines(logN) / 2 > 0 ? row_lines(logN) / 2 : 1)
        : rv == 2 ? ((row_lines(logN) * 2 <= (1 << logN) && row_lines(logN) * 2 * ((1 << logN) / 16) <= 1024)
                         ? row_lines(logN) * 2 : row_lines(logN))
                  : row_lines(logN);

@@ -39,6 +39,8 @@ cudaError_t launch_pass_a_n(const PassArgs<T>& a, int nslots, cudaStream_t s) {
   if constexpr (std::is_same<T, float>::value) {
     if (a.rowv == 1) return launch_a_shape<T, LOGN, false, 1>(a, nslots, s);
     if (a.rowv == 2) return launch_a_shape<T, LOGN, false, 2>(a, nslots, s);
+    if (a.rowv == 3) return launch_a_shape<T, LOGN, false, 3>(a, nslots, s);
+    if (a.rowv == 4) return launch_a_shape<T, LOGN, false, 4>(a, nslots, s);
   }
   return launch_a_shape<T, LOGN, false, 0>(a, nslots, s);
 }
@@ -80,6 +82,8 @@ cudaError_t launch_pass_ca_n(const PassArgs<T>& a, int nslots, cudaStream_t s) {
   if constexpr (std::is_same<T, float>::value) {
     if (a.rowv == 1) return launch_ca_shape<T, LOGN, 1>(a, nslots, s);
     if (a.rowv == 2) return launch_ca_shape<T, LOGN, 2>(a, nslots, s);
+    if (a.rowv == 3) return launch_ca_shape<T, LOGN, 3>(a, nslots, s);
+    if (a.rowv == 4) return launch_ca_shape<T, LOGN, 4>(a, nslots, s);
   }
   return launch_ca_shape<T, LOGN, 0>(a, nslots, s);
 }
@@ -100,6 +104,8 @@ cudaError_t launch_pass_c_n(const PassArgs<T>& a, int nslots, cudaStream_t s) {
   if constexpr (std::is_same<T, float>::value && MODE == PC_KS) {
     if (a.rowv == 1) return launch_c_shape<T, TO, LOGN, MODE, 1>(a, nslots, s);
     if (a.rowv == 2) return launch_c_shape<T, TO, LOGN, MODE, 2>(a, nslots, s);
+    if (a.rowv == 3) return launch_c_shape<T, TO, LOGN, MODE, 3>(a, nslots, s);
+    if (a.rowv == 4) return launch_c_shape<T, TO, LOGN, MODE, 4>(a, nslots, s);
   }
   return launch_c_shape<T, TO, LOGN, MODE, 0>(a, nslots, s);
 }

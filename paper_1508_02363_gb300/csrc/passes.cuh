@@ -68,7 +68,8 @@ __device__ __forceinline__ dd kappa_scale<dd>(dd c, dd den) {
 }
 
 // RV: row shape (row_lines_v); the blocks an SM keeps scale with 1/LINES so that the
-// register budget per thread is the same for every shape.
+// register budget per thread is the same for shapes 0-2; shapes 3 and 4 keep 3/4 as
+// many threads per SM, which allows ~85 registers per thread instead of 64.
 template <typename T, int LOGN, int RV = 0>
 struct RowG {
   static constexpr int N = 1 << LOGN, TPL = N / 16, LINES = row_lines_v(LOGN, RV), THREADS = LINES * TPL;
@@ -77,7 +78,8 @@ struct RowG {
 #define DBAR_ROW_MINB_F32 4
 #endif
   static constexpr int MINB0 = sizeof(T) == 4 ? DBAR_ROW_MINB_F32 : 2;
-  static constexpr int MINB = MINB0 * row_lines(LOGN) / LINES > 0 ? MINB0 * row_lines(LOGN) / LINES : 1;
+  static constexpr int MINB1 = (RV >= 3 ? MINB0 * 3 / 4 : MINB0) > 0 ? (RV >= 3 ? MINB0 * 3 / 4 : MINB0) : 1;
+  static constexpr int MINB = MINB1 * row_lines(LOGN) / LINES > 0 ? MINB1 * row_lines(LOGN) / LINES : 1;
 };
 template <typename T, int LOGN, int CV = 0>
 struct ColG {

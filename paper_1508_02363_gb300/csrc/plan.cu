@@ -150,7 +150,7 @@ struct dbar_plan {
   int colv = 0;         // FP32 column-pass tile variant (autotuned)
   double tune_ms[DBAR_COLUMN_VARIANTS] = {0.0, 0.0, 0.0};
   int rowv = 0;         // row-pass shape of the FP32 operator's row passes (autotuned)
-  double row_ms[DBAR_ROW_VARIANTS] = {0.0, 0.0, 0.0};
+  double row_ms[DBAR_ROW_VARIANTS] = {0.0, 0.0, 0.0, 0.0, 0.0};
   int* dmask = nullptr;  // [B] device copy of a slot mask
   int* hmask = nullptr;  // [B] pinned host staging of it
   long long nlaunch = 0;  // kernels launched by this plan
@@ -1190,7 +1190,7 @@ static dbar_status check_params(const dbar_params* p) {
   if (p->inner_M < 0 || p->inner_M > p->M) return fail(DBAR_EINVAL, "inner_M must be in [0, M]");
   if (!(p->gauss_w > 0.0) || !std::isfinite(p->gauss_w)) return fail(DBAR_EINVAL, "gauss_w must be finite and > 0");
   if (p->support_skip != 0 && p->support_skip != 1) return fail(DBAR_EINVAL, "support_skip must be 0 or 1");
-  if (p->row_shape < 0 || p->row_shape > DBAR_ROW_VARIANTS) return fail(DBAR_EINVAL, "row_shape must be in [0, 3]");
+  if (p->row_shape < 0 || p->row_shape > DBAR_ROW_VARIANTS) return fail(DBAR_EINVAL, "row_shape must be in [0, 5]");
   if (p->regularisation != DBAR_REG_TAYLOR && p->regularisation != DBAR_REG_CONV)
     return fail(DBAR_EINVAL, "regularisation must be DBAR_REG_TAYLOR or DBAR_REG_CONV");
   if (p->regularisation == DBAR_REG_CONV) {

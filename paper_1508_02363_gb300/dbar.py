@@ -315,7 +315,7 @@ def dbar_profile_read(plan, kind: int):
 
 
 COLUMN_VARIANTS = 3
-ROW_VARIANTS = 3
+ROW_VARIANTS = 5
 
 
 def dbar_plan_tuning(plan):
