@@ -806,44 +806,47 @@ def serving_leg(args, dbar, torch, clock_gpu=0):
     srv = dbar.Server(int(free * 0.7), prec="mixed", restart=args.restart, tol=1e-12, inner_tol=args.inner_tol,
                       max_batch=args.serve_batch)
     gen = cf.ThreadPoolExecutor(max_workers=6)
-    futs = {}
     LOOK = 64
-    kept_Q, kept_S, lat = {}, {}, []
-    status, resid = [], []
-    tickets = []
-    tickets_ready = threading.Condition()
-    late = [0]
+    kept_Q, kept_S = {}, {}
 
-    def generate(i):
-        N, k, mix = reqs[i]
-        return wl.gaussian_mixture(N, L, *mix)
+    def stream(arr, rq, keep):
+        """Submits rq[i] at arr[i] (generated just ahead by the pool), collects and releases each
+        result as it completes; keeps Q and S of the requests in `keep`.  Returns the latencies,
+        statuses and residuals in submission order, the wall time from the first submission to
+        the last completion, and the number of submissions more than 5 ms late."""
+        futs, lat, status, resid, tickets = {}, [], [], [], []
+        ready = threading.Condition()
+        late = [0]
 
-    def collect():
-        j = 0
-        while True:
-            with tickets_ready:
-                while j >= len(tickets):
-                    tickets_ready.wait()
-                item = tickets[j]
-            if item is None:
-                return
-            i, t = item
-            r = srv.wait(t, timeout_s=600, release=True, copy=i in sampled)
-            lat.append(r["latency_ms"])
-            status.append(r["status"])
-            resid.append(r["resid"])
-            if i in sampled:
-                kept_S[i] = r["S"]
-            j += 1
+        def generate(i):
+            N, k, mix = rq[i]
+            return wl.gaussian_mixture(N, L, *mix)
 
-    collector = threading.Thread(target=collect, daemon=True)
-    collector.start()
-    for i in range(min(LOOK, len(reqs))):
-        futs[i] = gen.submit(generate, i)
-    with ClockSampler(clock_gpu) as clk:
+        def collect():
+            j = 0
+            while True:
+                with ready:
+                    while j >= len(tickets):
+                        ready.wait()
+                    item = tickets[j]
+                if item is None:
+                    return
+                i, t = item
+                r = srv.wait(t, timeout_s=600, release=True, copy=i in keep)
+                lat.append(r["latency_ms"])
+                status.append(r["status"])
+                resid.append(r["resid"])
+                if i in keep:
+                    kept_S[i] = r["S"]
+                j += 1
+
+        collector = threading.Thread(target=collect, daemon=True)
+        collector.start()
+        for i in range(min(LOOK, len(rq))):
+            futs[i] = gen.submit(generate, i)
         t0 = time.perf_counter()
-        for i, ta in enumerate(arrivals):
-            if i + LOOK < len(reqs):
+        for i, ta in enumerate(arr):
+            if i + LOOK < len(rq):
                 futs[i + LOOK] = gen.submit(generate, i + LOOK)
             Q = futs.pop(i).result()
             dt = ta - (time.perf_counter() - t0)
@@ -851,20 +854,30 @@ def serving_leg(args, dbar, torch, clock_gpu=0):
                 time.sleep(dt)
             elif dt < -0.005:
                 late[0] += 1
-            N, k, _ = reqs[i]
+            N, k, _ = rq[i]
             t = srv.submit(N, L, Q, k)
-            if i in sampled:
+            if i in keep:
                 kept_Q[i] = Q
-            with tickets_ready:
+            with ready:
                 tickets.append((i, t))
-                tickets_ready.notify()
-        with tickets_ready:
+                ready.notify()
+        with ready:
             tickets.append(None)
-            tickets_ready.notify()
+            ready.notify()
         collector.join()
-        wall = time.perf_counter() - t0
+        return lat, status, resid, time.perf_counter() - t0, late[0]
+
+    # warm-up: a few seconds of the same kind of traffic (other requests), not counted, so
+    # that the measured stream sees the server in its steady state (lanes and plans built,
+    # page-locked host buffers allocated)
+    if args.serve_warmup > 0:
+        warr = wl.poisson_arrivals(args.rate, args.serve_warmup, seed=args.seed + 1)
+        wreq = [wl.serving_request(10_000_000 + i, base_seed=args.seed, L=L, kmax=KMAX, xi_q=XI_Q)
+                for i in range(warr.size)]
+        stream(warr, wreq, set())
+    with ClockSampler(clock_gpu) as clk:
+        lat, status, resid, wall, late = stream(arrivals, reqs, sampled)
     gen.shutdown()
-    st = srv.stats()
     srv.close()
     torch.cuda.empty_cache()
     # checks: the oracle on the sampled requests with N <= 512 (spawned pool, CPU), while the
@@ -895,14 +908,15 @@ def serving_leg(args, dbar, torch, clock_gpu=0):
     lat = np.array(lat)
     nmix = {str(N): int(sum(1 for r in reqs if r[0] == N)) for N in wl.SERVING_SIZES}
     return {"rate_req_s": args.rate, "duration_s": args.duration, "requests": len(reqs),
-            "solves_per_s": round(st["solves_per_s"], 2), "wall_s": round(wall, 2),
+            "solves_per_s": round(len(lat) / wall, 2), "wall_s": round(wall, 2),
+            "warmup_s": args.serve_warmup,
             "p50_ms": round(float(np.percentile(lat, 50)), 2), "p99_ms": round(float(np.percentile(lat, 99)), 2),
             "status_ok": int(sum(s_ == dbar.DBAR_OK for s_ in status)), "resid_max": float(max(resid)),
             "err_vs_fp64_gpu_max": float(max(err64)), "err_vs_fp64_gpu_sample": len(err64),
             "err_vs_oracle_max": float(max(err_orc)) if err_orc else None,
             "err_vs_oracle_sample": f"{len(err_orc)} requests with N <= 512 of the 2% sample "
                                     f"(N of the sample: {sorted(set(reqs[i][0] for i in orc_idx))})",
-            "late_submits": late[0], "n_mix": nmix,
+            "late_submits": late, "n_mix": nmix,
             "config": {"L": L, "kmax": KMAX, "xi_q": XI_Q, "per_request_seed": f"{args.seed} + request index",
                        "terms": "1-6 per request", "restart": args.restart, "inner_tol": args.inner_tol,
                        "serve_batch": args.serve_batch, "budget_bytes": int(free * 0.7)},
@@ -984,6 +998,8 @@ def main():
     ap.add_argument("--serve-oracle", dest="serve_oracle", type=int, default=32,
                     help="serving: at most this many sampled requests (N <= 512) checked against the CPU oracle")
     ap.add_argument("--no-serving", action="store_true", help="default workload: skip the serving leg")
+    ap.add_argument("--serve-warmup", dest="serve_warmup", type=float, default=3.0,
+                    help="serving: seconds of uncounted traffic before the measured stream")
     ap.add_argument("--no-fp64-resid", dest="no_fp64_resid", action="store_true",
                     help="default workload: skip the leg with the refinement in native FP64")
     ap.add_argument("--seed", type=int, default=5)

@@ -13,7 +13,9 @@
 //
 // Device memory is admitted by a budget: a lane gets as many slots as the
 // budget leaves room for; idle lanes are dropped when another grid class
-// needs the memory.  A lane whose GPU work fails has its in-flight requests
+// needs the memory.  Host copies of potentials and results live in
+// page-locked buffers recycled through a pool (no page faults, and the
+// copies to and from the GPU run at the host link's rate).  A lane whose GPU work fails has its in-flight requests
 // re-queued once (then failed with the error) and is rebuilt on demand.
 #include <cuda_runtime.h>
 
@@ -37,11 +39,57 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+// Page-locked host buffers of 2 N^2 doubles, recycled by size.
+class HostPool {
+ public:
+  double* get(size_t n) {
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      std::vector<double*>& f = free_[n];
+      if (!f.empty()) {
+        double* p = f.back();
+        f.pop_back();
+        pooled_ -= n * sizeof(double);
+        return p;
+      }
+    }
+    void* p = nullptr;
+    if (cudaHostAlloc(&p, n * sizeof(double), cudaHostAllocPortable) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return static_cast<double*>(p);
+  }
+  void put(double* p, size_t n) {
+    if (!p) return;
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      if (pooled_ + n * sizeof(double) <= kMaxPooled) {
+        free_[n].push_back(p);
+        pooled_ += n * sizeof(double);
+        return;
+      }
+    }
+    cudaFreeHost(p);
+  }
+  ~HostPool() {
+    for (auto& kv : free_)
+      for (double* p : kv.second) cudaFreeHost(p);
+  }
+
+ private:
+  static constexpr size_t kMaxPooled = (size_t)8 << 30;  // idle pinned bytes kept for reuse
+  std::mutex mu_;
+  std::map<size_t, std::vector<double*>> free_;
+  size_t pooled_ = 0;
+};
+
 struct Request {
   uint64_t ticket = 0;
   int N = 0;
   double L = 0.0;
-  std::vector<double> Q;  // 2 N^2 (copied at submit)
+  size_t n2 = 0;          // 2 N^2 doubles per field
+  double* Q = nullptr;    // copied at submit (pool buffer), returned once the request is finished
   double k1 = 0.0, k2 = 0.0;
   int want_m = 0;
   int retries = 0;
@@ -49,7 +97,8 @@ struct Request {
   int status = DBAR_EBUSY;
   int itot = 0, ncyc = 0;
   double resid = 0.0;
-  std::vector<double> S, m;
+  double* S = nullptr;    // results (pool buffers), returned at release
+  double* m = nullptr;
   bool released = false;
 };
 
@@ -90,6 +139,7 @@ struct dbar_server {
   std::vector<double> latencies;
   double first_submit = -1.0, last_done = -1.0;
   uint64_t completed = 0;
+  HostPool pool;
 
   double now_ms() const { return std::chrono::duration<double, std::milli>(Clock::now() - t0).count(); }
 };
@@ -147,8 +197,8 @@ void finish(dbar_server* S, Request* r, int status) {
   S->latencies.push_back(r->t_done - r->t_submit);
   S->last_done = r->t_done;
   S->completed += 1;
-  r->Q.clear();
-  r->Q.shrink_to_fit();
+  S->pool.put(r->Q, r->n2);
+  r->Q = nullptr;
 }
 
 // A lane's GPU work failed: re-queue its in-flight requests once, fail repeat
@@ -193,12 +243,13 @@ bool step_lane(dbar_server* S, Lane* ln) {
   for (int s = 0; s < B; ++s) {
     Request* r = ln->slot[s];
     if (!r || act[s]) continue;
-    const size_t n2 = 2 * (size_t)r->N * r->N;
-    r->S.resize(n2);
-    if (r->want_m) r->m.resize(n2);
     lk.unlock();
-    st = plan_read_slot(ln->plan, s, r->S.data(), r->want_m ? r->m.data() : nullptr, &r->itot, &r->ncyc, &r->resid,
-                        ln->stream);
+    if (!r->S) r->S = S->pool.get(r->n2);
+    if (r->want_m && !r->m) r->m = S->pool.get(r->n2);
+    st = (!r->S || (r->want_m && !r->m))
+             ? dbar_internal_fail(DBAR_ENOMEM, "page-locked host buffer for a result")
+             : plan_read_slot(ln->plan, s, r->S, r->want_m ? r->m : nullptr, &r->itot, &r->ncyc, &r->resid,
+                              ln->stream);
     lk.lock();
     if (st != DBAR_OK) {
       lane_failed(S, ln, st);
@@ -228,7 +279,7 @@ bool step_lane(dbar_server* S, Lane* ln) {
   lk.unlock();
   st = DBAR_OK;
   for (int s = 0; s < B && st == DBAR_OK; ++s)
-    if (admit[s]) st = plan_load_slot(ln->plan, s, admit[s]->Q.data(), admit[s]->k1, admit[s]->k2, ln->stream);
+    if (admit[s]) st = plan_load_slot(ln->plan, s, admit[s]->Q, admit[s]->k1, admit[s]->k2, ln->stream);
   if (st == DBAR_OK && nnew) st = plan_begin(ln->plan, B, mask.data(), ln->stream);
   if (st == DBAR_OK && occupied) st = plan_step(ln->plan, B, ln->stream);
   if (st == DBAR_OK && inject) st = dbar_internal_fail(DBAR_ECUDA, "injected lane failure");
@@ -262,10 +313,22 @@ void worker_main(dbar_server* S) {
   }
 }
 
-bool finite_all(const double* p, size_t n) {
-  for (size_t i = 0; i < n; ++i)
-    if (!std::isfinite(p[i])) return false;
-  return true;
+// dst = src (n doubles); false if some entry is not finite
+bool copy_finite(double* __restrict__ dst, const double* __restrict__ src, size_t n) {
+  bool ok = true;
+  for (size_t i = 0; i < n; ++i) {
+    const double v = src[i];
+    ok &= std::isfinite(v);
+    dst[i] = v;
+  }
+  return ok;
+}
+
+void free_request(dbar_server* S, Request* r) {
+  S->pool.put(r->Q, r->n2);
+  S->pool.put(r->S, r->n2);
+  S->pool.put(r->m, r->n2);
+  delete r;
 }
 
 void fill_result(const dbar_server* S, const Request* r, dbar_result* out) {
@@ -276,8 +339,8 @@ void fill_result(const dbar_server* S, const Request* r, dbar_result* out) {
   out->latency_ms = r->t_done - r->t_submit;
   out->queue_ms = r->t_start >= 0 ? r->t_start - r->t_submit : 0.0;
   out->run_ms = r->t_start >= 0 ? r->t_done - r->t_start : 0.0;
-  out->S = r->S.empty() ? nullptr : r->S.data();
-  out->m = r->m.empty() ? nullptr : r->m.data();
+  out->S = r->t_done >= 0 ? r->S : nullptr;
+  out->m = r->t_done >= 0 ? r->m : nullptr;
   (void)S;
 }
 
@@ -319,15 +382,25 @@ extern "C" dbar_status dbar_serve_submit(dbar_server_t S, const dbar_request* rq
   if (!rq->Q) return dbar_internal_fail(DBAR_EINVAL, "request Q is NULL");
   if (!std::isfinite(rq->k_re) || !std::isfinite(rq->k_im)) return dbar_internal_fail(DBAR_EINVAL, "k is not finite");
   const size_t n2 = 2 * (size_t)N * N;
-  if (!finite_all(rq->Q, n2)) return dbar_internal_fail(DBAR_EINVAL, "Q has a non-finite entry");
   dbar_params p = lane_params(S, N, rq->L, 1);
   if (plan_fixed_bytes(&p) + plan_slot_bytes(&p, 1) > S->budget)
     return dbar_internal_fail(DBAR_ENOMEM, "one slot of this grid does not fit the memory budget");
+  // copy into a page-locked pool buffer and check for non-finite entries in the same pass
+  double* q = S->pool.get(n2);
+  if (!q) return dbar_internal_fail(DBAR_ENOMEM, "page-locked host buffer for the potential");
+  if (!copy_finite(q, rq->Q, n2)) {
+    S->pool.put(q, n2);
+    return dbar_internal_fail(DBAR_EINVAL, "Q has a non-finite entry");
+  }
   Request* r = new (std::nothrow) Request();
-  if (!r) return dbar_internal_fail(DBAR_ENOMEM, "host allocation failed");
+  if (!r) {
+    S->pool.put(q, n2);
+    return dbar_internal_fail(DBAR_ENOMEM, "host allocation failed");
+  }
   r->N = N;
   r->L = rq->L;
-  r->Q.assign(rq->Q, rq->Q + n2);
+  r->n2 = n2;
+  r->Q = q;
   r->k1 = rq->k_re;
   r->k2 = rq->k_im;
   r->want_m = rq->want_m;
@@ -385,7 +458,7 @@ extern "C" dbar_status dbar_serve_release(dbar_server_t S, uint64_t ticket) {
   auto it = S->reqs.find(ticket);
   if (it == S->reqs.end()) return dbar_internal_fail(DBAR_EINVAL, "unknown ticket");
   if (it->second->t_done < 0) return dbar_internal_fail(DBAR_EBUSY, "request still running");
-  delete it->second;
+  free_request(S, it->second);
   S->reqs.erase(it);
   return DBAR_OK;
 }
@@ -440,7 +513,7 @@ extern "C" dbar_status dbar_serve_destroy(dbar_server_t S) {
     if (l->stream) cudaStreamDestroy(l->stream);
     delete l;
   }
-  for (auto& kv : S->reqs) delete kv.second;
+  for (auto& kv : S->reqs) free_request(S, kv.second);
   cudaStreamDestroy(S->stream);
   delete S;
   return DBAR_OK;
