@@ -146,11 +146,12 @@ typedef struct {
                         Plan creation briefly takes 2(M+1) FP64 fields more
                         for building its tables                               */
   int support_skip;  /* DBAR_MIXED, one potential per plan, Sec. 4 equation: 1
-                        (default): the FP32 inner operator skips the grid
-                        columns (and its column pass the rows) on which Q is
-                        exactly zero in FP32, where w = E_k Q conj(h) is exactly
-                        zero -- the same values, less work and traffic for a
-                        potential concentrated near the origin; 0: every column */
+                        (default): the FP32 inner operator and the double-float
+                        residual skip the grid columns on which Q is exactly
+                        zero in FP32 (and in its double-float copy, a pair of
+                        floats), where w = E_k Q conj(h) is exactly zero --
+                        the same values, less work and traffic for a potential
+                        concentrated near the origin; 0: every column         */
   int row_shape;     /* DBAR_MIXED: lines per block of the FP32 operator's row
                         passes.  0 (default): timed at plan creation with
                         autotune = 1 (else the first shape); 1..5: the first

@@ -291,13 +291,21 @@ __global__ void __launch_bounds__(ColG<T, LOGN, CV>::THREADS, ColG<T, LOGN, CV>:
     const cx<T> fill = coef[M + 1];
 #pragma unroll
     for (int q = 0; q < 16; ++q) v[q] = v[q] + fill;
+    // rows outside [sy0, sy1) (operator only, where the plan sets a band): Q = 0 there
+    // and w = 0 below, so their table loads are skipped; a branch uniform over the grid
+    const bool band = MODE != PB_HOUT && (a.sy0 > 0 || a.sy1 < N);
     for (int n = 0; n <= M; ++n) {
       const cx<T> cn = coef[n];
       const cx<T>* D = a.Delta + ((size_t)n * N + t) * N + j1;
+      if (band) {
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const int y = t + q * TPL;  // operator and its first half: rows where Q = 0 give w = 0 below
-        if (MODE == PB_HOUT || (y >= a.sy0 && y < a.sy1)) v[q] = v[q] + cmul(cn, ldg(D + (size_t)q * TPL * N));
+        for (int q = 0; q < 16; ++q) {
+          const int y = t + q * TPL;
+          if (y >= a.sy0 && y < a.sy1) v[q] = v[q] + cmul(cn, ldg(D + (size_t)q * TPL * N));
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) v[q] = v[q] + cmul(cn, ldg(D + (size_t)q * TPL * N));
       }
     }
   }
@@ -306,15 +314,23 @@ __global__ void __launch_bounds__(ColG<T, LOGN, CV>::THREADS, ColG<T, LOGN, CV>:
     const cx<T> exv = cscale(ldg(a.ex + (size_t)slot * N + j1), (T)a.sw);
     const cx<T>* EY = a.ey + (size_t)slot * N + t;
     const cx<T>* QC = a.Q + (size_t)slot * a.q_ss + (size_t)t * N + j1;
+    if (a.sy0 > 0 || a.sy1 < N) {
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const int y = t + q * TPL;
-      if (!(y >= a.sy0 && y < a.sy1)) {
-        v[q] = mkc((T)0, (T)0);  // Q = 0 on this row: w = 0 exactly
-        continue;
+      for (int q = 0; q < 16; ++q) {
+        const int y = t + q * TPL;
+        if (!(y >= a.sy0 && y < a.sy1)) {
+          v[q] = mkc((T)0, (T)0);  // Q = 0 on this row: w = 0 exactly
+          continue;
+        }
+        const cx<T> eq = cmul(cmul(exv, ldg(EY + q * TPL)), ldg(QC + (size_t)q * TPL * N));
+        v[q] = (MODE == PB_RHS) ? eq : cmulc(eq, v[q]);
       }
-      const cx<T> eq = cmul(cmul(exv, ldg(EY + q * TPL)), ldg(QC + (size_t)q * TPL * N));
-      v[q] = (MODE == PB_RHS) ? eq : cmulc(eq, v[q]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const cx<T> eq = cmul(cmul(exv, ldg(EY + q * TPL)), ldg(QC + (size_t)q * TPL * N));
+        v[q] = (MODE == PB_RHS) ? eq : cmulc(eq, v[q]);
+      }
     }
     if (MODE != PB_W) fft_line<T, LOGN, false, std::is_same<T, float>::value>(v, sl, t, a.tw);
   }
@@ -372,13 +388,23 @@ __global__ void __launch_bounds__(ColG<T, LOGN, 0>::THREADS, 1) k_pass_b2(const 
       vb[q] = vb[q] + fb;
     }
   }
+  const bool band = a.sy0 > 0 || a.sy1 < N;
   for (int n = 0; n <= M; ++n) {
     const cx<T> ca = coef[n], cb = coef[M + 2 + n];
     const cx<T>* D = a.Delta + ((size_t)n * N + t) * N + j1;
+    if (band) {  // rows outside [sy0, sy1): Q = 0, w = 0 below; no table loads
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const int y = t + q * TPL;  // rows where Q = 0 give w = 0 below
-      if (y >= a.sy0 && y < a.sy1) {
+      for (int q = 0; q < 16; ++q) {
+        const int y = t + q * TPL;
+        if (y >= a.sy0 && y < a.sy1) {
+          const cx<T> d = ldg(D + (size_t)q * TPL * N);
+          va[q] = va[q] + cmul(ca, d);
+          vb[q] = vb[q] + cmul(cb, d);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
         const cx<T> d = ldg(D + (size_t)q * TPL * N);
         va[q] = va[q] + cmul(ca, d);
         vb[q] = vb[q] + cmul(cb, d);
@@ -395,7 +421,7 @@ __global__ void __launch_bounds__(ColG<T, LOGN, 0>::THREADS, 1) k_pass_b2(const 
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       const int y = t + q * TPL;
-      if (!(y >= a.sy0 && y < a.sy1)) {  // Q = 0 on this row: w = 0 exactly
+      if (band && !(y >= a.sy0 && y < a.sy1)) {  // Q = 0 on this row: w = 0 exactly
         va[q] = mkc((T)0, (T)0);
         vb[q] = mkc((T)0, (T)0);
         continue;

@@ -56,6 +56,10 @@ dbar_status dbar_internal_fail(dbar_status st, const std::string& msg) { return 
                   std::string(#call) + ": " + cudaGetErrorString(e_));                       \
   } while (0)
 
+// Taylor orders up to which the column pass also skips its table loads on the rows
+// outside the potential's support
+constexpr int kRowBandMaxM = 4;
+
 // Kernel kinds for the event profiler (dbar_profile_*).
 enum {
   K_PASS_A, K_PASS_B, K_PASS_C, K_DOTS, K_UPDATE, K_SCALAR, K_XUPDATE,
@@ -209,7 +213,7 @@ struct dbar_plan {
   int* h_dshift = nullptr;      // [B][2] host staging
   int* h_err = nullptr;         // pinned copy of flag[1]: a bounded device wait ran out
   // support of the potential in FP32 (Q32 exactly zero outside): columns [sx0, sx1), aligned
-  // to every column-pass tile width, and rows [sy0, sy1); used by the FP32 inner operator
+  // to every column-pass tile width; used by the FP32 inner operator and the double-float residual
   bool sup = false;
   int sx0 = 0, sx1 = 0, sy0 = 0, sy1 = 0;
   int* supflag = nullptr;       // [2N] device: column, then row flags of the support scan
@@ -511,9 +515,10 @@ PassArgs<dd> base_args<dd>(const dbar_plan* P) {
 // E = 1 in the column pass: per-slot rows of ones in place of the slot's E_k
 // factors (K_0 of the iterated equation, its right-hand side); the same layout
 // keeps the column pass's indexing unchanged
-// The FP32 inner operator's passes skip the columns (and pass B the rows) where the
-// potential is exactly zero in FP32: there w = E_k Q conj(h) = 0, so the skipped work
-// is exactly zero (the same values as the full passes).  The double-float copy of Q
+// The FP32 inner operator's passes skip the columns where the potential is exactly
+// zero in FP32 (and its column pass the table loads on the rows where it is): there
+// w = E_k Q conj(h) = 0, so the skipped work is exactly zero (the same values as the
+// full passes).  The double-float copy of Q
 // is a pair of floats, zero exactly where the FP32 copy is, so the double-float
 // right-hand side and residual passes skip the same columns and rows.
 template <typename T>
@@ -522,8 +527,12 @@ static void set_support(const dbar_plan* P, PassArgs<T>& a) {
     if (P->sup) {
       a.sx0 = P->sx0;
       a.sx1 = P->sx1;
-      a.sy0 = P->sy0;
-      a.sy1 = P->sy1;
+      // the row band only for low Taylor orders: at larger ones the per-row test costs the
+      // table loads' batching more than the skipped loads save
+      if ((std::is_same<T, float>::value ? P->Min : P->M) <= kRowBandMaxM) {
+        a.sy0 = P->sy0;
+        a.sy1 = P->sy1;
+      }
     }
   }
 }
@@ -790,9 +799,11 @@ static void account_cycle(dbar_plan* P, const int* act, const int* ns, int nb, i
   if (!P->prof.on) return;
   const double F = (double)P->n * P->inner_elem(), F64 = (double)P->n * sizeof(cx<double>);
   const double fx = P->sup ? (double)(P->sx1 - P->sx0) / P->N : 1.0;
-  const double fy = P->sup ? (double)(P->sy1 - P->sy0) / P->N : 1.0;
-  // the double-float residual passes skip the same columns and rows (FP64 ones do not)
-  const double rx = P->resid_dd ? fx : 1.0, ry = P->resid_dd ? fy : 1.0;
+  // table rows the column passes read (the support's rows at low Taylor orders)
+  const double fy = (P->sup && (P->mixed ? P->Min : P->M) <= kRowBandMaxM) ? (double)(P->sy1 - P->sy0) / P->N : 1.0;
+  // the double-float residual passes skip the same columns (FP64 ones do not)
+  const double rx = P->resid_dd ? fx : 1.0;
+  const double ry = (P->resid_dd && P->sup && P->M <= kRowBandMaxM) ? (double)(P->sy1 - P->sy0) / P->N : 1.0;
   double* by = P->prof.bytes;
   int nact = 0;
   for (int s = 0; s < nb; ++s) {
@@ -839,7 +850,7 @@ static void account_cycle(dbar_plan* P, const int* act, const int* ns, int nb, i
     by[K_RES_C] += (2.0 + rx) * F64 + F;
   }
   if (P->conv) return;
-  // shared tables Q, Delta_n per launch, on the support's columns and rows
+  // shared tables Q, Delta_n per launch, on the support's columns (and rows)
   by[K_PASS_B] += (double)launched_steps * ((P->mixed ? P->Min : P->M) + 2) * F * fx * fy;
   if (nact) by[K_RES_B] += (P->M + 2) * F64 * rx * ry;
 }
@@ -1779,7 +1790,7 @@ static dbar_status load_Q_device(dbar_plan* P, const cx<double>* Qd, cudaStream_
   CK(timed(P, st, K_OTHER, [&] { return launch_check_finite(reinterpret_cast<const double*>(Qd), 2 * P->n, P->flag, st); }));
   CK(timed(P, st, K_OTHER, [&] { return launch_load_q(Qd, P->Q64, P->Q32, P->N, st); }));
   if (P->resid_dd) CK(timed(P, st, K_OTHER, [&] { return launch_split_fields(P->Q64, P->Q_dd, P->n, st); }));
-  // support of the FP32 potential (the inner operator skips the columns and rows where it is zero)
+  // support of the FP32 potential (the inner operator skips the columns where it is zero)
   const bool scan = P->mixed && !P->per_slot_q && !P->iter && !P->conv && P->p.support_skip;
   std::vector<int> fl(scan ? 2 * P->N : 0);
   if (scan) {

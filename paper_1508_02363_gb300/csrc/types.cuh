@@ -54,11 +54,12 @@ struct PassArgs {
   // grid offset (s1, s2) of xi0 by which the input was rolled, so that the divisor of rolled
   // element p is the unwrapped xi_{p + s} - xi0 (nullable: the plain divisor xi_p)
   const int* dshift;
-  // support of the potential in the FP32 inner operator: the columns [sx0, sx1) (a
-  // multiple of every column-pass tile width) and rows [sy0, sy1) outside which Q is
-  // exactly zero, so that w = E_k Q conj(h) is exactly zero there: pass A stores and
-  // pass C loads only those columns of the pass intermediates, pass B transforms only
-  // those columns and loads its tables only on those rows.  Full ranges elsewhere.
+  // support of the potential in the FP32 inner operator (and the double-float
+  // residual): the columns [sx0, sx1) (a multiple of every column-pass tile width)
+  // outside which Q is exactly zero, so that w = E_k Q conj(h) is exactly zero there:
+  // pass A stores and pass C loads only those columns of the pass intermediates, and
+  // pass B transforms only those columns.  Rows [sy0, sy1): pass B loads its tables
+  // only there (the full range -- no per-row test -- unless the plan sets a band).
   int sx0, sx1, sy0, sy1;
 };
 

@@ -150,7 +150,7 @@ def test_memory_budget_bounds_the_plan(dbar):
 @pytest.mark.parametrize("N,L,nk", [(256, 8.0, 5), (1024, 10.0, 3)])
 def test_support_skip_gives_the_same_solution(dbar, N, L, nk):
     # A potential concentrated near the origin (narrow Gaussians): Q is exactly zero in
-    # FP32 on most columns and rows of the box, where the FP32 inner operator skips its
+    # FP32 on most columns of the box, where the FP32 inner operator skips its
     # work; the solution is the same as with every column processed, value for value
     rng = np.random.default_rng(31)
     Q = wl.gaussian_mixture(N, L, rng.uniform(-1.5, 1.5, (3, 2)), rng.uniform(0.4, 0.8, 3),
