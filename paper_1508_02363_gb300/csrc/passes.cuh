@@ -183,11 +183,17 @@ __device__ __forceinline__ void row_a(const PassArgs<T>& a, cx<T> (&v)[16], int 
     }
   }
   fft_line<T, LOGN, true, std::is_same<T, float>::value>(v, sl, t, a.tw);
-  // only the columns the column pass reads (those where Q is not zero)
+  // only the columns the column pass reads (those where Q is not zero); the test is
+  // skipped (a grid-uniform branch) when every column is read
+  if (a.sx0 > 0 || a.sx1 < N) {
 #pragma unroll
-  for (int q = 0; q < 16; ++q) {
-    const int x = t + q * TPL;
-    if (x >= a.sx0 && x < a.sx1) dst[q * TPL] = v[q];
+    for (int q = 0; q < 16; ++q) {
+      const int x = t + q * TPL;
+      if (x >= a.sx0 && x < a.sx1) dst[q * TPL] = v[q];
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 16; ++q) dst[q * TPL] = v[q];
   }
 }
 
@@ -230,10 +236,15 @@ __global__ void __launch_bounds__(RowG<T, LOGN, RV>::THREADS, RowG<T, LOGN, RV>:
   cx<T> v[16];
   const cx<T>* src = a.in + (size_t)slot * a.in_ss + (size_t)p2 * N + t;
   // columns outside the potential's support are exactly zero (not stored by the column pass)
+  if (a.sx0 > 0 || a.sx1 < N) {
 #pragma unroll
-  for (int q = 0; q < 16; ++q) {
-    const int x = t + q * TPL;
-    v[q] = (x >= a.sx0 && x < a.sx1) ? ldg(src + q * TPL) : mkc((T)0, (T)0);
+    for (int q = 0; q < 16; ++q) {
+      const int x = t + q * TPL;
+      v[q] = (x >= a.sx0 && x < a.sx1) ? ldg(src + q * TPL) : mkc((T)0, (T)0);
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = ldg(src + q * TPL);
   }
   fft_line<T, LOGN, false, std::is_same<T, float>::value>(v, sl, t, a.tw);
   cx<T>* kp = reinterpret_cast<cx<T>*>(a.out) + (size_t)slot * a.out_ss + (size_t)p2 * N + t;
@@ -563,10 +574,15 @@ __global__ void __launch_bounds__(RowG<T, LOGN, RV>::THREADS, RowG<T, LOGN, RV>:
   const cx<T>* src = a.in + (size_t)slot * a.in_ss + (size_t)p2 * N + t;
   cx<T> v[16];
   // columns outside the potential's support are exactly zero (not stored by the column pass)
+  if (a.sx0 > 0 || a.sx1 < N) {
 #pragma unroll
-  for (int q = 0; q < 16; ++q) {
-    const int x = t + q * TPL;
-    v[q] = (x >= a.sx0 && x < a.sx1) ? ldg(src + q * TPL) : mkc((T)0, (T)0);
+    for (int q = 0; q < 16; ++q) {
+      const int x = t + q * TPL;
+      v[q] = (x >= a.sx0 && x < a.sx1) ? ldg(src + q * TPL) : mkc((T)0, (T)0);
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = ldg(src + q * TPL);
   }
   fft_line<T, LOGN, MODE == PC_INV, std::is_same<T, float>::value>(v, sl, t, a.tw);
   // squared-norm partials.  FP64 for FP64 fields and for the right-hand side
