@@ -116,8 +116,9 @@ def test_rhs_matches_oracle(dbar, torch_cuda, prec):
 
 
 @pytest.mark.parametrize("fp32", [False, True])
-@pytest.mark.parametrize("N", [64, 128, 2048])
+@pytest.mark.parametrize("N", [64, 128, 1024, 2048])
 def test_operator_application_matches_oracle(dbar, torch_cuda, fp32, N):
+    # (the FP32 rows of N = 1024 run the radix-32 x 32 kernels, the other sizes radix 16)
     torch = torch_cuda
     L = 6.0
     rng = np.random.default_rng(N + fp32)
@@ -127,7 +128,7 @@ def test_operator_application_matches_oracle(dbar, torch_cuda, fp32, N):
     Sd = dev(torch, S, fp32)
     ASd = torch.empty_like(Sd)
     dbar.dbar_apply(plan.handle, dev(torch, w.Q), w.k, Sd, ASd, fp32)
-    for i in range(3 if N < 2048 else 1):   # one oracle operator at the largest grid
+    for i in range(3 if N < 1024 else 1):   # one oracle operator at the largest grids
         P = orc.CGOProblem(w.Q, w.k[i], N, L, M=2)
         ref = P.apply(S[i].astype(np.complex64).astype(complex) if fp32 else S[i])
         assert rel(ASd[i].cpu().numpy(), ref) < (2e-5 if fp32 else 1e-13)
