@@ -244,6 +244,7 @@ def run_ours(args):
                      autotune=args.autotune, row_shape=args.row_shape)
     colv, tune = dbar.dbar_plan_tuning(plan.handle)
     rowv, rtune = dbar.dbar_plan_row_tuning(plan.handle)
+    rowv_ac, rtune_ac = dbar.dbar_plan_row_tuning(plan.handle, "plain")
     stream = torch.cuda.current_stream()
     Qd = torch.from_numpy(w.Q).cuda()
     Sd = torch.empty((nk, N, N), dtype=torch.complex128, device="cuda")
@@ -284,6 +285,7 @@ def run_ours(args):
             print(json.dumps({"quick": True, "workload": w.name, "nk": nk, "ms_per_step": ms_per_step,
                               "solves_per_s": value, "iters_inner_mean": float(np.mean(iters[:, 0])),
                               "resid_max": float(np.max(resid)), "gpu_launches": int(launches),
+                              "column_variant": colv, "row_shape": rowv, "row_shape_plain": rowv_ac,
                               "kinds": {k: [round(v[0], 3), v[1], round(v[2] / (v[0] / 1e3) / 1e9, 1)
                                             if v[0] > 0 else 0] for k, v in prof.items()}}))
         return
@@ -385,6 +387,7 @@ def run_ours(args):
                       "inner_tol": args.inner_tol,
                       "column_variant": colv, "column_tune_ms": [round(x, 4) for x in tune],
                       "row_shape": rowv, "row_tune_ms": [round(x, 4) for x in rtune],
+                      "row_shape_plain": rowv_ac, "row_tune_ms_plain": [round(x, 4) for x in rtune_ac],
                       "parallelism": f"replicas over k x{world}",
                       "l2": "inputs larger than L2 (device working set %.1f GB)" % (plan.device_bytes / 1e9)},
            "step_p50_ms": round(statistics.median(step_ms), 3),
@@ -508,8 +511,10 @@ def run_uneven(args):
            "resid_max": resid_max, "err_vs_fp64_max": max(errs), "err_sample": len(errs),
            "groups": {f"{N}/{'ab'[pot]}": len(v) for (N, pot), v in sorted(groups.items())},
            "autotune": bool(args.autotune),
-           "tiles": {str(N): dict(zip(("column_variant", "ms_per_variant", "row_shape", "ms_per_row_shape"),
-                                      dbar.dbar_plan_tuning(p.handle) + dbar.dbar_plan_row_tuning(p.handle)))
+           "tiles": {str(N): dict(zip(("column_variant", "ms_per_variant", "row_shape", "ms_per_row_shape",
+                                       "row_shape_plain", "ms_per_row_shape_plain"),
+                                      dbar.dbar_plan_tuning(p.handle) + dbar.dbar_plan_row_tuning(p.handle)
+                                      + dbar.dbar_plan_row_tuning(p.handle, "plain")))
                      for N, p in sorted(plans.items())},
            "config": {"L": L, "kmax": 12.0, "restart": args.restart, "inner_tol": args.inner_tol},
            "clocks": clk.summary()}

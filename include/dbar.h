@@ -436,6 +436,14 @@ dbar_status dbar_profile_read(dbar_plan_t plan, int kind, double* ms, long long*
 dbar_status dbar_plan_tuning(dbar_plan_t plan, int* column_variant, double* ms_per_variant, int* row_shape,
                              double* ms_per_row_shape);
 
+/* The row-pass shape of the FP32 operator's plain row passes (pass A of each
+ * block's first vector, pass C of the last), tuned apart from the fused chain
+ * pass that dbar_plan_tuning reports (their best shapes differ): the shape in
+ * use (0-based) and the ms per pass A + pass C pair of each shape in
+ * ms_per_row_shape[DBAR_ROW_VARIANTS] (0 when not tuned).  A fixed row_shape
+ * parameter sets both.  Either pointer may be NULL; DBAR_EINVAL for a NULL plan. */
+dbar_status dbar_plan_row_tuning(dbar_plan_t plan, int* row_shape, double* ms_per_row_shape);
+
 /* Test hook for the device-side bounded waits (no counterpart in the paper):
  * the next block-update launch of this plan announces 16 bytes more on its
  * first bulk-copy stage than the copy delivers, so that stage's mbarrier phase

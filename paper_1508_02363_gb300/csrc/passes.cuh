@@ -98,7 +98,7 @@ struct ColG {
 // dst (this thread's first element of the row).  Used by k_pass_a and by the
 // fused row pass k_pass_ca.
 // ---------------------------------------------------------------------------
-template <typename T, int LOGN, bool SH = false>
+template <typename T, int LOGN, bool SH = false, bool MOM = true>
 __device__ __forceinline__ void row_a(const PassArgs<T>& a, cx<T> (&v)[16], int slot, int p2, int t, cx<T>* sl,
                                       cx<T>* dst) {
   using G = RowG<T, LOGN>;
@@ -118,7 +118,8 @@ __device__ __forceinline__ void row_a(const PassArgs<T>& a, cx<T> (&v)[16], int 
     const cx<T> s0 = v[0];
     part[0] = mkc((PT)s0.re * N, (PT)s0.im * N);
   }
-  for (int aa = 1; aa <= MA; ++aa) {
+  // (MOM false: the a >= 1 partials were written from the row's column-pass output, ca_moments)
+  for (int aa = 1; MOM && aa <= MA; ++aa) {
     cx<T> acc = mkc((T)0, (T)0);
     const cx<T>* D = a.Da + (size_t)aa * N + t;
 #pragma unroll
@@ -218,6 +219,45 @@ __global__ void __launch_bounds__(RowG<T, LOGN, RV>::THREADS, RowG<T, LOGN, RV>:
 }
 
 // ---------------------------------------------------------------------------
+// Row moments of the next chain vector S' = K p from the column-pass output T2
+// of p, before the row DFT.  With S'(p1,p2) = i (-1)^{p1+p2} sum_x T2(x,p2)
+// e^{-2 pi i p1 x/N} and D_a(p1) = sum_j x_j^a e^{+2 pi i p1 j/N}, the sum over
+// p1 collapses (sum_p1 e^{2 pi i p1 (j - x)/N} = N delta_jx):
+//     R_a(p2) = sum_p1 (-1)^p1 S'(p1,p2) D_a(p1) = i N (-1)^{p2} sum_x x_x^a T2(x,p2),
+// a real-weighted sum with x_j = (2 pi L/N)(j - N/2) formed in registers: no
+// table loads (the fused row pass is bound by its L1/shared-memory traffic).
+// Written as row_a's per-warp-segment partials, a = 1..MA; row_a still writes
+// the a = 0 moment.  FP32 only.
+// ---------------------------------------------------------------------------
+template <int LOGN>
+__device__ __forceinline__ void ca_moments(const PassArgs<float>& a, const cx<float> (&v)[16], int slot, int p2,
+                                           int t) {
+  using G = RowG<float, LOGN>;
+  constexpr int N = G::N, TPL = G::TPL;
+  constexpr int SEGW = TPL >= 32 ? 32 : TPL, NSEG = TPL >= 32 ? TPL / 32 : 1;
+  const int M = a.M, MA = M > 1 ? M : 1;
+  const int seg = TPL >= 32 ? t / 32 : 0;
+  cx<float>* part = reinterpret_cast<cx<float>*>(a.partA) + ((size_t)slot * N + p2) * NSEG * (MA + 1);
+  const float tm = (float)(t - N / 2), hx = a.hx_f;
+  const float sN = (p2 & 1) ? -(float)N : (float)N;  // N (-1)^{p2}
+  float pw[16];  // x^a of this thread's columns
+#pragma unroll
+  for (int q = 0; q < 16; ++q) pw[q] = 1.f;
+  for (int aa = 1; aa <= MA; ++aa) {
+    float re = 0.f, im = 0.f;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      pw[q] *= hx * (tm + (float)(q * TPL));
+      re = fmaf(pw[q], v[q].re, re);
+      im = fmaf(pw[q], v[q].im, im);
+    }
+    re = warp_sum_t(re, SEGW);
+    im = warp_sum_t(im, SEGW);
+    if ((t & (SEGW - 1)) == 0) part[seg * (MA + 1) + aa] = mkc(-im * sN, re * sN);  // i N (-1)^p2 (re + i im)
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Fused row pass of a Krylov chain step: pass C of K p_i (row DFT of the
 // column pass output, K p_i = i (-1)^p DFT(w) -> out, the next chain vector)
 // followed, on the same rows still in registers, by pass A of K p_i (-> out2).
@@ -246,7 +286,9 @@ __global__ void __launch_bounds__(RowG<T, LOGN, RV>::THREADS, RowG<T, LOGN, RV>:
 #pragma unroll
     for (int q = 0; q < 16; ++q) v[q] = ldg(src + q * TPL);
   }
-  fft_line<T, LOGN, false, std::is_same<T, float>::value>(v, sl, t, a.tw);
+  constexpr bool F32 = std::is_same<T, float>::value;
+  if constexpr (F32) ca_moments<LOGN>(a, v, slot, p2, t);  // moments of K p from T2 (FP32)
+  fft_line<T, LOGN, false, F32>(v, sl, t, a.tw);
   cx<T>* kp = reinterpret_cast<cx<T>*>(a.out) + (size_t)slot * a.out_ss + (size_t)p2 * N + t;
 #pragma unroll
   for (int q = 0; q < 16; ++q) {
@@ -257,8 +299,8 @@ __global__ void __launch_bounds__(RowG<T, LOGN, RV>::THREADS, RowG<T, LOGN, RV>:
     v[q] = y;
   }
   // (the inverse transform's first stage synchronises before it reuses the line buffer)
-  row_a<T, LOGN>(a, v, slot, p2, t, sl,
-                 reinterpret_cast<cx<T>*>(a.out2) + (size_t)slot * a.out2_ss + (size_t)p2 * N + t);
+  row_a<T, LOGN, false, !F32>(a, v, slot, p2, t, sl,
+                             reinterpret_cast<cx<T>*>(a.out2) + (size_t)slot * a.out2_ss + (size_t)p2 * N + t);
 }
 
 // ---------------------------------------------------------------------------

@@ -153,8 +153,10 @@ struct dbar_plan {
   int per_slot_q = 0;   // 1: every slot has its own potential (serving); 0: one Q for all
   int colv = 0;         // FP32 column-pass tile variant (autotuned)
   double tune_ms[DBAR_COLUMN_VARIANTS] = {0.0, 0.0, 0.0};
-  int rowv = 0;         // row-pass shape of the FP32 operator's row passes (autotuned)
+  int rowv = 0;         // row-pass shape of the FP32 fused chain pass (autotuned)
   double row_ms[DBAR_ROW_VARIANTS] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  int rowv_ac = 0;      // row-pass shape of the FP32 passes A and C (autotuned separately)
+  double row_ms_ac[DBAR_ROW_VARIANTS] = {0.0, 0.0, 0.0, 0.0, 0.0};
   int* dmask = nullptr;  // [B] device copy of a slot mask
   int* hmask = nullptr;  // [B] pinned host staging of it
   long long nlaunch = 0;  // kernels launched by this plan
@@ -446,6 +448,7 @@ PassArgs<double> base_args<double>(const dbar_plan* P) {
   a.ey = P->ey64;
   a.inv2piL = P->inv2piL;
   a.inv2piL_f = (float)P->inv2piL;
+  a.hx_f = (float)(2.0 * M_PI * P->p.L / P->N);
   a.sw = P->sw;
   a.fillscale = P->fillscale;
   a.partA = P->partA;
@@ -461,7 +464,7 @@ PassArgs<float> base_args<float>(const dbar_plan* P) {
   PassArgs<float> a;
   std::memset(&a, 0, sizeof(a));
   a.colv = P->colv;
-  a.rowv = P->rowv;
+  a.rowv = P->rowv_ac;  // passes A and C; the fused chain pass sets its own (P->rowv)
   a.g = make_geo<float>(P->N);
   a.sx1 = a.sy1 = P->N;
   a.M = P->Min;
@@ -474,6 +477,7 @@ PassArgs<float> base_args<float>(const dbar_plan* P) {
   a.ey = P->ey32;
   a.inv2piL = P->inv2piL;
   a.inv2piL_f = (float)P->inv2piL;
+  a.hx_f = (float)(2.0 * M_PI * P->p.L / P->N);
   a.sw = P->sw;
   a.fillscale = P->fillscale;
   a.partA = P->partA;
@@ -501,6 +505,7 @@ PassArgs<dd> base_args<dd>(const dbar_plan* P) {
   a.ey = P->ey_dd;
   a.inv2piL = P->inv2piL;
   a.inv2piL_f = (float)P->inv2piL;
+  a.hx_f = (float)(2.0 * M_PI * P->p.L / P->N);
   a.sw = P->sw;
   a.fillscale = P->fillscale;
   a.partA = P->partA;
@@ -962,7 +967,9 @@ static dbar_status block_steps(dbar_plan* P, int nb, int j0, int j1, cudaStream_
       if (i + 1 < S) {
         a.out2 = P->T1;
         a.out2_ss = n;
-        CK(timed(P, st, K_PASS_CA, [&] { return launch_pass_ca<TI>(a, nb, st); }));
+        PassArgs<TI> ca = a;
+        ca.rowv = P->rowv;  // the fused pass's own shape
+        CK(timed(P, st, K_PASS_CA, [&] { return launch_pass_ca<TI>(ca, nb, st); }));
       } else {
         CK(timed(P, st, K_PASS_C, [&] { return launch_pass_c<TI, TI, PC_KS>(a, nb, st); }));
       }
@@ -1372,9 +1379,9 @@ static dbar_status plan_tables(dbar_plan* P) {
 // only affects speed; it is cached per (device, N, M) for the process.
 static std::mutex g_tune_mu;
 struct TuneResult {
-  int colv, rowv;
+  int colv, rowv, rowv_ac;
   std::array<double, DBAR_COLUMN_VARIANTS> col_ms;
-  std::array<double, DBAR_ROW_VARIANTS> row_ms;
+  std::array<double, DBAR_ROW_VARIANTS> row_ms, row_ms_ac;
 };
 static std::map<std::tuple<int, int, int>, TuneResult> g_tune_cache;
 
@@ -1386,8 +1393,10 @@ static dbar_status autotune_columns(dbar_plan* P) {
     if (it != g_tune_cache.end()) {
       P->colv = it->second.colv;
       P->rowv = it->second.rowv;
+      P->rowv_ac = it->second.rowv_ac;
       for (int v = 0; v < DBAR_COLUMN_VARIANTS; ++v) P->tune_ms[v] = it->second.col_ms[v];
       for (int v = 0; v < DBAR_ROW_VARIANTS; ++v) P->row_ms[v] = it->second.row_ms[v];
+      for (int v = 0; v < DBAR_ROW_VARIANTS; ++v) P->row_ms_ac[v] = it->second.row_ms_ac[v];
       return DBAR_OK;
     }
   }
@@ -1453,15 +1462,49 @@ static dbar_status autotune_columns(dbar_plan* P) {
       rchoice = rv;
     }
   }
+  P->rowv = rchoice;
+  // shapes of the plain row passes, timed on a pass A (scaled input) and a pass C (K S) per rep
+  best = 1e300;
+  int acchoice = 0;
+  for (int rv = 0; rv < DBAR_ROW_VARIANTS; ++rv) {
+    PassArgs<float> a = base_args<float>(P);
+    a.rowv = rv;
+    a.in = reinterpret_cast<const cx<float>*>(P->T2);
+    a.in_ss = (long long)n;
+    PassArgs<float> c = a;
+    a.out = P->T1;
+    a.out_ss = (long long)n;
+    c.out = P->KS;
+    c.out_ss = (long long)n;
+    auto once = [&]() -> cudaError_t {
+      cudaError_t e = launch_pass_a<float>(a, nb, st);
+      return e != cudaSuccess ? e : launch_pass_c<float, float, PC_KS>(c, nb, st);
+    };
+    for (int w = 0; w < 2; ++w) CK(once());
+    CK(cudaEventRecord(e0, st));
+    const int reps = 5;
+    for (int r = 0; r < reps; ++r) CK(once());
+    CK(cudaEventRecord(e1, st));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    P->row_ms_ac[rv] = ms / reps;
+    if (ms < best) {
+      best = ms;
+      acchoice = rv;
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  P->rowv = rchoice;
+  P->rowv_ac = acchoice;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   TuneResult t;
   t.colv = choice;
   t.rowv = rchoice;
+  t.rowv_ac = acchoice;
   for (int v = 0; v < DBAR_COLUMN_VARIANTS; ++v) t.col_ms[v] = P->tune_ms[v];
   for (int v = 0; v < DBAR_ROW_VARIANTS; ++v) t.row_ms[v] = P->row_ms[v];
+  for (int v = 0; v < DBAR_ROW_VARIANTS; ++v) t.row_ms_ac[v] = P->row_ms_ac[v];
   g_tune_cache[key] = t;
   return DBAR_OK;
 }
@@ -1712,7 +1755,7 @@ dbar_status plan_create_ex(const dbar_params* p, int per_slot_q, dbar_plan** out
   if (s == DBAR_OK && P->mixed && p->autotune == 1) s = autotune_columns(P);
   if (P->mixed && p->autotune == 2) P->colv = 1;  // fixed second variant (tests)
   if (P->mixed && p->autotune == 3) P->colv = 2;  // fixed third variant (tests)
-  if (P->mixed && p->row_shape > 0) P->rowv = p->row_shape - 1;  // fixed row-pass shape
+  if (P->mixed && p->row_shape > 0) P->rowv = P->rowv_ac = p->row_shape - 1;  // fixed row-pass shape
   if (s != DBAR_OK) {
     delete P;
     return s;
@@ -2340,6 +2383,14 @@ extern "C" dbar_status dbar_plan_tuning(dbar_plan_t P, int* column_variant, doub
   if (row_shape) *row_shape = P->rowv;
   if (ms_per_row_shape)
     for (int v = 0; v < DBAR_ROW_VARIANTS; ++v) ms_per_row_shape[v] = P->row_ms[v];
+  return DBAR_OK;
+}
+
+extern "C" dbar_status dbar_plan_row_tuning(dbar_plan_t P, int* row_shape, double* ms_per_row_shape) {
+  if (!P) return fail(DBAR_EINVAL, "plan is NULL");
+  if (row_shape) *row_shape = P->rowv_ac;
+  if (ms_per_row_shape)
+    for (int v = 0; v < DBAR_ROW_VARIANTS; ++v) ms_per_row_shape[v] = P->row_ms_ac[v];
   return DBAR_OK;
 }
 

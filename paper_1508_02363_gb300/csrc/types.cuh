@@ -41,6 +41,7 @@ struct PassArgs {
   const cx<T>* ey;       // [slot][N]  e^{-2 i k1 y_j}
   double inv2piL;        // 1/(2 pi L)
   float inv2piL_f;       // the same, rounded once on the host (FP32 pass A)
+  float hx_f;            // grid spacing 2 pi L / N, rounded once (FP32 fused row pass moments)
   double sw;             // 2 pi L^2 / N^2
   double fillscale;      // 1/(2 pi L^2), or 0 for the zero-fill reading
   cx<double>* partA;     // [slot][p2][nseg][MA+1] row-moment partials (pass A -> k_coef);

@@ -29,7 +29,8 @@ EXPORTED = ["dbar_params_init", "dbar_last_error", "dbar_plan_create", "dbar_pla
             "dbar_launch_count", "dbar_fft2_noalloc", "dbar_serve_create", "dbar_serve_submit",
             "dbar_serve_poll", "dbar_serve_wait", "dbar_serve_release", "dbar_serve_stats",
             "dbar_serve_inject_fault", "dbar_serve_destroy", "dbar_plan_tuning", "dbar_reflection",
-            "dbar_ds2_potential", "dbar_plan_inject_wait_timeout", "dbar_solve_batches"]
+            "dbar_ds2_potential", "dbar_plan_inject_wait_timeout", "dbar_solve_batches",
+            "dbar_plan_row_tuning"]
 
 
 class dbar_params(ctypes.Structure):
@@ -93,6 +94,7 @@ _lib.dbar_launch_count.argtypes = [_vp, ctypes.POINTER(ctypes.c_longlong)]
 _lib.dbar_plan_inject_wait_timeout.argtypes = [_vp]
 _lib.dbar_solve_batches.argtypes = [ctypes.POINTER(dbar_batch), _int, _vp]
 _lib.dbar_plan_tuning.argtypes = [_vp, _ip, _dp, _ip, _dp]
+_lib.dbar_plan_row_tuning.argtypes = [_vp, _ip, _dp]
 _u64 = ctypes.c_uint64
 _lib.dbar_serve_create.argtypes = [ctypes.POINTER(dbar_params), ctypes.c_size_t, ctypes.POINTER(_vp)]
 _lib.dbar_serve_submit.argtypes = [_vp, ctypes.POINTER(dbar_request), ctypes.POINTER(_u64)]
@@ -325,10 +327,17 @@ def dbar_plan_tuning(plan):
     return v.value, list(ms)
 
 
-def dbar_plan_row_tuning(plan):
-    """(row-pass shape in use, [ms per fused row-pass launch of each shape])."""
+def dbar_plan_row_tuning(plan, passes: str = "fused"):
+    """passes "fused": (shape of the fused chain row pass, [ms per launch of each shape]),
+    from dbar_plan_tuning; "plain": (shape of the row passes A and C, [ms per A + C pair of
+    each shape]), from dbar_plan_row_tuning."""
     v, ms = ctypes.c_int(), (ctypes.c_double * ROW_VARIANTS)()
-    _check(_lib.dbar_plan_tuning(plan, None, None, ctypes.byref(v), ms))
+    if passes == "fused":
+        _check(_lib.dbar_plan_tuning(plan, None, None, ctypes.byref(v), ms))
+    elif passes == "plain":
+        _check(_lib.dbar_plan_row_tuning(plan, ctypes.byref(v), ms))
+    else:
+        raise ValueError("passes must be 'fused' or 'plain'")
     return v.value, list(ms)
 
 

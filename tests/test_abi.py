@@ -72,6 +72,15 @@ def test_params_defaults_and_solve_signature(lib):
     assert st == dbar.DBAR_EINVAL and "plan" in dbar.dbar_last_error()
 
 
+def test_row_tuning_rejects_a_null_plan(lib):
+    from paper_1508_02363_gb300 import dbar
+    with pytest.raises(dbar.DbarError) as e:
+        dbar.dbar_plan_row_tuning(None, "plain")
+    assert e.value.status == dbar.DBAR_EINVAL
+    with pytest.raises(ValueError):
+        dbar.dbar_plan_row_tuning(None, "columns")
+
+
 def test_wait_hook_rejects_a_null_plan(lib):
     from paper_1508_02363_gb300 import dbar
     with pytest.raises(dbar.DbarError) as e:

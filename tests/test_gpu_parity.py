@@ -320,11 +320,12 @@ def test_row_pass_shapes_give_identical_results(dbar, N, nk, L):
     for shape in (1, 2, 3, 4, 5, 0):
         plan = dbar.Plan(w.N, w.L, M=2, prec="mixed", restart=24, tol=1e-12, max_batch=nk, row_shape=shape)
         res.append(plan.solve(w.Q, w.k, want_m=False))
-        rv, ms = dbar.dbar_plan_row_tuning(plan.handle)
-        if shape:
-            assert rv == shape - 1
-        else:
-            assert rv in range(dbar.ROW_VARIANTS) and len(ms) == dbar.ROW_VARIANTS and min(ms) > 0
+        for passes in ("fused", "plain"):  # the fused chain pass and the row passes A / C
+            rv, ms = dbar.dbar_plan_row_tuning(plan.handle, passes)
+            if shape:
+                assert rv == shape - 1
+            else:
+                assert rv in range(dbar.ROW_VARIANTS) and len(ms) == dbar.ROW_VARIANTS and min(ms) > 0
     for r in res[1:]:
         assert np.array_equal(res[0]["S"], r["S"]) and np.array_equal(res[0]["iters"], r["iters"])
     assert res[0]["status"] == dbar.DBAR_OK
