@@ -241,7 +241,7 @@ def run_ours(args):
     nk = w.k.size
     plan = dbar.Plan(N, w.L, M=w.M, prec="mixed" if w.mixed else "fp64", tol=w.tol, restart=args.restart,
                      inner_tol=args.inner_tol, max_batch=nk, max_outer=args.max_outer, sstep=args.sstep,
-                     autotune=args.autotune, row_shape=args.row_shape)
+                     autotune=args.autotune, row_shape=args.row_shape, row_shape_plain=args.row_shape_plain)
     colv, tune = dbar.dbar_plan_tuning(plan.handle)
     rowv, rtune = dbar.dbar_plan_row_tuning(plan.handle)
     rowv_ac, rtune_ac = dbar.dbar_plan_row_tuning(plan.handle, "plain")
@@ -1013,6 +1013,8 @@ def main():
                     help="column-pass tiles: 1 timed at plan creation (default); 0, 2 or 3 pin variant 0, 1 or 2")
     ap.add_argument("--row-shape", dest="row_shape", type=int, default=0,
                     help="row-pass shape of the FP32 passes: 0 chosen by the autotuner; 1..5 pin one")
+    ap.add_argument("--row-shape-plain", dest="row_shape_plain", type=int, default=0,
+                    help="row-pass shape of the plain FP32 row passes A and C alone (1..5; 0: as --row-shape)")
     ap.add_argument("--quick", action="store_true",
                     help="time the solve only (no FP64 comparison, end-to-end leg or CPU baseline)")
     args = ap.parse_args()

@@ -159,7 +159,12 @@ typedef struct {
                         or third shape (twice as many), and the first two with
                         a larger register budget per thread (three quarters
                         of the threads resident per SM).  The arithmetic per
-                        line is the same in every shape                       */
+                        line is the same in every shape.  Pins the fused chain
+                        row pass, and the plain row passes A and C unless
+                        row_shape_plain is set                                */
+  int row_shape_plain; /* DBAR_MIXED: 1..5 pins the shape of the plain row
+                        passes A and C alone (tuned apart from the fused chain
+                        pass, whose best shape differs); 0: row_shape's rule   */
 } dbar_params;
 
 typedef struct dbar_plan* dbar_plan_t;

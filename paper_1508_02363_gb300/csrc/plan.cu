@@ -1209,6 +1209,8 @@ static dbar_status check_params(const dbar_params* p) {
   if (!(p->gauss_w > 0.0) || !std::isfinite(p->gauss_w)) return fail(DBAR_EINVAL, "gauss_w must be finite and > 0");
   if (p->support_skip != 0 && p->support_skip != 1) return fail(DBAR_EINVAL, "support_skip must be 0 or 1");
   if (p->row_shape < 0 || p->row_shape > DBAR_ROW_VARIANTS) return fail(DBAR_EINVAL, "row_shape must be in [0, 5]");
+  if (p->row_shape_plain < 0 || p->row_shape_plain > DBAR_ROW_VARIANTS)
+    return fail(DBAR_EINVAL, "row_shape_plain must be in [0, 5]");
   if (p->regularisation != DBAR_REG_TAYLOR && p->regularisation != DBAR_REG_CONV)
     return fail(DBAR_EINVAL, "regularisation must be DBAR_REG_TAYLOR or DBAR_REG_CONV");
   if (p->regularisation == DBAR_REG_CONV) {
@@ -1756,6 +1758,7 @@ dbar_status plan_create_ex(const dbar_params* p, int per_slot_q, dbar_plan** out
   if (P->mixed && p->autotune == 2) P->colv = 1;  // fixed second variant (tests)
   if (P->mixed && p->autotune == 3) P->colv = 2;  // fixed third variant (tests)
   if (P->mixed && p->row_shape > 0) P->rowv = P->rowv_ac = p->row_shape - 1;  // fixed row-pass shape
+  if (P->mixed && p->row_shape_plain > 0) P->rowv_ac = p->row_shape_plain - 1;  // plain passes A, C
   if (s != DBAR_OK) {
     delete P;
     return s;

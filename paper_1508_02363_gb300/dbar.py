@@ -40,7 +40,8 @@ class dbar_params(ctypes.Structure):
                 ("max_outer", ctypes.c_int), ("resid_mode", ctypes.c_int), ("graphs", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("sstep", ctypes.c_int), ("iterated", ctypes.c_int),
                 ("regularisation", ctypes.c_int), ("inner_M", ctypes.c_int), ("gauss_w", ctypes.c_double),
-                ("mem_budget", ctypes.c_size_t), ("support_skip", ctypes.c_int), ("row_shape", ctypes.c_int)]
+                ("mem_budget", ctypes.c_size_t), ("support_skip", ctypes.c_int), ("row_shape", ctypes.c_int),
+                ("row_shape_plain", ctypes.c_int)]
 
 
 class dbar_request(ctypes.Structure):

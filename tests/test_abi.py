@@ -48,7 +48,8 @@ def test_parameter_validation_is_host_side(lib):
                 dict(regularisation=1), dict(regularisation=1, prec=0, N=512),
                 dict(regularisation=1, prec=0, iterated=1),
                 dict(regularisation=1, prec=0, max_batch=5000), dict(inner_M=3), dict(inner_M=-1), dict(autotune=4),
-                dict(gauss_w=0.0), dict(gauss_w=-1.0), dict(gauss_w=float("nan")), dict(support_skip=2), dict(row_shape=6), dict(row_shape=-1)):
+                dict(gauss_w=0.0), dict(gauss_w=-1.0), dict(gauss_w=float("nan")), dict(support_skip=2), dict(row_shape=6), dict(row_shape=-1),
+                dict(row_shape_plain=6), dict(row_shape_plain=-1)):
         args = dict(N=64, L=4.0)
         args.update(bad)
         p = dbar.dbar_params_init(args.pop("N"), args.pop("L"), **args)

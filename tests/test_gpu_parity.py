@@ -317,13 +317,15 @@ def test_row_pass_shapes_give_identical_results(dbar, N, nk, L):
     # times them all and records its choice
     w = wl.mixed_1024(N=N, nk=nk, L=L)
     res = []
-    for shape in (1, 2, 3, 4, 5, 0):
-        plan = dbar.Plan(w.N, w.L, M=2, prec="mixed", restart=24, tol=1e-12, max_batch=nk, row_shape=shape)
+    for shape, plain in ((1, 0), (2, 0), (3, 0), (4, 0), (5, 0), (5, 2), (0, 0)):
+        plan = dbar.Plan(w.N, w.L, M=2, prec="mixed", restart=24, tol=1e-12, max_batch=nk, row_shape=shape,
+                         row_shape_plain=plain)
         res.append(plan.solve(w.Q, w.k, want_m=False))
         for passes in ("fused", "plain"):  # the fused chain pass and the row passes A / C
             rv, ms = dbar.dbar_plan_row_tuning(plan.handle, passes)
-            if shape:
-                assert rv == shape - 1
+            pinned = plain if (passes == "plain" and plain) else shape
+            if pinned:
+                assert rv == pinned - 1
             else:
                 assert rv in range(dbar.ROW_VARIANTS) and len(ms) == dbar.ROW_VARIANTS and min(ms) > 0
     for r in res[1:]:
