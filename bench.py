@@ -91,6 +91,27 @@ def hbm_roofline(prof, variant=None, traffic_ok=False):
                       for k, v in prof.items() if v[1]}}
 
 
+def fp64_column_roofline(kind, N, M):
+    """FP64 arithmetic roofline of the FP64 column pass (its bound: FP64 runs at 1/64 of
+    FP32 here).  Elements per launch from the profiler's algorithmic bytes (2 F64 per
+    slot and step, plus the (M+2) F64 tables per launch); algorithmic flops per element:
+    two length-N FFTs at the textbook 5 log2 N each, the Delta_n sum 8(M+1) and the
+    product E_k Q conj(h) 12.  FFT additions issue on the FP64 pipe like FMAs but count
+    one flop, so 1.0 is out of reach even at a saturated pipe."""
+    import math
+    ms, launches, nbytes = kind
+    f64 = 16.0 * N * N
+    elems = max(nbytes - launches * (M + 2) * f64, 0.0) / (2.0 * f64) * N * N
+    flop = elems * (10.0 * math.log2(N) + 8.0 * (M + 1) + 12.0)
+    peak = N_SM * FP64_FLOP_PER_CLK_SM * 2070e6 / 1e12
+    achieved = flop / (ms / 1e3) / 1e12
+    return {"bound": "alu", "kernel": "inner_pass_b_cols (FP64)", "achieved": round(achieved, 4),
+            "peak": round(peak, 4), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+            "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz",
+            "flop_per_launch": flop / max(launches, 1), "avg_launch_ms": ms / max(launches, 1),
+            "flop_model": "per element and step: 2 x 5 log2 N (FFTs) + 8 (M+1) (Delta_n sum) + 12 (product)"}
+
+
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
 
@@ -398,6 +419,8 @@ def run_ours(args):
            "fp64_plain_single_k_solves_per_s": round(fp64_single_rate, 3),
            "fp64_plain_single_k_latency_ms": round(1e3 / fp64_single_rate, 3),
            "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline, "clocks": clk.summary()}
+    if not w.mixed and prof.get("inner_pass_b_cols", (0, 0, 0))[0] > 0:
+        out["roofline_fp64_alu"] = fp64_column_roofline(prof["inner_pass_b_cols"], N, w.M)
 
     if w.mixed and S64r is not None:
         out["fp64_resid"] = fp64_resid

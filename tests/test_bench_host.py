@@ -44,3 +44,18 @@ def test_traffic_scales_the_captured_ratio_per_variant(bench, monkeypatch):
 def test_traffic_is_null_once_the_kernels_changed(bench, monkeypatch):
     monkeypatch.setattr(bench, "source_digest", lambda: "0" * 16)
     assert bench.ncu_traffic("inner_pass_b_cols", 1.0e9, variant=0) is None
+
+
+def test_fp64_column_roofline_counts_elements_from_the_profiled_bytes(bench):
+    # 3 launches of the FP64 column pass over 10 slot-steps of an N = 64 grid: bytes =
+    # 10 x 2 F64 + 3 x (M+2) F64 tables; flops per element 2 x 5 log2 N + 8 (M+1) + 12
+    N, M = 64, 2
+    f64 = 16.0 * N * N
+    nbytes = 10 * 2 * f64 + 3 * (M + 2) * f64
+    r = bench.fp64_column_roofline((2.0, 3, nbytes), N, M)
+    flop = 10 * N * N * (10 * 6 + 8 * 3 + 12)
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert r["flop_per_launch"] == pytest.approx(flop / 3)
+    assert r["achieved"] == pytest.approx(flop / 2e-3 / 1e12, abs=1e-4)
+    assert r["peak"] == pytest.approx(152 * 4 * 2.07e9 / 1e12, abs=1e-4)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"], abs=1e-3)
