@@ -264,6 +264,24 @@ def test_sstep_blocks_match_oracle(dbar, sstep):
     assert np.all(r["iters"][:, 0] <= ref["iters"][:, 0] + 2 * sstep * ref["iters"][:, 1])
 
 
+@pytest.mark.parametrize("N,L,M", [(32, 3.0, 2), (64, 4.0, 2), (64, 4.0, 5), (256, 6.0, 2)])
+def test_chain_moments_at_every_row_width_match_the_oracle(dbar, N, L, M):
+    # The fused chain row pass forms the next vector's Taylor row moments from the
+    # column-pass output (warp segments of N/16 threads below N = 512, several warps
+    # above); wrong moments would leave the FP32 chain on another operator and cost inner
+    # iterations.  The s-step solve matches the oracle and needs no more inner
+    # iterations than one vector per sweep, up to the rounding to whole blocks.
+    w = wl.mixed_1024(N=N, nk=2, L=L)
+    kw = dict(M=M, prec="mixed", restart=24, tol=1e-12, max_batch=2)
+    r = dbar.Plan(w.N, w.L, sstep=4, **kw).solve(w.Q, w.k)
+    ref = dbar.Plan(w.N, w.L, sstep=1, **kw).solve(w.Q, w.k)
+    assert r["status"] == dbar.DBAR_OK and np.all(r["resid"] <= 1e-12)
+    for i in range(w.k.size):
+        o = orc.solve_cgo(w.Q, w.k[i], w.N, w.L, M=M, tol=1e-14, restart=60)
+        assert rel(r["S"][i], o["S"]) < 1e-10, i
+    assert np.all(r["iters"][:, 0] <= ref["iters"][:, 0] + 2 * 4 * ref["iters"][:, 1])
+
+
 def test_sstep_fp64_ragged_batches_match_single_solves_and_oracle(dbar):
     # FP64 s-step cycles; 7 k values through 3 slots (batches 3, 3, 1) and alone
     w = wl.batched_fp64(N=64, nk_side=3)
