@@ -63,7 +63,7 @@ template <int S>
 cudaError_t launch_bscalar(const BlockArgs& a, const CycleState& c, double* Hraw, double* bcoef, int* upd, int J,
                            int nslots, cudaStream_t s) {
   if (nslots <= 0) return cudaSuccess;
-  const size_t sm = (size_t)(block_items(J, S) + (J + S) * S) * sizeof(double);
+  const size_t sm = (size_t)(block_items(J, S) + (J + S) * S + S * S + S + 1) * sizeof(double);
   k_bscalar<S><<<nslots, KR_THREADS, sm, s>>>(a, c, Hraw, bcoef, upd, J);
   return cudaGetLastError();
 }

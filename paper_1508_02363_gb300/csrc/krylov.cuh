@@ -411,7 +411,9 @@ __global__ void __launch_bounds__(KR_THREADS) k_bdots(const BlockArgs a, const c
 }
 
 // Per-slot FP64 step of a block (one CTA per slot; thread 0 does the small
-// dense algebra).  Writes the block's Hessenberg columns J-1.. (unrotated into
+// dense algebra, warp 0 the row-parallel parts: on GB300 a warp's FP64
+// instruction holds the narrow FP64 pipe for many cycles whatever its active
+// lanes, so the element-wise loops run one element per lane).  Writes the block's Hessenberg columns J-1.. (unrotated into
 // Hraw, rotated into c.H with the Givens steps), the sweep coefficients, the
 // scales of the new vectors, and upd[slot] = 1 for every slot that ran the
 // block (its new vectors need the update sweep even when it stops here).
@@ -419,7 +421,7 @@ template <int S>
 static __global__ void __launch_bounds__(KR_THREADS) k_bscalar(BlockArgs a, CycleState c, double* __restrict__ Hraw,
                                                                double* __restrict__ bcoef, int* __restrict__ upd,
                                                                int J) {
-  extern __shared__ double sm[];  // val[nit], X[(J + S) * S]
+  extern __shared__ double sm[];  // val[nit], X[(J + S) * S], R[S][S], Sg[S + 1]
   const int slot = blockIdx.x;
   if (!c.run[slot]) {
     if (threadIdx.x == 0) upd[slot] = 0;
@@ -428,6 +430,8 @@ static __global__ void __launch_bounds__(KR_THREADS) k_bscalar(BlockArgs a, Cycl
   const int nit = block_items(J, S);
   double* val = sm;
   double* X = sm + nit;
+  double(*R)[S] = reinterpret_cast<double(*)[S]>(X + (J + S) * S);
+  double* Sg = X + (J + S) * S + S * S;
   for (int q = threadIdx.x; q < nit; q += blockDim.x) {
     const double* p = a.part + ((size_t)slot * a.nitem + q) * a.nchunk;
     double s = 0.0;
@@ -435,28 +439,35 @@ static __global__ void __launch_bounds__(KR_THREADS) k_bscalar(BlockArgs a, Cycl
     val[q] = s;
   }
   __syncthreads();
-  if (threadIdx.x != 0) return;
   const int m = c.m, rows = J + S;
   double* sg = c.sigma + (size_t)slot * (m + 1);
-  // chain norms Sg[i] = ||p_i|| (Sg[0] = 1: v_{J-1} has unit norm)
-  double Sg[S + 1], G[S][S], R[S][S], Ri[S][S];
-  Sg[0] = 1.0;
+  // chain norms Sg[i] = ||p_i|| (Sg[0] = 1: v_{J-1} has unit norm); the diagonal items
+  // of p^T p follow the J S items of V^T p
+  if (threadIdx.x <= S) {
+    const int i = threadIdx.x - 1;
+    Sg[threadIdx.x] = threadIdx.x == 0 ? 1.0 : sqrt(fmax(val[J * S + i * S - i * (i - 1) / 2], 0.0));
+  }
+  __syncthreads();
+  double G[S][S];
   {
     int it = J * S;
     for (int i = 0; i < S; ++i)
-      for (int l = i; l < S; ++l, ++it) {
-        G[i][l] = val[it];
-        if (l == i) Sg[i + 1] = sqrt(fmax(val[it], 0.0));
-      }
+      for (int l = i; l < S; ++l, ++it) G[i][l] = val[it];
   }
-  // C^ = coordinates of p^_{i+1} on v_r (in place in val)
-  for (int r = 0; r < J; ++r)
-    for (int i = 0; i < S; ++i) {
-      const double d = Sg[i + 1];
-      val[r * S + i] = d > 0.0 ? val[r * S + i] * sg[r] / d : 0.0;
-    }
-  // G = p^T p (normalised) - C^T C, Cholesky G = R^T R
+  __syncthreads();  // the items of p^T p are read before C^ overwrites the V^T p items
+  // C^ = coordinates of p^_{i+1} on v_r (in place in val), one item per thread
+  for (int q = threadIdx.x; q < J * S; q += blockDim.x) {
+    const int r = q / S, i = q - r * S;
+    const double d = Sg[i + 1];
+    val[q] = d > 0.0 ? val[q] * sg[r] / d : 0.0;
+  }
+  __syncthreads();
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  double Ri[S][S];
+  // G = p^T p (normalised) - C^T C, Cholesky G = R^T R (lane 0; R shared with the warp)
   int nok = S;
+  if (lane == 0) {
   for (int i = 0; i < S; ++i)
     for (int l = 0; l < S; ++l) R[i][l] = 0.0;
   for (int i = 0; i < S && nok == S; ++i) {
@@ -476,6 +487,9 @@ static __global__ void __launch_bounds__(KR_THREADS) k_bscalar(BlockArgs a, Cycl
       }
     }
   }
+  }
+  nok = __shfl_sync(0xffffffffu, nok, 0);
+  __syncwarp();
   const int ncols = nok > 0 ? nok : 1;  // nok = 0: p_1 lies in span(V), a happy breakdown column
   // R^{-1} on the accepted columns (zero elsewhere)
   for (int i = 0; i < S; ++i)
@@ -495,10 +509,10 @@ static __global__ void __launch_bounds__(KR_THREADS) k_bscalar(BlockArgs a, Cycl
     const int q = r - J;
     return q <= k - 1 ? R[q][k - 1] : 0.0;
   };
-  // H_new = (T B - [H_prev Z; 0]) U^{-1}, column by column
+  // H_new = (T B - [H_prev Z; 0]) U^{-1}, column by column, one row per lane
   for (int i = 0; i < ncols; ++i) {
     const double bsub = Sg[i + 1] / Sg[i];
-    for (int r = 0; r < rows; ++r) {
+    for (int r = lane; r < rows; r += 32) {
       double v = T(r, i) + T(r, i + 1) * bsub;
       if (r < J && i > 0)
         for (int q = (r > 0 ? r - 1 : 0); q < J - 1; ++q)
@@ -507,7 +521,22 @@ static __global__ void __launch_bounds__(KR_THREADS) k_bscalar(BlockArgs a, Cycl
       const double uii = i == 0 ? 1.0 : R[i - 1][i - 1];
       X[r * S + i] = r <= J + i ? v / uii : 0.0;
     }
+    __syncwarp();
   }
+  // sweep coefficients: Q = P^ R^{-1} - V C^ R^{-1}, on the raw stored vectors (one item per lane)
+  double* bc = bcoef + (size_t)slot * (S * S + (m + 1) * S);
+  for (int q = lane; q < S * S; q += 32) {
+    const int k = q / S, i = q - k * S;
+    bc[q] = Sg[k + 1] > 0.0 ? Ri[k][i] / Sg[k + 1] : 0.0;
+  }
+  for (int q = lane; q < J * S; q += 32) {
+    const int r = q / S, i = q - r * S;
+    double s = 0.0;
+    for (int k = 0; k <= i; ++k) s += val[r * S + k] * Ri[k][i];
+    bc[S * S + q] = -s * sg[r];
+  }
+  __syncwarp();
+  if (lane != 0) return;
   // columns J-1+i: unrotated copy, then the Givens steps
   bool stop = false;
   for (int i = 0; i < ncols && !stop; ++i) {
@@ -518,16 +547,6 @@ static __global__ void __launch_bounds__(KR_THREADS) k_bscalar(BlockArgs a, Cycl
     stop = givens_column(c, slot, j, Hc);
   }
   if (ncols < S || J - 1 + 2 * S > m) stop = true;
-  // sweep coefficients: Q = P^ R^{-1} - V C^ R^{-1}, on the raw stored vectors
-  double* bc = bcoef + (size_t)slot * (S * S + (m + 1) * S);
-  for (int k = 0; k < S; ++k)
-    for (int i = 0; i < S; ++i) bc[k * S + i] = Sg[k + 1] > 0.0 ? Ri[k][i] / Sg[k + 1] : 0.0;
-  for (int r = 0; r < J; ++r)
-    for (int i = 0; i < S; ++i) {
-      double s = 0.0;
-      for (int k = 0; k <= i; ++k) s += val[r * S + k] * Ri[k][i];
-      bc[S * S + r * S + i] = -s * sg[r];
-    }
   for (int i = 0; i < S; ++i) sg[J + i] = 1.0;
   upd[slot] = 1;
   if (stop) {
