@@ -1720,7 +1720,6 @@ dbar_status plan_create_ex(const dbar_params* p, int per_slot_q, dbar_plan** out
     }
   }
   P->B = B;
-  const size_t n = (size_t)P->n;
   const int m = P->m;
   CycleState& c = P->cs;
   {
