@@ -935,6 +935,9 @@ def serving_leg(args, dbar, torch, clock_gpu=0):
         pool.join()
     lat = np.array(lat)
     nmix = {str(N): int(sum(1 for r in reqs if r[0] == N)) for N in wl.SERVING_SIZES}
+    lat_by_n = {}
+    for i, t in enumerate(lat):  # latencies in submission order
+        lat_by_n.setdefault(reqs[i][0], []).append(t)
     return {"rate_req_s": args.rate, "duration_s": args.duration, "requests": len(reqs),
             "solves_per_s": round(len(lat) / wall, 2), "wall_s": round(wall, 2),
             "warmup_s": args.serve_warmup,
@@ -945,6 +948,8 @@ def serving_leg(args, dbar, torch, clock_gpu=0):
             "err_vs_oracle_sample": f"{len(err_orc)} requests with N <= 512 of the 2% sample "
                                     f"(N of the sample: {sorted(set(reqs[i][0] for i in orc_idx))})",
             "late_submits": late, "n_mix": nmix,
+            "p50_p99_ms_by_N": {str(n): [round(float(np.percentile(lat_n, 50)), 2), round(float(np.percentile(lat_n, 99)), 2)]
+                                for n, lat_n in sorted(lat_by_n.items())},
             "config": {"L": L, "kmax": KMAX, "xi_q": XI_Q, "per_request_seed": f"{args.seed} + request index",
                        "terms": "1-6 per request", "restart": args.restart, "inner_tol": args.inner_tol,
                        "serve_batch": args.serve_batch, "budget_bytes": int(free * 0.7)},
