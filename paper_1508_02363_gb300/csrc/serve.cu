@@ -111,6 +111,12 @@ struct Lane {
   size_t bytes = 0;
   std::deque<Request*> waiting;
   std::vector<Request*> slot;
+  // completion of the last cycle launched on `stream`: the worker steps a lane only once
+  // its previous cycle has finished, so a long cycle of one grid class never holds up
+  // the cycle boundaries of the others
+  cudaEvent_t done = nullptr;
+  bool inflight = false;
+  bool ready() const { return !inflight || cudaEventQuery(done) != cudaErrorNotReady; }
   bool busy() const {
     if (!waiting.empty()) return true;
     for (Request* r : slot)
@@ -282,6 +288,10 @@ bool step_lane(dbar_server* S, Lane* ln) {
     if (admit[s]) st = plan_load_slot(ln->plan, s, admit[s]->Q, admit[s]->k1, admit[s]->k2, ln->stream);
   if (st == DBAR_OK && nnew) st = plan_begin(ln->plan, B, mask.data(), ln->stream);
   if (st == DBAR_OK && occupied) st = plan_step(ln->plan, B, ln->stream);
+  if (st == DBAR_OK && occupied) {
+    if (!ln->done && cudaEventCreateWithFlags(&ln->done, cudaEventDisableTiming) != cudaSuccess) ln->done = nullptr;
+    ln->inflight = ln->done && cudaEventRecord(ln->done, ln->stream) == cudaSuccess;
+  }
   if (st == DBAR_OK && inject) st = dbar_internal_fail(DBAR_ECUDA, "injected lane failure");
   if (st != DBAR_OK) {
     cudaStreamSynchronize(ln->stream);
@@ -308,8 +318,9 @@ void worker_main(dbar_server* S) {
         if (l->busy()) todo.push_back(l);
     }
     bool progressed = false;
-    for (Lane* l : todo) progressed |= step_lane(S, l);
-    if (!progressed) std::this_thread::sleep_for(std::chrono::milliseconds(1));
+    for (Lane* l : todo)
+      if (l->ready()) progressed |= step_lane(S, l);  // lanes still running their cycle are skipped
+    if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(100));
   }
 }
 
@@ -510,6 +521,7 @@ extern "C" dbar_status dbar_serve_destroy(dbar_server_t S) {
   for (Lane* l : S->lanes) {
     if (l->stream) cudaStreamSynchronize(l->stream);
     if (l->plan) dbar_plan_destroy(l->plan);
+    if (l->done) cudaEventDestroy(l->done);
     if (l->stream) cudaStreamDestroy(l->stream);
     delete l;
   }
