@@ -851,22 +851,38 @@ def serving_leg(args, dbar, torch, clock_gpu=0):
             return wl.gaussian_mixture(N, L, *mix)
 
         def collect():
-            j = 0
-            while True:
+            # results in completion order (a polling client): each one's page-locked
+            # buffers go back to the server's pool as soon as it is done, not after the
+            # slower requests submitted before it
+            j, pending, got, last = 0, {}, {}, False
+            while not last or pending:
                 with ready:
-                    while j >= len(tickets):
+                    while j >= len(tickets) and not pending:
                         ready.wait()
-                    item = tickets[j]
-                if item is None:
-                    return
-                i, t = item
-                r = srv.wait(t, timeout_s=600, release=True, copy=i in keep)
-                lat.append(r["latency_ms"])
-                status.append(r["status"])
-                resid.append(r["resid"])
-                if i in keep:
-                    kept_S[i] = r["S"]
-                j += 1
+                    while j < len(tickets):
+                        if tickets[j] is None:
+                            last = True
+                        else:
+                            pending[tickets[j][0]] = tickets[j][1]
+                        j += 1
+                done = []
+                for i, t in pending.items():
+                    r = srv.poll(t, copy=i in keep)
+                    if r is None:
+                        continue
+                    srv.release(t)
+                    got[i] = (r["latency_ms"], r["status"], r["resid"])
+                    if i in keep:
+                        kept_S[i] = r["S"]
+                    done.append(i)
+                for i in done:
+                    del pending[i]
+                if not done:
+                    time.sleep(0.001)
+            for i in sorted(got):  # submission order
+                lat.append(got[i][0])
+                status.append(got[i][1])
+                resid.append(got[i][2])
 
         collector = threading.Thread(target=collect, daemon=True)
         collector.start()

@@ -430,10 +430,11 @@ def _result_dict(res: dbar_result, N: int, copy: bool = True):
             "S": arr(res.S), "m": arr(res.m)}
 
 
-def dbar_serve_poll(srv, ticket: int, N: int):
+def dbar_serve_poll(srv, ticket: int, N: int, copy: bool = True):
+    """None while the request runs; else its result (copy=False leaves S and m out)."""
     res = dbar_result()
     st = _check(_lib.dbar_serve_poll(srv, ticket, ctypes.byref(res)), (DBAR_OK, DBAR_EBUSY))
-    return None if st == DBAR_EBUSY else _result_dict(res, N)
+    return None if st == DBAR_EBUSY else _result_dict(res, N, copy)
 
 
 def dbar_serve_wait(srv, ticket: int, N: int, timeout_s: float = -1.0, copy: bool = True):
@@ -477,8 +478,8 @@ class Server:
         self._N[t] = N
         return t
 
-    def poll(self, ticket: int):
-        return dbar_serve_poll(self.handle, ticket, self._N[ticket])
+    def poll(self, ticket: int, copy: bool = True):
+        return dbar_serve_poll(self.handle, ticket, self._N[ticket], copy)
 
     def wait(self, ticket: int, timeout_s: float = -1.0, release: bool = True, copy: bool = True):
         r = dbar_serve_wait(self.handle, ticket, self._N[ticket], timeout_s, copy)
