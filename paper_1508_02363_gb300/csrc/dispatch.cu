@@ -95,7 +95,7 @@ template cudaError_t launch_pass_c<double, float, PC_RES>(const PassArgs<double>
 template cudaError_t launch_pass_a<dd>(const PassArgs<dd>&, int, cudaStream_t);
 template cudaError_t launch_pass_b<dd, PB_MATVEC>(const PassArgs<dd>&, int, cudaStream_t);
 template cudaError_t launch_pass_b<dd, PB_RHS>(const PassArgs<dd>&, int, cudaStream_t);
-template cudaError_t launch_pass_b<dd, PB_W>(const PassArgs<dd>&, int, cudaStream_t);
+template cudaError_t launch_pass_b<dd, PB_WF>(const PassArgs<dd>&, int, cudaStream_t);
 template cudaError_t launch_pass_b<dd, PB_FWD>(const PassArgs<dd>&, int, cudaStream_t);
 template cudaError_t launch_pass_c<dd, float, PC_RHS>(const PassArgs<dd>&, int, cudaStream_t);
 template cudaError_t launch_pass_c<dd, float, PC_RES>(const PassArgs<dd>&, int, cudaStream_t);

@@ -116,7 +116,7 @@ typedef DBAR_T TT;
 template cudaError_t launch_pass_a_n<dd, DBAR_LOGN>(const PassArgs<dd>&, int, cudaStream_t);
 template cudaError_t launch_pass_b_n<dd, DBAR_LOGN, PB_MATVEC, 0>(const PassArgs<dd>&, int, cudaStream_t);
 template cudaError_t launch_pass_b_n<dd, DBAR_LOGN, PB_RHS, 0>(const PassArgs<dd>&, int, cudaStream_t);
-template cudaError_t launch_pass_b_n<dd, DBAR_LOGN, PB_W, 0>(const PassArgs<dd>&, int, cudaStream_t);
+template cudaError_t launch_pass_b_n<dd, DBAR_LOGN, PB_WF, 0>(const PassArgs<dd>&, int, cudaStream_t);
 template cudaError_t launch_pass_b_n<dd, DBAR_LOGN, PB_FWD, 0>(const PassArgs<dd>&, int, cudaStream_t);
 template cudaError_t launch_pass_c_n<dd, float, DBAR_LOGN, PC_RHS>(const PassArgs<dd>&, int, cudaStream_t);
 template cudaError_t launch_pass_c_n<dd, float, DBAR_LOGN, PC_RES>(const PassArgs<dd>&, int, cudaStream_t);

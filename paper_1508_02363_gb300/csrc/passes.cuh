@@ -305,7 +305,12 @@ __global__ void __launch_bounds__(RowG<T, LOGN, RV>::THREADS, RowG<T, LOGN, RV>:
 
 // ---------------------------------------------------------------------------
 // Pass B: columns.  MODE PB_MATVEC operator, PB_RHS right-hand side, PB_HOUT h
-// only (m output), PB_FWD / PB_INV raw column DFTs.  A warp covers CW
+// only (m output), PB_FWD / PB_INV raw column DFTs.  PB_WF: the operator with
+// one copy of the transform's code for both transforms (the inverse as
+// conj(DFT(conj(x))), the two in a loop), for the double-float pass whose two
+// inlined transforms would not fit the instruction cache (measured 12 % faster
+// than its first half, PB_W, followed by a separate PB_FWD launch, which moved
+// the support columns through HBM once more).  A warp covers CW
 // neighbouring columns x TW consecutive t, so the 16 loads and stores of each
 // thread (rows t + q TPL of column j1) are coalesced row segments.
 // ---------------------------------------------------------------------------
@@ -327,18 +332,31 @@ __global__ void __launch_bounds__(ColG<T, LOGN, CV>::THREADS, ColG<T, LOGN, CV>:
   constexpr size_t off = ((size_t)G::COLS * P * sizeof(cx<T>) + 15) & ~(size_t)15;
   cx<T>* coef = reinterpret_cast<cx<T>*>(smem + off);  // [M+1] c_n, then the fill d'
 
+  constexpr bool WF = MODE == PB_WF;
   cx<T> v[16];
   if (MODE != PB_RHS) {
     const cx<T>* src = a.in + (size_t)slot * a.in_ss + (size_t)t * N + j1;
 #pragma unroll
     for (int q = 0; q < 16; ++q) v[q] = ldg(src + (size_t)q * TPL * N);
     // Taylor coefficients of this slot (k_coef), issued after the field loads
-    if ((MODE == PB_MATVEC || MODE == PB_HOUT || MODE == PB_W) && threadIdx.x < M + 2)
+    if ((MODE == PB_MATVEC || MODE == PB_HOUT || MODE == PB_W || WF) && threadIdx.x < M + 2)
       coef[threadIdx.x] = ccast<T>(a.coef[(size_t)slot * (M + 2) + threadIdx.x]);
     if (MODE == PB_FWD) fft_line<T, LOGN, false, std::is_same<T, float>::value>(v, sl, t, a.tw);
-    else fft_line<T, LOGN, true, std::is_same<T, float>::value>(v, sl, t, a.tw);
+    else if (!WF) fft_line<T, LOGN, true, std::is_same<T, float>::value>(v, sl, t, a.tw);
   }
-  if (MODE == PB_MATVEC || MODE == PB_HOUT || MODE == PB_W) {
+#pragma unroll 1
+  for (int ph = 0; ph < (WF ? 2 : 1); ++ph) {
+  if constexpr (WF) {
+    if (ph == 0) {
+#pragma unroll
+      for (int q = 0; q < 16; ++q) v[q].im = -v[q].im;
+    }
+    fft_line<T, LOGN, false, false>(v, sl, t, a.tw);
+    if (ph == 1) break;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q].im = -v[q].im;
+  }
+  if (MODE == PB_MATVEC || MODE == PB_HOUT || MODE == PB_W || WF) {
     __syncthreads();  // coefficients visible
     // h = u + sum_n c_n Delta_n + d'  (n outer, 16 independent loads per n)
     const cx<T> fill = coef[M + 1];
@@ -346,7 +364,7 @@ __global__ void __launch_bounds__(ColG<T, LOGN, CV>::THREADS, ColG<T, LOGN, CV>:
     for (int q = 0; q < 16; ++q) v[q] = v[q] + fill;
     // rows outside [sy0, sy1) (operator only, where the plan sets a band): Q = 0 there
     // and w = 0 below, so their table loads are skipped; a branch uniform over the grid
-    const bool band = MODE != PB_HOUT && (a.sy0 > 0 || a.sy1 < N);
+    const bool band = MODE != PB_HOUT && (a.sy0 > 0 || a.sy1 < N);  // (WF: as MATVEC)
     for (int n = 0; n <= M; ++n) {
       const cx<T> cn = coef[n];
       const cx<T>* D = a.Delta + ((size_t)n * N + t) * N + j1;
@@ -362,7 +380,7 @@ __global__ void __launch_bounds__(ColG<T, LOGN, CV>::THREADS, ColG<T, LOGN, CV>:
       }
     }
   }
-  if (MODE == PB_MATVEC || MODE == PB_RHS || MODE == PB_W) {
+  if (MODE == PB_MATVEC || MODE == PB_RHS || MODE == PB_W || WF) {
     // w = (2 pi L^2/N^2) E_k Q conj(h)   (right-hand side: E_k Q)
     const cx<T> exv = cscale(ldg(a.ex + (size_t)slot * N + j1), (T)a.sw);
     const cx<T>* EY = a.ey + (size_t)slot * N + t;
@@ -385,7 +403,8 @@ __global__ void __launch_bounds__(ColG<T, LOGN, CV>::THREADS, ColG<T, LOGN, CV>:
         v[q] = (MODE == PB_RHS) ? eq : cmulc(eq, v[q]);
       }
     }
-    if (MODE != PB_W) fft_line<T, LOGN, false, std::is_same<T, float>::value>(v, sl, t, a.tw);
+    if (MODE != PB_W && !WF) fft_line<T, LOGN, false, std::is_same<T, float>::value>(v, sl, t, a.tw);
+  }
   }
   cx<T>* dst = reinterpret_cast<cx<T>*>(a.out) + (size_t)slot * a.out_ss + (size_t)t * N + j1;
 #pragma unroll

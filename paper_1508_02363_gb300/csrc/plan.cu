@@ -728,12 +728,9 @@ static dbar_status true_residual_t(dbar_plan* P, int nb, cudaStream_t st) {
     a.in = reinterpret_cast<const cx<TC>*>(P->T1);
     a.out = P->T2;
     if constexpr (std::is_same<TC, dd>::value) {
-      // two launches (column IDFT + pointwise, then column DFT): the fused
-      // double-float column pass is too large for the instruction cache
-      // (the column DFT runs in place: each block owns its columns)
-      CK(timed(P, st, K_RES_B, [&] { return launch_pass_b<TC, PB_W>(a, nb, st); }));
-      a.in = reinterpret_cast<const cx<TC>*>(P->T2);
-      CK(timed(P, st, K_RES_B, [&] { return launch_pass_b<TC, PB_FWD>(a, nb, st); }));
+      // one launch whose two transforms share one copy of the code (PB_WF): two
+      // inlined double-float transforms would not fit the instruction cache
+      CK(timed(P, st, K_RES_B, [&] { return launch_pass_b<TC, PB_WF>(a, nb, st); }));
     } else {
       CK(timed(P, st, K_RES_B, [&] { return launch_pass_b<TC, PB_MATVEC>(a, nb, st); }));
     }

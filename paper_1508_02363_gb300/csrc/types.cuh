@@ -132,7 +132,7 @@ struct CycleState {
 
 // pass B modes: operator, right-hand side, h only, raw column DFTs, and the
 // operator's first half (column IDFT, h, w = E_k Q conj(h); no column DFT)
-enum { PB_MATVEC = 0, PB_RHS = 1, PB_HOUT = 2, PB_FWD = 3, PB_INV = 4, PB_W = 5 };
+enum { PB_MATVEC = 0, PB_RHS = 1, PB_HOUT = 2, PB_FWD = 3, PB_INV = 4, PB_W = 5, PB_WF = 6 };
 // pass C modes: K S, right-hand side, FP64 residual, raw row DFTs
 enum { PC_KS = 0, PC_RHS = 1, PC_RES = 2, PC_FWD = 3, PC_INV = 4 };
 
