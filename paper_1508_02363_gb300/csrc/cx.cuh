@@ -332,6 +332,37 @@ __device__ __forceinline__ void fft_stage(cx<T> (&v)[16], cx<T>* line, int t, co
 // of the block calls this together (it synchronises the block).  TWM: stage
 // twiddles w^r formed as products of loaded powers of two (fewer L1 loads;
 // measured faster in every FP32 pass; FP32 only).
+// The first two radix-16 stages of a transform with N >= 512 as one loop body (stage
+// span NS = 1, then 16, at run time): the same operations as fft_stage, one copy of
+// the code.  Used by the double-float column pass (fft_line_compact), whose two
+// transforms of fully inlined stages would miss in the instruction cache.
+template <typename T, int N, bool INV>
+__device__ __forceinline__ void fft_stages16_looped(cx<T> (&v)[16], cx<T>* line, int t, const cx<T>* __restrict__ tw) {
+  constexpr int R = 16, NB = N / R;
+#pragma unroll 1
+  for (int s = 0; s < 2; ++s) {
+    const int NS = s == 0 ? 1 : 16;
+    const int k = t & (NS - 1);
+    if (s > 0) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = line[padi(t + r * NB)];
+      const int STEP = N / (NS * R);
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        cx<T> w = ldg(tw + r * k * STEP);
+        if (INV) w.im = -w.im;
+        v[r] = cmul(v[r], w);
+      }
+    }
+    dft_reg<T, R, INV>(v);
+    __syncthreads();  // every thread has read the inputs of this stage
+    const int base = (t - k) * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) line[padi(base + r * NS)] = v[r];
+    __syncthreads();
+  }
+}
+
 template <typename T, int LOGN, bool INV, bool TWM = false>
 __device__ __forceinline__ void fft_line(cx<T> (&v)[16], cx<T>* line, int t, const cx<T>* __restrict__ tw) {
   constexpr int N = 1 << LOGN;
@@ -345,6 +376,20 @@ __device__ __forceinline__ void fft_line(cx<T> (&v)[16], cx<T>* line, int t, con
     fft_stage<T, N, 16, 1, INV, true, false, TWM>(v, line, t, tw);
     fft_stage<T, N, 16, 16, INV, false, false, TWM>(v, line, t, tw);
     fft_stage<T, N, (1 << (L1 - 4)), 256, INV, false, true, TWM>(v, line, t, tw);
+  }
+}
+
+// fft_line with the first two radix-16 stages looped (fft_stages16_looped) at N >= 512:
+// the same results, less code.
+template <typename T, int LOGN, bool INV>
+__device__ __forceinline__ void fft_line_compact(cx<T> (&v)[16], cx<T>* line, int t, const cx<T>* __restrict__ tw) {
+  constexpr int N = 1 << LOGN;
+  constexpr int L1 = LOGN - 4;
+  if constexpr (L1 > 4) {
+    fft_stages16_looped<T, N, INV>(v, line, t, tw);
+    fft_stage<T, N, (1 << (L1 - 4)), 256, INV, false, true, false>(v, line, t, tw);
+  } else {
+    fft_line<T, LOGN, INV, false>(v, line, t, tw);
   }
 }
 

@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(ColG<T, LOGN, CV>::THREADS, ColG<T, LOGN, CV>:
 #pragma unroll
       for (int q = 0; q < 16; ++q) v[q].im = -v[q].im;
     }
-    fft_line<T, LOGN, false, false>(v, sl, t, a.tw);
+    fft_line_compact<T, LOGN, false>(v, sl, t, a.tw);
     if (ph == 1) break;
 #pragma unroll
     for (int q = 0; q < 16; ++q) v[q].im = -v[q].im;
