@@ -118,7 +118,7 @@ def test_rhs_matches_oracle(dbar, torch_cuda, prec):
 @pytest.mark.parametrize("fp32", [False, True])
 @pytest.mark.parametrize("N", [64, 128, 1024, 2048])
 def test_operator_application_matches_oracle(dbar, torch_cuda, fp32, N):
-    # (the FP32 rows of N = 1024 run the radix-32 x 32 kernels, the other sizes radix 16)
+    # 1024 and 2048: the grids of the benchmark and of the serving workload's largest class
     torch = torch_cuda
     L = 6.0
     rng = np.random.default_rng(N + fp32)
@@ -230,6 +230,18 @@ def test_iteration_cap_reports_no_convergence(dbar):
     r = plan.solve(w.Q, w.k)
     assert r["status"] == dbar.DBAR_ENOCONV
     assert r["resid"][0] > 1e-13 and r["iters"][0, 0] == 4
+
+
+def test_mixed_solve_at_the_largest_grid_matches_the_fp64_solve(dbar):
+    # N = 2048: the double-float residual's one-launch column pass with a radix-8 last
+    # stage, the FP32 passes at their largest size.  The CPU oracle needs minutes per solve
+    # here; the FP64 GPU path it pins at the smaller grids stands in (mixed bar 1e-10).
+    w = wl.mixed_1024(N=2048, nk=2, L=12.0)
+    r = dbar.Plan(w.N, w.L, M=2, prec="mixed", restart=32, tol=1e-12, max_batch=2).solve(w.Q, w.k, want_m=False)
+    ref = dbar.Plan(w.N, w.L, M=2, prec="fp64", restart=32, tol=1e-13, max_batch=2).solve(w.Q, w.k, want_m=False)
+    assert r["status"] == dbar.DBAR_OK and np.all(r["resid"] <= 1e-12)
+    for i in range(w.k.size):
+        assert rel(r["S"][i], ref["S"][i]) < 1e-10, i
 
 
 @pytest.mark.slow
