@@ -837,12 +837,15 @@ def serving_leg(args, dbar, torch, clock_gpu=0):
     LOOK = 64
     kept_Q, kept_S = {}, {}
 
+    queue, cycles = [], []  # per request of the last stream, in submission order
+
     def stream(arr, rq, keep):
         """Submits rq[i] at arr[i] (generated just ahead by the pool), collects and releases each
         result as it completes; keeps Q and S of the requests in `keep`.  Returns the latencies,
         statuses and residuals in submission order, the wall time from the first submission to
         the last completion, and the number of submissions more than 5 ms late."""
         futs, lat, status, resid, tickets = {}, [], [], [], []
+        del queue[:], cycles[:]
         ready = threading.Condition()
         late = [0]
 
@@ -871,7 +874,7 @@ def serving_leg(args, dbar, torch, clock_gpu=0):
                     if r is None:
                         continue
                     srv.release(t)
-                    got[i] = (r["latency_ms"], r["status"], r["resid"])
+                    got[i] = (r["latency_ms"], r["status"], r["resid"], r["queue_ms"], r["cycles"])
                     if i in keep:
                         kept_S[i] = r["S"]
                     done.append(i)
@@ -883,6 +886,8 @@ def serving_leg(args, dbar, torch, clock_gpu=0):
                 lat.append(got[i][0])
                 status.append(got[i][1])
                 resid.append(got[i][2])
+                queue.append(got[i][3])
+                cycles.append(got[i][4])
 
         collector = threading.Thread(target=collect, daemon=True)
         collector.start()
@@ -951,9 +956,11 @@ def serving_leg(args, dbar, torch, clock_gpu=0):
         pool.join()
     lat = np.array(lat)
     nmix = {str(N): int(sum(1 for r in reqs if r[0] == N)) for N in wl.SERVING_SIZES}
-    lat_by_n = {}
+    lat_by_n, q_by_n, cyc_by_n = {}, {}, {}
     for i, t in enumerate(lat):  # latencies in submission order
         lat_by_n.setdefault(reqs[i][0], []).append(t)
+        q_by_n.setdefault(reqs[i][0], []).append(queue[i])
+        cyc_by_n.setdefault(reqs[i][0], []).append(cycles[i])
     return {"rate_req_s": args.rate, "duration_s": args.duration, "requests": len(reqs),
             "solves_per_s": round(len(lat) / wall, 2), "wall_s": round(wall, 2),
             "warmup_s": args.serve_warmup,
@@ -966,6 +973,9 @@ def serving_leg(args, dbar, torch, clock_gpu=0):
             "late_submits": late, "n_mix": nmix,
             "p50_p99_ms_by_N": {str(n): [round(float(np.percentile(lat_n, 50)), 2), round(float(np.percentile(lat_n, 99)), 2)]
                                 for n, lat_n in sorted(lat_by_n.items())},
+            "queue_p50_p99_ms_by_N": {str(n): [round(float(np.percentile(q, 50)), 2), round(float(np.percentile(q, 99)), 2)]
+                                      for n, q in sorted(q_by_n.items())},
+            "cycles_max_by_N": {str(n): int(max(c)) for n, c in sorted(cyc_by_n.items())},
             "config": {"L": L, "kmax": KMAX, "xi_q": XI_Q, "per_request_seed": f"{args.seed} + request index",
                        "terms": "1-6 per request", "restart": args.restart, "inner_tol": args.inner_tol,
                        "serve_batch": args.serve_batch, "budget_bytes": int(free * 0.7)},
