@@ -244,6 +244,7 @@ struct dbar_plan {
   int* upd = nullptr;       // [B] slots whose block needs the update sweep
   // host staging
   int* h_active = nullptr;
+  int* h_run = nullptr;  // [B] page-locked copy of the run flags after a cycle part (server stepping)
   int* h_nsteps = nullptr;
   cx<double>* h_ek = nullptr;  // pinned [B][2N]
   double* h_k = nullptr;       // pinned [B][2] k values of the batch being loaded
@@ -282,6 +283,7 @@ struct dbar_plan {
     if (hmask) cudaFreeHost(hmask);
     if (h_ek) cudaFreeHost(h_ek);
     if (h_k) cudaFreeHost(h_k);
+    if (h_run) cudaFreeHost(h_run);
     cudaSetDevice(cur);
   }
   size_t inner_elem() const { return mixed ? sizeof(cx<float>) : sizeof(cx<double>); }
@@ -1089,8 +1091,9 @@ static dbar_status capture_part(dbar_plan* P, GraphPart* g, F&& body) {
   return DBAR_OK;
 }
 
+// The captured parts of a cycle for nb slots (captured on first use).
 template <typename TI>
-static dbar_status graph_cycle(dbar_plan* P, int nb, cudaStream_t st, int* launched_steps, bool early_stop = true) {
+static dbar_status cycle_graph(dbar_plan* P, int nb, CycleGraph** out) {
   CycleGraph* g = nullptr;
   for (CycleGraph& c : P->graphs)
     if (!c.parts.empty() && c.nb == nb && c.prof == P->prof.on) g = &c;
@@ -1113,6 +1116,16 @@ static dbar_status graph_cycle(dbar_plan* P, int nb, cudaStream_t st, int* launc
     g->nb = nb;
     g->prof = P->prof.on;
   }
+  *out = g;
+  return DBAR_OK;
+}
+
+template <typename TI>
+static dbar_status graph_cycle(dbar_plan* P, int nb, cudaStream_t st, int* launched_steps, bool early_stop = true) {
+  CycleGraph* g = nullptr;
+  const dbar_status gs = cycle_graph<TI>(P, nb, &g);
+  if (gs != DBAR_OK) return gs;
+  const int nchunks = (P->m + kGraphChunk - 1) / kGraphChunk;
   int launched = 0;
   for (int c = 0; c < nchunks; ++c) {
     CK(cudaGraphLaunch(g->parts[c].exec, st));
@@ -1739,6 +1752,7 @@ dbar_status plan_create_ex(const dbar_params* p, int per_slot_q, dbar_plan** out
   c.tol = p->tol;
   c.inner_tol = P->mixed ? p->inner_tol : 0.0;
   if (cudaMallocHost(&P->h_active, (size_t)B * sizeof(int)) != cudaSuccess ||
+      cudaMallocHost(&P->h_run, (size_t)B * sizeof(int)) != cudaSuccess ||
       cudaMallocHost(&P->hmask, (size_t)B * sizeof(int)) != cudaSuccess ||
       cudaMallocHost(&P->h_nsteps, (size_t)B * sizeof(int)) != cudaSuccess ||
       cudaMallocHost(&P->h_rolls, 2 * (size_t)B * sizeof(int)) != cudaSuccess ||
@@ -2320,6 +2334,43 @@ dbar_status plan_step(dbar_plan* P, int nb, cudaStream_t st) {
   if (P->p.graphs)
     return P->mixed ? graph_cycle<float>(P, nb, st, &launched, false) : graph_cycle<double>(P, nb, st, &launched, false);
   return P->mixed ? one_cycle<float>(P, nb, st, &launched, false) : one_cycle<double>(P, nb, st, &launched, false);
+}
+
+// One part of a cycle: part c < plan_cycle_parts launches Krylov steps
+// [c kGraphChunk, (c + 1) kGraphChunk) and queues a copy of the run flags to page-locked
+// memory (plan_parts_running reads it once the stream has passed this point);
+// part == plan_cycle_parts launches the cycle's tail.  No host synchronisation.
+template <typename TI>
+static dbar_status cycle_part(dbar_plan* P, int nb, int c, cudaStream_t st) {
+  const int nchunks = (P->m + kGraphChunk - 1) / kGraphChunk;
+  if (P->p.graphs) {
+    CycleGraph* g = nullptr;
+    const dbar_status gs = cycle_graph<TI>(P, nb, &g);
+    if (gs != DBAR_OK) return gs;
+    CK(cudaGraphLaunch(g->parts[c].exec, st));
+    P->nlaunch += g->parts[c].kernels;
+    if (P->prof.on) P->graph_ran.push_back(&g->parts[c]);
+  } else {
+    const dbar_status s = c < nchunks ? cycle_steps<TI>(P, nb, c * kGraphChunk, std::min(P->m, (c + 1) * kGraphChunk), st)
+                                      : cycle_tail<TI>(P, nb, st);
+    if (s != DBAR_OK) return s;
+  }
+  if (c < nchunks) CK(cudaMemcpyAsync(P->h_run, P->cs.run, nb * sizeof(int), cudaMemcpyDeviceToHost, st));
+  return DBAR_OK;
+}
+
+int plan_cycle_parts(const dbar_plan* P) { return (P->m + kGraphChunk - 1) / kGraphChunk; }
+
+dbar_status plan_step_part(dbar_plan* P, int nb, int part, cudaStream_t st) {
+  if (!P || nb < 0 || nb > P->B || part < 0 || part > plan_cycle_parts(P))
+    return fail(DBAR_EINVAL, "plan_step_part: bad argument");
+  return P->mixed ? cycle_part<float>(P, nb, part, st) : cycle_part<double>(P, nb, part, st);
+}
+
+bool plan_parts_running(const dbar_plan* P, int nb) {
+  int any = 0;
+  for (int i = 0; i < nb; ++i) any |= P->h_run[i];
+  return any != 0;
 }
 
 dbar_status plan_read_slot(dbar_plan* P, int slot, double* S, double* m, int* itot, int* ncyc, double* resid,

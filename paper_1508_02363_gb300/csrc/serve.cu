@@ -4,7 +4,8 @@
 // parallelise over k).  A server takes requests (N, L, Q, k) from any host
 // thread and solves them on one GPU.  Requests of one grid class (N, L) share
 // a "lane": a plan whose slots each hold one request with its own potential.
-// A single worker thread advances the lanes one GMRES cycle at a time; at
+// A single worker thread advances the lanes one GMRES cycle at a time (each cycle
+// launched in parts, the remaining Krylov chunks skipped once no slot iterates); at
 // every cycle boundary a lane retires its finished slots and admits waiting
 // requests into the free ones, so new work joins while older work is still
 // iterating.  Every slot's arithmetic is independent of the other slots
@@ -111,11 +112,14 @@ struct Lane {
   size_t bytes = 0;
   std::deque<Request*> waiting;
   std::vector<Request*> slot;
-  // completion of the last cycle launched on `stream`: the worker steps a lane only once
-  // its previous cycle has finished, so a long cycle of one grid class never holds up
-  // the cycle boundaries of the others
+  // completion of the last cycle part launched on `stream`: the worker steps a lane only
+  // once that has finished, so a long cycle of one grid class never holds up the
+  // cycle boundaries of the others
   cudaEvent_t done = nullptr;
   bool inflight = false;
+  // the cycle in progress runs part by part (plan_step_part): the next part to launch,
+  // -1 between cycles.  Once no slot iterates, the remaining chunks are skipped.
+  int part = -1;
   bool ready() const { return !inflight || cudaEventQuery(done) != cudaErrorNotReady; }
   bool busy() const {
     if (!waiting.empty()) return true;
@@ -210,6 +214,7 @@ void finish(dbar_server* S, Request* r, int status) {
 // A lane's GPU work failed: re-queue its in-flight requests once, fail repeat
 // offenders, and drop the plan (rebuilt when work arrives).  Caller holds mu.
 void lane_failed(dbar_server* S, Lane* ln, int status) {
+  ln->part = -1;
   for (Request*& r : ln->slot) {
     if (!r) continue;
     if (r->retries++ < 1) {
@@ -232,11 +237,33 @@ void lane_failed(dbar_server* S, Lane* ln, int status) {
 
 // One cycle boundary of one lane: retire, admit, start, advance.  Returns
 // false when the lane could not run (no memory for its plan yet).
+// Records the lane's completion event after what was just queued on its stream.
+void mark_inflight(Lane* ln) {
+  if (!ln->done && cudaEventCreateWithFlags(&ln->done, cudaEventDisableTiming) != cudaSuccess) ln->done = nullptr;
+  ln->inflight = ln->done && cudaEventRecord(ln->done, ln->stream) == cudaSuccess;
+}
+
 bool step_lane(dbar_server* S, Lane* ln) {
   std::unique_lock<std::mutex> lk(S->mu);
   if (!ln->plan && !ln->waiting.empty() && !open_lane(S, ln)) return false;
   if (!ln->plan) return false;
   const int B = ln->B;
+  if (ln->part >= 0) {  // the next part of the cycle in progress (its previous part has finished)
+    lk.unlock();
+    const int np = plan_cycle_parts(ln->plan);
+    int next = ln->part;
+    if (next < np && !plan_parts_running(ln->plan, B)) next = np;  // every slot done: the tail
+    const dbar_status sp = plan_step_part(ln->plan, B, next, ln->stream);
+    lk.lock();
+    if (sp != DBAR_OK) {
+      cudaStreamSynchronize(ln->stream);
+      lane_failed(S, ln, sp);
+      return true;
+    }
+    ln->part = next < np ? next + 1 : -1;
+    mark_inflight(ln);
+    return true;
+  }
   std::vector<int> act(B, 0), mask(B, 0);
   lk.unlock();
   dbar_status st = plan_active(ln->plan, B, act.data(), ln->stream);
@@ -287,10 +314,10 @@ bool step_lane(dbar_server* S, Lane* ln) {
   for (int s = 0; s < B && st == DBAR_OK; ++s)
     if (admit[s]) st = plan_load_slot(ln->plan, s, admit[s]->Q, admit[s]->k1, admit[s]->k2, ln->stream);
   if (st == DBAR_OK && nnew) st = plan_begin(ln->plan, B, mask.data(), ln->stream);
-  if (st == DBAR_OK && occupied) st = plan_step(ln->plan, B, ln->stream);
+  if (st == DBAR_OK && occupied) st = plan_step_part(ln->plan, B, 0, ln->stream);  // first part of a cycle
   if (st == DBAR_OK && occupied) {
-    if (!ln->done && cudaEventCreateWithFlags(&ln->done, cudaEventDisableTiming) != cudaSuccess) ln->done = nullptr;
-    ln->inflight = ln->done && cudaEventRecord(ln->done, ln->stream) == cudaSuccess;
+    ln->part = 1;
+    mark_inflight(ln);
   }
   if (st == DBAR_OK && inject) st = dbar_internal_fail(DBAR_ECUDA, "injected lane failure");
   if (st != DBAR_OK) {
