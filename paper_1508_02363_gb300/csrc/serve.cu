@@ -191,7 +191,16 @@ bool open_lane(dbar_server* S, Lane* ln) {
   B = std::min<int>(B, (int)std::max<size_t>(1, ln->waiting.size() + 8));
   p.max_batch = B;
   dbar_plan* P = nullptr;
-  if (!ln->stream && cudaStreamCreateWithFlags(&ln->stream, cudaStreamNonBlocking) != cudaSuccess) return false;
+  if (!ln->stream) {
+    // larger grids get the higher stream priority: their cycles are the longest, and the
+    // latency tail is theirs; the small grids' short cycles fill the gaps
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);  // lo: least, hi: greatest (numerically lower)
+    int lg = 0;
+    while ((1 << (lg + 1)) <= ln->N) ++lg;
+    const int prio = std::max(hi, lo - std::max(0, lg - 8));  // N <= 256: least; each doubling one step up
+    if (cudaStreamCreateWithPriority(&ln->stream, cudaStreamNonBlocking, prio) != cudaSuccess) return false;
+  }
   if (plan_create_ex(&p, 1, &P) != DBAR_OK) return false;
   ln->plan = P;
   ln->B = plan_batch(P);
