@@ -2326,16 +2326,6 @@ dbar_status plan_active(dbar_plan* P, int nb, int* active, cudaStream_t st) {
   return DBAR_OK;
 }
 
-dbar_status plan_step(dbar_plan* P, int nb, cudaStream_t st) {
-  if (!P || nb < 0 || nb > P->B) return fail(DBAR_EINVAL, "plan_step: bad argument");
-  // the whole cycle is launched without host synchronisation, so a server can
-  // service other plans while this one runs
-  int launched = 0;
-  if (P->p.graphs)
-    return P->mixed ? graph_cycle<float>(P, nb, st, &launched, false) : graph_cycle<double>(P, nb, st, &launched, false);
-  return P->mixed ? one_cycle<float>(P, nb, st, &launched, false) : one_cycle<double>(P, nb, st, &launched, false);
-}
-
 // One part of a cycle: part c < plan_cycle_parts launches Krylov steps
 // [c kGraphChunk, (c + 1) kGraphChunk) and queues a copy of the run flags to page-locked
 // memory (plan_parts_running reads it once the stream has passed this point);

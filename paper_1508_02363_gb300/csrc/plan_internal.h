@@ -26,13 +26,12 @@ dbar_status plan_load_slot(dbar_plan* P, int slot, const double* Q, double k1, d
 dbar_status plan_begin(dbar_plan* P, int nb, const int* hmask, cudaStream_t st);
 // Synchronises the stream and returns each slot's "still iterating" flag.
 dbar_status plan_active(dbar_plan* P, int nb, int* active, cudaStream_t st);
-// Launches one cycle for every active slot among the first nb.
-dbar_status plan_step(dbar_plan* P, int nb, cudaStream_t st);
-// The same cycle in plan_cycle_parts(P) + 1 parts, one per call, without host
-// synchronisation: part c < plan_cycle_parts(P) launches a chunk of Krylov steps and
-// queues a copy of the run flags; once the stream has passed it, plan_parts_running
-// says whether any slot still iterates (if none, the caller launches the tail part,
-// plan_cycle_parts(P), at once instead of the remaining chunks).
+// One cycle for every active slot among the first nb, in plan_cycle_parts(P) + 1
+// parts, one per call, without host synchronisation: part c < plan_cycle_parts(P)
+// launches a chunk of Krylov steps and queues a copy of the run flags; once the stream
+// has passed it, plan_parts_running says whether any slot still iterates (if none, the
+// caller launches the tail part, plan_cycle_parts(P), at once instead of the remaining
+// chunks).
 int plan_cycle_parts(const dbar_plan* P);
 dbar_status plan_step_part(dbar_plan* P, int nb, int part, cudaStream_t st);
 bool plan_parts_running(const dbar_plan* P, int nb);
