@@ -47,6 +47,62 @@ __device__ __forceinline__ double f2d_bits(float f) {
   return __longlong_as_double((long long)b);
 }
 
+// hi + lo (two floats) rounded to double, to nearest with ties to even, in integer
+// arithmetic: the same result as f2d_bits(hi) + f2d_bits(lo), without the FP64 pipe (on
+// GB300 a warp's FP64 add holds that narrow pipe for many cycles).  Both significands
+// are placed in a 64-bit integer (the larger at bit 63's side, the other shifted, its
+// dropped bits kept as a sticky flag), added or subtracted, and the sum is rounded to 53
+// bits.  Zeros, subnormals and non-finite values take the FP64 add.
+__device__ __forceinline__ double dd_sum_rn(float hi, float lo) {
+  unsigned int uh = __float_as_uint(hi), ul = __float_as_uint(lo);
+  if ((ul & 0x7fffffffu) == 0u) return f2d_bits(hi);
+  const unsigned int eh = (uh >> 23) & 0xffu, el = (ul >> 23) & 0xffu;
+  if (eh == 0u || el == 0u || eh == 0xffu || el == 0xffu) return f2d_bits(hi) + f2d_bits(lo);
+  unsigned long long mh = (uh & 0x7fffffu) | 0x800000u, ml = (ul & 0x7fffffu) | 0x800000u;
+  int Eh = (int)eh - 150, El = (int)el - 150;  // value = m 2^E
+  unsigned int nh = uh >> 31, nl = ul >> 31;
+  if (El > Eh || (El == Eh && ml > mh)) {  // the larger magnitude first
+    const unsigned long long tm = mh; mh = ml; ml = tm;
+    const int te = Eh; Eh = El; El = te;
+    const unsigned int tn = nh; nh = nl; nl = tn;
+  }
+  const int d = Eh - El;
+  const unsigned long long A = mh << 39;
+  unsigned long long B = 0ull;
+  bool sticky = false;
+  if (d <= 39) {
+    B = ml << (39 - d);
+  } else if (d < 64) {
+    B = ml >> (d - 39);
+    sticky = (ml & ((1ull << (d - 39)) - 1ull)) != 0ull;
+  } else {
+    sticky = true;
+  }
+  unsigned long long S;
+  if (nh == nl) {
+    S = A + B;
+  } else {
+    S = A - B;
+    if (sticky) S -= 1ull;  // the dropped fraction borrows one unit; it stays sticky
+  }
+  if (S == 0ull) return 0.0;
+  int sh = 11 - __clzll((long long)S);  // bits below the 53 kept
+  unsigned long long q;
+  if (sh > 0) {
+    const unsigned long long rem = S & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    q = S >> sh;
+    if (rem > half || (rem == half && (sticky || (q & 1ull)))) ++q;
+    if (q == (1ull << 53)) {
+      q >>= 1;
+      ++sh;
+    }
+  } else {
+    q = S << (-sh);
+  }
+  const unsigned long long ef = (unsigned long long)(Eh - 39 + sh + 52 + 1023);
+  return __longlong_as_double((long long)(((unsigned long long)nh << 63) | (ef << 52) | (q & ((1ull << 52) - 1ull))));
+}
+
 __global__ void k_dd_to_fp64(const cx<dd>* __restrict__ in, cx<double>* __restrict__ out, long long n) {
   // four independent 16-byte loads in flight per thread before the conversions; both
   // buffers 16-byte aligned
@@ -64,7 +120,7 @@ __global__ void k_dd_to_fp64(const cx<dd>* __restrict__ in, cx<double>* __restri
     for (int u = 0; u < 4; ++u) {
       const long long i = i0 + u * stride;
       if (i < n)
-        dst[i] = make_double2(f2d_bits(v[u].x) + f2d_bits(v[u].y), f2d_bits(v[u].z) + f2d_bits(v[u].w));
+        dst[i] = make_double2(dd_sum_rn(v[u].x, v[u].y), dd_sum_rn(v[u].z, v[u].w));
     }
   }
 }
