@@ -55,7 +55,10 @@ __device__ __forceinline__ double f2d_bits(float f) {
 // bits.  Zeros, subnormals and non-finite values take the FP64 add.
 __device__ __forceinline__ double dd_sum_rn(float hi, float lo) {
   unsigned int uh = __float_as_uint(hi), ul = __float_as_uint(lo);
-  if ((ul & 0x7fffffffu) == 0u) return f2d_bits(hi);
+  if ((ul & 0x7fffffffu) == 0u) {  // lo = +-0: hi, or a zero whose sign the FP64 add would give
+    if ((uh & 0x7fffffffu) == 0u) return ((uh & ul) >> 31) ? -0.0 : 0.0;
+    return f2d_bits(hi);
+  }
   const unsigned int eh = (uh >> 23) & 0xffu, el = (ul >> 23) & 0xffu;
   if (eh == 0u || el == 0u || eh == 0xffu || el == 0xffu) return f2d_bits(hi) + f2d_bits(lo);
   unsigned long long mh = (uh & 0x7fffffu) | 0x800000u, ml = (ul & 0x7fffffu) | 0x800000u;
